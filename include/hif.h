@@ -1,0 +1,185 @@
+/*
+ * hif.h -- C ABI of the GB300 (sm_103a) HIF-IE library.
+ *
+ * The library factors the dense matrix of a discretized integral equation
+ * (Sec. 1, Eq. (1.1); Sec. 3.1, Eq. (3.1))
+ *
+ *      A = diag(a) + diag(b) K diag(c),     K_ij = G(|x_i - x_j|) w_j   (i != j),
+ *                                          K_ii = integral of G over the cell of x_i,
+ *
+ * with G the Laplace kernel of Eq. (1.3) (kernel_id 0: -log(r)/(2 pi) in 2D,
+ * kernel_id 1: 1/(4 pi r) in 3D), by the hierarchical interpolative
+ * factorization HIF-IE (Sec. 4, Algorithms 4.1 and 4.2, with the second-kind
+ * modifications of Sec. 4.4), and applies the factorization F ~ A and its
+ * inverse in factored form (Eqs. (4.1), (4.2)).  The cell of DOF i is the
+ * square/cube of volume w_i centred at x_i; its self term is the exact
+ * integral in closed form.
+ *
+ * Conventions common to every call
+ *  - Pointers: arrays may live in host memory or in device memory of the
+ *    current CUDA device; the library inspects each pointer and copies host
+ *    arrays to the device itself.  The caller keeps ownership of every array
+ *    it passes; the handle copies what it keeps.
+ *  - Points are N x dim, row-major (x_0, y_0[, z_0], x_1, ...), FP64.
+ *  - Vectors are FP64, column-major N x nrhs with leading dimension ld >= N.
+ *  - Work is issued on the stream given in hif_options (NULL = legacy default
+ *    stream); every call returns after its results are complete.
+ *  - Errors are returned as hif_status, never thrown.  On failure *out is
+ *    set to NULL and nothing is leaked.  A handle is not thread-safe.
+ */
+#ifndef HIF_H
+#define HIF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hif_handle_s* hif_handle;
+
+typedef enum {
+    HIF_OK = 0,
+    HIF_EINVAL = 1,      /* bad argument (size, pointer, option)               */
+    HIF_ENOMEM = 2,      /* device or host allocation failed                   */
+    HIF_ESINGULAR = 3,   /* zero pivot in an elimination block (Lemma 2.1)     */
+    HIF_ENUMERIC = 4,    /* NaN/Inf produced or met in the inputs              */
+    HIF_ECUDA = 5,       /* a CUDA runtime call failed                         */
+    HIF_ETIMEOUT = 6,    /* a bounded device-side wait gave up                 */
+    HIF_ENOTCONV = 7     /* iterative refinement / GMRES missed its tolerance  */
+} hif_status;
+
+typedef struct {
+    int dim;                /* 2 or 3                                                      */
+    int leaf_occupancy;     /* max DOFs per finest cell; sets the depth L (default 64)     */
+    int second_kind;        /* 1: Sec. 4.4 modifications (rho_g tolerance, split groups)   */
+    int precision;          /* 0: FP64 factorization, 1: FP32 factorization                */
+    int fractional_levels;  /* 1: HIF-IE (cells + edges[/faces]); 0: RSF (cells only)      */
+    int skip_levels;        /* skip the fractional sublevels of the first skip_levels levels */
+    int proxy_points;       /* number of proxy points P (64 in 2D, 512 in 3D, Sec. 3.3)    */
+    double proxy_radius;    /* proxy radius in units of the cell width (1.5, Sec. 3.3)     */
+    const double* proxy_dirs; /* P x dim unit vectors (host or device); NULL = 2D circle   */
+    double fp32_tol_floor;  /* FP32 factorization: local ID tolerance >= this (2^-20)      */
+    double root_lo[3];      /* root box lower corner; used when root_width > 0            */
+    double root_width;      /* <= 0: bounding cube of the DOF cells                        */
+    void* stream;           /* cudaStream_t                                                */
+} hif_options;
+
+typedef struct {
+    int64_t N;
+    int dim;
+    int levels;             /* L                                                           */
+    int sublevels;          /* skeletonization sublevels actually run                      */
+    int64_t top_size;       /* |s_L|                                                       */
+    int64_t factor_bytes;   /* m_f: bytes held by the factors (T, L, D, U, X, Y, top LU)   */
+    int64_t skeletons[64];  /* per sublevel: sum of skeleton sizes                         */
+    int64_t redundant[64];  /* per sublevel: sum of redundant sizes                        */
+    int64_t boxes[64];      /* per sublevel: number of non-empty boxes                     */
+    int kinds[64];          /* per sublevel: 0 cell, 1 face, 2 edge                        */
+    int max_box[64];        /* per sublevel: largest |c|                                   */
+    double factor_seconds;  /* wall time of hif_factor                                     */
+    double flops;           /* algorithmic FP work of the factorization (see DESIGN)       */
+    double kernel_evals;    /* kernel evaluations spent on the proxy matrices Y_c          */
+} hif_stats_t;
+
+/* Defaults for dimension dim (2 or 3): occupancy 64, second_kind 1, FP64,
+ * fractional levels on, proxy 64 points (2D) / 512 (3D) at radius 1.5,
+ * fp32_tol_floor 2^-20, bounding-cube root box, default stream. */
+hif_status hif_options_default(int dim, hif_options* opt);
+
+/*
+ * hif_factor -- HIF-IE of A (Algorithm 4.1 for dim 2, Algorithm 4.2 for dim 3).
+ *   points   N x dim collocation points (row-major)
+ *   weights  N cell volumes w_j (quadrature weights of Eq. (3.1))
+ *   a, b, c  N samples of the coefficient functions of Eq. (1.1)
+ *   kernel_id 0 (2D log kernel) or 1 (3D 1/r kernel), must match dim
+ *   eps      base relative precision of the interpolative decompositions (>= 0)
+ *   opt      options (NULL = hif_options_default(2))
+ *   out      receives the handle (NULL on failure)
+ * Errors: HIF_EINVAL on bad sizes/options, HIF_ENOMEM, HIF_ESINGULAR when an
+ * elimination block B_rr (Lemma 2.3) or the top block is singular,
+ * HIF_ENUMERIC on non-finite input or results, HIF_ECUDA.
+ */
+hif_status hif_factor(const double* points, int64_t N, const double* weights,
+                      const double* a, const double* b, const double* c,
+                      int kernel_id, double eps, const hif_options* opt, hif_handle* out);
+
+/* y = F x  (Eq. (4.1) first line; generalized FMM).  x, y: N x nrhs, ld >= N. */
+hif_status hif_apply(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld);
+/* y = F^T x. */
+hif_status hif_apply_transpose(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld);
+/* x = F^{-1} b  (Eq. (4.1) second line; direct solver / preconditioner). */
+hif_status hif_solve(hif_handle h, const double* b, double* x, int64_t nrhs, int64_t ld);
+/* x = F^{-T} b. */
+hif_status hif_solve_transpose(hif_handle h, const double* b, double* x, int64_t nrhs, int64_t ld);
+
+/*
+ * hif_matvec -- y = A x (trans = 0) or y = A^T x (trans = 1) by FP64 direct
+ * summation over all N^2 pairs, exactly the operator the handle factored
+ * (same quadrature, same self terms).  x, y: N x nrhs, ld >= N.
+ */
+hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y,
+                      int64_t nrhs, int64_t ld);
+
+/*
+ * hif_solve_refined -- solve A u = f (trans = 0) or A^T u = f (trans = 1) to
+ * relative residual |f - A u| / |f| <= tol per column, with F^{-1} as right
+ * preconditioner: method 0 = iterative refinement u += F^{-1}(f - A u),
+ * method 1 = right-preconditioned restarted GMRES(20) with modified
+ * Gram-Schmidt (Sec. 5).  Residuals use hif_matvec (FP64 direct sum).
+ *   iters   (may be NULL) receives the largest iteration count over columns
+ *   relres  (may be NULL) receives the largest final relative residual
+ * Returns HIF_ENOTCONV (with u holding the last iterate) when maxit is reached.
+ */
+hif_status hif_solve_refined(hif_handle h, int trans, const double* f, double* u,
+                             int64_t nrhs, int64_t ld, double tol, int maxit, int method,
+                             int* iters, double* relres);
+
+/* Factorization statistics (Sec. 5 columns |s_L|, m_f, t_f and ranks per sublevel). */
+hif_status hif_stats(hif_handle h, hif_stats_t* st);
+
+/* Releases every resource the handle owns.  NULL is accepted. */
+hif_status hif_destroy(hif_handle h);
+
+/* Static, human-readable name of a status code. */
+const char* hif_status_string(hif_status s);
+
+/* Detail of the last failure on the calling thread (file:line and the CUDA
+ * error text when the failure came from the runtime); empty if none. */
+const char* hif_last_error(void);
+
+/*
+ * hif_kernel_block -- entries A_ij = a_i delta_ij + b_i K_ij c_j (Eq. (3.1))
+ * for i in rows[0..nr), j in cols[0..nc), written column-major to
+ * out (nr x nc, leading dimension ldo >= nr).  All arrays on the device or all
+ * on the host.  Entries are generated on demand (Sec. 3.1: A is never stored).
+ */
+hif_status hif_kernel_block(const double* points, int64_t N, int dim, const double* weights,
+                            const double* a, const double* b, const double* c, int kernel_id,
+                            const int32_t* rows, int64_t nr, const int32_t* cols, int64_t nc,
+                            double* out, int64_t ldo, void* stream);
+
+/*
+ * hif_id_batched -- interpolative decompositions of `count` independent
+ * matrices by column-pivoted Householder QR (Sec. 2.2, Lemma 2.2) with
+ * adaptive rank: k = number of pivots with |R_jj| > tol[i] |R_11|.
+ *   mats    column-major m[i] x n[i] blocks at offsets off[i] (FP64, device or host)
+ *   tol     per-matrix relative tolerance
+ *   k       out: rank per matrix
+ *   perm    out: n[i] column indices per matrix at poff[i]: skeletons in pivot
+ *           order, then redundant columns in ascending order
+ *   T       out: k[i] x (n[i]-k[i]) column-major at toff[i] (room for n[i]^2/4
+ *           doubles must be reserved)
+ * The pivot is the remaining column of largest 2-norm (ties: lowest index);
+ * norms are recomputed exactly after each step.
+ */
+hif_status hif_id_batched(int count, const double* mats, const int64_t* off,
+                          const int32_t* m, const int32_t* n, const double* tol,
+                          int32_t* k, int32_t* perm, const int64_t* poff,
+                          double* T, const int64_t* toff, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIF_H */

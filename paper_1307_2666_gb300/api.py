@@ -1,0 +1,150 @@
+"""torch-facing wrappers of the C ABI: one factorization handle per object,
+and the autograd function of the adjoint method.  Argument marshalling only;
+the arithmetic runs in the library's kernels."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import hif as _h
+
+
+def _colmajor(x: torch.Tensor) -> torch.Tensor:
+    """View/copy of an (N,) or (N, nrhs) FP64 tensor in column-major layout."""
+    if x.dtype != torch.float64:
+        raise TypeError("vectors must be float64")
+    if x.ndim == 1:
+        return x.contiguous()
+    if x.stride(0) == 1 and x.stride(1) >= x.shape[0]:
+        return x
+    return x.t().contiguous().t()
+
+
+def _empty_like_cm(x: torch.Tensor) -> torch.Tensor:
+    if x.ndim == 1:
+        return torch.empty_like(x)
+    return torch.empty((x.shape[1], x.shape[0]), dtype=x.dtype, device=x.device).t()
+
+
+class Factorization:
+    """HIF-IE factorization F ~ A of A = diag(a) + diag(b) K diag(c).
+
+    points (N, dim), weights/a/b/c (N,) FP64 tensors (CUDA or CPU).
+    precision: "fp64" or "fp32" (factorization precision; vectors stay FP64).
+    """
+
+    def __init__(self, points, weights, a, b, c, kernel_id: int, eps: float, *, precision: str = "fp64",
+                 second_kind: bool = True, occupancy: int = 64, proxy_dirs=None, fractional: bool = True,
+                 skip_levels: int = 0, proxy_radius: float = 1.5, fp32_tol_floor: float | None = None,
+                 root=None, stream=None):
+        dim = points.shape[1]
+        opt = _h.hif_options_default(dim)
+        opt.leaf_occupancy = int(occupancy)
+        opt.second_kind = 1 if second_kind else 0
+        opt.precision = 0 if precision == "fp64" else 1
+        opt.fractional_levels = 1 if fractional else 0
+        opt.skip_levels = int(skip_levels)
+        opt.proxy_radius = float(proxy_radius)
+        self._keep = []
+        if proxy_dirs is not None:
+            pd = np.ascontiguousarray(np.asarray(proxy_dirs.cpu() if hasattr(proxy_dirs, "cpu") else proxy_dirs,
+                                                 dtype=np.float64))
+            self._keep.append(pd)
+            opt.proxy_points = pd.shape[0]
+            opt.proxy_dirs = pd.ctypes.data
+        if fp32_tol_floor is not None:
+            opt.fp32_tol_floor = float(fp32_tol_floor)
+        if root is not None:
+            lo, width = root
+            for k in range(dim):
+                opt.root_lo[k] = float(lo[k])
+            opt.root_width = float(width)
+        if stream is not None:
+            opt.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self.N, self.dim = points.shape
+        self.kernel_id = kernel_id
+        self.eps = eps
+        self.device = points.device if hasattr(points, "device") else torch.device("cpu")
+        self.a, self.b, self.c = a, b, c
+        self.h = _h.hif_factor(points.contiguous(), weights.contiguous(), a.contiguous(), b.contiguous(),
+                               c.contiguous(), kernel_id, eps, opt)
+
+    # -- factored operators ------------------------------------------------
+    def _op(self, fn, x):
+        xin = _colmajor(x)
+        out = _empty_like_cm(xin)
+        fn(self.h, xin, out)
+        return out
+
+    def solve(self, b):
+        return self._op(_h.hif_solve, b)
+
+    def solve_transpose(self, b):
+        return self._op(_h.hif_solve_transpose, b)
+
+    def apply(self, x):
+        return self._op(_h.hif_apply, x)
+
+    def apply_transpose(self, x):
+        return self._op(_h.hif_apply_transpose, x)
+
+    def matvec(self, x, trans: bool = False):
+        xin = _colmajor(x)
+        out = _empty_like_cm(xin)
+        _h.hif_matvec(self.h, 1 if trans else 0, xin, out)
+        return out
+
+    def solve_refined(self, f, trans: bool = False, tol: float = 1e-10, maxit: int = 50, method: str = "ir"):
+        fin = _colmajor(f)
+        out = _empty_like_cm(fin)
+        st, its, rel = _h.hif_solve_refined(self.h, 1 if trans else 0, fin, out, tol, maxit,
+                                            0 if method == "ir" else 1)
+        return out, its, rel
+
+    def stats(self) -> dict:
+        return _h.hif_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _h.hif_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HIFSolve(torch.autograd.Function):
+    """u = A^{-1} f through a refined solve with the factorization as
+    preconditioner; backward is the adjoint method:
+
+        lambda = A^{-T} g            (transposed refined solve)
+        dL/df = lambda,  dL/da = -lambda * u,
+        dL/db = -lambda * K(c u),     K(c u)     = (F u - a u) / b,
+        dL/dc = -u * K^T(b lambda),   K^T(b l)   = (F^T lambda - a lambda) / c,
+
+    with F the factorization's fast apply.  ``fac`` must have been built from
+    the same a, b, c."""
+
+    @staticmethod
+    def forward(ctx, f, a, b, c, fac: Factorization, tol: float = 1e-12):
+        u, _, _ = fac.solve_refined(f, tol=tol)
+        ctx.fac = fac
+        ctx.tol = tol
+        ctx.save_for_backward(u, a, b, c)
+        return u
+
+    @staticmethod
+    def backward(ctx, g):
+        u, a, b, c = ctx.saved_tensors
+        fac = ctx.fac
+        lam, _, _ = fac.solve_refined(g.contiguous(), trans=True, tol=ctx.tol)
+        Fu = fac.apply(u)
+        Ftl = fac.apply_transpose(lam)
+        Kcu = (Fu - a * u) / b
+        Ktbl = (Ftl - a * lam) / c
+        return lam, -lam * u, -lam * Kcu, -u * Ktbl, None, None

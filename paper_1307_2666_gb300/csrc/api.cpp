@@ -1,0 +1,1150 @@
+// C ABI of the HIF-IE library: factorization driver (Algorithms 4.1 / 4.2),
+// apply / solve sweeps, FP64 direct-sum operator and refinement loops.
+//
+// The host runs the integer bookkeeping of each sublevel (geometry.cpp) and
+// launches the floating-point work: per sublevel one fold launch (proxy
+// matrices folded into R factors), one ID launch over all column groups and
+// one elimination launch; the host reads back only the ranks and skeleton
+// permutations it needs to form the next sublevel.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hif.h"
+#include "geometry.h"
+#include "launch.h"
+
+namespace hif {
+
+// ------------------------------------------------------------ plumbing --
+
+struct Err {
+    hif_status s;
+};
+
+#define HIF_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            std::snprintf(g_last_error, sizeof(g_last_error), "%s:%d %s: %s", __FILE__, \
+                          __LINE__, #call, cudaGetErrorString(e_));                     \
+            throw Err{e_ == cudaErrorMemoryAllocation ? HIF_ENOMEM : HIF_ECUDA};        \
+        }                                                                               \
+    } while (0)
+
+static thread_local char g_last_error[512];
+
+static void fail(hif_status s, const char* msg) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+    throw Err{s};
+}
+
+// Device allocation that frees itself.
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void* ensure(size_t b) {
+        if (b <= bytes && p) return p;
+        release();
+        const size_t want = std::max<size_t>(b, 256);
+        HIF_CUDA(cudaMalloc(&p, want));
+        bytes = want;
+        return p;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <typename T>
+static void upload(DevMem& d, const std::vector<T>& h, cudaStream_t st) {
+    d.ensure(h.size() * sizeof(T));
+    if (!h.empty()) HIF_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Input array: device pointer used in place, host array copied.
+struct InArr {
+    const double* d = nullptr;
+    DevMem own;
+    void set(const double* p, size_t count, cudaStream_t st) {
+        if (is_device_ptr(p)) {
+            d = p;
+        } else {
+            own.ensure(count * sizeof(double));
+            HIF_CUDA(cudaMemcpyAsync(own.p, p, count * sizeof(double), cudaMemcpyHostToDevice, st));
+            d = own.as<double>();
+        }
+    }
+};
+
+struct SubFactor {
+    int kind = 0, level = 0;
+    int nbox = 0;                  // boxes with r > 0
+    std::vector<BoxFac> hbox;
+    DevMem boxes, sk, rd, pool, perm;
+    int max_kr2 = 0;               // max over boxes of k + 2 r
+};
+
+}  // namespace hif
+
+struct hif_handle_s {
+    int dim = 2, kernel_id = 0, precision = 0, second_kind = 1;
+    int64_t N = 0;
+    double eps = 0;
+    hif_options opt{};
+    cudaStream_t st = nullptr;
+    int elem = 8;
+    hif::DevMem x, w, a, b, c, kself, proxy;
+    std::vector<double> hx, hw;
+    hif::Tree tree{};
+    int P = 0;
+    // SCI store
+    hif::DevMem sci_blk, sci_loc, blk_ptr, blk_k;
+    std::vector<void*> blk_ptr_h;
+    std::vector<int> blk_k_h;
+    std::vector<std::unique_ptr<hif::DevMem>> sci_pools;
+    // factors
+    std::vector<std::unique_ptr<hif::SubFactor>> subs;
+    int nL = 0;
+    hif::DevMem top_ids, topA, topLU, top_piv, topInv;
+    // uniform grid for the direct sum
+    bool grid = false;
+    int gn = 0;
+    double gh = 0;
+    hif::DevMem dof_of, table, vbuf, ybuf;
+    // work buffers
+    hif::DevMem work, work2, tmp, status;
+    hif_stats_t stats{};
+};
+
+namespace hif {
+
+static GeomDev geom(hif_handle h) {
+    GeomDev g;
+    g.x = h->x.as<double>();
+    g.w = h->w.as<double>();
+    g.a = h->a.as<double>();
+    g.b = h->b.as<double>();
+    g.c = h->c.as<double>();
+    g.kself = h->kself.as<double>();
+    g.N = h->N;
+    g.dim = h->dim;
+    g.kernel_id = h->kernel_id;
+    return g;
+}
+
+static SciDev scidev(hif_handle h, int nsub) {
+    SciDev s;
+    s.blk = h->sci_blk.as<int>();
+    s.loc = h->sci_loc.as<int>();
+    s.ptr = h->blk_ptr.as<void*>();
+    s.kb = h->blk_k.as<int>();
+    s.nsub = nsub;
+    s.N = h->N;
+    return s;
+}
+
+static void check_status(hif_handle h) {
+    int st = 0;
+    HIF_CUDA(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    HIF_CUDA(cudaStreamSynchronize(h->st));
+    if (st & DEV_SINGULAR) fail(HIF_ESINGULAR, "zero pivot in an elimination block");
+    if (st & DEV_NONFINITE) fail(HIF_ENUMERIC, "non-finite value in the factorization");
+}
+
+// Detect a full uniform tensor grid: x = lo + h (idx + 1/2), equal weights h^d.
+static void detect_grid(hif_handle h) {
+    h->grid = false;
+    const int d = h->dim;
+    const int64_t N = h->N;
+    const int n = (int)std::llround(std::pow((double)N, 1.0 / d));
+    int64_t nn = 1;
+    for (int k = 0; k < d; ++k) nn *= n;
+    if (n < 2 || nn != N) return;
+    double lo[3], hx = 0;
+    for (int k = 0; k < d; ++k) {
+        double mn = h->hx[k], mx = h->hx[k];
+        for (int64_t i = 0; i < N; ++i) {
+            mn = std::min(mn, h->hx[d * i + k]);
+            mx = std::max(mx, h->hx[d * i + k]);
+        }
+        const double hk = (mx - mn) / (n - 1);
+        if (k == 0) hx = hk;
+        if (std::fabs(hk - hx) > 1e-12 * hx) return;
+        lo[k] = mn;
+    }
+    const double wv = h->hw[0];
+    for (int64_t i = 0; i < N; ++i)
+        if (h->hw[i] != wv) return;
+    if (std::fabs(std::pow(wv, 1.0 / d) - hx) > 1e-9 * hx) return;
+    std::vector<int> dof_of(N, -1);
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t gpos = 0;
+        for (int k = 0; k < d; ++k) {
+            const double t = (h->hx[d * i + k] - lo[k]) / hx;
+            const int64_t id = std::llround(t);
+            if (id < 0 || id >= n || std::fabs(t - id) > 1e-6) return;
+            gpos = gpos * n + id;
+        }
+        if (dof_of[gpos] != -1) return;
+        dof_of[gpos] = (int)i;
+    }
+    // the one-point rule gives K_ij = G(h |i - j|) w exactly when the
+    // coordinates are exactly lo + h idx; require that to within rounding
+    h->grid = true;
+    h->gn = n;
+    h->gh = hx;
+    upload(h->dof_of, dof_of, h->st);
+}
+
+template <typename T>
+static void run_factor(hif_handle h) {
+    const cudaStream_t st = h->st;
+    const int d = h->dim;
+    const int64_t N = h->N;
+    const GeomDev g = geom(h);
+    Tree& t = h->tree;
+    t.dim = d;
+    if (h->opt.root_width > 0) {
+        for (int k = 0; k < 3; ++k) t.lo[k] = h->opt.root_lo[k];
+        t.W = h->opt.root_width;
+    } else {
+        root_box(h->hx.data(), h->hw.data(), N, d, t.lo, &t.W);
+    }
+    t.L = num_levels(h->hx.data(), N, d, t.lo, t.W, h->opt.leaf_occupancy);
+    std::vector<int> kinds, levels;
+    plan_sublevels(d, t.L, h->opt.fractional_levels != 0, h->opt.skip_levels, kinds, levels);
+    if ((int)kinds.size() > kMaxSub) fail(HIF_EINVAL, "too many sublevels");
+
+    h->sci_blk.ensure(sizeof(int) * (size_t)kMaxSub * N);
+    h->sci_loc.ensure(sizeof(int) * (size_t)kMaxSub * N);
+    HIF_CUDA(cudaMemsetAsync(h->sci_blk.p, 0xff, sizeof(int) * (size_t)kMaxSub * N, st));
+    HIF_CUDA(cudaMemsetAsync(h->sci_loc.p, 0, sizeof(int) * (size_t)kMaxSub * N, st));
+    h->status.ensure(sizeof(int));
+    HIF_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), st));
+
+    SciHost sci;
+    std::vector<char> active(N, 1);
+    std::vector<int> box_of(N, -1);
+    DevMem d_boxes, d_groups, d_cols, d_near, Rws, GKws, GSws, Tws, Wws, Woff, perm_out, k_out;
+    DevMem d_ed, d_eg, d_sk, d_rd, ews, piv_scratch;
+    double flops = 0, evals = 0;
+    const double tol_floor = sizeof(T) == 4 ? h->opt.fp32_tol_floor : 0.0;
+
+    for (size_t tau = 0; tau < kinds.size(); ++tau) {
+        const int kind = kinds[tau], ell = levels[tau];
+        const int s = 1 << (t.L - ell);
+        const double wl = t.W / s;
+        std::vector<int> act_ids;
+        act_ids.reserve(N);
+        for (int64_t i = 0; i < N; ++i)
+            if (active[i]) act_ids.push_back((int)i);
+        for (int i : act_ids) box_of[i] = -1;
+        SublevelPlan p;
+        partition(t, h->hx.data(), kind, s, act_ids, p, box_of);
+        build_near_groups(t, h->hx.data(), s, h->opt.proxy_radius, h->second_kind, act_ids, active, box_of, sci, p);
+        const int nb = p.nbox;
+        const int64_t ngr = p.grp_off[nb];
+
+        // ---- descriptors for the fold and ID launches
+        std::vector<BoxDesc> bd(nb);
+        std::vector<GroupDesc> gd(ngr);
+        int64_t Roff = 0, Toff = 0, Woffs = 0;
+        int maxn = 0, maxng = 0, maxmrow = 0;
+        bool any_sci = false;
+        std::vector<int64_t> woff(ngr);
+        for (int bI = 0; bI < nb; ++bI) {
+            BoxDesc& b = bd[bI];
+            b.n = (int)(p.box_off[bI + 1] - p.box_off[bI]);
+            b.m_near = (int)(p.near_off[bI + 1] - p.near_off[bI]);
+            b.ngroups = (int)(p.grp_off[bI + 1] - p.grp_off[bI]);
+            b.has_sci = p.box_sci[bI];
+            any_sci = any_sci || b.has_sci;
+            b.col_off = p.box_off[bI];
+            b.near_off = p.near_off[bI];
+            b.grp_off = p.grp_off[bI];
+            b.R_off = Roff;
+            Roff += (int64_t)b.n * b.n;
+            for (int k = 0; k < 3; ++k) b.ctr[k] = p.centers[3 * bI + k];
+            b.radius = h->opt.proxy_radius * wl;
+            maxn = std::max(maxn, b.n);
+            const double m = 2.0 * (b.m_near + h->P);
+            evals += (m / 2) * b.n;
+            flops += 2.0 * m * b.n * b.n;
+            for (int q = 0; q < b.ngroups; ++q) {
+                const int64_t gi = b.grp_off + q;
+                GroupDesc& G = gd[gi];
+                G.box = bI;
+                G.col0 = p.grp_col0[gi];
+                G.n = p.grp_n[gi];
+                G.has_sci = p.grp_sci[gi];
+                G.T_off = Toff;
+                Toff += (int64_t)G.n * G.n;
+                G.perm_off = b.col_off + G.col0;
+                const int mrow = G.col0 + G.n;
+                woff[gi] = Woffs;
+                Woffs += (int64_t)(mrow | 1) * G.n;
+                maxng = std::max(maxng, G.n);
+                maxmrow = std::max(maxmrow, mrow);
+            }
+        }
+        upload(d_boxes, bd, st);
+        upload(d_groups, gd, st);
+        upload(d_cols, p.cols, st);
+        upload(d_near, p.near, st);
+        upload(Woff, woff, st);
+        Rws.ensure(sizeof(T) * std::max<int64_t>(Roff, 1));
+        const bool grams = h->second_kind && any_sci;
+        if (grams) {
+            GKws.ensure(sizeof(T) * Roff);
+            GSws.ensure(sizeof(T) * Roff);
+        }
+        Tws.ensure(sizeof(T) * std::max<int64_t>(Toff, 1));
+        perm_out.ensure(sizeof(int) * std::max<size_t>(p.cols.size(), 1));
+        k_out.ensure(sizeof(int) * std::max<int64_t>(ngr, 1));
+
+        FoldArgs fa{};
+        fa.g = g;
+        fa.sci = scidev(h, (int)tau);
+        fa.boxes = d_boxes.as<BoxDesc>();
+        fa.cols = d_cols.as<int>();
+        fa.near = d_near.as<int>();
+        fa.groups = d_groups.as<GroupDesc>();
+        fa.proxy = h->proxy.as<double>();
+        fa.P = h->P;
+        fa.bpairs = 16;
+        fa.second_kind = h->second_kind;
+        fa.Rws = Rws.p;
+        fa.GKws = grams ? GKws.p : nullptr;
+        fa.GSws = grams ? GSws.p : nullptr;
+        size_t smem = fold_smem_bytes(maxn, fa.bpairs, grams, true, sizeof(T));
+        fa.R_in_smem = smem <= 200 * 1024;
+        if (!fa.R_in_smem) {
+            fa.bpairs = maxn > 512 ? 4 : 8;
+            smem = fold_smem_bytes(maxn, fa.bpairs, grams, false, sizeof(T));
+            if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
+        }
+        HIF_CUDA((launch_fold<T>(fa, nb, smem, st)));
+
+        IdArgs ia{};
+        ia.groups = d_groups.as<GroupDesc>();
+        ia.boxes = d_boxes.as<BoxDesc>();
+        ia.Rws = Rws.p;
+        ia.GKws = grams ? GKws.p : nullptr;
+        ia.GSws = grams ? GSws.p : nullptr;
+        ia.second_kind = h->second_kind;
+        ia.Tws = Tws.p;
+        ia.perm_out = perm_out.as<int>();
+        ia.k_out = k_out.as<int>();
+        ia.eps = h->eps;
+        ia.tol_floor = tol_floor;
+        size_t ismem = id_smem_bytes(maxng, maxmrow, true, sizeof(T));
+        ia.W_in_smem = ismem <= 200 * 1024;
+        if (!ia.W_in_smem) {
+            Wws.ensure(sizeof(T) * std::max<int64_t>(Woffs, 1));
+            ismem = id_smem_bytes(maxng, maxmrow, false, sizeof(T));
+        }
+        ia.Wws = Wws.p;
+        ia.W_off = Woff.as<int64_t>();
+        HIF_CUDA((launch_id<T>(ia, (int)ngr, ismem, st)));
+
+        std::vector<int> kg(ngr), permh(p.cols.size());
+        if (ngr) HIF_CUDA(cudaMemcpyAsync(kg.data(), k_out.p, sizeof(int) * ngr, cudaMemcpyDeviceToHost, st));
+        if (!permh.empty())
+            HIF_CUDA(cudaMemcpyAsync(permh.data(), perm_out.p, sizeof(int) * permh.size(), cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaStreamSynchronize(st));
+
+        // ---- skeleton / redundant sets, elimination descriptors
+        auto sf = std::make_unique<SubFactor>();
+        sf->kind = kind;
+        sf->level = ell;
+        std::vector<ElimDesc> ed;
+        std::vector<ElimGroup> eg;
+        std::vector<int> skv, rdv;
+        int64_t fac_off = 0, piv_off = 0, sci_off = 0, ws_off = 0;
+        struct NewBlock { int box; int64_t sk_off; int k; int64_t sci_off; };
+        std::vector<NewBlock> nblk;
+        int64_t ksum = 0, rsum = 0;
+        int maxbox = 0;
+        for (int bI = 0; bI < nb; ++bI) {
+            const BoxDesc& b = bd[bI];
+            maxbox = std::max(maxbox, b.n);
+            int k = 0, r = 0;
+            for (int q = 0; q < b.ngroups; ++q) {
+                k += kg[b.grp_off + q];
+                r += gd[b.grp_off + q].n - kg[b.grp_off + q];
+            }
+            ksum += k;
+            rsum += r;
+            if (r == 0) continue;
+            ElimDesc e{};
+            e.k = k;
+            e.r = r;
+            e.ngroups = b.ngroups;
+            e.sk_off = (int64_t)skv.size();
+            e.rd_off = (int64_t)rdv.size();
+            e.grp_off = (int64_t)eg.size();
+            int ko = 0, ro = 0;
+            for (int q = 0; q < b.ngroups; ++q) {
+                const GroupDesc& G = gd[b.grp_off + q];
+                const int kq = kg[b.grp_off + q];
+                for (int l = 0; l < kq; ++l) skv.push_back(p.cols[b.col_off + G.col0 + permh[G.perm_off + l]]);
+                ElimGroup E{};
+                E.kg = kq;
+                E.rg = G.n - kq;
+                E.ko = ko;
+                E.ro = ro;
+                E.T_off = G.T_off;
+                eg.push_back(E);
+                ko += kq;
+                ro += G.n - kq;
+            }
+            for (int q = 0; q < b.ngroups; ++q) {
+                const GroupDesc& G = gd[b.grp_off + q];
+                const int kq = kg[b.grp_off + q];
+                for (int l = kq; l < G.n; ++l) rdv.push_back(p.cols[b.col_off + G.col0 + permh[G.perm_off + l]]);
+            }
+            const int n = k + r;
+            e.ws_off = ws_off;
+            ws_off += (int64_t)n * n + (int64_t)k * r;
+            e.T_out = fac_off; fac_off += (int64_t)k * r;
+            e.LU_out = fac_off; fac_off += (int64_t)r * r;
+            e.LUi_out = fac_off; fac_off += (int64_t)r * r;
+            e.D_out = fac_off; fac_off += r;
+            e.X_out = fac_off; fac_off += (int64_t)k * r;
+            e.Y_out = fac_off; fac_off += (int64_t)r * k;
+            e.piv_out = piv_off; piv_off += r;
+            if (k > 0) {
+                e.sci_out = sci_off;
+                nblk.push_back({bI, e.sk_off, k, sci_off});
+                sci_off += (int64_t)k * k;
+            } else {
+                e.sci_out = -1;
+            }
+            BoxFac bf{};
+            bf.k = k;
+            bf.r = r;
+            bf.sk_off = e.sk_off;
+            bf.rd_off = e.rd_off;
+            bf.T_off = e.T_out;
+            bf.LU_off = e.LU_out;
+            bf.LUi_off = e.LUi_out;
+            bf.D_off = e.D_out;
+            bf.X_off = e.X_out;
+            bf.Y_off = e.Y_out;
+            bf.piv_off = e.piv_out;
+            sf->hbox.push_back(bf);
+            sf->max_kr2 = std::max(sf->max_kr2, k + 2 * r);
+            ed.push_back(e);
+            const double kk = k, rr = r;
+            flops += 2.0 * (kk * kk * rr + 2 * kk * rr * rr + kk * kk * rr) + 2.0 / 3.0 * rr * rr * rr +
+                     2.0 * kk * rr * rr + 2.0 * kk * kk * rr;
+        }
+        sf->nbox = (int)ed.size();
+        h->stats.kinds[tau] = kind;
+        h->stats.boxes[tau] = nb;
+        h->stats.skeletons[tau] = ksum;
+        h->stats.redundant[tau] = rsum;
+        h->stats.max_box[tau] = maxbox;
+
+        // SCI pool of this sublevel and the block table
+        auto pool = std::make_unique<DevMem>();
+        pool->ensure(sizeof(T) * std::max<int64_t>(sci_off, 1));
+        const int first_block = (int)h->blk_k_h.size();
+        for (const NewBlock& nbk : nblk) {
+            h->blk_ptr_h.push_back(static_cast<char*>(pool->p) + sizeof(T) * nbk.sci_off);
+            h->blk_k_h.push_back(nbk.k);
+        }
+        if (sf->nbox) {
+            upload(d_ed, ed, st);
+            upload(d_eg, eg, st);
+            upload(sf->sk, skv, st);
+            upload(sf->rd, rdv, st);
+            ews.ensure(sizeof(T) * std::max<int64_t>(ws_off, 1));
+            sf->pool.ensure(sizeof(T) * std::max<int64_t>(fac_off, 1));
+            sf->perm.ensure(sizeof(int) * std::max<int64_t>(piv_off, 1));
+            piv_scratch.ensure(sizeof(int) * std::max<int64_t>(piv_off, 1));
+            upload(sf->boxes, sf->hbox, st);
+            ElimArgs ea{};
+            ea.g = g;
+            ea.sci = scidev(h, (int)tau);
+            ea.boxes = d_ed.as<ElimDesc>();
+            ea.groups = d_eg.as<ElimGroup>();
+            ea.sk_ids = sf->sk.as<int>();
+            ea.rd_ids = sf->rd.as<int>();
+            ea.Tws = Tws.p;
+            ea.ws = ews.p;
+            ea.fac_pool = sf->pool.p;
+            ea.piv_pool = piv_scratch.as<int>();
+            ea.perm_pool = sf->perm.as<int>();
+            ea.sci_pool = pool->p;
+            ea.status = h->status.as<int>();
+            HIF_CUDA((launch_elim<T>(ea, sf->nbox, st)));
+            h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
+        }
+        h->sci_pools.push_back(std::move(pool));
+
+        // ---- state for the next sublevel: active set and SCI membership
+        sci.blk.emplace_back(N, -1);
+        sci.loc.emplace_back(N, 0);
+        std::vector<int>& hb = sci.blk.back();
+        std::vector<int>& hl = sci.loc.back();
+        for (size_t q = 0; q < nblk.size(); ++q) {
+            const NewBlock& nbk = nblk[q];
+            std::vector<int> mem(skv.begin() + nbk.sk_off, skv.begin() + nbk.sk_off + nbk.k);
+            for (int l = 0; l < nbk.k; ++l) {
+                hb[mem[l]] = first_block + (int)q;
+                hl[mem[l]] = l;
+            }
+            sci.members.push_back(std::move(mem));
+        }
+        for (int i : rdv) active[i] = 0;
+        HIF_CUDA(cudaStreamSynchronize(st));   // kernels of this sublevel hold the old block table
+        HIF_CUDA(cudaMemcpyAsync(h->sci_blk.as<int>() + tau * N, hb.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        HIF_CUDA(cudaMemcpyAsync(h->sci_loc.as<int>() + tau * N, hl.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        upload(h->blk_ptr, h->blk_ptr_h, st);
+        upload(h->blk_k, h->blk_k_h, st);
+        HIF_CUDA(cudaStreamSynchronize(st));
+        check_status(h);
+        h->subs.push_back(std::move(sf));
+    }
+    h->stats.sublevels = (int)kinds.size();
+    h->stats.levels = t.L;
+
+    // ---- top block D_L over s_L
+    std::vector<int> top;
+    for (int64_t i = 0; i < N; ++i)
+        if (active[i]) top.push_back((int)i);
+    h->nL = (int)top.size();
+    h->stats.top_size = h->nL;
+    if (h->nL > 0) {
+        const int n = h->nL;
+        upload(h->top_ids, top, st);
+        h->topA.ensure(sizeof(T) * (size_t)n * n);
+        h->topLU.ensure(sizeof(T) * (size_t)n * n);
+        h->topInv.ensure(sizeof(T) * (size_t)n * n);
+        h->top_piv.ensure(sizeof(int) * n);
+        TopArgs ta{};
+        ta.g = g;
+        ta.sci = scidev(h, (int)kinds.size());
+        ta.ids = h->top_ids.as<int>();
+        ta.n = n;
+        ta.A = h->topA.p;
+        HIF_CUDA((launch_top_assemble<T>(ta, st)));
+        HIF_CUDA(cudaMemcpyAsync(h->topLU.p, h->topA.p, sizeof(T) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
+        HIF_CUDA((top_lu<T>(h->topLU.as<T>(), n, h->top_piv.as<int>(), h->status.as<int>(), st)));
+        check_status(h);
+        HIF_CUDA((top_inverse<T>(h->topLU.as<T>(), h->top_piv.as<int>(), n, h->topInv.as<T>(), st)));
+        HIF_CUDA(cudaStreamSynchronize(st));
+        h->stats.factor_bytes += (int64_t)3 * n * n * sizeof(T);
+        flops += 2.0 / 3.0 * (double)n * n * n + 2.0 * (double)n * n * n;
+    }
+    h->stats.flops = flops;
+    h->stats.kernel_evals = evals;
+}
+
+// ---------------------------------------------------------- sweeps ------
+
+enum { SOLVE_UP = 0, SOLVE_DOWN = 1, APPLY_UP = 2, APPLY_DOWN = 3,
+       SOLVET_UP = 4, SOLVET_DOWN = 5, APPLYT_UP = 6, APPLYT_DOWN = 7 };
+
+template <typename T>
+static void sweep_all(hif_handle h, T* xw, int64_t ldx, int nrhs, int op) {
+    // op: 0 solve, 1 apply, 2 solve^T, 3 apply^T
+    const int up = op == 0 ? SOLVE_UP : op == 1 ? APPLY_UP : op == 2 ? SOLVET_UP : APPLYT_UP;
+    const int down = up + 1;
+    const cudaStream_t st = h->st;
+    auto run = [&](SubFactor& sf, int mode) {
+        if (!sf.nbox) return;
+        const size_t per_col = (size_t)sf.max_kr2 * sizeof(T);
+        int batch = (int)std::min<size_t>((size_t)nrhs, std::max<size_t>(1, (200 * 1024) / per_col));
+        if (per_col > 220 * 1024) fail(HIF_EINVAL, "box too large for the sweep kernel");
+        for (int r0 = 0; r0 < nrhs; r0 += batch) {
+            const int nr = std::min(batch, nrhs - r0);
+            SweepArgs a{};
+            a.boxes = sf.boxes.as<BoxFac>();
+            a.sk_ids = sf.sk.as<int>();
+            a.rd_ids = sf.rd.as<int>();
+            a.pool = sf.pool.p;
+            a.perm = sf.perm.as<int>();
+            a.x = xw + ldx * r0;
+            a.ldx = ldx;
+            a.nrhs = nr;
+            const size_t smem = per_col * nr + 64;
+            a.mode = mode | (int)(smem << 8);
+            HIF_CUDA((launch_sweep<T>(a, sf.nbox, st)));
+        }
+    };
+    for (auto& sf : h->subs) run(*sf, up);
+    if (h->nL) {
+        const T* M = (op == 0 || op == 2) ? h->topInv.as<T>() : h->topA.as<T>();
+        h->tmp.ensure(sizeof(T) * (size_t)h->nL * nrhs);
+        HIF_CUDA((launch_top_gemm<T>(M, h->nL, op >= 2, h->top_ids.as<int>(), xw, ldx, nrhs, h->tmp.as<T>(), st)));
+    }
+    for (auto it = h->subs.rbegin(); it != h->subs.rend(); ++it) run(**it, down);
+}
+
+static void apply_op(hif_handle h, const double* in, double* out, int64_t nrhs, int64_t ld, int op) {
+    if (!h) fail(HIF_EINVAL, "null handle");
+    if (nrhs < 0 || ld < h->N || !in || !out) fail(HIF_EINVAL, "bad vector arguments");
+    if (nrhs == 0) return;
+    const cudaStream_t st = h->st;
+    const int64_t N = h->N;
+    // device views of the caller's arrays
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    DevMem tin, tout;
+    const double* din_p = in;
+    double* dout_p = out;
+    int64_t ldi = ld, ldo = ld;
+    if (!din) {
+        tin.ensure(sizeof(double) * N * nrhs);
+        HIF_CUDA(cudaMemcpy2DAsync(tin.p, sizeof(double) * N, in, sizeof(double) * ld, sizeof(double) * N, nrhs,
+                                   cudaMemcpyHostToDevice, st));
+        din_p = tin.as<double>();
+        ldi = N;
+    }
+    if (!dout) {
+        tout.ensure(sizeof(double) * N * nrhs);
+        dout_p = tout.as<double>();
+        ldo = N;
+    }
+    if (h->precision == 0) {
+        h->work.ensure(sizeof(double) * N * nrhs);
+        double* xw = h->work.as<double>();
+        HIF_CUDA(launch_to_work<double>(din_p, ldi, xw, N, N, (int)nrhs, st));
+        sweep_all<double>(h, xw, N, (int)nrhs, op);
+        HIF_CUDA(launch_from_work<double>(xw, N, dout_p, ldo, N, (int)nrhs, st));
+    } else {
+        h->work.ensure(sizeof(float) * N * nrhs);
+        float* xw = h->work.as<float>();
+        HIF_CUDA(launch_to_work<float>(din_p, ldi, xw, N, N, (int)nrhs, st));
+        sweep_all<float>(h, xw, N, (int)nrhs, op);
+        HIF_CUDA(launch_from_work<float>(xw, N, dout_p, ldo, N, (int)nrhs, st));
+    }
+    if (!dout)
+        HIF_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * ld, dout_p, sizeof(double) * N, sizeof(double) * N, nrhs,
+                                   cudaMemcpyDeviceToHost, st));
+    HIF_CUDA(cudaStreamSynchronize(st));
+}
+
+// FP64 direct sum on device arrays.
+static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs) {
+    const cudaStream_t st = h->st;
+    if (h->grid) {
+        const int64_t N = h->N;
+        h->vbuf.ensure(sizeof(double) * N * nrhs);
+        h->ybuf.ensure(sizeof(double) * N * nrhs);
+        GridDirectArgs ga{};
+        ga.table = h->table.as<double>();
+        ga.dof_of = h->dof_of.as<int>();
+        ga.n = h->gn;
+        ga.dim = h->dim;
+        ga.a = h->a.as<double>();
+        ga.b = h->b.as<double>();
+        ga.c = h->c.as<double>();
+        ga.w = h->w.as<double>();
+        ga.x = x;
+        ga.ldx = ldx;
+        ga.y = y;
+        ga.ldy = ldy;
+        ga.nrhs = nrhs;
+        ga.trans = trans;
+        ga.vbuf = h->vbuf.as<double>();
+        ga.ybuf = h->ybuf.as<double>();
+        HIF_CUDA(launch_direct_grid(ga, st));
+    } else {
+        DirectArgs da{};
+        da.g = geom(h);
+        da.x = x;
+        da.ldx = ldx;
+        da.y = y;
+        da.ldy = ldy;
+        da.nrhs = nrhs;
+        da.trans = trans;
+        HIF_CUDA(launch_direct_general(da, st));
+    }
+}
+
+static void solve_dev(hif_handle h, int trans, const double* b, double* x, int nrhs) {
+    // x = F^{-1} b or F^{-T} b, device arrays with ld = N
+    const cudaStream_t st = h->st;
+    const int64_t N = h->N;
+    const int op = trans ? 2 : 0;
+    if (h->precision == 0) {
+        h->work.ensure(sizeof(double) * N * nrhs);
+        double* xw = h->work.as<double>();
+        HIF_CUDA(launch_to_work<double>(b, N, xw, N, N, nrhs, st));
+        sweep_all<double>(h, xw, N, nrhs, op);
+        HIF_CUDA(launch_from_work<double>(xw, N, x, N, N, nrhs, st));
+    } else {
+        h->work.ensure(sizeof(float) * N * nrhs);
+        float* xw = h->work.as<float>();
+        HIF_CUDA(launch_to_work<float>(b, N, xw, N, N, nrhs, st));
+        sweep_all<float>(h, xw, N, nrhs, op);
+        HIF_CUDA(launch_from_work<float>(xw, N, x, N, N, nrhs, st));
+    }
+}
+
+static std::vector<double> col_norms(hif_handle h, const double* v, int nrhs) {
+    h->tmp.ensure(sizeof(double) * std::max(nrhs, 1));
+    HIF_CUDA(launch_col_dots(h->N, nrhs, v, h->N, v, h->N, h->tmp.as<double>(), h->st));
+    std::vector<double> out(nrhs);
+    HIF_CUDA(cudaMemcpyAsync(out.data(), h->tmp.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, h->st));
+    HIF_CUDA(cudaStreamSynchronize(h->st));
+    for (double& o : out) o = std::sqrt(std::max(o, 0.0));
+    return out;
+}
+
+// Iterative refinement: u = F^{-1} f; r = f - A u; u += F^{-1} r ...
+static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u, int nrhs, double tol, int maxit,
+                            int* iters, double* relres) {
+    const int64_t N = h->N;
+    DevMem r, du;
+    r.ensure(sizeof(double) * N * nrhs);
+    du.ensure(sizeof(double) * N * nrhs);
+    const std::vector<double> fn = col_norms(h, f, nrhs);
+    solve_dev(h, trans, f, u, nrhs);
+    int it = 0;
+    double worst = 0;
+    for (;; ++it) {
+        matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs);
+        HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, h->st));
+        const std::vector<double> rn = col_norms(h, r.as<double>(), nrhs);
+        worst = 0;
+        for (int c = 0; c < nrhs; ++c) worst = std::max(worst, fn[c] > 0 ? rn[c] / fn[c] : 0.0);
+        if (worst <= tol || it >= maxit) break;
+        solve_dev(h, trans, r.as<double>(), du.as<double>(), nrhs);
+        HIF_CUDA(launch_axpby(N, nrhs, 1.0, du.as<double>(), N, 1.0, u, N, h->st));
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = worst;
+    return worst <= tol ? HIF_OK : HIF_ENOTCONV;
+}
+
+// Right-preconditioned GMRES(m), all columns advanced together, modified
+// Gram-Schmidt in FP64; the Hessenberg least-squares problems are solved on
+// the host (they are at most (m+1) x m per column).
+static hif_status refine_gmres(hif_handle h, int trans, const double* f, double* u, int nrhs, double tol, int maxit,
+                               int* iters, double* relres) {
+    const int m = 20;
+    const int64_t N = h->N;
+    const cudaStream_t st = h->st;
+    DevMem V, Z, wv, r, tmpc;
+    V.ensure(sizeof(double) * N * nrhs * (m + 1));
+    Z.ensure(sizeof(double) * N * nrhs * m);
+    wv.ensure(sizeof(double) * N * nrhs);
+    r.ensure(sizeof(double) * N * nrhs);
+    tmpc.ensure(sizeof(double) * nrhs);
+    double* Vp = V.as<double>();
+    double* Zp = Z.as<double>();
+    auto Vc = [&](int j) { return Vp + (int64_t)j * N * nrhs; };
+    auto Zc = [&](int j) { return Zp + (int64_t)j * N * nrhs; };
+    const std::vector<double> fn = col_norms(h, f, nrhs);
+    HIF_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * N * nrhs, st));
+    int its = 0;
+    double worst = 1.0;
+    std::vector<double> beta(nrhs);
+    for (int c = 0; c < nrhs; ++c) beta[c] = fn[c];
+    HIF_CUDA(cudaMemcpyAsync(r.p, f, sizeof(double) * N * nrhs, cudaMemcpyDeviceToDevice, st));
+    while (true) {
+        worst = 0;
+        for (int c = 0; c < nrhs; ++c) worst = std::max(worst, fn[c] > 0 ? beta[c] / fn[c] : 0.0);
+        if (worst <= tol || its >= maxit) break;
+        // V_0 = r / beta (column scaling on the device through a tiny kernel: use axpby per column)
+        for (int c = 0; c < nrhs; ++c)
+            HIF_CUDA(launch_axpby(N, 1, beta[c] > 0 ? 1.0 / beta[c] : 0.0, r.as<double>() + N * c, N, 0.0,
+                                  Vc(0) + N * c, N, st));
+        std::vector<std::vector<double>> H(nrhs, std::vector<double>((m + 1) * m, 0.0));
+        std::vector<std::vector<double>> gvec(nrhs, std::vector<double>(m + 1, 0.0));
+        std::vector<std::vector<double>> cs(nrhs, std::vector<double>(m)), sn(nrhs, std::vector<double>(m));
+        for (int c = 0; c < nrhs; ++c) gvec[c][0] = beta[c];
+        int jdone = 0;
+        std::vector<double> dots(nrhs);
+        for (int j = 0; j < m; ++j) {
+            solve_dev(h, trans, Vc(j), Zc(j), nrhs);
+            matvec_dev(h, trans, Zc(j), N, wv.as<double>(), N, nrhs);
+            for (int i = 0; i <= j; ++i) {
+                HIF_CUDA(launch_col_dots(N, nrhs, Vc(i), N, wv.as<double>(), N, tmpc.as<double>(), st));
+                HIF_CUDA(cudaMemcpyAsync(dots.data(), tmpc.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+                HIF_CUDA(cudaStreamSynchronize(st));
+                for (int c = 0; c < nrhs; ++c) {
+                    H[c][i + (m + 1) * j] = dots[c];
+                    HIF_CUDA(launch_axpby(N, 1, -dots[c], Vc(i) + N * c, N, 1.0, wv.as<double>() + N * c, N, st));
+                }
+            }
+            const std::vector<double> hn = col_norms(h, wv.as<double>(), nrhs);
+            bool all_conv = true;
+            for (int c = 0; c < nrhs; ++c) {
+                H[c][j + 1 + (m + 1) * j] = hn[c];
+                HIF_CUDA(launch_axpby(N, 1, hn[c] > 0 ? 1.0 / hn[c] : 0.0, wv.as<double>() + N * c, N, 0.0,
+                                      Vc(j + 1) + N * c, N, st));
+                double* Hc = H[c].data();
+                for (int i = 0; i < j; ++i) {
+                    const double t0 = cs[c][i] * Hc[i + (m + 1) * j] + sn[c][i] * Hc[i + 1 + (m + 1) * j];
+                    Hc[i + 1 + (m + 1) * j] = -sn[c][i] * Hc[i + (m + 1) * j] + cs[c][i] * Hc[i + 1 + (m + 1) * j];
+                    Hc[i + (m + 1) * j] = t0;
+                }
+                const double den = std::hypot(Hc[j + (m + 1) * j], Hc[j + 1 + (m + 1) * j]);
+                cs[c][j] = den > 0 ? Hc[j + (m + 1) * j] / den : 1.0;
+                sn[c][j] = den > 0 ? Hc[j + 1 + (m + 1) * j] / den : 0.0;
+                Hc[j + (m + 1) * j] = cs[c][j] * Hc[j + (m + 1) * j] + sn[c][j] * Hc[j + 1 + (m + 1) * j];
+                Hc[j + 1 + (m + 1) * j] = 0.0;
+                gvec[c][j + 1] = -sn[c][j] * gvec[c][j];
+                gvec[c][j] = cs[c][j] * gvec[c][j];
+                if (fn[c] > 0 && std::fabs(gvec[c][j + 1]) / fn[c] > tol) all_conv = false;
+            }
+            ++its;
+            jdone = j + 1;
+            if (all_conv || its >= maxit) break;
+        }
+        // u += Z y per column
+        for (int c = 0; c < nrhs; ++c) {
+            std::vector<double> y(jdone, 0.0);
+            for (int i = jdone - 1; i >= 0; --i) {
+                double v = gvec[c][i];
+                for (int l = i + 1; l < jdone; ++l) v -= H[c][i + (m + 1) * l] * y[l];
+                const double dg = H[c][i + (m + 1) * i];
+                y[i] = dg != 0 ? v / dg : 0.0;
+            }
+            for (int i = 0; i < jdone; ++i)
+                HIF_CUDA(launch_axpby(N, 1, y[i], Zc(i) + N * c, N, 1.0, u + N * c, N, st));
+        }
+        matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs);
+        HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, st));
+        beta = col_norms(h, r.as<double>(), nrhs);
+    }
+    if (iters) *iters = its;
+    if (relres) *relres = worst;
+    return worst <= tol ? HIF_OK : HIF_ENOTCONV;
+}
+
+template <typename F>
+static hif_status guard(F&& fn) {
+    try {
+        fn();
+        return HIF_OK;
+    } catch (const Err& e) {
+        return e.s;
+    } catch (const std::bad_alloc&) {
+        return HIF_ENOMEM;
+    }
+}
+
+// Runs fn on device copies (ld = N) of a caller input and output, copying
+// host arrays in and out.
+template <typename F>
+static void with_dev_io(hif_handle h, const double* in, double* out, int64_t nrhs, int64_t ld, F&& fn) {
+    const int64_t N = h->N;
+    const cudaStream_t st = h->st;
+    DevMem din, dout;
+    din.ensure(sizeof(double) * N * nrhs);
+    dout.ensure(sizeof(double) * N * nrhs);
+    HIF_CUDA(cudaMemcpy2DAsync(din.p, sizeof(double) * N, in, sizeof(double) * ld, sizeof(double) * N, nrhs,
+                               is_device_ptr(in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    fn(din.as<double>(), dout.as<double>());
+    HIF_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * ld, dout.p, sizeof(double) * N, sizeof(double) * N, nrhs,
+                               is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    HIF_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace hif
+
+using namespace hif;
+
+extern "C" {
+
+const char* hif_status_string(hif_status s) {
+    switch (s) {
+        case HIF_OK: return "HIF_OK";
+        case HIF_EINVAL: return "HIF_EINVAL: invalid argument";
+        case HIF_ENOMEM: return "HIF_ENOMEM: out of memory";
+        case HIF_ESINGULAR: return "HIF_ESINGULAR: singular elimination block";
+        case HIF_ENUMERIC: return "HIF_ENUMERIC: non-finite value";
+        case HIF_ECUDA: return "HIF_ECUDA: CUDA runtime error";
+        case HIF_ETIMEOUT: return "HIF_ETIMEOUT: bounded wait expired";
+        case HIF_ENOTCONV: return "HIF_ENOTCONV: tolerance not reached";
+    }
+    return "unknown hif_status";
+}
+
+const char* hif_last_error(void) { return g_last_error; }
+
+hif_status hif_options_default(int dim, hif_options* opt) {
+    if (!opt || (dim != 2 && dim != 3)) return HIF_EINVAL;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->dim = dim;
+    opt->leaf_occupancy = 64;
+    opt->second_kind = 1;
+    opt->precision = 0;
+    opt->fractional_levels = 1;
+    opt->skip_levels = 0;
+    opt->proxy_points = dim == 2 ? 64 : 512;
+    opt->proxy_radius = 1.5;
+    opt->proxy_dirs = nullptr;
+    opt->fp32_tol_floor = std::ldexp(1.0, -20);
+    opt->root_width = 0.0;
+    opt->stream = nullptr;
+    return HIF_OK;
+}
+
+hif_status hif_factor(const double* points, int64_t N, const double* weights, const double* a, const double* b,
+                      const double* c, int kernel_id, double eps, const hif_options* opt_in, hif_handle* out) {
+    if (!out) return HIF_EINVAL;
+    *out = nullptr;
+    hif_options opt;
+    if (opt_in) opt = *opt_in;
+    else hif_options_default(2, &opt);
+    if (N <= 0 || N > (int64_t)2000000000 || !points || !weights || !a || !b || !c) return HIF_EINVAL;
+    if (opt.dim != 2 && opt.dim != 3) return HIF_EINVAL;
+    if ((opt.dim == 2 && kernel_id != 0) || (opt.dim == 3 && kernel_id != 1)) return HIF_EINVAL;
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return HIF_EINVAL;
+    if (opt.leaf_occupancy < 1 || opt.proxy_points < 1 || !(opt.proxy_radius > 0)) return HIF_EINVAL;
+    if (opt.precision != 0 && opt.precision != 1) return HIF_EINVAL;
+    if (opt.dim == 3 && !opt.proxy_dirs) return HIF_EINVAL;
+    auto h = std::make_unique<hif_handle_s>();
+    const auto t0 = std::chrono::steady_clock::now();
+    hif_status s = guard([&] {
+        h->dim = opt.dim;
+        h->kernel_id = kernel_id;
+        h->precision = opt.precision;
+        h->second_kind = opt.second_kind ? 1 : 0;
+        h->N = N;
+        h->eps = eps;
+        h->opt = opt;
+        h->st = static_cast<cudaStream_t>(opt.stream);
+        h->elem = opt.precision == 0 ? 8 : 4;
+        const int d = opt.dim;
+        const cudaStream_t st = h->st;
+        // inputs: device copies owned by the handle, host copies of the geometry
+        auto take = [&](DevMem& dst, const double* src, size_t cnt) {
+            dst.ensure(cnt * sizeof(double));
+            HIF_CUDA(cudaMemcpyAsync(dst.p, src, cnt * sizeof(double),
+                                     is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        };
+        take(h->x, points, (size_t)N * d);
+        take(h->w, weights, (size_t)N);
+        take(h->a, a, (size_t)N);
+        take(h->b, b, (size_t)N);
+        take(h->c, c, (size_t)N);
+        h->hx.resize((size_t)N * d);
+        h->hw.resize((size_t)N);
+        HIF_CUDA(cudaMemcpyAsync(h->hx.data(), h->x.p, sizeof(double) * N * d, cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaMemcpyAsync(h->hw.data(), h->w.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        std::vector<double> ha(N), hbv(N), hc(N);
+        HIF_CUDA(cudaMemcpyAsync(ha.data(), h->a.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaMemcpyAsync(hbv.data(), h->b.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaMemcpyAsync(hc.data(), h->c.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < N; ++i) {
+            if (!std::isfinite(ha[i]) || !std::isfinite(hbv[i]) || !std::isfinite(hc[i]) || !(h->hw[i] > 0) ||
+                !std::isfinite(h->hw[i]))
+                fail(HIF_ENUMERIC, "non-finite or non-positive input");
+            for (int k = 0; k < d; ++k)
+                if (!std::isfinite(h->hx[d * i + k])) fail(HIF_ENUMERIC, "non-finite point");
+        }
+        // proxy directions
+        h->P = opt.proxy_points;
+        std::vector<double> pd((size_t)h->P * d);
+        if (opt.proxy_dirs) {
+            if (is_device_ptr(opt.proxy_dirs))
+                HIF_CUDA(cudaMemcpy(pd.data(), opt.proxy_dirs, sizeof(double) * pd.size(), cudaMemcpyDeviceToHost));
+            else
+                std::memcpy(pd.data(), opt.proxy_dirs, sizeof(double) * pd.size());
+        } else {
+            for (int k = 0; k < h->P; ++k) {
+                const double th = 2.0 * kPi * k / h->P;
+                pd[2 * k] = std::cos(th);
+                pd[2 * k + 1] = std::sin(th);
+            }
+        }
+        upload(h->proxy, pd, st);
+        h->kself.ensure(sizeof(double) * N);
+        HIF_CUDA(launch_kself(geom(h.get()), h->kself.as<double>(), st));
+        detect_grid(h.get());
+        if (h->grid) {
+            const int64_t tsz = d == 2 ? (int64_t)h->gn * h->gn : (int64_t)h->gn * h->gn * h->gn;
+            h->table.ensure(sizeof(double) * tsz);
+            double k0 = 0;
+            HIF_CUDA(cudaMemcpyAsync(&k0, h->kself.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+            HIF_CUDA(cudaStreamSynchronize(st));
+            HIF_CUDA(launch_grid_table(h->table.as<double>(), h->gn, d, h->gh, kernel_id, k0 / h->hw[0], st));
+        }
+        h->stats.N = N;
+        h->stats.dim = d;
+        if (h->precision == 0) run_factor<double>(h.get());
+        else run_factor<float>(h.get());
+        HIF_CUDA(cudaStreamSynchronize(st));
+    });
+    if (s != HIF_OK) return s;
+    h->stats.factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h.release();
+    return HIF_OK;
+}
+
+hif_status hif_apply(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld) {
+    return guard([&] { apply_op(h, x, y, nrhs, ld, 1); });
+}
+hif_status hif_apply_transpose(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld) {
+    return guard([&] { apply_op(h, x, y, nrhs, ld, 3); });
+}
+hif_status hif_solve(hif_handle h, const double* bb, double* x, int64_t nrhs, int64_t ld) {
+    return guard([&] { apply_op(h, bb, x, nrhs, ld, 0); });
+}
+hif_status hif_solve_transpose(hif_handle h, const double* bb, double* x, int64_t nrhs, int64_t ld) {
+    return guard([&] { apply_op(h, bb, x, nrhs, ld, 2); });
+}
+
+hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y, int64_t nrhs, int64_t ld) {
+    if (!h || !x || !y || nrhs < 0 || ld < (h ? h->N : 0)) return HIF_EINVAL;
+    if (nrhs == 0) return HIF_OK;
+    return guard([&] {
+        with_dev_io(h, x, y, nrhs, ld, [&](const double* dx, double* dy) {
+            matvec_dev(h, trans ? 1 : 0, dx, h->N, dy, h->N, (int)nrhs);
+        });
+    });
+}
+
+hif_status hif_solve_refined(hif_handle h, int trans, const double* f, double* u, int64_t nrhs, int64_t ld, double tol,
+                             int maxit, int method, int* iters, double* relres) {
+    if (!h || !f || !u || nrhs < 0 || ld < (h ? h->N : 0) || !(tol > 0) || maxit < 0 || (method != 0 && method != 1))
+        return HIF_EINVAL;
+    if (nrhs == 0) return HIF_OK;
+    hif_status res = HIF_OK;
+    hif_status s = guard([&] {
+        with_dev_io(h, f, u, nrhs, ld, [&](const double* df, double* du) {
+            res = method == 0 ? refine_ir(h, trans ? 1 : 0, df, du, (int)nrhs, tol, maxit, iters, relres)
+                              : refine_gmres(h, trans ? 1 : 0, df, du, (int)nrhs, tol, maxit, iters, relres);
+        });
+    });
+    return s != HIF_OK ? s : res;
+}
+
+hif_status hif_stats(hif_handle h, hif_stats_t* st) {
+    if (!h || !st) return HIF_EINVAL;
+    *st = h->stats;
+    return HIF_OK;
+}
+
+hif_status hif_destroy(hif_handle h) {
+    if (!h) return HIF_OK;
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    delete h;
+    return HIF_OK;
+}
+
+hif_status hif_kernel_block(const double* points, int64_t N, int dim, const double* weights, const double* a,
+                            const double* b, const double* c, int kernel_id, const int32_t* rows, int64_t nr,
+                            const int32_t* cols, int64_t nc, double* out, int64_t ldo, void* stream) {
+    if (N <= 0 || (dim != 2 && dim != 3) || (kernel_id != 0 && kernel_id != 1) || nr < 0 || nc < 0 || ldo < nr ||
+        !points || !weights || !a || !b || !c || !rows || !cols || !out)
+        return HIF_EINVAL;
+    return guard([&] {
+        const cudaStream_t st = static_cast<cudaStream_t>(stream);
+        InArr px, pw, pa, pb, pc;
+        px.set(points, (size_t)N * dim, st);
+        pw.set(weights, N, st);
+        pa.set(a, N, st);
+        pb.set(b, N, st);
+        pc.set(c, N, st);
+        DevMem dr, dc, dk, dout;
+        const int* drp = rows;
+        const int* dcp = cols;
+        if (!is_device_ptr(rows)) {
+            dr.ensure(sizeof(int) * std::max<int64_t>(nr, 1));
+            if (nr) HIF_CUDA(cudaMemcpyAsync(dr.p, rows, sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+            drp = dr.as<int>();
+        }
+        if (!is_device_ptr(cols)) {
+            dc.ensure(sizeof(int) * std::max<int64_t>(nc, 1));
+            if (nc) HIF_CUDA(cudaMemcpyAsync(dc.p, cols, sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+            dcp = dc.as<int>();
+        }
+        dk.ensure(sizeof(double) * N);
+        GeomDev g{px.d, pw.d, pa.d, pb.d, pc.d, dk.as<double>(), N, dim, kernel_id};
+        HIF_CUDA(launch_kself(g, dk.as<double>(), st));
+        const bool dev_out = is_device_ptr(out);
+        double* o = out;
+        if (!dev_out) {
+            dout.ensure(sizeof(double) * std::max<int64_t>(ldo * nc, 1));
+            o = dout.as<double>();
+        }
+        HIF_CUDA(launch_kernel_block(g, drp, nr, dcp, nc, o, ldo, st));
+        if (!dev_out && nr * nc)
+            HIF_CUDA(cudaMemcpyAsync(out, o, sizeof(double) * ldo * nc, cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+hif_status hif_id_batched(int count, const double* mats, const int64_t* off, const int32_t* m, const int32_t* n,
+                          const double* tol, int32_t* k, int32_t* perm, const int64_t* poff, double* T,
+                          const int64_t* toff, void* stream) {
+    if (count < 0 || !mats || !off || !m || !n || !tol || !k || !perm || !poff || !T || !toff) return HIF_EINVAL;
+    if (count == 0) return HIF_OK;
+    return guard([&] {
+        const cudaStream_t st = static_cast<cudaStream_t>(stream);
+        // all metadata to the device; matrices may be host or device
+        std::vector<int64_t> hoff(off, off + count), hpoff(poff, poff + count), htoff(toff, toff + count);
+        std::vector<int> hm(m, m + count), hn(n, n + count);
+        int64_t mat_end = 0, perm_end = 0, t_end = 0;
+        for (int i = 0; i < count; ++i) {
+            if (hm[i] < 0 || hn[i] < 0) fail(HIF_EINVAL, "negative size");
+            mat_end = std::max(mat_end, hoff[i] + (int64_t)hm[i] * hn[i]);
+            perm_end = std::max(perm_end, hpoff[i] + hn[i]);
+            t_end = std::max(t_end, htoff[i] + (int64_t)hn[i] * hn[i] / 4 + hn[i]);
+        }
+        std::vector<double> htol(tol, tol + count);
+        DevMem dmats, doff, dm, dn, dtol, dk, dperm, dpoff, dT, dtoff;
+        const double* mp = mats;
+        if (!is_device_ptr(mats)) {
+            dmats.ensure(sizeof(double) * std::max<int64_t>(mat_end, 1));
+            HIF_CUDA(cudaMemcpyAsync(dmats.p, mats, sizeof(double) * mat_end, cudaMemcpyHostToDevice, st));
+            mp = dmats.as<double>();
+        }
+        upload(doff, hoff, st);
+        upload(dm, hm, st);
+        upload(dn, hn, st);
+        upload(dtol, htol, st);
+        upload(dpoff, hpoff, st);
+        upload(dtoff, htoff, st);
+        dk.ensure(sizeof(int) * count);
+        dperm.ensure(sizeof(int) * std::max<int64_t>(perm_end, 1));
+        dT.ensure(sizeof(double) * std::max<int64_t>(t_end, 1));
+        HIF_CUDA(launch_id_batched(count, mp, doff.as<int64_t>(), dm.as<int>(), dn.as<int>(), dtol.as<double>(),
+                                   dk.as<int>(), dperm.as<int>(), dpoff.as<int64_t>(), dT.as<double>(),
+                                   dtoff.as<int64_t>(), st));
+        const bool dk_dev = is_device_ptr(k), dp_dev = is_device_ptr(perm), dt_dev = is_device_ptr(T);
+        HIF_CUDA(cudaMemcpyAsync(k, dk.p, sizeof(int) * count, dk_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaMemcpyAsync(perm, dperm.p, sizeof(int) * perm_end,
+                                 dp_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaMemcpyAsync(T, dT.p, sizeof(double) * t_end, dt_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,335 @@
+// Host-side index bookkeeping of HIF-IE sublevels (see geometry.h).
+//
+// The arithmetic that decides memberships (cell floor indices, squared
+// distances to edge/face centres and to the proxy centre) is written as plain
+// IEEE double operations in a fixed order and compiled without FMA
+// contraction, so that the same inputs always give the same index sets.
+#include "geometry.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <unordered_map>
+
+namespace hif {
+
+void root_box(const double* x, const double* w, int64_t N, int dim, double lo[3], double* W) {
+    double hi[3];
+    for (int k = 0; k < 3; ++k) { lo[k] = 0.0; hi[k] = 0.0; }
+    for (int64_t i = 0; i < N; ++i) {
+        const double side = dim == 2 ? std::sqrt(w[i]) : std::cbrt(w[i]);
+        const double half = 0.5 * side;
+        for (int k = 0; k < dim; ++k) {
+            const double a = x[dim * i + k] - half, b = x[dim * i + k] + half;
+            if (i == 0 || a < lo[k]) lo[k] = a;
+            if (i == 0 || b > hi[k]) hi[k] = b;
+        }
+    }
+    double Wm = 0.0;
+    for (int k = 0; k < dim; ++k) Wm = std::max(Wm, hi[k] - lo[k]);
+    *W = Wm;
+}
+
+static inline int cell_coord(double xk, double lo, double w, int s) {
+    const double t = std::floor((xk - lo) / w);
+    int c = t < 0.0 ? 0 : (t > (double)(s - 1) ? s - 1 : (int)t);
+    return c;
+}
+
+int num_levels(const double* x, int64_t N, int dim, const double lo[3], double W, int occupancy) {
+    for (int L = 0; L <= 24; ++L) {
+        const int s = 1 << L;
+        const double w = W / s;
+        std::unordered_map<int64_t, int> cnt;
+        cnt.reserve((size_t)std::min<int64_t>(N, (int64_t)1 << 22));
+        int mx = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            int64_t flat = 0;
+            for (int k = 0; k < dim; ++k) flat = flat * s + cell_coord(x[dim * i + k], lo[k], w, s);
+            mx = std::max(mx, ++cnt[flat]);
+            if (mx > occupancy) break;
+        }
+        if (mx <= occupancy) return L;
+    }
+    return 24;
+}
+
+void plan_sublevels(int dim, int L, bool fractional, int skip_levels, std::vector<int>& kinds,
+                    std::vector<int>& levels) {
+    kinds.clear();
+    levels.clear();
+    for (int l = 0; l < L; ++l) {
+        kinds.push_back(KIND_CELL);
+        levels.push_back(l);
+        if (fractional && l >= skip_levels) {
+            if (dim == 3) {
+                kinds.push_back(KIND_FACE);
+                levels.push_back(l);
+            }
+            kinds.push_back(KIND_EDGE);
+            levels.push_back(l);
+        }
+    }
+}
+
+// Families of centres (Sec. 4.1, 4.2): per axis 'I' = on a cell boundary
+// (index 1..s-1, offset 0), 'H' = mid-cell (index 0..s-1, offset 1/2).
+struct Family {
+    int nf;
+    bool I[3][3];
+};
+
+static Family families(int dim, int kind) {
+    Family f{};
+    auto set = [&](int q, bool a, bool b, bool c) { f.I[q][0] = a; f.I[q][1] = b; f.I[q][2] = c; };
+    if (kind == KIND_CELL) { f.nf = 1; set(0, false, false, false); }
+    else if (dim == 2) { f.nf = 2; set(0, true, false, false); set(1, false, true, false); }
+    else if (kind == KIND_FACE) { f.nf = 3; set(0, true, false, false); set(1, false, true, false); set(2, false, false, true); }
+    else { f.nf = 3; set(0, true, true, false); set(1, true, false, true); set(2, false, true, true); }
+    return f;
+}
+
+void partition(const Tree& t, const double* x, int kind, int s, const std::vector<int>& active_ids,
+               SublevelPlan& out, std::vector<int>& box_of) {
+    const int dim = t.dim;
+    const double w = t.W / s;
+    const Family fam = families(dim, kind);
+    // family sizes and offsets (ids follow the paper's listing order)
+    int64_t fam_off[4] = {0, 0, 0, 0};
+    int64_t ext[3][3];
+    for (int q = 0; q < fam.nf; ++q) {
+        int64_t sz = 1;
+        for (int k = 0; k < dim; ++k) {
+            ext[q][k] = fam.I[q][k] ? s - 1 : s;
+            sz *= ext[q][k];
+        }
+        fam_off[q + 1] = fam_off[q] + sz;
+    }
+    const int64_t ncent = fam_off[fam.nf];
+    const int64_t na = (int64_t)active_ids.size();
+    std::vector<int64_t> owner(na);
+
+#pragma omp parallel for schedule(static)
+    for (int64_t a = 0; a < na; ++a) {
+        const int i = active_ids[a];
+        const double* p = x + (int64_t)dim * i;
+        int c[3] = {0, 0, 0};
+        for (int k = 0; k < dim; ++k) c[k] = cell_coord(p[k], t.lo[k], w, s);
+        if (kind == KIND_CELL) {
+            int64_t flat = 0;
+            for (int k = 0; k < dim; ++k) flat = flat * s + c[k];
+            owner[a] = flat;
+            continue;
+        }
+        int64_t best_id = -1;
+        double best = 0.0;
+        for (int q = 0; q < fam.nf; ++q) {
+            int jlo[3], jhi[3];
+            for (int k = 0; k < 3; ++k) { jlo[k] = 0; jhi[k] = 0; }
+            for (int k = 0; k < dim; ++k) {
+                if (fam.I[q][k]) { jlo[k] = std::max(1, c[k] - 1); jhi[k] = std::min(s - 1, c[k] + 2); }
+                else { jlo[k] = std::max(0, c[k] - 1); jhi[k] = std::min(s - 1, c[k] + 1); }
+            }
+            for (int j0 = jlo[0]; j0 <= jhi[0]; ++j0)
+                for (int j1 = jlo[1]; j1 <= jhi[1]; ++j1)
+                    for (int j2 = jlo[2]; j2 <= jhi[2]; ++j2) {
+                        const int js[3] = {j0, j1, j2};
+                        int64_t id = 0;
+                        double d2 = 0.0;
+                        for (int k = 0; k < dim; ++k) {
+                            const double ck = t.lo[k] + ((double)js[k] + (fam.I[q][k] ? 0.0 : 0.5)) * w;
+                            const double dd = p[k] - ck;
+                            d2 = d2 + dd * dd;
+                            id = id * ext[q][k] + (fam.I[q][k] ? js[k] - 1 : js[k]);
+                        }
+                        id += fam_off[q];
+                        if (best_id < 0 || d2 < best || (d2 == best && id < best_id)) {
+                            best = d2;
+                            best_id = id;
+                        }
+                    }
+        }
+        owner[a] = best_id;
+    }
+    // bucket by owner (stable: ascending DOF ids inside a box)
+    std::vector<int64_t> count(ncent + 1, 0);
+    for (int64_t a = 0; a < na; ++a) count[owner[a] + 1]++;
+    for (int64_t b = 0; b < ncent; ++b) count[b + 1] += count[b];
+    std::vector<int> sorted(na);
+    {
+        std::vector<int64_t> pos(count.begin(), count.end() - 1);
+        for (int64_t a = 0; a < na; ++a) sorted[pos[owner[a]]++] = active_ids[a];
+    }
+    out.box_off.clear();
+    out.members.clear();
+    out.centers.clear();
+    out.box_off.push_back(0);
+    for (int64_t b = 0; b < ncent; ++b) {
+        if (count[b + 1] == count[b]) continue;
+        // centre of box b
+        int q = 0;
+        while (b >= fam_off[q + 1]) ++q;
+        int64_t rem = b - fam_off[q];
+        int js[3] = {0, 0, 0};
+        for (int k = dim - 1; k >= 0; --k) {
+            js[k] = (int)(rem % ext[q][k]);
+            rem /= ext[q][k];
+            if (fam.I[q][k]) js[k] += 1;
+        }
+        for (int k = 0; k < 3; ++k) {
+            out.centers.push_back(k < dim ? t.lo[k] + ((double)js[k] + (fam.I[q][k] ? 0.0 : 0.5)) * w : 0.0);
+        }
+        for (int64_t e = count[b]; e < count[b + 1]; ++e) {
+            out.members.push_back(sorted[e]);
+            box_of[sorted[e]] = (int)(out.box_off.size() - 1);
+        }
+        out.box_off.push_back((int64_t)out.members.size());
+    }
+    out.nbox = (int)out.box_off.size() - 1;
+}
+
+void build_near_groups(const Tree& t, const double* x, int s, double proxy_radius, int second_kind,
+                       const std::vector<int>& active_ids, const std::vector<char>& active,
+                       const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p) {
+    const int dim = t.dim;
+    const double w = t.W / s;
+    const double R = proxy_radius * w;
+    const double R2 = R * R;
+    const int nsub = (int)sci.blk.size();
+    // bins of the active DOFs: cells of width w at this level
+    int64_t nbins = 1;
+    for (int k = 0; k < dim; ++k) nbins *= s;
+    std::vector<int64_t> boff(nbins + 1, 0);
+    std::vector<int64_t> bin_of(active_ids.size());
+    for (size_t a = 0; a < active_ids.size(); ++a) {
+        const double* q = x + (int64_t)dim * active_ids[a];
+        int64_t flat = 0;
+        for (int k = 0; k < dim; ++k) flat = flat * s + cell_coord(q[k], t.lo[k], w, s);
+        bin_of[a] = flat;
+        boff[flat + 1]++;
+    }
+    for (int64_t b = 0; b < nbins; ++b) boff[b + 1] += boff[b];
+    std::vector<int> bins(active_ids.size());
+    {
+        std::vector<int64_t> pos(boff.begin(), boff.end() - 1);
+        for (size_t a = 0; a < active_ids.size(); ++a) bins[pos[bin_of[a]]++] = active_ids[a];
+    }
+
+    const int nb = p.nbox;
+    std::vector<std::vector<int>> near(nb), cols(nb);
+    std::vector<std::vector<int>> gcol0(nb), gn(nb), gsci(nb);
+    std::vector<int> bsci(nb, 0);
+
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < nb; ++b) {
+        const double* ctr = &p.centers[3 * (size_t)b];
+        std::vector<int>& nl = near[b];
+        // proxy interior
+        int lo_b[3] = {0, 0, 0}, hi_b[3] = {0, 0, 0};
+        for (int k = 0; k < dim; ++k) {
+            lo_b[k] = cell_coord(ctr[k] - R, t.lo[k], w, s);
+            hi_b[k] = cell_coord(ctr[k] + R, t.lo[k], w, s);
+        }
+        for (int b0 = lo_b[0]; b0 <= hi_b[0]; ++b0)
+            for (int b1 = lo_b[1]; b1 <= hi_b[1]; ++b1)
+                for (int b2 = lo_b[2]; b2 <= hi_b[2]; ++b2) {
+                    int64_t flat = (int64_t)b0 * s + b1;
+                    if (dim == 3) flat = flat * s + b2;
+                    for (int64_t e = boff[flat]; e < boff[flat + 1]; ++e) {
+                        const int i = bins[e];
+                        if (box_of[i] == b) continue;
+                        const double* q = x + (int64_t)dim * i;
+                        double d2 = 0.0;
+                        for (int k = 0; k < dim; ++k) {
+                            const double dd = q[k] - ctr[k];
+                            d2 = d2 + dd * dd;
+                        }
+                        if (d2 < R2) nl.push_back(i);
+                    }
+                    if (dim == 2) break;
+                }
+        // SCI-coupled DOFs
+        std::vector<int> blocks;
+        for (int64_t e = p.box_off[b]; e < p.box_off[b + 1]; ++e) {
+            const int j = p.members[e];
+            for (int q = 0; q < nsub; ++q) {
+                const int bid = sci.blk[q][j];
+                if (bid >= 0) blocks.push_back(bid);
+            }
+        }
+        std::sort(blocks.begin(), blocks.end());
+        blocks.erase(std::unique(blocks.begin(), blocks.end()), blocks.end());
+        for (int bid : blocks)
+            for (int i : sci.members[bid])
+                if (active[i] && box_of[i] != b) nl.push_back(i);
+        std::sort(nl.begin(), nl.end());
+        nl.erase(std::unique(nl.begin(), nl.end()), nl.end());
+
+        // groups by structural SCI pattern (Sec. 4.4); columns ascending inside
+        const int64_t n0 = p.box_off[b], n1 = p.box_off[b + 1];
+        const int nc = (int)(n1 - n0);
+        std::vector<std::vector<int>> pats(nc);
+        bool any = false;
+        for (int l = 0; l < nc; ++l) {
+            const int j = p.members[n0 + l];
+            std::vector<int>& pt = pats[l];
+            for (int q = 0; q < nsub; ++q) {
+                const int bid = sci.blk[q][j];
+                if (bid < 0) continue;
+                for (int i : sci.members[bid])
+                    if (active[i] && box_of[i] != b) pt.push_back(i);
+            }
+            std::sort(pt.begin(), pt.end());
+            pt.erase(std::unique(pt.begin(), pt.end()), pt.end());
+            if (!pt.empty()) any = true;
+        }
+        bsci[b] = any ? 1 : 0;
+        std::vector<int> gid(nc, 0);
+        int ng = 1;
+        if (second_kind) {
+            std::vector<int> first;  // representative column of each group
+            for (int l = 0; l < nc; ++l) {
+                int g = -1;
+                for (size_t q = 0; q < first.size(); ++q)
+                    if (pats[first[q]] == pats[l]) { g = (int)q; break; }
+                if (g < 0) { g = (int)first.size(); first.push_back(l); }
+                gid[l] = g;
+            }
+            ng = (int)first.size();
+        }
+        std::vector<int>& cl = cols[b];
+        for (int g = 0; g < ng; ++g) {
+            gcol0[b].push_back((int)cl.size());
+            bool gs = false;
+            for (int l = 0; l < nc; ++l)
+                if (gid[l] == g) {
+                    cl.push_back(p.members[n0 + l]);
+                    if (!pats[l].empty()) gs = true;
+                }
+            gn[b].push_back((int)cl.size() - gcol0[b].back());
+            gsci[b].push_back(second_kind ? (gs ? 1 : 0) : (any ? 1 : 0));
+        }
+    }
+    p.near_off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) p.near_off[b + 1] = p.near_off[b] + (int64_t)near[b].size();
+    p.near.resize(p.near_off[nb]);
+    p.cols.resize(p.members.size());
+    p.grp_off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) p.grp_off[b + 1] = p.grp_off[b] + (int64_t)gn[b].size();
+    p.grp_col0.resize(p.grp_off[nb]);
+    p.grp_n.resize(p.grp_off[nb]);
+    p.grp_sci.resize(p.grp_off[nb]);
+    p.box_sci = bsci;
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < nb; ++b) {
+        std::copy(near[b].begin(), near[b].end(), p.near.begin() + p.near_off[b]);
+        std::copy(cols[b].begin(), cols[b].end(), p.cols.begin() + p.box_off[b]);
+        for (size_t g = 0; g < gn[b].size(); ++g) {
+            p.grp_col0[p.grp_off[b] + g] = gcol0[b][g];
+            p.grp_n[p.grp_off[b] + g] = gn[b][g];
+            p.grp_sci[p.grp_off[b] + g] = gsci[b][g];
+        }
+    }
+}
+
+}  // namespace hif

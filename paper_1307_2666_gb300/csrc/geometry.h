@@ -1,0 +1,56 @@
+// Host-side integer bookkeeping of one skeletonization sublevel: the index
+// sets C_l (cells by floor index, edges/faces by nearest interior centre --
+// Sec. 4.1 / 4.2), their near fields (Sec. 3.3 proxy interior plus the
+// SCI-coupled DOFs of Sec. 4.3) and the column groups of Sec. 4.4.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace hif {
+
+enum BoxKind { KIND_CELL = 0, KIND_FACE = 1, KIND_EDGE = 2 };
+
+struct Tree {
+    int dim;
+    double lo[3];
+    double W;
+    int L;
+};
+
+// Past SCI blocks: DOF i belongs to block blk[s][i] (or -1) at loc[s][i].
+struct SciHost {
+    std::vector<std::vector<int>> blk;      // per past sublevel, size N
+    std::vector<std::vector<int>> loc;
+    std::vector<std::vector<int>> members;  // per block id: skeleton DOFs in order
+};
+
+struct SublevelPlan {
+    int nbox;
+    std::vector<int64_t> box_off;           // members CSR
+    std::vector<int> members;               // ascending within a box
+    std::vector<double> centers;            // nbox x 3
+    // filled by build_near_groups
+    std::vector<int64_t> near_off;
+    std::vector<int> near;
+    std::vector<int> cols;                  // group-ordered columns (CSR = box_off)
+    std::vector<int64_t> grp_off;           // per box: first group
+    std::vector<int> grp_col0, grp_n, grp_sci;
+    std::vector<int> box_sci;
+};
+
+void root_box(const double* x, const double* w, int64_t N, int dim, double lo[3], double* W);
+int num_levels(const double* x, int64_t N, int dim, const double lo[3], double W, int occupancy);
+void plan_sublevels(int dim, int L, bool fractional, int skip_levels, std::vector<int>& kinds,
+                    std::vector<int>& levels);
+
+// Partition the active DOFs (ascending ids) into the boxes of (kind, s).
+void partition(const Tree& t, const double* x, int kind, int s, const std::vector<int>& active_ids,
+               SublevelPlan& out, std::vector<int>& box_of);
+
+// Near fields and groups; `active` flags DOFs active at the start of the sublevel.
+void build_near_groups(const Tree& t, const double* x, int s, double proxy_radius, int second_kind,
+                       const std::vector<int>& active_ids, const std::vector<char>& active,
+                       const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p);
+
+}  // namespace hif

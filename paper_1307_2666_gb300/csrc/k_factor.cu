@@ -1,0 +1,682 @@
+// Skeletonization kernels of one sublevel (sm_103a).
+//
+//  fold_kernel   one CTA per box c: generates the proxy matrix Y_c of Eq. (3.3)
+//                (near-field rows A_{cN,c}, A_{c,cN}^T and proxy rows of
+//                Lemma 3.3) chunk by chunk in shared memory and folds every
+//                chunk into the triangular factor R_c of Y_c = Q_c R_c by
+//                Householder reflections; Y_c itself never reaches HBM.  In
+//                second-kind mode it also accumulates the Gram matrices of the
+//                kernel part Y^K and the SCI part Y^S (Sec. 4.4).
+//  id_kernel     one CTA per column group g: rho_g = min(1, |Y^K_g|/|Y^S_g|)
+//                by power iteration, then the column-pivoted QR interpolative
+//                decomposition (Lemma 2.2) of R_c[:, g] -- equal to the ID of
+//                Y_c[:, g] because Q_c has orthonormal columns.
+//  elim_kernel   one CTA per box: the B blocks of Lemma 2.3, LU with partial
+//                pivoting of B_rr (Lemma 2.1), X, Y and the Schur update
+//                B_ss - B_sr B_rr^{-1} B_rs recorded as a new SCI block.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "cta_linalg.cuh"
+#include "hif_common.cuh"
+#include "launch.h"
+
+namespace hif {
+
+namespace {
+
+template <typename T>
+__device__ inline T* align_ptr(unsigned char*& p, size_t count) {
+    uintptr_t v = reinterpret_cast<uintptr_t>(p);
+    v = (v + 15) & ~uintptr_t(15);
+    T* out = reinterpret_cast<T*>(v);
+    p = reinterpret_cast<unsigned char*>(v + count * sizeof(T));
+    return out;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- fold ------
+
+template <typename T>
+__global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
+    const BoxDesc bx = args.boxes[blockIdx.x];
+    const int n = bx.n;
+    const int bp = args.bpairs;          // row pairs per chunk
+    const int rows = 2 * bp;
+    const int ldc = rows + 1;            // odd leading dimension: conflict-free columns
+    const int nsub = args.sci.nsub;
+    const bool scival = bx.has_sci && nsub > 0;          // SCI entries present in Y_c
+    const bool sci = scival && args.second_kind;         // keep Y^S apart for rho_g
+    const int dim = args.g.dim;
+    const int kid = args.g.kernel_id;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* sp = smem;
+    T* cxl = align_ptr<T>(sp, (size_t)n * 3);
+    T* cwc = align_ptr<T>(sp, n);
+    T* cb = align_ptr<T>(sp, n);
+    T* cbw = align_ptr<T>(sp, n);
+    int* cid = align_ptr<int>(sp, n);
+    int* cgrp_end = align_ptr<int>(sp, n);          // end column of the column's group
+    T* rxl = align_ptr<T>(sp, (size_t)bp * 3);
+    T* rb = align_ptr<T>(sp, bp);
+    T* rwc = align_ptr<T>(sp, bp);
+    int* rid = align_ptr<int>(sp, bp);
+    T* CK = align_ptr<T>(sp, (size_t)ldc * n);
+    T* CS = sci ? align_ptr<T>(sp, (size_t)ldc * n) : nullptr;
+    T* hh = align_ptr<T>(sp, 4);
+    T* R;
+    T* const Rws = static_cast<T*>(args.Rws);
+    if (args.R_in_smem) R = align_ptr<T>(sp, (size_t)n * n);
+    else R = Rws + bx.R_off;
+    T* GK = sci ? static_cast<T*>(args.GKws) + bx.R_off : nullptr;
+    T* GS = sci ? static_cast<T*>(args.GSws) + bx.R_off : nullptr;
+
+    const int* cols = args.cols + bx.col_off;
+    const int* near = args.near + bx.near_off;
+    const double c0 = bx.ctr[0], c1 = bx.ctr[1], c2 = dim == 3 ? bx.ctr[2] : 0.0;
+
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        const int j = cols[l];
+        cid[l] = j;
+        cxl[3 * l + 0] = (T)(args.g.x[(int64_t)dim * j + 0] - c0);
+        cxl[3 * l + 1] = (T)(args.g.x[(int64_t)dim * j + 1] - c1);
+        cxl[3 * l + 2] = dim == 3 ? (T)(args.g.x[(int64_t)dim * j + 2] - c2) : T(0);
+        cwc[l] = (T)(args.g.w[j] * args.g.c[j]);
+        cb[l] = (T)args.g.b[j];
+        cbw[l] = (T)(args.g.b[j] * args.g.w[j]);
+    }
+    for (int gi = 0; gi < bx.ngroups; ++gi) {
+        const GroupDesc gd = args.groups[bx.grp_off + gi];
+        for (int l = gd.col0 + threadIdx.x; l < gd.col0 + gd.n; l += blockDim.x) cgrp_end[l] = gd.col0 + gd.n;
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        R[e] = T(0);
+        if (sci) { GK[e] = T(0); GS[e] = T(0); }
+    }
+    __syncthreads();
+
+    const int npairs = bx.m_near + args.P;
+    for (int p0 = 0; p0 < npairs; p0 += bp) {
+        const int np = min(bp, npairs - p0);
+        // ---- row data of this chunk
+        for (int q = threadIdx.x; q < bp; q += blockDim.x) {
+            const int p = p0 + q;
+            if (q >= np) {
+                rid[q] = -2;
+            } else if (p < bx.m_near) {
+                const int i = near[p];
+                rid[q] = i;
+                rxl[3 * q + 0] = (T)(args.g.x[(int64_t)dim * i + 0] - c0);
+                rxl[3 * q + 1] = (T)(args.g.x[(int64_t)dim * i + 1] - c1);
+                rxl[3 * q + 2] = dim == 3 ? (T)(args.g.x[(int64_t)dim * i + 2] - c2) : T(0);
+                rb[q] = (T)args.g.b[i];
+                rwc[q] = (T)(args.g.w[i] * args.g.c[i]);
+            } else {
+                const int kx = p - bx.m_near;
+                rid[q] = -1;
+                rxl[3 * q + 0] = (T)(bx.radius * args.proxy[dim * kx + 0]);
+                rxl[3 * q + 1] = (T)(bx.radius * args.proxy[dim * kx + 1]);
+                rxl[3 * q + 2] = dim == 3 ? (T)(bx.radius * args.proxy[dim * kx + 2]) : T(0);
+                rb[q] = T(1);
+                rwc[q] = T(1);
+            }
+        }
+        __syncthreads();
+        // ---- generate the chunk: rows (2q, 2q+1) = (outgoing, incoming) of pair q
+        for (int l = threadIdx.x; l < n; l += blockDim.x) {
+            const T xj0 = cxl[3 * l], xj1 = cxl[3 * l + 1], xj2 = cxl[3 * l + 2];
+            const int j = cid[l];
+            for (int q = 0; q < bp; ++q) {
+                T k1 = T(0), k2 = T(0), s1 = T(0), s2 = T(0);
+                const int i = rid[q];
+                if (i != -2) {
+                    const T d0 = rxl[3 * q] - xj0, d1 = rxl[3 * q + 1] - xj1, d2 = rxl[3 * q + 2] - xj2;
+                    const T gk = Green<T>::eval(kid, d0 * d0 + d1 * d1 + d2 * d2);
+                    if (i >= 0) {
+                        k1 = rb[q] * gk * cwc[l];    // A_{ij} kernel part
+                        k2 = cb[l] * gk * rwc[q];    // A_{ji} kernel part
+                        if (scival) {
+                            for (int s = 0; s < nsub; ++s) {
+                                const int bi = args.sci.blk[(int64_t)s * args.sci.N + i];
+                                if (bi >= 0 && bi == args.sci.blk[(int64_t)s * args.sci.N + j]) {
+                                    const int kb = args.sci.kb[bi];
+                                    const T* P = static_cast<const T*>(args.sci.ptr[bi]);
+                                    const int li = args.sci.loc[(int64_t)s * args.sci.N + i];
+                                    const int lj = args.sci.loc[(int64_t)s * args.sci.N + j];
+                                    s1 += P[li + (int64_t)kb * lj];
+                                    s2 += P[lj + (int64_t)kb * li];
+                                }
+                            }
+                        }
+                    } else {
+                        k1 = gk * cwc[l];            // proxy-out: G w_j c_j
+                        k2 = cbw[l] * gk;            // proxy-in:  b_j G w_j
+                    }
+                }
+                if (sci) {
+                    CK[2 * q + ldc * l] = k1;
+                    CK[2 * q + 1 + ldc * l] = k2;
+                    CS[2 * q + ldc * l] = s1;
+                    CS[2 * q + 1 + ldc * l] = s2;
+                } else {
+                    CK[2 * q + ldc * l] = k1 + s1;
+                    CK[2 * q + 1 + ldc * l] = k2 + s2;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- Gram matrices of Y^K and Y^S inside each group (second kind)
+        if (sci) {
+            for (int l = threadIdx.x; l < n; l += blockDim.x) {
+                const int lend = cgrp_end[l];
+                for (int l2 = l; l2 < lend; ++l2) {
+                    T gk = T(0), gs = T(0);
+                    for (int i = 0; i < rows; ++i) {
+                        gk += CK[i + ldc * l] * CK[i + ldc * l2];
+                        gs += CS[i + ldc * l] * CS[i + ldc * l2];
+                    }
+                    GK[(int64_t)l * n + l2] += gk;
+                    GS[(int64_t)l * n + l2] += gs;
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < ldc * n; e += blockDim.x) CK[e] += CS[e];
+            __syncthreads();
+        }
+        // ---- fold the chunk into R: QR of [R; C] (row-major R, n x n)
+        for (int j = 0; j < n; ++j) {
+            if (threadIdx.x < 32) {
+                T s = T(0);
+                for (int i = threadIdx.x; i < rows; i += 32) {
+                    const T v = CK[i + ldc * j];
+                    s += v * v;
+                }
+                s = warp_sum(s);
+                if (threadIdx.x == 0) {
+                    const T alpha = R[(int64_t)j * n + j];
+                    if (s == T(0)) {
+                        hh[0] = T(0);
+                        hh[1] = T(0);
+                    } else {
+                        const T beta = -copysign(sqrt(alpha * alpha + s), alpha);
+                        hh[0] = (beta - alpha) / beta;       // tau
+                        hh[1] = T(1) / (alpha - beta);       // scale of v
+                        R[(int64_t)j * n + j] = beta;
+                    }
+                }
+            }
+            __syncthreads();
+            const T tau = hh[0];
+            if (tau != T(0)) {
+                const T scal = hh[1];
+                for (int i = threadIdx.x; i < rows; i += blockDim.x) CK[i + ldc * j] *= scal;
+                __syncthreads();
+                for (int l = j + 1 + threadIdx.x; l < n; l += blockDim.x) {
+                    T w = R[(int64_t)j * n + l];
+                    for (int i = 0; i < rows; ++i) w += CK[i + ldc * j] * CK[i + ldc * l];
+                    w *= tau;
+                    R[(int64_t)j * n + l] -= w;
+                    for (int i = 0; i < rows; ++i) CK[i + ldc * l] -= w * CK[i + ldc * j];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (args.R_in_smem) {
+        T* Rg = Rws + bx.R_off;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rg[e] = R[e];
+    }
+}
+
+// --------------------------------------------------------------- ID ------
+
+// Column-pivoted Householder QR of W (mrow x ng, column-major, leading
+// dimension ldw, overwritten) to relative tolerance tol (Lemma 2.2 with the
+// adaptive rank of Sec. 2.2): pivot = largest remaining column 2-norm (ties:
+// lowest original index), norms recomputed exactly in FP64 after every step,
+// stop at the first step whose pivot norm is <= tol times the first one.
+// Writes k, the column order (skeletons in pivot order, then redundants in
+// ascending order) and T = R1^{-1} R2 (k x (ng-k), column-major, columns in
+// the redundant order).  perm, rank_of: ng ints; redv/redi: blockDim entries.
+template <typename T>
+__device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm, int* perm, int* rank_of,
+                        double* redv, int* redi, T* hh, T* Tout, int* pout, int* kout) {
+    for (int l = threadIdx.x; l < ng; l += blockDim.x) perm[l] = l;
+    __syncthreads();
+    // ---- column-pivoted Householder QR with exact norm recomputation
+    for (int l = threadIdx.x; l < ng; l += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < mrow; ++i) {
+            const double v = (double)W[i + (int64_t)ldw * l];
+            s += v * v;
+        }
+        nrm[l] = s;
+    }
+    __syncthreads();
+    const int kmax = min(mrow, ng);
+    double nu0 = 0.0;
+    int k = 0;
+    for (int j = 0; j < kmax; ++j) {
+        // pivot: largest remaining norm, ties to the lowest original column
+        double best = -1.0;
+        int bo = 1 << 30, bl = -1;
+        for (int l = j + threadIdx.x; l < ng; l += blockDim.x) {
+            const double v = nrm[l];
+            if (v > best || (v == best && perm[l] < bo)) { best = v; bo = perm[l]; bl = l; }
+        }
+        redv[threadIdx.x] = best;
+        redi[threadIdx.x] = bl;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double v2 = redv[threadIdx.x + s];
+                const int l2 = redi[threadIdx.x + s];
+                const double v1 = redv[threadIdx.x];
+                const int l1 = redi[threadIdx.x];
+                if (l2 >= 0 && (l1 < 0 || v2 > v1 || (v2 == v1 && perm[l2] < perm[l1]))) {
+                    redv[threadIdx.x] = v2;
+                    redi[threadIdx.x] = l2;
+                }
+            }
+            __syncthreads();
+        }
+        const double bsq = redv[0];
+        const int p = redi[0];
+        __syncthreads();
+        const double bnorm = sqrt(fmax(bsq, 0.0));
+        if (j == 0) nu0 = bnorm;
+        if (bnorm <= tol * nu0 || bnorm == 0.0) break;
+        if (p != j) {
+            for (int i = threadIdx.x; i < mrow; i += blockDim.x) {
+                const T t = W[i + (int64_t)ldw * j];
+                W[i + (int64_t)ldw * j] = W[i + (int64_t)ldw * p];
+                W[i + (int64_t)ldw * p] = t;
+            }
+            if (threadIdx.x == 0) {
+                const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+                const double tn = nrm[j]; nrm[j] = nrm[p]; nrm[p] = tn;
+            }
+        }
+        __syncthreads();
+        // Householder reflector for W[j:, j]
+        if (threadIdx.x < 32) {
+            T s = T(0);
+            for (int i = j + 1 + threadIdx.x; i < mrow; i += 32) {
+                const T v = W[i + (int64_t)ldw * j];
+                s += v * v;
+            }
+            s = warp_sum(s);
+            if (threadIdx.x == 0) {
+                const T alpha = W[j + (int64_t)ldw * j];
+                if (s == T(0)) {
+                    hh[0] = T(0);
+                    hh[1] = T(0);
+                } else {
+                    const T beta = -copysign(sqrt(alpha * alpha + s), alpha);
+                    hh[0] = (beta - alpha) / beta;
+                    hh[1] = T(1) / (alpha - beta);
+                    W[j + (int64_t)ldw * j] = beta;
+                }
+            }
+        }
+        __syncthreads();
+        const T tau = hh[0];
+        if (tau != T(0)) {
+            const T scal = hh[1];
+            for (int i = j + 1 + threadIdx.x; i < mrow; i += blockDim.x) W[i + (int64_t)ldw * j] *= scal;
+        }
+        __syncthreads();
+        for (int l = j + 1 + threadIdx.x; l < ng; l += blockDim.x) {
+            T* col = W + (int64_t)ldw * l;
+            const T* v = W + (int64_t)ldw * j;
+            if (tau != T(0)) {
+                T w = col[j];
+                for (int i = j + 1; i < mrow; ++i) w += v[i] * col[i];
+                w *= tau;
+                col[j] -= w;
+                for (int i = j + 1; i < mrow; ++i) col[i] -= w * v[i];
+            }
+            double s = 0.0;
+            for (int i = j + 1; i < mrow; ++i) {
+                const double c = (double)col[i];
+                s += c * c;
+            }
+            nrm[l] = s;
+        }
+        __syncthreads();
+        k = j + 1;
+    }
+    // ---- T = R1^{-1} R2, written with the redundant columns in ascending order
+    const int r = ng - k;
+    for (int l = threadIdx.x; l < r; l += blockDim.x) {
+        const int o = perm[k + l];
+        int pos = 0;
+        for (int q = 0; q < r; ++q) pos += perm[k + q] < o;
+        rank_of[l] = pos;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < r; l += blockDim.x) {
+        T* col = W + (int64_t)ldw * (k + l);
+        for (int i = k - 1; i >= 0; --i) {
+            T v = col[i];
+            for (int q = i + 1; q < k; ++q) v -= W[i + (int64_t)ldw * q] * col[q];
+            col[i] = v / W[i + (int64_t)ldw * i];
+        }
+        const int pos = rank_of[l];
+        for (int i = 0; i < k; ++i) Tout[i + (int64_t)k * pos] = col[i];
+    }
+    for (int l = threadIdx.x; l < k; l += blockDim.x) pout[l] = perm[l];
+    for (int l = threadIdx.x; l < r; l += blockDim.x) pout[k + rank_of[l]] = perm[k + l];
+    if (threadIdx.x == 0) *kout = k;
+}
+
+
+template <typename T>
+__global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
+    const GroupDesc gd = args.groups[blockIdx.x];
+    const BoxDesc bx = args.boxes[gd.box];
+    const int n = bx.n;
+    const int ng = gd.n;
+    const int mrow = gd.col0 + ng;                 // rows of R[:, g] that can be nonzero
+    const int ldw = mrow | 1;
+    const T* R = static_cast<const T*>(args.Rws) + bx.R_off;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* sp = smem;
+    double* nrm = align_ptr<double>(sp, ng);
+    int* perm = align_ptr<int>(sp, ng);
+    int* rank_of = align_ptr<int>(sp, ng);
+    double* redv = align_ptr<double>(sp, blockDim.x);
+    int* redi = align_ptr<int>(sp, blockDim.x);
+    T* vec = align_ptr<T>(sp, 2 * (size_t)ng);
+    T* hh = align_ptr<T>(sp, 4);
+    T* W;
+    if (args.W_in_smem) W = align_ptr<T>(sp, (size_t)ldw * ng);
+    else W = static_cast<T*>(args.Wws) + args.W_off[blockIdx.x];
+
+    for (int e = threadIdx.x; e < mrow * ng; e += blockDim.x) {
+        const int i = e % mrow, l = e / mrow;
+        W[i + (int64_t)ldw * l] = R[(int64_t)i * n + gd.col0 + l];
+    }
+    __syncthreads();
+
+    // ---- rho_g (Sec. 4.4): 8 power iterations from the all-ones vector on
+    // the Gram matrices of Y^K_g and Y^S_g
+    double rho = 1.0;
+    if (args.second_kind && gd.has_sci && bx.has_sci && args.GKws != nullptr) {
+        double est[2];
+        for (int which = 0; which < 2; ++which) {
+            const T* G = static_cast<const T*>(which == 0 ? args.GKws : args.GSws) + bx.R_off;
+            T* v = vec;
+            T* wv = vec + ng;
+            for (int l = threadIdx.x; l < ng; l += blockDim.x) v[l] = T(1) / sqrt(T(ng));
+            __syncthreads();
+            double result = 0.0;
+            for (int it = 0; it <= 8; ++it) {
+                // w = G v (G symmetric, upper triangle stored row-major)
+                for (int l = threadIdx.x; l < ng; l += blockDim.x) {
+                    T acc = T(0);
+                    const int gl = gd.col0 + l;
+                    for (int q = 0; q < ng; ++q) {
+                        const int gq = gd.col0 + q;
+                        const T gv = gl <= gq ? G[(int64_t)gl * n + gq] : G[(int64_t)gq * n + gl];
+                        acc += gv * v[q];
+                    }
+                    wv[l] = acc;
+                }
+                __syncthreads();
+                // it < 8: normalize; it == 8: |Y v|^2 = v^T G v
+                double part = 0.0;
+                for (int l = threadIdx.x; l < ng; l += blockDim.x)
+                    part += it < 8 ? (double)wv[l] * (double)wv[l] : (double)v[l] * (double)wv[l];
+                redv[threadIdx.x] = part;
+                __syncthreads();
+                for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+                    if (threadIdx.x < s) redv[threadIdx.x] += redv[threadIdx.x + s];
+                    __syncthreads();
+                }
+                const double tot = redv[0];
+                __syncthreads();
+                if (it == 8) { result = sqrt(fmax(tot, 0.0)); break; }
+                if (tot == 0.0) { result = 0.0; break; }
+                const double inv = 1.0 / sqrt(tot);
+                for (int l = threadIdx.x; l < ng; l += blockDim.x) v[l] = (T)(wv[l] * inv);
+                __syncthreads();
+            }
+            est[which] = result;
+        }
+        if (est[1] > 0.0) rho = fmin(1.0, est[0] / est[1]);
+    }
+    double tol = rho * args.eps;
+    if (tol < args.tol_floor) tol = args.tol_floor;
+
+    cpqr_id<T>(W, ldw, mrow, ng, tol, nrm, perm, rank_of, redv, redi, hh,
+               static_cast<T*>(args.Tws) + gd.T_off, args.perm_out + gd.perm_off, args.k_out + blockIdx.x);
+}
+
+// ------------------------------------------------------ elimination ------
+
+template <typename T>
+__global__ void __launch_bounds__(128) elim_kernel(ElimArgs args) {
+    const ElimDesc ed = args.boxes[blockIdx.x];
+    const int k = ed.k, r = ed.r, n = k + r;
+    T* A = static_cast<T*>(args.ws) + ed.ws_off;   // n x n, order (rd, sk), column-major
+    T* Tm = A + (int64_t)n * n;          // k x r
+    const int* sk = args.sk_ids + ed.sk_off;
+    const int* rd = args.rd_ids + ed.rd_off;
+    __shared__ T redv[128];
+    __shared__ int redi[128];
+    int* piv = args.piv_pool + ed.piv_out;
+
+    // interpolation matrix T = diag(T_g)
+    for (int e = threadIdx.x; e < k * r; e += blockDim.x) Tm[e] = T(0);
+    __syncthreads();
+    for (int gi = 0; gi < ed.ngroups; ++gi) {
+        const ElimGroup eg = args.groups[ed.grp_off + gi];
+        const T* Tg = static_cast<const T*>(args.Tws) + eg.T_off;
+        for (int e = threadIdx.x; e < eg.kg * eg.rg; e += blockDim.x) {
+            const int i = e % eg.kg, j = e / eg.kg;
+            Tm[(eg.ko + i) + (int64_t)k * (eg.ro + j)] = Tg[e];
+        }
+    }
+    // active-matrix block A_cc in (rd, sk) order
+    const int ref = r > 0 ? rd[0] : sk[0];
+    const int d = args.g.dim;
+    const double r0 = args.g.x[(int64_t)d * ref], r1 = args.g.x[(int64_t)d * ref + 1];
+    const double r2 = d == 3 ? args.g.x[(int64_t)d * ref + 2] : 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int p = e % n, q = e / n;
+        const int i = p < r ? rd[p] : sk[p - r];
+        const int j = q < r ? rd[q] : sk[q - r];
+        A[e] = entry<T>(args.g, args.sci, i, j, r0, r1, r2);
+    }
+    __syncthreads();
+    T* Arr = A;
+    T* Asr = A + r;
+    T* Ars = A + (int64_t)n * r;
+    T* Ass = A + (int64_t)n * r + r;
+    const int64_t ld = n;
+    // B_sr = A_sr - A_ss T            (Lemma 2.3)
+    cta_gemm<T>(k, r, k, T(-1), Ass, ld, false, Tm, k, false, Asr, ld);
+    // B_rr = A_rr - T^T B_sr - A_rs T  (= A_rr - T^T A_sr - A_rs T + T^T A_ss T)
+    cta_gemm<T>(r, r, k, T(-1), Tm, k, true, Asr, ld, false, Arr, ld);
+    cta_gemm<T>(r, r, k, T(-1), Ars, ld, false, Tm, k, false, Arr, ld);
+    // B_rs = A_rs - T^T A_ss
+    cta_gemm<T>(r, k, k, T(-1), Tm, k, true, Ass, ld, false, Ars, ld);
+    // P B_rr = L (D U)                (Lemma 2.1)
+    const bool ok = cta_lu<T>(r, Arr, ld, piv, redv, redi);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(args.status, (int)DEV_SINGULAR);
+        return;
+    }
+    // X = B_sr (DU)^{-1}
+    cta_trsm_right_upper<T>(r, Arr, ld, Asr, ld, k);
+    // Z = L^{-1} P B_rs
+    cta_apply_piv<T>(r, piv, Ars, ld, k);
+    cta_trsm_lower_unit<T>(r, Arr, ld, Ars, ld, k);
+    // Schur update -X Z on the skeletons (new SCI block)
+    if (k > 0 && ed.sci_out >= 0) {
+        T* S = static_cast<T*>(args.sci_pool) + ed.sci_out;
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) S[e] = T(0);
+        __syncthreads();
+        cta_gemm<T>(k, k, r, T(-1), Asr, ld, false, Ars, ld, false, S, k);
+    }
+    // outputs: D, U = (DU)/D, Y = D^{-1} Z, T, X, LU, inverses of L and U
+    T* pool = static_cast<T*>(args.fac_pool);
+    T* Dv = pool + ed.D_out;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) Dv[i] = Arr[i + ld * i];
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int i = e % r, j = e / r;
+        if (i < j) Arr[i + ld * j] /= Dv[i];
+    }
+    for (int e = threadIdx.x; e < r * k; e += blockDim.x) {
+        const int i = e % r, j = e / r;
+        Ars[i + ld * j] /= Dv[i];
+    }
+    __syncthreads();
+    T* LUo = pool + ed.LU_out;
+    T* Xo = pool + ed.X_out;
+    T* Yo = pool + ed.Y_out;
+    T* To = pool + ed.T_out;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int i = e % r, j = e / r;
+        LUo[e] = i == j ? T(0) : Arr[i + ld * j];
+    }
+    for (int e = threadIdx.x; e < k * r; e += blockDim.x) {
+        const int i = e % k, j = e / k;
+        Xo[e] = Asr[i + ld * j];
+        To[e] = Tm[e];
+    }
+    for (int e = threadIdx.x; e < r * k; e += blockDim.x) {
+        const int i = e % r, j = e / r;
+        Yo[e] = Ars[i + ld * j];
+    }
+    __syncthreads();
+    cta_unit_tri_inverses<T>(r, LUo, r, pool + ed.LUi_out, r);
+    // convert LAPACK-style interchanges into the permutation perm with
+    // (P x)_i = x[perm[i]]
+    if (threadIdx.x == 0) {
+        int* pm = args.perm_pool + ed.piv_out;
+        for (int i = 0; i < r; ++i) pm[i] = i;
+        for (int j = 0; j < r; ++j) {
+            const int p = piv[j];
+            const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
+        }
+    }
+}
+
+// Batched ID on caller matrices: one CTA per matrix, matrix copied into a
+// global workspace and reduced there.
+__global__ void __launch_bounds__(128) id_batched_kernel(const double* mats, const int64_t* off, const int* m,
+                                                          const int* n, const double* tol, int* k, int* perm,
+                                                          const int64_t* poff, double* T, const int64_t* toff,
+                                                          double* ws, const int64_t* wsoff) {
+    const int b = blockIdx.x;
+    const int mm = m[b], nn = n[b];
+    const int ldw = mm | 1;
+    double* W = ws + wsoff[b];
+    const double* M = mats + off[b];
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* sp = smem;
+    double* nrm = align_ptr<double>(sp, nn);
+    int* pm = align_ptr<int>(sp, nn);
+    int* rk = align_ptr<int>(sp, nn);
+    double* redv = align_ptr<double>(sp, blockDim.x);
+    int* redi = align_ptr<int>(sp, blockDim.x);
+    double* hh = align_ptr<double>(sp, 4);
+    for (int e = threadIdx.x; e < mm * nn; e += blockDim.x) W[(e % mm) + (int64_t)ldw * (e / mm)] = M[e];
+    __syncthreads();
+    cpqr_id<double>(W, ldw, mm, nn, tol[b], nrm, pm, rk, redv, redi, hh, T + toff[b], perm + poff[b], k + b);
+}
+
+cudaError_t launch_id_batched(int count, const double* mats, const int64_t* off, const int* m, const int* n,
+                              const double* tol, int* k, int* perm, const int64_t* poff, double* T,
+                              const int64_t* toff, cudaStream_t st) {
+    // workspace offsets need the sizes on the host
+    std::vector<int> hm(count), hn(count);
+    cudaError_t e = cudaMemcpyAsync(hm.data(), m, sizeof(int) * count, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hn.data(), n, sizeof(int) * count, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    std::vector<int64_t> wso(count);
+    int64_t tot = 0;
+    int maxn = 1;
+    for (int i = 0; i < count; ++i) {
+        wso[i] = tot;
+        tot += (int64_t)(hm[i] | 1) * hn[i];
+        maxn = std::max(maxn, hn[i]);
+    }
+    double* ws = nullptr;
+    int64_t* dwso = nullptr;
+    e = cudaMalloc(&ws, sizeof(double) * std::max<int64_t>(tot, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&dwso, sizeof(int64_t) * count);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dwso, wso.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st);
+    const size_t smem = (size_t)maxn * 16 + 128 * 12 + 256;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(id_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        id_batched_kernel<<<count, 128, smem, st>>>(mats, off, m, n, tol, k, perm, poff, T, toff, ws, dwso);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ws) cudaFree(ws);
+    if (dwso) cudaFree(dwso);
+    return e;
+}
+
+// ---------------------------------------------------------- launchers ----
+
+size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem) {
+    const size_t rows = 2 * (size_t)bpairs + 1;
+    size_t b = 0;
+    b += (size_t)n * 6 * elem + 64;       // cxl, cwc, cb, cbw
+    b += (size_t)n * 8 + 32;              // cid, cgrp_end
+    b += (size_t)bpairs * (5 * elem + 4) + 64;
+    b += rows * n * elem * (sci ? 2 : 1) + 32;
+    b += 4 * elem + 16;
+    if (R_in_smem) b += (size_t)n * n * elem + 16;
+    return b + 128;
+}
+
+size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem) {
+    size_t b = (size_t)ng * 16 + 128 * 12 + 2 * (size_t)ng * elem + 4 * elem + 160;
+    if (W_in_smem) b += (size_t)(mrow | 1) * ng * elem + 16;
+    return b + 64;
+}
+
+template <typename T>
+cudaError_t launch_fold(const FoldArgs& a, int nbox, size_t smem, cudaStream_t st) {
+    if (nbox == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fold_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fold_kernel<T><<<nbox, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_id(const IdArgs& a, int ngroups, size_t smem, cudaStream_t st) {
+    if (ngroups == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    id_kernel<T><<<ngroups, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_elim(const ElimArgs& a, int nbox, cudaStream_t st) {
+    if (nbox == 0) return cudaSuccess;
+    elim_kernel<T><<<nbox, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fold<double>(const FoldArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_fold<float>(const FoldArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_id<double>(const IdArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_id<float>(const IdArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_elim<double>(const ElimArgs&, int, cudaStream_t);
+template cudaError_t launch_elim<float>(const ElimArgs&, int, cudaStream_t);
+
+}  // namespace hif

@@ -1,0 +1,241 @@
+// Apply / solve sweeps of the factorization in factored form (sm_103a).
+//
+// F^{-1} = V_0 ... V_last D^{-1} U_last^T ... U_0^T and F = U_0^{-T} ... D ...
+// V_0^{-1} (Eqs. (3.4), (4.1), (4.2)).  One launch per sublevel and direction,
+// one CTA per box: the box's skeleton and redundant entries of the working
+// vectors are gathered into shared memory, the box's small factors (T, L, U,
+// X, Y, D of Lemmas 2.1 and 2.3) are streamed once from HBM, and the result
+// is scattered back.  Boxes of one sublevel touch disjoint DOFs.  The
+// diagonal D^{-1} (or D) is fused into the sweep that last touches a box's
+// redundant DOFs.
+#include <algorithm>
+
+#include "hif_common.cuh"
+#include "launch.h"
+
+namespace hif {
+
+enum SweepMode {
+    SOLVE_UP = 0, SOLVE_DOWN = 1, APPLY_UP = 2, APPLY_DOWN = 3,
+    SOLVET_UP = 4, SOLVET_DOWN = 5, APPLYT_UP = 6, APPLYT_DOWN = 7
+};
+
+namespace {
+
+// out (p x nr) += s * op(M) in, op(M) p x q; M column-major with leading dim ld.
+template <typename T>
+__device__ void mv(T* out, int p, const T* in, int q, const T* M, int64_t ld, bool trans, T s, int nr) {
+    if (!trans) {
+        for (int e = threadIdx.x; e < p * nr; e += blockDim.x) {
+            const int i = e % p, c = e / p;
+            T acc = T(0);
+            for (int l = 0; l < q; ++l) acc += M[i + ld * l] * in[l + q * c];
+            out[i + p * c] += s * acc;
+        }
+    } else {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int e = wid; e < p * nr; e += nw) {
+            const int i = e % p, c = e / p;
+            T acc = T(0);
+            for (int l = lane; l < q; l += 32) acc += M[l + ld * i] * in[l + q * c];
+            acc = warp_sum(acc);
+            if (lane == 0) out[i + p * c] += s * acc;
+        }
+    }
+    __syncthreads();
+}
+
+// out = (I + strict triangle of op(M)) in, n x nr.  lowerStore: the strict
+// part sits in M's lower triangle (else upper); trans: op(M) = M^T.
+template <typename T>
+__device__ void tri(T* out, const T* in, int n, const T* M, int64_t ld, bool lowerStore, bool trans, int nr) {
+    for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
+        const int i = e % n, c = e / n;
+        T acc = in[i + n * c];
+        // op(M)[i,l] = trans ? M[l,i] : M[i,l]; nonzero for l<i if op is lower
+        const bool opLower = lowerStore != trans;
+        if (opLower) {
+            for (int l = 0; l < i; ++l) acc += (trans ? M[l + ld * i] : M[i + ld * l]) * in[l + n * c];
+        } else {
+            for (int l = i + 1; l < n; ++l) acc += (trans ? M[l + ld * i] : M[i + ld * l]) * in[l + n * c];
+        }
+        out[i + n * c] = acc;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void permute(T* out, const T* in, int n, const int* perm, bool inverse, int nr) {
+    for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
+        const int i = e % n, c = e / n;
+        if (!inverse) out[i + n * c] = in[perm[i] + n * c];      // P x
+        else out[perm[i] + n * c] = in[i + n * c];               // P^T x
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void copyv(T* out, const T* in, int cnt) {
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) out[e] = in[e];
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void scale_rows(T* v, const T* D, int n, bool divide, int nr) {
+    for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
+        const int i = e % n;
+        v[e] = divide ? v[e] / D[i] : v[e] * D[i];
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+    const BoxFac bf = a.boxes[blockIdx.x];
+    const int k = bf.k, r = bf.r, nr = a.nrhs;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);
+    T* xr = xs + (size_t)k * nr;
+    T* tmp = xr + (size_t)r * nr;
+    T* x = static_cast<T*>(a.x);
+    const int* sk = a.sk_ids + bf.sk_off;
+    const int* rd = a.rd_ids + bf.rd_off;
+    const T* pool = static_cast<const T*>(a.pool);
+    const T* Tm = pool + bf.T_off;
+    const T* LU = pool + bf.LU_off;
+    const T* LUi = pool + bf.LUi_off;
+    const T* D = pool + bf.D_off;
+    const T* X = pool + bf.X_off;
+    const T* Y = pool + bf.Y_off;
+    const int* perm = a.perm + bf.piv_off;
+
+    for (int e = threadIdx.x; e < k * nr; e += blockDim.x) xs[e] = x[sk[e % k] + a.ldx * (e / k)];
+    for (int e = threadIdx.x; e < r * nr; e += blockDim.x) xr[e] = x[rd[e % r] + a.ldx * (e / r)];
+    __syncthreads();
+
+    if (MODE == SOLVE_UP) {                 // U^T: Q^T then R^T
+        mv<T>(xr, r, xs, k, Tm, k, true, T(-1), nr);
+        permute<T>(tmp, xr, r, perm, false, nr);
+        tri<T>(xr, tmp, r, LUi, r, true, false, nr);
+        mv<T>(xs, k, xr, r, X, k, false, T(-1), nr);
+    } else if (MODE == SOLVE_DOWN) {        // D^{-1} then V = Q S
+        scale_rows<T>(xr, D, r, true, nr);
+        mv<T>(xr, r, xs, k, Y, r, false, T(-1), nr);
+        copyv<T>(tmp, xr, r * nr);
+        tri<T>(xr, tmp, r, LUi, r, false, false, nr);
+        mv<T>(xs, k, xr, r, Tm, k, false, T(-1), nr);
+    } else if (MODE == APPLY_UP) {          // V^{-1} = S^{-1} Q^{-1}, then D
+        mv<T>(xs, k, xr, r, Tm, k, false, T(1), nr);
+        copyv<T>(tmp, xr, r * nr);
+        tri<T>(xr, tmp, r, LU, r, false, false, nr);
+        mv<T>(xr, r, xs, k, Y, r, false, T(1), nr);
+        scale_rows<T>(xr, D, r, false, nr);
+    } else if (MODE == APPLY_DOWN) {        // U^{-T} = Q^{-T} R^{-T}
+        mv<T>(xs, k, xr, r, X, k, false, T(1), nr);
+        tri<T>(tmp, xr, r, LU, r, true, false, nr);
+        permute<T>(xr, tmp, r, perm, true, nr);
+        mv<T>(xr, r, xs, k, Tm, k, true, T(1), nr);
+    } else if (MODE == SOLVET_UP) {         // V^T = S^T Q^T
+        mv<T>(xr, r, xs, k, Tm, k, true, T(-1), nr);
+        copyv<T>(tmp, xr, r * nr);
+        tri<T>(xr, tmp, r, LUi, r, false, true, nr);
+        mv<T>(xs, k, xr, r, Y, r, true, T(-1), nr);
+    } else if (MODE == SOLVET_DOWN) {       // D^{-T} then U = Q R
+        scale_rows<T>(xr, D, r, true, nr);
+        mv<T>(xr, r, xs, k, X, k, true, T(-1), nr);
+        tri<T>(tmp, xr, r, LUi, r, true, true, nr);
+        permute<T>(xr, tmp, r, perm, true, nr);
+        mv<T>(xs, k, xr, r, Tm, k, false, T(-1), nr);
+    } else if (MODE == APPLYT_UP) {         // U^{-1} = R^{-1} Q^{-1}, then D
+        mv<T>(xs, k, xr, r, Tm, k, false, T(1), nr);
+        permute<T>(tmp, xr, r, perm, false, nr);
+        tri<T>(xr, tmp, r, LU, r, true, true, nr);
+        mv<T>(xr, r, xs, k, X, k, true, T(1), nr);
+        scale_rows<T>(xr, D, r, false, nr);
+    } else {                                // APPLYT_DOWN: V^{-T} = Q^{-T} S^{-T}
+        mv<T>(xs, k, xr, r, Y, r, true, T(1), nr);
+        copyv<T>(tmp, xr, r * nr);
+        tri<T>(xr, tmp, r, LU, r, false, true, nr);
+        mv<T>(xr, r, xs, k, Tm, k, true, T(1), nr);
+    }
+
+    for (int e = threadIdx.x; e < k * nr; e += blockDim.x) x[sk[e % k] + a.ldx * (e / k)] = xs[e];
+    for (int e = threadIdx.x; e < r * nr; e += blockDim.x) x[rd[e % r] + a.ldx * (e / r)] = xr[e];
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_mode(const SweepArgs& a, int nbox, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep_kernel<T, MODE><<<nbox, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// The caller sizes a.nrhs so that (k + 2r) * nrhs * sizeof(T) fits; the
+// dynamic shared memory is passed through a.mode's high bits.
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs& a, int nbox, cudaStream_t st) {
+    if (nbox == 0) return cudaSuccess;
+    const size_t smem = (size_t)(a.mode >> 8);
+    switch (a.mode & 0xff) {
+        case SOLVE_UP: return launch_mode<T, SOLVE_UP>(a, nbox, smem, st);
+        case SOLVE_DOWN: return launch_mode<T, SOLVE_DOWN>(a, nbox, smem, st);
+        case APPLY_UP: return launch_mode<T, APPLY_UP>(a, nbox, smem, st);
+        case APPLY_DOWN: return launch_mode<T, APPLY_DOWN>(a, nbox, smem, st);
+        case SOLVET_UP: return launch_mode<T, SOLVET_UP>(a, nbox, smem, st);
+        case SOLVET_DOWN: return launch_mode<T, SOLVET_DOWN>(a, nbox, smem, st);
+        case APPLYT_UP: return launch_mode<T, APPLYT_UP>(a, nbox, smem, st);
+        case APPLYT_DOWN: return launch_mode<T, APPLYT_DOWN>(a, nbox, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_sweep<double>(const SweepArgs&, int, cudaStream_t);
+template cudaError_t launch_sweep<float>(const SweepArgs&, int, cudaStream_t);
+
+// ---------------------------------------------------- precision moves ----
+
+template <typename T>
+__global__ void to_work_kernel(const double* src, int64_t lds, T* dst, int64_t ldd, int64_t N, int nrhs) {
+    const int64_t tot = N * nrhs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % N, c = e / N;
+        dst[i + ldd * c] = (T)src[i + lds * c];
+    }
+}
+
+template <typename T>
+__global__ void from_work_kernel(const T* src, int64_t lds, double* dst, int64_t ldd, int64_t N, int nrhs) {
+    const int64_t tot = N * nrhs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % N, c = e / N;
+        dst[i + ldd * c] = (double)src[i + lds * c];
+    }
+}
+
+template <typename T>
+cudaError_t launch_to_work(const double* src, int64_t lds, T* dst, int64_t ldd, int64_t N, int nrhs, cudaStream_t st) {
+    const int64_t tot = N * nrhs;
+    if (tot == 0) return cudaSuccess;
+    const int blocks = (int)((tot + 255) / 256 < 152 * 16 ? (tot + 255) / 256 : 152 * 16);
+    to_work_kernel<T><<<blocks, 256, 0, st>>>(src, lds, dst, ldd, N, nrhs);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_from_work(const T* src, int64_t lds, double* dst, int64_t ldd, int64_t N, int nrhs, cudaStream_t st) {
+    const int64_t tot = N * nrhs;
+    if (tot == 0) return cudaSuccess;
+    const int blocks = (int)((tot + 255) / 256 < 152 * 16 ? (tot + 255) / 256 : 152 * 16);
+    from_work_kernel<T><<<blocks, 256, 0, st>>>(src, lds, dst, ldd, N, nrhs);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_to_work<double>(const double*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);
+template cudaError_t launch_to_work<float>(const double*, int64_t, float*, int64_t, int64_t, int, cudaStream_t);
+template cudaError_t launch_from_work<double>(const double*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);
+template cudaError_t launch_from_work<float>(const float*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);
+
+}  // namespace hif

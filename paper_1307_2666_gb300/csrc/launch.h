@@ -1,0 +1,152 @@
+// Kernel argument blocks and host-side launchers (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hif_types.h"
+
+namespace hif {
+
+struct FoldArgs {
+    GeomDev g;
+    SciDev sci;
+    const BoxDesc* boxes;
+    const int* cols;
+    const int* near;
+    const GroupDesc* groups;
+    const double* proxy;      // P x dim unit directions
+    int P;
+    int bpairs;
+    int second_kind;
+    int R_in_smem;
+    void* Rws;
+    void* GKws;
+    void* GSws;
+};
+
+struct IdArgs {
+    const GroupDesc* groups;
+    const BoxDesc* boxes;
+    const void* Rws;
+    const void* GKws;
+    const void* GSws;
+    void* Wws;
+    const int64_t* W_off;
+    int W_in_smem;
+    int second_kind;
+    void* Tws;
+    int* perm_out;
+    int* k_out;
+    double eps;
+    double tol_floor;
+};
+
+struct ElimArgs {
+    GeomDev g;
+    SciDev sci;
+    const ElimDesc* boxes;
+    const ElimGroup* groups;
+    const int* sk_ids;
+    const int* rd_ids;
+    const void* Tws;
+    void* ws;
+    void* fac_pool;
+    int* piv_pool;
+    int* perm_pool;
+    void* sci_pool;
+    int* status;
+};
+
+struct TopArgs {            // assembly of A_L over s_L (Sec. 3.1, level L)
+    GeomDev g;
+    SciDev sci;
+    const int* ids;
+    int n;
+    void* A;                // n x n column-major
+};
+
+struct SweepArgs {
+    const BoxFac* boxes;
+    const int* sk_ids;
+    const int* rd_ids;
+    const void* pool;
+    const int* perm;
+    void* x;                // working vectors, N x nrhs column-major (factor precision)
+    int64_t ldx;
+    int nrhs;
+    int mode;               // see k_sweep.cu
+};
+
+size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem);
+size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem);
+
+template <typename T> cudaError_t launch_fold(const FoldArgs&, int nbox, size_t smem, cudaStream_t);
+template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t smem, cudaStream_t);
+template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStream_t);
+
+// top block
+template <typename T> cudaError_t launch_top_assemble(const TopArgs&, cudaStream_t);
+template <typename T> cudaError_t top_lu(T* A, int n, int* piv, int* status, cudaStream_t);
+template <typename T> cudaError_t top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t);
+template <typename T> cudaError_t launch_top_gemm(const T* M, int n, bool trans, const int* ids,
+                                                  T* x, int64_t ldx, int nrhs, T* tmp, cudaStream_t);
+
+// sweeps
+template <typename T> cudaError_t launch_sweep(const SweepArgs&, int nbox, cudaStream_t);
+
+// vectors and direct sums (FP64 inputs)
+template <typename T> cudaError_t launch_to_work(const double* src, int64_t lds, T* dst, int64_t ldd,
+                                                 int64_t N, int nrhs, cudaStream_t);
+template <typename T> cudaError_t launch_from_work(const T* src, int64_t lds, double* dst, int64_t ldd,
+                                                   int64_t N, int nrhs, cudaStream_t);
+
+struct DirectArgs {
+    GeomDev g;
+    const double* x;        // N x nrhs
+    int64_t ldx;
+    double* y;
+    int64_t ldy;
+    int nrhs;
+    int trans;
+};
+cudaError_t launch_direct_general(const DirectArgs&, cudaStream_t);
+
+struct GridDirectArgs {     // uniform tensor grid: K depends on the index offset only
+    const double* table;    // n^dim entries: G(h |delta|) for delta != 0, K_self / w at 0
+    const int* dof_of;      // grid position -> DOF id
+    int n;                  // points per side
+    int dim;
+    const double* a;
+    const double* b;
+    const double* c;
+    const double* w;
+    const double* x;
+    int64_t ldx;
+    double* y;
+    int64_t ldy;
+    int nrhs;
+    int trans;
+    double* vbuf;           // N x nrhs scratch (grid order)
+    double* ybuf;           // N x nrhs scratch (grid order)
+};
+cudaError_t launch_direct_grid(const GridDirectArgs&, cudaStream_t);
+cudaError_t launch_grid_table(double* table, int n, int dim, double h, int kernel_id, double kself_over_w,
+                              cudaStream_t);
+
+cudaError_t launch_kernel_block(const GeomDev& g, const int* rows, int64_t nr, const int* cols, int64_t nc,
+                                double* out, int64_t ldo, cudaStream_t);
+cudaError_t launch_kself(const GeomDev& g, double* kself, cudaStream_t);
+
+// BLAS-1 helpers for the refinement loops (FP64)
+cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int64_t ldx, double beta,
+                         double* y, int64_t ldy, cudaStream_t);
+cudaError_t launch_col_dots(int64_t N, int nrhs, const double* x, int64_t ldx, const double* y, int64_t ldy,
+                            double* out, cudaStream_t);
+
+// Batched ID on caller-provided matrices (hif_id_batched)
+cudaError_t launch_id_batched(int count, const double* mats, const int64_t* off, const int* m, const int* n,
+                              const double* tol, int* k, int* perm, const int64_t* poff, double* T,
+                              const int64_t* toff, cudaStream_t);
+
+}  // namespace hif

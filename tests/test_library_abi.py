@@ -1,0 +1,88 @@
+"""The C ABI library builds, loads without a GPU and exports every symbol the
+public header declares; the Python binding mirrors the header's structs."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(hif_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1307_2666_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["hif_factor", "hif_apply", "hif_solve", "hif_solve_transpose", "hif_destroy",
+                     "hif_apply_transpose", "hif_matvec", "hif_solve_refined", "hif_stats"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header(lib):
+    from paper_1307_2666_gb300 import hif
+    for name in _declared():
+        assert name in hif.EXPORTS, name
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_1307_2666_gb300 import hif
+    # hif_options_default fills every field; defaults from the header comment
+    o = hif.hif_options_default(2)
+    assert (o.dim, o.leaf_occupancy, o.second_kind, o.precision, o.fractional_levels) == (2, 64, 1, 0, 1)
+    assert o.proxy_points == 64 and o.proxy_radius == 1.5 and o.fp32_tol_floor == 2.0 ** -20
+    o3 = hif.hif_options_default(3)
+    assert o3.proxy_points == 512
+
+
+def test_ctypes_layouts_match_c_compiler(tmp_path):
+    # compile a probe against the header and compare sizes / offsets
+    import subprocess
+    from paper_1307_2666_gb300 import hif
+    src = tmp_path / "probe.c"
+    src.write_text('''#include <stdio.h>
+#include <stddef.h>
+#include "hif.h"
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hif_options), offsetof(hif_options, proxy_radius),
+ offsetof(hif_options, stream), sizeof(hif_stats_t), offsetof(hif_stats_t, kinds), offsetof(hif_stats_t, flops),
+ offsetof(hif_stats_t, top_size)); return 0;}''')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    O, S = hif.hif_options, hif.hif_stats_t
+    want = [ctypes.sizeof(O), O.proxy_radius.offset, O.stream.offset, ctypes.sizeof(S), S.kinds.offset,
+            S.flops.offset, S.top_size.offset]
+    assert got == want
+
+
+def test_status_strings_and_argument_errors(lib):
+    from paper_1307_2666_gb300 import hif
+    L = hif.load()
+    assert L.hif_status_string(0) == b"HIF_OK"
+    assert b"EINVAL" in L.hif_status_string(1)
+    # invalid arguments are rejected before any device work (no GPU needed)
+    h = ctypes.c_void_p()
+    assert L.hif_factor(None, 10, None, None, None, None, 0, 1e-6, None, ctypes.byref(h)) == hif.HIF_EINVAL
+    assert h.value is None
+    assert L.hif_options_default(4, None) == hif.HIF_EINVAL
+    assert L.hif_destroy(None) == hif.HIF_OK
+    assert L.hif_apply(None, None, None, 1, 1) == hif.HIF_EINVAL
