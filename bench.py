@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput of the HIF-IE hot path on GB300.
+
+One step = factor A (Algorithm 4.1, second-kind modifications of Sec. 4.4) in
+FP32 and solve all right-hand sides to relative residual 1e-10 by iterative
+refinement preconditioned with the factorization, residuals from the FP64
+direct-sum operator.  Workload: 2D second-kind volume IE on the unit square,
+n = 1024 (N = 1,048,576), kernel -log(r)/(2 pi), a = 1, b = c = 1 + 0.5 phi
+(16 random-phase cosines), eps = 1e-6, 8 Gaussian right-hand sides.
+
+value = (all ranks) N * nrhs / (time per step): unknowns solved to 1e-10 per
+second, factorization included.  Multi-GPU runs are independent replicas
+(weak scaling; the single-problem path has no data-parallel split).
+
+``--impl reference`` times the CPU oracle (plain numpy, FP64) on a bounded
+sample of the same workload on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "factor s + solve DOF/s on GB300 at stated rel. err; FP32+refine/batched vs FP64"
+UNIT = "DOF/s"
+TOL = 1e-10
+ORACLE_SAMPLE_N = 64
+
+
+def workload_config(n, nrhs, eps):
+    return {
+        "workload": (f"2D second-kind volume IE, unit square, n={n} (N={n * n}), kernel -log(r)/2pi, "
+                     f"a=1, b=c=1+0.5*phi (16 random-phase cosines, seed 1002), eps={eps:g}, "
+                     f"{nrhs} Gaussian RHS (seed 1003); FP32 HIF-IE factorization + iterative refinement "
+                     f"to rel. residual {TOL:g} with FP64 direct-sum residual"),
+        "n": n, "N": n * n, "nrhs": nrhs, "eps": eps, "tol": TOL,
+        "l2": "inputs larger than L2 (factor data and the 8-RHS vectors exceed the 129 MB L2)",
+    }
+
+
+# ----------------------------------------------------------------- oracle --
+
+def oracle_sample(n=ORACLE_SAMPLE_N, eps=1e-6):
+    """The oracle as it stands on a bounded sample: FP64 sequential HIF-IE
+    factorization + iterative refinement to 1e-10 with the oracle's direct-sum
+    matvec, one right-hand side."""
+    import numpy as np
+    import hif_inputs as hi
+    from oracle import hifie, kernels, krylov
+    pb = hi.volume_problem(n, 2, smooth_seed=1002, rhs_seed=1003, nrhs=1)
+    t0 = time.perf_counter()
+    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, eps, pb.proxy)
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    u, its, hist = krylov.refine(op.matvec, pb.f[:, 0], F.solve, tol=TOL)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "N": pb.N, "nrhs": 1, "value": pb.N / dt, "iters": its, "relres": float(hist[-1]),
+            "sample": (f"oracle FP64 HIF-IE factor + iterative refinement to {TOL:g} (oracle direct-sum residual), "
+                       f"1 RHS, n={n} grid (N={pb.N}) of the same IE; value = N/time")}
+
+
+def run_oracle_subprocess(n=ORACLE_SAMPLE_N):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample-json", str(n)],
+                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stdout[-2000:] + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU arm ---
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    import __graft_entry__
+    __graft_entry__.build()
+    import hif_inputs as hi
+    import paper_1307_2666_gb300 as P
+    from paper_1307_2666_gb300 import hif as H
+
+    dev = torch.device(f"cuda:{local}")
+    n, nrhs, eps = args.n, args.nrhs, args.eps
+    pb = hi.volume_problem(n, 2, smooth_seed=1002, rhs_seed=1003, nrhs=nrhs)
+    T = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev)
+    pts, w, a, b, c = T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)
+    F = T(pb.f.T).t()                                    # column-major N x nrhs on the device
+    N = pb.N
+    stats = {}
+
+    def step(precision="fp32"):
+        fac = P.Factorization(pts, w, a, b, c, 0, eps, precision=precision)
+        u, its, rel = fac.solve_refined(F, tol=TOL, method="ir")
+        stats.update(iters=its, relres=rel, top=fac.stats()["top_size"], mf=fac.stats()["factor_bytes"],
+                     t_factor=fac.stats()["factor_seconds"])
+        fac.close()
+        return u
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = H.hif_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    barrier()
+    launches = H.hif_kernel_launches() - launches0
+    clocks = sampler.stop()
+    t_local = ev0.elapsed_time(ev1) / 1000.0
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    ms_per_step = 1000.0 * t_max / args.steps
+    value = world * N * nrhs * args.steps / t_max
+
+    # ---- solve-only split of one step, for the report
+    fac = P.Factorization(pts, w, a, b, c, 0, eps, precision="fp32")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    u, its, rel = fac.solve_refined(F, tol=TOL, method="ir")
+    e1.record()
+    torch.cuda.synchronize()
+    t_solve = e0.elapsed_time(e1) / 1000.0
+    t_factor = fac.stats()["factor_seconds"]
+
+    # ---- dominant kernel: FP64 direct-sum matvec (uniform-grid convolution), all RHS in one launch
+    y = torch.empty_like(F)
+    reps = 2
+    e0.record()
+    for _ in range(reps):
+        P.hif_matvec(fac.h, 0, F, y)
+    e1.record()
+    torch.cuda.synchronize()
+    t_mv = e0.elapsed_time(e1) / 1000.0 / reps
+    flops_mv = 2.0 * N * N * nrhs
+    fac.close()
+    peaks = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12                # TFLOP/s: 152 SMs x 2 FP64 FMA/clk
+    achieved = flops_mv / t_mv / 1e12
+    roofline = {"kernel": "grid_conv_kernel (FP64 direct sum, uniform-grid convolution)",
+                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz (no measured FP64 peak)",
+                "algorithmic_per_launch": f"2*N^2*nrhs = {flops_mv:.3e} flop", "traffic": None}
+
+    # ---- FP64 factorization path for comparison (one step)
+    fp64 = None
+    if args.compare_fp64:
+        e0.record()
+        step("fp64")
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1000.0
+        fp64 = {"ms_per_step": 1000 * t64, "value": N * nrhs / t64, "iters": stats.get("iters"),
+                "relres": stats.get("relres"), "top_size": stats.get("top"), "t_factor_s": stats.get("t_factor")}
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    hp = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64).pin_memory()
+    h_pts, h_w, h_a, h_b, h_c = hp(pb.points), hp(pb.weights), hp(pb.a), hp(pb.b), hp(pb.c)
+    h_f = hp(pb.f.T).t()
+    h_u = torch.empty((nrhs, N), dtype=torch.float64).pin_memory().t()
+    opt = H.hif_options_default(2)
+    opt.precision = 1
+    barrier()
+    t0 = time.perf_counter()
+    e0.record()
+    hdl = H.hif_factor(h_pts, h_w, h_a, h_b, h_c, 0, eps, opt)
+    H.hif_solve_refined(hdl, 0, h_f, h_u, TOL, 50, 0)
+    e1.record()
+    torch.cuda.synchronize()
+    t_e2e = max(e0.elapsed_time(e1) / 1000.0, time.perf_counter() - t0)
+    H.hif_destroy(hdl)
+    h2d = (pb.points.nbytes + 4 * pb.weights.nbytes + pb.f.nbytes)
+    d2h = pb.f.nbytes
+    e2e = {"value": N * nrhs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "seconds": t_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = run_oracle_subprocess()
+        cpu = {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": s["sample"],
+               "seconds": s["seconds"], "iters": s["iters"], "relres": s["relres"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 factorization, f64 residual", "data": "synthetic",
+            "config": dict(workload_config(n, nrhs, eps), parallelism=f"replicas x{world}"),
+            "t_factor_s": t_factor, "t_solve_s": t_solve, "refine_iters": its, "relres": rel,
+            "top_size": stats.get("top"), "factor_bytes": stats.get("mf"),
+            "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    sample = None
+    for _ in range(args.warmup):
+        run_oracle_subprocess()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = run_oracle_subprocess()
+        vals.append(s["seconds"])
+        sample = s
+    t = time.perf_counter() - t0
+    value = sample["N"] * args.steps / sum(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(vals) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(args.n, args.nrhs, args.eps), parallelism="host cores x1"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": t}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--nrhs", type=int, default=8)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample-json", type=int, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample_json is not None:
+        print(json.dumps(oracle_sample(args.oracle_sample_json)))
+        return
+    if args.warmup < 3 and args.impl == "gpu":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -148,6 +148,10 @@ const char* hif_status_string(hif_status s);
  * error text when the failure came from the runtime); empty if none. */
 const char* hif_last_error(void);
 
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all handles, all threads); callers difference it around a region. */
+uint64_t hif_kernel_launches(void);
+
 /*
  * hif_kernel_block -- entries A_ij = a_i delta_ij + b_i K_ij c_j (Eq. (3.1))
  * for i in rows[0..nr), j in cols[0..nc), written column-major to

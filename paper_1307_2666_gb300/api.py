@@ -17,6 +17,8 @@ def _colmajor(x: torch.Tensor) -> torch.Tensor:
         raise TypeError("vectors must be float64")
     if x.ndim == 1:
         return x.contiguous()
+    if x.shape[1] == 1:
+        return x.contiguous()
     if x.stride(0) == 1 and x.stride(1) >= x.shape[0]:
         return x
     return x.t().contiguous().t()

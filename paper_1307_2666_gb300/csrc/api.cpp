@@ -7,9 +7,11 @@
 // one elimination launch; the host reads back only the ranks and skeleton
 // permutations it needs to form the next sublevel.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -41,6 +43,9 @@ struct Err {
     } while (0)
 
 static thread_local char g_last_error[512];
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static void fail(hif_status s, const char* msg) {
     std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
@@ -222,6 +227,115 @@ static void detect_grid(hif_handle h) {
     upload(h->dof_of, dof_of, h->st);
 }
 
+static int env_int(const char* name, int dflt) {
+    const char* v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    return std::atoi(v);
+}
+
+struct BigBuffers {
+    DevMem bb, bg, state, YK, YS, vv, vw, vt, est, nrm, perm;
+};
+
+// ID of the large boxes of one sublevel: Y_c materialized in HBM, pivoted QR
+// by per-step launches shared by all large column groups.
+template <typename T>
+static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd, const std::vector<GroupDesc>& gd,
+                       const SublevelPlan& p, const std::vector<int>& big_boxes, DevMem& d_boxes, DevMem& d_groups,
+                       DevMem& d_cols, DevMem& d_near, DevMem& Tws, DevMem& perm_out, DevMem& k_out,
+                       double tol_floor, BigBuffers& B) {
+    (void)p;
+    const cudaStream_t st = h->st;
+    std::vector<BigBox> bbv;
+    std::vector<BigGroup> bgv;
+    int64_t yoff = 0, voff = 0, roff = 0, max_entries = 0;
+    int max_m = 0, max_n = 0, maxk = 0;
+    bool split = false;
+    for (int bI : big_boxes) {
+        const BoxDesc& b = bd[bI];
+        BigBox x{};
+        x.box = bI;
+        x.m = 2 * (b.m_near + h->P);
+        x.y_off = yoff;
+        yoff += (int64_t)x.m * b.n;
+        max_entries = std::max(max_entries, (int64_t)(b.m_near + h->P) * b.n);
+        if (b.has_sci && h->second_kind && tau > 0) split = true;
+        for (int q = 0; q < b.ngroups; ++q) {
+            const int64_t gi = b.grp_off + q;
+            const GroupDesc& G = gd[gi];
+            BigGroup y{};
+            y.group = (int)gi;
+            y.n = G.n;
+            y.m = x.m;
+            y.need_rho = (h->second_kind && G.has_sci && b.has_sci && tau > 0) ? 1 : 0;
+            y.y_off = x.y_off + (int64_t)x.m * G.col0;
+            y.vec_off = voff;
+            y.row_off = roff;
+            voff += G.n;
+            roff += x.m;
+            max_m = std::max(max_m, x.m);
+            max_n = std::max(max_n, G.n);
+            maxk = std::max(maxk, std::min(x.m, G.n));
+            bgv.push_back(y);
+        }
+        bbv.push_back(x);
+    }
+    const int ng = (int)bgv.size();
+    upload(B.bb, bbv, st);
+    upload(B.bg, bgv, st);
+    B.state.ensure(sizeof(BigState) * ng);
+    B.YK.ensure(sizeof(T) * std::max<int64_t>(yoff, 1));
+    if (split) B.YS.ensure(sizeof(T) * yoff);
+    B.vv.ensure(sizeof(double) * 2 * std::max<int64_t>(voff, 1));
+    B.vw.ensure(sizeof(double) * 2 * std::max<int64_t>(voff, 1));
+    B.vt.ensure(sizeof(double) * 2 * std::max<int64_t>(roff, 1));
+    B.est.ensure(sizeof(double) * 2 * ng);
+    B.nrm.ensure(sizeof(double) * std::max<int64_t>(voff, 1));
+    B.perm.ensure(sizeof(int) * std::max<int64_t>(voff, 1));
+    BigArgs a{};
+    a.g = geom(h);
+    a.sci = scidev(h, (int)tau);
+    a.boxes = d_boxes.as<BoxDesc>();
+    a.bigboxes = B.bb.as<BigBox>();
+    a.cols = d_cols.as<int>();
+    a.near = d_near.as<int>();
+    a.proxy = h->proxy.as<double>();
+    a.P = h->P;
+    a.second_kind = h->second_kind;
+    a.YK = B.YK.p;
+    a.YS = split ? B.YS.p : nullptr;
+    a.groups = B.bg.as<BigGroup>();
+    a.state = B.state.as<BigState>();
+    a.gdesc = d_groups.as<GroupDesc>();
+    a.vec_v = B.vv.as<double>();
+    a.vec_w = B.vw.as<double>();
+    a.vec_t = B.vt.as<double>();
+    a.est = B.est.as<double>();
+    a.nrm = B.nrm.as<double>();
+    a.perm = B.perm.as<int>();
+    a.Tws = Tws.p;
+    a.perm_out = perm_out.as<int>();
+    a.k_out = k_out.as<int>();
+    a.eps = h->eps;
+    a.tol_floor = tol_floor;
+    HIF_CUDA((big_ygen<T>(a, (int)bbv.size(), max_entries, st)));
+    HIF_CUDA((big_rho<T>(a, ng, max_m, max_n, st)));
+    if (split) HIF_CUDA((big_add<T>(B.YK.p, B.YS.p, yoff, st)));
+    HIF_CUDA((big_qr_init<T>(a, ng, max_n, st)));
+    std::vector<BigState> hs(ng);
+    for (int j = 0; j < maxk; ++j) {
+        HIF_CUDA((big_qr_step<T>(a, ng, max_n, j, st)));
+        if ((j + 1) % 16 == 0) {
+            HIF_CUDA(cudaMemcpyAsync(hs.data(), B.state.p, sizeof(BigState) * ng, cudaMemcpyDeviceToHost, st));
+            HIF_CUDA(cudaStreamSynchronize(st));
+            bool all = true;
+            for (const BigState& x : hs) all = all && x.stop;
+            if (all) break;
+        }
+    }
+    HIF_CUDA((big_finish<T>(a, ng, max_n, st)));
+}
+
 template <typename T>
 static void run_factor(hif_handle h) {
     const cudaStream_t st = h->st;
@@ -252,7 +366,11 @@ static void run_factor(hif_handle h) {
     std::vector<char> active(N, 1);
     std::vector<int> box_of(N, -1);
     DevMem d_boxes, d_groups, d_cols, d_near, Rws, GKws, GSws, Tws, Wws, Woff, perm_out, k_out;
-    DevMem d_ed, d_eg, d_sk, d_rd, ews, piv_scratch;
+    DevMem d_ed, d_eg, d_sk, d_rd, ews, piv_scratch, d_small_boxes, d_small_groups;
+    BigBuffers big;
+    const int big_id_n = env_int("HIF_BIG_ID", sizeof(T) == 8 ? 128 : 256);
+    const int big_elim_n = env_int("HIF_BIG_ELIM", 600);
+    const bool trace = env_int("HIF_TRACE", 0) != 0;
     double flops = 0, evals = 0;
     const double tol_floor = sizeof(T) == 4 ? h->opt.fp32_tol_floor : 0.0;
 
@@ -265,6 +383,7 @@ static void run_factor(hif_handle h) {
         for (int64_t i = 0; i < N; ++i)
             if (active[i]) act_ids.push_back((int)i);
         for (int i : act_ids) box_of[i] = -1;
+        const auto tr0 = std::chrono::steady_clock::now();
         SublevelPlan p;
         partition(t, h->hx.data(), kind, s, act_ids, p, box_of);
         build_near_groups(t, h->hx.data(), s, h->opt.proxy_radius, h->second_kind, act_ids, active, box_of, sci, p);
@@ -278,21 +397,27 @@ static void run_factor(hif_handle h) {
         int maxn = 0, maxng = 0, maxmrow = 0;
         bool any_sci = false;
         std::vector<int64_t> woff(ngr);
+        std::vector<int> small_boxes, small_groups, big_boxes;
         for (int bI = 0; bI < nb; ++bI) {
             BoxDesc& b = bd[bI];
+            const bool big = (p.box_off[bI + 1] - p.box_off[bI]) > big_id_n;
             b.n = (int)(p.box_off[bI + 1] - p.box_off[bI]);
             b.m_near = (int)(p.near_off[bI + 1] - p.near_off[bI]);
             b.ngroups = (int)(p.grp_off[bI + 1] - p.grp_off[bI]);
             b.has_sci = p.box_sci[bI];
-            any_sci = any_sci || b.has_sci;
             b.col_off = p.box_off[bI];
             b.near_off = p.near_off[bI];
             b.grp_off = p.grp_off[bI];
             b.R_off = Roff;
-            Roff += (int64_t)b.n * b.n;
+            if (!big) Roff += (int64_t)b.n * b.n;
             for (int k = 0; k < 3; ++k) b.ctr[k] = p.centers[3 * bI + k];
             b.radius = h->opt.proxy_radius * wl;
-            maxn = std::max(maxn, b.n);
+            if (big) big_boxes.push_back(bI);
+            else {
+                small_boxes.push_back(bI);
+                maxn = std::max(maxn, b.n);
+                if (b.has_sci) any_sci = true;
+            }
             const double m = 2.0 * (b.m_near + h->P);
             evals += (m / 2) * b.n;
             flops += 2.0 * m * b.n * b.n;
@@ -308,9 +433,12 @@ static void run_factor(hif_handle h) {
                 G.perm_off = b.col_off + G.col0;
                 const int mrow = G.col0 + G.n;
                 woff[gi] = Woffs;
-                Woffs += (int64_t)(mrow | 1) * G.n;
-                maxng = std::max(maxng, G.n);
-                maxmrow = std::max(maxmrow, mrow);
+                if (!big) {
+                    small_groups.push_back((int)gi);
+                    Woffs += (int64_t)(mrow | 1) * G.n;
+                    maxng = std::max(maxng, G.n);
+                    maxmrow = std::max(maxmrow, mrow);
+                }
             }
         }
         upload(d_boxes, bd, st);
@@ -318,6 +446,8 @@ static void run_factor(hif_handle h) {
         upload(d_cols, p.cols, st);
         upload(d_near, p.near, st);
         upload(Woff, woff, st);
+        upload(d_small_boxes, small_boxes, st);
+        upload(d_small_groups, small_groups, st);
         Rws.ensure(sizeof(T) * std::max<int64_t>(Roff, 1));
         const bool grams = h->second_kind && any_sci;
         if (grams) {
@@ -328,62 +458,70 @@ static void run_factor(hif_handle h) {
         perm_out.ensure(sizeof(int) * std::max<size_t>(p.cols.size(), 1));
         k_out.ensure(sizeof(int) * std::max<int64_t>(ngr, 1));
 
-        FoldArgs fa{};
-        fa.g = g;
-        fa.sci = scidev(h, (int)tau);
-        fa.boxes = d_boxes.as<BoxDesc>();
-        fa.cols = d_cols.as<int>();
-        fa.near = d_near.as<int>();
-        fa.groups = d_groups.as<GroupDesc>();
-        fa.proxy = h->proxy.as<double>();
-        fa.P = h->P;
-        fa.bpairs = 16;
-        fa.second_kind = h->second_kind;
-        fa.Rws = Rws.p;
-        fa.GKws = grams ? GKws.p : nullptr;
-        fa.GSws = grams ? GSws.p : nullptr;
-        size_t smem = fold_smem_bytes(maxn, fa.bpairs, grams, true, sizeof(T));
-        fa.R_in_smem = smem <= 200 * 1024;
-        if (!fa.R_in_smem) {
-            fa.bpairs = maxn > 512 ? 4 : 8;
-            smem = fold_smem_bytes(maxn, fa.bpairs, grams, false, sizeof(T));
-            if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
-        }
-        HIF_CUDA((launch_fold<T>(fa, nb, smem, st)));
+        if (!small_boxes.empty()) {
+            FoldArgs fa{};
+            fa.g = g;
+            fa.sci = scidev(h, (int)tau);
+            fa.boxes = d_boxes.as<BoxDesc>();
+            fa.box_list = d_small_boxes.as<int>();
+            fa.cols = d_cols.as<int>();
+            fa.near = d_near.as<int>();
+            fa.groups = d_groups.as<GroupDesc>();
+            fa.proxy = h->proxy.as<double>();
+            fa.P = h->P;
+            fa.bpairs = 16;
+            fa.second_kind = h->second_kind;
+            fa.Rws = Rws.p;
+            fa.GKws = grams ? GKws.p : nullptr;
+            fa.GSws = grams ? GSws.p : nullptr;
+            size_t smem = fold_smem_bytes(maxn, fa.bpairs, grams, true, sizeof(T));
+            fa.R_in_smem = smem <= 200 * 1024;
+            if (!fa.R_in_smem) {
+                fa.bpairs = 8;
+                smem = fold_smem_bytes(maxn, fa.bpairs, grams, false, sizeof(T));
+                if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
+            }
+            HIF_CUDA((launch_fold<T>(fa, (int)small_boxes.size(), smem, st)));
 
-        IdArgs ia{};
-        ia.groups = d_groups.as<GroupDesc>();
-        ia.boxes = d_boxes.as<BoxDesc>();
-        ia.Rws = Rws.p;
-        ia.GKws = grams ? GKws.p : nullptr;
-        ia.GSws = grams ? GSws.p : nullptr;
-        ia.second_kind = h->second_kind;
-        ia.Tws = Tws.p;
-        ia.perm_out = perm_out.as<int>();
-        ia.k_out = k_out.as<int>();
-        ia.eps = h->eps;
-        ia.tol_floor = tol_floor;
-        size_t ismem = id_smem_bytes(maxng, maxmrow, true, sizeof(T));
-        ia.W_in_smem = ismem <= 200 * 1024;
-        if (!ia.W_in_smem) {
-            Wws.ensure(sizeof(T) * std::max<int64_t>(Woffs, 1));
-            ismem = id_smem_bytes(maxng, maxmrow, false, sizeof(T));
+            IdArgs ia{};
+            ia.groups = d_groups.as<GroupDesc>();
+            ia.group_list = d_small_groups.as<int>();
+            ia.boxes = d_boxes.as<BoxDesc>();
+            ia.Rws = Rws.p;
+            ia.GKws = grams ? GKws.p : nullptr;
+            ia.GSws = grams ? GSws.p : nullptr;
+            ia.second_kind = h->second_kind;
+            ia.Tws = Tws.p;
+            ia.perm_out = perm_out.as<int>();
+            ia.k_out = k_out.as<int>();
+            ia.eps = h->eps;
+            ia.tol_floor = tol_floor;
+            size_t ismem = id_smem_bytes(maxng, maxmrow, true, sizeof(T));
+            ia.W_in_smem = ismem <= 200 * 1024;
+            if (!ia.W_in_smem) {
+                Wws.ensure(sizeof(T) * std::max<int64_t>(Woffs, 1));
+                ismem = id_smem_bytes(maxng, maxmrow, false, sizeof(T));
+            }
+            ia.Wws = Wws.p;
+            ia.W_off = Woff.as<int64_t>();
+            HIF_CUDA((launch_id<T>(ia, (int)small_groups.size(), ismem, st)));
         }
-        ia.Wws = Wws.p;
-        ia.W_off = Woff.as<int64_t>();
-        HIF_CUDA((launch_id<T>(ia, (int)ngr, ismem, st)));
+        if (!big_boxes.empty()) run_big_id<T>(h, tau, bd, gd, p, big_boxes, d_boxes, d_groups, d_cols, d_near, Tws,
+                                              perm_out, k_out, tol_floor, big);
 
+        const auto tr1 = std::chrono::steady_clock::now();
         std::vector<int> kg(ngr), permh(p.cols.size());
         if (ngr) HIF_CUDA(cudaMemcpyAsync(kg.data(), k_out.p, sizeof(int) * ngr, cudaMemcpyDeviceToHost, st));
         if (!permh.empty())
             HIF_CUDA(cudaMemcpyAsync(permh.data(), perm_out.p, sizeof(int) * permh.size(), cudaMemcpyDeviceToHost, st));
         HIF_CUDA(cudaStreamSynchronize(st));
+        const auto tr2 = std::chrono::steady_clock::now();
 
         // ---- skeleton / redundant sets, elimination descriptors
         auto sf = std::make_unique<SubFactor>();
         sf->kind = kind;
         sf->level = ell;
-        std::vector<ElimDesc> ed;
+        std::vector<ElimDesc> ed, ed_big;
         std::vector<ElimGroup> eg;
         std::vector<int> skv, rdv;
         int64_t fac_off = 0, piv_off = 0, sci_off = 0, ws_off = 0;
@@ -460,12 +598,13 @@ static void run_factor(hif_handle h) {
             bf.piv_off = e.piv_out;
             sf->hbox.push_back(bf);
             sf->max_kr2 = std::max(sf->max_kr2, k + 2 * r);
-            ed.push_back(e);
+            if (k + r > big_elim_n) ed_big.push_back(e);
+            else ed.push_back(e);
             const double kk = k, rr = r;
             flops += 2.0 * (kk * kk * rr + 2 * kk * rr * rr + kk * kk * rr) + 2.0 / 3.0 * rr * rr * rr +
                      2.0 * kk * rr * rr + 2.0 * kk * kk * rr;
         }
-        sf->nbox = (int)ed.size();
+        sf->nbox = (int)sf->hbox.size();
         h->stats.kinds[tau] = kind;
         h->stats.boxes[tau] = nb;
         h->stats.skeletons[tau] = ksum;
@@ -504,7 +643,11 @@ static void run_factor(hif_handle h) {
             ea.perm_pool = sf->perm.as<int>();
             ea.sci_pool = pool->p;
             ea.status = h->status.as<int>();
-            HIF_CUDA((launch_elim<T>(ea, sf->nbox, st)));
+            HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), st)));
+            for (const ElimDesc& eb : ed_big)
+                HIF_CUDA((big_elim_box<T>(g, ea.sci, eb, d_eg.as<ElimGroup>(), sf->sk.as<int>(), sf->rd.as<int>(), Tws.p,
+                                          ews.p, sf->pool.p, piv_scratch.as<int>(), sf->perm.as<int>(), pool->p,
+                                          h->status.as<int>(), st)));
             h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
         }
         h->sci_pools.push_back(std::move(pool));
@@ -531,6 +674,12 @@ static void run_factor(hif_handle h) {
         upload(h->blk_k, h->blk_k_h, st);
         HIF_CUDA(cudaStreamSynchronize(st));
         check_status(h);
+        if (trace) {
+            const auto tr3 = std::chrono::steady_clock::now();
+            auto ms = [](auto a0, auto b0) { return std::chrono::duration<double, std::milli>(b0 - a0).count(); };
+            std::fprintf(stderr, "[hif] sub %2zu kind %d level %d boxes %d big %zu maxn %d | plan+launch %.1f ms, id %.1f ms, elim+host %.1f ms\n",
+                         tau, kind, ell, nb, big_boxes.size(), maxbox, ms(tr0, tr1), ms(tr1, tr2), ms(tr2, tr3));
+        }
         h->subs.push_back(std::move(sf));
     }
     h->stats.sublevels = (int)kinds.size();
@@ -893,6 +1042,8 @@ const char* hif_status_string(hif_status s) {
 }
 
 const char* hif_last_error(void) { return g_last_error; }
+
+uint64_t hif_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 hif_status hif_options_default(int dim, hif_options* opt) {
     if (!opt || (dim != 2 && dim != 3)) return HIF_EINVAL;

@@ -61,6 +61,40 @@ __device__ inline T entry(const GeomDev& g, const SciDev& s, int i, int j, doubl
     return v + sci_value<T>(s, i, j);
 }
 
+// Entries of one row pair of Y_c (Eq. (3.3)) in column j: row 2p holds the
+// outgoing entry, row 2p+1 the incoming one (Lemma 3.3 with quadrature
+// weights).  Coordinates are relative to the box centre.  rid >= 0: near-field
+// DOF i (kernel part k1 = b_i G w_j c_j, k2 = b_j G w_i c_i, SCI parts s1 =
+// S_ij, s2 = S_ji); rid == -1: proxy point (k1 = G w_j c_j, k2 = b_j G w_j).
+template <typename T>
+__device__ inline void y_pair(int kid, int rid, T rx0, T rx1, T rx2, T rb, T rwc, int j, T cx0, T cx1, T cx2,
+                              T cwc, T cb, T cbw, bool scival, const SciDev& sci, T& k1, T& k2, T& s1, T& s2) {
+    k1 = k2 = s1 = s2 = T(0);
+    if (rid == -2) return;
+    const T d0 = rx0 - cx0, d1 = rx1 - cx1, d2 = rx2 - cx2;
+    const T gk = Green<T>::eval(kid, d0 * d0 + d1 * d1 + d2 * d2);
+    if (rid >= 0) {
+        k1 = rb * gk * cwc;
+        k2 = cb * gk * rwc;
+        if (scival) {
+            for (int s = 0; s < sci.nsub; ++s) {
+                const int bi = sci.blk[(int64_t)s * sci.N + rid];
+                if (bi >= 0 && bi == sci.blk[(int64_t)s * sci.N + j]) {
+                    const int kb = sci.kb[bi];
+                    const T* P = static_cast<const T*>(sci.ptr[bi]);
+                    const int li = sci.loc[(int64_t)s * sci.N + rid];
+                    const int lj = sci.loc[(int64_t)s * sci.N + j];
+                    s1 += P[li + (int64_t)kb * lj];
+                    s2 += P[lj + (int64_t)kb * li];
+                }
+            }
+        }
+    } else {
+        k1 = gk * cwc;
+        k2 = cbw * gk;
+    }
+}
+
 __device__ inline double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

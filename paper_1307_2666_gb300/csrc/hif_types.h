@@ -89,4 +89,7 @@ struct BoxFac {
 // Status word written by kernels that detect trouble (checked by the host).
 enum DevStatus : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADSIZE = 4 };
 
+// Counts kernel launches made by the library (diagnostic, see hif_kernel_launches).
+void note_launch();
+
 }  // namespace hif

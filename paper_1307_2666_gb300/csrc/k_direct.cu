@@ -36,6 +36,7 @@ __global__ void kself_kernel(GeomDev g, double* kself) {
 
 cudaError_t launch_kself(const GeomDev& g, double* kself, cudaStream_t st) {
     if (g.N == 0) return cudaSuccess;
+    note_launch();
     kself_kernel<<<(int)std::min<int64_t>((g.N + 255) / 256, 4096), 256, 0, st>>>(g, kself);
     return cudaGetLastError();
 }
@@ -65,6 +66,7 @@ cudaError_t launch_kernel_block(const GeomDev& g, const int* rows, int64_t nr, c
                                 double* out, int64_t ldo, cudaStream_t st) {
     const int64_t tot = nr * nc;
     if (tot == 0) return cudaSuccess;
+    note_launch();
     kernel_block_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 16), 256, 0, st>>>(g, rows, nr, cols, nc, out, ldo);
     return cudaGetLastError();
 }
@@ -119,6 +121,7 @@ cudaError_t launch_direct_general(const DirectArgs& a, cudaStream_t st) {
     if (a.g.N == 0) return cudaSuccess;
     const int blocks = (int)((a.g.N + DS_T - 1) / DS_T);
     for (int r0 = 0; r0 < a.nrhs; r0 += DS_R) {
+        note_launch();
         direct_general_kernel<<<blocks, DS_T, 0, st>>>(a, r0, std::min(DS_R, a.nrhs - r0));
     }
     return cudaGetLastError();
@@ -143,6 +146,7 @@ __global__ void grid_table_kernel(double* table, int n, int dim, double h, int k
 cudaError_t launch_grid_table(double* table, int n, int dim, double h, int kernel_id, double kself_over_w,
                               cudaStream_t st) {
     const int64_t tot = dim == 2 ? (int64_t)n * n : (int64_t)n * n * n;
+    note_launch();
     grid_table_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, st>>>(table, n, dim, h, kernel_id,
                                                                                  kself_over_w);
     return cudaGetLastError();
@@ -230,15 +234,18 @@ cudaError_t launch_direct_grid(const GridDirectArgs& a, cudaStream_t st) {
     const int64_t N = a.dim == 2 ? (int64_t)a.n * a.n : (int64_t)a.n * a.n * a.n;
     if (N == 0) return cudaSuccess;
     const int eb = (int)std::min<int64_t>((N * a.nrhs + 255) / 256, 152 * 16);
+    note_launch();
     grid_scatter_kernel<<<eb, 256, 0, st>>>(a, N);
     int tiles;
     if (a.dim == 2) tiles = ((a.n + 15) / 16) * ((a.n + 15) / 16);
     else tiles = ((a.n + 7) / 8) * ((a.n + 7) / 8) * ((a.n + 3) / 4);
     for (int r0 = 0; r0 < a.nrhs; r0 += DS_R) {
         const int nr = std::min(DS_R, a.nrhs - r0);
+        note_launch();
         if (a.dim == 2) grid_conv_kernel<2><<<tiles, 256, 0, st>>>(a, r0, nr);
         else grid_conv_kernel<3><<<tiles, 256, 0, st>>>(a, r0, nr);
     }
+    note_launch();
     grid_finish_kernel<<<eb, 256, 0, st>>>(a, N);
     return cudaGetLastError();
 }
@@ -256,6 +263,7 @@ __global__ void axpby_kernel(int64_t N, int nrhs, double alpha, const double* x,
 cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int64_t ldx, double beta, double* y,
                          int64_t ldy, cudaStream_t st) {
     if (N * nrhs == 0) return cudaSuccess;
+    note_launch();
     axpby_kernel<<<(int)std::min<int64_t>((N * nrhs + 255) / 256, 152 * 16), 256, 0, st>>>(N, nrhs, alpha, x, ldx, beta, y, ldy);
     return cudaGetLastError();
 }
@@ -278,6 +286,7 @@ __global__ void col_dots_kernel(int64_t N, const double* x, int64_t ldx, const d
 cudaError_t launch_col_dots(int64_t N, int nrhs, const double* x, int64_t ldx, const double* y, int64_t ldy,
                             double* out, cudaStream_t st) {
     if (nrhs == 0) return cudaSuccess;
+    note_launch();
     col_dots_kernel<<<nrhs, 256, 0, st>>>(N, x, ldx, y, ldy, out);
     return cudaGetLastError();
 }

@@ -41,7 +41,7 @@ __device__ inline T* align_ptr(unsigned char*& p, size_t count) {
 
 template <typename T>
 __global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
-    const BoxDesc bx = args.boxes[blockIdx.x];
+    const BoxDesc bx = args.boxes[args.box_list[blockIdx.x]];
     const int n = bx.n;
     const int bp = args.bpairs;          // row pairs per chunk
     const int rows = 2 * bp;
@@ -130,32 +130,9 @@ __global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
             const T xj0 = cxl[3 * l], xj1 = cxl[3 * l + 1], xj2 = cxl[3 * l + 2];
             const int j = cid[l];
             for (int q = 0; q < bp; ++q) {
-                T k1 = T(0), k2 = T(0), s1 = T(0), s2 = T(0);
-                const int i = rid[q];
-                if (i != -2) {
-                    const T d0 = rxl[3 * q] - xj0, d1 = rxl[3 * q + 1] - xj1, d2 = rxl[3 * q + 2] - xj2;
-                    const T gk = Green<T>::eval(kid, d0 * d0 + d1 * d1 + d2 * d2);
-                    if (i >= 0) {
-                        k1 = rb[q] * gk * cwc[l];    // A_{ij} kernel part
-                        k2 = cb[l] * gk * rwc[q];    // A_{ji} kernel part
-                        if (scival) {
-                            for (int s = 0; s < nsub; ++s) {
-                                const int bi = args.sci.blk[(int64_t)s * args.sci.N + i];
-                                if (bi >= 0 && bi == args.sci.blk[(int64_t)s * args.sci.N + j]) {
-                                    const int kb = args.sci.kb[bi];
-                                    const T* P = static_cast<const T*>(args.sci.ptr[bi]);
-                                    const int li = args.sci.loc[(int64_t)s * args.sci.N + i];
-                                    const int lj = args.sci.loc[(int64_t)s * args.sci.N + j];
-                                    s1 += P[li + (int64_t)kb * lj];
-                                    s2 += P[lj + (int64_t)kb * li];
-                                }
-                            }
-                        }
-                    } else {
-                        k1 = gk * cwc[l];            // proxy-out: G w_j c_j
-                        k2 = cbw[l] * gk;            // proxy-in:  b_j G w_j
-                    }
-                }
+                T k1, k2, s1, s2;
+                y_pair<T>(kid, rid[q], rxl[3 * q], rxl[3 * q + 1], rxl[3 * q + 2], rb[q], rwc[q], j, xj0, xj1, xj2,
+                          cwc[l], cb[l], cbw[l], scival, args.sci, k1, k2, s1, s2);
                 if (sci) {
                     CK[2 * q + ldc * l] = k1;
                     CK[2 * q + 1 + ldc * l] = k2;
@@ -376,7 +353,8 @@ __device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm
 
 template <typename T>
 __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
-    const GroupDesc gd = args.groups[blockIdx.x];
+    const int gidx = args.group_list[blockIdx.x];
+    const GroupDesc gd = args.groups[gidx];
     const BoxDesc bx = args.boxes[gd.box];
     const int n = bx.n;
     const int ng = gd.n;
@@ -395,7 +373,7 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
     T* hh = align_ptr<T>(sp, 4);
     T* W;
     if (args.W_in_smem) W = align_ptr<T>(sp, (size_t)ldw * ng);
-    else W = static_cast<T*>(args.Wws) + args.W_off[blockIdx.x];
+    else W = static_cast<T*>(args.Wws) + args.W_off[gidx];
 
     for (int e = threadIdx.x; e < mrow * ng; e += blockDim.x) {
         const int i = e % mrow, l = e / mrow;
@@ -454,7 +432,7 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
     if (tol < args.tol_floor) tol = args.tol_floor;
 
     cpqr_id<T>(W, ldw, mrow, ng, tol, nrm, perm, rank_of, redv, redi, hh,
-               static_cast<T*>(args.Tws) + gd.T_off, args.perm_out + gd.perm_off, args.k_out + blockIdx.x);
+               static_cast<T*>(args.Tws) + gd.T_off, args.perm_out + gd.perm_off, args.k_out + gidx);
 }
 
 // ------------------------------------------------------ elimination ------
@@ -618,6 +596,7 @@ cudaError_t launch_id_batched(int count, const double* mats, const int64_t* off,
     const size_t smem = (size_t)maxn * 16 + 128 * 12 + 256;
     if (e == cudaSuccess) e = cudaFuncSetAttribute(id_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
+        note_launch();
         id_batched_kernel<<<count, 128, smem, st>>>(mats, off, m, n, tol, k, perm, poff, T, toff, ws, dwso);
         e = cudaGetLastError();
     }
@@ -652,6 +631,7 @@ cudaError_t launch_fold(const FoldArgs& a, int nbox, size_t smem, cudaStream_t s
     if (nbox == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(fold_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     fold_kernel<T><<<nbox, 128, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -661,6 +641,7 @@ cudaError_t launch_id(const IdArgs& a, int ngroups, size_t smem, cudaStream_t st
     if (ngroups == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     id_kernel<T><<<ngroups, 128, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -668,6 +649,7 @@ cudaError_t launch_id(const IdArgs& a, int ngroups, size_t smem, cudaStream_t st
 template <typename T>
 cudaError_t launch_elim(const ElimArgs& a, int nbox, cudaStream_t st) {
     if (nbox == 0) return cudaSuccess;
+    note_launch();
     elim_kernel<T><<<nbox, 128, 0, st>>>(a);
     return cudaGetLastError();
 }

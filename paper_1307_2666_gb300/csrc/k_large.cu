@@ -1,0 +1,653 @@
+// Skeletonization of large boxes (sm_103a): boxes whose column count is too
+// large for one CTA are spread over the whole GPU.
+//
+//  * big_ygen        materializes the proxy matrices Y_c of Eq. (3.3) of all
+//                    large boxes of a sublevel in HBM (kernel and SCI parts
+//                    apart when rho_g is needed, Sec. 4.4);
+//  * big_pow_*       rho_g = min(1, |Y^K_g| / |Y^S_g|) by 8 power iterations
+//                    from the all-ones vector, directly on Y_g;
+//  * big_step /      column-pivoted Householder QR (Lemma 2.2), one pair of
+//    big_update      launches per pivot step for all large groups at once: one
+//                    CTA per group picks the pivot and forms the reflector, a
+//                    warp per remaining column applies it and recomputes the
+//                    column norm in FP64;
+//  * big_T           T = R1^{-1} R2 and the skeleton / redundant order;
+//  * gemm / trsm / elimination helpers: Lemma 2.3 blocks, Lemma 2.1 LU
+//                    (blocked, multi-CTA) and the Schur update for one large
+//                    box at a time.
+#include <algorithm>
+
+#include "hif_common.cuh"
+#include "launch.h"
+
+namespace hif {
+
+// --------------------------------------------------------------- Y gen ----
+
+template <typename T>
+__global__ void big_ygen_kernel(BigArgs a) {
+    const BigBox bb = a.bigboxes[blockIdx.y];
+    const BoxDesc bx = a.boxes[bb.box];
+    const int n = bx.n, npairs = bx.m_near + a.P;
+    const int dim = a.g.dim;
+    const bool scival = bx.has_sci && a.sci.nsub > 0;
+    const bool split = scival && a.second_kind;
+    T* YK = static_cast<T*>(a.YK) + bb.y_off;
+    T* YS = split ? static_cast<T*>(a.YS) + bb.y_off : nullptr;
+    const int64_t m = bb.m;
+    const int* cols = a.cols + bx.col_off;
+    const int* near = a.near + bx.near_off;
+    const double c0 = bx.ctr[0], c1 = bx.ctr[1], c2 = dim == 3 ? bx.ctr[2] : 0.0;
+    const int64_t tot = (int64_t)npairs * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(e % npairs), l = (int)(e / npairs);
+        const int j = cols[l];
+        const T cx0 = (T)(a.g.x[(int64_t)dim * j] - c0), cx1 = (T)(a.g.x[(int64_t)dim * j + 1] - c1);
+        const T cx2 = dim == 3 ? (T)(a.g.x[(int64_t)dim * j + 2] - c2) : T(0);
+        int rid;
+        T rx0, rx1, rx2, rb, rwc;
+        if (p < bx.m_near) {
+            rid = near[p];
+            rx0 = (T)(a.g.x[(int64_t)dim * rid] - c0);
+            rx1 = (T)(a.g.x[(int64_t)dim * rid + 1] - c1);
+            rx2 = dim == 3 ? (T)(a.g.x[(int64_t)dim * rid + 2] - c2) : T(0);
+            rb = (T)a.g.b[rid];
+            rwc = (T)(a.g.w[rid] * a.g.c[rid]);
+        } else {
+            const int kx = p - bx.m_near;
+            rid = -1;
+            rx0 = (T)(bx.radius * a.proxy[dim * kx]);
+            rx1 = (T)(bx.radius * a.proxy[dim * kx + 1]);
+            rx2 = dim == 3 ? (T)(bx.radius * a.proxy[dim * kx + 2]) : T(0);
+            rb = T(1);
+            rwc = T(1);
+        }
+        T k1, k2, s1, s2;
+        y_pair<T>(a.g.kernel_id, rid, rx0, rx1, rx2, rb, rwc, j, cx0, cx1, cx2, (T)(a.g.w[j] * a.g.c[j]),
+                  (T)a.g.b[j], (T)(a.g.b[j] * a.g.w[j]), scival, a.sci, k1, k2, s1, s2);
+        T* col = YK + m * l;
+        if (split) {
+            col[2 * p] = k1;
+            col[2 * p + 1] = k2;
+            YS[m * l + 2 * p] = s1;
+            YS[m * l + 2 * p + 1] = s2;
+        } else {
+            col[2 * p] = k1 + s1;
+            col[2 * p + 1] = k2 + s2;
+        }
+    }
+}
+
+// ------------------------------------------------------- rho_g (Sec 4.4) --
+
+// t = Y_g v   (which: 0 = Y^K, 1 = Y^S), one thread per row
+template <typename T>
+__global__ void big_pow_tv_kernel(BigArgs a) {
+    const BigGroup G = a.groups[blockIdx.y];
+    if (!G.need_rho) return;
+    const int which = blockIdx.z;
+    const T* Y = static_cast<const T*>(which == 0 ? a.YK : a.YS) + G.y_off;
+    const double* v = a.vec_v + 2 * G.vec_off + which * (int64_t)G.n;
+    double* t = a.vec_t + 2 * G.row_off + which * (int64_t)G.m;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.m; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int l = 0; l < G.n; ++l) acc += (double)Y[i + (int64_t)G.m * l] * v[l];
+        t[i] = acc;
+    }
+}
+
+// w = Y_g^T t, one warp per column
+template <typename T>
+__global__ void big_pow_w_kernel(BigArgs a) {
+    const BigGroup G = a.groups[blockIdx.y];
+    if (!G.need_rho) return;
+    const int which = blockIdx.z;
+    const T* Y = static_cast<const T*>(which == 0 ? a.YK : a.YS) + G.y_off;
+    const double* t = a.vec_t + 2 * G.row_off + which * (int64_t)G.m;
+    double* w = a.vec_w + 2 * G.vec_off + which * (int64_t)G.n;
+    const int lane = threadIdx.x & 31;
+    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (l >= G.n) return;
+    double acc = 0.0;
+    for (int i = lane; i < G.m; i += 32) acc += (double)Y[i + (int64_t)G.m * l] * t[i];
+    acc = warp_sum(acc);
+    if (lane == 0) w[l] = acc;
+}
+
+// mode 0: v = w / |w| (v = 0 when w = 0); mode 1: est = |t|; mode 2: v = 1/sqrt(n)
+__global__ void big_pow_norm_kernel(BigArgs a, int mode) {
+    const BigGroup G = a.groups[blockIdx.x];
+    if (!G.need_rho) return;
+    const int which = blockIdx.y;
+    double* v = a.vec_v + 2 * G.vec_off + which * (int64_t)G.n;
+    const double* w = a.vec_w + 2 * G.vec_off + which * (int64_t)G.n;
+    const double* t = a.vec_t + 2 * G.row_off + which * (int64_t)G.m;
+    __shared__ double red[256];
+    if (mode == 2) {
+        for (int l = threadIdx.x; l < G.n; l += blockDim.x) v[l] = 1.0 / sqrt((double)G.n);
+        return;
+    }
+    const double* src = mode == 0 ? w : t;
+    const int len = mode == 0 ? G.n : G.m;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) s += src[i] * src[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    const double tot = red[0];
+    if (mode == 1) {
+        if (threadIdx.x == 0) a.est[2 * blockIdx.x + which] = sqrt(tot);
+        return;
+    }
+    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+    for (int l = threadIdx.x; l < G.n; l += blockDim.x) v[l] = w[l] * inv;
+}
+
+// tolerance per group and Y = Y^K + Y^S
+__global__ void big_tol_kernel(BigArgs a, int ngroups) {
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ngroups) return;
+    BigGroup& G = a.groups[gi];
+    double rho = 1.0;
+    if (G.need_rho) {
+        const double eK = a.est[2 * gi], eS = a.est[2 * gi + 1];
+        if (eS > 0.0) rho = fmin(1.0, eK / eS);
+    }
+    double tol = rho * a.eps;
+    if (tol < a.tol_floor) tol = a.tol_floor;
+    G.tol = tol;
+}
+
+template <typename T>
+__global__ void big_add_kernel(T* YK, const T* YS, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        YK[e] += YS[e];
+}
+
+// --------------------------------------------------- pivoted QR steps ----
+
+template <typename T>
+__global__ void big_norm_init_kernel(BigArgs a) {
+    const BigGroup G = a.groups[blockIdx.y];
+    const T* Y = static_cast<const T*>(a.YK) + G.y_off;
+    const int lane = threadIdx.x & 31;
+    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        BigState& S = a.state[blockIdx.y];
+        S.k = 0;
+        S.stop = 0;
+        S.nu0 = 0.0;
+        S.tau = 0.0;
+    }
+    if (l >= G.n) return;
+    double s = 0.0;
+    for (int i = lane; i < G.m; i += 32) {
+        const double v = (double)Y[i + (int64_t)G.m * l];
+        s += v * v;
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+        a.nrm[G.vec_off + l] = s;
+        a.perm[G.vec_off + l] = l;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) big_step_kernel(BigArgs a, int j) {
+    const BigGroup G = a.groups[blockIdx.x];
+    BigState* S = a.state + blockIdx.x;
+    if (S->stop) return;
+    T* W = static_cast<T*>(a.YK) + G.y_off;
+    const int64_t ld = G.m;
+    double* nrm = a.nrm + G.vec_off;
+    int* perm = a.perm + G.vec_off;
+    __shared__ double redv[256];
+    __shared__ int redi[256];
+    __shared__ T hs[256];
+    const int kmax = min(G.m, G.n);
+    if (j >= kmax) {
+        if (threadIdx.x == 0) S->stop = 1;
+        return;
+    }
+    double best = -1.0;
+    int bl = -1, bo = 1 << 30;
+    for (int l = j + threadIdx.x; l < G.n; l += blockDim.x) {
+        const double v = nrm[l];
+        if (v > best || (v == best && perm[l] < bo)) { best = v; bo = perm[l]; bl = l; }
+    }
+    redv[threadIdx.x] = best;
+    redi[threadIdx.x] = bl;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double v2 = redv[threadIdx.x + s], v1 = redv[threadIdx.x];
+            const int l2 = redi[threadIdx.x + s], l1 = redi[threadIdx.x];
+            if (l2 >= 0 && (l1 < 0 || v2 > v1 || (v2 == v1 && perm[l2] < perm[l1]))) {
+                redv[threadIdx.x] = v2;
+                redi[threadIdx.x] = l2;
+            }
+        }
+        __syncthreads();
+    }
+    const double bnorm = sqrt(fmax(redv[0], 0.0));
+    const int p = redi[0];
+    const double nu0 = j == 0 ? bnorm : S->nu0;
+    __syncthreads();
+    if (bnorm <= G.tol * nu0 || bnorm == 0.0 || p < j) {
+        if (threadIdx.x == 0) {
+            S->stop = 1;
+            if (j == 0) S->nu0 = bnorm;
+        }
+        return;
+    }
+    if (p != j) {
+        for (int i = threadIdx.x; i < G.m; i += blockDim.x) {
+            const T t = W[i + ld * j];
+            W[i + ld * j] = W[i + ld * p];
+            W[i + ld * p] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && p != j) {
+        const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+        const double tn = nrm[j]; nrm[j] = nrm[p]; nrm[p] = tn;
+    }
+    // reflector for W[j:, j]
+    T s = T(0);
+    for (int i = j + 1 + threadIdx.x; i < G.m; i += blockDim.x) {
+        const T v = W[i + ld * j];
+        s += v * v;
+    }
+    hs[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) hs[threadIdx.x] += hs[threadIdx.x + k];
+        __syncthreads();
+    }
+    const T ss = hs[0];
+    const T alpha = W[j + ld * j];
+    T tau = T(0), scal = T(0);
+    if (ss != T(0)) {
+        const T beta = -copysign(sqrt(alpha * alpha + ss), alpha);
+        tau = (beta - alpha) / beta;
+        scal = T(1) / (alpha - beta);
+    }
+    __syncthreads();
+    if (tau != T(0)) {
+        for (int i = j + 1 + threadIdx.x; i < G.m; i += blockDim.x) W[i + ld * j] *= scal;
+        if (threadIdx.x == 0) W[j + ld * j] = -copysign(sqrt(alpha * alpha + ss), alpha);
+    }
+    if (threadIdx.x == 0) {
+        if (j == 0) S->nu0 = bnorm;
+        S->tau = (double)tau;
+        S->k = j + 1;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) big_update_kernel(BigArgs a, int j) {
+    const BigGroup G = a.groups[blockIdx.y];
+    const BigState S = a.state[blockIdx.y];
+    if (S.k != j + 1 || S.stop) return;
+    const int lane = threadIdx.x & 31;
+    const int l = j + 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (l >= G.n) return;
+    T* W = static_cast<T*>(a.YK) + G.y_off;
+    const int64_t ld = G.m;
+    T* col = W + ld * l;
+    const T* v = W + ld * j;
+    const T tau = (T)S.tau;
+    if (tau != T(0)) {
+        T w = T(0);
+        for (int i = j + 1 + lane; i < G.m; i += 32) w += v[i] * col[i];
+        w = warp_sum(w);
+        w = (w + col[j]) * tau;
+        __syncwarp();
+        if (lane == 0) col[j] -= w;
+        for (int i = j + 1 + lane; i < G.m; i += 32) col[i] -= w * v[i];
+    }
+    double s = 0.0;
+    for (int i = j + 1 + lane; i < G.m; i += 32) {
+        const double c = (double)col[i];
+        s += c * c;
+    }
+    s = warp_sum(s);
+    if (lane == 0) a.nrm[G.vec_off + l] = s;
+}
+
+// T = R1^{-1} R2 (redundant columns in ascending original order), outputs
+template <typename T>
+__global__ void big_T_kernel(BigArgs a) {
+    const BigGroup G = a.groups[blockIdx.y];
+    const GroupDesc gd = a.gdesc[G.group];
+    const int k = a.state[blockIdx.y].k;
+    const int n = G.n, r = n - k;
+    const T* W = static_cast<const T*>(a.YK) + G.y_off;
+    const int64_t ld = G.m;
+    const int* perm = a.perm + G.vec_off;
+    T* Tout = static_cast<T*>(a.Tws) + gd.T_off;
+    int* pout = a.perm_out + gd.perm_off;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.k_out[G.group] = k;
+    if (l < k) pout[l] = perm[l];
+    if (l >= r) return;
+    const int o = perm[k + l];
+    int pos = 0;
+    for (int q = 0; q < r; ++q) pos += perm[k + q] < o;
+    pout[k + pos] = o;
+    // back substitution in a local copy held in the T output column
+    T* tcol = Tout + (int64_t)k * pos;
+    const T* rcol = W + ld * (k + l);
+    for (int i = k - 1; i >= 0; --i) {
+        T v = rcol[i];
+        for (int q = i + 1; q < k; ++q) v -= W[i + ld * q] * tcol[q];
+        tcol[i] = v / W[i + ld * i];
+    }
+}
+
+// ---------------------------------------------------------- launchers ----
+
+template <typename T>
+cudaError_t big_ygen(const BigArgs& a, int nbig, int64_t max_entries, cudaStream_t st) {
+    if (nbig == 0) return cudaSuccess;
+    dim3 grid((unsigned)std::min<int64_t>((max_entries + 255) / 256, 4096), nbig);
+    note_launch();
+    big_ygen_kernel<T><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t big_rho(const BigArgs& a, int ngroups, int max_m, int max_n, cudaStream_t st) {
+    if (ngroups == 0) return cudaSuccess;
+    dim3 gn(ngroups, 2);
+    dim3 gtv((max_m + 255) / 256, ngroups, 2);
+    dim3 gw((max_n + 7) / 8, ngroups, 2);
+    note_launch();
+    big_pow_norm_kernel<<<gn, 256, 0, st>>>(a, 2);
+    for (int it = 0; it < 8; ++it) {
+        note_launch();
+        big_pow_tv_kernel<T><<<gtv, 256, 0, st>>>(a);
+        note_launch();
+        big_pow_w_kernel<T><<<gw, 256, 0, st>>>(a);
+        note_launch();
+        big_pow_norm_kernel<<<gn, 256, 0, st>>>(a, 0);
+    }
+    note_launch();
+    big_pow_tv_kernel<T><<<gtv, 256, 0, st>>>(a);
+    note_launch();
+    big_pow_norm_kernel<<<gn, 256, 0, st>>>(a, 1);
+    note_launch();
+    big_tol_kernel<<<(ngroups + 127) / 128, 128, 0, st>>>(a, ngroups);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t big_add(void* YK, const void* YS, int64_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    note_launch();
+    big_add_kernel<T><<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(
+        static_cast<T*>(YK), static_cast<const T*>(YS), n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t big_qr_init(const BigArgs& a, int ngroups, int max_n, cudaStream_t st) {
+    if (ngroups == 0) return cudaSuccess;
+    dim3 g((max_n + 7) / 8, ngroups);
+    note_launch();
+    big_norm_init_kernel<T><<<g, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t big_qr_step(const BigArgs& a, int ngroups, int max_n, int j, cudaStream_t st) {
+    note_launch();
+    big_step_kernel<T><<<ngroups, 256, 0, st>>>(a, j);
+    const int cols = max_n - j - 1;
+    if (cols > 0) {
+        dim3 g((cols + 7) / 8, ngroups);
+        note_launch();
+        big_update_kernel<T><<<g, 256, 0, st>>>(a, j);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t big_finish(const BigArgs& a, int ngroups, int max_n, cudaStream_t st) {
+    if (ngroups == 0) return cudaSuccess;
+    dim3 g((max_n + 127) / 128, ngroups);
+    note_launch();
+    big_T_kernel<T><<<g, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------- dense helpers ------
+
+// C (m x n) += alpha op(A) op(B); 64 x 64 tiles, K staged 16 at a time.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_kernel(int m, int n, int kk, T alpha, const T* A, int64_t lda, int tA,
+                                                   const T* B, int64_t ldb, int tB, T* C, int64_t ldc) {
+    __shared__ T As[16][64 + 1];
+    __shared__ T Bs[16][64 + 1];
+    const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4] = {};
+    for (int l0 = 0; l0 < kk; l0 += 16) {
+        for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+            const int r = e % 64, l = e / 64;           // A tile: rows i0+r, k l0+l
+            const int i = i0 + r, kx = l0 + l;
+            T v = T(0);
+            if (i < m && kx < kk) v = tA ? A[kx + lda * i] : A[i + lda * kx];
+            As[l][r] = v;
+            const int jj = j0 + r;                      // B tile: k l0+l, cols j0+r
+            T u = T(0);
+            if (jj < n && kx < kk) u = tB ? B[jj + ldb * kx] : B[kx + ldb * jj];
+            Bs[l][r] = u;
+        }
+        __syncthreads();
+        for (int l = 0; l < 16; ++l) {
+            T av[4], bv[4];
+            for (int q = 0; q < 4; ++q) av[q] = As[l][tx + 16 * q];
+            for (int q = 0; q < 4; ++q) bv[q] = Bs[l][ty + 16 * q];
+            for (int p = 0; p < 4; ++p)
+                for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+        }
+        __syncthreads();
+    }
+    for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + tx + 16 * p, jj = j0 + ty + 16 * q;
+            if (i < m && jj < n) C[i + ldc * jj] += alpha * acc[p][q];
+        }
+}
+
+template <typename T>
+cudaError_t gemm(int m, int n, int kk, T alpha, const T* A, int64_t lda, bool tA, const T* B, int64_t ldb, bool tB,
+                 T* C, int64_t ldc, cudaStream_t st) {
+    if (m == 0 || n == 0 || kk == 0) return cudaSuccess;
+    dim3 g((m + 63) / 64, (n + 63) / 64);
+    note_launch();
+    gemm_kernel<T><<<g, 256, 0, st>>>(m, n, kk, alpha, A, lda, tA ? 1 : 0, B, ldb, tB ? 1 : 0, C, ldc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void big_gather_kernel(GeomDev g, SciDev sci, const int* rd, int r, const int* sk, int k, T* A) {
+    const int n = k + r;
+    const int ref = r > 0 ? rd[0] : sk[0];
+    const int d = g.dim;
+    const double r0 = g.x[(int64_t)d * ref], r1 = g.x[(int64_t)d * ref + 1];
+    const double r2 = d == 3 ? g.x[(int64_t)d * ref + 2] : 0.0;
+    const int64_t tot = (int64_t)n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(e % n), q = (int)(e / n);
+        const int i = p < r ? rd[p] : sk[p - r];
+        const int j = q < r ? rd[q] : sk[q - r];
+        A[e] = entry<T>(g, sci, i, j, r0, r1, r2);
+    }
+}
+
+template <typename T>
+__global__ void big_T_assemble_kernel(const ElimGroup* eg, int ng, const T* Tws, int k, int r, T* Tm) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * r; e += gridDim.x * blockDim.x) Tm[e] = T(0);
+    __syncthreads();   // single-CTA launch
+    for (int gi = 0; gi < ng; ++gi) {
+        const ElimGroup G = eg[gi];
+        for (int e = threadIdx.x; e < G.kg * G.rg; e += blockDim.x) {
+            const int i = e % G.kg, jj = e / G.kg;
+            Tm[(G.ko + i) + (int64_t)k * (G.ro + jj)] = Tws[G.T_off + e];
+        }
+    }
+}
+
+// X (m x n) <- X U^{-1}, U upper with diagonal; one thread per row of X
+template <typename T>
+__global__ void trsm_right_upper_rows(int n, const T* U, int64_t ldu, T* X, int64_t ldx, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    for (int j = 0; j < n; ++j) {
+        T v = X[i + ldx * j];
+        for (int l = 0; l < j; ++l) v -= X[i + ldx * l] * U[l + ldu * j];
+        X[i + ldx * j] = v / U[j + ldu * j];
+    }
+}
+
+// B (n x m) <- L^{-1} P B with LAPACK interchanges piv; one thread per column
+template <typename T>
+__global__ void piv_lower_cols(int n, const T* L, int64_t ldl, const int* piv, T* B, int64_t ldb, int m) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    T* col = B + ldb * c;
+    for (int j = 0; j < n; ++j) {
+        const int p = piv[j];
+        if (p != j) { const T t = col[j]; col[j] = col[p]; col[p] = t; }
+    }
+    for (int i = 0; i < n; ++i) {
+        T v = col[i];
+        for (int l = 0; l < i; ++l) v -= L[i + ldl * l] * col[l];
+        col[i] = v;
+    }
+}
+
+// outputs of one eliminated large box (same layout as the one-CTA path)
+template <typename T>
+__global__ void big_elim_out_kernel(int k, int r, const T* A, int64_t ld, const T* Tm, T* pool, ElimDesc ed) {
+    const T* Arr = A;
+    const T* Asr = A + r;
+    const T* Ars = A + ld * r;
+    T* Dv = pool + ed.D_out;
+    T* LUo = pool + ed.LU_out;
+    T* Xo = pool + ed.X_out;
+    T* Yo = pool + ed.Y_out;
+    T* To = pool + ed.T_out;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t e = t0; e < r; e += stride) Dv[e] = Arr[e + ld * e];
+    for (int64_t e = t0; e < (int64_t)r * r; e += stride) {
+        const int i = (int)(e % r), j = (int)(e / r);
+        LUo[e] = i == j ? T(0) : (i < j ? Arr[i + ld * j] / Arr[i + ld * i] : Arr[i + ld * j]);
+    }
+    for (int64_t e = t0; e < (int64_t)k * r; e += stride) {
+        const int i = (int)(e % k), j = (int)(e / k);
+        Xo[e] = Asr[i + ld * j];
+        To[e] = Tm[e];
+    }
+    for (int64_t e = t0; e < (int64_t)r * k; e += stride) {
+        const int i = (int)(e % r), j = (int)(e / r);
+        Yo[e] = Ars[i + ld * j] / Arr[i + ld * i];
+    }
+}
+
+// inverses of the unit triangular factors stored in LU (one thread per column)
+template <typename T>
+__global__ void tri_inv_cols(int n, const T* A, T* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int64_t ld = n;
+    out[c + ld * c] = T(0);
+    for (int i = c + 1; i < n; ++i) {
+        T v = -A[i + ld * c];
+        for (int l = c + 1; l < i; ++l) v -= A[i + ld * l] * out[l + ld * c];
+        out[i + ld * c] = v;
+    }
+    for (int i = c - 1; i >= 0; --i) {
+        T v = -A[i + ld * c];
+        for (int l = i + 1; l < c; ++l) v -= A[i + ld * l] * out[l + ld * c];
+        out[i + ld * c] = v;
+    }
+}
+
+__global__ void piv_to_perm_kernel(const int* piv, int r, int* pm) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int i = 0; i < r; ++i) pm[i] = i;
+    for (int j = 0; j < r; ++j) {
+        const int p = piv[j];
+        const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
+    }
+}
+
+template <typename T>
+cudaError_t big_elim_box(const GeomDev& g, const SciDev& sci, const ElimDesc& ed, const ElimGroup* d_groups,
+                         const int* d_sk, const int* d_rd, const void* Tws, void* ws, void* fac_pool, int* piv_pool,
+                         int* perm_pool, void* sci_pool, int* status, cudaStream_t st) {
+    const int k = ed.k, r = ed.r, n = k + r;
+    T* A = static_cast<T*>(ws) + ed.ws_off;
+    T* Tm = A + (int64_t)n * n;
+    const int* sk = d_sk + ed.sk_off;
+    const int* rd = d_rd + ed.rd_off;
+    const int64_t ld = n;
+    note_launch();
+    big_gather_kernel<T><<<(unsigned)std::min<int64_t>(((int64_t)n * n + 255) / 256, 152 * 16), 256, 0, st>>>(
+        g, sci, rd, r, sk, k, A);
+    note_launch();
+    big_T_assemble_kernel<T><<<1, 256, 0, st>>>(d_groups + ed.grp_off, ed.ngroups, static_cast<const T*>(Tws), k, r, Tm);
+    T* Arr = A;
+    T* Asr = A + r;
+    T* Ars = A + ld * r;
+    T* Ass = A + ld * r + r;
+    cudaError_t e;
+    if ((e = gemm<T>(k, r, k, T(-1), Ass, ld, false, Tm, k, false, Asr, ld, st)) != cudaSuccess) return e;
+    if ((e = gemm<T>(r, r, k, T(-1), Tm, k, true, Asr, ld, false, Arr, ld, st)) != cudaSuccess) return e;
+    if ((e = gemm<T>(r, r, k, T(-1), Ars, ld, false, Tm, k, false, Arr, ld, st)) != cudaSuccess) return e;
+    if ((e = gemm<T>(r, k, k, T(-1), Tm, k, true, Ass, ld, false, Ars, ld, st)) != cudaSuccess) return e;
+    int* piv = piv_pool + ed.piv_out;
+    if ((e = lu_blocked<T>(Arr, r, ld, piv, status, st)) != cudaSuccess) return e;
+    if (k > 0) {
+        note_launch();
+        trsm_right_upper_rows<T><<<(k + 127) / 128, 128, 0, st>>>(r, Arr, ld, Asr, ld, k);
+        note_launch();
+        piv_lower_cols<T><<<(k + 127) / 128, 128, 0, st>>>(r, Arr, ld, piv, Ars, ld, k);
+        if (ed.sci_out >= 0) {
+            T* S = static_cast<T*>(sci_pool) + ed.sci_out;
+            if ((e = cudaMemsetAsync(S, 0, sizeof(T) * (size_t)k * k, st)) != cudaSuccess) return e;
+            if ((e = gemm<T>(k, k, r, T(-1), Asr, ld, false, Ars, ld, false, S, k, st)) != cudaSuccess) return e;
+        }
+    }
+    T* pool = static_cast<T*>(fac_pool);
+    note_launch();
+    big_elim_out_kernel<T><<<(unsigned)std::min<int64_t>(((int64_t)n * n + 255) / 256, 1024), 256, 0, st>>>(
+        k, r, A, ld, Tm, pool, ed);
+    note_launch();
+    tri_inv_cols<T><<<(r + 127) / 128, 128, 0, st>>>(r, pool + ed.LU_out, pool + ed.LUi_out);
+    note_launch();
+    piv_to_perm_kernel<<<1, 1, 0, st>>>(piv, r, perm_pool + ed.piv_out);
+    return cudaGetLastError();
+}
+
+#define HIF_INST(T)                                                                                            \
+    template cudaError_t big_ygen<T>(const BigArgs&, int, int64_t, cudaStream_t);                              \
+    template cudaError_t big_rho<T>(const BigArgs&, int, int, int, cudaStream_t);                              \
+    template cudaError_t big_add<T>(void*, const void*, int64_t, cudaStream_t);                                \
+    template cudaError_t big_qr_init<T>(const BigArgs&, int, int, cudaStream_t);                               \
+    template cudaError_t big_qr_step<T>(const BigArgs&, int, int, int, cudaStream_t);                          \
+    template cudaError_t big_finish<T>(const BigArgs&, int, int, cudaStream_t);                                \
+    template cudaError_t big_elim_box<T>(const GeomDev&, const SciDev&, const ElimDesc&, const ElimGroup*,      \
+                                         const int*, const int*, const void*, void*, void*, int*, int*, void*, \
+                                         int*, cudaStream_t);
+HIF_INST(double)
+HIF_INST(float)
+
+}  // namespace hif

@@ -169,6 +169,7 @@ template <typename T, int MODE>
 static cudaError_t launch_mode(const SweepArgs& a, int nbox, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     sweep_kernel<T, MODE><<<nbox, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -220,6 +221,7 @@ cudaError_t launch_to_work(const double* src, int64_t lds, T* dst, int64_t ldd, 
     const int64_t tot = N * nrhs;
     if (tot == 0) return cudaSuccess;
     const int blocks = (int)((tot + 255) / 256 < 152 * 16 ? (tot + 255) / 256 : 152 * 16);
+    note_launch();
     to_work_kernel<T><<<blocks, 256, 0, st>>>(src, lds, dst, ldd, N, nrhs);
     return cudaGetLastError();
 }
@@ -229,6 +231,7 @@ cudaError_t launch_from_work(const T* src, int64_t lds, double* dst, int64_t ldd
     const int64_t tot = N * nrhs;
     if (tot == 0) return cudaSuccess;
     const int blocks = (int)((tot + 255) / 256 < 152 * 16 ? (tot + 255) / 256 : 152 * 16);
+    note_launch();
     from_work_kernel<T><<<blocks, 256, 0, st>>>(src, lds, dst, ldd, N, nrhs);
     return cudaGetLastError();
 }

@@ -30,6 +30,7 @@ cudaError_t launch_top_assemble(const TopArgs& a, cudaStream_t st) {
     if (a.n == 0) return cudaSuccess;
     const int64_t tot = (int64_t)a.n * a.n;
     const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 32);
+    note_launch();
     top_assemble_kernel<T><<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -39,10 +40,9 @@ cudaError_t launch_top_assemble(const TopArgs& a, cudaStream_t st) {
 constexpr int NB = 32;
 
 template <typename T>
-__global__ void __launch_bounds__(256) panel_kernel(T* A, int n, int j0, int nb, int* piv, int* status) {
+__global__ void __launch_bounds__(256) panel_kernel(T* A, int n, int64_t ld, int j0, int nb, int* piv, int* status) {
     __shared__ T redv[256];
     __shared__ int redi[256];
-    const int64_t ld = n;
     for (int j = j0 + threadIdx.x; j < j0 + nb; j += blockDim.x) piv[j] = j;
     __syncthreads();
     for (int j = j0; j < j0 + nb; ++j) {
@@ -72,10 +72,9 @@ __global__ void __launch_bounds__(256) panel_kernel(T* A, int n, int j0, int nb,
 }
 
 template <typename T>
-__global__ void swap_trsm_kernel(T* A, int n, int j0, int nb, const int* piv) {
+__global__ void swap_trsm_kernel(T* A, int n, int64_t ld, int j0, int nb, const int* piv) {
     // one thread per column outside the panel: row interchanges, then for
     // columns right of the panel U12 = L11^{-1} A12
-    const int64_t ld = n;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n || (c >= j0 && c < j0 + nb)) return;
     for (int j = j0; j < j0 + nb; ++j) {
@@ -96,11 +95,10 @@ __global__ void swap_trsm_kernel(T* A, int n, int j0, int nb, const int* piv) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) update_kernel(T* A, int n, int j0, int nb) {
+__global__ void __launch_bounds__(256) update_kernel(T* A, int n, int64_t ld, int j0, int nb) {
     // A22 -= L21 U12 on 64 x 64 tiles, K = nb <= 32
     __shared__ T Ls[64][NB + 1];
     __shared__ T Us[NB][64 + 1];
-    const int64_t ld = n;
     const int s = j0 + nb;
     const int i0 = s + blockIdx.x * 64, c0 = s + blockIdx.y * 64;
     for (int e = threadIdx.x; e < 64 * nb; e += blockDim.x) {
@@ -129,18 +127,26 @@ __global__ void __launch_bounds__(256) update_kernel(T* A, int n, int j0, int nb
 }
 
 template <typename T>
-cudaError_t top_lu(T* A, int n, int* piv, int* status, cudaStream_t st) {
+cudaError_t lu_blocked(T* A, int n, int64_t ld, int* piv, int* status, cudaStream_t st) {
     for (int j0 = 0; j0 < n; j0 += NB) {
         const int nb = std::min(NB, n - j0);
-        panel_kernel<T><<<1, 256, 0, st>>>(A, n, j0, nb, piv, status);
-        swap_trsm_kernel<T><<<(n + 127) / 128, 128, 0, st>>>(A, n, j0, nb, piv);
+        note_launch();
+        panel_kernel<T><<<1, 256, 0, st>>>(A, n, ld, j0, nb, piv, status);
+        note_launch();
+        swap_trsm_kernel<T><<<(n + 127) / 128, 128, 0, st>>>(A, n, ld, j0, nb, piv);
         const int rest = n - j0 - nb;
         if (rest > 0) {
             dim3 grid((rest + 63) / 64, (rest + 63) / 64);
-            update_kernel<T><<<grid, 256, 0, st>>>(A, n, j0, nb);
+            note_launch();
+            update_kernel<T><<<grid, 256, 0, st>>>(A, n, ld, j0, nb);
         }
     }
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t top_lu(T* A, int n, int* piv, int* status, cudaStream_t st) {
+    return lu_blocked<T>(A, n, n, piv, status, st);
 }
 
 // ---- inverse from the LU factors: Ainv = U^{-1} L^{-1} P ------------------
@@ -186,6 +192,7 @@ __global__ void __launch_bounds__(256) lu_inverse_kernel(const T* LU, const int*
 template <typename T>
 cudaError_t top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     lu_inverse_kernel<T><<<(n + 7) / 8, 256, 0, st>>>(LU, piv, n, Ainv);
     return cudaGetLastError();
 }
@@ -226,7 +233,9 @@ template <typename T>
 cudaError_t launch_top_gemm(const T* M, int n, bool trans, const int* ids, T* x, int64_t ldx, int nrhs, T* tmp,
                             cudaStream_t st) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     gather_kernel<T><<<std::min(1024, (n * nrhs + 255) / 256), 256, 0, st>>>(x, ldx, ids, n, nrhs, tmp);
+    note_launch();
     top_mv_kernel<T><<<std::min(152 * 8, (n * nrhs * (trans ? 32 : 1) + 255) / 256), 256, 0, st>>>(M, n, trans ? 1 : 0,
                                                                                                ids, x, ldx, nrhs, tmp);
     return cudaGetLastError();
@@ -235,6 +244,8 @@ cudaError_t launch_top_gemm(const T* M, int n, bool trans, const int* ids, T* x,
 template cudaError_t launch_top_assemble<double>(const TopArgs&, cudaStream_t);
 template cudaError_t launch_top_assemble<float>(const TopArgs&, cudaStream_t);
 template cudaError_t top_lu<double>(double*, int, int*, int*, cudaStream_t);
+template cudaError_t lu_blocked<double>(double*, int, int64_t, int*, int*, cudaStream_t);
+template cudaError_t lu_blocked<float>(float*, int, int64_t, int*, int*, cudaStream_t);
 template cudaError_t top_lu<float>(float*, int, int*, int*, cudaStream_t);
 template cudaError_t top_inverse<double>(const double*, const int*, int, double*, cudaStream_t);
 template cudaError_t top_inverse<float>(const float*, const int*, int, float*, cudaStream_t);

@@ -12,6 +12,7 @@ struct FoldArgs {
     GeomDev g;
     SciDev sci;
     const BoxDesc* boxes;
+    const int* box_list;      // boxes handled by this launch (blockIdx.x -> box)
     const int* cols;
     const int* near;
     const GroupDesc* groups;
@@ -27,6 +28,7 @@ struct FoldArgs {
 
 struct IdArgs {
     const GroupDesc* groups;
+    const int* group_list;    // groups handled by this launch (blockIdx.x -> group)
     const BoxDesc* boxes;
     const void* Rws;
     const void* GKws;
@@ -78,6 +80,70 @@ struct SweepArgs {
     int mode;               // see k_sweep.cu
 };
 
+// ---- large boxes (k_large.cu)
+struct BigBox {
+    int box;                // index into the sublevel's BoxDesc array
+    int m;                  // rows of Y_c
+    int64_t y_off;          // Y_c (m x n, column-major) in the large-box workspace
+};
+
+struct BigGroup {
+    int group;              // index into the sublevel's GroupDesc array
+    int n;                  // columns
+    int m;                  // rows (= the box's m)
+    int need_rho;           // second-kind tolerance needed
+    int64_t y_off;          // first column of the group in the workspace
+    int64_t vec_off;        // prefix sum of n over groups
+    int64_t row_off;        // prefix sum of m over groups
+    double tol;             // relative ID tolerance (filled on the device)
+};
+
+struct BigState {
+    int k;
+    int stop;
+    double nu0;
+    double tau;
+};
+
+struct BigArgs {
+    GeomDev g;
+    SciDev sci;
+    const BoxDesc* boxes;
+    const BigBox* bigboxes;
+    const int* cols;
+    const int* near;
+    const double* proxy;
+    int P;
+    int second_kind;
+    void* YK;
+    void* YS;
+    BigGroup* groups;
+    BigState* state;
+    const GroupDesc* gdesc;
+    double* vec_v;
+    double* vec_w;
+    double* vec_t;
+    double* est;
+    double* nrm;
+    int* perm;
+    void* Tws;
+    int* perm_out;
+    int* k_out;
+    double eps;
+    double tol_floor;
+};
+
+template <typename T> cudaError_t big_ygen(const BigArgs&, int nbig, int64_t max_entries, cudaStream_t);
+template <typename T> cudaError_t big_rho(const BigArgs&, int ngroups, int max_m, int max_n, cudaStream_t);
+template <typename T> cudaError_t big_add(void* YK, const void* YS, int64_t n, cudaStream_t);
+template <typename T> cudaError_t big_qr_init(const BigArgs&, int ngroups, int max_n, cudaStream_t);
+template <typename T> cudaError_t big_qr_step(const BigArgs&, int ngroups, int max_n, int j, cudaStream_t);
+template <typename T> cudaError_t big_finish(const BigArgs&, int ngroups, int max_n, cudaStream_t);
+template <typename T>
+cudaError_t big_elim_box(const GeomDev&, const SciDev&, const ElimDesc&, const ElimGroup* d_groups, const int* d_sk,
+                         const int* d_rd, const void* Tws, void* ws, void* fac_pool, int* piv_pool, int* perm_pool,
+                         void* sci_pool, int* status, cudaStream_t);
+
 size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem);
 size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem);
 
@@ -88,6 +154,7 @@ template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStr
 // top block
 template <typename T> cudaError_t launch_top_assemble(const TopArgs&, cudaStream_t);
 template <typename T> cudaError_t top_lu(T* A, int n, int* piv, int* status, cudaStream_t);
+template <typename T> cudaError_t lu_blocked(T* A, int n, int64_t ld, int* piv, int* status, cudaStream_t);
 template <typename T> cudaError_t top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t);
 template <typename T> cudaError_t launch_top_gemm(const T* M, int n, bool trans, const int* ids,
                                                   T* x, int64_t ldx, int nrhs, T* tmp, cudaStream_t);

@@ -71,6 +71,7 @@ EXPORTS = {
     "hif_destroy": (C.c_int, [C.c_void_p]),
     "hif_status_string": (C.c_char_p, [C.c_int]),
     "hif_last_error": (C.c_char_p, []),
+    "hif_kernel_launches": (C.c_uint64, []),
     "hif_kernel_block": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                    C.c_void_p]),
@@ -130,6 +131,10 @@ def _ld(a):
         return a.shape[0], 1
     if hasattr(a, "stride") and callable(a.stride):
         s0, s1 = a.stride()
+        if a.shape[1] == 1:                     # one column: its stride is meaningless
+            if s0 != 1 and a.shape[0] > 1:
+                raise ValueError("vectors must be column-major (stride 1 along rows)")
+            return a.shape[0], 1
         if s0 != 1:
             raise ValueError("vectors must be column-major (stride 1 along rows)")
         return s1, a.shape[1]
@@ -207,6 +212,10 @@ def hif_stats(h) -> dict:
         "per_sublevel": [dict(kind=kind[s.kinds[i]], boxes=s.boxes[i], skeletons=s.skeletons[i],
                               redundant=s.redundant[i], max_box=s.max_box[i]) for i in range(n)],
     }
+
+
+def hif_kernel_launches() -> int:
+    return int(load().hif_kernel_launches())
 
 
 def hif_destroy(h):
