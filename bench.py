@@ -219,7 +219,7 @@ def run_gpu(args):
     t_solve = e0.elapsed_time(e1) / 1000.0
     t_factor = fac.stats()["factor_seconds"]
 
-    # ---- dominant kernel: FP64 direct-sum matvec (uniform-grid convolution), all RHS in one launch
+    # ---- dominant kernel: the paired-FP32 direct-sum convolution (one launch per 8 RHS)
     y = torch.empty_like(F)
     reps = 2
     e0.record()
@@ -228,17 +228,21 @@ def run_gpu(args):
     e1.record()
     torch.cuda.synchronize()
     t_mv = e0.elapsed_time(e1) / 1000.0 / reps
-    flops_mv = 2.0 * N * N * nrhs
     fac.close()
     peaks = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12                # TFLOP/s: 152 SMs x 2 FP64 FMA/clk
-    achieved = flops_mv / t_mv / 1e12
-    roofline = {"kernel": "grid_conv_kernel (FP64 direct sum, uniform-grid convolution)",
-                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz (no measured FP64 peak)",
-                "algorithmic_per_launch": f"2*N^2*nrhs = {flops_mv:.3e} flop", "traffic": None}
+    # 11 FP32 instructions per (pair, right-hand side): 1 mul, 3 fma, 7 add/sub
+    ops_mv = 11.0 * N * N * nrhs
+    fp32_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+    achieved = ops_mv / t_mv / 1e12
+    roofline = {"kernel": "grid_conv_df_kernel<2,8> (paired-FP32 direct sum, uniform-grid convolution)",
+                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x sm_max_mhz, one FP32 instruction per lane "
+                               "per clock (MEASURED_PEAKS has no FP32 SIMT figure)",
+                "algorithmic_per_launch": f"11 FP32 ops x N^2 x nrhs = {ops_mv:.3e}",
+                "launch_seconds": t_mv, "traffic": None,
+                "traffic_note": "compute-bound O(N^2) sweep over O(N) data held in L2; see profiles/"}
 
     # ---- FP64 factorization path for comparison (one step)
     fp64 = None

@@ -59,10 +59,12 @@ typedef struct {
     int proxy_points;       /* number of proxy points P (64 in 2D, 512 in 3D, Sec. 3.3)    */
     double proxy_radius;    /* proxy radius in units of the cell width (1.5, Sec. 3.3)     */
     const double* proxy_dirs; /* P x dim unit vectors (host or device); NULL = 2D circle   */
-    double fp32_tol_floor;  /* FP32 factorization: local ID tolerance >= this (2^-20)      */
+    double fp32_tol_floor;  /* FP32 factorization: local ID tolerance >= this (2^-17)      */
     double root_lo[3];      /* root box lower corner; used when root_width > 0            */
     double root_width;      /* <= 0: bounding cube of the DOF cells                        */
     void* stream;           /* cudaStream_t                                                */
+    int direct_precision;   /* direct sum on uniform grids: 0 = paired FP32 (~2^-48 relative,
+                               default), 1 = FP64; other point sets always use FP64         */
 } hif_options;
 
 typedef struct {
@@ -84,7 +86,8 @@ typedef struct {
 
 /* Defaults for dimension dim (2 or 3): occupancy 64, second_kind 1, FP64,
  * fractional levels on, proxy 64 points (2D) / 512 (3D) at radius 1.5,
- * fp32_tol_floor 2^-20, bounding-cube root box, default stream. */
+ * fp32_tol_floor 2^-17, bounding-cube root box, default stream, paired-FP32
+ * direct sums. */
 hif_status hif_options_default(int dim, hif_options* opt);
 
 /*
@@ -114,9 +117,13 @@ hif_status hif_solve(hif_handle h, const double* b, double* x, int64_t nrhs, int
 hif_status hif_solve_transpose(hif_handle h, const double* b, double* x, int64_t nrhs, int64_t ld);
 
 /*
- * hif_matvec -- y = A x (trans = 0) or y = A^T x (trans = 1) by FP64 direct
+ * hif_matvec -- y = A x (trans = 0) or y = A^T x (trans = 1) by direct
  * summation over all N^2 pairs, exactly the operator the handle factored
- * (same quadrature, same self terms).  x, y: N x nrhs, ld >= N.
+ * (same quadrature, same self terms), with FP64 inputs and outputs.  On a
+ * full uniform grid the sum is a convolution with an FP64 table; it is
+ * accumulated in FP64 (direct_precision = 1) or in paired FP32 with
+ * error-free transformations, good to ~2^-48 relative per operation
+ * (direct_precision = 0).  x, y: N x nrhs, ld >= N.
  */
 hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y,
                       int64_t nrhs, int64_t ld);

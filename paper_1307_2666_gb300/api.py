@@ -40,7 +40,7 @@ class Factorization:
     def __init__(self, points, weights, a, b, c, kernel_id: int, eps: float, *, precision: str = "fp64",
                  second_kind: bool = True, occupancy: int = 64, proxy_dirs=None, fractional: bool = True,
                  skip_levels: int = 0, proxy_radius: float = 1.5, fp32_tol_floor: float | None = None,
-                 root=None, stream=None):
+                 root=None, stream=None, direct: str = "df64"):
         dim = points.shape[1]
         opt = _h.hif_options_default(dim)
         opt.leaf_occupancy = int(occupancy)
@@ -49,6 +49,7 @@ class Factorization:
         opt.fractional_levels = 1 if fractional else 0
         opt.skip_levels = int(skip_levels)
         opt.proxy_radius = float(proxy_radius)
+        opt.direct_precision = 0 if direct == "df64" else 1
         self._keep = []
         if proxy_dirs is not None:
             pd = np.ascontiguousarray(np.asarray(proxy_dirs.cpu() if hasattr(proxy_dirs, "cpu") else proxy_dirs,

@@ -141,7 +141,7 @@ struct hif_handle_s {
     bool grid = false;
     int gn = 0;
     double gh = 0;
-    hif::DevMem dof_of, table, vbuf, ybuf;
+    hif::DevMem dof_of, table, table_df, vbuf, ybuf, vdf;
     // work buffers
     hif::DevMem work, work2, tmp, status;
     hif_stats_t stats{};
@@ -366,7 +366,7 @@ static void run_factor(hif_handle h) {
     std::vector<char> active(N, 1);
     std::vector<int> box_of(N, -1);
     DevMem d_boxes, d_groups, d_cols, d_near, Rws, GKws, GSws, Tws, Wws, Woff, perm_out, k_out;
-    DevMem d_ed, d_eg, d_sk, d_rd, ews, piv_scratch, d_small_boxes, d_small_groups;
+    DevMem d_ed, d_ed_big, d_eg, d_sk, d_rd, ews, piv_scratch, d_small_boxes, d_small_groups;
     BigBuffers big;
     const int big_id_n = env_int("HIF_BIG_ID", sizeof(T) == 8 ? 128 : 256);
     const int big_elim_n = env_int("HIF_BIG_ELIM", 600);
@@ -644,10 +644,31 @@ static void run_factor(hif_handle h) {
             ea.sci_pool = pool->p;
             ea.status = h->status.as<int>();
             HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), st)));
-            for (const ElimDesc& eb : ed_big)
-                HIF_CUDA((big_elim_box<T>(g, ea.sci, eb, d_eg.as<ElimGroup>(), sf->sk.as<int>(), sf->rd.as<int>(), Tws.p,
-                                          ews.p, sf->pool.p, piv_scratch.as<int>(), sf->perm.as<int>(), pool->p,
-                                          h->status.as<int>(), st)));
+            if (!ed_big.empty()) {
+                upload(d_ed_big, ed_big, st);
+                int mxn = 0, mxk = 0, mxr = 0;
+                for (const ElimDesc& eb : ed_big) {
+                    mxn = std::max(mxn, eb.k + eb.r);
+                    mxk = std::max(mxk, eb.k);
+                    mxr = std::max(mxr, eb.r);
+                }
+                BatchElimArgs ba{};
+                ba.g = g;
+                ba.sci = ea.sci;
+                ba.ed = d_ed_big.as<ElimDesc>();
+                ba.nbox = (int)ed_big.size();
+                ba.groups = d_eg.as<ElimGroup>();
+                ba.sk = sf->sk.as<int>();
+                ba.rd = sf->rd.as<int>();
+                ba.Tws = Tws.p;
+                ba.ws = ews.p;
+                ba.pool = sf->pool.p;
+                ba.piv = piv_scratch.as<int>();
+                ba.perm = sf->perm.as<int>();
+                ba.sci_pool = pool->p;
+                ba.status = h->status.as<int>();
+                HIF_CUDA((big_elim_batch<T>(ba, mxn, mxk, mxr, st)));
+            }
             h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
         }
         h->sci_pools.push_back(std::move(pool));
@@ -825,7 +846,12 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
         ga.trans = trans;
         ga.vbuf = h->vbuf.as<double>();
         ga.ybuf = h->ybuf.as<double>();
-        HIF_CUDA(launch_direct_grid(ga, st));
+        if (h->opt.direct_precision == 0) {
+            h->vdf.ensure(sizeof(float2) * N * nrhs);
+            HIF_CUDA(launch_direct_grid_df(ga, h->table_df.as<float2>(), h->vdf.as<float2>(), st));
+        } else {
+            HIF_CUDA(launch_direct_grid(ga, st));
+        }
     } else {
         DirectArgs da{};
         da.g = geom(h);
@@ -1057,7 +1083,8 @@ hif_status hif_options_default(int dim, hif_options* opt) {
     opt->proxy_points = dim == 2 ? 64 : 512;
     opt->proxy_radius = 1.5;
     opt->proxy_dirs = nullptr;
-    opt->fp32_tol_floor = std::ldexp(1.0, -20);
+    opt->fp32_tol_floor = std::ldexp(1.0, -17);
+    opt->direct_precision = 0;
     opt->root_width = 0.0;
     opt->stream = nullptr;
     return HIF_OK;
@@ -1076,6 +1103,7 @@ hif_status hif_factor(const double* points, int64_t N, const double* weights, co
     if (!(eps >= 0.0) || !std::isfinite(eps)) return HIF_EINVAL;
     if (opt.leaf_occupancy < 1 || opt.proxy_points < 1 || !(opt.proxy_radius > 0)) return HIF_EINVAL;
     if (opt.precision != 0 && opt.precision != 1) return HIF_EINVAL;
+    if (opt.direct_precision != 0 && opt.direct_precision != 1) return HIF_EINVAL;
     if (opt.dim == 3 && !opt.proxy_dirs) return HIF_EINVAL;
     auto h = std::make_unique<hif_handle_s>();
     const auto t0 = std::chrono::steady_clock::now();
@@ -1144,6 +1172,8 @@ hif_status hif_factor(const double* points, int64_t N, const double* weights, co
             HIF_CUDA(cudaMemcpyAsync(&k0, h->kself.p, sizeof(double), cudaMemcpyDeviceToHost, st));
             HIF_CUDA(cudaStreamSynchronize(st));
             HIF_CUDA(launch_grid_table(h->table.as<double>(), h->gn, d, h->gh, kernel_id, k0 / h->hw[0], st));
+            h->table_df.ensure(sizeof(float2) * tsz);
+            HIF_CUDA(launch_split_df(h->table.as<double>(), h->table_df.as<float2>(), tsz, st));
         }
         h->stats.N = N;
         h->stats.dim = d;

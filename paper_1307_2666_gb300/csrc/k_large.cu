@@ -589,51 +589,405 @@ __global__ void piv_to_perm_kernel(const int* piv, int r, int* pm) {
     }
 }
 
+// ---------------------------------------------- batched elimination ----
+//
+// All large boxes of a sublevel are eliminated together: every stage below is
+// one launch whose last grid dimension runs over the boxes.  Box e works on
+// its own workspace A_e (n x n, order (rd, sk)) and T_e (k x r).
+
 template <typename T>
-cudaError_t big_elim_box(const GeomDev& g, const SciDev& sci, const ElimDesc& ed, const ElimGroup* d_groups,
-                         const int* d_sk, const int* d_rd, const void* Tws, void* ws, void* fac_pool, int* piv_pool,
-                         int* perm_pool, void* sci_pool, int* status, cudaStream_t st) {
-    const int k = ed.k, r = ed.r, n = k + r;
-    T* A = static_cast<T*>(ws) + ed.ws_off;
-    T* Tm = A + (int64_t)n * n;
-    const int* sk = d_sk + ed.sk_off;
-    const int* rd = d_rd + ed.rd_off;
-    const int64_t ld = n;
-    note_launch();
-    big_gather_kernel<T><<<(unsigned)std::min<int64_t>(((int64_t)n * n + 255) / 256, 152 * 16), 256, 0, st>>>(
-        g, sci, rd, r, sk, k, A);
-    note_launch();
-    big_T_assemble_kernel<T><<<1, 256, 0, st>>>(d_groups + ed.grp_off, ed.ngroups, static_cast<const T*>(Tws), k, r, Tm);
-    T* Arr = A;
-    T* Asr = A + r;
-    T* Ars = A + ld * r;
-    T* Ass = A + ld * r + r;
-    cudaError_t e;
-    if ((e = gemm<T>(k, r, k, T(-1), Ass, ld, false, Tm, k, false, Asr, ld, st)) != cudaSuccess) return e;
-    if ((e = gemm<T>(r, r, k, T(-1), Tm, k, true, Asr, ld, false, Arr, ld, st)) != cudaSuccess) return e;
-    if ((e = gemm<T>(r, r, k, T(-1), Ars, ld, false, Tm, k, false, Arr, ld, st)) != cudaSuccess) return e;
-    if ((e = gemm<T>(r, k, k, T(-1), Tm, k, true, Ass, ld, false, Ars, ld, st)) != cudaSuccess) return e;
-    int* piv = piv_pool + ed.piv_out;
-    if ((e = lu_blocked<T>(Arr, r, ld, piv, status, st)) != cudaSuccess) return e;
-    if (k > 0) {
-        note_launch();
-        trsm_right_upper_rows<T><<<(k + 127) / 128, 128, 0, st>>>(r, Arr, ld, Asr, ld, k);
-        note_launch();
-        piv_lower_cols<T><<<(k + 127) / 128, 128, 0, st>>>(r, Arr, ld, piv, Ars, ld, k);
-        if (ed.sci_out >= 0) {
-            T* S = static_cast<T*>(sci_pool) + ed.sci_out;
-            if ((e = cudaMemsetAsync(S, 0, sizeof(T) * (size_t)k * k, st)) != cudaSuccess) return e;
-            if ((e = gemm<T>(k, k, r, T(-1), Asr, ld, false, Ars, ld, false, S, k, st)) != cudaSuccess) return e;
+struct EBox {
+    int k, r, n;
+    T* A;
+    T* Tm;
+    __device__ EBox(const BatchElimArgs& a, int e) {
+        const ElimDesc& d = a.ed[e];
+        k = d.k;
+        r = d.r;
+        n = k + r;
+        A = static_cast<T*>(a.ws) + d.ws_off;
+        Tm = A + (int64_t)n * n;
+    }
+};
+
+template <typename T>
+__global__ void be_gather_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> B(a, e);
+    const int* sk = a.sk + d.sk_off;
+    const int* rd = a.rd + d.rd_off;
+    const int ref = B.r > 0 ? rd[0] : sk[0];
+    const int dm = a.g.dim;
+    const double r0 = a.g.x[(int64_t)dm * ref], r1 = a.g.x[(int64_t)dm * ref + 1];
+    const double r2 = dm == 3 ? a.g.x[(int64_t)dm * ref + 2] : 0.0;
+    const int64_t tot = (int64_t)B.n * B.n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(q % B.n), c = (int)(q / B.n);
+        const int i = p < B.r ? rd[p] : sk[p - B.r];
+        const int j = c < B.r ? rd[c] : sk[c - B.r];
+        B.A[q] = entry<T>(a.g, a.sci, i, j, r0, r1, r2);
+    }
+}
+
+template <typename T>
+__global__ void be_T_kernel(BatchElimArgs a) {
+    const int e = blockIdx.x;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> B(a, e);
+    for (int q = threadIdx.x; q < B.k * B.r; q += blockDim.x) B.Tm[q] = T(0);
+    __syncthreads();
+    const T* Tws = static_cast<const T*>(a.Tws);
+    for (int gi = 0; gi < d.ngroups; ++gi) {
+        const ElimGroup G = a.groups[d.grp_off + gi];
+        for (int q = threadIdx.x; q < G.kg * G.rg; q += blockDim.x) {
+            const int i = q % G.kg, jj = q / G.kg;
+            B.Tm[(G.ko + i) + (int64_t)B.k * (G.ro + jj)] = Tws[G.T_off + q];
         }
     }
-    T* pool = static_cast<T*>(fac_pool);
+}
+
+// the GEMMs of Lemma 2.3 and the Schur update, one op per launch:
+// 0: B_sr = A_sr - A_ss T     1: B_rr -= T^T B_sr     2: B_rr -= A_rs T
+// 3: B_rs = A_rs - T^T A_ss   4: S = -X Z (into the SCI pool)
+template <typename T>
+__global__ void __launch_bounds__(256) be_gemm_kernel(BatchElimArgs a, int op) {
+    __shared__ T As[16][64 + 1];
+    __shared__ T Bs[16][64 + 1];
+    const int e = blockIdx.z;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    const int64_t ld = Bx.n;
+    T* Arr = Bx.A;
+    T* Asr = Bx.A + r;
+    T* Ars = Bx.A + ld * r;
+    T* Ass = Bx.A + ld * r + r;
+    int m, n, kk;
+    const T* A;
+    const T* Bm;
+    T* C;
+    int64_t lda, ldb, ldc;
+    bool tA = false, tB = false;
+    switch (op) {
+        case 0: m = k; n = r; kk = k; A = Ass; lda = ld; Bm = Bx.Tm; ldb = k; C = Asr; ldc = ld; break;
+        case 1: m = r; n = r; kk = k; A = Bx.Tm; lda = k; tA = true; Bm = Asr; ldb = ld; C = Arr; ldc = ld; break;
+        case 2: m = r; n = r; kk = k; A = Ars; lda = ld; Bm = Bx.Tm; ldb = k; C = Arr; ldc = ld; break;
+        case 3: m = r; n = k; kk = k; A = Bx.Tm; lda = k; tA = true; Bm = Ass; ldb = ld; C = Ars; ldc = ld; break;
+        default:
+            if (k == 0 || d.sci_out < 0) return;
+            m = k; n = k; kk = r; A = Asr; lda = ld; Bm = Ars; ldb = ld;
+            C = static_cast<T*>(a.sci_pool) + d.sci_out; ldc = k;
+            break;
+    }
+    const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+    if (i0 >= m || j0 >= n || kk == 0) return;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4] = {};
+    for (int l0 = 0; l0 < kk; l0 += 16) {
+        for (int q = threadIdx.x; q < 64 * 16; q += 256) {
+            const int rr = q % 64, l = q / 64;
+            const int i = i0 + rr, kx = l0 + l;
+            T v = T(0);
+            if (i < m && kx < kk) v = tA ? A[kx + lda * i] : A[i + lda * kx];
+            As[l][rr] = v;
+            const int jj = j0 + rr;
+            T u = T(0);
+            if (jj < n && kx < kk) u = tB ? Bm[jj + ldb * kx] : Bm[kx + ldb * jj];
+            Bs[l][rr] = u;
+        }
+        __syncthreads();
+        for (int l = 0; l < 16; ++l) {
+            T av[4], bv[4];
+            for (int q = 0; q < 4; ++q) av[q] = As[l][tx + 16 * q];
+            for (int q = 0; q < 4; ++q) bv[q] = Bs[l][ty + 16 * q];
+            for (int p = 0; p < 4; ++p)
+                for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+        }
+        __syncthreads();
+    }
+    for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + tx + 16 * p, jj = j0 + ty + 16 * q;
+            if (i < m && jj < n) {
+                if (op == 4) C[i + ldc * jj] = -acc[p][q];
+                else C[i + ldc * jj] -= acc[p][q];
+            }
+        }
+}
+
+// blocked LU of B_rr (Lemma 2.1), panel / interchange+TRSM / update stages
+template <typename T>
+__global__ void __launch_bounds__(256) be_panel_kernel(BatchElimArgs a, int j0) {
+    const int e = blockIdx.x;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int n = Bx.r;
+    if (j0 >= n) return;
+    const int nb = min(32, n - j0);
+    const int64_t ld = Bx.n;
+    T* A = Bx.A;
+    int* piv = a.piv + d.piv_out;
+    __shared__ T redv[256];
+    __shared__ int redi[256];
+    for (int j = j0 + threadIdx.x; j < j0 + nb; j += blockDim.x) piv[j] = j;
+    __syncthreads();
+    for (int j = j0; j < j0 + nb; ++j) {
+        T best = T(-1);
+        int bi = j;
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+            const T v = fabs(A[i + ld * j]);
+            if (v > best) { best = v; bi = i; }
+        }
+        redv[threadIdx.x] = best;
+        redi[threadIdx.x] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const T v2 = redv[threadIdx.x + s];
+                const int i2 = redi[threadIdx.x + s];
+                if (v2 > redv[threadIdx.x] || (v2 == redv[threadIdx.x] && i2 < redi[threadIdx.x])) {
+                    redv[threadIdx.x] = v2;
+                    redi[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        int p = redi[0];
+        if (p < j || p >= n) p = j;
+        __syncthreads();
+        if (threadIdx.x == 0) piv[j] = p;
+        if (p != j)
+            for (int c = j0 + threadIdx.x; c < j0 + nb; c += blockDim.x) {
+                const T t = A[j + ld * c];
+                A[j + ld * c] = A[p + ld * c];
+                A[p + ld * c] = t;
+            }
+        __syncthreads();
+        const T dg = A[j + ld * j];
+        if (dg == T(0) || !isfinite((double)dg)) {
+            if (threadIdx.x == 0) atomicOr(a.status, (int)DEV_SINGULAR);
+            return;
+        }
+        const T inv = T(1) / dg;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const T l = A[i + ld * j] * inv;
+            A[i + ld * j] = l;
+            for (int c = j + 1; c < j0 + nb; ++c) A[i + ld * c] -= l * A[j + ld * c];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void be_swap_trsm_kernel(BatchElimArgs a, int j0) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int n = Bx.r;
+    if (j0 >= n) return;
+    const int nb = min(32, n - j0);
+    const int64_t ld = Bx.n;
+    T* A = Bx.A;
+    const int* piv = a.piv + d.piv_out;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || (c >= j0 && c < j0 + nb)) return;
+    for (int j = j0; j < j0 + nb; ++j) {
+        const int p = piv[j];
+        if (p != j) {
+            const T t = A[j + ld * c];
+            A[j + ld * c] = A[p + ld * c];
+            A[p + ld * c] = t;
+        }
+    }
+    if (c >= j0 + nb)
+        for (int i = j0; i < j0 + nb; ++i) {
+            T v = A[i + ld * c];
+            for (int l = j0; l < i; ++l) v -= A[i + ld * l] * A[l + ld * c];
+            A[i + ld * c] = v;
+        }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) be_update_kernel(BatchElimArgs a, int j0) {
+    const int e = blockIdx.z;
+    const EBox<T> Bx(a, e);
+    const int n = Bx.r;
+    if (j0 >= n) return;
+    const int nb = min(32, n - j0);
+    const int s = j0 + nb;
+    const int i0 = s + blockIdx.x * 64, c0 = s + blockIdx.y * 64;
+    if (i0 >= n || c0 >= n) return;
+    const int64_t ld = Bx.n;
+    T* A = Bx.A;
+    __shared__ T Ls[64][33];
+    __shared__ T Us[32][65];
+    for (int q = threadIdx.x; q < 64 * nb; q += blockDim.x) {
+        const int i = q % 64, l = q / 64;
+        Ls[i][l] = (i0 + i < n) ? A[(i0 + i) + ld * (j0 + l)] : T(0);
+    }
+    for (int q = threadIdx.x; q < 64 * nb; q += blockDim.x) {
+        const int l = q % nb, c = q / nb;
+        Us[l][c] = (c0 + c < n) ? A[(j0 + l) + ld * (c0 + c)] : T(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4] = {};
+    for (int l = 0; l < nb; ++l) {
+        T av[4], bv[4];
+        for (int q = 0; q < 4; ++q) av[q] = Ls[tx + 16 * q][l];
+        for (int q = 0; q < 4; ++q) bv[q] = Us[l][ty + 16 * q];
+        for (int p = 0; p < 4; ++p)
+            for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+    }
+    for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + tx + 16 * p, c = c0 + ty + 16 * q;
+            if (i < n && c < n) A[i + ld * c] -= acc[p][q];
+        }
+}
+
+// X = B_sr (DU)^{-1} (thread per row of X) and Z = L^{-1} P B_rs (thread per column)
+template <typename T>
+__global__ void be_tri_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    const int64_t ld = Bx.n;
+    const T* U = Bx.A;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < k) {
+        T* X = Bx.A + r;
+        for (int j = 0; j < r; ++j) {
+            T v = X[t + ld * j];
+            for (int l = 0; l < j; ++l) v -= X[t + ld * l] * U[l + ld * j];
+            X[t + ld * j] = v / U[j + ld * j];
+        }
+    } else if (t < 2 * k) {
+        const int c = t - k;
+        T* col = Bx.A + ld * r + ld * c;
+        const int* piv = a.piv + d.piv_out;
+        for (int j = 0; j < r; ++j) {
+            const int p = piv[j];
+            if (p != j) { const T tt = col[j]; col[j] = col[p]; col[p] = tt; }
+        }
+        for (int i = 0; i < r; ++i) {
+            T v = col[i];
+            for (int l = 0; l < i; ++l) v -= U[i + ld * l] * col[l];
+            col[i] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void be_out_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    const int64_t ld = Bx.n;
+    const T* Arr = Bx.A;
+    const T* Asr = Bx.A + r;
+    const T* Ars = Bx.A + ld * r;
+    T* pool = static_cast<T*>(a.pool);
+    T* Dv = pool + d.D_out;
+    T* LUo = pool + d.LU_out;
+    T* Xo = pool + d.X_out;
+    T* Yo = pool + d.Y_out;
+    T* To = pool + d.T_out;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t q = t0; q < r; q += stride) Dv[q] = Arr[q + ld * q];
+    for (int64_t q = t0; q < (int64_t)r * r; q += stride) {
+        const int i = (int)(q % r), j = (int)(q / r);
+        LUo[q] = i == j ? T(0) : (i < j ? Arr[i + ld * j] / Arr[i + ld * i] : Arr[i + ld * j]);
+    }
+    for (int64_t q = t0; q < (int64_t)k * r; q += stride) {
+        const int i = (int)(q % k), j = (int)(q / k);
+        Xo[q] = Asr[i + ld * j];
+        To[q] = Bx.Tm[q];
+    }
+    for (int64_t q = t0; q < (int64_t)r * k; q += stride) {
+        const int i = (int)(q % r), j = (int)(q / r);
+        Yo[q] = Ars[i + ld * j] / Arr[i + ld * i];
+    }
+}
+
+// unit triangular inverses (thread per column) and LAPACK pivots -> permutation
+template <typename T>
+__global__ void be_inv_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const int r = d.r;
+    T* pool = static_cast<T*>(a.pool);
+    const T* A = pool + d.LU_out;
+    T* out = pool + d.LUi_out;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) {
+        int* pm = a.perm + d.piv_out;
+        const int* piv = a.piv + d.piv_out;
+        for (int i = 0; i < r; ++i) pm[i] = i;
+        for (int j = 0; j < r; ++j) {
+            const int p = piv[j];
+            const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
+        }
+    }
+    if (c >= r) return;
+    const int64_t ld = r;
+    out[c + ld * c] = T(0);
+    for (int i = c + 1; i < r; ++i) {
+        T v = -A[i + ld * c];
+        for (int l = c + 1; l < i; ++l) v -= A[i + ld * l] * out[l + ld * c];
+        out[i + ld * c] = v;
+    }
+    for (int i = c - 1; i >= 0; --i) {
+        T v = -A[i + ld * c];
+        for (int l = i + 1; l < c; ++l) v -= A[i + ld * l] * out[l + ld * c];
+        out[i + ld * c] = v;
+    }
+}
+
+template <typename T>
+cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max_r, cudaStream_t st) {
+    const int nb = a.nbox;
+    if (nb == 0) return cudaSuccess;
     note_launch();
-    big_elim_out_kernel<T><<<(unsigned)std::min<int64_t>(((int64_t)n * n + 255) / 256, 1024), 256, 0, st>>>(
-        k, r, A, ld, Tm, pool, ed);
+    be_gather_kernel<T><<<dim3((unsigned)std::min<int64_t>(((int64_t)max_n * max_n + 255) / 256, 1024), nb), 256, 0, st>>>(a);
     note_launch();
-    tri_inv_cols<T><<<(r + 127) / 128, 128, 0, st>>>(r, pool + ed.LU_out, pool + ed.LUi_out);
+    be_T_kernel<T><<<nb, 256, 0, st>>>(a);
+    const int tk = (max_k + 63) / 64, tr = (max_r + 63) / 64;
+    if (max_k > 0) {
+        note_launch();
+        be_gemm_kernel<T><<<dim3(tk, tr, nb), 256, 0, st>>>(a, 0);
+        note_launch();
+        be_gemm_kernel<T><<<dim3(tr, tr, nb), 256, 0, st>>>(a, 1);
+        note_launch();
+        be_gemm_kernel<T><<<dim3(tr, tr, nb), 256, 0, st>>>(a, 2);
+        note_launch();
+        be_gemm_kernel<T><<<dim3(tr, tk, nb), 256, 0, st>>>(a, 3);
+    }
+    for (int j0 = 0; j0 < max_r; j0 += 32) {
+        note_launch();
+        be_panel_kernel<T><<<nb, 256, 0, st>>>(a, j0);
+        note_launch();
+        be_swap_trsm_kernel<T><<<dim3((max_r + 127) / 128, nb), 128, 0, st>>>(a, j0);
+        const int rest = max_r - j0 - 32;
+        if (rest > 0) {
+            note_launch();
+            be_update_kernel<T><<<dim3((rest + 63) / 64, (rest + 63) / 64, nb), 256, 0, st>>>(a, j0);
+        }
+    }
+    if (max_k > 0) {
+        note_launch();
+        be_tri_kernel<T><<<dim3((2 * max_k + 127) / 128, nb), 128, 0, st>>>(a);
+        note_launch();
+        be_gemm_kernel<T><<<dim3(tk, tk, nb), 256, 0, st>>>(a, 4);
+    }
     note_launch();
-    piv_to_perm_kernel<<<1, 1, 0, st>>>(piv, r, perm_pool + ed.piv_out);
+    be_out_kernel<T><<<dim3((unsigned)std::min<int64_t>(((int64_t)max_n * max_n + 255) / 256, 512), nb), 256, 0, st>>>(a);
+    note_launch();
+    be_inv_kernel<T><<<dim3((max_r + 127) / 128, nb), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -644,9 +998,7 @@ cudaError_t big_elim_box(const GeomDev& g, const SciDev& sci, const ElimDesc& ed
     template cudaError_t big_qr_init<T>(const BigArgs&, int, int, cudaStream_t);                               \
     template cudaError_t big_qr_step<T>(const BigArgs&, int, int, int, cudaStream_t);                          \
     template cudaError_t big_finish<T>(const BigArgs&, int, int, cudaStream_t);                                \
-    template cudaError_t big_elim_box<T>(const GeomDev&, const SciDev&, const ElimDesc&, const ElimGroup*,      \
-                                         const int*, const int*, const void*, void*, void*, int*, int*, void*, \
-                                         int*, cudaStream_t);
+    template cudaError_t big_elim_batch<T>(const BatchElimArgs&, int, int, int, cudaStream_t);
 HIF_INST(double)
 HIF_INST(float)
 

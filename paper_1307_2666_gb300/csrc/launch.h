@@ -139,10 +139,23 @@ template <typename T> cudaError_t big_add(void* YK, const void* YS, int64_t n, c
 template <typename T> cudaError_t big_qr_init(const BigArgs&, int ngroups, int max_n, cudaStream_t);
 template <typename T> cudaError_t big_qr_step(const BigArgs&, int ngroups, int max_n, int j, cudaStream_t);
 template <typename T> cudaError_t big_finish(const BigArgs&, int ngroups, int max_n, cudaStream_t);
-template <typename T>
-cudaError_t big_elim_box(const GeomDev&, const SciDev&, const ElimDesc&, const ElimGroup* d_groups, const int* d_sk,
-                         const int* d_rd, const void* Tws, void* ws, void* fac_pool, int* piv_pool, int* perm_pool,
-                         void* sci_pool, int* status, cudaStream_t);
+struct BatchElimArgs {
+    GeomDev g;
+    SciDev sci;
+    const ElimDesc* ed;       // the large boxes
+    int nbox;
+    const ElimGroup* groups;
+    const int* sk;
+    const int* rd;
+    const void* Tws;
+    void* ws;
+    void* pool;
+    int* piv;
+    int* perm;
+    void* sci_pool;
+    int* status;
+};
+template <typename T> cudaError_t big_elim_batch(const BatchElimArgs&, int max_n, int max_k, int max_r, cudaStream_t);
 
 size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem);
 size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem);
@@ -198,6 +211,10 @@ struct GridDirectArgs {     // uniform tensor grid: K depends on the index offse
     double* ybuf;           // N x nrhs scratch (grid order)
 };
 cudaError_t launch_direct_grid(const GridDirectArgs&, cudaStream_t);
+// same sum in paired-FP32 arithmetic; tdf: the table split into (hi, lo)
+// floats, vdf: N x nrhs float2 scratch
+cudaError_t launch_direct_grid_df(const GridDirectArgs&, const float2* tdf, float2* vdf, cudaStream_t);
+cudaError_t launch_split_df(const double* src, float2* dst, int64_t n, cudaStream_t);
 cudaError_t launch_grid_table(double* table, int n, int dim, double h, int kernel_id, double kself_over_w,
                               cudaStream_t);
 

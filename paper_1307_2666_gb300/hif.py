@@ -34,6 +34,7 @@ class hif_options(C.Structure):
         ("root_lo", C.c_double * 3),
         ("root_width", C.c_double),
         ("stream", C.c_void_p),
+        ("direct_precision", C.c_int),
     ]
 
 

@@ -152,6 +152,21 @@ def test_direct_sum_grid_matches_oracle(lib, trans):
     fac.close()
 
 
+def test_direct_sum_paired_fp32_matches_fp64(lib):
+    # the paired-FP32 convolution agrees with the FP64 one to ~1e-14
+    P = lib
+    pb = hi.volume_problem(96, 2, smooth_seed=1002)
+    x = T(hi.gaussian_rhs(pb.N, 5, 8))
+    f1 = factor(P, pb, 1e-3, direct="df64")
+    f2 = factor(P, pb, 1e-3, direct="fp64")
+    for trans in (False, True):
+        y1 = f1.matvec(x, trans=trans).cpu().numpy()
+        y2 = f2.matvec(x, trans=trans).cpu().numpy()
+        assert np.abs(y1 - y2).max() <= 1e-13 * np.abs(y2).max()
+    f1.close()
+    f2.close()
+
+
 def test_direct_sum_general_points_matches_oracle(lib):
     P = lib
     pb = hi.volume_problem(24, 2, smooth_seed=5)

@@ -49,7 +49,8 @@ def test_struct_layouts_match_header(lib):
     # hif_options_default fills every field; defaults from the header comment
     o = hif.hif_options_default(2)
     assert (o.dim, o.leaf_occupancy, o.second_kind, o.precision, o.fractional_levels) == (2, 64, 1, 0, 1)
-    assert o.proxy_points == 64 and o.proxy_radius == 1.5 and o.fp32_tol_floor == 2.0 ** -20
+    assert o.proxy_points == 64 and o.proxy_radius == 1.5 and o.fp32_tol_floor == 2.0 ** -17
+    assert o.direct_precision == 0
     o3 = hif.hif_options_default(3)
     assert o3.proxy_points == 512
 
