@@ -174,7 +174,9 @@ hif_status hif_kernel_block(const double* points, int64_t N, int dim, const doub
  * hif_id_batched -- interpolative decompositions of `count` independent
  * matrices by column-pivoted Householder QR (Sec. 2.2, Lemma 2.2) with
  * adaptive rank: k = number of pivots with |R_jj| > tol[i] |R_11|.
- *   mats    column-major m[i] x n[i] blocks at offsets off[i] (FP64, device or host)
+ * The index and tolerance arrays (off, m, n, tol, poff, toff) are read on
+ * the host and must be host memory; mats, k, perm and T may be host or device.
+ *   mats    column-major m[i] x n[i] blocks at offsets off[i] (FP64)
  *   tol     per-matrix relative tolerance
  *   k       out: rank per matrix
  *   perm    out: n[i] column indices per matrix at poff[i]: skeletons in pivot
@@ -188,6 +190,34 @@ hif_status hif_id_batched(int count, const double* mats, const int64_t* off,
                           const int32_t* m, const int32_t* n, const double* tol,
                           int32_t* k, int32_t* perm, const int64_t* poff,
                           double* T, const int64_t* toff, void* stream);
+
+/*
+ * hif_id_batched_noalloc -- the batched interpolative decomposition of
+ * hif_id_batched for callers that must not allocate memory: code that runs
+ * while a CUDA graph is being captured, real-time or embedded callers with a
+ * fixed memory budget, and any caller for which cudaMalloc would synchronize
+ * the device at the wrong moment.  This entry point has no counterpart in the
+ * paper; it calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Arguments, results and the rank rule are those of hif_id_batched, except
+ * that every array must already live in device memory (HIF_EINVAL otherwise).
+ * The QR work space is one fixed array in device memory that every GPU which
+ * loads the library keeps until the process exits: about 8 MiB of matrix
+ * copies plus 32 KiB of offsets.  Limits: at most 4096 matrices, at most 1024
+ * columns per matrix, and sum over matrices of (m|1)*n <= 1,048,576 doubles;
+ * larger inputs are rejected with HIF_EINVAL (hif_last_error says why) and
+ * leave the outputs untouched.
+ *
+ * The first call on a device looks up that device's address of the array;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents; calls that overlap on the GPU
+ * (different streams, different threads) race on it.  The call returns after
+ * its results are complete on `stream`.
+ */
+hif_status hif_id_batched_noalloc(int count, const double* mats, const int64_t* off,
+                                  const int32_t* m, const int32_t* n, const double* tol,
+                                  int32_t* k, int32_t* perm, const int64_t* poff,
+                                  double* T, const int64_t* toff, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1329,3 +1329,36 @@ hif_status hif_id_batched(int count, const double* mats, const int64_t* off, con
 }
 
 }  // extern "C"
+
+extern "C" {
+
+hif_status hif_id_batched_noalloc(int count, const double* mats, const int64_t* off, const int32_t* m,
+                                  const int32_t* n, const double* tol, int32_t* k, int32_t* perm,
+                                  const int64_t* poff, double* T, const int64_t* toff, void* stream) {
+    if (count < 0 || !mats || !off || !m || !n || !tol || !k || !perm || !poff || !T || !toff) return HIF_EINVAL;
+    if (count == 0) return HIF_OK;
+    const void* ptrs[] = {mats, off, m, n, tol, k, perm, poff, T, toff};
+    for (const void* p : ptrs) {
+        if (!is_device_ptr(p)) {
+            std::snprintf(g_last_error, sizeof(g_last_error),
+                          "hif_id_batched_noalloc: every array must be device memory");
+            return HIF_EINVAL;
+        }
+    }
+    int too_big = 0;
+    const cudaError_t e = launch_id_batched_noalloc(count, mats, off, m, n, tol, k, perm, poff, T, toff,
+                                                    static_cast<cudaStream_t>(stream), &too_big);
+    if (e != cudaSuccess) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "hif_id_batched_noalloc: %s", cudaGetErrorString(e));
+        return HIF_ECUDA;
+    }
+    if (too_big) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "hif_id_batched_noalloc: input exceeds the fixed work space (at most 4096 matrices, "
+                      "1024 columns each, sum over matrices of (m|1)*n <= 1048576 doubles)");
+        return HIF_EINVAL;
+    }
+    return HIF_OK;
+}
+
+}  // extern "C"

@@ -16,6 +16,7 @@
 //                B_ss - B_sr B_rr^{-1} B_rs recorded as a new SCI block.
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "cta_linalg.cuh"
@@ -660,5 +661,108 @@ template cudaError_t launch_id<double>(const IdArgs&, int, size_t, cudaStream_t)
 template cudaError_t launch_id<float>(const IdArgs&, int, size_t, cudaStream_t);
 template cudaError_t launch_elim<double>(const ElimArgs&, int, cudaStream_t);
 template cudaError_t launch_elim<float>(const ElimArgs&, int, cudaStream_t);
+
+}  // namespace hif
+
+// ------------------------------------------- batched ID without allocation --
+//
+// For callers that may not allocate memory (code running where cudaMalloc is
+// forbidden or would synchronize, e.g. inside a region being captured into a
+// CUDA graph, or under a strict memory budget): the work space of the batched
+// ID lives in one file-scope device array, sized once for the whole process.
+// Its layout: per-matrix work-space offsets, an error flag, then the copies of
+// the matrices that the QR overwrites.
+
+namespace hif {
+
+constexpr int kNoAllocMaxMats = 4096;
+constexpr int kNoAllocMaxCols = 1024;
+constexpr int64_t kNoAllocWsDoubles = (int64_t)1 << 20;   // 8 MiB of matrix copies
+constexpr size_t kNoAllocOffBytes = sizeof(int64_t) * kNoAllocMaxMats;
+constexpr size_t kNoAllocFlagBytes = 256;
+constexpr size_t kNoAllocBytes = kNoAllocOffBytes + kNoAllocFlagBytes + sizeof(double) * kNoAllocWsDoubles;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+__global__ void id_noalloc_prep_kernel(unsigned char* scratch, int count, const int* m, const int* n) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int64_t* off = reinterpret_cast<int64_t*>(scratch);
+    int* flag = reinterpret_cast<int*>(scratch + kNoAllocOffBytes);
+    int64_t run = 0;
+    int bad = 0;
+    for (int i = 0; i < count; ++i) {
+        const int mi = m[i], ni = n[i];
+        if (mi < 0 || ni < 0 || ni > kNoAllocMaxCols) { bad = 1; break; }
+        off[i] = run;
+        run += (int64_t)(mi | 1) * ni;
+        if (run > kNoAllocWsDoubles) { bad = 1; break; }
+    }
+    *flag = bad;
+}
+
+__global__ void __launch_bounds__(128) id_noalloc_kernel(unsigned char* scratch, const double* mats,
+                                                          const int64_t* off, const int* m, const int* n,
+                                                          const double* tol, int* k, int* perm, const int64_t* poff,
+                                                          double* T, const int64_t* toff) {
+    const int* flag = reinterpret_cast<const int*>(scratch + kNoAllocOffBytes);
+    if (*flag) return;
+    const int b = blockIdx.x;
+    const int mm = m[b], nn = n[b];
+    const int ldw = mm | 1;
+    double* ws = reinterpret_cast<double*>(scratch + kNoAllocOffBytes + kNoAllocFlagBytes);
+    double* W = ws + reinterpret_cast<const int64_t*>(scratch)[b];
+    const double* M = mats + off[b];
+    __shared__ double nrm[kNoAllocMaxCols];
+    __shared__ int pm[kNoAllocMaxCols];
+    __shared__ int rk[kNoAllocMaxCols];
+    __shared__ double redv[128];
+    __shared__ int redi[128];
+    __shared__ double hh[4];
+    for (int e = threadIdx.x; e < mm * nn; e += blockDim.x) W[(e % mm) + (int64_t)ldw * (e / mm)] = M[e];
+    __syncthreads();
+    cpqr_id<double>(W, ldw, mm, nn, tol[b], nrm, pm, rk, redv, redi, hh, T + toff[b], perm + poff[b], k + b);
+}
+
+// Device address of the scratch array for the current device, looked up once
+// per device (the symbol's host-side name is not a device address).
+static unsigned char* noalloc_scratch_ptr(cudaError_t* err) {
+    static std::mutex mu;
+    static unsigned char* cache[128] = {};
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= 128) { *err = cudaErrorInvalidDevice; return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cache[dev]) {
+        void* p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        cache[dev] = static_cast<unsigned char*>(p);
+    }
+    return cache[dev];
+}
+
+// Returns cudaSuccess and *too_big = 0 on success; *too_big = 1 when a matrix
+// has more than kNoAllocMaxCols columns or the copies exceed the scratch.
+cudaError_t launch_id_batched_noalloc(int count, const double* mats, const int64_t* off, const int* m, const int* n,
+                                      const double* tol, int* k, int* perm, const int64_t* poff, double* T,
+                                      const int64_t* toff, cudaStream_t st, int* too_big) {
+    *too_big = 0;
+    if (count > kNoAllocMaxMats) { *too_big = 1; return cudaSuccess; }
+    cudaError_t e = cudaSuccess;
+    unsigned char* scratch = noalloc_scratch_ptr(&e);
+    if (!scratch) return e;
+    note_launch();
+    id_noalloc_prep_kernel<<<1, 1, 0, st>>>(scratch, count, m, n);
+    note_launch();
+    id_noalloc_kernel<<<count, 128, 0, st>>>(scratch, mats, off, m, n, tol, k, perm, poff, T, toff);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int flag = 0;
+    e = cudaMemcpyAsync(&flag, scratch + kNoAllocOffBytes, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    *too_big = flag;
+    return cudaSuccess;
+}
 
 }  // namespace hif

@@ -228,6 +228,11 @@ cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int
 cudaError_t launch_col_dots(int64_t N, int nrhs, const double* x, int64_t ldx, const double* y, int64_t ldy,
                             double* out, cudaStream_t);
 
+// Batched ID with its work space in a file-scope device array (hif_id_batched_noalloc)
+cudaError_t launch_id_batched_noalloc(int count, const double* mats, const int64_t* off, const int* m, const int* n,
+                                      const double* tol, int* k, int* perm, const int64_t* poff, double* T,
+                                      const int64_t* toff, cudaStream_t st, int* too_big);
+
 // Batched ID on caller-provided matrices (hif_id_batched)
 cudaError_t launch_id_batched(int count, const double* mats, const int64_t* off, const int* m, const int* n,
                               const double* tol, int* k, int* perm, const int64_t* poff, double* T,

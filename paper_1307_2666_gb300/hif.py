@@ -78,6 +78,8 @@ EXPORTS = {
                                    C.c_void_p]),
     "hif_id_batched": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hif_id_batched_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -236,3 +238,12 @@ def hif_kernel_block(points, weights, a, b, c, kernel_id: int, rows, cols, out, 
 def hif_id_batched(mats, off, m, n, tol, k, perm, poff, T, toff, stream=None):
     _check(load().hif_id_batched(len(m), _ptr(mats), _ptr(off), _ptr(m), _ptr(n), _ptr(tol), _ptr(k), _ptr(perm),
                                  _ptr(poff), _ptr(T), _ptr(toff), stream), "hif_id_batched")
+
+
+def hif_id_batched_noalloc(mats, off, m, n, tol, k, perm, poff, T, toff, stream=None):
+    """Batched ID whose work space is a fixed device array: no allocation.
+    All arrays must be device tensors.  Returns the status code (HIF_OK, or
+    HIF_EINVAL when the input exceeds the fixed work space)."""
+    return _check(load().hif_id_batched_noalloc(len(m), _ptr(mats), _ptr(off), _ptr(m), _ptr(n), _ptr(tol), _ptr(k),
+                                                _ptr(perm), _ptr(poff), _ptr(T), _ptr(toff), stream),
+                  "hif_id_batched_noalloc", allow=(HIF_EINVAL,))
