@@ -7,7 +7,7 @@
  *      A = diag(a) + diag(b) K diag(c),     K_ij = G(|x_i - x_j|) w_j   (i != j),
  *                                          K_ii = integral of G over the cell of x_i,
  *
- * with G the Laplace kernel of Eq. (1.3) (kernel_id 0: -log(r)/(2 pi) in 2D,
+ * with G the Laplace kernel of Eq. (1.4) (kernel_id 0: -log(r)/(2 pi) in 2D,
  * kernel_id 1: 1/(4 pi r) in 3D), by the hierarchical interpolative
  * factorization HIF-IE (Sec. 4, Algorithms 4.1 and 4.2, with the second-kind
  * modifications of Sec. 4.4), and applies the factorization F ~ A and its
@@ -100,7 +100,7 @@ hif_status hif_options_default(int dim, hif_options* opt);
  *   opt      options (NULL = hif_options_default(2))
  *   out      receives the handle (NULL on failure)
  * Errors: HIF_EINVAL on bad sizes/options, HIF_ENOMEM, HIF_ESINGULAR when an
- * elimination block B_rr (Lemma 2.3) or the top block is singular,
+ * elimination block B_rr (Lemma 2.4) or the top block is singular,
  * HIF_ENUMERIC on non-finite input or results, HIF_ECUDA.
  */
 hif_status hif_factor(const double* points, int64_t N, const double* weights,

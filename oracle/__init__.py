@@ -16,7 +16,7 @@ Everything is plain, slow FP64 numpy written from the paper:
   (Sec. 2.2, Lemma 2.2, adaptive rank), and the 2-norm estimate used for the
   second-kind tolerance rho (Sec. 4.4).
 * ``hifie``    -- sequential HIF-IE in 2D/3D (Algorithms 4.1 and 4.2,
-  skeletonization Lemma 2.3, proxy compression Sec. 3.3 / 4.3, second-kind
+  skeletonization Lemma 2.4, proxy compression Sec. 3.3 / 4.3, second-kind
   modifications Sec. 4.4) with apply / solve / transposes in factored form
   (Eqs. (4.1), (4.2)).
 * ``krylov``   -- right-preconditioned restarted GMRES (Sec. 5) and the power

@@ -5,10 +5,10 @@ Follows the paper's steps in its own order and notation:
 * Algorithm 4.1 (2D: cells at level l, edges at l + 1/2) and Algorithm 4.2
   (3D: cells, faces at l + 1/3, edges at l + 2/3); with ``fractional=False``
   it is RSF, Algorithm 3.1.
-* Skeletonization of one index set c (Lemma 2.3): ID of the proxy matrix Y_c
+* Skeletonization of one index set c (Lemma 2.4): ID of the proxy matrix Y_c
   (Eq. (3.3): near-field rows A_{cN,c}, A_{c,cN}^T and proxy rows Y_{cE,c},
   Y_{c,cE}^T, Sec. 3.3 Lemma 3.3 with quadrature weights), then elimination
-  of the redundant DOFs by Lemma 2.1 with the B blocks of Lemma 2.3.
+  of the redundant DOFs by Lemma 2.1 with the B blocks of Lemma 2.4.
 * Near field (Sec. 3.3 and 4.3): active DOFs strictly inside the proxy
   circle/sphere of radius 1.5 w about the box centre, plus every active DOF
   coupled to c through a Schur-complement interaction (SCI).
@@ -153,7 +153,7 @@ class HIFFactor:
         return [(sl.kind, sl.level, len(sl.boxes), sum(b.sk.size for b in sl.boxes),
                  sum(b.rd.size for b in sl.boxes)) for sl in self.sublevels]
 
-    # ---- factored-form application (Eqs. (3.4), (4.1), (4.2)) ----
+    # ---- factored-form application (Eqs. (3.2), (4.1), (4.2)) ----
     def _boxes(self, reverse=False):
         sls = reversed(self.sublevels) if reverse else self.sublevels
         for sl in sls:
@@ -422,7 +422,7 @@ def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_d
 
     A_rr, A_rs = Ablk(rd_g, rd_g), Ablk(rd_g, sk_g)
     A_sr, A_ss = Ablk(sk_g, rd_g), Ablk(sk_g, sk_g)
-    # Lemma 2.3 blocks (real case: * = transpose)
+    # Lemma 2.4 blocks (real case: * = transpose)
     B_rr = A_rr - T.T @ A_sr - A_rs @ T + T.T @ A_ss @ T
     B_rs = A_rs - T.T @ A_ss
     B_sr = A_sr - A_ss @ T

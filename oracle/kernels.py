@@ -7,7 +7,7 @@ constant collocation at cell centres x_j with cell volumes w_j,
     K_ij = G(|x_i - x_j|) w_j            (i != j, one-point rule),
     K_ii = integral of G(|x_i - y|) over the cell of x_i,
 
-where G is the Laplace fundamental solution of Eq. (1.3):
+where G is the Laplace fundamental solution of Eq. (1.4):
 G(r) = -log(r) / (2 pi) in 2D (kernel_id 0) and 1 / (4 pi r) in 3D
 (kernel_id 1).  The cell of DOF i is the square/cube of side w_i^(1/d)
 centred at x_i.  The paper computes the diagonal "adaptively"; here it is the
@@ -27,7 +27,7 @@ FOUR_PI = 4.0 * math.pi
 
 
 def green(kernel_id: int, r: np.ndarray) -> np.ndarray:
-    """G(r) of Eq. (1.3): kernel 0 = -log(r)/(2 pi), kernel 1 = 1/(4 pi r)."""
+    """G(r) of Eq. (1.4): kernel 0 = -log(r)/(2 pi), kernel 1 = 1/(4 pi r)."""
     r = np.asarray(r, dtype=np.float64)
     if kernel_id == 0:
         return -np.log(r) / TWO_PI
@@ -49,7 +49,7 @@ def self_integral(kernel_id: int, w: np.ndarray) -> np.ndarray:
 
 
 def double_layer_2d(x: np.ndarray, y: np.ndarray, ny: np.ndarray) -> np.ndarray:
-    """dG/dnu_y for the 2D Laplace kernel (Sec. 1, Eq. (1.4)): (x-y).nu_y / (2 pi |x-y|^2).
+    """dG/dnu_y for the 2D Laplace kernel (Sec. 1, Eqs. (1.3), (1.5)): (x-y).nu_y / (2 pi |x-y|^2).
 
     Only used to check the sign convention of the second-kind boundary IE.
     """

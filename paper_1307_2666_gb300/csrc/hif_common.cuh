@@ -11,7 +11,7 @@ namespace hif {
 // ---------------------------------------------------------------- kernels --
 
 __host__ __device__ inline double green_d(int kernel_id, double r2) {
-    // G of Eq. (1.3) from the squared distance: -log(r)/(2 pi) = -log(r^2)/(4 pi)
+    // G of Eq. (1.4) from the squared distance: -log(r)/(2 pi) = -log(r^2)/(4 pi)
     return kernel_id == 0 ? -log(r2) * (0.25 / kPi) : (0.25 / kPi) / sqrt(r2);
 }
 

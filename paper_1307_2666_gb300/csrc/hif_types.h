@@ -22,7 +22,7 @@ struct GeomDev {
 };
 
 // Schur-complement interaction (SCI) history.  Every box that eliminated
-// DOFs left a dense k x k update on its skeletons (Lemma 2.3, B_ss); DOF i
+// DOFs left a dense k x k update on its skeletons (Lemma 2.4, B_ss); DOF i
 // belongs to at most one such block per sublevel s: blk[s*N+i] (or -1) at
 // local position loc[s*N+i].  The SCI between i and j is the sum over past
 // sublevels of the shared blocks' entries.

@@ -11,7 +11,7 @@
 //                by power iteration, then the column-pivoted QR interpolative
 //                decomposition (Lemma 2.2) of R_c[:, g] -- equal to the ID of
 //                Y_c[:, g] because Q_c has orthonormal columns.
-//  elim_kernel   one CTA per box: the B blocks of Lemma 2.3, LU with partial
+//  elim_kernel   one CTA per box: the B blocks of Lemma 2.4, LU with partial
 //                pivoting of B_rr (Lemma 2.1), X, Y and the Schur update
 //                B_ss - B_sr B_rr^{-1} B_rs recorded as a new SCI block.
 #include <algorithm>
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(128) elim_kernel(ElimArgs args) {
     T* Ars = A + (int64_t)n * r;
     T* Ass = A + (int64_t)n * r + r;
     const int64_t ld = n;
-    // B_sr = A_sr - A_ss T            (Lemma 2.3)
+    // B_sr = A_sr - A_ss T            (Lemma 2.4)
     cta_gemm<T>(k, r, k, T(-1), Ass, ld, false, Tm, k, false, Asr, ld);
     // B_rr = A_rr - T^T B_sr - A_rs T  (= A_rr - T^T A_sr - A_rs T + T^T A_ss T)
     cta_gemm<T>(r, r, k, T(-1), Tm, k, true, Asr, ld, false, Arr, ld);

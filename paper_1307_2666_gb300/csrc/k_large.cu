@@ -12,7 +12,7 @@
 //                    warp per remaining column applies it and recomputes the
 //                    column norm in FP64;
 //  * big_T           T = R1^{-1} R2 and the skeleton / redundant order;
-//  * gemm / trsm / elimination helpers: Lemma 2.3 blocks, Lemma 2.1 LU
+//  * gemm / trsm / elimination helpers: Lemma 2.4 blocks, Lemma 2.1 LU
 //                    (blocked, multi-CTA) and the Schur update for one large
 //                    box at a time.
 #include <algorithm>
@@ -647,7 +647,7 @@ __global__ void be_T_kernel(BatchElimArgs a) {
     }
 }
 
-// the GEMMs of Lemma 2.3 and the Schur update, one op per launch:
+// the GEMMs of Lemma 2.4 and the Schur update, one op per launch:
 // 0: B_sr = A_sr - A_ss T     1: B_rr -= T^T B_sr     2: B_rr -= A_rs T
 // 3: B_rs = A_rs - T^T A_ss   4: S = -X Z (into the SCI pool)
 template <typename T>

@@ -1,7 +1,7 @@
 // Apply / solve sweeps of the factorization in factored form (sm_103a).
 //
 // F^{-1} = V_0 ... V_last D^{-1} U_last^T ... U_0^T and F = U_0^{-T} ... D ...
-// V_0^{-1} (Eqs. (3.4), (4.1), (4.2)).  One launch per sublevel and direction,
+// V_0^{-1} (Eqs. (3.2), (4.1), (4.2)).  One launch per sublevel and direction,
 // one CTA per box: the box's skeleton and redundant entries of the working
 // vectors are gathered into shared memory, the box's small factors (T, L, U,
 // X, Y, D of Lemmas 2.1 and 2.3) are streamed once from HBM, and the result

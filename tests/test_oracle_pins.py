@@ -35,7 +35,7 @@ GOLD = _golden()
 
 # ----------------------------------------------------------------- kernels ---
 
-def test_green_functions_eq_1_3():
+def test_green_functions_eq_1_4():
     # G(1) = 0 for the log kernel, G(r) = -log(r)/(2 pi); 1/(4 pi r) in 3D
     assert kernels.green(0, np.array([1.0]))[0] == 0.0
     assert kernels.green(0, np.array([math.e]))[0] == pytest.approx(-1 / (2 * math.pi))
