@@ -107,6 +107,32 @@ hif_status hif_factor(const double* points, int64_t N, const double* weights,
                       const double* a, const double* b, const double* c,
                       int kernel_id, double eps, const hif_options* opt, hif_handle* out);
 
+/*
+ * One problem of a batch: the arrays of hif_factor for one integral equation.
+ */
+typedef struct {
+    const double* points;   /* N x dim, row-major */
+    int64_t N;
+    const double* weights;
+    const double* a;
+    const double* b;
+    const double* c;
+} hif_problem;
+
+/*
+ * hif_factor_batched -- HIF-IE of `count` independent problems in one handle.
+ * Every problem gets its own tree; the boxes of the same sublevel (counted
+ * from the leaves) of all problems are skeletonized in the same kernel
+ * launches (Sec. 3.1: boxes of one level are independent).  The handle's
+ * operator is block diagonal: vectors are the concatenation of the problems'
+ * vectors in the order given (problem q at rows off_q .. off_q + N_q - 1,
+ * off_q = N_0 + ... + N_{q-1}), and every call below acts on all problems at
+ * once.  hif_solve_refined with method 0 judges the residual problem by
+ * problem and column by column.  Options and errors as for hif_factor.
+ */
+hif_status hif_factor_batched(int count, const hif_problem* problems, int kernel_id, double eps,
+                              const hif_options* opt, hif_handle* out);
+
 /* y = F x  (Eq. (4.1) first line; generalized FMM).  x, y: N x nrhs, ld >= N. */
 hif_status hif_apply(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld);
 /* y = F^T x. */

@@ -41,7 +41,7 @@ class Factorization:
                  second_kind: bool = True, occupancy: int = 64, proxy_dirs=None, fractional: bool = True,
                  skip_levels: int = 0, proxy_radius: float = 1.5, fp32_tol_floor: float | None = None,
                  root=None, stream=None, direct: str = "df64"):
-        dim = points.shape[1]
+        dim = (points[0][0] if isinstance(points, (list, tuple)) else points).shape[1]
         opt = _h.hif_options_default(dim)
         opt.leaf_occupancy = int(occupancy)
         opt.second_kind = 1 if second_kind else 0
@@ -66,13 +66,29 @@ class Factorization:
             opt.root_width = float(width)
         if stream is not None:
             opt.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-        self.N, self.dim = points.shape
         self.kernel_id = kernel_id
         self.eps = eps
-        self.device = points.device if hasattr(points, "device") else torch.device("cpu")
         self.a, self.b, self.c = a, b, c
+        if isinstance(points, (list, tuple)):
+            # a batch of independent problems: points = [(points, weights, a, b, c), ...]
+            probs = [tuple(t.contiguous() for t in pr) for pr in points]
+            self._keep.append(probs)
+            self.offsets = np.cumsum([0] + [pr[0].shape[0] for pr in probs])
+            self.N, self.dim = int(self.offsets[-1]), probs[0][0].shape[1]
+            self.device = probs[0][0].device
+            self.h = _h.hif_factor_batched(probs, kernel_id, eps, opt)
+            return
+        self.N, self.dim = points.shape
+        self.offsets = np.array([0, self.N])
+        self.device = points.device if hasattr(points, "device") else torch.device("cpu")
         self.h = _h.hif_factor(points.contiguous(), weights.contiguous(), a.contiguous(), b.contiguous(),
                                c.contiguous(), kernel_id, eps, opt)
+
+    @classmethod
+    def batched(cls, problems, kernel_id: int, eps: float, **kw):
+        """One handle over independent problems [(points, weights, a, b, c), ...];
+        vectors are their concatenation (see ``offsets``)."""
+        return cls(list(problems), None, None, None, None, kernel_id, eps, **kw)
 
     # -- factored operators ------------------------------------------------
     def _op(self, fn, x):
@@ -145,9 +161,11 @@ class HIFSolve(torch.autograd.Function):
     def backward(ctx, g):
         u, a, b, c = ctx.saved_tensors
         fac = ctx.fac
-        lam, _, _ = fac.solve_refined(g.contiguous(), trans=True, tol=ctx.tol)
+        lam, _, _ = fac.solve_refined(g, trans=True, tol=ctx.tol)
         Fu = fac.apply(u)
         Ftl = fac.apply_transpose(lam)
-        Kcu = (Fu - a * u) / b
-        Ktbl = (Ftl - a * lam) / c
-        return lam, -lam * u, -lam * Kcu, -u * Ktbl, None, None
+        col = (lambda v: v[:, None]) if u.ndim == 2 else (lambda v: v)
+        Kcu = (Fu - col(a) * u) / col(b)
+        Ktbl = (Ftl - col(a) * lam) / col(c)
+        red = (lambda v: v.sum(dim=1)) if u.ndim == 2 else (lambda v: v)
+        return lam, red(-lam * u), red(-lam * Kcu), red(-u * Ktbl), None, None

@@ -107,6 +107,24 @@ struct InArr {
     }
 };
 
+// One independent problem of a handle: DOFs [off, off + N) of the
+// concatenated arrays, with its own tree and direct-sum structure.
+struct Segment {
+    int64_t off = 0, N = 0;
+    Tree tree{};
+    std::vector<int> kinds, levels;
+    bool grid = false;
+    int gn = 0;
+    double gh = 0;
+    DevMem dof_of, table, table_df;
+};
+
+struct FactorScratch {
+    DevMem d_ed, d_ed_big, d_eg, ews, piv;
+};
+
+constexpr int KIND_TOP = 3;   // the top blocks, eliminated as boxes without skeletons
+
 struct SubFactor {
     int kind = 0, level = 0;
     int nbox = 0;                  // boxes with r > 0
@@ -126,7 +144,8 @@ struct hif_handle_s {
     int elem = 8;
     hif::DevMem x, w, a, b, c, kself, proxy;
     std::vector<double> hx, hw;
-    hif::Tree tree{};
+    std::vector<std::unique_ptr<hif::Segment>> segs;
+    hif::DevMem seg_off, seg_n;
     int P = 0;
     // SCI store
     hif::DevMem sci_blk, sci_loc, blk_ptr, blk_k;
@@ -135,15 +154,10 @@ struct hif_handle_s {
     std::vector<std::unique_ptr<hif::DevMem>> sci_pools;
     // factors
     std::vector<std::unique_ptr<hif::SubFactor>> subs;
-    int nL = 0;
-    hif::DevMem top_ids, topA, topLU, top_piv, topInv;
-    // uniform grid for the direct sum
-    bool grid = false;
-    int gn = 0;
-    double gh = 0;
-    hif::DevMem dof_of, table, table_df, vbuf, ybuf, vdf;
+    // direct-sum scratch
+    hif::DevMem vbuf, ybuf, vdf;
     // work buffers
-    hif::DevMem work, work2, tmp, status;
+    hif::DevMem work, work2, tmp, status, sweep_ws, sweep_off;
     hif_stats_t stats{};
 };
 
@@ -182,49 +196,51 @@ static void check_status(hif_handle h) {
     if (st & DEV_NONFINITE) fail(HIF_ENUMERIC, "non-finite value in the factorization");
 }
 
-// Detect a full uniform tensor grid: x = lo + h (idx + 1/2), equal weights h^d.
-static void detect_grid(hif_handle h) {
-    h->grid = false;
+// Detect whether a problem is a full uniform tensor grid: x = lo + h (idx + 1/2)
+// with equal weights h^d.  Then K_ij = G(h |idx_i - idx_j|) w exactly and the
+// direct sum is a convolution.
+static void detect_grid(hif_handle h, Segment& sg) {
+    sg.grid = false;
     const int d = h->dim;
-    const int64_t N = h->N;
+    const int64_t N = sg.N;
+    const double* X = h->hx.data() + (size_t)d * sg.off;
+    const double* Wt = h->hw.data() + sg.off;
     const int n = (int)std::llround(std::pow((double)N, 1.0 / d));
     int64_t nn = 1;
     for (int k = 0; k < d; ++k) nn *= n;
     if (n < 2 || nn != N) return;
     double lo[3], hx = 0;
     for (int k = 0; k < d; ++k) {
-        double mn = h->hx[k], mx = h->hx[k];
+        double mn = X[k], mx = X[k];
         for (int64_t i = 0; i < N; ++i) {
-            mn = std::min(mn, h->hx[d * i + k]);
-            mx = std::max(mx, h->hx[d * i + k]);
+            mn = std::min(mn, X[d * i + k]);
+            mx = std::max(mx, X[d * i + k]);
         }
         const double hk = (mx - mn) / (n - 1);
         if (k == 0) hx = hk;
         if (std::fabs(hk - hx) > 1e-12 * hx) return;
         lo[k] = mn;
     }
-    const double wv = h->hw[0];
+    const double wv = Wt[0];
     for (int64_t i = 0; i < N; ++i)
-        if (h->hw[i] != wv) return;
+        if (Wt[i] != wv) return;
     if (std::fabs(std::pow(wv, 1.0 / d) - hx) > 1e-9 * hx) return;
     std::vector<int> dof_of(N, -1);
     for (int64_t i = 0; i < N; ++i) {
         int64_t gpos = 0;
         for (int k = 0; k < d; ++k) {
-            const double t = (h->hx[d * i + k] - lo[k]) / hx;
+            const double t = (X[d * i + k] - lo[k]) / hx;
             const int64_t id = std::llround(t);
             if (id < 0 || id >= n || std::fabs(t - id) > 1e-6) return;
             gpos = gpos * n + id;
         }
         if (dof_of[gpos] != -1) return;
-        dof_of[gpos] = (int)i;
+        dof_of[gpos] = (int)(sg.off + i);
     }
-    // the one-point rule gives K_ij = G(h |i - j|) w exactly when the
-    // coordinates are exactly lo + h idx; require that to within rounding
-    h->grid = true;
-    h->gn = n;
-    h->gh = hx;
-    upload(h->dof_of, dof_of, h->st);
+    sg.grid = true;
+    sg.gn = n;
+    sg.gh = hx;
+    upload(sg.dof_of, dof_of, h->st);
 }
 
 static int env_int(const char* name, int dflt) {
@@ -337,23 +353,135 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
 }
 
 template <typename T>
+static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc>& ed,
+                         const std::vector<ElimDesc>& ed_big, const std::vector<ElimGroup>& eg,
+                         const std::vector<int>& skv, const std::vector<int>& rdv, int64_t fac_off, int64_t piv_off,
+                         int64_t ws_off, void* sci_pool, int nsub_sci, DevMem& Tws, FactorScratch& S) {
+    const cudaStream_t st = h->st;
+    upload(S.d_ed, ed, st);
+    upload(S.d_eg, eg, st);
+    upload(sf.sk, skv, st);
+    upload(sf.rd, rdv, st);
+    S.ews.ensure(sizeof(T) * std::max<int64_t>(ws_off, 1));
+    sf.pool.ensure(sizeof(T) * std::max<int64_t>(fac_off, 1));
+    sf.perm.ensure(sizeof(int) * std::max<int64_t>(piv_off, 1));
+    S.piv.ensure(sizeof(int) * std::max<int64_t>(piv_off, 1));
+    upload(sf.boxes, sf.hbox, st);
+    Tws.ensure(sizeof(T));
+    ElimArgs ea{};
+    ea.g = geom(h);
+    ea.sci = scidev(h, nsub_sci);
+    ea.boxes = S.d_ed.as<ElimDesc>();
+    ea.groups = S.d_eg.as<ElimGroup>();
+    ea.sk_ids = sf.sk.as<int>();
+    ea.rd_ids = sf.rd.as<int>();
+    ea.Tws = Tws.p;
+    ea.ws = S.ews.p;
+    ea.fac_pool = sf.pool.p;
+    ea.piv_pool = S.piv.as<int>();
+    ea.perm_pool = sf.perm.as<int>();
+    ea.sci_pool = sci_pool;
+    ea.status = h->status.as<int>();
+    HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), st)));
+    if (!ed_big.empty()) {
+        upload(S.d_ed_big, ed_big, st);
+        int mxn = 0, mxk = 0, mxr = 0;
+        for (const ElimDesc& eb : ed_big) {
+            mxn = std::max(mxn, eb.k + eb.r);
+            mxk = std::max(mxk, eb.k);
+            mxr = std::max(mxr, eb.r);
+        }
+        BatchElimArgs ba{};
+        ba.g = ea.g;
+        ba.sci = ea.sci;
+        ba.ed = S.d_ed_big.as<ElimDesc>();
+        ba.nbox = (int)ed_big.size();
+        ba.groups = S.d_eg.as<ElimGroup>();
+        ba.sk = sf.sk.as<int>();
+        ba.rd = sf.rd.as<int>();
+        ba.Tws = Tws.p;
+        ba.ws = S.ews.p;
+        ba.pool = sf.pool.p;
+        ba.piv = S.piv.as<int>();
+        ba.perm = sf.perm.as<int>();
+        ba.sci_pool = sci_pool;
+        ba.status = h->status.as<int>();
+        HIF_CUDA((big_elim_batch<T>(ba, mxn, mxk, mxr, st)));
+    }
+    h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
+}
+
+// Factor offsets of one eliminated box inside its sublevel's pools.
+static void place_box(ElimDesc& e, BoxFac& bf, int k, int r, int64_t& fac_off, int64_t& piv_off, int64_t& ws_off) {
+    const int n = k + r;
+    e.k = k;
+    e.r = r;
+    e.ws_off = ws_off;
+    ws_off += (int64_t)n * n + (int64_t)k * r;
+    e.T_out = fac_off; fac_off += (int64_t)k * r;
+    e.LU_out = fac_off; fac_off += (int64_t)r * r;
+    e.LUi_out = fac_off; fac_off += (int64_t)r * r;
+    e.D_out = fac_off; fac_off += r;
+    e.X_out = fac_off; fac_off += (int64_t)k * r;
+    e.Y_out = fac_off; fac_off += (int64_t)r * k;
+    e.piv_out = piv_off; piv_off += r;
+    bf.k = k;
+    bf.r = r;
+    bf.sk_off = e.sk_off;
+    bf.rd_off = e.rd_off;
+    bf.T_off = e.T_out;
+    bf.LU_off = e.LU_out;
+    bf.LUi_off = e.LUi_out;
+    bf.D_off = e.D_out;
+    bf.X_off = e.X_out;
+    bf.Y_off = e.Y_out;
+    bf.piv_off = e.piv_out;
+}
+
+static void append_plan(SublevelPlan& p, const SublevelPlan& q) {
+    const int64_t mo = (int64_t)p.members.size(), no = (int64_t)p.near.size(), go = p.grp_off.back();
+    for (int b = 1; b <= q.nbox; ++b) {
+        p.box_off.push_back(q.box_off[b] + mo);
+        p.near_off.push_back(q.near_off[b] + no);
+        p.grp_off.push_back(q.grp_off[b] + go);
+    }
+    p.members.insert(p.members.end(), q.members.begin(), q.members.end());
+    p.cols.insert(p.cols.end(), q.cols.begin(), q.cols.end());
+    p.near.insert(p.near.end(), q.near.begin(), q.near.end());
+    p.centers.insert(p.centers.end(), q.centers.begin(), q.centers.end());
+    p.grp_col0.insert(p.grp_col0.end(), q.grp_col0.begin(), q.grp_col0.end());
+    p.grp_n.insert(p.grp_n.end(), q.grp_n.begin(), q.grp_n.end());
+    p.grp_sci.insert(p.grp_sci.end(), q.grp_sci.begin(), q.grp_sci.end());
+    p.box_sci.insert(p.box_sci.end(), q.box_sci.begin(), q.box_sci.end());
+    p.nbox += q.nbox;
+}
+
+template <typename T>
 static void run_factor(hif_handle h) {
     const cudaStream_t st = h->st;
     const int d = h->dim;
     const int64_t N = h->N;
     const GeomDev g = geom(h);
-    Tree& t = h->tree;
-    t.dim = d;
-    if (h->opt.root_width > 0) {
-        for (int k = 0; k < 3; ++k) t.lo[k] = h->opt.root_lo[k];
-        t.W = h->opt.root_width;
-    } else {
-        root_box(h->hx.data(), h->hw.data(), N, d, t.lo, &t.W);
+    size_t nsub = 0;
+    int maxL = 0;
+    for (auto& sp : h->segs) {
+        Segment& sg = *sp;
+        Tree& t = sg.tree;
+        t.dim = d;
+        const double* xs = h->hx.data() + (size_t)d * sg.off;
+        const double* wsg = h->hw.data() + sg.off;
+        if (h->opt.root_width > 0) {
+            for (int k = 0; k < 3; ++k) t.lo[k] = h->opt.root_lo[k];
+            t.W = h->opt.root_width;
+        } else {
+            root_box(xs, wsg, sg.N, d, t.lo, &t.W);
+        }
+        t.L = num_levels(xs, sg.N, d, t.lo, t.W, h->opt.leaf_occupancy);
+        plan_sublevels(d, t.L, h->opt.fractional_levels != 0, h->opt.skip_levels, sg.kinds, sg.levels);
+        nsub = std::max(nsub, sg.kinds.size());
+        maxL = std::max(maxL, t.L);
     }
-    t.L = num_levels(h->hx.data(), N, d, t.lo, t.W, h->opt.leaf_occupancy);
-    std::vector<int> kinds, levels;
-    plan_sublevels(d, t.L, h->opt.fractional_levels != 0, h->opt.skip_levels, kinds, levels);
-    if ((int)kinds.size() > kMaxSub) fail(HIF_EINVAL, "too many sublevels");
+    if ((int)nsub + 1 > kMaxSub) fail(HIF_EINVAL, "too many sublevels");
 
     h->sci_blk.ensure(sizeof(int) * (size_t)kMaxSub * N);
     h->sci_loc.ensure(sizeof(int) * (size_t)kMaxSub * N);
@@ -366,7 +494,8 @@ static void run_factor(hif_handle h) {
     std::vector<char> active(N, 1);
     std::vector<int> box_of(N, -1);
     DevMem d_boxes, d_groups, d_cols, d_near, Rws, GKws, GSws, Tws, Wws, Woff, perm_out, k_out;
-    DevMem d_ed, d_ed_big, d_eg, d_sk, d_rd, ews, piv_scratch, d_small_boxes, d_small_groups;
+    DevMem d_small_boxes, d_small_groups;
+    FactorScratch S;
     BigBuffers big;
     const int big_id_n = env_int("HIF_BIG_ID", sizeof(T) == 8 ? 128 : 256);
     const int big_elim_n = env_int("HIF_BIG_ELIM", 600);
@@ -374,19 +503,35 @@ static void run_factor(hif_handle h) {
     double flops = 0, evals = 0;
     const double tol_floor = sizeof(T) == 4 ? h->opt.fp32_tol_floor : 0.0;
 
-    for (size_t tau = 0; tau < kinds.size(); ++tau) {
-        const int kind = kinds[tau], ell = levels[tau];
-        const int s = 1 << (t.L - ell);
-        const double wl = t.W / s;
-        std::vector<int> act_ids;
-        act_ids.reserve(N);
-        for (int64_t i = 0; i < N; ++i)
-            if (active[i]) act_ids.push_back((int)i);
-        for (int i : act_ids) box_of[i] = -1;
+    for (size_t tau = 0; tau < nsub; ++tau) {
         const auto tr0 = std::chrono::steady_clock::now();
+        // ---- index sets of this sublevel, problem by problem, merged
         SublevelPlan p;
-        partition(t, h->hx.data(), kind, s, act_ids, p, box_of);
-        build_near_groups(t, h->hx.data(), s, h->opt.proxy_radius, h->second_kind, act_ids, active, box_of, sci, p);
+        p.nbox = 0;
+        p.box_off.assign(1, 0);
+        p.near_off.assign(1, 0);
+        p.grp_off.assign(1, 0);
+        std::vector<double> radius;
+        int kind = -1, ell = -1;
+        for (auto& sp : h->segs) {
+            Segment& sg = *sp;
+            if (tau >= sg.kinds.size()) continue;
+            const int kd = sg.kinds[tau], lv = sg.levels[tau];
+            if (kind < 0) { kind = kd; ell = lv; }
+            const int s = 1 << (sg.tree.L - lv);
+            const double wl = sg.tree.W / s;
+            std::vector<int> act_ids;
+            act_ids.reserve(sg.N);
+            for (int64_t i = sg.off; i < sg.off + sg.N; ++i)
+                if (active[i]) act_ids.push_back((int)i);
+            for (int i : act_ids) box_of[i] = -1;
+            SublevelPlan ps;
+            partition(sg.tree, h->hx.data(), kd, s, act_ids, ps, box_of);
+            build_near_groups(sg.tree, h->hx.data(), s, h->opt.proxy_radius, h->second_kind, act_ids, active, box_of,
+                              sci, ps);
+            append_plan(p, ps);
+            radius.insert(radius.end(), ps.nbox, h->opt.proxy_radius * wl);
+        }
         const int nb = p.nbox;
         const int64_t ngr = p.grp_off[nb];
 
@@ -400,7 +545,7 @@ static void run_factor(hif_handle h) {
         std::vector<int> small_boxes, small_groups, big_boxes;
         for (int bI = 0; bI < nb; ++bI) {
             BoxDesc& b = bd[bI];
-            const bool big = (p.box_off[bI + 1] - p.box_off[bI]) > big_id_n;
+            const bool isbig = (p.box_off[bI + 1] - p.box_off[bI]) > big_id_n;
             b.n = (int)(p.box_off[bI + 1] - p.box_off[bI]);
             b.m_near = (int)(p.near_off[bI + 1] - p.near_off[bI]);
             b.ngroups = (int)(p.grp_off[bI + 1] - p.grp_off[bI]);
@@ -409,10 +554,10 @@ static void run_factor(hif_handle h) {
             b.near_off = p.near_off[bI];
             b.grp_off = p.grp_off[bI];
             b.R_off = Roff;
-            if (!big) Roff += (int64_t)b.n * b.n;
+            if (!isbig) Roff += (int64_t)b.n * b.n;
             for (int k = 0; k < 3; ++k) b.ctr[k] = p.centers[3 * bI + k];
-            b.radius = h->opt.proxy_radius * wl;
-            if (big) big_boxes.push_back(bI);
+            b.radius = radius[bI];
+            if (isbig) big_boxes.push_back(bI);
             else {
                 small_boxes.push_back(bI);
                 maxn = std::max(maxn, b.n);
@@ -433,7 +578,7 @@ static void run_factor(hif_handle h) {
                 G.perm_off = b.col_off + G.col0;
                 const int mrow = G.col0 + G.n;
                 woff[gi] = Woffs;
-                if (!big) {
+                if (!isbig) {
                     small_groups.push_back((int)gi);
                     Woffs += (int64_t)(mrow | 1) * G.n;
                     maxng = std::max(maxng, G.n);
@@ -541,8 +686,6 @@ static void run_factor(hif_handle h) {
             rsum += r;
             if (r == 0) continue;
             ElimDesc e{};
-            e.k = k;
-            e.r = r;
             e.ngroups = b.ngroups;
             e.sk_off = (int64_t)skv.size();
             e.rd_off = (int64_t)rdv.size();
@@ -567,16 +710,8 @@ static void run_factor(hif_handle h) {
                 const int kq = kg[b.grp_off + q];
                 for (int l = kq; l < G.n; ++l) rdv.push_back(p.cols[b.col_off + G.col0 + permh[G.perm_off + l]]);
             }
-            const int n = k + r;
-            e.ws_off = ws_off;
-            ws_off += (int64_t)n * n + (int64_t)k * r;
-            e.T_out = fac_off; fac_off += (int64_t)k * r;
-            e.LU_out = fac_off; fac_off += (int64_t)r * r;
-            e.LUi_out = fac_off; fac_off += (int64_t)r * r;
-            e.D_out = fac_off; fac_off += r;
-            e.X_out = fac_off; fac_off += (int64_t)k * r;
-            e.Y_out = fac_off; fac_off += (int64_t)r * k;
-            e.piv_out = piv_off; piv_off += r;
+            BoxFac bf{};
+            place_box(e, bf, k, r, fac_off, piv_off, ws_off);
             if (k > 0) {
                 e.sci_out = sci_off;
                 nblk.push_back({bI, e.sk_off, k, sci_off});
@@ -584,18 +719,6 @@ static void run_factor(hif_handle h) {
             } else {
                 e.sci_out = -1;
             }
-            BoxFac bf{};
-            bf.k = k;
-            bf.r = r;
-            bf.sk_off = e.sk_off;
-            bf.rd_off = e.rd_off;
-            bf.T_off = e.T_out;
-            bf.LU_off = e.LU_out;
-            bf.LUi_off = e.LUi_out;
-            bf.D_off = e.D_out;
-            bf.X_off = e.X_out;
-            bf.Y_off = e.Y_out;
-            bf.piv_off = e.piv_out;
             sf->hbox.push_back(bf);
             sf->max_kr2 = std::max(sf->max_kr2, k + 2 * r);
             if (k + r > big_elim_n) ed_big.push_back(e);
@@ -619,58 +742,8 @@ static void run_factor(hif_handle h) {
             h->blk_ptr_h.push_back(static_cast<char*>(pool->p) + sizeof(T) * nbk.sci_off);
             h->blk_k_h.push_back(nbk.k);
         }
-        if (sf->nbox) {
-            upload(d_ed, ed, st);
-            upload(d_eg, eg, st);
-            upload(sf->sk, skv, st);
-            upload(sf->rd, rdv, st);
-            ews.ensure(sizeof(T) * std::max<int64_t>(ws_off, 1));
-            sf->pool.ensure(sizeof(T) * std::max<int64_t>(fac_off, 1));
-            sf->perm.ensure(sizeof(int) * std::max<int64_t>(piv_off, 1));
-            piv_scratch.ensure(sizeof(int) * std::max<int64_t>(piv_off, 1));
-            upload(sf->boxes, sf->hbox, st);
-            ElimArgs ea{};
-            ea.g = g;
-            ea.sci = scidev(h, (int)tau);
-            ea.boxes = d_ed.as<ElimDesc>();
-            ea.groups = d_eg.as<ElimGroup>();
-            ea.sk_ids = sf->sk.as<int>();
-            ea.rd_ids = sf->rd.as<int>();
-            ea.Tws = Tws.p;
-            ea.ws = ews.p;
-            ea.fac_pool = sf->pool.p;
-            ea.piv_pool = piv_scratch.as<int>();
-            ea.perm_pool = sf->perm.as<int>();
-            ea.sci_pool = pool->p;
-            ea.status = h->status.as<int>();
-            HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), st)));
-            if (!ed_big.empty()) {
-                upload(d_ed_big, ed_big, st);
-                int mxn = 0, mxk = 0, mxr = 0;
-                for (const ElimDesc& eb : ed_big) {
-                    mxn = std::max(mxn, eb.k + eb.r);
-                    mxk = std::max(mxk, eb.k);
-                    mxr = std::max(mxr, eb.r);
-                }
-                BatchElimArgs ba{};
-                ba.g = g;
-                ba.sci = ea.sci;
-                ba.ed = d_ed_big.as<ElimDesc>();
-                ba.nbox = (int)ed_big.size();
-                ba.groups = d_eg.as<ElimGroup>();
-                ba.sk = sf->sk.as<int>();
-                ba.rd = sf->rd.as<int>();
-                ba.Tws = Tws.p;
-                ba.ws = ews.p;
-                ba.pool = sf->pool.p;
-                ba.piv = piv_scratch.as<int>();
-                ba.perm = sf->perm.as<int>();
-                ba.sci_pool = pool->p;
-                ba.status = h->status.as<int>();
-                HIF_CUDA((big_elim_batch<T>(ba, mxn, mxk, mxr, st)));
-            }
-            h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
-        }
+        if (sf->nbox)
+            launch_elims<T>(h, *sf, ed, ed_big, eg, skv, rdv, fac_off, piv_off, ws_off, pool->p, (int)tau, Tws, S);
         h->sci_pools.push_back(std::move(pool));
 
         // ---- state for the next sublevel: active set and SCI membership
@@ -703,36 +776,49 @@ static void run_factor(hif_handle h) {
         }
         h->subs.push_back(std::move(sf));
     }
-    h->stats.sublevels = (int)kinds.size();
-    h->stats.levels = t.L;
+    h->stats.sublevels = (int)nsub;
+    h->stats.levels = maxL;
 
-    // ---- top block D_L over s_L
-    std::vector<int> top;
-    for (int64_t i = 0; i < N; ++i)
-        if (active[i]) top.push_back((int)i);
-    h->nL = (int)top.size();
-    h->stats.top_size = h->nL;
-    if (h->nL > 0) {
-        const int n = h->nL;
-        upload(h->top_ids, top, st);
-        h->topA.ensure(sizeof(T) * (size_t)n * n);
-        h->topLU.ensure(sizeof(T) * (size_t)n * n);
-        h->topInv.ensure(sizeof(T) * (size_t)n * n);
-        h->top_piv.ensure(sizeof(int) * n);
-        TopArgs ta{};
-        ta.g = g;
-        ta.sci = scidev(h, (int)kinds.size());
-        ta.ids = h->top_ids.as<int>();
-        ta.n = n;
-        ta.A = h->topA.p;
-        HIF_CUDA((launch_top_assemble<T>(ta, st)));
-        HIF_CUDA(cudaMemcpyAsync(h->topLU.p, h->topA.p, sizeof(T) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
-        HIF_CUDA((top_lu<T>(h->topLU.as<T>(), n, h->top_piv.as<int>(), h->status.as<int>(), st)));
-        check_status(h);
-        HIF_CUDA((top_inverse<T>(h->topLU.as<T>(), h->top_piv.as<int>(), n, h->topInv.as<T>(), st)));
-        HIF_CUDA(cudaStreamSynchronize(st));
-        h->stats.factor_bytes += (int64_t)3 * n * n * sizeof(T);
-        flops += 2.0 / 3.0 * (double)n * n * n + 2.0 * (double)n * n * n;
+    // ---- top blocks D = A_L over s_L (Sec. 3.1, level L), one per problem,
+    // eliminated as boxes without skeletons: L, D, U of Lemma 2.1 and the
+    // unit-triangular inverses used by the sweeps
+    {
+        auto sf = std::make_unique<SubFactor>();
+        sf->kind = KIND_TOP;
+        sf->level = maxL;
+        std::vector<ElimDesc> ed, ed_big;
+        std::vector<ElimGroup> eg;
+        std::vector<int> skv, rdv;
+        int64_t fac_off = 0, piv_off = 0, ws_off = 0, top = 0;
+        for (auto& sp : h->segs) {
+            const Segment& sg = *sp;
+            ElimDesc e{};
+            e.ngroups = 0;
+            e.sk_off = 0;
+            e.rd_off = (int64_t)rdv.size();
+            e.grp_off = 0;
+            e.sci_out = -1;
+            for (int64_t i = sg.off; i < sg.off + sg.N; ++i)
+                if (active[i]) rdv.push_back((int)i);
+            const int r = (int)((int64_t)rdv.size() - e.rd_off);
+            if (r == 0) continue;
+            top += r;
+            BoxFac bf{};
+            place_box(e, bf, 0, r, fac_off, piv_off, ws_off);
+            sf->hbox.push_back(bf);
+            sf->max_kr2 = std::max(sf->max_kr2, 2 * r);
+            if (r > big_elim_n) ed_big.push_back(e);
+            else ed.push_back(e);
+            flops += 2.0 / 3.0 * (double)r * r * r + 2.0 * (double)r * r * r / 3.0;
+        }
+        sf->nbox = (int)sf->hbox.size();
+        h->stats.top_size = top;
+        if (sf->nbox) {
+            launch_elims<T>(h, *sf, ed, ed_big, eg, skv, rdv, fac_off, piv_off, ws_off, nullptr, (int)nsub, Tws, S);
+            HIF_CUDA(cudaStreamSynchronize(st));
+            check_status(h);
+        }
+        h->subs.push_back(std::move(sf));
     }
     h->stats.flops = flops;
     h->stats.kernel_evals = evals;
@@ -752,8 +838,22 @@ static void sweep_all(hif_handle h, T* xw, int64_t ldx, int nrhs, int op) {
     auto run = [&](SubFactor& sf, int mode) {
         if (!sf.nbox) return;
         const size_t per_col = (size_t)sf.max_kr2 * sizeof(T);
-        int batch = (int)std::min<size_t>((size_t)nrhs, std::max<size_t>(1, (200 * 1024) / per_col));
-        if (per_col > 220 * 1024) fail(HIF_EINVAL, "box too large for the sweep kernel");
+        const bool global = per_col > 200 * 1024;      // vectors of the largest box do not fit in smem
+        int batch = global ? nrhs : (int)std::min<size_t>((size_t)nrhs, std::max<size_t>(1, (200 * 1024) / per_col));
+        void* gws = nullptr;
+        const int64_t* gws_off = nullptr;
+        if (global) {
+            std::vector<int64_t> offs(sf.hbox.size());
+            int64_t tot = 0;
+            for (size_t q = 0; q < sf.hbox.size(); ++q) {
+                offs[q] = tot;
+                tot += (int64_t)(sf.hbox[q].k + 2 * sf.hbox[q].r) * nrhs;
+            }
+            h->sweep_ws.ensure(sizeof(T) * std::max<int64_t>(tot, 1));
+            upload(h->sweep_off, offs, st);
+            gws = h->sweep_ws.p;
+            gws_off = h->sweep_off.as<int64_t>();
+        }
         for (int r0 = 0; r0 < nrhs; r0 += batch) {
             const int nr = std::min(batch, nrhs - r0);
             SweepArgs a{};
@@ -765,17 +865,14 @@ static void sweep_all(hif_handle h, T* xw, int64_t ldx, int nrhs, int op) {
             a.x = xw + ldx * r0;
             a.ldx = ldx;
             a.nrhs = nr;
-            const size_t smem = per_col * nr + 64;
+            const size_t smem = global ? 0 : per_col * nr + 64;
             a.mode = mode | (int)(smem << 8);
+            a.gws = gws;
+            a.gws_off = gws_off;
             HIF_CUDA((launch_sweep<T>(a, sf.nbox, st)));
         }
     };
     for (auto& sf : h->subs) run(*sf, up);
-    if (h->nL) {
-        const T* M = (op == 0 || op == 2) ? h->topInv.as<T>() : h->topA.as<T>();
-        h->tmp.ensure(sizeof(T) * (size_t)h->nL * nrhs);
-        HIF_CUDA((launch_top_gemm<T>(M, h->nL, op >= 2, h->top_ids.as<int>(), xw, ldx, nrhs, h->tmp.as<T>(), st)));
-    }
     for (auto it = h->subs.rbegin(); it != h->subs.rend(); ++it) run(**it, down);
 }
 
@@ -822,46 +919,52 @@ static void apply_op(hif_handle h, const double* in, double* out, int64_t nrhs, 
     HIF_CUDA(cudaStreamSynchronize(st));
 }
 
-// FP64 direct sum on device arrays.
+// Direct sum on device arrays, problem by problem (the operator of a handle
+// is block diagonal over its problems).
 static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs) {
     const cudaStream_t st = h->st;
-    if (h->grid) {
-        const int64_t N = h->N;
-        h->vbuf.ensure(sizeof(double) * N * nrhs);
-        h->ybuf.ensure(sizeof(double) * N * nrhs);
-        GridDirectArgs ga{};
-        ga.table = h->table.as<double>();
-        ga.dof_of = h->dof_of.as<int>();
-        ga.n = h->gn;
-        ga.dim = h->dim;
-        ga.a = h->a.as<double>();
-        ga.b = h->b.as<double>();
-        ga.c = h->c.as<double>();
-        ga.w = h->w.as<double>();
-        ga.x = x;
-        ga.ldx = ldx;
-        ga.y = y;
-        ga.ldy = ldy;
-        ga.nrhs = nrhs;
-        ga.trans = trans;
-        ga.vbuf = h->vbuf.as<double>();
-        ga.ybuf = h->ybuf.as<double>();
-        if (h->opt.direct_precision == 0) {
-            h->vdf.ensure(sizeof(float2) * N * nrhs);
-            HIF_CUDA(launch_direct_grid_df(ga, h->table_df.as<float2>(), h->vdf.as<float2>(), st));
+    for (auto& sp : h->segs) {
+        Segment& sg = *sp;
+        if (sg.grid) {
+            const int64_t n = sg.N;
+            h->vbuf.ensure(sizeof(double) * n * nrhs);
+            h->ybuf.ensure(sizeof(double) * n * nrhs);
+            GridDirectArgs ga{};
+            ga.table = sg.table.as<double>();
+            ga.dof_of = sg.dof_of.as<int>();
+            ga.n = sg.gn;
+            ga.dim = h->dim;
+            ga.a = h->a.as<double>();
+            ga.b = h->b.as<double>();
+            ga.c = h->c.as<double>();
+            ga.w = h->w.as<double>();
+            ga.x = x;
+            ga.ldx = ldx;
+            ga.y = y;
+            ga.ldy = ldy;
+            ga.nrhs = nrhs;
+            ga.trans = trans;
+            ga.vbuf = h->vbuf.as<double>();
+            ga.ybuf = h->ybuf.as<double>();
+            if (h->opt.direct_precision == 0) {
+                h->vdf.ensure(sizeof(float2) * n * nrhs);
+                HIF_CUDA(launch_direct_grid_df(ga, sg.table_df.as<float2>(), h->vdf.as<float2>(), st));
+            } else {
+                HIF_CUDA(launch_direct_grid(ga, st));
+            }
         } else {
-            HIF_CUDA(launch_direct_grid(ga, st));
+            DirectArgs da{};
+            da.g = geom(h);
+            da.x = x;
+            da.ldx = ldx;
+            da.y = y;
+            da.ldy = ldy;
+            da.nrhs = nrhs;
+            da.trans = trans;
+            da.seg_off = sg.off;
+            da.seg_n = sg.N;
+            HIF_CUDA(launch_direct_general(da, st));
         }
-    } else {
-        DirectArgs da{};
-        da.g = geom(h);
-        da.x = x;
-        da.ldx = ldx;
-        da.y = y;
-        da.ldy = ldy;
-        da.nrhs = nrhs;
-        da.trans = trans;
-        HIF_CUDA(launch_direct_general(da, st));
     }
 }
 
@@ -895,6 +998,19 @@ static std::vector<double> col_norms(hif_handle h, const double* v, int nrhs) {
     return out;
 }
 
+// 2-norms of every column restricted to every problem: nseg x nrhs, column-major.
+static std::vector<double> seg_norms(hif_handle h, const double* v, int nrhs) {
+    const int ns = (int)h->segs.size();
+    h->tmp.ensure(sizeof(double) * std::max(ns * nrhs, 1));
+    HIF_CUDA(launch_seg_dots(ns, h->seg_off.as<int64_t>(), h->seg_n.as<int64_t>(), nrhs, v, h->N, v, h->N,
+                             h->tmp.as<double>(), h->st));
+    std::vector<double> out((size_t)ns * nrhs);
+    HIF_CUDA(cudaMemcpyAsync(out.data(), h->tmp.p, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, h->st));
+    HIF_CUDA(cudaStreamSynchronize(h->st));
+    for (double& o : out) o = std::sqrt(std::max(o, 0.0));
+    return out;
+}
+
 // Iterative refinement: u = F^{-1} f; r = f - A u; u += F^{-1} r ...
 static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u, int nrhs, double tol, int maxit,
                             int* iters, double* relres) {
@@ -902,16 +1018,17 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
     DevMem r, du;
     r.ensure(sizeof(double) * N * nrhs);
     du.ensure(sizeof(double) * N * nrhs);
-    const std::vector<double> fn = col_norms(h, f, nrhs);
+    // relative residuals are judged per problem and per column
+    const std::vector<double> fn = seg_norms(h, f, nrhs);
     solve_dev(h, trans, f, u, nrhs);
     int it = 0;
     double worst = 0;
     for (;; ++it) {
         matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs);
         HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, h->st));
-        const std::vector<double> rn = col_norms(h, r.as<double>(), nrhs);
+        const std::vector<double> rn = seg_norms(h, r.as<double>(), nrhs);
         worst = 0;
-        for (int c = 0; c < nrhs; ++c) worst = std::max(worst, fn[c] > 0 ? rn[c] / fn[c] : 0.0);
+        for (size_t q = 0; q < rn.size(); ++q) worst = std::max(worst, fn[q] > 0 ? rn[q] / fn[q] : 0.0);
         if (worst <= tol || it >= maxit) break;
         solve_dev(h, trans, r.as<double>(), du.as<double>(), nrhs);
         HIF_CUDA(launch_axpby(N, nrhs, 1.0, du.as<double>(), N, 1.0, u, N, h->st));
@@ -1090,14 +1207,21 @@ hif_status hif_options_default(int dim, hif_options* opt) {
     return HIF_OK;
 }
 
-hif_status hif_factor(const double* points, int64_t N, const double* weights, const double* a, const double* b,
-                      const double* c, int kernel_id, double eps, const hif_options* opt_in, hif_handle* out) {
+static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id, double eps, const hif_options* opt_in,
+                              hif_handle* out) {
     if (!out) return HIF_EINVAL;
     *out = nullptr;
     hif_options opt;
     if (opt_in) opt = *opt_in;
     else hif_options_default(2, &opt);
-    if (N <= 0 || N > (int64_t)2000000000 || !points || !weights || !a || !b || !c) return HIF_EINVAL;
+    if (count <= 0 || !probs) return HIF_EINVAL;
+    int64_t N = 0;
+    for (int q = 0; q < count; ++q) {
+        const hif_problem& pr = probs[q];
+        if (pr.N <= 0 || !pr.points || !pr.weights || !pr.a || !pr.b || !pr.c) return HIF_EINVAL;
+        N += pr.N;
+    }
+    if (N > (int64_t)2000000000) return HIF_EINVAL;
     if (opt.dim != 2 && opt.dim != 3) return HIF_EINVAL;
     if ((opt.dim == 2 && kernel_id != 0) || (opt.dim == 3 && kernel_id != 1)) return HIF_EINVAL;
     if (!(eps >= 0.0) || !std::isfinite(eps)) return HIF_EINVAL;
@@ -1119,17 +1243,36 @@ hif_status hif_factor(const double* points, int64_t N, const double* weights, co
         h->elem = opt.precision == 0 ? 8 : 4;
         const int d = opt.dim;
         const cudaStream_t st = h->st;
-        // inputs: device copies owned by the handle, host copies of the geometry
-        auto take = [&](DevMem& dst, const double* src, size_t cnt) {
-            dst.ensure(cnt * sizeof(double));
-            HIF_CUDA(cudaMemcpyAsync(dst.p, src, cnt * sizeof(double),
+        // inputs: one concatenated device copy owned by the handle (problem q
+        // holds rows [off_q, off_q + N_q)), and host copies of the geometry
+        h->x.ensure(sizeof(double) * N * d);
+        h->w.ensure(sizeof(double) * N);
+        h->a.ensure(sizeof(double) * N);
+        h->b.ensure(sizeof(double) * N);
+        h->c.ensure(sizeof(double) * N);
+        auto take = [&](DevMem& dst, int64_t off, const double* src, size_t cnt) {
+            HIF_CUDA(cudaMemcpyAsync(dst.as<double>() + off, src, cnt * sizeof(double),
                                      is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         };
-        take(h->x, points, (size_t)N * d);
-        take(h->w, weights, (size_t)N);
-        take(h->a, a, (size_t)N);
-        take(h->b, b, (size_t)N);
-        take(h->c, c, (size_t)N);
+        std::vector<int64_t> soff(count), sn(count);
+        int64_t off = 0;
+        for (int q = 0; q < count; ++q) {
+            const hif_problem& pr = probs[q];
+            take(h->x, off * d, pr.points, (size_t)pr.N * d);
+            take(h->w, off, pr.weights, (size_t)pr.N);
+            take(h->a, off, pr.a, (size_t)pr.N);
+            take(h->b, off, pr.b, (size_t)pr.N);
+            take(h->c, off, pr.c, (size_t)pr.N);
+            auto sg = std::make_unique<Segment>();
+            sg->off = off;
+            sg->N = pr.N;
+            soff[q] = off;
+            sn[q] = pr.N;
+            h->segs.push_back(std::move(sg));
+            off += pr.N;
+        }
+        upload(h->seg_off, soff, st);
+        upload(h->seg_n, sn, st);
         h->hx.resize((size_t)N * d);
         h->hw.resize((size_t)N);
         HIF_CUDA(cudaMemcpyAsync(h->hx.data(), h->x.p, sizeof(double) * N * d, cudaMemcpyDeviceToHost, st));
@@ -1164,16 +1307,19 @@ hif_status hif_factor(const double* points, int64_t N, const double* weights, co
         upload(h->proxy, pd, st);
         h->kself.ensure(sizeof(double) * N);
         HIF_CUDA(launch_kself(geom(h.get()), h->kself.as<double>(), st));
-        detect_grid(h.get());
-        if (h->grid) {
-            const int64_t tsz = d == 2 ? (int64_t)h->gn * h->gn : (int64_t)h->gn * h->gn * h->gn;
-            h->table.ensure(sizeof(double) * tsz);
-            double k0 = 0;
-            HIF_CUDA(cudaMemcpyAsync(&k0, h->kself.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-            HIF_CUDA(cudaStreamSynchronize(st));
-            HIF_CUDA(launch_grid_table(h->table.as<double>(), h->gn, d, h->gh, kernel_id, k0 / h->hw[0], st));
-            h->table_df.ensure(sizeof(float2) * tsz);
-            HIF_CUDA(launch_split_df(h->table.as<double>(), h->table_df.as<float2>(), tsz, st));
+        std::vector<double> hks(N);
+        HIF_CUDA(cudaMemcpyAsync(hks.data(), h->kself.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaStreamSynchronize(st));
+        for (auto& sp : h->segs) {
+            Segment& sg = *sp;
+            detect_grid(h.get(), sg);
+            if (!sg.grid) continue;
+            const int64_t tsz = d == 2 ? (int64_t)sg.gn * sg.gn : (int64_t)sg.gn * sg.gn * sg.gn;
+            sg.table.ensure(sizeof(double) * tsz);
+            HIF_CUDA(launch_grid_table(sg.table.as<double>(), sg.gn, d, sg.gh, kernel_id,
+                                       hks[sg.off] / h->hw[sg.off], st));
+            sg.table_df.ensure(sizeof(float2) * tsz);
+            HIF_CUDA(launch_split_df(sg.table.as<double>(), sg.table_df.as<float2>(), tsz, st));
         }
         h->stats.N = N;
         h->stats.dim = d;
@@ -1185,6 +1331,17 @@ hif_status hif_factor(const double* points, int64_t N, const double* weights, co
     h->stats.factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = h.release();
     return HIF_OK;
+}
+
+hif_status hif_factor(const double* points, int64_t N, const double* weights, const double* a, const double* b,
+                      const double* c, int kernel_id, double eps, const hif_options* opt, hif_handle* out) {
+    const hif_problem pr{points, N, weights, a, b, c};
+    return factor_impl(1, &pr, kernel_id, eps, opt, out);
+}
+
+hif_status hif_factor_batched(int count, const hif_problem* problems, int kernel_id, double eps,
+                              const hif_options* opt, hif_handle* out) {
+    return factor_impl(count, problems, kernel_id, eps, opt, out);
 }
 
 hif_status hif_apply(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld) {

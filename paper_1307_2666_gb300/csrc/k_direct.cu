@@ -82,15 +82,16 @@ __global__ void __launch_bounds__(DS_T) direct_general_kernel(DirectArgs a, int 
     __shared__ double sv[DS_S * DS_R];
     const GeomDev& g = a.g;
     const int dim = g.dim;
-    const int64_t i = blockIdx.x * (int64_t)DS_T + threadIdx.x;
-    const bool valid = i < g.N;
+    const int64_t s_end = a.seg_off + a.seg_n;
+    const int64_t i = a.seg_off + blockIdx.x * (int64_t)DS_T + threadIdx.x;
+    const bool valid = i < s_end;
     double xi[3] = {0, 0, 0};
     if (valid)
         for (int d = 0; d < dim; ++d) xi[d] = g.x[(int64_t)dim * i + d];
     double acc[DS_R];
     for (int c = 0; c < DS_R; ++c) acc[c] = 0.0;
-    for (int64_t j0 = 0; j0 < g.N; j0 += DS_S) {
-        const int ns = (int)(g.N - j0 < DS_S ? g.N - j0 : DS_S);
+    for (int64_t j0 = a.seg_off; j0 < s_end; j0 += DS_S) {
+        const int ns = (int)(s_end - j0 < DS_S ? s_end - j0 : DS_S);
         __syncthreads();
         for (int s = threadIdx.x; s < ns; s += DS_T) {
             const int64_t j = j0 + s;
@@ -118,8 +119,8 @@ __global__ void __launch_bounds__(DS_T) direct_general_kernel(DirectArgs a, int 
 }
 
 cudaError_t launch_direct_general(const DirectArgs& a, cudaStream_t st) {
-    if (a.g.N == 0) return cudaSuccess;
-    const int blocks = (int)((a.g.N + DS_T - 1) / DS_T);
+    if (a.seg_n == 0) return cudaSuccess;
+    const int blocks = (int)((a.seg_n + DS_T - 1) / DS_T);
     for (int r0 = 0; r0 < a.nrhs; r0 += DS_R) {
         note_launch();
         direct_general_kernel<<<blocks, DS_T, 0, st>>>(a, r0, std::min(DS_R, a.nrhs - r0));
@@ -422,6 +423,31 @@ __global__ void col_dots_kernel(int64_t N, const double* x, int64_t ldx, const d
         __syncthreads();
     }
     if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void seg_dots_kernel(const int64_t* off, const int64_t* cnt, const double* x, int64_t ldx, const double* y,
+                                int64_t ldy, double* out) {
+    // CTA (s, c): sum over rows of problem s of x[:, c] * y[:, c], tree reduction
+    __shared__ double red[256];
+    const int s = blockIdx.x, c = blockIdx.y;
+    const int64_t o = off[s], n = cnt[s];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += x[o + i + ldx * c] * y[o + i + ldy * c];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[s + (int64_t)gridDim.x * c] = red[0];
+}
+
+cudaError_t launch_seg_dots(int nseg, const int64_t* off, const int64_t* cnt, int nrhs, const double* x, int64_t ldx,
+                            const double* y, int64_t ldy, double* out, cudaStream_t st) {
+    if (nseg == 0 || nrhs == 0) return cudaSuccess;
+    note_launch();
+    seg_dots_kernel<<<dim3(nseg, nrhs), 256, 0, st>>>(off, cnt, x, ldx, y, ldy, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_col_dots(int64_t N, int nrhs, const double* x, int64_t ldx, const double* y, int64_t ldy,

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
     const BoxFac bf = a.boxes[blockIdx.x];
     const int k = bf.k, r = bf.r, nr = a.nrhs;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xs = reinterpret_cast<T*>(smem_raw);
+    T* xs = a.gws ? static_cast<T*>(a.gws) + a.gws_off[blockIdx.x] : reinterpret_cast<T*>(smem_raw);
     T* xr = xs + (size_t)k * nr;
     T* tmp = xr + (size_t)r * nr;
     T* x = static_cast<T*>(a.x);

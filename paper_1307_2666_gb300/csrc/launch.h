@@ -60,14 +60,6 @@ struct ElimArgs {
     int* status;
 };
 
-struct TopArgs {            // assembly of A_L over s_L (Sec. 3.1, level L)
-    GeomDev g;
-    SciDev sci;
-    const int* ids;
-    int n;
-    void* A;                // n x n column-major
-};
-
 struct SweepArgs {
     const BoxFac* boxes;
     const int* sk_ids;
@@ -78,6 +70,8 @@ struct SweepArgs {
     int64_t ldx;
     int nrhs;
     int mode;               // see k_sweep.cu
+    void* gws;              // non-null: per-box vectors in global memory at gws_off (boxes too large for smem)
+    const int64_t* gws_off;
 };
 
 // ---- large boxes (k_large.cu)
@@ -164,14 +158,6 @@ template <typename T> cudaError_t launch_fold(const FoldArgs&, int nbox, size_t 
 template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t smem, cudaStream_t);
 template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStream_t);
 
-// top block
-template <typename T> cudaError_t launch_top_assemble(const TopArgs&, cudaStream_t);
-template <typename T> cudaError_t top_lu(T* A, int n, int* piv, int* status, cudaStream_t);
-template <typename T> cudaError_t lu_blocked(T* A, int n, int64_t ld, int* piv, int* status, cudaStream_t);
-template <typename T> cudaError_t top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t);
-template <typename T> cudaError_t launch_top_gemm(const T* M, int n, bool trans, const int* ids,
-                                                  T* x, int64_t ldx, int nrhs, T* tmp, cudaStream_t);
-
 // sweeps
 template <typename T> cudaError_t launch_sweep(const SweepArgs&, int nbox, cudaStream_t);
 
@@ -189,6 +175,8 @@ struct DirectArgs {
     int64_t ldy;
     int nrhs;
     int trans;
+    int64_t seg_off;        // the problem's DOF range [seg_off, seg_off + seg_n)
+    int64_t seg_n;
 };
 cudaError_t launch_direct_general(const DirectArgs&, cudaStream_t);
 
@@ -225,6 +213,8 @@ cudaError_t launch_kself(const GeomDev& g, double* kself, cudaStream_t);
 // BLAS-1 helpers for the refinement loops (FP64)
 cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int64_t ldx, double beta,
                          double* y, int64_t ldy, cudaStream_t);
+cudaError_t launch_seg_dots(int nseg, const int64_t* off, const int64_t* cnt, int nrhs, const double* x, int64_t ldx,
+                            const double* y, int64_t ldy, double* out, cudaStream_t);
 cudaError_t launch_col_dots(int64_t N, int nrhs, const double* x, int64_t ldx, const double* y, int64_t ldy,
                             double* out, cudaStream_t);
 

@@ -38,6 +38,17 @@ class hif_options(C.Structure):
     ]
 
 
+class hif_problem(C.Structure):
+    _fields_ = [
+        ("points", C.c_void_p),
+        ("N", C.c_int64),
+        ("weights", C.c_void_p),
+        ("a", C.c_void_p),
+        ("b", C.c_void_p),
+        ("c", C.c_void_p),
+    ]
+
+
 class hif_stats_t(C.Structure):
     _fields_ = [
         ("N", C.c_int64),
@@ -61,6 +72,8 @@ EXPORTS = {
     "hif_options_default": (C.c_int, [C.c_int, C.POINTER(hif_options)]),
     "hif_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_int, C.c_double, C.POINTER(hif_options), C.POINTER(C.c_void_p)]),
+    "hif_factor_batched": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_double, C.POINTER(hif_options),
+                                     C.POINTER(C.c_void_p)]),
     "hif_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "hif_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "hif_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
@@ -159,6 +172,20 @@ def hif_factor(points, weights, a, b, c, kernel_id: int, eps: float, opt: hif_op
     st = lib.hif_factor(_ptr(points), N, _ptr(weights), _ptr(a), _ptr(b), _ptr(c), int(kernel_id), float(eps),
                         C.byref(opt) if opt is not None else None, C.byref(h))
     _check(st, "hif_factor")
+    return h
+
+
+def hif_factor_batched(problems, kernel_id: int, eps: float, opt: hif_options | None = None):
+    """problems: sequence of (points, weights, a, b, c) array tuples."""
+    lib = load()
+    arr = (hif_problem * len(problems))()
+    for q, (pts, w, a, b, c) in enumerate(problems):
+        arr[q] = hif_problem(_ptr(pts).value, pts.shape[0], _ptr(w).value, _ptr(a).value, _ptr(b).value,
+                             _ptr(c).value)
+    h = C.c_void_p()
+    st = lib.hif_factor_batched(len(problems), C.cast(arr, C.c_void_p), int(kernel_id), float(eps),
+                                C.byref(opt) if opt is not None else None, C.byref(h))
+    _check(st, "hif_factor_batched")
     return h
 
 
