@@ -64,7 +64,9 @@ typedef struct {
     double root_width;      /* <= 0: bounding cube of the DOF cells                        */
     void* stream;           /* cudaStream_t                                                */
     int direct_precision;   /* direct sum on uniform grids: 0 = paired FP32 (~2^-48 relative,
-                               default), 1 = FP64; other point sets always use FP64         */
+                               default), 1 = FP64, 2 = tensor cores on exact 8-bit digits
+                               (~2^-55 of max|K| max|x| per term, FP64 class sums);
+                               other point sets always use FP64                          */
 } hif_options;
 
 typedef struct {
@@ -147,9 +149,12 @@ hif_status hif_solve_transpose(hif_handle h, const double* b, double* x, int64_t
  * summation over all N^2 pairs, exactly the operator the handle factored
  * (same quadrature, same self terms), with FP64 inputs and outputs.  On a
  * full uniform grid the sum is a convolution with an FP64 table; it is
- * accumulated in FP64 (direct_precision = 1) or in paired FP32 with
+ * accumulated in FP64 (direct_precision = 1), in paired FP32 with
  * error-free transformations, good to ~2^-48 relative per operation
- * (direct_precision = 0).  x, y: N x nrhs, ld >= N.
+ * (direct_precision = 0), or on the tensor cores from exact signed 8-bit
+ * digits of table and sources with integer class sums (direct_precision = 2;
+ * HIF_ETIMEOUT if a pipeline wait in the kernel expired).  x, y: N x nrhs,
+ * ld >= N.
  */
 hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y,
                       int64_t nrhs, int64_t ld);

@@ -49,7 +49,7 @@ class Factorization:
         opt.fractional_levels = 1 if fractional else 0
         opt.skip_levels = int(skip_levels)
         opt.proxy_radius = float(proxy_radius)
-        opt.direct_precision = 0 if direct == "df64" else 1
+        opt.direct_precision = {"df64": 0, "fp64": 1, "tc": 2}[direct]
         self._keep = []
         if proxy_dirs is not None:
             pd = np.ascontiguousarray(np.asarray(proxy_dirs.cpu() if hasattr(proxy_dirs, "cpu") else proxy_dirs,

@@ -117,6 +117,7 @@ struct Segment {
     int gn = 0;
     double gh = 0;
     DevMem dof_of, table, table_df;
+    DevMem tc_rows, tc_tmax;      // digit rows of the table for the tensor-core sum (built on first use)
 };
 
 struct FactorScratch {
@@ -155,7 +156,8 @@ struct hif_handle_s {
     // factors
     std::vector<std::unique_ptr<hif::SubFactor>> subs;
     // direct-sum scratch
-    hif::DevMem vbuf, ybuf, vdf;
+    hif::DevMem vbuf, ybuf, vdf, tc_xb, tc_xmax, tc_status;
+    int num_sms = 0;
     // work buffers
     hif::DevMem work, work2, tmp, status, sweep_ws, sweep_off;
     hif_stats_t stats{};
@@ -949,6 +951,24 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
             if (h->opt.direct_precision == 0) {
                 h->vdf.ensure(sizeof(float2) * n * nrhs);
                 HIF_CUDA(launch_direct_grid_df(ga, sg.table_df.as<float2>(), h->vdf.as<float2>(), st));
+            } else if (h->opt.direct_precision == 2) {
+                if (!sg.tc_rows.p) {
+                    sg.tc_tmax.ensure(sizeof(unsigned long long));
+                    sg.tc_rows.ensure(tc_table_rows_bytes(sg.gn, h->dim));
+                    HIF_CUDA(launch_tc_table(sg.table.as<double>(), sg.gn, h->dim,
+                                             sg.tc_tmax.as<unsigned long long>(), sg.tc_rows.p, st));
+                }
+                h->tc_xb.ensure(tc_source_digits_bytes(sg.gn, h->dim));
+                h->tc_xmax.ensure(8 * sizeof(unsigned long long));
+                h->tc_status.ensure(sizeof(int));
+                HIF_CUDA(cudaMemsetAsync(h->tc_status.p, 0, sizeof(int), st));
+                HIF_CUDA(launch_direct_grid_tc(ga, sg.tc_rows.p, sg.tc_tmax.as<unsigned long long>(), h->tc_xb.p,
+                                               h->tc_xmax.as<unsigned long long>(), h->tc_status.as<int>(),
+                                               h->num_sms, st));
+                int flag = 0;
+                HIF_CUDA(cudaMemcpyAsync(&flag, h->tc_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+                HIF_CUDA(cudaStreamSynchronize(st));
+                if (flag) fail(HIF_ETIMEOUT, "tensor-core direct sum: a pipeline wait expired");
             } else {
                 HIF_CUDA(launch_direct_grid(ga, st));
             }
@@ -1227,7 +1247,7 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
     if (!(eps >= 0.0) || !std::isfinite(eps)) return HIF_EINVAL;
     if (opt.leaf_occupancy < 1 || opt.proxy_points < 1 || !(opt.proxy_radius > 0)) return HIF_EINVAL;
     if (opt.precision != 0 && opt.precision != 1) return HIF_EINVAL;
-    if (opt.direct_precision != 0 && opt.direct_precision != 1) return HIF_EINVAL;
+    if (opt.direct_precision < 0 || opt.direct_precision > 2) return HIF_EINVAL;
     if (opt.dim == 3 && !opt.proxy_dirs) return HIF_EINVAL;
     auto h = std::make_unique<hif_handle_s>();
     const auto t0 = std::chrono::steady_clock::now();
@@ -1240,6 +1260,11 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
         h->eps = eps;
         h->opt = opt;
         h->st = static_cast<cudaStream_t>(opt.stream);
+        {
+            int dev = 0;
+            HIF_CUDA(cudaGetDevice(&dev));
+            HIF_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        }
         h->elem = opt.precision == 0 ? 8 : 4;
         const int d = opt.dim;
         const cudaStream_t st = h->st;

@@ -172,6 +172,16 @@ __global__ void grid_finish_kernel(GridDirectArgs a, int64_t N) {
     }
 }
 
+void grid_scatter_kernel_launch(const GridDirectArgs& a, int64_t N, int eb, cudaStream_t st) {
+    note_launch();
+    grid_scatter_kernel<<<eb, 256, 0, st>>>(a, N);
+}
+
+void grid_finish_kernel_launch(const GridDirectArgs& a, int64_t N, int eb, cudaStream_t st) {
+    note_launch();
+    grid_finish_kernel<<<eb, 256, 0, st>>>(a, N);
+}
+
 // Tile shapes: 2D 16 x 16, 3D 8 x 8 x 4 (256 points either way).
 template <int DIM>
 __global__ void __launch_bounds__(256) grid_conv_kernel(GridDirectArgs a, int r0, int nr) {

@@ -203,6 +203,20 @@ cudaError_t launch_direct_grid(const GridDirectArgs&, cudaStream_t);
 // floats, vdf: N x nrhs float2 scratch
 cudaError_t launch_direct_grid_df(const GridDirectArgs&, const float2* tdf, float2* vdf, cudaStream_t);
 cudaError_t launch_split_df(const double* src, float2* dst, int64_t n, cudaStream_t);
+// grid-order staging v = (source weight) x and the final y = a x + (target
+// weight) ybuf, shared by the grid sums (eb blocks of 256 threads)
+void grid_scatter_kernel_launch(const GridDirectArgs&, int64_t N, int eb, cudaStream_t);
+void grid_finish_kernel_launch(const GridDirectArgs&, int64_t N, int eb, cudaStream_t);
+// same sum on the tensor cores in exact 8-bit digits (k_tcconv.cu):
+// R = mirrored table digit rows (tc_table_rows_bytes), built once per grid by
+// launch_tc_table with tmax its max |entry|; XB = tc_source_digits_bytes of
+// scratch, xmax 8 entries, status one int (set to 1 if a wait expired)
+size_t tc_table_rows_bytes(int n, int dim);
+size_t tc_source_digits_bytes(int n, int dim);
+cudaError_t launch_tc_table(const double* table, int n, int dim, unsigned long long* tmax, void* R,
+                            cudaStream_t);
+cudaError_t launch_direct_grid_tc(const GridDirectArgs&, const void* R, const unsigned long long* tmax,
+                                  void* XB, unsigned long long* xmax, int* status, int num_sms, cudaStream_t);
 cudaError_t launch_grid_table(double* table, int n, int dim, double h, int kernel_id, double kself_over_w,
                               cudaStream_t);
 

@@ -1,0 +1,121 @@
+"""Tensor-core direct sum (exact 8-bit digits, integer class sums) vs the
+oracle's FP64 direct sum, element by element.
+
+The sum is the refinement residual operator (Sec. 5) over all N^2 pairs of
+the assembled K (Sec. 3.1, Eq. (3.1)).  The only rounding is the digits it
+drops (below 2^-55 of max|K| max|x| per term) and the FP64 combination of
+the class sums, so every entry must agree with FP64 to 1e-13 of the largest
+entry of its column.
+"""
+import numpy as np
+import pytest
+import torch
+
+import hif_inputs as hi
+from oracle import kernels
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1307_2666_gb300 as P
+    return P
+
+
+def T(v):
+    return torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=DEV)
+
+
+def handle(P, pb, direct="tc", eps=1e-3, precision="fp32"):
+    return P.Factorization(T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c), pb.kernel_id, eps,
+                           proxy_dirs=pb.proxy if pb.dim == 3 else None, precision=precision, direct=direct)
+
+
+def close_cols(y, ref, tol=1e-13):
+    y = np.atleast_2d(y.T).T
+    ref = np.atleast_2d(ref.T).T
+    scale = np.abs(ref).max(axis=0)
+    err = np.abs(y - ref).max(axis=0)
+    assert np.all(err <= tol * scale), (err / np.maximum(scale, 1e-300))
+
+
+# 2D: one tile and chunk, ragged tiles/chunks, exactly two, several; nrhs
+# below, at and above the 8 columns of one launch
+@pytest.mark.parametrize("n,nrhs", [(64, 1), (100, 3), (128, 8), (130, 11), (47, 16)])
+def test_tc_sum_2d_matches_oracle(P, n, nrhs):
+    pb = hi.volume_problem(n, 2, smooth_seed=1002 + n)
+    x = hi.gaussian_rhs(pb.N, nrhs, 40 + n)
+    fac = handle(P, pb)
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    for trans in (False, True):
+        y = fac.matvec(T(x), trans=trans).cpu().numpy()
+        close_cols(y, op.matvec(x, trans=trans))
+    fac.close()
+
+
+@pytest.mark.parametrize("n,nrhs", [(12, 2), (20, 9)])
+def test_tc_sum_3d_matches_oracle(P, n, nrhs):
+    pb = hi.volume_problem(n, 3, smooth_seed=77 + n)
+    x = hi.gaussian_rhs(pb.N, nrhs, 50 + n)
+    fac = handle(P, pb)
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 1)
+    for trans in (False, True):
+        y = fac.matvec(T(x), trans=trans).cpu().numpy()
+        close_cols(y, op.matvec(x, trans=trans))
+    fac.close()
+
+
+def test_tc_sum_matches_fp64_grid_sum(P):
+    # two ragged tiles per line, 8 + 2 right-hand sides, with column scales
+    # spread over 40 orders of magnitude and an all-zero column
+    pb = hi.volume_problem(200, 2, smooth_seed=31)
+    x = hi.gaussian_rhs(pb.N, 10, 7)
+    x *= np.logspace(-20, 20, 10)[None, :]
+    x[:, 3] = 0.0
+    f_tc = handle(P, pb)
+    f_64 = handle(P, pb, direct="fp64")
+    for trans in (False, True):
+        y = f_tc.matvec(T(x), trans=trans).cpu().numpy()
+        ref = f_64.matvec(T(x), trans=trans).cpu().numpy()
+        assert np.all(y[:, 3] == 0.0)
+        cols = [c for c in range(10) if c != 3]
+        close_cols(y[:, cols], ref[:, cols])
+    f_tc.close()
+    f_64.close()
+
+
+def test_tc_sum_batched_segments(P):
+    sizes = [40, 17, 64, 33]
+    pbs = [hi.volume_problem(n, 2, smooth_seed=900 + q) for q, n in enumerate(sizes)]
+    probs = [(T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)) for pb in pbs]
+    fb = P.Factorization.batched(probs, 0, 1e-3, precision="fp32", direct="tc")
+    x = hi.gaussian_rhs(sum(pb.N for pb in pbs), 3, 5)
+    y = fb.matvec(T(x)).cpu().numpy()
+    off = fb.offsets
+    for q, pb in enumerate(pbs):
+        op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+        close_cols(y[off[q]:off[q + 1]], op.matvec(x[off[q]:off[q + 1]]))
+    fb.close()
+
+
+def test_tc_sum_full_size_sampled_rows(P):
+    # the refinement workload: n = 1024 (N = 1,048,576), 8 right-hand sides,
+    # one launch over all 8192 tiles; rows sampled at tile and chunk edges
+    n = 1024
+    pb = hi.volume_problem(n, 2, smooth_seed=1002, rhs_seed=1003, nrhs=8)
+    fac = handle(P, pb, eps=1e-6)
+    y = fac.matvec(T(pb.f)).cpu().numpy()
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    rng = np.random.default_rng(11)
+    rows = np.unique(np.concatenate([[0, 127, 128, n - 1, n, n * n - 1, 511 * n + 383],
+                                     rng.integers(0, pb.N, 9)]))
+    ref = op.matvec_rows(pb.f, rows)
+    scale = np.abs(ref).max(axis=0)
+    err = np.abs(y[rows] - ref).max(axis=0)
+    assert np.all(err <= 1e-13 * scale), err / scale
+    fac.close()
