@@ -21,18 +21,29 @@
 // reverse order it is a Hankel matrix A[i][q] = v[i + q], whose 8 x 8 core
 // matrices depend only on the sum of their block indices: the shared-memory
 // operand stores the 31 distinct core matrices of each digit slice once and
-// the MMA descriptor walks them with equal leading and stride offsets.
+// the MMA descriptor walks them with equal leading and stride offsets (144 B:
+// a 16-B gap after every core matrix keeps the builders' stores free of
+// shared-memory bank conflicts).
+//
+// The block also depends only on |offset| along the slowest axis, so the
+// source lines at -d and +d from the target line share it: one MMA takes
+// both source chunks as the two halves of its B operand (rows ordered digit,
+// half, rhs), which doubles N per instruction.  Every tcgen05.mma with M = 128
+// costs a fixed ~46 cycles up to N ~ 90, so the pair roughly halves the
+// instruction time per source; a line without a mirror partner gets a zero
+// half.
 //
 // CTA roles (256 threads, persistent, one CTA per SM, TMEM 512 columns):
 //   warps 0-3  epilogue: TMEM -> integer class sums -> FP64 y (one thread
 //              per target row),
-//   warp 4     one thread: bulk copies of the source digits and the MMAs,
-//   warps 5-7  builders of the Hankel operand from mirrored digit rows.
-// Chunks of 128 sources flow through a 4-stage shared-memory ring; two TMEM
-// accumulator buffers of 256 columns alternate between 1024-source groups so
-// the epilogue of one group overlaps the MMAs of the next.  Every wait is
-// bounded; on time-out the kernel sets *status = 1, drains its own MMAs and
-// copies, frees TMEM and returns.
+//   warp 4     one thread: the MMAs,
+//   warps 5-7  builders of the Hankel operand from mirrored digit rows; one
+//              of them also issues the bulk copies of the source digits.
+// Slots (one Hankel operand, a pair of 128-source chunks) flow through a
+// 3-stage shared-memory ring into one 512-column accumulator that the
+// epilogue drains every 8 slots.  Every wait is bounded; on time-out the
+// kernel sets *status = 1, drains its own MMAs and copies, frees TMEM and
+// returns.
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cstdint>
@@ -49,30 +60,36 @@ constexpr int ST = 7;                           // table digits
 constexpr int SX = 8;                           // source digits
 constexpr int NR = 8;                           // right-hand sides per launch
 constexpr int NBLK = (TM + KC) / 8 - 1;         // distinct Hankel core matrices per slice (31)
-constexpr int A_SLICE = NBLK * 128;             // bytes
+constexpr int CM = 144;                         // core-matrix stride: 128 B + 16 B so that the
+                                                // builders' 16-B row stores of consecutive core
+                                                // matrices fall in different bank groups
+constexpr int A_SLICE = NBLK * CM;              // bytes
 constexpr int A_BYTES = ST * A_SLICE;
-constexpr int B_BYTES = SX * NR * KC * 2;       // (digit, rhs) rows x KC sources, BF16
+constexpr int CHUNK = SX * NR * KC * 2;         // one source chunk: (digit, rhs) rows x KC, BF16
+constexpr int TBLK = NR * KC * 2;               // the rows of one digit of one chunk
+constexpr int B_BYTES = 2 * CHUNK;              // the mirrored pair
 constexpr int STAGE = A_BYTES + B_BYTES;
-constexpr int NST = 4;                          // ring depth
-constexpr int GROUP = 8;                        // chunks per exact FP32 window (1024 sources)
-constexpr int ACC = 256;                        // TMEM columns per accumulator buffer
+constexpr int NST = 3;                          // ring depth
+constexpr int GROUP = 8;                        // slots per exact FP32 window (1024 sources per column)
+constexpr int ACC = 512;                        // TMEM columns of the accumulator
 constexpr int NBUILD = 96;                      // builder threads
-constexpr int NPAIR = ST * NBLK;                // (slice, core matrix) build items per chunk
+constexpr int NPAIR = ST * NBLK;                // (slice, core matrix) build items per slot
 constexpr long long WAIT_CYCLES = 4000000000LL; // ~2 s at GB300 clocks
 
-static_assert(STAGE % 128 == 0, "stage alignment");
+static_assert(STAGE % 16 == 0 && A_BYTES % 16 == 0 && TBLK % 16 == 0, "stage alignment");
 static_assert(GROUP * KC * 128 * 128 <= (1 << 24), "exact FP32 window");
 
-// accumulator columns of table digit s: (source digit t, rhs) rows of B, t
-// limited so that s + t <= 7 (rounded up to the 16-column MMA granularity)
-__host__ __device__ constexpr int ncols(int s) { return s == 0 ? 64 : s <= 2 ? 48 : s <= 4 ? 32 : 16; }
+// accumulator columns of table digit s: (source digit t, half, rhs) rows of
+// B, t limited so that s + t <= 7 (rounded up to the 16-row MMA granularity
+// per half)
+__host__ __device__ constexpr int ncols(int s) { return s == 0 ? 128 : s <= 2 ? 96 : s <= 4 ? 64 : 32; }
 __host__ __device__ constexpr int coloff(int s) {
-    return s == 0 ? 0 : s == 1 ? 64 : s == 2 ? 112 : s == 3 ? 160 : s == 4 ? 192 : s == 5 ? 224 : 240;
+    return s == 0 ? 0 : s == 1 ? 128 : s == 2 ? 224 : s == 3 ? 320 : s == 4 ? 384 : s == 5 ? 448 : 480;
 }
 __host__ __device__ constexpr int col_slice(int c) {
-    return c < 64 ? 0 : c < 112 ? 1 : c < 160 ? 2 : c < 192 ? 3 : c < 224 ? 4 : c < 240 ? 5 : 6;
+    return c < 128 ? 0 : c < 224 ? 1 : c < 320 ? 2 : c < 384 ? 3 : c < 448 ? 4 : c < 480 ? 5 : 6;
 }
-__host__ __device__ constexpr int col_class(int c) { return col_slice(c) + (c - coloff(col_slice(c))) / 8; }
+__host__ __device__ constexpr int col_class(int c) { return col_slice(c) + (c - coloff(col_slice(c))) / 16; }
 __host__ __device__ constexpr int col_rhs(int c) { return (c - coloff(col_slice(c))) % 8; }
 static_assert(coloff(6) + ncols(6) == ACC, "column map");
 
@@ -98,10 +115,11 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 
 struct Bars {
-    uint64_t full[NST];
+    uint64_t full[NST];         // Hankel operand built (NBUILD arrivals)
+    uint64_t bfull[NST];        // source digits landed (1 arrival + bytes)
     uint64_t mma_done[NST];
-    uint64_t acc_full[2];
-    uint64_t acc_empty[2];
+    uint64_t acc_full;
+    uint64_t acc_empty;
     uint64_t drain;
     uint32_t tmem;
     int abort;
@@ -197,7 +215,7 @@ __global__ void tc_source_digits_kernel(const double* v, int64_t N, int n, int64
 
 struct TcConvArgs {
     const __nv_bfloat16* R;     // mirrored table digit rows
-    const uint4* XB;            // source digit chunks
+    const unsigned char* XB;    // source digit chunks, then one zero chunk
     const unsigned long long* tmax;
     const unsigned long long* xmax;   // NR entries
     double* ybuf;               // N x nrhs, grid order
@@ -211,6 +229,56 @@ struct TcConvArgs {
     int* status;
 };
 
+namespace {
+
+// The slot sequence of one CTA, identical in every role: its tiles
+// (round-robin), and per tile the offsets d0 = 0..max(i0, n-1-i0) along the
+// slowest axis, the middle source coordinate j1 (3D), the chunk c.
+struct Walk {
+    int n, dim, nb, nc;
+    int64_t tiles, step, tile;
+    int64_t L;
+    int b, i0, i1, dmax, d0, j1, c;
+    bool ok;
+
+    __device__ void init(const TcConvArgs& a, int64_t first, int64_t stride) {
+        n = a.n; dim = a.dim; nb = a.nb; nc = a.nc; tiles = a.tiles; step = stride; tile = first;
+        ok = tile < tiles;
+        if (ok) start();
+    }
+    __device__ void start() {
+        L = tile / nb;
+        b = (int)(tile % nb);
+        i0 = dim == 2 ? (int)L : (int)(L / n);
+        i1 = dim == 2 ? 0 : (int)(L % n);
+        dmax = i0 > n - 1 - i0 ? i0 : n - 1 - i0;
+        d0 = 0; j1 = 0; c = 0;
+    }
+    __device__ int64_t slots() const { return (int64_t)(dmax + 1) * (dim == 3 ? n : 1) * nc; }
+    __device__ bool tile_end() const { return c == nc - 1 && (dim == 2 || j1 == n - 1) && d0 == dmax; }
+    __device__ void next() {
+        if (++c < nc) return;
+        c = 0;
+        if (dim == 3 && ++j1 < n) return;
+        j1 = 0;
+        if (++d0 <= dmax) return;
+        tile += step;
+        ok = tile < tiles;
+        if (ok) start();
+    }
+    // offset index of the line pair (all but the last coordinate)
+    __device__ int64_t dl() const { return d0 + (dim == 3 ? (int64_t)n * (i1 > j1 ? i1 - j1 : j1 - i1) : 0); }
+    // source line of half h (h = 0: i0 - d0, h = 1: i0 + d0), -1 if none
+    __device__ int64_t src_line(int h) const {
+        if (h == 1 && d0 == 0) return -1;
+        const int j0 = h == 0 ? i0 - d0 : i0 + d0;
+        if (j0 < 0 || j0 >= n) return -1;
+        return dim == 2 ? (int64_t)j0 : (int64_t)j0 * n + j1;
+    }
+};
+
+}  // namespace
+
 __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -220,146 +288,177 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NST; ++i) {
-            tc::mbar_init(&bars->full[i], NBUILD + 1);
+            tc::mbar_init(&bars->full[i], NBUILD);
+            tc::mbar_init(&bars->bfull[i], 1);
             tc::mbar_init(&bars->mma_done[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&bars->acc_full[i], 1);
-            tc::mbar_init(&bars->acc_empty[i], 128);
-        }
+        tc::mbar_init(&bars->acc_full, 1);
+        tc::mbar_init(&bars->acc_empty, 128);
         tc::mbar_init(&bars->drain, 1);
         bars->abort = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(&bars->tmem, 2 * ACC);
+    if (warp == 0) tc::tmem_alloc(&bars->tmem, ACC);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = bars->tmem;
-
-    const int64_t cpt = a.lines * a.nc;                    // chunks per tile
-    const int64_t my_tiles = a.tiles > blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t my_chunks = my_tiles * cpt;
     const int64_t Z0 = 128LL * a.nc - 1, RL = 256LL * a.nc;
-
-    // line offset index of a (target line, source line) pair
-    auto dline = [&](int64_t L, int64_t J) -> int64_t {
-        if (a.dim == 2) return L > J ? L - J : J - L;
-        const int64_t i0 = L / a.n, i1 = L % a.n, j0 = J / a.n, j1 = J % a.n;
-        return (i0 > j0 ? i0 - j0 : j0 - i0) + (int64_t)a.n * (i1 > j1 ? i1 - j1 : j1 - i1);
-    };
+    const int64_t zero_chunk = a.lines * a.nc;
 
     if (warp == 4) {
-        // ------------------------------------------------ issuer / B loader
+        // ---------------------------------------------------------- issuer
+        // (counters are stepped, not divided, and the thread does nothing
+        // but wait and issue: its scalar work between MMA batches shows up
+        // as tensor-pipe idle time)
         if (lane == 0) {
-            int64_t issued_loads = 0, consumed = 0;
-            auto load_B = [&](int64_t gc) {
-                const int st = (int)(gc % NST);
-                const int64_t ch = gc % cpt;                            // = J * nc + c
-                unsigned char* dst = smem + st * STAGE + A_BYTES;
-                tc::mbar_arrive_expect_tx(&bars->full[st], B_BYTES);
-                tc::bulk_g2s(dst, (const unsigned char*)a.XB + ch * (int64_t)B_BYTES, B_BYTES, &bars->full[st]);
-                ++issued_loads;
-            };
-            const int64_t pre = my_chunks < NST - 1 ? my_chunks : NST - 1;
-            for (int64_t gc = 0; gc < pre; ++gc) load_B(gc);
-            int64_t G = 0;
-            uint32_t buf = 0;
+            Walk w;
+            w.init(a, blockIdx.x, gridDim.x);
+            int st = 0;
+            uint32_t ph = 0;
+            int64_t si = 0, G = 0;
             bool ok = true;
-            for (int64_t gc = 0; gc < my_chunks && ok; ++gc) {
-                const int st = (int)(gc % NST);
-                const uint32_t use = (uint32_t)(gc / NST);
-                const int64_t ci = gc % cpt;
-                const bool first = ci % GROUP == 0;
-                const bool last = ci % GROUP == GROUP - 1 || ci == cpt - 1;
-                if (first) {
-                    buf = (uint32_t)(G & 1);
-                    if (G >= 2 && !wait_bounded(&bars->acc_empty[buf], (uint32_t)(((G >> 1) - 1) & 1), abort)) {
-                        ok = false;
-                        break;
-                    }
-                }
-                if (!wait_bounded(&bars->full[st], use & 1, abort)) {
+            while (w.ok) {
+                const bool first = (si & (GROUP - 1)) == 0;
+                const bool tend = w.tile_end();
+                const bool last = (si & (GROUP - 1)) == GROUP - 1 || tend;
+                if (first && G >= 1 && !wait_bounded(&bars->acc_empty, (uint32_t)((G - 1) & 1), abort)) {
                     ok = false;
                     break;
                 }
-                ++consumed;
+                if (!wait_bounded(&bars->full[st], ph, abort) || !wait_bounded(&bars->bfull[st], ph, abort)) {
+                    ok = false;
+                    break;
+                }
                 tc::tc_fence_after();
                 // descriptors of the stage; moving the start address by 16 B
                 // adds 1 to the descriptor (addresses stay below 256 KB)
                 const uint32_t a_st = tc::smem_addr(smem + st * STAGE);
-                const uint64_t a0 = tc::sdesc(a_st, 128, 128);
+                const uint64_t a0 = tc::sdesc(a_st, CM, CM);
                 const uint64_t b0 = tc::sdesc(a_st + A_BYTES, 128, (KC / 8) * 128);
-#pragma unroll 1
-                for (int kk = 0; kk < KC / 16; ++kk) {
-                    const uint64_t bdesc = b0 + (uint64_t)(16 * kk);
-                    const bool accum = !(first && kk == 0);
+                // slice by slice: consecutive MMAs of one slice read
+                // overlapping Hankel windows and keep N and D fixed, which
+                // the tensor core streams faster than alternating slices
 #pragma unroll
-                    for (int s = 0; s < ST; ++s)
-                        tc::mma_bf16(tmem + buf * ACC + coloff(s), a0 + (uint64_t)((s * A_SLICE) / 16 + 16 * kk), bdesc,
-                                     tc::idesc_bf16_f32(TM, ncols(s)), accum);
+                for (int s = 0; s < ST; ++s) {
+                    const uint64_t as = a0 + (uint64_t)(s * A_SLICE / 16);
+                    const uint32_t d = tmem + coloff(s);
+#pragma unroll
+                    for (int kk = 0; kk < KC / 16; ++kk)
+                        tc::mma_bf16(d, as + (uint64_t)(2 * CM * kk / 16), b0 + (uint64_t)(16 * kk),
+                                     tc::idesc_bf16_f32(TM, ncols(s)), !(first && kk == 0));
                 }
                 tc::mma_commit(&bars->mma_done[st]);
                 if (last) {
-                    tc::mma_commit(&bars->acc_full[buf]);
+                    tc::mma_commit(&bars->acc_full);
                     ++G;
                 }
-                const int64_t nx = gc + NST - 1;
-                if (nx < my_chunks) {
-                    if (gc >= 1 && !wait_bounded(&bars->mma_done[(gc - 1) % NST], (uint32_t)(((gc - 1) / NST) & 1),
-                                                 abort)) {
-                        ok = false;
-                        break;
-                    }
-                    load_B(nx);
+                si = tend ? 0 : si + 1;
+                w.next();
+                if (++st == NST) {
+                    st = 0;
+                    ph ^= 1;
                 }
             }
-            // drain: every MMA issued so far, then every bulk copy not consumed
+            // drain: every MMA issued so far
             tc::mma_commit(&bars->drain);
             const long long t0 = clock64();
             while (!tc::mbar_try_wait(&bars->drain, 0) && clock64() - t0 < WAIT_CYCLES) {}
-            for (int64_t gc = consumed; gc < issued_loads; ++gc) {
-                const int st = (int)(gc % NST);
-                const long long t1 = clock64();
-                while (!tc::mbar_try_wait(&bars->full[st], (uint32_t)((gc / NST) & 1)) && clock64() - t1 < WAIT_CYCLES) {}
-            }
             if (!ok) *abort = 1;
         }
     } else if (warp >= 5) {
         // ------------------------------------------------------- builders
+        // each thread owns up to PPT (slice, core matrix) items per slot; the
+        // 16 digits of every item are fetched one slot ahead, so the L2
+        // latency overlaps the build of the current slot
+        constexpr int PPT = (NPAIR + NBUILD - 1) / NBUILD;
         const int bt = threadIdx.x - 160;
-        for (int64_t gc = 0; gc < my_chunks; ++gc) {
-            const int st = (int)(gc % NST);
-            const uint32_t use = (uint32_t)(gc / NST);
-            if (use > 0 && !wait_bounded(&bars->mma_done[st], (use - 1) & 1, abort)) break;
-            const int64_t tile = blockIdx.x + (gc / cpt) * gridDim.x;
-            const int64_t L = tile / a.nb;
-            const int b = (int)(tile % a.nb);
-            const int64_t ci = gc % cpt;
-            const int64_t J = ci / a.nc;
-            const int c = (int)(ci % a.nc);
-            const int64_t dl = dline(L, J);
-            const int64_t base = (int64_t)TM * b + TM - 1 - (int64_t)KC * c;
-            const int64_t idx0 = Z0 - base;                         // multiple of 8
+        uint4 cur[PPT][2], nxt[PPT][2];
+        auto fetch = [&](const Walk& v, uint4 (&buf)[PPT][2]) {
+            const int64_t dl = v.dl();
+            const int64_t idx0 = Z0 - ((int64_t)TM * v.b + TM - 1 - (int64_t)KC * v.c);   // multiple of 8
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int pr = bt + NBUILD * j;
+                if (pr < NPAIR) {
+                    const int s = pr / NBLK, m = pr % NBLK;
+                    const uint4* src =
+                        reinterpret_cast<const uint4*>(a.R + ((int64_t)s * a.lines + dl) * RL + idx0 + 8 * m);
+                    buf[j][0] = __ldg(src);
+                    buf[j][1] = __ldg(src + 1);
+                }
+            }
+        };
+        Walk w, wn;
+        w.init(a, blockIdx.x, gridDim.x);
+        wn = w;
+        if (w.ok) {
+            fetch(w, cur);
+            wn.next();
+        }
+        int st = 0;
+        uint32_t ph = 0;
+        int64_t gs = 0, issued = 0;
+        while (w.ok) {
+            if (wn.ok) fetch(wn, nxt);
+            if (gs >= NST && !wait_bounded(&bars->mma_done[st], ph ^ 1, abort)) break;
             unsigned char* a_st = smem + st * STAGE;
-            for (int pr = bt; pr < NPAIR; pr += NBUILD) {
-                const int s = pr / NBLK, m = pr % NBLK;
-                const uint4* src = reinterpret_cast<const uint4*>(a.R + ((int64_t)s * a.lines + dl) * RL + idx0 + 8 * m);
-                const uint4 lo = __ldg(src), hi = __ldg(src + 1);
-                const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-                uint4* dst = reinterpret_cast<uint4*>(a_st + s * A_SLICE + m * 128);
+            if (bt == 0) {
+                // source digits of both halves, digit block by digit block
+                // into rows (digit, half, rhs); a missing half reads zeros
+                tc::mbar_arrive_expect_tx(&bars->bfull[st], B_BYTES);
 #pragma unroll
-                for (int rho = 0; rho < 8; ++rho) {
-                    uint32_t o[4];
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t J = w.src_line(h);
+                    const int64_t chunk = J >= 0 ? J * a.nc + w.c : zero_chunk;
+                    const unsigned char* src = a.XB + chunk * (int64_t)CHUNK;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        o[j] = (rho & 1) ? __funnelshift_r(w[rho / 2 + j], w[rho / 2 + j + 1], 16) : w[rho / 2 + j];
-                    dst[rho] = make_uint4(o[0], o[1], o[2], o[3]);
+                    for (int t = 0; t < SX; ++t)
+                        tc::bulk_g2s(a_st + A_BYTES + (2 * t + h) * TBLK, src + t * TBLK, TBLK, &bars->bfull[st]);
+                }
+                ++issued;
+            }
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int pr = bt + NBUILD * j;
+                if (pr < NPAIR) {
+                    const int s = pr / NBLK, m = pr % NBLK;
+                    const uint32_t wd[8] = {cur[j][0].x, cur[j][0].y, cur[j][0].z, cur[j][0].w,
+                                            cur[j][1].x, cur[j][1].y, cur[j][1].z, cur[j][1].w};
+                    uint4* dst = reinterpret_cast<uint4*>(a_st + s * A_SLICE + m * CM);
+#pragma unroll
+                    for (int rho = 0; rho < 8; ++rho) {
+                        uint32_t o[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            o[q] = (rho & 1) ? __funnelshift_r(wd[rho / 2 + q], wd[rho / 2 + q + 1], 16)
+                                             : wd[rho / 2 + q];
+                        dst[rho] = make_uint4(o[0], o[1], o[2], o[3]);
+                    }
                 }
             }
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&bars->full[st]);
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                cur[j][0] = nxt[j][0];
+                cur[j][1] = nxt[j][1];
+            }
+            w = wn;
+            if (wn.ok) wn.next();
+            ++gs;
+            if (++st == NST) {
+                st = 0;
+                ph ^= 1;
+            }
         }
+        // drain: the latest copy into every stage has landed before exit
+        if (bt == 0)
+            for (int64_t i = issued > NST ? issued - NST : 0; i < issued; ++i) {
+                const long long t1 = clock64();
+                while (!tc::mbar_try_wait(&bars->bfull[i % NST], (uint32_t)((i / NST) & 1)) &&
+                       clock64() - t1 < WAIT_CYCLES) {}
+            }
     } else if (warp < 4) {
         // ------------------------------------------------------- epilogue
         long long acc[8][NR];
@@ -367,20 +466,20 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
         for (int k = 0; k < 8; ++k)
 #pragma unroll
             for (int r = 0; r < NR; ++r) acc[k][r] = 0;
-        const int ngr = (int)((cpt + GROUP - 1) / GROUP);
         const int eT = scale_exp(*a.tmax);
         int64_t G = 0;
         bool ok = true;
-        for (int64_t it = 0; it < my_tiles && ok; ++it) {
-            const int64_t tile = blockIdx.x + it * gridDim.x;
-            for (int g = 0; g < ngr; ++g, ++G) {
-                const uint32_t buf = (uint32_t)(G & 1);
-                if (!wait_bounded(&bars->acc_full[buf], (uint32_t)((G >> 1) & 1), abort)) {
+        for (int64_t tile = blockIdx.x; tile < a.tiles && ok; tile += gridDim.x) {
+            Walk w;
+            w.init(a, tile, a.tiles);                          // this tile only
+            const int64_t ngr = (w.slots() + GROUP - 1) / GROUP;
+            for (int64_t g = 0; g < ngr; ++g, ++G) {
+                if (!wait_bounded(&bars->acc_full, (uint32_t)(G & 1), abort)) {
                     ok = false;
                     break;
                 }
                 tc::tc_fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16) + buf * ACC;
+                const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
                 for (int cb = 0; cb < ACC / 16; ++cb) {
                     float v[16];
@@ -390,20 +489,18 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
                         acc[col_class(16 * cb + i)][col_rhs(16 * cb + i)] += (long long)__float2int_rn(v[i]);
                 }
                 tc::tc_fence_before();
-                tc::mbar_arrive(&bars->acc_empty[buf]);
+                tc::mbar_arrive(&bars->acc_empty);
             }
             if (!ok) break;
-            const int64_t L = tile / a.nb;
-            const int b = (int)(tile % a.nb);
-            const int il = TM * b + TM - 1 - (32 * warp + lane);
+            const int il = TM * w.b + TM - 1 - (32 * warp + lane);
             if (il < a.n) {
-                const int64_t gpos = L * a.n + il;
+                const int64_t gpos = w.L * a.n + il;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     if (r < a.nr) {
-                        double y = 0.0, w = 1.0 / 72057594037927936.0;          // 2^-56
+                        double y = 0.0, wt = 1.0 / 72057594037927936.0;          // 2^-56
 #pragma unroll
-                        for (int k = 7; k >= 0; --k, w *= 256.0) y += (double)acc[k][r] * w;
+                        for (int k = 7; k >= 0; --k, wt *= 256.0) y += (double)acc[k][r] * wt;
                         a.ybuf[gpos + a.N * (a.r0 + r)] = ldexp(y, eT + scale_exp(a.xmax[r]) - 16);
                     }
                 }
@@ -419,7 +516,7 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
     if (threadIdx.x == 0 && bars->abort) atomicExch(a.status, 1);
     if (warp == 0) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, 2 * ACC);
+        tc::tmem_dealloc(tmem, ACC);
     }
 }
 
@@ -434,7 +531,7 @@ size_t tc_table_rows_bytes(int n, int dim) {
 size_t tc_source_digits_bytes(int n, int dim) {
     const int nc = (n + KC - 1) / KC;
     const int64_t lines = dim == 2 ? (int64_t)n : (int64_t)n * n;
-    return (size_t)lines * nc * B_BYTES;
+    return (size_t)(lines * nc + 1) * CHUNK;                 // + one zero chunk
 }
 
 cudaError_t launch_tc_table(const double* table, int n, int dim, unsigned long long* tmax, void* R,
@@ -468,6 +565,10 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
         attr_set = true;
     }
     grid_scatter_kernel_launch(a, N, eb, st);
+    {
+        cudaError_t e = cudaMemsetAsync((unsigned char*)XB + lines * nc * (int64_t)CHUNK, 0, CHUNK, st);
+        if (e != cudaSuccess) return e;
+    }
     for (int r0 = 0; r0 < a.nrhs; r0 += NR) {
         const int nr = std::min(NR, a.nrhs - r0);
         cudaError_t e = cudaMemsetAsync(xmax, 0, NR * sizeof(unsigned long long), st);
@@ -481,7 +582,7 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
             a.vbuf, N, a.n, lines, nc, r0, nr, xmax, (uint4*)XB);
         TcConvArgs t{};
         t.R = (const __nv_bfloat16*)R;
-        t.XB = (const uint4*)XB;
+        t.XB = (const unsigned char*)XB;
         t.tmax = tmax;
         t.xmax = xmax;
         t.ybuf = a.ybuf;
