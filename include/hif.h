@@ -63,9 +63,9 @@ typedef struct {
     double root_lo[3];      /* root box lower corner; used when root_width > 0            */
     double root_width;      /* <= 0: bounding cube of the DOF cells                        */
     void* stream;           /* cudaStream_t                                                */
-    int direct_precision;   /* direct sum on uniform grids: 0 = paired FP32 (~2^-48 relative,
-                               default), 1 = FP64, 2 = tensor cores on exact 8-bit digits
-                               (~2^-55 of max|K| max|x| per term, FP64 class sums);
+    int direct_precision;   /* direct sum on uniform grids: 0 = paired FP32 (~2^-48 relative),
+                               1 = FP64, 2 = tensor cores on exact 8-bit digits (~2^-55 of
+                               max|K| max|x| per term, FP64 class sums; default);
                                other point sets always use FP64                          */
 } hif_options;
 
@@ -189,6 +189,15 @@ const char* hif_last_error(void);
 /* Number of CUDA kernels the library has launched in this process so far
  * (all handles, all threads); callers difference it around a region. */
 uint64_t hif_kernel_launches(void);
+
+/* Device time of the tensor-core direct-sum kernel (direct_precision = 2),
+ * for measurement: while enabled, every launch is bracketed by a pair of CUDA
+ * events on its own stream.  Each call returns in *ms the summed event time
+ * and in *launches the number of launches recorded since the previous call
+ * (either pointer may be NULL), synchronizing on the recorded events, and
+ * then sets recording on (enable != 0) or off.  Process-wide; not
+ * thread-safe against concurrent direct sums.  The paper has no counterpart. */
+hif_status hif_kernel_timing(int enable, double* ms, int64_t* launches);
 
 /*
  * hif_kernel_block -- entries A_ij = a_i delta_ij + b_i K_ij c_j (Eq. (3.1))

@@ -35,12 +35,14 @@ class Factorization:
 
     points (N, dim), weights/a/b/c (N,) FP64 tensors (CUDA or CPU).
     precision: "fp64" or "fp32" (factorization precision; vectors stay FP64).
+    direct: direct sum on uniform grids, "tc" (tensor cores on exact 8-bit
+    digits), "df64" (paired FP32) or "fp64".
     """
 
     def __init__(self, points, weights, a, b, c, kernel_id: int, eps: float, *, precision: str = "fp64",
                  second_kind: bool = True, occupancy: int = 64, proxy_dirs=None, fractional: bool = True,
                  skip_levels: int = 0, proxy_radius: float = 1.5, fp32_tol_floor: float | None = None,
-                 root=None, stream=None, direct: str = "df64"):
+                 root=None, stream=None, direct: str = "tc"):
         dim = (points[0][0] if isinstance(points, (list, tuple)) else points).shape[1]
         opt = _h.hif_options_default(dim)
         opt.leaf_occupancy = int(occupancy)

@@ -1208,6 +1208,13 @@ const char* hif_last_error(void) { return g_last_error; }
 
 uint64_t hif_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+hif_status hif_kernel_timing(int enable, double* ms, int64_t* launches) {
+    return guard([&] {
+        HIF_CUDA(tc_timing_collect(ms, launches));
+        tc_timing_set(enable != 0);
+    });
+}
+
 hif_status hif_options_default(int dim, hif_options* opt) {
     if (!opt || (dim != 2 && dim != 3)) return HIF_EINVAL;
     std::memset(opt, 0, sizeof(*opt));
@@ -1221,7 +1228,7 @@ hif_status hif_options_default(int dim, hif_options* opt) {
     opt->proxy_radius = 1.5;
     opt->proxy_dirs = nullptr;
     opt->fp32_tol_floor = std::ldexp(1.0, -17);
-    opt->direct_precision = 0;
+    opt->direct_precision = 2;
     opt->root_width = 0.0;
     opt->stream = nullptr;
     return HIF_OK;

@@ -46,6 +46,9 @@
 // returns.
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
 #include <cstdint>
 #include "hif_types.h"
 #include "launch.h"
@@ -522,6 +525,36 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
 
 // ---- host side ----------------------------------------------------------------
 
+namespace {
+std::mutex g_tm_mu;
+bool g_tm_on = false;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tm_ev;
+}  // namespace
+
+void tc_timing_set(bool enable) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    g_tm_on = enable;
+}
+
+cudaError_t tc_timing_collect(double* ms, int64_t* launches) {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    double tot = 0.0;
+    cudaError_t err = cudaSuccess;
+    for (auto& e : g_tm_ev) {
+        float t = 0.f;
+        cudaError_t r = cudaEventSynchronize(e.second);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&t, e.first, e.second);
+        if (r != cudaSuccess && err == cudaSuccess) err = r;
+        tot += t;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = (int64_t)g_tm_ev.size();
+    g_tm_ev.clear();
+    return err;
+}
+
 size_t tc_table_rows_bytes(int n, int dim) {
     const int nc = (n + KC - 1) / KC;
     const int64_t lines = dim == 2 ? (int64_t)n : (int64_t)n * n;
@@ -597,8 +630,19 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
         t.nr = nr;
         t.status = status;
         const int grid = (int)std::min<int64_t>(t.tiles, num_sms);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_tm_mu);
+            if (g_tm_on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+                cudaEventRecord(e0, st);
+                g_tm_ev.emplace_back(e0, e1);
+            } else {
+                e1 = nullptr;
+            }
+        }
         note_launch();
         tc_conv_kernel<<<grid, 256, smem, st>>>(t);
+        if (e1) cudaEventRecord(e1, st);
     }
     grid_finish_kernel_launch(a, N, eb, st);
     return cudaGetLastError();

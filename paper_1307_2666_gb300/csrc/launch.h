@@ -215,6 +215,9 @@ size_t tc_table_rows_bytes(int n, int dim);
 size_t tc_source_digits_bytes(int n, int dim);
 cudaError_t launch_tc_table(const double* table, int n, int dim, unsigned long long* tmax, void* R,
                             cudaStream_t);
+// CUDA-event timing of tc_conv_kernel launches (see hif_kernel_timing)
+void tc_timing_set(bool enable);
+cudaError_t tc_timing_collect(double* ms, int64_t* launches);
 cudaError_t launch_direct_grid_tc(const GridDirectArgs&, const void* R, const unsigned long long* tmax,
                                   void* XB, unsigned long long* xmax, int* status, int num_sms, cudaStream_t);
 cudaError_t launch_grid_table(double* table, int n, int dim, double h, int kernel_id, double kself_over_w,

@@ -86,6 +86,7 @@ EXPORTS = {
     "hif_status_string": (C.c_char_p, [C.c_int]),
     "hif_last_error": (C.c_char_p, []),
     "hif_kernel_launches": (C.c_uint64, []),
+    "hif_kernel_timing": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "hif_kernel_block": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                    C.c_void_p]),
@@ -246,6 +247,15 @@ def hif_stats(h) -> dict:
 
 def hif_kernel_launches() -> int:
     return int(load().hif_kernel_launches())
+
+
+def hif_kernel_timing(enable: bool) -> tuple[float, int]:
+    """(device ms, launches) of the tensor-core direct sum since the previous
+    call; then turns event recording on or off."""
+    ms = C.c_double(0.0)
+    n = C.c_int64(0)
+    _check(load().hif_kernel_timing(1 if enable else 0, C.byref(ms), C.byref(n)), "hif_kernel_timing")
+    return ms.value, n.value
 
 
 def hif_destroy(h):

@@ -50,7 +50,7 @@ def test_struct_layouts_match_header(lib):
     o = hif.hif_options_default(2)
     assert (o.dim, o.leaf_occupancy, o.second_kind, o.precision, o.fractional_levels) == (2, 64, 1, 0, 1)
     assert o.proxy_points == 64 and o.proxy_radius == 1.5 and o.fp32_tol_floor == 2.0 ** -17
-    assert o.direct_precision == 0
+    assert o.direct_precision == 2
     o3 = hif.hif_options_default(3)
     assert o3.proxy_points == 512
 
