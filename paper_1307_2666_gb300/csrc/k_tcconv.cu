@@ -483,13 +483,14 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
                 }
                 tc::tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
+                // 64 columns per TMEM load and wait
 #pragma unroll
-                for (int cb = 0; cb < ACC / 16; ++cb) {
-                    float v[16];
-                    tc::tmem_ld16(tbase + 16 * cb, v);
+                for (int cb = 0; cb < ACC / 64; ++cb) {
+                    float v[64];
+                    tc::tmem_ld64(tbase + 64 * cb, v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        acc[col_class(16 * cb + i)][col_rhs(16 * cb + i)] += (long long)__float2int_rn(v[i]);
+                    for (int i = 0; i < 64; ++i)
+                        acc[col_class(64 * cb + i)][col_rhs(64 * cb + i)] += (long long)__float2int_rn(v[i]);
                 }
                 tc::tc_fence_before();
                 tc::mbar_arrive(&bars->acc_empty);
