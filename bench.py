@@ -35,6 +35,10 @@ METRIC = "factor s + solve DOF/s on GB300 at stated rel. err; FP32+refine/batche
 UNIT = "DOF/s"
 TOL = 1e-10
 ORACLE_SAMPLE_N = 64
+# DRAM bytes (read + write) of one 8-RHS launch of the tensor-core direct sum
+# at n = 1024, from one ncu capture (profiles/tc_conv_n1024_dram.md); valid
+# only for the kernel source with this sha256 prefix
+TC_TRAFFIC = {"n": 1024, "bytes": 116.76e9 + 95.09e6, "source_sha256": "ce53d56acc1c774f"}
 
 
 def workload_config(n, nrhs, eps):
@@ -138,6 +142,20 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- GPU arm ---
+
+def tc_traffic(n, nrhs):
+    """The captured DRAM bytes per launch, or None if the workload or the
+    kernel source differs from the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "k_tcconv.cu"), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    if n != TC_TRAFFIC["n"] or nrhs != 8 or not sha.startswith(TC_TRAFFIC["source_sha256"]):
+        return None
+    return TC_TRAFFIC["bytes"]
+
 
 def measured_peaks():
     try:
@@ -250,7 +268,7 @@ def run_gpu(args):
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside the step)"
                                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained"),
                 "algorithmic_per_launch": f"256 BF16 digit MACs x N^2 per 8 RHS = {flops_launch:.3e} flop",
-                "launch_seconds": t_launch, "launches_timed": tc_launches, "traffic": None,
+                "launch_seconds": t_launch, "launches_timed": tc_launches, "traffic": tc_traffic(n, nrhs),
                 "fp64_equivalent_tflops": 2.0 * N * N * min(nrhs, 8) / t_launch / 1e12,
                 "matvec_seconds": t_mv, "matvec_launches_per_call": groups}
 
@@ -309,6 +327,88 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Independent problems in one handle: P 2D second-kind IEs with n drawn
+    from {32, 48, ..., 256} (seed 3), eps 1e-6, 4 Gaussian RHS each; one step
+    = factor all problems in one batched handle + refine all RHS to 1e-10.
+    Reported next to the same problems factored and refined one handle at a
+    time (FP64, the plain path) and to the batched handle in FP32."""
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import hif_inputs as hi
+    import paper_1307_2666_gb300 as P
+    from paper_1307_2666_gb300 import hif as H
+    dev = torch.device(f"cuda:{local}")
+    T = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev)
+    sizes = hi.batched_sizes(args.problems, seed=3)
+    pbs = [hi.volume_problem(n, 2, smooth_seed=5000 + q, rhs_seed=6000 + q, nrhs=4) for q, n in enumerate(sizes)]
+    probs = [(T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)) for pb in pbs]
+    F = T(np.vstack([pb.f for pb in pbs]).T).t()
+    dofs = sum(pb.N for pb in pbs)
+
+    def batched(precision):
+        fb = P.Factorization.batched(probs, 0, 1e-6, precision=precision)
+        u, its, rel = fb.solve_refined(F, tol=TOL)
+        fb.close()
+        return its, rel
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0, out
+
+    for _ in range(args.warmup):
+        batched("fp32")
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = H.hif_kernel_launches()
+    ts = []
+    for _ in range(args.steps):
+        t, (its, rel) = timed(lambda: batched("fp32"))
+        ts.append(t)
+    launches = (H.hif_kernel_launches() - l0) // max(args.steps, 1)
+    clocks = sampler.stop()
+    t32 = sum(ts) / len(ts)
+    t64, (its64, rel64) = timed(lambda: batched("fp64"))
+
+    def sequential():
+        worst, its_max = 0.0, 0
+        for q, pb in enumerate(pbs):
+            fi = P.Factorization(*probs[q], 0, 1e-6, precision="fp64")
+            u, it, r = fi.solve_refined(T(pb.f.T).t(), tol=TOL)
+            worst, its_max = max(worst, r), max(its_max, it)
+            fi.close()
+        return its_max, worst
+    tseq, (itss, rels) = timed(sequential) if not args.no_sequential else (float("nan"), (None, None))
+    if rank == 0:
+        line = {
+            "metric": "batched factor + solve DOF/s to rel. residual 1e-10 (independent problems, one handle)",
+            "value": world * dofs * 4 / t32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t32, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 factor; residual bf16 digits, exact int sums", "data": "synthetic",
+            "config": {"workload": (f"batched: {args.problems} independent 2D second-kind volume IEs, n drawn from "
+                                    f"{{32,48,...,256}} (seed 3), eps 1e-6, 4 Gaussian RHS each, refined to "
+                                    f"{TOL:g}"), "problems": args.problems, "dofs": dofs, "nrhs": 4,
+                       "parallelism": f"replicas x{world}"},
+            "refine_iters": its, "relres": rel, "gpu_launches": int(launches), "clocks": clocks,
+            "batched_fp64": {"seconds": t64, "value": dofs * 4 / t64, "iters": its64, "relres": rel64},
+            "sequential_fp64": {"seconds": tseq, "value": dofs * 4 / tseq if tseq == tseq else None,
+                                "iters": itss, "relres": rels},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -345,6 +445,10 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["grid", "batched"], default="grid",
+                    help="grid: the n x n bench workload (default); batched: independent problems in one handle")
+    ap.add_argument("--problems", type=int, default=256, help="batched workload: number of problems")
+    ap.add_argument("--no-sequential", action="store_true", help="batched workload: skip the one-by-one leg")
     ap.add_argument("--oracle-sample-json", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample_json is not None:
@@ -354,6 +458,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 

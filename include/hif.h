@@ -67,6 +67,11 @@ typedef struct {
                                1 = FP64, 2 = tensor cores on exact 8-bit digits (~2^-55 of
                                max|K| max|x| per term, FP64 class sums; default);
                                other point sets always use FP64                          */
+    int use_graphs;         /* capture the sweeps of each (operation, nrhs) in a CUDA graph
+                               and replay it (default 1)                                   */
+    int autotune;           /* time the candidate CTA sizes of every sublevel's sweep after
+                               the factorization and keep the fastest (default 1; the
+                               sweep's arithmetic does not depend on it)                   */
 } hif_options;
 
 typedef struct {

@@ -37,12 +37,14 @@ class Factorization:
     precision: "fp64" or "fp32" (factorization precision; vectors stay FP64).
     direct: direct sum on uniform grids, "tc" (tensor cores on exact 8-bit
     digits), "df64" (paired FP32) or "fp64".
+    graphs: replay the factored-form sweeps from captured CUDA graphs.
+    autotune: pick each sublevel's sweep CTA size by timing after factoring.
     """
 
     def __init__(self, points, weights, a, b, c, kernel_id: int, eps: float, *, precision: str = "fp64",
                  second_kind: bool = True, occupancy: int = 64, proxy_dirs=None, fractional: bool = True,
                  skip_levels: int = 0, proxy_radius: float = 1.5, fp32_tol_floor: float | None = None,
-                 root=None, stream=None, direct: str = "tc"):
+                 root=None, stream=None, direct: str = "tc", graphs: bool = True, autotune: bool = True):
         dim = (points[0][0] if isinstance(points, (list, tuple)) else points).shape[1]
         opt = _h.hif_options_default(dim)
         opt.leaf_occupancy = int(occupancy)
@@ -52,6 +54,8 @@ class Factorization:
         opt.skip_levels = int(skip_levels)
         opt.proxy_radius = float(proxy_radius)
         opt.direct_precision = {"df64": 0, "fp64": 1, "tc": 2}[direct]
+        opt.use_graphs = 1 if graphs else 0
+        opt.autotune = 1 if autotune else 0
         self._keep = []
         if proxy_dirs is not None:
             pd = np.ascontiguousarray(np.asarray(proxy_dirs.cpu() if hasattr(proxy_dirs, "cpu") else proxy_dirs,

@@ -132,6 +132,22 @@ struct SubFactor {
     std::vector<BoxFac> hbox;
     DevMem boxes, sk, rd, pool, perm;
     int max_kr2 = 0;               // max over boxes of k + 2 r
+    // sweep plan: boxes whose vectors exceed shared memory use a global work
+    // space (offsets per right-hand side); the CTA size is tuned per sublevel
+    bool global = false;
+    DevMem gws_off;
+    int64_t gws_units = 0;
+    int threads = 256;
+};
+
+// A captured sequence of sweeps (one operation, one right-hand-side count, one
+// work buffer) and the number of kernels in it.
+struct SweepGraph {
+    int op = 0, nrhs = 0;
+    void* xw = nullptr;            // the buffers baked into the graph
+    void* ws = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;
 };
 
 }  // namespace hif
@@ -161,6 +177,14 @@ struct hif_handle_s {
     // work buffers
     hif::DevMem work, work2, tmp, status, sweep_ws, sweep_off;
     hif_stats_t stats{};
+    // CUDA graphs of the sweeps, captured on a stream of the handle's own
+    std::vector<hif::SweepGraph> graphs;
+    cudaStream_t cap_st = nullptr;
+    ~hif_handle_s() {
+        for (auto& g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (cap_st) cudaStreamDestroy(cap_st);
+    }
 };
 
 namespace hif {
@@ -831,51 +855,141 @@ static void run_factor(hif_handle h) {
 enum { SOLVE_UP = 0, SOLVE_DOWN = 1, APPLY_UP = 2, APPLY_DOWN = 3,
        SOLVET_UP = 4, SOLVET_DOWN = 5, APPLYT_UP = 6, APPLYT_DOWN = 7 };
 
+// One sublevel in one direction for all right-hand sides (CTA size: the
+// sublevel's tuned value unless threads > 0).
 template <typename T>
-static void sweep_all(hif_handle h, T* xw, int64_t ldx, int nrhs, int op) {
+static void sweep_one(hif_handle h, SubFactor& sf, int mode, T* xw, int64_t ldx, int nrhs, int threads,
+                      cudaStream_t st) {
+    if (!sf.nbox) return;
+    const size_t per_col = (size_t)sf.max_kr2 * sizeof(T);
+    const int batch = sf.global ? nrhs : (int)std::min<size_t>((size_t)nrhs, std::max<size_t>(1, (200 * 1024) / per_col));
+    for (int r0 = 0; r0 < nrhs; r0 += batch) {
+        const int nr = std::min(batch, nrhs - r0);
+        SweepArgs a{};
+        a.boxes = sf.boxes.as<BoxFac>();
+        a.sk_ids = sf.sk.as<int>();
+        a.rd_ids = sf.rd.as<int>();
+        a.pool = sf.pool.p;
+        a.perm = sf.perm.as<int>();
+        a.x = xw + ldx * r0;
+        a.ldx = ldx;
+        a.nrhs = nr;
+        const size_t smem = sf.global ? 0 : per_col * nr + 64;
+        a.mode = mode | (int)(smem << 8);
+        a.gws = sf.global ? h->sweep_ws.p : nullptr;
+        a.gws_off = sf.global ? sf.gws_off.as<int64_t>() : nullptr;
+        HIF_CUDA((launch_sweep<T>(a, sf.nbox, threads > 0 ? threads : sf.threads, st)));
+    }
+}
+
+template <typename T>
+static void sweep_seq(hif_handle h, T* xw, int64_t ldx, int nrhs, int op, cudaStream_t st) {
     // op: 0 solve, 1 apply, 2 solve^T, 3 apply^T
     const int up = op == 0 ? SOLVE_UP : op == 1 ? APPLY_UP : op == 2 ? SOLVET_UP : APPLYT_UP;
-    const int down = up + 1;
+    for (auto& sf : h->subs) sweep_one<T>(h, *sf, up, xw, ldx, nrhs, 0, st);
+    for (auto it = h->subs.rbegin(); it != h->subs.rend(); ++it) sweep_one<T>(h, **it, up + 1, xw, ldx, nrhs, 0, st);
+}
+
+static void ensure_sweep_ws(hif_handle h, int nrhs, size_t elem) {
+    int64_t units = 1;
+    for (auto& sf : h->subs) units = std::max(units, sf->gws_units);
+    h->sweep_ws.ensure(elem * (size_t)units * (size_t)std::max(nrhs, 1));
+}
+
+// All sweeps of one operation.  With use_graphs the launch sequence for this
+// (operation, nrhs, work buffer) is captured once into a CUDA graph on the
+// handle's capture stream and replayed on the handle's stream.
+template <typename T>
+static void sweep_all(hif_handle h, T* xw, int64_t ldx, int nrhs, int op) {
+    ensure_sweep_ws(h, nrhs, sizeof(T));
+    if (!h->opt.use_graphs || ldx != h->N) {
+        sweep_seq<T>(h, xw, ldx, nrhs, op, h->st);
+        return;
+    }
+    SweepGraph* g = nullptr;
+    for (auto& c : h->graphs)
+        if (c.op == op && c.nrhs == nrhs && c.xw == (void*)xw && c.ws == h->sweep_ws.p) g = &c;
+    if (!g) {
+        if (!h->cap_st) HIF_CUDA(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+        const uint64_t before = g_launches.load();
+        HIF_CUDA(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t graph = nullptr;
+        try {
+            sweep_seq<T>(h, xw, ldx, nrhs, op, h->cap_st);
+        } catch (...) {
+            cudaStreamEndCapture(h->cap_st, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        HIF_CUDA(cudaStreamEndCapture(h->cap_st, &graph));
+        const uint64_t kernels = g_launches.load() - before;
+        g_launches.fetch_sub(kernels);                 // counted when the graph runs
+        SweepGraph ng;
+        ng.op = op;
+        ng.nrhs = nrhs;
+        ng.xw = xw;
+        ng.ws = h->sweep_ws.p;
+        ng.kernels = kernels;
+        const cudaError_t e = cudaGraphInstantiate(&ng.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        HIF_CUDA(e);
+        h->graphs.push_back(ng);
+        g = &h->graphs.back();
+    }
+    HIF_CUDA(cudaGraphLaunch(g->exec, h->st));
+    g_launches.fetch_add(g->kernels);
+}
+
+// After the factorization: the global work-space offsets of every sublevel,
+// and (with autotune) the CTA size of each sublevel's sweep, picked by timing
+// one solve sweep per candidate on the work vector.
+template <typename T>
+static void prepare_sweeps(hif_handle h) {
     const cudaStream_t st = h->st;
-    auto run = [&](SubFactor& sf, int mode) {
-        if (!sf.nbox) return;
-        const size_t per_col = (size_t)sf.max_kr2 * sizeof(T);
-        const bool global = per_col > 200 * 1024;      // vectors of the largest box do not fit in smem
-        int batch = global ? nrhs : (int)std::min<size_t>((size_t)nrhs, std::max<size_t>(1, (200 * 1024) / per_col));
-        void* gws = nullptr;
-        const int64_t* gws_off = nullptr;
-        if (global) {
-            std::vector<int64_t> offs(sf.hbox.size());
-            int64_t tot = 0;
-            for (size_t q = 0; q < sf.hbox.size(); ++q) {
-                offs[q] = tot;
-                tot += (int64_t)(sf.hbox[q].k + 2 * sf.hbox[q].r) * nrhs;
+    for (auto& sp : h->subs) {
+        SubFactor& sf = *sp;
+        sf.global = (size_t)sf.max_kr2 * sizeof(T) > 200 * 1024;
+        if (!sf.global || !sf.nbox) continue;
+        std::vector<int64_t> offs(sf.hbox.size());
+        int64_t tot = 0;
+        for (size_t q = 0; q < sf.hbox.size(); ++q) {
+            offs[q] = tot;
+            tot += (int64_t)(sf.hbox[q].k + 2 * sf.hbox[q].r);
+        }
+        upload(sf.gws_off, offs, st);
+        sf.gws_units = tot;
+    }
+    if (!h->opt.autotune) return;
+    const int64_t N = h->N;
+    h->work.ensure(sizeof(T) * N);
+    T* xw = h->work.as<T>();
+    HIF_CUDA(cudaMemsetAsync(xw, 0, sizeof(T) * N, st));
+    ensure_sweep_ws(h, 1, sizeof(T));
+    cudaEvent_t e0, e1;
+    HIF_CUDA(cudaEventCreate(&e0));
+    HIF_CUDA(cudaEventCreate(&e1));
+    const int cand[3] = {128, 256, 512};
+    for (auto& sp : h->subs) {
+        SubFactor& sf = *sp;
+        if (!sf.nbox) continue;
+        float best = 1e30f;
+        for (int c : cand) {
+            float t = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {           // the first run warms the factor data
+                HIF_CUDA(cudaEventRecord(e0, st));
+                sweep_one<T>(h, sf, SOLVE_UP, xw, N, 1, c, st);
+                HIF_CUDA(cudaEventRecord(e1, st));
+                HIF_CUDA(cudaEventSynchronize(e1));
+                HIF_CUDA(cudaEventElapsedTime(&t, e0, e1));
             }
-            h->sweep_ws.ensure(sizeof(T) * std::max<int64_t>(tot, 1));
-            upload(h->sweep_off, offs, st);
-            gws = h->sweep_ws.p;
-            gws_off = h->sweep_off.as<int64_t>();
+            if (t < best) {
+                best = t;
+                sf.threads = c;
+            }
         }
-        for (int r0 = 0; r0 < nrhs; r0 += batch) {
-            const int nr = std::min(batch, nrhs - r0);
-            SweepArgs a{};
-            a.boxes = sf.boxes.as<BoxFac>();
-            a.sk_ids = sf.sk.as<int>();
-            a.rd_ids = sf.rd.as<int>();
-            a.pool = sf.pool.p;
-            a.perm = sf.perm.as<int>();
-            a.x = xw + ldx * r0;
-            a.ldx = ldx;
-            a.nrhs = nr;
-            const size_t smem = global ? 0 : per_col * nr + 64;
-            a.mode = mode | (int)(smem << 8);
-            a.gws = gws;
-            a.gws_off = gws_off;
-            HIF_CUDA((launch_sweep<T>(a, sf.nbox, st)));
-        }
-    };
-    for (auto& sf : h->subs) run(*sf, up);
-    for (auto it = h->subs.rbegin(); it != h->subs.rend(); ++it) run(**it, down);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
 }
 
 static void apply_op(hif_handle h, const double* in, double* out, int64_t nrhs, int64_t ld, int op) {
@@ -1229,6 +1343,8 @@ hif_status hif_options_default(int dim, hif_options* opt) {
     opt->proxy_dirs = nullptr;
     opt->fp32_tol_floor = std::ldexp(1.0, -17);
     opt->direct_precision = 2;
+    opt->use_graphs = 1;
+    opt->autotune = 1;
     opt->root_width = 0.0;
     opt->stream = nullptr;
     return HIF_OK;
@@ -1355,8 +1471,13 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
         }
         h->stats.N = N;
         h->stats.dim = d;
-        if (h->precision == 0) run_factor<double>(h.get());
-        else run_factor<float>(h.get());
+        if (h->precision == 0) {
+            run_factor<double>(h.get());
+            prepare_sweeps<double>(h.get());
+        } else {
+            run_factor<float>(h.get());
+            prepare_sweeps<float>(h.get());
+        }
         HIF_CUDA(cudaStreamSynchronize(st));
     });
     if (s != HIF_OK) return s;

@@ -92,11 +92,11 @@ __device__ void scale_rows(T* v, const T* D, int n, bool divide, int nr) {
 }  // namespace
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     const BoxFac bf = a.boxes[blockIdx.x];
     const int k = bf.k, r = bf.r, nr = a.nrhs;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xs = a.gws ? static_cast<T*>(a.gws) + a.gws_off[blockIdx.x] : reinterpret_cast<T*>(smem_raw);
+    T* xs = a.gws ? static_cast<T*>(a.gws) + a.gws_off[blockIdx.x] * nr : reinterpret_cast<T*>(smem_raw);
     T* xr = xs + (size_t)k * nr;
     T* tmp = xr + (size_t)r * nr;
     T* x = static_cast<T*>(a.x);
@@ -166,35 +166,36 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 }
 
 template <typename T, int MODE>
-static cudaError_t launch_mode(const SweepArgs& a, int nbox, size_t smem, cudaStream_t st) {
+static cudaError_t launch_mode(const SweepArgs& a, int nbox, int threads, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    sweep_kernel<T, MODE><<<nbox, 256, smem, st>>>(a);
+    sweep_kernel<T, MODE><<<nbox, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 // The caller sizes a.nrhs so that (k + 2r) * nrhs * sizeof(T) fits; the
 // dynamic shared memory is passed through a.mode's high bits.
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs& a, int nbox, cudaStream_t st) {
+cudaError_t launch_sweep(const SweepArgs& a, int nbox, int threads, cudaStream_t st) {
     if (nbox == 0) return cudaSuccess;
+    if (threads < 32 || threads > 512 || threads % 32) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(a.mode >> 8);
     switch (a.mode & 0xff) {
-        case SOLVE_UP: return launch_mode<T, SOLVE_UP>(a, nbox, smem, st);
-        case SOLVE_DOWN: return launch_mode<T, SOLVE_DOWN>(a, nbox, smem, st);
-        case APPLY_UP: return launch_mode<T, APPLY_UP>(a, nbox, smem, st);
-        case APPLY_DOWN: return launch_mode<T, APPLY_DOWN>(a, nbox, smem, st);
-        case SOLVET_UP: return launch_mode<T, SOLVET_UP>(a, nbox, smem, st);
-        case SOLVET_DOWN: return launch_mode<T, SOLVET_DOWN>(a, nbox, smem, st);
-        case APPLYT_UP: return launch_mode<T, APPLYT_UP>(a, nbox, smem, st);
-        case APPLYT_DOWN: return launch_mode<T, APPLYT_DOWN>(a, nbox, smem, st);
+        case SOLVE_UP: return launch_mode<T, SOLVE_UP>(a, nbox, threads, smem, st);
+        case SOLVE_DOWN: return launch_mode<T, SOLVE_DOWN>(a, nbox, threads, smem, st);
+        case APPLY_UP: return launch_mode<T, APPLY_UP>(a, nbox, threads, smem, st);
+        case APPLY_DOWN: return launch_mode<T, APPLY_DOWN>(a, nbox, threads, smem, st);
+        case SOLVET_UP: return launch_mode<T, SOLVET_UP>(a, nbox, threads, smem, st);
+        case SOLVET_DOWN: return launch_mode<T, SOLVET_DOWN>(a, nbox, threads, smem, st);
+        case APPLYT_UP: return launch_mode<T, APPLYT_UP>(a, nbox, threads, smem, st);
+        case APPLYT_DOWN: return launch_mode<T, APPLYT_DOWN>(a, nbox, threads, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template cudaError_t launch_sweep<double>(const SweepArgs&, int, cudaStream_t);
-template cudaError_t launch_sweep<float>(const SweepArgs&, int, cudaStream_t);
+template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, cudaStream_t);
+template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, cudaStream_t);
 
 // ---------------------------------------------------- precision moves ----
 

@@ -70,8 +70,8 @@ struct SweepArgs {
     int64_t ldx;
     int nrhs;
     int mode;               // see k_sweep.cu
-    void* gws;              // non-null: per-box vectors in global memory at gws_off (boxes too large for smem)
-    const int64_t* gws_off;
+    void* gws;              // non-null: per-box vectors in global memory at gws_off[box] * nrhs
+    const int64_t* gws_off; // (boxes too large for shared memory); offsets per right-hand side
 };
 
 // ---- large boxes (k_large.cu)
@@ -159,7 +159,9 @@ template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t s
 template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStream_t);
 
 // sweeps
-template <typename T> cudaError_t launch_sweep(const SweepArgs&, int nbox, cudaStream_t);
+// threads: CTA size, a multiple of 32 up to 512 (the sweep's arithmetic does
+// not depend on it)
+template <typename T> cudaError_t launch_sweep(const SweepArgs&, int nbox, int threads, cudaStream_t);
 
 // vectors and direct sums (FP64 inputs)
 template <typename T> cudaError_t launch_to_work(const double* src, int64_t lds, T* dst, int64_t ldd,

@@ -35,6 +35,8 @@ class hif_options(C.Structure):
         ("root_width", C.c_double),
         ("stream", C.c_void_p),
         ("direct_precision", C.c_int),
+        ("use_graphs", C.c_int),
+        ("autotune", C.c_int),
     ]
 
 

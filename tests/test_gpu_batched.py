@@ -89,3 +89,29 @@ def test_batched_refined_solve_per_problem(P):
         r = fq - op.matvec(u[off[q]:off[q + 1]])
         assert np.linalg.norm(r, axis=0).max() <= 1e-10 * np.linalg.norm(fq, axis=0).min()
     fb.close()
+
+
+def test_graphs_and_autotune_leave_results_unchanged(P):
+    # the sweeps replayed from captured CUDA graphs with tuned CTA sizes give
+    # bitwise the same solves and applies as plain launches at 256 threads,
+    # and the launch counter still counts every kernel that ran
+    from paper_1307_2666_gb300 import hif as H
+    sizes = [24, 64, 40]
+    pbs = _problems(sizes, seed0=2300)
+    probs = [(T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)) for pb in pbs]
+    F = T(np.vstack([pb.f for pb in pbs]))
+    outs, counts = [], []
+    for graphs, tune in ((True, True), (False, False)):
+        fb = P.Factorization.batched(probs, 0, 1e-6, precision="fp32", graphs=graphs, autotune=tune)
+        res = []
+        for _ in range(2):                         # the second call replays the captured graph
+            l0 = H.hif_kernel_launches()
+            res.append((fb.solve(F), fb.apply(F), fb.solve_transpose(F)))
+            torch.cuda.synchronize()
+            counts.append(H.hif_kernel_launches() - l0)
+        outs.append(res)
+        fb.close()
+    for k in range(2):
+        for a, b in zip(outs[0][k], outs[1][k]):
+            assert torch.equal(a, b)
+    assert counts[0] == counts[1] == counts[2] == counts[3] > 0
