@@ -277,10 +277,13 @@ static int env_int(const char* name, int dflt) {
 
 struct BigBuffers {
     DevMem bb, bg, state, YK, YS, vv, vw, vt, est, nrm, perm;
+    DevMem q_yoff, q_m, q_n, q_tau, q_G, q_T, q_W, q_Gp, q_Wp, q_gpoff, q_wpoff;
 };
 
-// ID of the large boxes of one sublevel: Y_c materialized in HBM, pivoted QR
-// by per-step launches shared by all large column groups.
+// ID of the large boxes of one sublevel: Y_c materialized in HBM and, when it
+// has more rows than columns, reduced to its n x n factor R by a blocked
+// unpivoted QR (same ID); then pivoted QR by per-step launches shared by all
+// large column groups.
 template <typename T>
 static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd, const std::vector<GroupDesc>& gd,
                        const SublevelPlan& p, const std::vector<int>& big_boxes, DevMem& d_boxes, DevMem& d_groups,
@@ -309,6 +312,7 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
             y.group = (int)gi;
             y.n = G.n;
             y.m = x.m;
+            y.ld = x.m;
             y.need_rho = (h->second_kind && G.has_sci && b.has_sci && tau > 0) ? 1 : 0;
             y.y_off = x.y_off + (int64_t)x.m * G.col0;
             y.vec_off = voff;
@@ -363,6 +367,68 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
     HIF_CUDA((big_ygen<T>(a, (int)bbv.size(), max_entries, st)));
     HIF_CUDA((big_rho<T>(a, ng, max_m, max_n, st)));
     if (split) HIF_CUDA((big_add<T>(B.YK.p, B.YS.p, yoff, st)));
+    // Opt-in (HIF_BIG_RFIRST=1): measured slower at present, see k_bigqr.cu.
+    if (env_int("HIF_BIG_RFIRST", 0)) {
+        // Y_c = Q R for the tall boxes; the groups then work on R's rows
+        std::vector<int64_t> qy;
+        std::vector<int> qm, qn;
+        int qmax_m = 0, qmax_n = 0;
+        for (const BigBox& x : bbv) {
+            qy.push_back(x.y_off);
+            qm.push_back(x.m);
+            qn.push_back(bd[x.box].n);
+            if (x.m > bd[x.box].n) {
+                qmax_m = std::max(qmax_m, x.m);
+                qmax_n = std::max(qmax_n, bd[x.box].n);
+            }
+        }
+        if (qmax_n > 0) {
+            const int nbx = (int)bbv.size();
+            upload(B.q_yoff, qy, st);
+            upload(B.q_m, qm, st);
+            upload(B.q_n, qn, st);
+            B.q_tau.ensure(sizeof(T) * 16 * nbx);
+            B.q_G.ensure(sizeof(double) * 16 * 16 * nbx);
+            B.q_T.ensure(sizeof(T) * 16 * 16 * nbx);
+            B.q_W.ensure(sizeof(T) * 16 * (size_t)qmax_n * nbx);
+            BigQRArgs q{};
+            q.Y = B.YK.p;
+            q.y_off = B.q_yoff.as<int64_t>();
+            q.m = B.q_m.as<int>();
+            q.n = B.q_n.as<int>();
+            q.tau = B.q_tau.p;
+            q.G = B.q_G.p;
+            q.Tf = B.q_T.p;
+            q.W = B.q_W.p;
+            q.wld = qmax_n;
+            std::vector<int64_t> gpo, wpo;
+            int64_t wp_total = 0;
+            const size_t gp_total = big_geqrf_partials(qm.data(), qn.data(), nbx, gpo, wpo, &wp_total);
+            upload(B.q_gpoff, gpo, st);
+            upload(B.q_wpoff, wpo, st);
+            B.q_Gp.ensure(sizeof(double) * std::max<size_t>(gp_total, 1));
+            B.q_Wp.ensure(sizeof(double) * (size_t)std::max<int64_t>(wp_total, 1));
+            q.Gp = B.q_Gp.as<double>();
+            q.gp_off = B.q_gpoff.as<int64_t>();
+            q.Wp = B.q_Wp.as<double>();
+            q.wp_off = B.q_wpoff.as<int64_t>();
+            HIF_CUDA((big_geqrf<T>(q, nbx, qmax_m, qmax_n, st)));
+            // the tolerances were filled on the device: read the groups back
+            // before changing their row counts
+            HIF_CUDA(cudaMemcpyAsync(bgv.data(), B.bg.p, sizeof(BigGroup) * bgv.size(), cudaMemcpyDeviceToHost, st));
+            HIF_CUDA(cudaStreamSynchronize(st));
+            size_t gi = 0;
+            maxk = 0;
+            for (const BigBox& x : bbv) {
+                const int nbox = bd[x.box].n;
+                for (int q2 = 0; q2 < bd[x.box].ngroups; ++q2, ++gi) {
+                    if (x.m > nbox) bgv[gi].m = nbox;
+                    maxk = std::max(maxk, std::min(bgv[gi].m, bgv[gi].n));
+                }
+            }
+            upload(B.bg, bgv, st);
+        }
+    }
     HIF_CUDA((big_qr_init<T>(a, ng, max_n, st)));
     std::vector<BigState> hs(ng);
     for (int j = 0; j < maxk; ++j) {

@@ -185,7 +185,7 @@ __global__ void big_norm_init_kernel(BigArgs a) {
     if (l >= G.n) return;
     double s = 0.0;
     for (int i = lane; i < G.m; i += 32) {
-        const double v = (double)Y[i + (int64_t)G.m * l];
+        const double v = (double)Y[i + (int64_t)G.ld * l];
         s += v * v;
     }
     s = warp_sum(s);
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) big_step_kernel(BigArgs a, int j) {
     BigState* S = a.state + blockIdx.x;
     if (S->stop) return;
     T* W = static_cast<T*>(a.YK) + G.y_off;
-    const int64_t ld = G.m;
+    const int64_t ld = G.ld;
     double* nrm = a.nrm + G.vec_off;
     int* perm = a.perm + G.vec_off;
     __shared__ double redv[256];
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256) big_update_kernel(BigArgs a, int j) {
     const int l = j + 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (l >= G.n) return;
     T* W = static_cast<T*>(a.YK) + G.y_off;
-    const int64_t ld = G.m;
+    const int64_t ld = G.ld;
     T* col = W + ld * l;
     const T* v = W + ld * j;
     const T tau = (T)S.tau;
@@ -326,7 +326,7 @@ __global__ void big_T_kernel(BigArgs a) {
     const int k = a.state[blockIdx.y].k;
     const int n = G.n, r = n - k;
     const T* W = static_cast<const T*>(a.YK) + G.y_off;
-    const int64_t ld = G.m;
+    const int64_t ld = G.ld;
     const int* perm = a.perm + G.vec_off;
     T* Tout = static_cast<T*>(a.Tws) + gd.T_off;
     int* pout = a.perm_out + gd.perm_off;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "hif_types.h"
@@ -74,6 +75,27 @@ struct SweepArgs {
     const int64_t* gws_off; // (boxes too large for shared memory); offsets per right-hand side
 };
 
+// ---- large boxes: unpivoted blocked QR to the n x n factor R (k_bigqr.cu)
+struct BigQRArgs {
+    void* Y;                // proxy matrices, column-major, ld = m, at y_off per box
+    const int64_t* y_off;
+    const int* m;
+    const int* n;
+    void* tau;              // per box 16 (the current panel's reflectors)
+    void* G;                // per box 16 x 16 FP64 (Gram of the panel's reflectors)
+    void* Tf;               // per box 16 x 16 (compact-WY factor)
+    void* W;                // per box 16 x wld
+    int64_t wld;            // >= the largest n
+    double* Gp;             // partial Grams, per box at gp_off (see big_geqrf_partials)
+    const int64_t* gp_off;
+    double* Wp;             // partial V^T C, per box at wp_off
+    const int64_t* wp_off;
+};
+// offsets of the partial-sum slots; returns the Gram slots' total (doubles)
+size_t big_geqrf_partials(const int* m, const int* n, int nbox, std::vector<int64_t>& gp_off,
+                          std::vector<int64_t>& wp_off, int64_t* wp_total);
+template <typename T> cudaError_t big_geqrf(const BigQRArgs&, int nbox, int max_m, int max_n, cudaStream_t);
+
 // ---- large boxes (k_large.cu)
 struct BigBox {
     int box;                // index into the sublevel's BoxDesc array
@@ -84,7 +106,8 @@ struct BigBox {
 struct BigGroup {
     int group;              // index into the sublevel's GroupDesc array
     int n;                  // columns
-    int m;                  // rows (= the box's m)
+    int m;                  // rows (the box's m, or its n once the box is reduced to R)
+    int ld;                 // leading dimension (the box's m)
     int need_rho;           // second-kind tolerance needed
     int64_t y_off;          // first column of the group in the workspace
     int64_t vec_off;        // prefix sum of n over groups
