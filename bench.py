@@ -157,6 +157,24 @@ def tc_traffic(n, nrhs):
     return TC_TRAFFIC["bytes"]
 
 
+def max_over_ranks(t_local, world, device):
+    """The slowest rank's time: every rank's timed region ends at a barrier
+    and the job's throughput is counted against the maximum."""
+    if world <= 1:
+        return float(t_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, t_max):
+    """Whole-job throughput of independent replicas (weak scaling): every
+    rank processes the same units; no collective in the data path."""
+    return world * units_per_rank / t_max
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -222,13 +240,9 @@ def run_gpu(args):
     launches = H.hif_kernel_launches() - launches0
     tc_ms, tc_launches = H.hif_kernel_timing(False)
     clocks = sampler.stop()
-    t_local = ev0.elapsed_time(ev1) / 1000.0
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = max_over_ranks(ev0.elapsed_time(ev1) / 1000.0, world, dev)
     ms_per_step = 1000.0 * t_max / args.steps
-    value = world * N * nrhs * args.steps / t_max
+    value = job_value(N * nrhs * args.steps, world, t_max)
 
     # ---- solve-only split of one step, for the report
     fac = P.Factorization(pts, w, a, b, c, 0, eps, precision="fp32")
@@ -335,10 +349,13 @@ def run_batched(args):
     time (FP64, the plain path) and to the batched handle in FP32."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     import __graft_entry__
     __graft_entry__.build()
     import hif_inputs as hi
@@ -370,6 +387,8 @@ def run_batched(args):
 
     for _ in range(args.warmup):
         batched("fp32")
+    if world > 1:
+        dist.barrier()
     sampler = ClockSampler(local)
     sampler.start()
     l0 = H.hif_kernel_launches()
@@ -379,7 +398,7 @@ def run_batched(args):
         ts.append(t)
     launches = (H.hif_kernel_launches() - l0) // max(args.steps, 1)
     clocks = sampler.stop()
-    t32 = sum(ts) / len(ts)
+    t32 = max_over_ranks(sum(ts) / len(ts), world, dev)
     t64, (its64, rel64) = timed(lambda: batched("fp64"))
 
     def sequential():
@@ -394,7 +413,7 @@ def run_batched(args):
     if rank == 0:
         line = {
             "metric": "batched factor + solve DOF/s to rel. residual 1e-10 (independent problems, one handle)",
-            "value": world * dofs * 4 / t32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "value": job_value(dofs * 4, world, t32), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * t32, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 factor; residual bf16 digits, exact int sums", "data": "synthetic",
             "config": {"workload": (f"batched: {args.problems} independent 2D second-kind volume IEs, n drawn from "
@@ -407,6 +426,9 @@ def run_batched(args):
                                 "iters": itss, "relres": rels},
         }
         print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def run_reference(args):
