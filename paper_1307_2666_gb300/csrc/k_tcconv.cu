@@ -46,6 +46,7 @@
 // returns.
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -230,6 +231,7 @@ struct TcConvArgs {
     int64_t tiles;
     int r0, nr;
     int* status;
+    int stall;                  // test of the bounded waits: issue no MMA at all
 };
 
 namespace {
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
         // as tensor-pipe idle time)
         if (lane == 0) {
             Walk w;
-            w.init(a, blockIdx.x, gridDim.x);
+            w.init(a, a.stall ? a.tiles : (int64_t)blockIdx.x, gridDim.x);
             int st = 0;
             uint32_t ph = 0;
             int64_t si = 0, G = 0;
@@ -630,6 +632,13 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
         t.r0 = r0;
         t.nr = nr;
         t.status = status;
+        {
+            // test of the bounded waits (HIF_TC_TEST_STALL=1): the MMA thread
+            // issues nothing, the builders' stage-reuse waits run out after
+            // ~2 s and the call returns HIF_ETIMEOUT with the context intact
+            const char* e = getenv("HIF_TC_TEST_STALL");
+            t.stall = (e && atoi(e) != 0) ? 1 : 0;
+        }
         const int grid = (int)std::min<int64_t>(t.tiles, num_sms);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         {

@@ -119,3 +119,25 @@ def test_tc_sum_full_size_sampled_rows(P):
     err = np.abs(y[rows] - ref).max(axis=0)
     assert np.all(err <= 1e-13 * scale), err / scale
     fac.close()
+
+
+def test_tc_sum_bounded_wait_reports_timeout_and_context_survives(P):
+    # the MMA thread is told to issue nothing: the builders' waits for their
+    # shared-memory stages run out (~2 s), the kernel drains its copies,
+    # frees TMEM and returns; the call reports HIF_ETIMEOUT and the same
+    # handle then computes a correct sum
+    import os
+    from paper_1307_2666_gb300 import hif as H
+    pb = hi.volume_problem(64, 2, smooth_seed=4)
+    x = hi.gaussian_rhs(pb.N, 2, 6)
+    fac = handle(P, pb)
+    os.environ["HIF_TC_TEST_STALL"] = "1"
+    try:
+        with pytest.raises(H.HIFError) as err:
+            fac.matvec(T(x))
+        assert err.value.status == H.HIF_ETIMEOUT
+    finally:
+        os.environ.pop("HIF_TC_TEST_STALL", None)
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    close_cols(fac.matvec(T(x)).cpu().numpy(), op.matvec(x))
+    fac.close()
