@@ -38,7 +38,7 @@ ORACLE_SAMPLE_N = 64
 # DRAM bytes (read + write) of one 8-RHS launch of the tensor-core direct sum
 # at n = 1024, from one ncu capture (profiles/tc_conv_n1024_dram.md); valid
 # only for the kernel source with this sha256 prefix
-TC_TRAFFIC = {"n": 1024, "bytes": 116.76e9 + 95.09e6, "source_sha256": "ce53d56acc1c774f"}
+TC_TRAFFIC = {"n": 1024, "bytes": 116.40e9 + 92.49e6, "source_sha256": "6ed77bb75d683753"}
 
 
 def workload_config(n, nrhs, eps):
