@@ -359,3 +359,41 @@ def test_host_and_device_pointers_agree(lib):
     np.testing.assert_allclose(x_host, x_dev, rtol=1e-13, atol=1e-15)
     P.hif_destroy(h1)
     fac.close()
+
+
+def test_full_size_refined_solve_residual_by_oracle_rows(lib):
+    # the bench workload end to end: n = 1024 (N = 1,048,576), FP32
+    # factorization, 8 right-hand sides refined to 1e-10; the residual
+    # f - A u is then recomputed at sampled rows by the oracle's own FP64
+    # operator, independent of the GPU direct sum
+    P = lib
+    pb = hi.volume_problem(1024, 2, smooth_seed=1002, rhs_seed=1003, nrhs=8)
+    fac = factor(P, pb, 1e-6, precision="fp32")
+    u, its, rel = fac.solve_refined(T(pb.f), tol=1e-10)
+    assert rel <= 1e-10
+    u = u.cpu().numpy()
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    rng = np.random.default_rng(5)
+    rows = rng.choice(pb.N, 24, replace=False)
+    r = pb.f[rows] - op.matvec_rows(u, rows)
+    # rows of a residual of relative norm <= 1e-10: every sampled entry is
+    # bounded by the whole residual's norm
+    assert np.all(np.abs(r) <= 1e-10 * np.linalg.norm(pb.f, axis=0)[None, :])
+    fac.close()
+
+
+@pytest.mark.slow
+def test_full_size_3d_refined_solve_residual_by_oracle_rows(lib):
+    # the 3D workload: n = 64 cube (N = 262,144), eps = 1e-3, FP32
+    # factorization, 16 right-hand sides refined to 1e-10
+    P = lib
+    pb = hi.volume_problem(64, 3, smooth_seed=2002, rhs_seed=2003, nrhs=16)
+    fac = factor(P, pb, 1e-3, precision="fp32")
+    u, its, rel = fac.solve_refined(T(pb.f), tol=1e-10, maxit=60)
+    assert rel <= 1e-10
+    u = u.cpu().numpy()
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 1)
+    rows = np.random.default_rng(6).choice(pb.N, 16, replace=False)
+    r = pb.f[rows] - op.matvec_rows(u, rows)
+    assert np.all(np.abs(r) <= 1e-10 * np.linalg.norm(pb.f, axis=0)[None, :])
+    fac.close()
