@@ -47,6 +47,15 @@ Readings of points the paper leaves open (the GPU path uses the same ones):
     order, each in pivot order; redundants: groups in order, each ascending.
  7. A Schur update is recorded (S and M over skel x skel) only when the box
     eliminated something and kept a skeleton.
+ 8. Symmetry (Sec. 5, opening paragraph): when A is symmetric the one-sided
+    Y'_c = [A_{cN,c}; Y_{cE,c}] is compressed instead of Y_c.  A is taken
+    as symmetric when b = c entrywise and all weights w_j are equal, the
+    sufficient form of b_i w_j c_j = b_j w_i c_i for all i != j.  The
+    dropped rows repeat the kept ones (the active matrix A + S stays
+    symmetric under symmetric elimination), so Y_c^T Y_c = 2 Y'_c^T Y'_c and
+    the pivoted QR picks the same skeletons with the same T.  The diagonal
+    blocks B_rr are still factored by LU with partial pivoting: the paper's
+    LDL changes how the block inverse is formed, not its value.
 """
 from __future__ import annotations
 
@@ -294,9 +303,17 @@ def sublevel_plan(dim: int, L: int, fractional: bool = True, skip_levels: int = 
 
 def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
            *, second_kind: bool = True, occupancy: int = 64, proxy_radius: float = 1.5,
-           fractional: bool = True, skip_levels: int = 0, trace=None) -> HIFFactor:
-    """HIF-IE (Algorithm 4.1 / 4.2) of A = diag(a) + diag(b) K diag(c)."""
+           fractional: bool = True, skip_levels: int = 0, symmetric=None, trace=None) -> HIFFactor:
+    """HIF-IE (Algorithm 4.1 / 4.2) of A = diag(a) + diag(b) K diag(c).
+
+    ``symmetric``: None compresses Y'_c exactly when ``is_symmetric`` holds,
+    False always compresses the full Y_c, True requires ``is_symmetric``.
+    """
     op = Operator(points, weights, a, b, c, kernel_id)
+    if symmetric is None:
+        symmetric = is_symmetric(op)
+    elif symmetric and not is_symmetric(op):
+        raise ValueError("symmetric=True needs b == c and equal weights")
     x = op.x
     N, d = x.shape
     proxy_dirs = np.asarray(proxy_dirs, dtype=np.float64)
@@ -333,7 +350,7 @@ def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
             if cbox.size == 0:
                 continue
             bf = _skeletonize(op, S, M, snapshot, cbox, ctr[bid], R2, proxy_radius * w,
-                              proxy_dirs, eps, second_kind)
+                              proxy_dirs, eps, second_kind, bool(symmetric))
             sl.boxes.append(bf)
             active[bf.rd] = False
             if trace is not None:
@@ -344,6 +361,11 @@ def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
     top_A = op.entries(top, top) + S[np.ix_(top, top)]
     top_lu = lu_factor(top_A) if top.size else None
     return HIFFactor(N=N, sublevels=sublevels, top=top, top_A=top_A, top_lu=top_lu)
+
+
+def is_symmetric(op: Operator) -> bool:
+    """Sufficient test for A = A^T: b = c entrywise and equal weights."""
+    return bool(np.array_equal(op.b, op.c) and np.all(op.w == op.w[0]))
 
 
 def sci_groups(pattern: np.ndarray):
@@ -360,7 +382,7 @@ def sci_groups(pattern: np.ndarray):
 
 
 def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_dirs,
-                 eps, second_kind) -> BoxFactor:
+                 eps, second_kind, symmetric=False) -> BoxFactor:
     x = op.x
     n = cbox.size
     inbox = np.zeros(op.N, dtype=bool)
@@ -371,17 +393,22 @@ def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_d
     sci = cand & M[:, cbox].any(axis=1)
     cN = np.nonzero(near | sci)[0]
 
-    # Y_c of Eq. (3.3), split as Y^K (kernel + proxy) and Y^S (SCI)
+    # Y_c of Eq. (3.3), split as Y^K (kernel + proxy) and Y^S (SCI); for a
+    # symmetric A the one-sided Y'_c of Sec. 5 (reading 8)
     xE = center[None, :] + radius * proxy_dirs
     YK_near1 = op.kernel_entries(cN, cbox)
-    YK_near2 = op.kernel_entries(cbox, cN).T
     dE = xE[:, None, :] - x[cbox][None, :, :]
     gE = green(op.kernel_id, np.sqrt((dE * dE).sum(axis=2)))          # P x n
     YK_out = gE * (op.w[cbox] * op.c[cbox])[None, :]
-    YK_in = gE * (op.b[cbox] * op.w[cbox])[None, :]
-    YK = np.vstack([YK_near1, YK_near2, YK_out, YK_in])
-    YS = np.vstack([S[np.ix_(cN, cbox)], S[np.ix_(cbox, cN)].T,
-                    np.zeros((2 * proxy_dirs.shape[0], n))])
+    if symmetric:
+        YK = np.vstack([YK_near1, YK_out])
+        YS = np.vstack([S[np.ix_(cN, cbox)], np.zeros((proxy_dirs.shape[0], n))])
+    else:
+        YK_near2 = op.kernel_entries(cbox, cN).T
+        YK_in = gE * (op.b[cbox] * op.w[cbox])[None, :]
+        YK = np.vstack([YK_near1, YK_near2, YK_out, YK_in])
+        YS = np.vstack([S[np.ix_(cN, cbox)], S[np.ix_(cbox, cN)].T,
+                        np.zeros((2 * proxy_dirs.shape[0], n))])
     Y = YK + YS
     m = Y.shape[0]
 

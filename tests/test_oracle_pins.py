@@ -356,6 +356,79 @@ def test_accuracy_bounds_2d(eps):
     assert abs(F.solve(x) @ y - x @ F.solve_transpose(y)) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
 
 
+def test_symmetry_test_matches_dense_transpose():
+    # b = c with equal weights gives A = A^T; b != c or unequal weights do not
+    pb, op = _setup(8, smooth=5)
+    A = op.dense()
+    assert hifie.is_symmetric(op)
+    assert np.allclose(A, A.T, rtol=1e-15, atol=0)
+    c2 = pb.c * (1.0 + 0.1 * hi.smooth_field(pb.points, 6))
+    op2 = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, c2, 0)
+    A2 = op2.dense()
+    assert not hifie.is_symmetric(op2)
+    assert np.abs(A2 - A2.T).max() > 1e-6 * np.abs(A2).max()
+    w3 = pb.weights.copy()
+    w3[0] *= 1.5
+    op3 = kernels.Operator(pb.points, w3, pb.a, pb.b, pb.c, 0)
+    assert not hifie.is_symmetric(op3)
+    assert not np.allclose(op3.dense(), op3.dense().T, rtol=1e-12, atol=0)
+    with pytest.raises(ValueError):
+        hifie.factor(pb.points, pb.weights, pb.a, pb.b, c2, 0, 1e-6, pb.proxy, symmetric=True)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_symmetric_compression_equals_full_sec_5(eps):
+    # Sec. 5: for symmetric A the one-sided Y'_c holds every row of Y_c once,
+    # so Y_c^T Y_c = 2 Y'_c^T Y'_c: the same skeletons in the same pivot
+    # order with half the rows, and the same factorization F.  T itself is
+    # only as stable as the ID's R_11 (rounding in the SCI blocks moves it by
+    # up to ~1e-16 / eps^2 on the later sublevels), so it is compared on the
+    # first sublevel, and F as an operator
+    pb, op = _setup(32, smooth=1002)
+    Fs = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, eps, pb.proxy, symmetric=True)
+    Ff = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, eps, pb.proxy, symmetric=False)
+    assert len(Fs.sublevels) == len(Ff.sublevels)
+    nbox = 0
+    for t, (ss, sf) in enumerate(zip(Fs.sublevels, Ff.sublevels)):
+        assert len(ss.boxes) == len(sf.boxes)
+        for bs, bf in zip(ss.boxes, sf.boxes):
+            assert 2 * bs.m == bf.m
+            assert np.array_equal(bs.sk, bf.sk) and np.array_equal(bs.rd, bf.rd)
+            if t == 0 and bs.T.size:
+                assert np.abs(bs.T - bf.T).max() <= 1e-6 * max(1.0, np.abs(bf.T).max())
+            nbox += 1
+    assert nbox >= 40
+    assert np.array_equal(Fs.top, Ff.top)
+    x = np.random.default_rng(2).standard_normal(op.N)
+    for fs, ff in ((Fs.apply, Ff.apply), (Fs.solve, Ff.solve), (Fs.solve_transpose, Ff.solve_transpose)):
+        ys, yf = fs(x), ff(x)
+        assert np.linalg.norm(ys - yf) <= 1e-12 * np.linalg.norm(yf)
+
+
+def test_nonsymmetric_accuracy_full_compression():
+    # b != c: the full Y_c is compressed and the factorization keeps the
+    # accuracy of the symmetric case (Theorem 3.1 / Sec. 4 error model)
+    pb, _ = _setup(32, smooth=1002)
+    c = 1.0 + 0.5 * hi.smooth_field(pb.points, 1003)
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, c, 0)
+    assert not hifie.is_symmetric(op)
+    eps = 1e-6
+    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, c, 0, eps, pb.proxy)
+    P = pb.proxy.shape[0]
+    Fs = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.b, 0, eps, pb.proxy)
+    # two rows per near-field DOF and per proxy point, against one when b = c
+    assert all(bf.m % 2 == 0 and bf.m >= 2 * P for sl in F.sublevels for bf in sl.boxes)
+    assert all(bf.m >= P for sl in Fs.sublevels for bf in sl.boxes)
+    assert sum(bf.m for sl in Fs.sublevels for bf in sl.boxes) < sum(bf.m for sl in F.sublevels for bf in sl.boxes)
+    ds = dense.DenseSolver(op)
+    x = np.random.default_rng(0).standard_normal(op.N)
+    Ax = ds.matvec(x)
+    assert np.linalg.norm(F.apply(x) - Ax) <= 10 * eps * np.linalg.norm(Ax)
+    f = pb.f[:, 0]
+    u = ds.solve(f)
+    assert np.linalg.norm(F.solve(f) - u) <= 100 * eps * np.linalg.norm(u)
+
+
 def test_second_kind_fix_matters_sec_4_4():
     # Sec. 4.4 / Example 2: without the rho_c tolerance and split compression the
     # error of hifie2 grows well above that of hifie2x (4.1e-4 vs 5.9e-7 at 512^2).
