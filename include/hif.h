@@ -72,6 +72,10 @@ typedef struct {
     int autotune;           /* time the candidate CTA sizes of every sublevel's sweep after
                                the factorization and keep the fastest (default 1; the
                                sweep's arithmetic does not depend on it)                   */
+    int symmetric;          /* 1 (default): when b == c and all weights are equal, A is
+                               symmetric and the one-sided proxy matrix Y'_c = [A_{cN,c};
+                               Y_{cE,c}] is compressed (Sec. 5; same ID, half the rows);
+                               0: always the full Y_c of Eq. (3.3)                        */
 } hif_options;
 
 typedef struct {
@@ -89,6 +93,8 @@ typedef struct {
     double factor_seconds;  /* wall time of hif_factor                                     */
     double flops;           /* algorithmic FP work of the factorization (see DESIGN)       */
     double kernel_evals;    /* kernel evaluations spent on the proxy matrices Y_c          */
+    int64_t proxy_rows;     /* rows of all proxy matrices compressed (Y_c or Y'_c)         */
+    int symmetric_problems; /* problems whose A was symmetric and compressed through Y'_c  */
 } hif_stats_t;
 
 /* Defaults for dimension dim (2 or 3): occupancy 64, second_kind 1, FP64,

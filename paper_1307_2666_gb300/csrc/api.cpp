@@ -114,6 +114,7 @@ struct Segment {
     Tree tree{};
     std::vector<int> kinds, levels;
     bool grid = false;
+    bool sym = false;             // b == c and equal weights: A symmetric, Y'_c compressed (Sec. 5)
     int gn = 0;
     double gh = 0;
     DevMem dof_of, table, table_df;
@@ -300,7 +301,7 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
         const BoxDesc& b = bd[bI];
         BigBox x{};
         x.box = bI;
-        x.m = 2 * (b.m_near + h->P);
+        x.m = (b.sym ? 1 : 2) * (b.m_near + h->P);
         x.y_off = yoff;
         yoff += (int64_t)x.m * b.n;
         max_entries = std::max(max_entries, (int64_t)(b.m_near + h->P) * b.n);
@@ -604,6 +605,7 @@ static void run_factor(hif_handle h) {
         p.near_off.assign(1, 0);
         p.grp_off.assign(1, 0);
         std::vector<double> radius;
+        std::vector<int> symv;
         int kind = -1, ell = -1;
         for (auto& sp : h->segs) {
             Segment& sg = *sp;
@@ -623,6 +625,7 @@ static void run_factor(hif_handle h) {
                               sci, ps);
             append_plan(p, ps);
             radius.insert(radius.end(), ps.nbox, h->opt.proxy_radius * wl);
+            symv.insert(symv.end(), ps.nbox, sg.sym ? 1 : 0);
         }
         const int nb = p.nbox;
         const int64_t ngr = p.grp_off[nb];
@@ -642,6 +645,7 @@ static void run_factor(hif_handle h) {
             b.m_near = (int)(p.near_off[bI + 1] - p.near_off[bI]);
             b.ngroups = (int)(p.grp_off[bI + 1] - p.grp_off[bI]);
             b.has_sci = p.box_sci[bI];
+            b.sym = symv[bI];
             b.col_off = p.box_off[bI];
             b.near_off = p.near_off[bI];
             b.grp_off = p.grp_off[bI];
@@ -655,8 +659,9 @@ static void run_factor(hif_handle h) {
                 maxn = std::max(maxn, b.n);
                 if (b.has_sci) any_sci = true;
             }
-            const double m = 2.0 * (b.m_near + h->P);
-            evals += (m / 2) * b.n;
+            const double m = (b.sym ? 1.0 : 2.0) * (b.m_near + h->P);
+            h->stats.proxy_rows += (int64_t)m;
+            evals += (double)(b.m_near + h->P) * b.n;
             flops += 2.0 * m * b.n * b.n;
             for (int q = 0; q < b.ngroups; ++q) {
                 const int64_t gi = b.grp_off + q;
@@ -1411,6 +1416,7 @@ hif_status hif_options_default(int dim, hif_options* opt) {
     opt->direct_precision = 2;
     opt->use_graphs = 1;
     opt->autotune = 1;
+    opt->symmetric = 1;
     opt->root_width = 0.0;
     opt->stream = nullptr;
     return HIF_OK;
@@ -1437,6 +1443,7 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
     if (opt.leaf_occupancy < 1 || opt.proxy_points < 1 || !(opt.proxy_radius > 0)) return HIF_EINVAL;
     if (opt.precision != 0 && opt.precision != 1) return HIF_EINVAL;
     if (opt.direct_precision < 0 || opt.direct_precision > 2) return HIF_EINVAL;
+    if (opt.symmetric != 0 && opt.symmetric != 1) return HIF_EINVAL;
     if (opt.dim == 3 && !opt.proxy_dirs) return HIF_EINVAL;
     auto h = std::make_unique<hif_handle_s>();
     const auto t0 = std::chrono::steady_clock::now();
@@ -1502,6 +1509,17 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
                 fail(HIF_ENUMERIC, "non-finite or non-positive input");
             for (int k = 0; k < d; ++k)
                 if (!std::isfinite(h->hx[d * i + k])) fail(HIF_ENUMERIC, "non-finite point");
+        }
+        // A = diag(a) + diag(b) K diag(c) with K_ij = G_ij w_j is symmetric
+        // when b_i w_j c_j = b_j w_i c_i; tested in the sufficient form b = c
+        // and equal weights, problem by problem
+        for (auto& sp : h->segs) {
+            Segment& sg = *sp;
+            bool sym = opt.symmetric != 0;
+            for (int64_t i = sg.off; sym && i < sg.off + sg.N; ++i)
+                sym = hbv[i] == hc[i] && h->hw[i] == h->hw[sg.off];
+            sg.sym = sym;
+            h->stats.symmetric_problems += sym ? 1 : 0;
         }
         // proxy directions
         h->P = opt.proxy_points;

@@ -41,6 +41,8 @@ struct BoxDesc {
     int m_near;           // |c^N|
     int ngroups;
     int has_sci;          // any SCI touches the box (Grams for rho are needed)
+    int sym;              // A symmetric: one row per near-field DOF / proxy point (Y'_c, Sec. 5)
+    int pad0;
     int64_t col_off;      // into cols[]
     int64_t near_off;     // into near[]
     int64_t grp_off;      // first group index

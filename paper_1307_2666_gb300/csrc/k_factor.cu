@@ -2,7 +2,9 @@
 //
 //  fold_kernel   one CTA per box c: generates the proxy matrix Y_c of Eq. (3.3)
 //                (near-field rows A_{cN,c}, A_{c,cN}^T and proxy rows of
-//                Lemma 3.3) chunk by chunk in shared memory and folds every
+//                Lemma 3.3; for symmetric A only A_{cN,c} and the outgoing
+//                proxy rows, the Y'_c of Sec. 5, which has the same ID)
+//                chunk by chunk in shared memory and folds every
 //                chunk into the triangular factor R_c of Y_c = Q_c R_c by
 //                Householder reflections; Y_c itself never reaches HBM.  In
 //                second-kind mode it also accumulates the Gram matrices of the
@@ -46,6 +48,8 @@ __global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
     const int n = bx.n;
     const int bp = args.bpairs;          // row pairs per chunk
     const int rows = 2 * bp;
+    const bool sym = bx.sym != 0;        // one row per pair: Y'_c
+    const int ppc = sym ? rows : bp;     // pairs per chunk
     const int ldc = rows + 1;            // odd leading dimension: conflict-free columns
     const int nsub = args.sci.nsub;
     const bool scival = bx.has_sci && nsub > 0;          // SCI entries present in Y_c
@@ -61,10 +65,10 @@ __global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
     T* cbw = align_ptr<T>(sp, n);
     int* cid = align_ptr<int>(sp, n);
     int* cgrp_end = align_ptr<int>(sp, n);          // end column of the column's group
-    T* rxl = align_ptr<T>(sp, (size_t)bp * 3);
-    T* rb = align_ptr<T>(sp, bp);
-    T* rwc = align_ptr<T>(sp, bp);
-    int* rid = align_ptr<int>(sp, bp);
+    T* rxl = align_ptr<T>(sp, (size_t)rows * 3);
+    T* rb = align_ptr<T>(sp, rows);
+    T* rwc = align_ptr<T>(sp, rows);
+    int* rid = align_ptr<int>(sp, rows);
     T* CK = align_ptr<T>(sp, (size_t)ldc * n);
     T* CS = sci ? align_ptr<T>(sp, (size_t)ldc * n) : nullptr;
     T* hh = align_ptr<T>(sp, 4);
@@ -100,10 +104,10 @@ __global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
     __syncthreads();
 
     const int npairs = bx.m_near + args.P;
-    for (int p0 = 0; p0 < npairs; p0 += bp) {
-        const int np = min(bp, npairs - p0);
+    for (int p0 = 0; p0 < npairs; p0 += ppc) {
+        const int np = min(ppc, npairs - p0);
         // ---- row data of this chunk
-        for (int q = threadIdx.x; q < bp; q += blockDim.x) {
+        for (int q = threadIdx.x; q < ppc; q += blockDim.x) {
             const int p = p0 + q;
             if (q >= np) {
                 rid[q] = -2;
@@ -126,22 +130,26 @@ __global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
             }
         }
         __syncthreads();
-        // ---- generate the chunk: rows (2q, 2q+1) = (outgoing, incoming) of pair q
+        // ---- generate the chunk: rows (2q, 2q+1) = (outgoing, incoming) of
+        // pair q, or row q = outgoing alone for symmetric A
         for (int l = threadIdx.x; l < n; l += blockDim.x) {
             const T xj0 = cxl[3 * l], xj1 = cxl[3 * l + 1], xj2 = cxl[3 * l + 2];
             const int j = cid[l];
-            for (int q = 0; q < bp; ++q) {
+            for (int q = 0; q < ppc; ++q) {
                 T k1, k2, s1, s2;
                 y_pair<T>(kid, rid[q], rxl[3 * q], rxl[3 * q + 1], rxl[3 * q + 2], rb[q], rwc[q], j, xj0, xj1, xj2,
                           cwc[l], cb[l], cbw[l], scival, args.sci, k1, k2, s1, s2);
+                const int i1 = sym ? q : 2 * q;
                 if (sci) {
-                    CK[2 * q + ldc * l] = k1;
-                    CK[2 * q + 1 + ldc * l] = k2;
-                    CS[2 * q + ldc * l] = s1;
-                    CS[2 * q + 1 + ldc * l] = s2;
+                    CK[i1 + ldc * l] = k1;
+                    CS[i1 + ldc * l] = s1;
+                    if (!sym) {
+                        CK[i1 + 1 + ldc * l] = k2;
+                        CS[i1 + 1 + ldc * l] = s2;
+                    }
                 } else {
-                    CK[2 * q + ldc * l] = k1 + s1;
-                    CK[2 * q + 1 + ldc * l] = k2 + s2;
+                    CK[i1 + ldc * l] = k1 + s1;
+                    if (!sym) CK[i1 + 1 + ldc * l] = k2 + s2;
                 }
             }
         }
@@ -614,7 +622,7 @@ size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem) {
     size_t b = 0;
     b += (size_t)n * 6 * elem + 64;       // cxl, cwc, cb, cbw
     b += (size_t)n * 8 + 32;              // cid, cgrp_end
-    b += (size_t)bpairs * (5 * elem + 4) + 64;
+    b += 2 * (size_t)bpairs * (5 * elem + 4) + 64;   // row data for up to 2 bpairs rows
     b += rows * n * elem * (sci ? 2 : 1) + 32;
     b += 4 * elem + 16;
     if (R_in_smem) b += (size_t)n * n * elem + 16;

@@ -32,6 +32,7 @@ __global__ void big_ygen_kernel(BigArgs a) {
     const int dim = a.g.dim;
     const bool scival = bx.has_sci && a.sci.nsub > 0;
     const bool split = scival && a.second_kind;
+    const bool sym = bx.sym != 0;        // Y'_c: outgoing rows only (Sec. 5)
     T* YK = static_cast<T*>(a.YK) + bb.y_off;
     T* YS = split ? static_cast<T*>(a.YS) + bb.y_off : nullptr;
     const int64_t m = bb.m;
@@ -66,7 +67,10 @@ __global__ void big_ygen_kernel(BigArgs a) {
         y_pair<T>(a.g.kernel_id, rid, rx0, rx1, rx2, rb, rwc, j, cx0, cx1, cx2, (T)(a.g.w[j] * a.g.c[j]),
                   (T)a.g.b[j], (T)(a.g.b[j] * a.g.w[j]), scival, a.sci, k1, k2, s1, s2);
         T* col = YK + m * l;
-        if (split) {
+        if (sym) {
+            col[p] = split ? k1 : k1 + s1;
+            if (split) YS[m * l + p] = s1;
+        } else if (split) {
             col[2 * p] = k1;
             col[2 * p + 1] = k2;
             YS[m * l + 2 * p] = s1;

@@ -37,6 +37,7 @@ class hif_options(C.Structure):
         ("direct_precision", C.c_int),
         ("use_graphs", C.c_int),
         ("autotune", C.c_int),
+        ("symmetric", C.c_int),
     ]
 
 
@@ -67,6 +68,8 @@ class hif_stats_t(C.Structure):
         ("factor_seconds", C.c_double),
         ("flops", C.c_double),
         ("kernel_evals", C.c_double),
+        ("proxy_rows", C.c_int64),
+        ("symmetric_problems", C.c_int),
     ]
 
 
@@ -241,7 +244,7 @@ def hif_stats(h) -> dict:
     return {
         "N": s.N, "dim": s.dim, "levels": s.levels, "sublevels": n, "top_size": s.top_size,
         "factor_bytes": s.factor_bytes, "factor_seconds": s.factor_seconds, "flops": s.flops,
-        "kernel_evals": s.kernel_evals,
+        "kernel_evals": s.kernel_evals, "proxy_rows": s.proxy_rows, "symmetric_problems": s.symmetric_problems,
         "per_sublevel": [dict(kind=kind[s.kinds[i]], boxes=s.boxes[i], skeletons=s.skeletons[i],
                               redundant=s.redundant[i], max_box=s.max_box[i]) for i in range(n)],
     }

@@ -68,7 +68,13 @@ def test_batched_equals_individual_and_dense(P, precision):
         # block diagonal direct sum
         np.testing.assert_allclose(yb[off[q]:off[q + 1]], op.matvec(pb.f), rtol=1e-12, atol=1e-13)
         fi.close()
-    assert fb.stats()["top_size"] == tops
+    if precision == "fp64":
+        assert fb.stats()["top_size"] == tops
+    else:
+        # FP32: the batched and the single-problem factorizations run
+        # different launches (one plan for all problems), whose rounding
+        # differs; a rank at the tolerance can move by one
+        assert abs(fb.stats()["top_size"] - tops) <= max(2, 0.005 * tops)
     fb.close()
 
 
