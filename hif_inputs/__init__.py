@@ -70,6 +70,12 @@ def gaussian_rhs(N: int, nrhs: int, seed: int) -> np.ndarray:
     return np.asfortranarray(rng.standard_normal((N, nrhs)))
 
 
+def uniform_vector(N: int, seed: int) -> np.ndarray:
+    """N standard uniform values on [0, 1): the start vector of the power
+    iterations and the right-hand side of the first-kind GMRES runs."""
+    return np.random.default_rng(seed).uniform(size=N)
+
+
 def proxy_directions(dim: int, count: int | None = None, seed: int = 7) -> np.ndarray:
     """Unit vectors of the proxy surface (Sec. 3.3).
 

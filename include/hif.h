@@ -184,6 +184,24 @@ hif_status hif_solve_refined(hif_handle h, int trans, const double* f, double* u
                              int64_t nrhs, int64_t ld, double tol, int maxit, int method,
                              int* iters, double* relres);
 
+/*
+ * hif_error_estimates -- the a posteriori operator errors of Sec. 5 by power
+ * iteration on E^T E: norms[0] ~ |A|, norms[1] ~ |A - F| and
+ * norms[2] ~ |I - A F^{-1}| (2-norms), so e_a = norms[1] / norms[0] and
+ * e_s = norms[2].  Each run starts from v0 / |v0| (N values, host or device;
+ * the paper uses a standard uniform random vector), takes w = E v,
+ * u = E^T w, the estimate sqrt(|u|) and v = u / |u|, and stops when the
+ * estimate moved by at most rtol of itself (the paper: 1e-2) or after maxit
+ * steps.  A is applied by the direct sum of hif_matvec, F by the factored
+ * form.  For a batched handle the operators are block diagonal and each norm
+ * is the largest over the problems.
+ *   iters   (may be NULL) receives the three step counts
+ * Returns HIF_ENOTCONV (norms still filled) when a run reached maxit, and
+ * HIF_EINVAL for a zero or non-finite v0.
+ */
+hif_status hif_error_estimates(hif_handle h, const double* v0, double rtol, int maxit,
+                               double* norms, int* iters);
+
 /* Factorization statistics (Sec. 5 columns |s_L|, m_f, t_f and ranks per sublevel). */
 hif_status hif_stats(hif_handle h, hif_stats_t* st);
 

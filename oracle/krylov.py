@@ -87,28 +87,37 @@ def refine(matvec, f, solve, tol=1e-10, maxit=50):
     return u, maxit, hist
 
 
-def power_norm(apply_op, apply_op_t, N, seed=0, rtol=1e-2, maxit=200):
-    """|E|_2 by power iteration on E^T E from a standard uniform start."""
-    rng = np.random.default_rng(seed)
-    v = rng.uniform(size=N)
+def power_norm(apply_op, apply_op_t, N, seed=0, rtol=1e-2, maxit=200, v0=None, return_iters=False):
+    """|E|_2 by power iteration on E^T E from a standard uniform start (Sec. 5).
+
+    v <- v / |v|; each step w = E^T E v, estimate sqrt(|w|), v = w / |w|; stop
+    when the estimate moved by at most rtol of itself.  ``v0`` replaces the
+    seeded start vector when given."""
+    if v0 is None:
+        rng = np.random.default_rng(seed)
+        v = rng.uniform(size=N)
+    else:
+        v = np.array(v0, dtype=np.float64)
     v /= np.linalg.norm(v)
     est = 0.0
-    for _ in range(maxit):
+    it = 0
+    for it in range(1, maxit + 1):
         w = apply_op_t(apply_op(v))
         nw = np.linalg.norm(w)
         if nw == 0.0:
-            return 0.0
+            return (0.0, it) if return_iters else 0.0
         new = np.sqrt(nw)
         v = w / nw
         if est > 0.0 and abs(new - est) <= rtol * new:
-            return new
+            return (new, it) if return_iters else new
         est = new
-    return est
+    return (est, it) if return_iters else est
 
 
-def error_estimates(A_mv, At_mv, F_mv, Ft_mv, Fi_mv, Fit_mv, N, seed=0):
+def error_estimates(A_mv, At_mv, F_mv, Ft_mv, Fi_mv, Fit_mv, N, seed=0, v0=None, rtol=1e-2, maxit=200):
     """(e_a, e_s) of Sec. 5: |A - F| / |A| and |I - A F^{-1}|."""
-    nA = power_norm(A_mv, At_mv, N, seed)
-    nE = power_norm(lambda v: A_mv(v) - F_mv(v), lambda v: At_mv(v) - Ft_mv(v), N, seed)
-    nS = power_norm(lambda v: v - A_mv(Fi_mv(v)), lambda v: v - Fit_mv(At_mv(v)), N, seed)
+    kw = dict(seed=seed, v0=v0, rtol=rtol, maxit=maxit)
+    nA = power_norm(A_mv, At_mv, N, **kw)
+    nE = power_norm(lambda v: A_mv(v) - F_mv(v), lambda v: At_mv(v) - Ft_mv(v), N, **kw)
+    nS = power_norm(lambda v: v - A_mv(Fi_mv(v)), lambda v: v - Fit_mv(At_mv(v)), N, **kw)
     return nE / nA, nS

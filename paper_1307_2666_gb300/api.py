@@ -132,6 +132,14 @@ class Factorization:
                                             0 if method == "ir" else 1)
         return out, its, rel
 
+    def error_estimates(self, v0, rtol: float = 1e-2, maxit: int = 200) -> dict:
+        """e_a ~ |A - F| / |A| and e_s ~ |I - A F^{-1}| (Sec. 5) by power
+        iteration from the start vector v0 (N,)."""
+        norms, its, conv = _h.hif_error_estimates(self.h, v0.contiguous() if hasattr(v0, "contiguous") else v0,
+                                                  rtol, maxit)
+        return {"e_a": norms[1] / norms[0], "e_s": norms[2], "norm_A": norms[0], "norm_E": norms[1],
+                "iters": its, "converged": conv}
+
     def stats(self) -> dict:
         return _h.hif_stats(self.h)
 

@@ -1173,11 +1173,10 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
     }
 }
 
-static void solve_dev(hif_handle h, int trans, const double* b, double* x, int nrhs) {
-    // x = F^{-1} b or F^{-T} b, device arrays with ld = N
+// x = F^{-1} b, F b, F^{-T} b or F^T b (op 0, 1, 2, 3) on device arrays with ld = N
+static void fac_dev(hif_handle h, int op, const double* b, double* x, int nrhs) {
     const cudaStream_t st = h->st;
     const int64_t N = h->N;
-    const int op = trans ? 2 : 0;
     if (h->precision == 0) {
         h->work.ensure(sizeof(double) * N * nrhs);
         double* xw = h->work.as<double>();
@@ -1191,6 +1190,10 @@ static void solve_dev(hif_handle h, int trans, const double* b, double* x, int n
         sweep_all<float>(h, xw, N, nrhs, op);
         HIF_CUDA(launch_from_work<float>(xw, N, x, N, N, nrhs, st));
     }
+}
+
+static void solve_dev(hif_handle h, int trans, const double* b, double* x, int nrhs) {
+    fac_dev(h, trans ? 2 : 0, b, x, nrhs);
 }
 
 static std::vector<double> col_norms(hif_handle h, const double* v, int nrhs) {
@@ -1241,6 +1244,69 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
     if (iters) *iters = it;
     if (relres) *relres = worst;
     return worst <= tol ? HIF_OK : HIF_ENOTCONV;
+}
+
+// |E|_2 by power iteration on E^T E (Sec. 5) for E_0 = A, E_1 = A - F and
+// E_2 = I - A F^{-1}, run side by side as the three columns of one block so
+// that each step costs one direct sum with A and one with A^T: v = v0 / |v0|;
+// every step w = E v, u = E^T w, the estimate sqrt(|u|), v = u / |u|; a
+// column stops when its estimate moved by at most rtol of itself, or after
+// maxit steps.  A is the direct sum, F the factored form.
+static bool power_norms_dev(hif_handle h, const double* v0, double rtol, int maxit, double* norms, int* iters) {
+    const int64_t N = h->N;
+    const cudaStream_t st = h->st;
+    DevMem V, X, W, U, Tv;
+    V.ensure(sizeof(double) * N * 3);
+    X.ensure(sizeof(double) * N * 3);
+    W.ensure(sizeof(double) * N * 3);
+    U.ensure(sizeof(double) * N * 3);
+    Tv.ensure(sizeof(double) * N);
+    double* vp = V.as<double>();
+    double* xp = X.as<double>();
+    double* wp = W.as<double>();
+    double* up = U.as<double>();
+    double* tp = Tv.as<double>();
+    HIF_CUDA(cudaMemcpyAsync(tp, v0, sizeof(double) * N,
+                             is_device_ptr(v0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    const double n0 = col_norms(h, tp, 1)[0];
+    if (!(n0 > 0) || !std::isfinite(n0)) fail(HIF_EINVAL, "start vector must be finite and nonzero");
+    for (int c = 0; c < 3; ++c) HIF_CUDA(launch_axpby(N, 1, 1.0 / n0, tp, N, 0.0, vp + N * c, N, st));
+    double est[3] = {0.0, 0.0, 0.0};
+    bool done[3] = {false, false, false};
+    for (int c = 0; c < 3; ++c) iters[c] = 0;
+    for (int it = 1; it <= maxit && !(done[0] && done[1] && done[2]); ++it) {
+        // W = E V: A [v0, v1, F^{-1} v2], then column 1 minus F v1, column 2 = v2 - (.)
+        HIF_CUDA(cudaMemcpyAsync(xp, vp, sizeof(double) * N * 2, cudaMemcpyDeviceToDevice, st));
+        fac_dev(h, 0, vp + 2 * N, xp + 2 * N, 1);
+        matvec_dev(h, 0, xp, N, wp, N, 3);
+        fac_dev(h, 1, vp + N, tp, 1);
+        HIF_CUDA(launch_axpby(N, 1, -1.0, tp, N, 1.0, wp + N, N, st));
+        HIF_CUDA(launch_axpby(N, 1, 1.0, vp + 2 * N, N, -1.0, wp + 2 * N, N, st));
+        // U = E^T W: A^T W, then column 1 minus F^T w1, column 2 = w2 - F^{-T} (.)
+        matvec_dev(h, 1, wp, N, up, N, 3);
+        fac_dev(h, 3, wp + N, tp, 1);
+        HIF_CUDA(launch_axpby(N, 1, -1.0, tp, N, 1.0, up + N, N, st));
+        fac_dev(h, 2, up + 2 * N, tp, 1);
+        HIF_CUDA(launch_axpby(N, 1, 1.0, wp + 2 * N, N, 0.0, up + 2 * N, N, st));
+        HIF_CUDA(launch_axpby(N, 1, -1.0, tp, N, 1.0, up + 2 * N, N, st));
+        const std::vector<double> nu = col_norms(h, up, 3);
+        for (int c = 0; c < 3; ++c) {
+            if (done[c]) continue;
+            iters[c] = it;
+            if (!std::isfinite(nu[c])) fail(HIF_ENUMERIC, "non-finite power iterate");
+            if (nu[c] == 0.0) {
+                est[c] = 0.0;
+                done[c] = true;
+                continue;
+            }
+            const double nw = std::sqrt(nu[c]);
+            HIF_CUDA(launch_axpby(N, 1, 1.0 / nu[c], up + N * c, N, 0.0, vp + N * c, N, st));
+            if (est[c] > 0.0 && std::fabs(nw - est[c]) <= rtol * nw) done[c] = true;
+            est[c] = nw;
+        }
+    }
+    for (int c = 0; c < 3; ++c) norms[c] = est[c];
+    return done[0] && done[1] && done[2];
 }
 
 // Right-preconditioned GMRES(m), all columns advanced together, modified
@@ -1617,6 +1683,19 @@ hif_status hif_solve_refined(hif_handle h, int trans, const double* f, double* u
         });
     });
     return s != HIF_OK ? s : res;
+}
+
+hif_status hif_error_estimates(hif_handle h, const double* v0, double rtol, int maxit, double* norms, int* iters) {
+    if (!h || !v0 || !norms || !(rtol > 0) || maxit < 1) return HIF_EINVAL;
+    bool all = true;
+    const hif_status s = guard([&] {
+        int its[3];
+        all = power_norms_dev(h, v0, rtol, maxit, norms, its);
+        if (iters)
+            for (int c = 0; c < 3; ++c) iters[c] = its[c];
+    });
+    if (s != HIF_OK) return s;
+    return all ? HIF_OK : HIF_ENOTCONV;
 }
 
 hif_status hif_stats(hif_handle h, hif_stats_t* st) {

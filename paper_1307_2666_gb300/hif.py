@@ -86,6 +86,8 @@ EXPORTS = {
     "hif_matvec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "hif_solve_refined": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                     C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "hif_error_estimates": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int)]),
     "hif_stats": (C.c_int, [C.c_void_p, C.POINTER(hif_stats_t)]),
     "hif_destroy": (C.c_int, [C.c_void_p]),
     "hif_status_string": (C.c_char_p, [C.c_int]),
@@ -234,6 +236,16 @@ def hif_solve_refined(h, trans: int, f, u, tol: float = 1e-10, maxit: int = 50, 
                                   C.byref(it), C.byref(rr))
     _check(st, "hif_solve_refined", allow=(HIF_ENOTCONV,))
     return st, it.value, rr.value
+
+
+def hif_error_estimates(h, v0, rtol: float = 1e-2, maxit: int = 200):
+    """((|A|, |A - F|, |I - A F^{-1}|), (steps,) * 3, converged) by power
+    iteration from v0 (Sec. 5); e_a = norms[1] / norms[0], e_s = norms[2]."""
+    norms = (C.c_double * 3)()
+    its = (C.c_int * 3)()
+    st = load().hif_error_estimates(h, _ptr(v0), float(rtol), int(maxit), norms, its)
+    _check(st, "hif_error_estimates", allow=(HIF_ENOTCONV,))
+    return tuple(norms), tuple(its), st == HIF_OK
 
 
 def hif_stats(h) -> dict:

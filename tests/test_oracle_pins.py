@@ -501,6 +501,70 @@ def test_gmres_exact_preconditioner_one_step():
     assert its == 1
 
 
+def test_error_estimates_match_dense_two_norms():
+    # Sec. 5 estimators against the exact 2-norms of the assembled matrices
+    pb, op = _setup(16, smooth=4)
+    pb.a = np.zeros(op.N)                                     # first kind, Example 1
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    A = op.dense()
+    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, 1e-4, pb.proxy, occupancy=16)
+    I = np.eye(op.N)
+    Fd = F.apply(I)
+    Fi = F.solve(I)
+    ex_a = np.linalg.norm(A - Fd, 2) / np.linalg.norm(A, 2)
+    ex_s = np.linalg.norm(I - A @ Fi, 2)
+    mv = [lambda v: A @ v, lambda v: A.T @ v, F.apply, F.apply_transpose, F.solve, F.solve_transpose]
+    v0 = hi.uniform_vector(op.N, 3)
+    ea, es = krylov.error_estimates(*mv, op.N, v0=v0, rtol=1e-12, maxit=5000)
+    assert ea == pytest.approx(ex_a, rel=1e-6) and es == pytest.approx(ex_s, rel=1e-6)
+    # the paper's stopping rule: from below, within a few percent
+    ea2, es2 = krylov.error_estimates(*mv, op.N, v0=v0)
+    assert 0.8 * ex_a <= ea2 <= ex_a * (1 + 1e-12)
+    assert 0.8 * ex_s <= es2 <= ex_s * (1 + 1e-12)
+    # a planted rank-one error of known size
+    u = np.random.default_rng(1).standard_normal(op.N)
+    u /= np.linalg.norm(u)
+    d = 1e-3 * np.linalg.norm(A, 2)
+    nE = krylov.power_norm(lambda v: d * u * (u @ v), lambda v: d * u * (u @ v), op.N, v0=v0)
+    assert nE == pytest.approx(d, rel=1e-12)
+
+
+@pytest.mark.parametrize("eps,ni_max", [(1e-3, 8), (1e-6, 4), (1e-9, 3)])
+def test_first_kind_example_1_preconditioner(eps, ni_max):
+    # Example 1 (a = 0, b = c = 1): F approximates A to O(eps) while
+    # |I - A F^{-1}| is far larger (an ill-conditioned first-kind system),
+    # and GMRES with F^{-1} as preconditioner still needs only a few steps
+    pb = hi.volume_problem(32, 2, a_value=0.0)
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    A = op.dense()
+    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, eps, pb.proxy)
+    I = np.eye(op.N)
+    Fd = F.apply(I)
+    ea = np.linalg.norm(A - Fd, 2) / np.linalg.norm(A, 2)
+    es = np.linalg.norm(I - A @ np.linalg.inv(Fd), 2)
+    assert ea <= 10 * eps and es >= 20 * ea
+    f = hi.uniform_vector(op.N, 5)
+    u, its, hist = krylov.gmres(lambda v: A @ v, f, precond=F.solve, tol=1e-12)
+    assert hist[-1] <= 1e-12 and its <= ni_max
+    assert np.linalg.norm(u - np.linalg.solve(A, f)) <= 1e-8 * np.linalg.norm(u)
+
+
+def test_rsf_top_block_exceeds_hif():
+    # Algorithm 3.1 (cells only) against Algorithm 4.1: without the edge
+    # sublevels the top skeleton set |s_L| is larger, and it grows faster
+    # with N (Tables of Examples 1-2)
+    tops = {}
+    for n in (16, 32):
+        pb = hi.volume_problem(n, 2, a_value=0.0)
+        for frac in (True, False):
+            F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, 1e-6, pb.proxy, fractional=frac,
+                             occupancy=16)
+            assert all(sl.kind == "cell" for sl in F.sublevels) == (not frac)
+            tops[n, frac] = F.sL
+    assert tops[32, False] > tops[32, True] and tops[16, False] >= tops[16, True]
+    assert tops[32, False] - tops[16, False] > tops[32, True] - tops[16, True]
+
+
 def test_power_iteration_error_estimate():
     d = np.linspace(0.1, 2.0, 64)
     est = krylov.power_norm(lambda v: d * v, lambda v: d * v, 64, rtol=1e-6, maxit=2000)
