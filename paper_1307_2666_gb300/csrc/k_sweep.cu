@@ -165,10 +165,22 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     for (int e = threadIdx.x; e < r * nr; e += blockDim.x) x[rd[e % r] + a.ldx * (e / r)] = xr[e];
 }
 
+// Largest dynamic shared memory of any sweep launch: the callers batch the
+// right-hand sides so that (k + 2 r) * nrhs * sizeof(T) <= 200 KB.
+constexpr size_t kSweepSmemMax = 200 * 1024 + 64;
+
 template <typename T, int MODE>
 static cudaError_t launch_mode(const SweepArgs& a, int nbox, int threads, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (smem > kSweepSmemMax) return cudaErrorInvalidValue;
+    // The kernel's dynamic shared-memory limit is only ever raised, to the
+    // one fixed ceiling: launches captured in a CUDA graph keep their own
+    // sizes, and no later launch may lower the limit below what a captured
+    // node needs.
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSweepSmemMax);
+        if (e != cudaSuccess) return e;
+    }
     note_launch();
     sweep_kernel<T, MODE><<<nbox, threads, smem, st>>>(a);
     return cudaGetLastError();
