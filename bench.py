@@ -254,7 +254,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_solve = e0.elapsed_time(e1) / 1000.0
     t_factor = fac.stats()["factor_seconds"]
-    fp32_stats = dict(top=fac.stats()["top_size"], mf=fac.stats()["factor_bytes"])
+    st32 = fac.stats()
+    fp32_stats = dict(top=st32["top_size"], mf=st32["factor_bytes"], sym=st32["symmetric_problems"] > 0,
+                      rows=st32["proxy_rows"])
 
     # ---- dominant kernel: the tensor-core direct sum (one launch per 8 RHS),
     # timed with CUDA events on its own stream inside the timed steps above
@@ -332,6 +334,7 @@ def run_gpu(args):
             "config": dict(workload_config(n, nrhs, eps), parallelism=f"replicas x{world}"),
             "t_factor_s": t_factor, "t_solve_s": t_solve, "refine_iters": its, "relres": rel,
             "top_size": fp32_stats["top"], "factor_bytes": fp32_stats["mf"],
+            "symmetric_compression": fp32_stats["sym"], "proxy_rows": fp32_stats["rows"],
             "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks,
         }
