@@ -434,15 +434,16 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
-def run_example1(args):
-    """The rows of the paper's Example 1 tables (Sec. 5): the first-kind
-    volume IE a = 0, b = c = 1 on the n x n grid, factored in FP64 by HIF-IE
-    and by RSF (fractional levels off, Algorithm 3.1) at each eps.  One JSON
-    line per (method, eps) with |s_L|, t_f, m_f, t_a/s (one apply and one
-    solve, 1 RHS), e_a and e_s (power iteration from a uniform start, stopped
-    at 1e-2) and n_i (GMRES with F^{-1} as right preconditioner to 1e-12 from
-    a uniform random right-hand side).  As in the paper's Example 1 the
-    second-kind modifications of Sec. 4.4 are off unless --second-kind."""
+def run_examples(args):
+    """The rows of the paper's Example 1 and Example 2 tables (Sec. 5): the
+    volume IE with a = 0 (Example 1, first kind) or a = 1 (Example 2, second
+    kind), b = c = 1, on the n x n grid, factored in FP64 by RSF (``rsf``:
+    fractional levels off, Algorithm 3.1), by HIF-IE without the Sec. 4.4
+    modifications (``hif``, the paper's hifie2) and with them (``hifx``,
+    hifie2x).  One JSON line per (method, eps) with |s_L|, t_f, m_f, t_a/s
+    (one apply and one solve, 1 RHS), e_a and e_s (power iteration from a
+    uniform start, stopped at 1e-2) and n_i (GMRES with F^{-1} as right
+    preconditioner to 1e-12 from a uniform random right-hand side)."""
     import numpy as np
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -455,7 +456,8 @@ def run_example1(args):
     import paper_1307_2666_gb300 as P
     dev = torch.device(f"cuda:{local}")
     T = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev)
-    pb = hi.volume_problem(args.n, 2, a_value=0.0)
+    example = 2 if args.workload == "example2" else 1
+    pb = hi.volume_problem(args.n, 2, a_value=0.0 if example == 1 else 1.0)
     ins = [T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)]
     v0 = T(hi.uniform_vector(pb.N, 3))
     f = T(hi.uniform_vector(pb.N, 5))
@@ -475,10 +477,11 @@ def run_example1(args):
     w.apply(f)
     w.matvec(f)
     w.close()
-    for method in args.methods.split(","):
+    methods = args.methods or ("hif,rsf" if example == 1 else "hif,hifx,rsf")
+    for method in methods.split(","):
         for eps in [float(e) for e in args.eps_list.split(",")]:
-            t_f, fac = timed(lambda: P.Factorization(*ins, 0, eps, fractional=method == "hif",
-                                                     second_kind=args.second_kind))
+            t_f, fac = timed(lambda: P.Factorization(*ins, 0, eps, fractional=method != "rsf",
+                                                     second_kind=method == "hifx"))
             fac.apply(f)
             fac.solve(f)
             t_a = min(timed(lambda: fac.apply(f))[0] for _ in range(3))
@@ -487,8 +490,9 @@ def run_example1(args):
             t_g, (u, n_i, rel) = timed(lambda: fac.solve_refined(f, tol=1e-12, method="gmres"))
             st = fac.stats()
             line = {
-                "metric": "Example 1 table row (first-kind volume IE, Sec. 5)", "method": method,
-                "n": args.n, "N": pb.N, "eps": eps, "second_kind_mode": bool(args.second_kind), "dtype": "f64",
+                "metric": f"Example {example} table row ({'first' if example == 1 else 'second'}-kind volume IE, "
+                          "Sec. 5)", "method": method,
+                "n": args.n, "N": pb.N, "eps": eps, "second_kind_mode": method == "hifx", "dtype": "f64",
                 "data": "synthetic",
                 "s_L": st["top_size"], "t_f": t_f, "m_f_gb": st["factor_bytes"] / 1e9, "t_a": t_a, "t_s": t_s,
                 "e_a": est["e_a"], "e_s": est["e_s"], "power_iters": est["iters"], "t_estimates": t_e,
@@ -535,12 +539,13 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["grid", "batched", "example1"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "batched", "example1", "example2"], default="grid",
                     help="grid: the n x n bench workload (default); batched: independent problems in one handle; "
-                         "example1: the first-kind table rows of the paper (HIF-IE and RSF)")
-    ap.add_argument("--methods", default="hif,rsf", help="example1 workload: hif and/or rsf")
-    ap.add_argument("--eps-list", default="1e-3,1e-6,1e-9", help="example1 workload: tolerances")
-    ap.add_argument("--second-kind", action="store_true", help="example1 workload: Sec. 4.4 modifications on")
+                         "example1 / example2: the paper's first- / second-kind table rows (RSF and HIF-IE)")
+    ap.add_argument("--methods", default=None,
+                    help="example workloads: any of rsf, hif (hifie2), hifx (hifie2x); default hif,rsf for "
+                         "example1 and hif,hifx,rsf for example2")
+    ap.add_argument("--eps-list", default="1e-3,1e-6,1e-9", help="example workloads: tolerances")
     ap.add_argument("--problems", type=int, default=256, help="batched workload: number of problems")
     ap.add_argument("--no-sequential", action="store_true", help="batched workload: skip the one-by-one leg")
     ap.add_argument("--oracle-sample-json", type=int, default=None, help=argparse.SUPPRESS)
@@ -554,8 +559,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
-    elif args.workload == "example1":
-        run_example1(args)
+    elif args.workload in ("example1", "example2"):
+        run_examples(args)
     else:
         run_gpu(args)
 
