@@ -503,6 +503,72 @@ def run_examples(args):
             fac.close()
 
 
+def run_adjoint(args):
+    """The adjoint workload: 2D second-kind IE on the n = 256 grid (N = 65,536),
+    b = c = 1 + 0.5 phi (seed 1005), eps = 1e-9, FP64 factorization; loss
+    0.5 |u - u*|^2 with u* Gaussian (seed 1007); one step = the forward refined
+    solve (to 1e-14) and the backward pass (transposed refined solve and the
+    coefficient gradients) through HIFSolve, after the factorization, which
+    is timed separately."""
+    import numpy as np
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import hif_inputs as hi
+    import paper_1307_2666_gb300 as P
+    from paper_1307_2666_gb300 import hif as H
+    dev = torch.device(f"cuda:{local}")
+    T = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev)
+    n, eps, tol = 256, 1e-9, 1e-14
+    pb = hi.volume_problem(n, 2, smooth_seed=1005, rhs_seed=1006)
+    ustar = T(hi.gaussian_rhs(pb.N, 1, 1007)[:, 0])
+    ins = [T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0, out
+
+    t_f, fac = timed(lambda: P.Factorization(*ins, 0, eps))
+
+    def step():
+        leaves = [T(pb.f[:, 0]).requires_grad_(True)] + [x.clone().requires_grad_(True) for x in ins[2:]]
+        u = P.HIFSolve.apply(*leaves, fac, tol)
+        loss = 0.5 * torch.sum((u - ustar) ** 2)
+        loss.backward()
+        return loss, [x.grad for x in leaves]
+
+    for _ in range(args.warmup):
+        step()
+    l0 = H.hif_kernel_launches()
+    ts = []
+    for _ in range(args.steps):
+        t, (loss, grads) = timed(step)
+        ts.append(t)
+    launches = (H.hif_kernel_launches() - l0) // max(args.steps, 1)
+    t_fwd, _ = timed(lambda: fac.solve_refined(T(pb.f[:, 0]), tol=tol))
+    ms = 1000 * sum(ts) / len(ts)
+    line = {"metric": "adjoint: forward + backward steps per second (refined solves to 1e-14, FP64 factor)",
+            "value": 1000.0 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "adjoint: 2D second-kind IE n=256 (N=65,536), b=c=1+0.5*phi (seed 1005), "
+                                   "eps=1e-9, FP64, loss 0.5|u-u*|^2, gradients wrt f, a, b, c"},
+            "t_factor_s": t_f, "t_forward_s": t_fwd, "loss": float(loss.detach()),
+            "grad_norms": {k: float(torch.linalg.norm(g)) for k, g in zip("fabc", grads)},
+            "gpu_launches": int(launches)}
+    fac.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -539,7 +605,7 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["grid", "batched", "example1", "example2"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "batched", "example1", "example2", "adjoint"], default="grid",
                     help="grid: the n x n bench workload (default); batched: independent problems in one handle; "
                          "example1 / example2: the paper's first- / second-kind table rows (RSF and HIF-IE)")
     ap.add_argument("--methods", default=None,
@@ -561,6 +627,8 @@ def main():
         run_batched(args)
     elif args.workload in ("example1", "example2"):
         run_examples(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_gpu(args)
 

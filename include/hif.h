@@ -185,6 +185,22 @@ hif_status hif_solve_refined(hif_handle h, int trans, const double* f, double* u
                              int* iters, double* relres);
 
 /*
+ * hif_adjoint_gradients -- the coefficient part of the adjoint method for a
+ * loss L(u) with A u = f (A = diag(a) + diag(b) K diag(c)): given the solution
+ * u and the adjoint solution lam = A^{-T} dL/du (N x nrhs each, column-major,
+ * leading dimension ld, host or device), writes the N-vectors
+ *   grad_a = -sum_col lam .* u,
+ *   grad_b = -sum_col lam .* (K (c .* u)),     K (c u)   = (F u - a u) / b,
+ *   grad_c = -sum_col u .* (K^T (b .* lam)),   K^T (b l) = (F^T lam - a lam) / c,
+ * with the factorization's fast apply F standing in for A (accurate to e_a);
+ * dL/df = lam itself.  Outputs are host or device arrays of N doubles.
+ * HIF_EINVAL when some b_i or c_i is zero.  Not a step of the paper: the
+ * solver's adjoint for gradient-based use.
+ */
+hif_status hif_adjoint_gradients(hif_handle h, const double* u, const double* lam, int64_t nrhs, int64_t ld,
+                                 double* grad_a, double* grad_b, double* grad_c);
+
+/*
  * hif_error_estimates -- the a posteriori operator errors of Sec. 5 by power
  * iteration on E^T E: norms[0] ~ |A|, norms[1] ~ |A - F| and
  * norms[2] ~ |I - A F^{-1}| (2-norms), so e_a = norms[1] / norms[0] and

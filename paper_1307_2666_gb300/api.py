@@ -132,6 +132,19 @@ class Factorization:
                                             0 if method == "ir" else 1)
         return out, its, rel
 
+    def adjoint_gradients(self, u, lam):
+        """(dL/da, dL/db, dL/dc) of the adjoint method from the solution u
+        and the adjoint solution lam = A^{-T} dL/du (same shape)."""
+        uc = _colmajor(u)
+        lc = _colmajor(lam)
+        if uc.ndim == 2 and (uc.stride(1) != uc.shape[0] or lc.stride(1) != lc.shape[0]):
+            uc = uc.t().contiguous().t()
+            lc = lc.t().contiguous().t()
+        N = uc.shape[0]
+        ga, gb, gc = (torch.empty(N, dtype=torch.float64, device=uc.device) for _ in range(3))
+        _h.hif_adjoint_gradients(self.h, uc, lc, ga, gb, gc)
+        return ga, gb, gc
+
     def error_estimates(self, v0, rtol: float = 1e-2, maxit: int = 200) -> dict:
         """e_a ~ |A - F| / |A| and e_s ~ |I - A F^{-1}| (Sec. 5) by power
         iteration from the start vector v0 (N,)."""
@@ -164,7 +177,8 @@ class HIFSolve(torch.autograd.Function):
         dL/db = -lambda * K(c u),     K(c u)     = (F u - a u) / b,
         dL/dc = -u * K^T(b lambda),   K^T(b l)   = (F^T lambda - a lambda) / c,
 
-    with F the factorization's fast apply.  ``fac`` must have been built from
+    with F the factorization's fast apply; the three coefficient gradients
+    come from one library call (``hif_adjoint_gradients``).  ``fac`` must have been built from
     the same a, b, c."""
 
     @staticmethod
@@ -180,10 +194,5 @@ class HIFSolve(torch.autograd.Function):
         u, a, b, c = ctx.saved_tensors
         fac = ctx.fac
         lam, _, _ = fac.solve_refined(g, trans=True, tol=ctx.tol)
-        Fu = fac.apply(u)
-        Ftl = fac.apply_transpose(lam)
-        col = (lambda v: v[:, None]) if u.ndim == 2 else (lambda v: v)
-        Kcu = (Fu - col(a) * u) / col(b)
-        Ktbl = (Ftl - col(a) * lam) / col(c)
-        red = (lambda v: v.sum(dim=1)) if u.ndim == 2 else (lambda v: v)
-        return lam, red(-lam * u), red(-lam * Kcu), red(-u * Ktbl), None, None
+        ga, gb, gc = fac.adjoint_gradients(u, lam)
+        return lam, ga, gb, gc, None, None

@@ -1688,6 +1688,43 @@ hif_status hif_solve_refined(hif_handle h, int trans, const double* f, double* u
     return s != HIF_OK ? s : res;
 }
 
+hif_status hif_adjoint_gradients(hif_handle h, const double* u, const double* lam, int64_t nrhs, int64_t ld,
+                                 double* grad_a, double* grad_b, double* grad_c) {
+    if (!h || !u || !lam || !grad_a || !grad_b || !grad_c || nrhs < 1 || ld < h->N || nrhs > (1 << 20))
+        return HIF_EINVAL;
+    return guard([&] {
+        const int64_t N = h->N;
+        const cudaStream_t st = h->st;
+        const int nr = (int)nrhs;
+        DevMem U, Lm, Fu, Ftl, G;
+        U.ensure(sizeof(double) * N * nr);
+        Lm.ensure(sizeof(double) * N * nr);
+        Fu.ensure(sizeof(double) * N * nr);
+        Ftl.ensure(sizeof(double) * N * nr);
+        G.ensure(sizeof(double) * N * 3);
+        HIF_CUDA(cudaMemcpy2DAsync(U.p, sizeof(double) * N, u, sizeof(double) * ld, sizeof(double) * N, nr,
+                                   is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        HIF_CUDA(cudaMemcpy2DAsync(Lm.p, sizeof(double) * N, lam, sizeof(double) * ld, sizeof(double) * N, nr,
+                                   is_device_ptr(lam) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        fac_dev(h, 1, U.as<double>(), Fu.as<double>(), nr);       // F u
+        fac_dev(h, 3, Lm.as<double>(), Ftl.as<double>(), nr);     // F^T lambda
+        h->status.ensure(sizeof(int));
+        HIF_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), st));
+        double* g = G.as<double>();
+        HIF_CUDA(launch_adjoint_coef(N, nr, h->a.as<double>(), h->b.as<double>(), h->c.as<double>(), U.as<double>(),
+                                     Lm.as<double>(), Fu.as<double>(), Ftl.as<double>(), g, g + N, g + 2 * N,
+                                     h->status.as<int>(), st));
+        int bad = 0;
+        HIF_CUDA(cudaMemcpyAsync(&bad, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        double* outs[3] = {grad_a, grad_b, grad_c};
+        for (int q = 0; q < 3; ++q)
+            HIF_CUDA(cudaMemcpyAsync(outs[q], g + q * N, sizeof(double) * N,
+                                     is_device_ptr(outs[q]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaStreamSynchronize(st));
+        if (bad) fail(HIF_EINVAL, "adjoint gradients need nonzero b and c");
+    });
+}
+
 hif_status hif_error_estimates(hif_handle h, const double* v0, double rtol, int maxit, double* norms, int* iters) {
     if (!h || !v0 || !norms || !(rtol > 0) || maxit < 1) return HIF_EINVAL;
     bool all = true;

@@ -420,6 +420,43 @@ cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int
     return cudaGetLastError();
 }
 
+// Coefficient gradients of the adjoint method for L(u), A u = f, per DOF i and
+// summed over the columns: ga_i = -sum lam u, gb_i = -sum lam (F u - a u)_i / b_i,
+// gc_i = -sum u (F^T lam - a lam)_i / c_i (F u - a u stands for b K c u, F^T lam
+// - a lam for c K^T b lam).  *bad is set when some b_i or c_i is zero.
+__global__ void adjoint_coef_kernel(int64_t N, int nrhs, const double* a, const double* b, const double* c,
+                                    const double* u, const double* lam, const double* Fu, const double* Ftl,
+                                    double* ga, double* gb, double* gc, int* bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ai = a[i], bi = b[i], ci = c[i];
+        if (bi == 0.0 || ci == 0.0) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        double sa = 0.0, sb = 0.0, sc = 0.0;
+        for (int col = 0; col < nrhs; ++col) {
+            const int64_t e = i + N * col;
+            const double ui = u[e], li = lam[e];
+            sa += li * ui;
+            sb += li * (Fu[e] - ai * ui);
+            sc += ui * (Ftl[e] - ai * li);
+        }
+        ga[i] = -sa;
+        gb[i] = -sb / bi;
+        gc[i] = -sc / ci;
+    }
+}
+
+cudaError_t launch_adjoint_coef(int64_t N, int nrhs, const double* a, const double* b, const double* c,
+                                const double* u, const double* lam, const double* Fu, const double* Ftl, double* ga,
+                                double* gb, double* gc, int* bad, cudaStream_t st) {
+    if (N == 0) return cudaSuccess;
+    note_launch();
+    adjoint_coef_kernel<<<(int)std::min<int64_t>((N + 255) / 256, 152 * 8), 256, 0, st>>>(N, nrhs, a, b, c, u, lam,
+                                                                                           Fu, Ftl, ga, gb, gc, bad);
+    return cudaGetLastError();
+}
+
 __global__ void col_dots_kernel(int64_t N, const double* x, int64_t ldx, const double* y, int64_t ldy, double* out) {
     // one CTA per column, deterministic tree reduction
     __shared__ double red[256];

@@ -253,6 +253,9 @@ cudaError_t launch_kernel_block(const GeomDev& g, const int* rows, int64_t nr, c
 cudaError_t launch_kself(const GeomDev& g, double* kself, cudaStream_t);
 
 // BLAS-1 helpers for the refinement loops (FP64)
+cudaError_t launch_adjoint_coef(int64_t N, int nrhs, const double* a, const double* b, const double* c,
+                                const double* u, const double* lam, const double* Fu, const double* Ftl, double* ga,
+                                double* gb, double* gc, int* bad, cudaStream_t st);
 cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int64_t ldx, double beta,
                          double* y, int64_t ldy, cudaStream_t);
 cudaError_t launch_seg_dots(int nseg, const int64_t* off, const int64_t* cnt, int nrhs, const double* x, int64_t ldx,

@@ -86,6 +86,8 @@ EXPORTS = {
     "hif_matvec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "hif_solve_refined": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                     C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "hif_adjoint_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]),
     "hif_error_estimates": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int)]),
     "hif_stats": (C.c_int, [C.c_void_p, C.POINTER(hif_stats_t)]),
@@ -236,6 +238,16 @@ def hif_solve_refined(h, trans: int, f, u, tol: float = 1e-10, maxit: int = 50, 
                                   C.byref(it), C.byref(rr))
     _check(st, "hif_solve_refined", allow=(HIF_ENOTCONV,))
     return st, it.value, rr.value
+
+
+def hif_adjoint_gradients(h, u, lam, ga, gb, gc):
+    """Coefficient gradients of the adjoint method into ga, gb, gc (N each)."""
+    ld, nrhs = _ld(u)
+    ld2, nrhs2 = _ld(lam)
+    if (ld, nrhs) != (ld2, nrhs2):
+        raise ValueError("u and lam must have the same shape and leading dimension")
+    _check(load().hif_adjoint_gradients(h, _ptr(u), _ptr(lam), nrhs, ld, _ptr(ga), _ptr(gb), _ptr(gc)),
+           "hif_adjoint_gradients")
 
 
 def hif_error_estimates(h, v0, rtol: float = 1e-2, maxit: int = 200):
