@@ -218,6 +218,17 @@ hif_status hif_adjoint_gradients(hif_handle h, const double* u, const double* la
 hif_status hif_error_estimates(hif_handle h, const double* v0, double rtol, int maxit,
                                double* norms, int* iters);
 
+/*
+ * hif_eliminated_dofs -- the DOFs eliminated at one sublevel: the redundant
+ * sets of the skeletonized boxes (Lemma 2.4), box by box, each in ascending
+ * order within its column groups, as 0-based indices into the handle's DOFs.
+ * Sublevels 0 .. hif_stats().sublevels - 1 are the skeletonization
+ * sublevels; sublevel hif_stats().sublevels is the top block s_L.  With
+ * out == NULL only *count is written; otherwise out (host or device) must
+ * hold cap >= *count ints.  HIF_EINVAL for a sublevel out of range.
+ */
+hif_status hif_eliminated_dofs(hif_handle h, int sublevel, int* out, int64_t cap, int64_t* count);
+
 /* Factorization statistics (Sec. 5 columns |s_L|, m_f, t_f and ranks per sublevel). */
 hif_status hif_stats(hif_handle h, hif_stats_t* st);
 

@@ -132,6 +132,11 @@ class Factorization:
                                             0 if method == "ir" else 1)
         return out, its, rel
 
+    def eliminated_dofs(self, sublevel: int):
+        """numpy int32 array of the DOFs eliminated at a sublevel; the index
+        ``stats()["sublevels"]`` is the top block."""
+        return _h.hif_eliminated_dofs(self.h, sublevel)
+
     def adjoint_gradients(self, u, lam):
         """(dL/da, dL/db, dL/dc) of the adjoint method from the solution u
         and the adjoint solution lam = A^{-T} dL/du (same shape)."""

@@ -1738,6 +1738,22 @@ hif_status hif_error_estimates(hif_handle h, const double* v0, double rtol, int 
     return all ? HIF_OK : HIF_ENOTCONV;
 }
 
+hif_status hif_eliminated_dofs(hif_handle h, int sublevel, int* out, int64_t cap, int64_t* count) {
+    if (!h || !count || sublevel < 0 || sublevel >= (int)h->subs.size()) return HIF_EINVAL;
+    const SubFactor& sf = *h->subs[sublevel];
+    int64_t n = 0;
+    for (const BoxFac& b : sf.hbox) n += b.r;
+    *count = n;
+    if (!out) return HIF_OK;
+    if (cap < n) return HIF_EINVAL;
+    return guard([&] {
+        if (n == 0) return;
+        HIF_CUDA(cudaMemcpyAsync(out, sf.rd.p, sizeof(int) * n,
+                                 is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+        HIF_CUDA(cudaStreamSynchronize(h->st));
+    });
+}
+
 hif_status hif_stats(hif_handle h, hif_stats_t* st) {
     if (!h || !st) return HIF_EINVAL;
     *st = h->stats;

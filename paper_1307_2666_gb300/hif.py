@@ -88,6 +88,7 @@ EXPORTS = {
                                     C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "hif_adjoint_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_void_p]),
+    "hif_eliminated_dofs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "hif_error_estimates": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int)]),
     "hif_stats": (C.c_int, [C.c_void_p, C.POINTER(hif_stats_t)]),
@@ -248,6 +249,16 @@ def hif_adjoint_gradients(h, u, lam, ga, gb, gc):
         raise ValueError("u and lam must have the same shape and leading dimension")
     _check(load().hif_adjoint_gradients(h, _ptr(u), _ptr(lam), nrhs, ld, _ptr(ga), _ptr(gb), _ptr(gc)),
            "hif_adjoint_gradients")
+
+
+def hif_eliminated_dofs(h, sublevel: int) -> np.ndarray:
+    """The DOFs eliminated at one sublevel (the last index: the top block)."""
+    lib = load()
+    n = C.c_int64(0)
+    _check(lib.hif_eliminated_dofs(h, int(sublevel), None, 0, C.byref(n)), "hif_eliminated_dofs")
+    out = np.empty(n.value, dtype=np.int32)
+    _check(lib.hif_eliminated_dofs(h, int(sublevel), _ptr(out), n.value, C.byref(n)), "hif_eliminated_dofs")
+    return out
 
 
 def hif_error_estimates(h, v0, rtol: float = 1e-2, maxit: int = 200):
