@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -89,3 +90,17 @@ def test_status_strings_and_argument_errors(lib):
     assert L.hif_options_default(4, None) == hif.HIF_EINVAL
     assert L.hif_destroy(None) == hif.HIF_OK
     assert L.hif_apply(None, None, None, 1, 1) == hif.HIF_EINVAL
+    norms = (ctypes.c_double * 3)()
+    its = (ctypes.c_int * 3)()
+    assert L.hif_error_estimates(None, None, 1e-2, 10, norms, its) == hif.HIF_EINVAL
+    cnt = ctypes.c_int64(-1)
+    assert L.hif_eliminated_dofs(None, 0, None, 0, ctypes.byref(cnt)) == hif.HIF_EINVAL
+    assert L.hif_adjoint_gradients(None, None, None, 1, 1, None, None, None) == hif.HIF_EINVAL
+    # a symmetric option outside {0, 1} is rejected before any device work
+    o = hif.hif_options_default(2)
+    o.symmetric = 2
+    pts = np.zeros((4, 2))
+    one = np.ones(4)
+    assert L.hif_factor(pts.ctypes.data, 4, one.ctypes.data, one.ctypes.data, one.ctypes.data, one.ctypes.data,
+                        0, 1e-6, ctypes.byref(o), ctypes.byref(h)) == hif.HIF_EINVAL
+    assert h.value is None
