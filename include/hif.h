@@ -99,8 +99,9 @@ typedef struct {
 
 /* Defaults for dimension dim (2 or 3): occupancy 64, second_kind 1, FP64,
  * fractional levels on, proxy 64 points (2D) / 512 (3D) at radius 1.5,
- * fp32_tol_floor 2^-17, bounding-cube root box, default stream, paired-FP32
- * direct sums. */
+ * fp32_tol_floor 2^-17, bounding-cube root box, default stream, direct sums
+ * on the tensor cores (direct_precision 2), graph-replayed and autotuned
+ * sweeps, symmetric shortcut on. */
 hif_status hif_options_default(int dim, hif_options* opt);
 
 /*
