@@ -10,8 +10,9 @@
  * with G the Laplace kernel of Eq. (1.4) (kernel_id 0: -log(r)/(2 pi) in 2D,
  * kernel_id 1: 1/(4 pi r) in 3D), by the hierarchical interpolative
  * factorization HIF-IE (Sec. 4, Algorithms 4.1 and 4.2, with the second-kind
- * modifications of Sec. 4.4), and applies the factorization F ~ A and its
- * inverse in factored form (Eqs. (4.1), (4.2)).  The cell of DOF i is the
+ * modifications of Sec. 4.4 and, for symmetric A, the one-sided proxy
+ * matrices of Sec. 5), and applies the factorization F ~ A and its inverse
+ * in factored form (Eqs. (4.1), (4.2)).  The cell of DOF i is the
  * square/cube of volume w_i centred at x_i; its self term is the exact
  * integral in closed form.
  *
