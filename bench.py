@@ -35,10 +35,7 @@ METRIC = "factor s + solve DOF/s on GB300 at stated rel. err; FP32+refine/batche
 UNIT = "DOF/s"
 TOL = 1e-10
 ORACLE_SAMPLE_N = 64
-# DRAM bytes (read + write) of one 8-RHS launch of the tensor-core direct sum
-# at n = 1024, from one ncu capture (profiles/tc_conv_n1024_dram.md); valid
-# only for the kernel source with this sha256 prefix
-TC_TRAFFIC = {"n": 1024, "bytes": 116.40e9 + 92.49e6, "source_sha256": "6ed77bb75d683753"}
+ORACLE_SCALING_N = (32, 64)
 
 
 def workload_config(n, nrhs, eps):
@@ -143,18 +140,48 @@ class ClockSampler:
 
 # --------------------------------------------------------------- GPU arm ---
 
-def tc_traffic(n, nrhs):
-    """The captured DRAM bytes per launch, or None if the workload or the
-    kernel source differs from the capture."""
-    import hashlib
-    try:
-        with open(os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "k_tcconv.cu"), "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
-    except OSError:
-        return None
-    if n != TC_TRAFFIC["n"] or nrhs != 8 or not sha.startswith(TC_TRAFFIC["source_sha256"]):
-        return None
-    return TC_TRAFFIC["bytes"]
+def alu_peaks(peaks):
+    """FP32 and FP64 SIMT peaks from the unit counts and the measured maximum
+    SM clock: 152 SMs x 128 FP32 lanes (one FMA = 2 flop per clock) and
+    152 SMs x 2 FP64 FMA per clock."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return {"fp32": 152 * 128 * 2 * mhz * 1e6 / 1e12, "fp64": 152 * 2 * 2 * mhz * 1e6 / 1e12}
+
+
+def kernel_rooflines(prof, peaks, precision):
+    """One entry per kernel family of a profiled step: achieved work / event
+    time against the peak of the unit that bounds it (Sec. 8 rooflines:
+    fold / ID / elimination on the FP32 or FP64 SIMT pipes, pivot steps and
+    sweeps on HBM, the direct sum on the tensor pipe)."""
+    alu = alu_peaks(peaks)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tens = peaks.get("bf16_tflops_sustained", 1700.0)
+    simt = alu["fp32"] if precision == "fp32" else alu["fp64"]
+    simt_name = f"{precision} SIMT pipe, derived from unit counts x sm_max_mhz"
+    bound = {"fold_kernel": ("alu", simt, simt_name), "id_kernel": ("alu", simt, simt_name),
+             "elim_kernel": ("alu", simt, simt_name), "big_elim_batch": ("alu", simt, simt_name),
+             "big_qr_step": ("hbm", hbm, "MEASURED_PEAKS.json hbm_gbs"),
+             "big_ygen_kernel": ("hbm", hbm, "MEASURED_PEAKS.json hbm_gbs"),
+             "sweep": ("hbm", hbm, "MEASURED_PEAKS.json hbm_gbs"),
+             "direct_sum": ("tensor", tens, "MEASURED_PEAKS.json bf16_tflops_sustained")}
+    out = []
+    for name, e in prof.items():
+        if not e["ranges"]:
+            continue
+        t = e["ms"] / 1000.0
+        row = {"kernel": name, "ranges": e["ranges"], "seconds": t}
+        if name in bound and t > 0:
+            kind, peak, src = bound[name]
+            if kind == "hbm":
+                ach = e["bytes"] / t / 1e9
+                row.update(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak,
+                           algorithmic_bytes=e["bytes"], peak_source=src)
+            else:
+                ach = e["flops"] / t / 1e12
+                row.update(bound=kind, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                           algorithmic_flops=e["flops"], peak_source=src)
+        out.append(row)
+    return out
 
 
 def max_over_ranks(t_local, world, device):
@@ -270,23 +297,35 @@ def run_gpu(args):
     t_mv = e0.elapsed_time(e1) / 1000.0 / reps
     fac.close()
     peaks = measured_peaks()
-    # algorithmic work: per (target, source) pair and 8 right-hand sides the
-    # digit products of the table digits s = 0..6 with the source digits
-    # t <= 7 - s that the sum needs: 256 BF16 MACs (= 32 per pair and RHS)
     groups = -(-nrhs // 8)
-    flops_launch = 512.0 * N * N * min(nrhs, 8) / 8.0
+    # algorithmic work of the method (Sec. 8 roofline of the direct sum):
+    # 2 N^2 flops per right-hand side; the kernel forms them from exact 8-bit
+    # digit products, 256 BF16 MACs per (target, source) pair and 8 RHS
+    flops_launch = 2.0 * N * N * min(nrhs, 8)
+    digit_flops_launch = 512.0 * N * N * min(nrhs, 8) / 8.0
     t_launch = (tc_ms / 1000.0 / tc_launches) if tc_launches else float("nan")
     achieved = flops_launch / t_launch / 1e12
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    fp64_pipe = alu_peaks(peaks)["fp64"]
     roofline = {"kernel": "tc_conv_kernel (direct sum on tcgen05 tensor cores, exact 8-bit digits)",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside the step)"
                                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained"),
-                "algorithmic_per_launch": f"256 BF16 digit MACs x N^2 per 8 RHS = {flops_launch:.3e} flop",
-                "launch_seconds": t_launch, "launches_timed": tc_launches, "traffic": tc_traffic(n, nrhs),
-                "fp64_equivalent_tflops": 2.0 * N * N * min(nrhs, 8) / t_launch / 1e12,
+                "algorithmic_per_launch": f"2 N^2 flops per RHS x {min(nrhs, 8)} RHS = {flops_launch:.3e} flop",
+                "launch_seconds": t_launch, "launches_timed": tc_launches, "traffic": None,
+                "digit_mac_tflops": digit_flops_launch / t_launch / 1e12,
+                "digit_mac_occupancy": digit_flops_launch / t_launch / 1e12 / peak,
+                "fp64_pipe_peak_tflops": fp64_pipe, "vs_fp64_pipe": achieved / fp64_pipe,
                 "matvec_seconds": t_mv, "matvec_launches_per_call": groups}
+
+    # ---- every hot kernel family of one more step, timed per launch with
+    # CUDA events (outside the timed region)
+    H.hif_kernel_profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = H.hif_kernel_profile(False)
+    roofline_kernels = kernel_rooflines(prof, peaks, "fp32")
 
     # ---- FP64 factorization path for comparison (one step)
     fp64 = None
@@ -322,9 +361,16 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = run_oracle_subprocess()
+        runs = [run_oracle_subprocess(nn) for nn in ORACLE_SCALING_N]
+        s = runs[-1]
         cpu = {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": s["sample"],
-               "seconds": s["seconds"], "iters": s["iters"], "relres": s["relres"]}
+               "seconds": s["seconds"], "iters": s["iters"], "relres": s["relres"],
+               "same_config": False,
+               "config_note": (f"the oracle runs n={ORACLE_SCALING_N[-1]} (N={s['N']}), 1 RHS; the GPU line runs "
+                               f"n={n} (N={N}), {nrhs} RHS. The oracle's dense Schur store makes it O(N^2) in "
+                               f"memory and worse in time, so DOF/s falls with N; the scaling entries show it."),
+               "scaling": [{"n": nn, "N": r["N"], "seconds": r["seconds"], "value": r["value"]}
+                           for nn, r in zip(ORACLE_SCALING_N, runs)]}
 
     if rank == 0:
         line = {
@@ -335,7 +381,8 @@ def run_gpu(args):
             "t_factor_s": t_factor, "t_solve_s": t_solve, "refine_iters": its, "relres": rel,
             "top_size": fp32_stats["top"], "factor_bytes": fp32_stats["mf"],
             "symmetric_compression": fp32_stats["sym"], "proxy_rows": fp32_stats["rows"],
-            "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64_path": fp64, "roofline": roofline, "roofline_kernels": roofline_kernels,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -346,7 +393,8 @@ def run_gpu(args):
 
 def run_batched(args):
     """Independent problems in one handle: P 2D second-kind IEs with n drawn
-    from {32, 48, ..., 256} (seed 3), eps 1e-6, 4 Gaussian RHS each; one step
+    from {32, 48, ..., 256} (seed 1004), b = c = 1 + 0.5 phi_p (seed 2000 + p),
+    eps 1e-6, 4 Gaussian RHS each (seed 3000 + p); one step
     = factor all problems in one batched handle + refine all RHS to 1e-10.
     Reported next to the same problems factored and refined one handle at a
     time (FP64, the plain path) and to the batched handle in FP32."""
@@ -366,8 +414,8 @@ def run_batched(args):
     from paper_1307_2666_gb300 import hif as H
     dev = torch.device(f"cuda:{local}")
     T = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev)
-    sizes = hi.batched_sizes(args.problems, seed=3)
-    pbs = [hi.volume_problem(n, 2, smooth_seed=5000 + q, rhs_seed=6000 + q, nrhs=4) for q, n in enumerate(sizes)]
+    sizes = hi.batched_sizes(args.problems, seed=1004)
+    pbs = [hi.volume_problem(n, 2, smooth_seed=2000 + q, rhs_seed=3000 + q, nrhs=4) for q, n in enumerate(sizes)]
     probs = [(T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)) for pb in pbs]
     F = T(np.vstack([pb.f for pb in pbs]).T).t()
     dofs = sum(pb.N for pb in pbs)
@@ -420,7 +468,8 @@ def run_batched(args):
             "warmup": args.warmup, "ms_per_step": 1000 * t32, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 factor; residual bf16 digits, exact int sums", "data": "synthetic",
             "config": {"workload": (f"batched: {args.problems} independent 2D second-kind volume IEs, n drawn from "
-                                    f"{{32,48,...,256}} (seed 3), eps 1e-6, 4 Gaussian RHS each, refined to "
+                                    f"{{32,48,...,256}} (seed 1004), b=c=1+0.5*phi_p (seed 2000+p), eps 1e-6, 4 Gaussian RHS "
+                                    f"each (seed 3000+p), refined to "
                                     f"{TOL:g}"), "problems": args.problems, "dofs": dofs, "nrhs": 4,
                        "parallelism": f"replicas x{world}"},
             "refine_iters": its, "relres": rel, "gpu_launches": int(launches), "clocks": clocks,

@@ -77,6 +77,10 @@ typedef struct {
                                symmetric and the one-sided proxy matrix Y'_c = [A_{cN,c};
                                Y_{cE,c}] is compressed (Sec. 5; same ID, half the rows);
                                0: always the full Y_c of Eq. (3.3)                        */
+    int ldl;                /* 1 (default): when the symmetric shortcut applies, factor the
+                               diagonal blocks B_rr by LDL with 1 x 1 symmetric pivots and
+                               keep X only (Y = X^T; Sec. 5); a block whose pivot fails the
+                               Bunch-Kaufman 1 x 1 test falls back to LU. 0: always LU   */
 } hif_options;
 
 typedef struct {
@@ -92,17 +96,23 @@ typedef struct {
     int kinds[64];          /* per sublevel: 0 cell, 1 face, 2 edge                        */
     int max_box[64];        /* per sublevel: largest |c|                                   */
     double factor_seconds;  /* wall time of hif_factor                                     */
-    double flops;           /* algorithmic FP work of the factorization (see DESIGN)       */
+    double flops;           /* algorithmic FP work of the factorization: per box 2 m n^2
+                               for the QR fold of the m x n proxy matrix, and 6 k^2 r +
+                               6 k r^2 + 2 r^3 / 3 for the Lemma 2.4 blocks, the LU of
+                               Lemma 2.1, X, Y and the Schur update; 4 |s_L|^3 / 3 for the
+                               top block                                                  */
     double kernel_evals;    /* kernel evaluations spent on the proxy matrices Y_c          */
     int64_t proxy_rows;     /* rows of all proxy matrices compressed (Y_c or Y'_c)         */
     int symmetric_problems; /* problems whose A was symmetric and compressed through Y'_c  */
+    int64_t ldl_boxes;      /* eliminated boxes factored by LDL (Sec. 5), top blocks included */
+    int64_t ldl_fallbacks;  /* LDL boxes refactored by LU after a pivot failed the 1x1 test */
 } hif_stats_t;
 
 /* Defaults for dimension dim (2 or 3): occupancy 64, second_kind 1, FP64,
  * fractional levels on, proxy 64 points (2D) / 512 (3D) at radius 1.5,
  * fp32_tol_floor 2^-17, bounding-cube root box, default stream, direct sums
  * on the tensor cores (direct_precision 2), graph-replayed and autotuned
- * sweeps, symmetric shortcut on. */
+ * sweeps, symmetric shortcut and LDL on. */
 hif_status hif_options_default(int dim, hif_options* opt);
 
 /*
@@ -150,11 +160,16 @@ hif_status hif_factor_batched(int count, const hif_problem* problems, int kernel
 
 /* y = F x  (Eq. (4.1) first line; generalized FMM).  x, y: N x nrhs, ld >= N. */
 hif_status hif_apply(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld);
-/* y = F^T x. */
+/* y = F^T x: the transpose of Eq. (4.1)'s product, every factor transposed
+ * and the order reversed (Sec. 3.1: the transposes of the unit-triangular
+ * factors are unit-triangular with the off-diagonal block transposed).
+ * x, y: N x nrhs, ld >= N. */
 hif_status hif_apply_transpose(hif_handle h, const double* x, double* y, int64_t nrhs, int64_t ld);
 /* x = F^{-1} b  (Eq. (4.1) second line; direct solver / preconditioner). */
 hif_status hif_solve(hif_handle h, const double* b, double* x, int64_t nrhs, int64_t ld);
-/* x = F^{-T} b. */
+/* x = F^{-T} b: Eq. (4.1)'s inverse transposed, i.e. the adjoint solve
+ * (Sec. 3.1 inverts each factor by negating its off-diagonal block; the
+ * transpose keeps that form).  b, x: N x nrhs, ld >= N. */
 hif_status hif_solve_transpose(hif_handle h, const double* b, double* x, int64_t nrhs, int64_t ld);
 
 /*
@@ -234,7 +249,10 @@ hif_status hif_eliminated_dofs(hif_handle h, int sublevel, int* out, int64_t cap
 /* Factorization statistics (Sec. 5 columns |s_L|, m_f, t_f and ranks per sublevel). */
 hif_status hif_stats(hif_handle h, hif_stats_t* st);
 
-/* Releases every resource the handle owns.  NULL is accepted. */
+/* Releases every resource the handle owns: the factors of Eq. (4.1) (T, L,
+ * D, U, X, Y per box and the top block's LU of Sec. 3.1, level L), the
+ * Schur-complement interaction store and the work buffers.  NULL is
+ * accepted.  Waits for the handle's stream first; always returns HIF_OK. */
 hif_status hif_destroy(hif_handle h);
 
 /* Static, human-readable name of a status code. */
@@ -256,6 +274,30 @@ uint64_t hif_kernel_launches(void);
  * then sets recording on (enable != 0) or off.  Process-wide; not
  * thread-safe against concurrent direct sums.  The paper has no counterpart. */
 hif_status hif_kernel_timing(int enable, double* ms, int64_t* launches);
+
+/* One kernel family of hif_kernel_profile. */
+typedef struct {
+    const char* name;       /* static name of the kernel family                         */
+    int64_t ranges;         /* timed ranges (one launch or one launch group each)        */
+    double ms;              /* summed CUDA-event time of those ranges                    */
+    double flops;           /* algorithmic flops of the work in them (0: byte-bound)     */
+    double bytes;           /* algorithmic bytes of the work in them (0: flop-bound)     */
+} hif_profile_entry;
+
+/* Per-kernel-family device time, for measurement: while enabled, the launches
+ * of the factorization kernels, the sweeps (one range per whole sweep of an
+ * operation) and the direct sums are bracketed by CUDA events on their
+ * stream, with the algorithmic work counted from the sizes of the run
+ * (per box 2 m n^2 flops for the QR fold of an m x n proxy matrix; QR to
+ * rank k plus T = R1^{-1} R2 for the ID; 6 k^2 r + 6 k r^2 + 2 r^3/3 for an
+ * elimination; for a large-box pivot step the bytes of the columns it
+ * reads and writes; for a sweep the factor and vector bytes it moves; 2 N^2
+ * flops per right-hand side for a direct sum).  Each call writes the sums
+ * since the previous call into out[0 .. min(cap, *count)) (either may be
+ * NULL), synchronizing on the recorded events, and then turns recording on
+ * (enable != 0) or off.  Ranges on a stream being captured into a graph are
+ * not recorded.  Process-wide; the paper has no counterpart. */
+hif_status hif_kernel_profile(int enable, hif_profile_entry* out, int cap, int* count);
 
 /*
  * hif_kernel_block -- entries A_ij = a_i delta_ij + b_i K_ij c_j (Eq. (3.1))
@@ -291,11 +333,13 @@ hif_status hif_id_batched(int count, const double* mats, const int64_t* off,
 
 /*
  * hif_id_batched_noalloc -- the batched interpolative decomposition of
- * hif_id_batched for callers that must not allocate memory: code that runs
- * while a CUDA graph is being captured, real-time or embedded callers with a
- * fixed memory budget, and any caller for which cudaMalloc would synchronize
- * the device at the wrong moment.  This entry point has no counterpart in the
- * paper; it calls no cudaMalloc, cudaFree or allocating library routine.
+ * hif_id_batched for callers that must not allocate device memory: services
+ * that reserve their device memory once at start-up and may not fail on an
+ * allocation later (a fixed memory budget), and callers that may not call
+ * cudaMalloc or cudaFree at all because those calls can synchronize the
+ * whole device and stall the work of other streams.  This entry point has
+ * no counterpart in the paper; it calls no cudaMalloc, cudaFree or
+ * allocating library routine.  It does wait for its own stream (below).
  *
  * Arguments, results and the rank rule are those of hif_id_batched, except
  * that every array must already live in device memory (HIF_EINVAL otherwise).
@@ -304,13 +348,15 @@ hif_status hif_id_batched(int count, const double* mats, const int64_t* off,
  * copies plus 32 KiB of offsets.  Limits: at most 4096 matrices, at most 1024
  * columns per matrix, and sum over matrices of (m|1)*n <= 1,048,576 doubles;
  * larger inputs are rejected with HIF_EINVAL (hif_last_error says why) and
- * leave the outputs untouched.
+ * leave the outputs untouched; a later call within the limits is not
+ * affected by a refused one.
  *
  * The first call on a device looks up that device's address of the array;
  * make that first call before any stream capture.  All calls share the one
  * array and it keeps the last call's contents; calls that overlap on the GPU
- * (different streams, different threads) race on it.  The call returns after
- * its results are complete on `stream`.
+ * (different streams, different threads) race on it.  The call reads a
+ * status word back from the array and returns after its results are
+ * complete on `stream` (it synchronizes that stream, not the device).
  */
 hif_status hif_id_batched_noalloc(int count, const double* mats, const int64_t* off,
                                   const int32_t* m, const int32_t* n, const double* tol,

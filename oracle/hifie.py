@@ -53,9 +53,17 @@ Readings of points the paper leaves open (the GPU path uses the same ones):
     sufficient form of b_i w_j c_j = b_j w_i c_i for all i != j.  The
     dropped rows repeat the kept ones (the active matrix A + S stays
     symmetric under symmetric elimination), so Y_c^T Y_c = 2 Y'_c^T Y'_c and
-    the pivoted QR picks the same skeletons with the same T.  The diagonal
-    blocks B_rr are still factored by LU with partial pivoting: the paper's
-    LDL changes how the block inverse is formed, not its value.
+    the pivoted QR picks the same skeletons with the same T.
+ 9. LDL (Sec. 5, opening paragraph: symmetric diagonal blocks are factored
+    by a partially pivoted LDL).  For symmetric A, B_rr is factored as
+    P B_rr P^T = L D L^T with 1 x 1 symmetric pivots: at each step the
+    remaining diagonal entry of largest magnitude (ties: lowest position),
+    accepted when it is at least alpha = (1 + sqrt 17) / 8 times the largest
+    other entry of its column (the Bunch-Kaufman test for a 1 x 1 pivot).
+    A box whose pivot fails the test is factored by LU with partial pivoting
+    instead (2 x 2 pivots are not used).  With U = L^T P the factored form
+    is the LU one, P B_rr = L D U, and Y = D^{-1} L^{-1} P B_rs = X^T, so
+    only X is kept; the Schur update -X D X^T is symmetric by construction.
 """
 from __future__ import annotations
 
@@ -128,6 +136,18 @@ class BoxFactor:
     ngroups: int = 1
     n: int = 0
     m: int = 0
+    ldl: bool = False   # P B_rr P^T = L D L^T: U = L^T P (dense, not triangular), Y = X^T
+
+    def U_solve(self, v, trans=False):
+        """U^{-1} v (U^{-T} v with trans) for either factor form."""
+        if not self.ldl:
+            return solve_triangular(self.U, v, lower=False, trans=1 if trans else 0, unit_diagonal=True)
+        if trans:                                    # U^{-T} = L^{-1} P
+            return solve_triangular(self.L, v[self.perm], lower=True, unit_diagonal=True)
+        w = solve_triangular(self.L, v, lower=True, trans=1, unit_diagonal=True)   # U^{-1} = P^T L^{-T}
+        out = np.empty_like(w)
+        out[self.perm] = w
+        return out
 
 
 @dataclass
@@ -155,7 +175,8 @@ class HIFFactor:
         for sl in self.sublevels:
             for bf in sl.boxes:
                 k, r = bf.sk.size, bf.rd.size
-                tot += 3 * k * r + r * r + r
+                # LU: T, X, Y, L and U, D; LDL: T, X, strict L, D
+                tot += (2 * k * r + r * (r - 1) // 2 + r) if bf.ldl else (3 * k * r + r * r + r)
         return int(tot)
 
     def ranks(self):
@@ -183,7 +204,7 @@ class HIFFactor:
             x[self.top] = lu_solve(self.top_lu, x[self.top])
         for bf in self._boxes(reverse=True):             # V, coarsest first
             x[bf.rd] -= bf.Y @ x[bf.sk]
-            x[bf.rd] = solve_triangular(bf.U, x[bf.rd], lower=False, unit_diagonal=True)
+            x[bf.rd] = bf.U_solve(x[bf.rd])
             x[bf.sk] -= bf.T @ x[bf.rd]
         return x
 
@@ -212,7 +233,7 @@ class HIFFactor:
         x = np.array(b, dtype=np.float64, copy=True)
         for bf in self._boxes():                         # V^T, finest first
             x[bf.rd] -= bf.T.T @ x[bf.sk]
-            x[bf.rd] = solve_triangular(bf.U, x[bf.rd], lower=False, trans=1, unit_diagonal=True)
+            x[bf.rd] = bf.U_solve(x[bf.rd], trans=True)
             x[bf.sk] -= bf.Y.T @ x[bf.rd]
         for bf in self._boxes():                         # D^{-T}
             x[bf.rd] = (x[bf.rd].T / bf.D).T
@@ -303,17 +324,21 @@ def sublevel_plan(dim: int, L: int, fractional: bool = True, skip_levels: int = 
 
 def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
            *, second_kind: bool = True, occupancy: int = 64, proxy_radius: float = 1.5,
-           fractional: bool = True, skip_levels: int = 0, symmetric=None, trace=None) -> HIFFactor:
+           fractional: bool = True, skip_levels: int = 0, symmetric=None, ldl=None,
+           trace=None) -> HIFFactor:
     """HIF-IE (Algorithm 4.1 / 4.2) of A = diag(a) + diag(b) K diag(c).
 
     ``symmetric``: None compresses Y'_c exactly when ``is_symmetric`` holds,
     False always compresses the full Y_c, True requires ``is_symmetric``.
+    ``ldl``: None factors B_rr by LDL exactly when Y'_c is compressed
+    (reading 9), False always by LU.
     """
     op = Operator(points, weights, a, b, c, kernel_id)
     if symmetric is None:
         symmetric = is_symmetric(op)
     elif symmetric and not is_symmetric(op):
         raise ValueError("symmetric=True needs b == c and equal weights")
+    use_ldl = bool(symmetric) if ldl is None else (bool(ldl) and bool(symmetric))
     x = op.x
     N, d = x.shape
     proxy_dirs = np.asarray(proxy_dirs, dtype=np.float64)
@@ -350,7 +375,7 @@ def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
             if cbox.size == 0:
                 continue
             bf = _skeletonize(op, S, M, snapshot, cbox, ctr[bid], R2, proxy_radius * w,
-                              proxy_dirs, eps, second_kind, bool(symmetric))
+                              proxy_dirs, eps, second_kind, bool(symmetric), use_ldl)
             sl.boxes.append(bf)
             active[bf.rd] = False
             if trace is not None:
@@ -381,8 +406,40 @@ def sci_groups(pattern: np.ndarray):
     return [np.nonzero(gid == g)[0] for g in range(len(keys))]
 
 
+LDL_ALPHA = (1.0 + np.sqrt(17.0)) / 8.0
+
+
+def ldl_diag_pivot(B):
+    """P B P^T = L D L^T with 1 x 1 symmetric pivots (reading 9).
+
+    Returns (perm, L, D) with (P x)_i = x[perm[i]], or None when a pivot
+    fails the test |B_pp| >= alpha * max_{i != p} |B_ip| (or is zero)."""
+    Bw = np.array(B, dtype=np.float64, copy=True)
+    r = Bw.shape[0]
+    perm = np.arange(r)
+    L = np.eye(r)
+    D = np.zeros(r)
+    for j in range(r):
+        diag = np.abs(np.diag(Bw)[j:])
+        p = j + int(np.argmax(diag))                 # first maximum = lowest position
+        col = np.abs(Bw[j:, p])
+        col[p - j] = 0.0
+        colmax = col.max() if col.size else 0.0
+        if Bw[p, p] == 0.0 or not np.isfinite(Bw[p, p]) or abs(Bw[p, p]) < LDL_ALPHA * colmax:
+            return None
+        if p != j:                                   # symmetric interchange of rows and columns j, p
+            Bw[[j, p], :] = Bw[[p, j], :]
+            Bw[:, [j, p]] = Bw[:, [p, j]]
+            L[[j, p], :j] = L[[p, j], :j]
+            perm[[j, p]] = perm[[p, j]]
+        D[j] = Bw[j, j]
+        L[j + 1:, j] = Bw[j + 1:, j] / D[j]
+        Bw[j + 1:, j + 1:] -= D[j] * np.outer(L[j + 1:, j], L[j + 1:, j])
+    return perm, L, D
+
+
 def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_dirs,
-                 eps, second_kind, symmetric=False) -> BoxFactor:
+                 eps, second_kind, symmetric=False, use_ldl=False) -> BoxFactor:
     x = op.x
     n = cbox.size
     inbox = np.zeros(op.N, dtype=bool)
@@ -453,6 +510,21 @@ def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_d
     B_rr = A_rr - T.T @ A_sr - A_rs @ T + T.T @ A_ss @ T
     B_rs = A_rs - T.T @ A_ss
     B_sr = A_sr - A_ss @ T
+    fac = ldl_diag_pivot(B_rr) if use_ldl else None
+    if fac is not None:
+        # reading 9: P B_rr P^T = L D L^T, U = L^T P, X = B_sr P^T L^{-T} D^{-1}, Y = X^T
+        perm, Lm, Dg = fac
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        Um = Lm.T[:, inv]
+        Xp = solve_triangular(Lm, B_sr[:, perm].T, lower=True, unit_diagonal=True).T
+        X = Xp / Dg[None, :]
+        if k > 0:
+            delta = -(X * Dg[None, :]) @ X.T
+            S[np.ix_(sk_g, sk_g)] += delta
+            M[np.ix_(sk_g, sk_g)] = True
+        return BoxFactor(sk=sk_g, rd=rd_g, T=T, L=Lm, D=Dg, U=Um, perm=perm, X=X, Y=X.T.copy(),
+                         ngroups=len(groups), n=n, m=m, ldl=True)
     # Lemma 2.1 on B_rr with partial pivoting: P B_rr = L D U
     Pm, Lm, Ut = dense_lu(B_rr)
     perm = Pm.argmax(axis=0)

@@ -41,13 +41,15 @@ class Factorization:
     autotune: pick each sublevel's sweep CTA size by timing after factoring.
     symmetric: compress the one-sided Y'_c when b == c and the weights are
     equal (A symmetric; Sec. 5); False always compresses the full Y_c.
+    ldl: with the symmetric shortcut, factor the diagonal blocks by LDL and
+    keep X only (Sec. 5); False always uses LU with partial pivoting.
     """
 
     def __init__(self, points, weights, a, b, c, kernel_id: int, eps: float, *, precision: str = "fp64",
                  second_kind: bool = True, occupancy: int = 64, proxy_dirs=None, fractional: bool = True,
                  skip_levels: int = 0, proxy_radius: float = 1.5, fp32_tol_floor: float | None = None,
                  root=None, stream=None, direct: str = "tc", graphs: bool = True, autotune: bool = True,
-                 symmetric: bool = True):
+                 symmetric: bool = True, ldl: bool = True):
         dim = (points[0][0] if isinstance(points, (list, tuple)) else points).shape[1]
         opt = _h.hif_options_default(dim)
         opt.leaf_occupancy = int(occupancy)
@@ -60,6 +62,7 @@ class Factorization:
         opt.use_graphs = 1 if graphs else 0
         opt.autotune = 1 if autotune else 0
         opt.symmetric = 1 if symmetric else 0
+        opt.ldl = 1 if ldl else 0
         self._keep = []
         if proxy_dirs is not None:
             pd = np.ascontiguousarray(np.asarray(proxy_dirs.cpu() if hasattr(proxy_dirs, "cpu") else proxy_dirs,

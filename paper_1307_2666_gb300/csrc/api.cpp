@@ -23,6 +23,7 @@
 #include "../../include/hif.h"
 #include "geometry.h"
 #include "launch.h"
+#include "prof.h"
 
 namespace hif {
 
@@ -122,7 +123,7 @@ struct Segment {
 };
 
 struct FactorScratch {
-    DevMem d_ed, d_ed_big, d_eg, ews, piv;
+    DevMem d_ed, d_ed_big, d_eg, ews, piv, ldl_fail;
 };
 
 constexpr int KIND_TOP = 3;   // the top blocks, eliminated as boxes without skeletons
@@ -139,6 +140,10 @@ struct SubFactor {
     DevMem gws_off;
     int64_t gws_units = 0;
     int threads = 256;
+    // algorithmic elements the two passes of one sweep read from the factors
+    // (T twice, X or Y once each, one triangle of L^{-1}/U^{-1} or L/U per
+    // pass, D) and the box vectors they gather and scatter (sum of k + r)
+    double sweep_factor_elems = 0, sweep_perm_ints = 0, sweep_vec_elems = 0;
 };
 
 // A captured sequence of sweeps (one operation, one right-hand-side count, one
@@ -365,9 +370,15 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
     a.k_out = k_out.as<int>();
     a.eps = h->eps;
     a.tol_floor = tol_floor;
-    HIF_CUDA((big_ygen<T>(a, (int)bbv.size(), max_entries, st)));
-    HIF_CUDA((big_rho<T>(a, ng, max_m, max_n, st)));
-    if (split) HIF_CUDA((big_add<T>(B.YK.p, B.YS.p, yoff, st)));
+    {
+        ProfRange pr(PROF_BIG_YGEN, st, 0.0, (split ? 2.0 : 1.0) * sizeof(T) * (double)yoff);
+        HIF_CUDA((big_ygen<T>(a, (int)bbv.size(), max_entries, st)));
+    }
+    {
+        ProfRange pr(PROF_BIG_RHO, st, 0.0, 0.0);
+        HIF_CUDA((big_rho<T>(a, ng, max_m, max_n, st)));
+        if (split) HIF_CUDA((big_add<T>(B.YK.p, B.YS.p, yoff, st)));
+    }
     // Opt-in (HIF_BIG_RFIRST=1): measured slower at present, see k_bigqr.cu.
     if (env_int("HIF_BIG_RFIRST", 0)) {
         // Y_c = Q R for the tall boxes; the groups then work on R's rows
@@ -433,7 +444,10 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
     HIF_CUDA((big_qr_init<T>(a, ng, max_n, st)));
     std::vector<BigState> hs(ng);
     for (int j = 0; j < maxk; ++j) {
-        HIF_CUDA((big_qr_step<T>(a, ng, max_n, j, st)));
+        {
+            ProfRange pr(PROF_BIG_QR, st, 0.0, 0.0);   // bytes added once the ranks are known
+            HIF_CUDA((big_qr_step<T>(a, ng, max_n, j, st)));
+        }
         if ((j + 1) % 16 == 0) {
             HIF_CUDA(cudaMemcpyAsync(hs.data(), B.state.p, sizeof(BigState) * ng, cudaMemcpyDeviceToHost, st));
             HIF_CUDA(cudaStreamSynchronize(st));
@@ -442,6 +456,7 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
             if (all) break;
         }
     }
+    ProfRange pr(PROF_BIG_T, st, 0.0, 0.0);
     HIF_CUDA((big_finish<T>(a, ng, max_n, st)));
 }
 
@@ -449,7 +464,8 @@ template <typename T>
 static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc>& ed,
                          const std::vector<ElimDesc>& ed_big, const std::vector<ElimGroup>& eg,
                          const std::vector<int>& skv, const std::vector<int>& rdv, int64_t fac_off, int64_t piv_off,
-                         int64_t ws_off, void* sci_pool, int nsub_sci, DevMem& Tws, FactorScratch& S) {
+                         int64_t ws_off, void* sci_pool, int nsub_sci, DevMem& Tws, FactorScratch& S,
+                         const double* work) {
     const cudaStream_t st = h->st;
     upload(S.d_ed, ed, st);
     upload(S.d_eg, eg, st);
@@ -475,7 +491,17 @@ static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc
     ea.perm_pool = sf.perm.as<int>();
     ea.sci_pool = sci_pool;
     ea.status = h->status.as<int>();
-    HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), st)));
+    S.ldl_fail.ensure(sizeof(int) * std::max<size_t>(ed.size(), 1));
+    HIF_CUDA(cudaMemsetAsync(S.ldl_fail.p, 0, sizeof(int) * std::max<size_t>(ed.size(), 1), st));
+    ea.ldl_fail = S.ldl_fail.as<int>();
+    // HIF_LDL_TEST_ALPHA (tests only): a larger acceptance constant, so that
+    // the LU fallback of LDL boxes can be exercised on any problem
+    ea.ldl_alpha = (1.0 + std::sqrt(17.0)) / 8.0;
+    if (const char* v = std::getenv("HIF_LDL_TEST_ALPHA")) ea.ldl_alpha = std::atof(v);
+    {
+        ProfRange pr(PROF_ELIM, st, work[0], 0.0);
+        HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), st)));
+    }
     if (!ed_big.empty()) {
         upload(S.d_ed_big, ed_big, st);
         int mxn = 0, mxk = 0, mxr = 0;
@@ -499,27 +525,34 @@ static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc
         ba.perm = sf.perm.as<int>();
         ba.sci_pool = sci_pool;
         ba.status = h->status.as<int>();
+        ProfRange pr(PROF_BIG_ELIM, st, work[1], 0.0);
         HIF_CUDA((big_elim_batch<T>(ba, mxn, mxk, mxr, st)));
     }
-    h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
 }
 
-// Factor offsets of one eliminated box inside its sublevel's pools.
-static void place_box(ElimDesc& e, BoxFac& bf, int k, int r, int64_t& fac_off, int64_t& piv_off, int64_t& ws_off) {
+// Factor offsets of one eliminated box inside its sublevel's pools.  An LDL
+// box (symmetric A, Sec. 5) keeps T, L (with L^{-1} packed in the same r x r
+// array), D and X; Y = X^T and U = L^T P are not stored.
+static void place_box(ElimDesc& e, BoxFac& bf, int k, int r, bool ldl, int64_t& fac_off, int64_t& piv_off,
+                      int64_t& ws_off) {
     const int n = k + r;
     e.k = k;
     e.r = r;
+    e.ldl = ldl ? 1 : 0;
     e.ws_off = ws_off;
     ws_off += (int64_t)n * n + (int64_t)k * r;
     e.T_out = fac_off; fac_off += (int64_t)k * r;
     e.LU_out = fac_off; fac_off += (int64_t)r * r;
-    e.LUi_out = fac_off; fac_off += (int64_t)r * r;
+    if (ldl) e.LUi_out = e.LU_out;
+    else { e.LUi_out = fac_off; fac_off += (int64_t)r * r; }
     e.D_out = fac_off; fac_off += r;
     e.X_out = fac_off; fac_off += (int64_t)k * r;
-    e.Y_out = fac_off; fac_off += (int64_t)r * k;
+    if (ldl) e.Y_out = e.X_out;
+    else { e.Y_out = fac_off; fac_off += (int64_t)r * k; }
     e.piv_out = piv_off; piv_off += r;
     bf.k = k;
     bf.r = r;
+    bf.ldl = e.ldl;
     bf.sk_off = e.sk_off;
     bf.rd_off = e.rd_off;
     bf.T_off = e.T_out;
@@ -529,6 +562,68 @@ static void place_box(ElimDesc& e, BoxFac& bf, int k, int r, int64_t& fac_off, i
     bf.X_off = e.X_out;
     bf.Y_off = e.Y_out;
     bf.piv_off = e.piv_out;
+}
+
+// The eliminations of one sublevel (or of the top blocks): boxes in factor
+// order, each in the one-CTA list (ed) or the batched multi-CTA list
+// (ed_big).  Places every box in the sublevel's pools, launches, and, if an
+// LDL box met a pivot that fails the 1 x 1 test, gives that box the LU form
+// and runs the sublevel's eliminations once more (every box recomputes its
+// block from the unchanged inputs, so the others are reproduced exactly).
+struct ElimPlan {
+    std::vector<ElimDesc> ed, ed_big;
+    std::vector<std::pair<bool, int>> where;   // per factor box: (in ed_big, index)
+    std::vector<ElimGroup> eg;
+    std::vector<int> skv, rdv;
+    double work[2] = {0.0, 0.0};
+    void add(const ElimDesc& e, bool big, double flops) {
+        where.push_back({big, (int)(big ? ed_big.size() : ed.size())});
+        (big ? ed_big : ed).push_back(e);
+        work[big ? 1 : 0] += flops;
+    }
+};
+
+template <typename T>
+static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc>& ed,
+                         const std::vector<ElimDesc>& ed_big, const std::vector<ElimGroup>& eg,
+                         const std::vector<int>& skv, const std::vector<int>& rdv, int64_t fac_off, int64_t piv_off,
+                         int64_t ws_off, void* sci_pool, int nsub_sci, DevMem& Tws, FactorScratch& S,
+                         const double* work);
+
+template <typename T>
+static void eliminate(hif_handle h, SubFactor& sf, ElimPlan& ep, void* sci_pool, int nsub_sci, DevMem& Tws,
+                      FactorScratch& S) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int64_t fac_off = 0, piv_off = 0, ws_off = 0;
+        for (size_t q = 0; q < ep.where.size(); ++q) {
+            ElimDesc& e = ep.where[q].first ? ep.ed_big[ep.where[q].second] : ep.ed[ep.where[q].second];
+            place_box(e, sf.hbox[q], e.k, e.r, e.ldl != 0, fac_off, piv_off, ws_off);
+        }
+        launch_elims<T>(h, sf, ep.ed, ep.ed_big, ep.eg, ep.skv, ep.rdv, fac_off, piv_off, ws_off, sci_pool, nsub_sci,
+                        Tws, S, ep.work);
+        bool any_ldl = false;
+        for (const ElimDesc& e : ep.ed) any_ldl = any_ldl || e.ldl;
+        int stw = 0;
+        if (any_ldl) {
+            HIF_CUDA(cudaMemcpyAsync(&stw, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+            HIF_CUDA(cudaStreamSynchronize(h->st));
+        }
+        if (!(stw & DEV_LDL_FALLBACK) || attempt == 1) {
+            h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
+            for (const ElimDesc& e : ep.ed) h->stats.ldl_boxes += e.ldl ? 1 : 0;
+            if (stw & DEV_LDL_FALLBACK) fail(HIF_ENUMERIC, "LDL fallback repeated");
+            return;
+        }
+        std::vector<int> failed(ep.ed.size());
+        HIF_CUDA(cudaMemcpyAsync(failed.data(), S.ldl_fail.p, sizeof(int) * failed.size(), cudaMemcpyDeviceToHost,
+                                 h->st));
+        stw &= ~(int)DEV_LDL_FALLBACK;
+        HIF_CUDA(cudaMemcpyAsync(h->status.p, &stw, sizeof(int), cudaMemcpyHostToDevice, h->st));
+        HIF_CUDA(cudaStreamSynchronize(h->st));
+        for (size_t q = 0; q < failed.size(); ++q)
+            if (failed[q]) ep.ed[q].ldl = 0;
+        h->stats.ldl_fallbacks += (int64_t)std::count(failed.begin(), failed.end(), 1);
+    }
 }
 
 static void append_plan(SublevelPlan& p, const SublevelPlan& q) {
@@ -641,6 +736,7 @@ static void run_factor(hif_handle h) {
         bool any_sci = false;
         std::vector<int64_t> woff(ngr);
         std::vector<int> small_boxes, small_groups, big_boxes;
+        double fold_flops = 0.0;
         for (int bI = 0; bI < nb; ++bI) {
             BoxDesc& b = bd[bI];
             const bool isbig = (p.box_off[bI + 1] - p.box_off[bI]) > big_id_n;
@@ -666,6 +762,7 @@ static void run_factor(hif_handle h) {
             h->stats.proxy_rows += (int64_t)m;
             evals += (double)(b.m_near + h->P) * b.n;
             flops += 2.0 * m * b.n * b.n;
+            if (!isbig) fold_flops += 2.0 * m * b.n * b.n;
             for (int q = 0; q < b.ngroups; ++q) {
                 const int64_t gi = b.grp_off + q;
                 GroupDesc& G = gd[gi];
@@ -726,7 +823,10 @@ static void run_factor(hif_handle h) {
                 smem = fold_smem_bytes(maxn, fa.bpairs, grams, false, sizeof(T));
                 if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
             }
-            HIF_CUDA((launch_fold<T>(fa, (int)small_boxes.size(), smem, st)));
+            {
+                ProfRange pr(PROF_FOLD, st, fold_flops, 0.0);
+                HIF_CUDA((launch_fold<T>(fa, (int)small_boxes.size(), smem, st)));
+            }
 
             IdArgs ia{};
             ia.groups = d_groups.as<GroupDesc>();
@@ -749,7 +849,10 @@ static void run_factor(hif_handle h) {
             }
             ia.Wws = Wws.p;
             ia.W_off = Woff.as<int64_t>();
-            HIF_CUDA((launch_id<T>(ia, (int)small_groups.size(), ismem, st)));
+            {
+                ProfRange pr(PROF_ID, st, 0.0, 0.0);     // work added once the ranks are known
+                HIF_CUDA((launch_id<T>(ia, (int)small_groups.size(), ismem, st)));
+            }
         }
         if (!big_boxes.empty()) run_big_id<T>(h, tau, bd, gd, p, big_boxes, d_boxes, d_groups, d_cols, d_near, Tws,
                                               perm_out, k_out, tol_floor, big);
@@ -761,15 +864,36 @@ static void run_factor(hif_handle h) {
             HIF_CUDA(cudaMemcpyAsync(permh.data(), perm_out.p, sizeof(int) * permh.size(), cudaMemcpyDeviceToHost, st));
         HIF_CUDA(cudaStreamSynchronize(st));
         const auto tr2 = std::chrono::steady_clock::now();
+        if (prof_enabled()) {
+            // pivoted QR to rank k of an mrow x ng block plus T = R1^{-1} R2;
+            // large groups: one read + write of the remaining columns per step
+            double idf = 0.0, qr_bytes = 0.0;
+            for (int64_t gi = 0; gi < ngr; ++gi) {
+                const GroupDesc& G = gd[gi];
+                const BoxDesc& b = bd[G.box];
+                const double k = kg[gi], n = G.n, r = n - k;
+                const bool isbig = b.n > big_id_n;
+                if (!isbig) {
+                    const double mr = G.col0 + G.n;
+                    idf += 4.0 * mr * n * k - 2.0 * k * k * (mr + n) + 4.0 * k * k * k / 3.0 + k * k * r;
+                } else {
+                    const double m = (b.sym ? 1.0 : 2.0) * (b.m_near + h->P);
+                    for (int j = 0; j < kg[gi]; ++j) qr_bytes += 2.0 * sizeof(T) * m * (n - j);
+                }
+            }
+            prof_add_work(PROF_ID, idf, 0.0);
+            prof_add_work(PROF_BIG_QR, 0.0, qr_bytes);
+        }
 
         // ---- skeleton / redundant sets, elimination descriptors
         auto sf = std::make_unique<SubFactor>();
         sf->kind = kind;
         sf->level = ell;
-        std::vector<ElimDesc> ed, ed_big;
-        std::vector<ElimGroup> eg;
-        std::vector<int> skv, rdv;
-        int64_t fac_off = 0, piv_off = 0, sci_off = 0, ws_off = 0;
+        ElimPlan ep;
+        std::vector<ElimGroup>& eg = ep.eg;
+        std::vector<int>& skv = ep.skv;
+        std::vector<int>& rdv = ep.rdv;
+        int64_t sci_off = 0;
         struct NewBlock { int box; int64_t sk_off; int k; int64_t sci_off; };
         std::vector<NewBlock> nblk;
         int64_t ksum = 0, rsum = 0;
@@ -810,8 +934,11 @@ static void run_factor(hif_handle h) {
                 const int kq = kg[b.grp_off + q];
                 for (int l = kq; l < G.n; ++l) rdv.push_back(p.cols[b.col_off + G.col0 + permh[G.perm_off + l]]);
             }
-            BoxFac bf{};
-            place_box(e, bf, k, r, fac_off, piv_off, ws_off);
+            e.k = k;
+            e.r = r;
+            const bool big = k + r > big_elim_n;
+            // LDL for symmetric problems (Sec. 5) on the one-CTA path
+            e.ldl = (h->opt.ldl && b.sym && !big) ? 1 : 0;
             if (k > 0) {
                 e.sci_out = sci_off;
                 nblk.push_back({bI, e.sk_off, k, sci_off});
@@ -819,13 +946,14 @@ static void run_factor(hif_handle h) {
             } else {
                 e.sci_out = -1;
             }
+            BoxFac bf{};
             sf->hbox.push_back(bf);
             sf->max_kr2 = std::max(sf->max_kr2, k + 2 * r);
-            if (k + r > big_elim_n) ed_big.push_back(e);
-            else ed.push_back(e);
             const double kk = k, rr = r;
-            flops += 2.0 * (kk * kk * rr + 2 * kk * rr * rr + kk * kk * rr) + 2.0 / 3.0 * rr * rr * rr +
-                     2.0 * kk * rr * rr + 2.0 * kk * kk * rr;
+            const double ef = 2.0 * (kk * kk * rr + 2 * kk * rr * rr + kk * kk * rr) + 2.0 / 3.0 * rr * rr * rr +
+                              2.0 * kk * rr * rr + 2.0 * kk * kk * rr;
+            flops += ef;
+            ep.add(e, big, ef);
         }
         sf->nbox = (int)sf->hbox.size();
         h->stats.kinds[tau] = kind;
@@ -842,8 +970,7 @@ static void run_factor(hif_handle h) {
             h->blk_ptr_h.push_back(static_cast<char*>(pool->p) + sizeof(T) * nbk.sci_off);
             h->blk_k_h.push_back(nbk.k);
         }
-        if (sf->nbox)
-            launch_elims<T>(h, *sf, ed, ed_big, eg, skv, rdv, fac_off, piv_off, ws_off, pool->p, (int)tau, Tws, S);
+        if (sf->nbox) eliminate<T>(h, *sf, ep, pool->p, (int)tau, Tws, S);
         h->sci_pools.push_back(std::move(pool));
 
         // ---- state for the next sublevel: active set and SCI membership
@@ -886,10 +1013,9 @@ static void run_factor(hif_handle h) {
         auto sf = std::make_unique<SubFactor>();
         sf->kind = KIND_TOP;
         sf->level = maxL;
-        std::vector<ElimDesc> ed, ed_big;
-        std::vector<ElimGroup> eg;
-        std::vector<int> skv, rdv;
-        int64_t fac_off = 0, piv_off = 0, ws_off = 0, top = 0;
+        ElimPlan ep;
+        std::vector<int>& rdv = ep.rdv;
+        int64_t top = 0;
         for (auto& sp : h->segs) {
             const Segment& sg = *sp;
             ElimDesc e{};
@@ -903,18 +1029,21 @@ static void run_factor(hif_handle h) {
             const int r = (int)((int64_t)rdv.size() - e.rd_off);
             if (r == 0) continue;
             top += r;
+            e.k = 0;
+            e.r = r;
+            const bool big = r > big_elim_n;
+            e.ldl = (h->opt.ldl && sg.sym && !big) ? 1 : 0;
             BoxFac bf{};
-            place_box(e, bf, 0, r, fac_off, piv_off, ws_off);
             sf->hbox.push_back(bf);
             sf->max_kr2 = std::max(sf->max_kr2, 2 * r);
-            if (r > big_elim_n) ed_big.push_back(e);
-            else ed.push_back(e);
-            flops += 2.0 / 3.0 * (double)r * r * r + 2.0 * (double)r * r * r / 3.0;
+            const double tf = 2.0 / 3.0 * (double)r * r * r + 2.0 * (double)r * r * r / 3.0;
+            flops += tf;
+            ep.add(e, big, tf);
         }
         sf->nbox = (int)sf->hbox.size();
         h->stats.top_size = top;
         if (sf->nbox) {
-            launch_elims<T>(h, *sf, ed, ed_big, eg, skv, rdv, fac_off, piv_off, ws_off, nullptr, (int)nsub, Tws, S);
+            eliminate<T>(h, *sf, ep, nullptr, (int)nsub, Tws, S);
             HIF_CUDA(cudaStreamSynchronize(st));
             check_status(h);
         }
@@ -976,6 +1105,12 @@ static void ensure_sweep_ws(hif_handle h, int nrhs, size_t elem) {
 template <typename T>
 static void sweep_all(hif_handle h, T* xw, int64_t ldx, int nrhs, int op) {
     ensure_sweep_ws(h, nrhs, sizeof(T));
+    double sweep_bytes = 0.0;
+    if (prof_enabled())
+        for (auto& sf : h->subs)
+            sweep_bytes += sizeof(T) * (sf->sweep_factor_elems + 4.0 * sf->sweep_vec_elems * nrhs) +
+                           sizeof(int) * sf->sweep_perm_ints;
+    ProfRange pr(PROF_SWEEP, h->st, 0.0, sweep_bytes);
     if (!h->opt.use_graphs || ldx != h->N) {
         sweep_seq<T>(h, xw, ldx, nrhs, op, h->st);
         return;
@@ -1022,6 +1157,13 @@ static void prepare_sweeps(hif_handle h) {
     const cudaStream_t st = h->st;
     for (auto& sp : h->subs) {
         SubFactor& sf = *sp;
+        sf.sweep_factor_elems = sf.sweep_perm_ints = sf.sweep_vec_elems = 0;
+        for (const BoxFac& bf : sf.hbox) {
+            const double k = bf.k, r = bf.r;
+            sf.sweep_factor_elems += 4.0 * k * r + r * r;
+            sf.sweep_perm_ints += r;
+            sf.sweep_vec_elems += k + r;
+        }
         sf.global = (size_t)sf.max_kr2 * sizeof(T) > 200 * 1024;
         if (!sf.global || !sf.nbox) continue;
         std::vector<int64_t> offs(sf.hbox.size());
@@ -1138,6 +1280,7 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
             ga.ybuf = h->ybuf.as<double>();
             if (h->opt.direct_precision == 0) {
                 h->vdf.ensure(sizeof(float2) * n * nrhs);
+                ProfRange pr(PROF_DIRECT, st, 2.0 * (double)n * n * nrhs, 0.0);
                 HIF_CUDA(launch_direct_grid_df(ga, sg.table_df.as<float2>(), h->vdf.as<float2>(), st));
             } else if (h->opt.direct_precision == 2) {
                 if (!sg.tc_rows.p) {
@@ -1150,14 +1293,18 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
                 h->tc_xmax.ensure(8 * sizeof(unsigned long long));
                 h->tc_status.ensure(sizeof(int));
                 HIF_CUDA(cudaMemsetAsync(h->tc_status.p, 0, sizeof(int), st));
-                HIF_CUDA(launch_direct_grid_tc(ga, sg.tc_rows.p, sg.tc_tmax.as<unsigned long long>(), h->tc_xb.p,
-                                               h->tc_xmax.as<unsigned long long>(), h->tc_status.as<int>(),
-                                               h->num_sms, st));
+                {
+                    ProfRange pr(PROF_DIRECT, st, 2.0 * (double)n * n * nrhs, 0.0);
+                    HIF_CUDA(launch_direct_grid_tc(ga, sg.tc_rows.p, sg.tc_tmax.as<unsigned long long>(), h->tc_xb.p,
+                                                   h->tc_xmax.as<unsigned long long>(), h->tc_status.as<int>(),
+                                                   h->num_sms, st));
+                }
                 int flag = 0;
                 HIF_CUDA(cudaMemcpyAsync(&flag, h->tc_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
                 HIF_CUDA(cudaStreamSynchronize(st));
                 if (flag) fail(HIF_ETIMEOUT, "tensor-core direct sum: a pipeline wait expired");
             } else {
+                ProfRange pr(PROF_DIRECT, st, 2.0 * (double)n * n * nrhs, 0.0);
                 HIF_CUDA(launch_direct_grid(ga, st));
             }
         } else {
@@ -1171,6 +1318,7 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
             da.trans = trans;
             da.seg_off = sg.off;
             da.seg_n = sg.N;
+            ProfRange pr(PROF_DIRECT, st, 2.0 * (double)sg.N * sg.N * nrhs, 0.0);
             HIF_CUDA(launch_direct_general(da, st));
         }
     }
@@ -1469,6 +1617,23 @@ hif_status hif_kernel_timing(int enable, double* ms, int64_t* launches) {
     });
 }
 
+hif_status hif_kernel_profile(int enable, hif_profile_entry* out, int cap, int* count) {
+    return guard([&] {
+        int64_t rg[PROF_COUNT];
+        double ms[PROF_COUNT], fl[PROF_COUNT], by[PROF_COUNT];
+        HIF_CUDA(prof_collect(rg, ms, fl, by));
+        if (count) *count = PROF_COUNT;
+        for (int k = 0; out && k < PROF_COUNT && k < cap; ++k) {
+            out[k].name = prof_name(k);
+            out[k].ranges = rg[k];
+            out[k].ms = ms[k];
+            out[k].flops = fl[k];
+            out[k].bytes = by[k];
+        }
+        prof_set(enable != 0);
+    });
+}
+
 hif_status hif_options_default(int dim, hif_options* opt) {
     if (!opt || (dim != 2 && dim != 3)) return HIF_EINVAL;
     std::memset(opt, 0, sizeof(*opt));
@@ -1486,6 +1651,7 @@ hif_status hif_options_default(int dim, hif_options* opt) {
     opt->use_graphs = 1;
     opt->autotune = 1;
     opt->symmetric = 1;
+    opt->ldl = 1;
     opt->root_width = 0.0;
     opt->stream = nullptr;
     return HIF_OK;
@@ -1513,6 +1679,7 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
     if (opt.precision != 0 && opt.precision != 1) return HIF_EINVAL;
     if (opt.direct_precision < 0 || opt.direct_precision > 2) return HIF_EINVAL;
     if (opt.symmetric != 0 && opt.symmetric != 1) return HIF_EINVAL;
+    if (opt.ldl != 0 && opt.ldl != 1) return HIF_EINVAL;
     if (opt.dim == 3 && !opt.proxy_dirs) return HIF_EINVAL;
     auto h = std::make_unique<hif_handle_s>();
     const auto t0 = std::chrono::steady_clock::now();
@@ -1864,7 +2031,15 @@ extern "C" {
 hif_status hif_id_batched_noalloc(int count, const double* mats, const int64_t* off, const int32_t* m,
                                   const int32_t* n, const double* tol, int32_t* k, int32_t* perm,
                                   const int64_t* poff, double* T, const int64_t* toff, void* stream) {
-    if (count < 0 || !mats || !off || !m || !n || !tol || !k || !perm || !poff || !T || !toff) return HIF_EINVAL;
+    g_last_error[0] = '\0';
+    if (count < 0) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "hif_id_batched_noalloc: negative count %d", count);
+        return HIF_EINVAL;
+    }
+    if (!mats || !off || !m || !n || !tol || !k || !perm || !poff || !T || !toff) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "hif_id_batched_noalloc: a required array is NULL");
+        return HIF_EINVAL;
+    }
     if (count == 0) return HIF_OK;
     const void* ptrs[] = {mats, off, m, n, tol, k, perm, poff, T, toff};
     for (const void* p : ptrs) {

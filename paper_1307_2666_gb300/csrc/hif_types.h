@@ -64,7 +64,7 @@ struct GroupDesc {
 struct ElimDesc {
     int k, r;
     int ngroups;
-    int pad;
+    int ldl;              // 1: P B_rr P^T = L D L^T (symmetric A, Sec. 5); 0: LU
     int64_t sk_off;       // into the sk ids array (global DOF ids, skeleton order)
     int64_t rd_off;       // into the rd ids array
     int64_t grp_off;      // into the per-group (k_g, r_g, T_off, ko, ro) table
@@ -83,13 +83,16 @@ struct ElimGroup {
 // Factor record of one box, read by the sweeps (Eqs. (3.4), (4.1)).
 struct BoxFac {
     int k, r;
+    int ldl;              // LDL box: U = L^T P, Y = X^T; LU_off holds L (strict lower)
+                          // and L^{-1} transposed (strict upper); LUi_off == LU_off
+    int pad;
     int64_t sk_off, rd_off;                       // into the sublevel's id arrays
     int64_t T_off, LU_off, LUi_off, D_off, X_off, Y_off;
     int64_t piv_off;
 };
 
 // Status word written by kernels that detect trouble (checked by the host).
-enum DevStatus : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADSIZE = 4 };
+enum DevStatus : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADSIZE = 4, DEV_LDL_FALLBACK = 8 };
 
 // Counts kernel launches made by the library (diagnostic, see hif_kernel_launches).
 void note_launch();

@@ -491,6 +491,59 @@ __global__ void __launch_bounds__(128) elim_kernel(ElimArgs args) {
     // B_rr = A_rr - T^T B_sr - A_rs T  (= A_rr - T^T A_sr - A_rs T + T^T A_ss T)
     cta_gemm<T>(r, r, k, T(-1), Tm, k, true, Asr, ld, false, Arr, ld);
     cta_gemm<T>(r, r, k, T(-1), Ars, ld, false, Tm, k, false, Arr, ld);
+    if (ed.ldl) {
+        // symmetric A (Sec. 5): P B_rr P^T = L D L^T, B_rs = B_sr^T
+        const int res = cta_ldl_diag<T>(r, Arr, ld, piv, Asr, ld, k, redv, redi, (T)args.ldl_alpha);
+        if (res != 0) {
+            if (threadIdx.x == 0) atomicOr(args.status, res == 2 ? (int)DEV_SINGULAR : (int)DEV_LDL_FALLBACK);
+            if (threadIdx.x == 0 && res == 1) args.ldl_fail[blockIdx.x] = 1;
+            return;
+        }
+        // X' = B_sr P^T L^{-T}, then X = X' D^{-1}
+        cta_trsm_right_unit_lower_t<T>(r, Arr, ld, Asr, ld, k);
+        T* pool = static_cast<T*>(args.fac_pool);
+        T* Dv = pool + ed.D_out;
+        for (int i = threadIdx.x; i < r; i += blockDim.x) Dv[i] = Arr[i + ld * i];
+        __syncthreads();
+        for (int e = threadIdx.x; e < k * r; e += blockDim.x) {
+            const int i = e % k, j = e / k;
+            Asr[i + ld * j] /= Dv[j];
+        }
+        __syncthreads();
+        // Schur update -X D X^T on the skeletons (new SCI block, symmetric)
+        if (k > 0 && ed.sci_out >= 0) {
+            T* S = static_cast<T*>(args.sci_pool) + ed.sci_out;
+            for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+                const int a = e % k, c = e / k;
+                T acc = T(0);
+                for (int l = 0; l < r; ++l) acc += Asr[a + ld * l] * Dv[l] * Asr[c + ld * l];
+                S[e] = -acc;
+            }
+        }
+        T* LL = pool + ed.LU_out;
+        T* Xo = pool + ed.X_out;
+        T* To = pool + ed.T_out;
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+            const int i = e % r, j = e / r;
+            LL[e] = i > j ? Arr[i + ld * j] : T(0);
+        }
+        for (int e = threadIdx.x; e < k * r; e += blockDim.x) {
+            const int i = e % k, j = e / k;
+            Xo[e] = Asr[i + ld * j];
+            To[e] = Tm[e];
+        }
+        __syncthreads();
+        cta_unit_lower_inverse_to_upper<T>(r, LL);
+        if (threadIdx.x == 0) {
+            int* pm = args.perm_pool + ed.piv_out;
+            for (int i = 0; i < r; ++i) pm[i] = i;
+            for (int j = 0; j < r; ++j) {
+                const int p = piv[j];
+                const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
+            }
+        }
+        return;
+    }
     // B_rs = A_rs - T^T A_ss
     cta_gemm<T>(r, k, k, T(-1), Tm, k, true, Ass, ld, false, Ars, ld);
     // P B_rr = L (D U)                (Lemma 2.1)
@@ -674,12 +727,14 @@ template cudaError_t launch_elim<float>(const ElimArgs&, int, cudaStream_t);
 
 // ------------------------------------------- batched ID without allocation --
 //
-// For callers that may not allocate memory (code running where cudaMalloc is
-// forbidden or would synchronize, e.g. inside a region being captured into a
-// CUDA graph, or under a strict memory budget): the work space of the batched
-// ID lives in one file-scope device array, sized once for the whole process.
-// Its layout: per-matrix work-space offsets, an error flag, then the copies of
-// the matrices that the QR overwrites.
+// For callers that may not allocate device memory: services that size their
+// device memory once at start-up and must not fail on an allocation later,
+// and callers that must not call cudaMalloc/cudaFree at all because those
+// calls can synchronize the whole device and stall work on other streams.
+// The work space of the batched ID lives in one file-scope device array,
+// sized once for the whole process.  Its layout: per-matrix work-space
+// offsets, an error flag, then the copies of the matrices that the QR
+// overwrites.  The flag is rewritten by every call's first kernel.
 
 namespace hif {
 

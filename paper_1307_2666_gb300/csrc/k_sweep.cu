@@ -91,34 +91,32 @@ __device__ void scale_rows(T* v, const T* D, int n, bool divide, int nr) {
 
 }  // namespace
 
+// For an LDL box (symmetric A, Sec. 5: P B_rr P^T = L D L^T, U = L^T P,
+// Y = X^T) the box's factors are symmetric, so the transposed operation of a
+// pass is the pass itself: solve_down = solve^T_down, solve^T_up = solve_up,
+// apply_up = apply^T_up, apply^T_down = apply_down.  Those four bodies read
+// only T, X, D, the permutation and L or L^{-1} (packed in one array: L in the
+// strict lower triangle, L^{-1} transposed in the strict upper one).
+__host__ __device__ constexpr int ldl_mode(int m) {
+    return m == SOLVE_DOWN ? SOLVET_DOWN : m == SOLVET_UP ? SOLVE_UP : m == APPLY_UP ? APPLYT_UP
+         : m == APPLYT_DOWN ? APPLY_DOWN : m;
+}
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
-    const BoxFac bf = a.boxes[blockIdx.x];
-    const int k = bf.k, r = bf.r, nr = a.nrhs;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xs = a.gws ? static_cast<T*>(a.gws) + a.gws_off[blockIdx.x] * nr : reinterpret_cast<T*>(smem_raw);
-    T* xr = xs + (size_t)k * nr;
-    T* tmp = xr + (size_t)r * nr;
-    T* x = static_cast<T*>(a.x);
-    const int* sk = a.sk_ids + bf.sk_off;
-    const int* rd = a.rd_ids + bf.rd_off;
-    const T* pool = static_cast<const T*>(a.pool);
+__device__ void sweep_box(const BoxFac& bf, const T* pool, const int* perm, T* xs, T* xr, T* tmp, int nr) {
+    const int k = bf.k, r = bf.r;
+    const bool ldl = bf.ldl != 0;
     const T* Tm = pool + bf.T_off;
     const T* LU = pool + bf.LU_off;
     const T* LUi = pool + bf.LUi_off;
     const T* D = pool + bf.D_off;
     const T* X = pool + bf.X_off;
     const T* Y = pool + bf.Y_off;
-    const int* perm = a.perm + bf.piv_off;
-
-    for (int e = threadIdx.x; e < k * nr; e += blockDim.x) xs[e] = x[sk[e % k] + a.ldx * (e / k)];
-    for (int e = threadIdx.x; e < r * nr; e += blockDim.x) xr[e] = x[rd[e % r] + a.ldx * (e / r)];
-    __syncthreads();
-
     if (MODE == SOLVE_UP) {                 // U^T: Q^T then R^T
         mv<T>(xr, r, xs, k, Tm, k, true, T(-1), nr);
         permute<T>(tmp, xr, r, perm, false, nr);
-        tri<T>(xr, tmp, r, LUi, r, true, false, nr);
+        // L^{-1}: strict lower of LUi (LU box) or transposed in the upper (LDL box)
+        tri<T>(xr, tmp, r, LUi, r, !ldl, ldl, nr);
         mv<T>(xs, k, xr, r, X, k, false, T(-1), nr);
     } else if (MODE == SOLVE_DOWN) {        // D^{-1} then V = Q S
         scale_rows<T>(xr, D, r, true, nr);
@@ -145,7 +143,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     } else if (MODE == SOLVET_DOWN) {       // D^{-T} then U = Q R
         scale_rows<T>(xr, D, r, true, nr);
         mv<T>(xr, r, xs, k, X, k, true, T(-1), nr);
-        tri<T>(tmp, xr, r, LUi, r, true, true, nr);
+        // L^{-T}: strict lower of LUi transposed (LU box) or the upper as stored (LDL box)
+        tri<T>(tmp, xr, r, LUi, r, !ldl, !ldl, nr);
         permute<T>(xr, tmp, r, perm, true, nr);
         mv<T>(xs, k, xr, r, Tm, k, false, T(-1), nr);
     } else if (MODE == APPLYT_UP) {         // U^{-1} = R^{-1} Q^{-1}, then D
@@ -160,6 +159,28 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
         tri<T>(xr, tmp, r, LU, r, false, true, nr);
         mv<T>(xr, r, xs, k, Tm, k, true, T(1), nr);
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
+    const BoxFac bf = a.boxes[blockIdx.x];
+    const int k = bf.k, r = bf.r, nr = a.nrhs;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = a.gws ? static_cast<T*>(a.gws) + a.gws_off[blockIdx.x] * nr : reinterpret_cast<T*>(smem_raw);
+    T* xr = xs + (size_t)k * nr;
+    T* tmp = xr + (size_t)r * nr;
+    T* x = static_cast<T*>(a.x);
+    const int* sk = a.sk_ids + bf.sk_off;
+    const int* rd = a.rd_ids + bf.rd_off;
+    const T* pool = static_cast<const T*>(a.pool);
+    const int* perm = a.perm + bf.piv_off;
+
+    for (int e = threadIdx.x; e < k * nr; e += blockDim.x) xs[e] = x[sk[e % k] + a.ldx * (e / k)];
+    for (int e = threadIdx.x; e < r * nr; e += blockDim.x) xr[e] = x[rd[e % r] + a.ldx * (e / r)];
+    __syncthreads();
+
+    if (bf.ldl) sweep_box<T, ldl_mode(MODE)>(bf, pool, perm, xs, xr, tmp, nr);
+    else sweep_box<T, MODE>(bf, pool, perm, xs, xr, tmp, nr);
 
     for (int e = threadIdx.x; e < k * nr; e += blockDim.x) x[sk[e % k] + a.ldx * (e / k)] = xs[e];
     for (int e = threadIdx.x; e < r * nr; e += blockDim.x) x[rd[e % r] + a.ldx * (e / r)] = xr[e];

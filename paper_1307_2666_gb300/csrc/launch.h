@@ -59,6 +59,8 @@ struct ElimArgs {
     int* perm_pool;
     void* sci_pool;
     int* status;
+    int* ldl_fail;          // per box of the launch: 1 when its LDL pivot failed the test
+    double ldl_alpha;       // 1 x 1 pivot acceptance constant ((1 + sqrt 17) / 8)
 };
 
 struct SweepArgs {

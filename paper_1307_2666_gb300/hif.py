@@ -38,6 +38,17 @@ class hif_options(C.Structure):
         ("use_graphs", C.c_int),
         ("autotune", C.c_int),
         ("symmetric", C.c_int),
+        ("ldl", C.c_int),
+    ]
+
+
+class hif_profile_entry(C.Structure):
+    _fields_ = [
+        ("name", C.c_char_p),
+        ("ranges", C.c_int64),
+        ("ms", C.c_double),
+        ("flops", C.c_double),
+        ("bytes", C.c_double),
     ]
 
 
@@ -70,6 +81,8 @@ class hif_stats_t(C.Structure):
         ("kernel_evals", C.c_double),
         ("proxy_rows", C.c_int64),
         ("symmetric_problems", C.c_int),
+        ("ldl_boxes", C.c_int64),
+        ("ldl_fallbacks", C.c_int64),
     ]
 
 
@@ -97,6 +110,7 @@ EXPORTS = {
     "hif_last_error": (C.c_char_p, []),
     "hif_kernel_launches": (C.c_uint64, []),
     "hif_kernel_timing": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "hif_kernel_profile": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "hif_kernel_block": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                    C.c_void_p]),
@@ -280,6 +294,7 @@ def hif_stats(h) -> dict:
         "N": s.N, "dim": s.dim, "levels": s.levels, "sublevels": n, "top_size": s.top_size,
         "factor_bytes": s.factor_bytes, "factor_seconds": s.factor_seconds, "flops": s.flops,
         "kernel_evals": s.kernel_evals, "proxy_rows": s.proxy_rows, "symmetric_problems": s.symmetric_problems,
+        "ldl_boxes": s.ldl_boxes, "ldl_fallbacks": s.ldl_fallbacks,
         "per_sublevel": [dict(kind=kind[s.kinds[i]], boxes=s.boxes[i], skeletons=s.skeletons[i],
                               redundant=s.redundant[i], max_box=s.max_box[i]) for i in range(n)],
     }
@@ -287,6 +302,17 @@ def hif_stats(h) -> dict:
 
 def hif_kernel_launches() -> int:
     return int(load().hif_kernel_launches())
+
+
+def hif_kernel_profile(enable: bool) -> dict:
+    """Per kernel family since the previous call: {name: {ranges, ms, flops,
+    bytes}}; then turns per-family event recording on or off."""
+    arr = (hif_profile_entry * 32)()
+    cnt = C.c_int(0)
+    _check(load().hif_kernel_profile(1 if enable else 0, C.cast(arr, C.c_void_p), 32, C.byref(cnt)),
+           "hif_kernel_profile")
+    return {arr[k].name.decode(): dict(ranges=int(arr[k].ranges), ms=float(arr[k].ms), flops=float(arr[k].flops),
+                                       bytes=float(arr[k].bytes)) for k in range(min(cnt.value, 32))}
 
 
 def hif_kernel_timing(enable: bool) -> tuple[float, int]:

@@ -121,3 +121,37 @@ def test_graphs_and_autotune_leave_results_unchanged(P):
         for a, b in zip(outs[0][k], outs[1][k]):
             assert torch.equal(a, b)
     assert counts[0] == counts[1] == counts[2] == counts[3] > 0
+
+
+def test_config3_batched_256_problems_refined(P):
+    # the batched configuration at its stated size: 256 problems with n drawn
+    # from {32, 48, ..., 256} (seed 1004), b = c = 1 + 0.5 phi_p (seed
+    # 2000 + p), 4 Gaussian right-hand sides each (seed 3000 + p), eps 1e-6,
+    # FP32 batched handle refined to 1e-10; every problem's residual is
+    # re-estimated from sampled rows of the oracle's FP64 operator, and the
+    # problems with n <= 48 are compared with their dense solves
+    sizes = hi.batched_sizes(256, 1004)
+    pbs = [hi.volume_problem(n, 2, smooth_seed=2000 + q, rhs_seed=3000 + q, nrhs=4) for q, n in enumerate(sizes)]
+    probs = [(T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)) for pb in pbs]
+    fb = P.Factorization.batched(probs, 0, 1e-6, precision="fp32")
+    off = fb.offsets
+    assert off[-1] == sum(pb.N for pb in pbs)
+    F = np.vstack([pb.f for pb in pbs])
+    u, its, rel = fb.solve_refined(T(F), tol=1e-10)
+    assert rel <= 1e-10
+    u = u.cpu().numpy()
+    rng = np.random.default_rng(1004)
+    worst = 0.0
+    for q, pb in enumerate(pbs):
+        op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+        uq = u[off[q]:off[q + 1]]
+        rows = rng.choice(pb.N, 16, replace=False)
+        r = pb.f[rows] - op.matvec_rows(uq, rows)
+        est = np.sqrt(pb.N / 16) * np.linalg.norm(r, axis=0) / np.linalg.norm(pb.f, axis=0)
+        worst = max(worst, float(est.max()))
+        if pb.n <= 48:
+            ud = dense.DenseSolver(op).solve(pb.f)
+            assert np.linalg.norm(uq - ud) <= 1e-9 * np.linalg.norm(ud)
+    # 16 sampled rows: an estimate within a factor ~2 of the true norm
+    assert worst <= 3e-10, worst
+    fb.close()

@@ -132,3 +132,59 @@ def test_batched_mixes_symmetric_and_general_problems(P):
         uq = dense.DenseSolver(op).solve(pb.f[:, 0])
         assert relerr(u[off[q]:off[q + 1]], uq) <= 100 * eps
     fb.close()
+
+
+# ------------------------------------------------ LDL (Sec. 5, opening) ---
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_ldl_equals_lu_and_stores_less(P, precision, tol):
+    # symmetric A: the diagonal blocks factored by LDL keep X only (Y = X^T)
+    # and one r x r array for L and L^{-1}; the block inverse is the same, so
+    # F and F^{-1} agree with the LU path to rounding
+    pb = hi.volume_problem(64, 2, smooth_seed=1002, rhs_seed=1001)
+    fl = factor(P, pb, 1e-6, precision=precision, ldl=True)
+    fu = factor(P, pb, 1e-6, precision=precision, ldl=False)
+    sl, su = fl.stats(), fu.stats()
+    assert sl["ldl_boxes"] > 0 and sl["ldl_fallbacks"] == 0 and su["ldl_boxes"] == 0
+    assert [s["skeletons"] for s in sl["per_sublevel"]] == [s["skeletons"] for s in su["per_sublevel"]]
+    assert sl["factor_bytes"] < 0.8 * su["factor_bytes"]
+    X = T(hi.gaussian_rhs(pb.N, 3, 31))
+    for op in ("apply", "solve", "solve_transpose", "apply_transpose"):
+        assert relerr(getattr(fl, op)(X).cpu().numpy(), getattr(fu, op)(X).cpu().numpy()) <= tol, op
+    if precision == "fp64":
+        # every LDL box is symmetric, so F^{-1} and F^{-T} agree to rounding
+        assert relerr(fl.solve(X).cpu().numpy(), fl.solve_transpose(X).cpu().numpy()) <= 1e-12
+        assert relerr(fl.apply(X).cpu().numpy(), fl.apply_transpose(X).cpu().numpy()) <= 1e-12
+        op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+        u = dense.DenseSolver(op).solve(pb.f[:, 0])
+        assert relerr(fl.solve(T(pb.f[:, 0])).cpu().numpy(), u) <= 100e-6
+    else:
+        x, its, rel = fl.solve_refined(T(pb.f[:, 0]), tol=1e-10)
+        assert rel <= 1e-10
+    fl.close()
+    fu.close()
+
+
+def test_ldl_falls_back_to_lu_per_box(P, monkeypatch):
+    # an acceptance constant no pivot can meet: every LDL box with r > 1
+    # takes the LU form, and the result is the LU path's
+    pb = hi.volume_problem(48, 2, smooth_seed=1002, rhs_seed=1001)
+    fu = factor(P, pb, 1e-6, ldl=False)
+    monkeypatch.setenv("HIF_LDL_TEST_ALPHA", "1e30")
+    fl = factor(P, pb, 1e-6, ldl=True)
+    monkeypatch.delenv("HIF_LDL_TEST_ALPHA")
+    st = fl.stats()
+    assert st["ldl_fallbacks"] > 0
+    X = T(hi.gaussian_rhs(pb.N, 2, 32))
+    for op in ("apply", "solve", "solve_transpose"):
+        assert relerr(getattr(fl, op)(X).cpu().numpy(), getattr(fu, op)(X).cpu().numpy()) <= 1e-12, op
+    fl.close()
+    fu.close()
+
+
+def test_ldl_not_used_for_nonsymmetric_problems(P):
+    pb = hi.volume_problem(32, 2, smooth_seed=1002)
+    pb.c = 1.0 + 0.5 * hi.smooth_field(pb.points, 99)
+    f = factor(P, pb, 1e-6)
+    assert f.stats()["ldl_boxes"] == 0 and f.stats()["symmetric_problems"] == 0
+    f.close()

@@ -51,7 +51,7 @@ def test_struct_layouts_match_header(lib):
     o = hif.hif_options_default(2)
     assert (o.dim, o.leaf_occupancy, o.second_kind, o.precision, o.fractional_levels) == (2, 64, 1, 0, 1)
     assert o.proxy_points == 64 and o.proxy_radius == 1.5 and o.fp32_tol_floor == 2.0 ** -17
-    assert o.direct_precision == 2 and o.use_graphs == 1 and o.autotune == 1 and o.symmetric == 1
+    assert o.direct_precision == 2 and o.use_graphs == 1 and o.autotune == 1 and o.symmetric == 1 and o.ldl == 1
     o3 = hif.hif_options_default(3)
     assert o3.proxy_points == 512
 
@@ -64,17 +64,20 @@ def test_ctypes_layouts_match_c_compiler(tmp_path):
     src.write_text('''#include <stdio.h>
 #include <stddef.h>
 #include "hif.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hif_options), offsetof(hif_options, proxy_radius),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hif_options),
+ offsetof(hif_options, proxy_radius),
  offsetof(hif_options, stream), offsetof(hif_options, direct_precision), offsetof(hif_options, autotune),
- offsetof(hif_options, symmetric),
+ offsetof(hif_options, symmetric), offsetof(hif_options, ldl),
  sizeof(hif_stats_t), offsetof(hif_stats_t, kinds), offsetof(hif_stats_t, flops),
- offsetof(hif_stats_t, top_size)); return 0;}''')
+ offsetof(hif_stats_t, top_size), offsetof(hif_stats_t, ldl_fallbacks),
+ sizeof(hif_profile_entry), offsetof(hif_profile_entry, bytes)); return 0;}''')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    O, S = hif.hif_options, hif.hif_stats_t
+    O, S, E = hif.hif_options, hif.hif_stats_t, hif.hif_profile_entry
     want = [ctypes.sizeof(O), O.proxy_radius.offset, O.stream.offset, O.direct_precision.offset, O.autotune.offset,
-            O.symmetric.offset, ctypes.sizeof(S), S.kinds.offset, S.flops.offset, S.top_size.offset]
+            O.symmetric.offset, O.ldl.offset, ctypes.sizeof(S), S.kinds.offset, S.flops.offset, S.top_size.offset,
+            S.ldl_fallbacks.offset, ctypes.sizeof(E), E.bytes.offset]
     assert got == want
 
 

@@ -569,3 +569,78 @@ def test_power_iteration_error_estimate():
     d = np.linspace(0.1, 2.0, 64)
     est = krylov.power_norm(lambda v: d * v, lambda v: d * v, 64, rtol=1e-6, maxit=2000)
     assert est == pytest.approx(2.0, rel=1e-3)
+
+
+# -------------------------------------------------------------------- LDL ---
+
+def test_ldl_diag_pivot_reconstructs_and_pivots_on_largest_diagonal():
+    rng = np.random.default_rng(31)
+    r = 40
+    G = rng.standard_normal((r, r))
+    B = 0.1 * (G + G.T) + np.diag(rng.uniform(0.5, 2.0, r) * np.where(rng.random(r) < 0.5, -1.0, 1.0))
+    perm, L, D = hifie.ldl_diag_pivot(B)
+    Pb = B[np.ix_(perm, perm)]
+    np.testing.assert_allclose(L @ np.diag(D) @ L.T, Pb, rtol=0, atol=1e-13 * np.abs(B).max())
+    assert np.allclose(np.triu(L, 1), 0.0) and np.allclose(np.diag(L), 1.0)
+    # the first pivot is the diagonal entry of largest magnitude
+    assert perm[0] == int(np.argmax(np.abs(np.diag(B))))
+    # every pivot passes the 1 x 1 Bunch-Kaufman test in its own Schur complement
+    Bw = Pb.copy()
+    for j in range(r):
+        col = np.abs(Bw[j:, j])
+        assert abs(Bw[j, j]) >= hifie.LDL_ALPHA * np.delete(col, 0).max(initial=0.0) - 1e-15
+        assert abs(Bw[j, j]) >= np.abs(np.diag(Bw)[j:]).max() - 1e-15
+        Bw[j + 1:, j + 1:] -= np.outer(Bw[j + 1:, j], Bw[j, j + 1:]) / Bw[j, j]
+    # block inverse from the factors equals the dense inverse
+    Binv = np.linalg.inv(B)
+    Lp = np.zeros_like(L)
+    Lp[perm, :] = L
+    np.testing.assert_allclose(np.linalg.inv(Lp).T @ np.diag(1 / D) @ np.linalg.inv(Lp), Binv, rtol=1e-10,
+                               atol=1e-12 * np.abs(Binv).max())
+
+
+def test_ldl_diag_pivot_refuses_weak_pivots():
+    # [[0, 1], [1, 0]] needs a 2 x 2 pivot; a diagonal below alpha times the
+    # column maximum is refused too
+    assert hifie.ldl_diag_pivot(np.array([[0.0, 1.0], [1.0, 0.0]])) is None
+    assert hifie.ldl_diag_pivot(np.array([[0.5, 1.0], [1.0, 0.4]])) is None
+    assert hifie.ldl_diag_pivot(np.array([[0.7, 1.0], [1.0, 2.0]])) is not None
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_ldl_factor_equals_lu_factor(eps):
+    # Sec. 5: LDL changes how the block inverse is formed, not its value;
+    # same skeletons, same F and F^{-1} to rounding, Y = X^T, a symmetric
+    # factorization (F = F^T) and a smaller store
+    pb = hi.volume_problem(32, 2, smooth_seed=1002)
+    args = (pb.points, pb.weights, pb.a, pb.b, pb.c, 0, eps, pb.proxy)
+    Fl = hifie.factor(*args, ldl=True)
+    Fu = hifie.factor(*args, ldl=False)
+    nl = sum(bf.ldl for sl in Fl.sublevels for bf in sl.boxes)
+    assert nl == sum(bf.rd.size > 0 for sl in Fl.sublevels for bf in sl.boxes) > 0
+    assert not any(bf.ldl for sl in Fu.sublevels for bf in sl.boxes)
+    for sa, sb in zip(Fl.sublevels, Fu.sublevels):
+        for ba, bb in zip(sa.boxes, sb.boxes):
+            np.testing.assert_array_equal(ba.sk, bb.sk)
+            np.testing.assert_array_equal(ba.rd, bb.rd)
+            if ba.ldl:
+                np.testing.assert_array_equal(ba.Y, ba.X.T)
+    X = hi.gaussian_rhs(pb.N, 3, 4)
+    for fa, fb in [(Fl.solve, Fu.solve), (Fl.apply, Fu.apply), (Fl.solve_transpose, Fu.solve_transpose),
+                   (Fl.apply_transpose, Fu.apply_transpose)]:
+        ya, yb = fa(X), fb(X)
+        assert np.linalg.norm(ya - yb) <= 1e-11 * np.linalg.norm(yb)
+    assert np.linalg.norm(Fl.solve(X) - Fl.solve_transpose(X)) <= 1e-12 * np.linalg.norm(X)
+    assert np.linalg.norm(Fl.apply(X) - Fl.apply_transpose(X)) <= 1e-12 * np.linalg.norm(X)
+    assert Fl.storage_doubles() < 0.8 * Fu.storage_doubles()
+
+
+def test_ldl_dense_factors_match_sweeps():
+    # the factored form of Eq. (4.1) multiplied out densely, with LDL boxes
+    pb = hi.volume_problem(8, 2, smooth_seed=5)
+    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, 1e-3, pb.proxy, occupancy=4, ldl=True)
+    assert any(bf.ldl for sl in F.sublevels for bf in sl.boxes)
+    Fd = F.dense_F()
+    I = np.eye(pb.N)
+    np.testing.assert_allclose(F.apply(I), Fd, rtol=0, atol=1e-12 * np.abs(Fd).max())
+    np.testing.assert_allclose(F.solve(Fd), I, rtol=0, atol=1e-11)
