@@ -682,7 +682,7 @@ static void run_factor(hif_handle h) {
     std::vector<char> active(N, 1);
     std::vector<int> box_of(N, -1);
     DevMem d_boxes, d_groups, d_cols, d_near, Rws, GKws, GSws, Tws, Wws, Woff, perm_out, k_out;
-    DevMem d_small_boxes, d_small_groups;
+    DevMem d_small_boxes, d_small_groups, d_small_sorted;
     FactorScratch S;
     BigBuffers big;
     const int big_id_n = env_int("HIF_BIG_ID", sizeof(T) == 8 ? 128 : 256);
@@ -789,6 +789,11 @@ static void run_factor(hif_handle h) {
         upload(d_near, p.near, st);
         upload(Woff, woff, st);
         upload(d_small_boxes, small_boxes, st);
+        // the small boxes by width, for the fold launches
+        std::vector<int> small_sorted(small_boxes);
+        std::stable_sort(small_sorted.begin(), small_sorted.end(),
+                         [&](int x, int y) { return bd[x].n < bd[y].n; });
+        upload(d_small_sorted, small_sorted, st);
         upload(d_small_groups, small_groups, st);
         Rws.ensure(sizeof(T) * std::max<int64_t>(Roff, 1));
         const bool grams = h->second_kind && any_sci;
@@ -816,16 +821,24 @@ static void run_factor(hif_handle h) {
             fa.Rws = Rws.p;
             fa.GKws = grams ? GKws.p : nullptr;
             fa.GSws = grams ? GSws.p : nullptr;
-            size_t smem = fold_smem_bytes(maxn, fa.bpairs, grams, true, sizeof(T));
-            fa.R_in_smem = smem <= 200 * 1024;
-            if (!fa.R_in_smem) {
-                fa.bpairs = 8;
-                smem = fold_smem_bytes(maxn, fa.bpairs, grams, false, sizeof(T));
-                if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
-            }
             {
+                // one launch per width bucket: a thread per column, so the
+                // CTA is the box width rounded up to a warp
                 ProfRange pr(PROF_FOLD, st, fold_flops, 0.0);
-                HIF_CUDA((launch_fold<T>(fa, (int)small_boxes.size(), smem, st)));
+                int64_t at = 0;
+                for (int w = 32; w <= 256 && at < (int64_t)small_boxes.size(); w += 32) {
+                    const int64_t b0 = at;
+                    while (at < (int64_t)small_boxes.size() && bd[small_sorted[at]].n <= w) ++at;
+                    if (at == b0) continue;
+                    FoldArgs fb = fa;
+                    fb.box_list = d_small_sorted.as<int>() + b0;
+                    size_t smem = fold_smem_bytes(w, 0, grams, true, sizeof(T));
+                    fb.R_in_smem = smem <= 200 * 1024;
+                    if (!fb.R_in_smem) smem = fold_smem_bytes(w, 0, grams, false, sizeof(T));
+                    if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
+                    HIF_CUDA((launch_fold<T>(fb, (int)(at - b0), w, smem, st)));
+                }
+                if (at != (int64_t)small_boxes.size()) fail(HIF_EINVAL, "box too wide for the fold kernel");
             }
 
             IdArgs ia{};

@@ -227,6 +227,7 @@ __device__ int cta_ldl_diag(int n, T* A, int64_t lda, int* piv, T* B, int64_t ld
         cta_max_lowest<T>(cm, ci, redv, redi);
         if (ci < 0) cm = T(0);
         const T dp = A[p + lda * p];
+        __syncthreads();                         // every thread has read A[p][p] before the swaps
         if (dp == T(0) || !isfinite((double)dp)) return 2;
         if (!(fabs(dp) >= alpha * cm)) return 1;
         if (threadIdx.x == 0) piv[j] = p;

@@ -41,72 +41,76 @@ __device__ inline T* align_ptr(unsigned char*& p, size_t count) {
 }  // namespace
 
 // ------------------------------------------------------------- fold ------
-
-template <typename T>
-__global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
+//
+// One CTA per box, one thread per column of Y_c (blockDim = n rounded up to
+// a warp).  Y_c is generated RC rows at a time; thread l holds its column's
+// RC entries in registers and folds them into column l of R by Householder
+// reflections of [R; C]: at step j the owner of column j forms the reflector
+// from its own registers and publishes it (RC values and tau) in shared
+// memory, then every column l > j applies it to its registers and to R[j][l].
+// Column l of R is touched by thread l only, so one CTA barrier per step
+// suffices (the reflector buffer is double-buffered).  In second-kind mode
+// the chunk's kernel and SCI parts also pass through shared memory for the
+// Gram matrices of Y^K and Y^S inside each column group (Sec. 4.4), stored
+// diagonal-major: G[l][l + t] at t * n + l.
+template <typename T, int RC>
+__global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
     const BoxDesc bx = args.boxes[args.box_list[blockIdx.x]];
     const int n = bx.n;
-    const int bp = args.bpairs;          // row pairs per chunk
-    const int rows = 2 * bp;
-    const bool sym = bx.sym != 0;        // one row per pair: Y'_c
-    const int ppc = sym ? rows : bp;     // pairs per chunk
-    const int ldc = rows + 1;            // odd leading dimension: conflict-free columns
+    const int l = threadIdx.x;                  // this thread's column
+    const bool col = l < n;
+    const bool sym = bx.sym != 0;               // one row per pair: Y'_c
+    const int ppc = sym ? RC : RC / 2;          // pairs per chunk
     const int nsub = args.sci.nsub;
-    const bool scival = bx.has_sci && nsub > 0;          // SCI entries present in Y_c
-    const bool sci = scival && args.second_kind;         // keep Y^S apart for rho_g
+    const bool scival = bx.has_sci && nsub > 0;
+    const bool grams = scival && args.second_kind;
     const int dim = args.g.dim;
     const int kid = args.g.kernel_id;
 
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* sp = smem;
-    T* cxl = align_ptr<T>(sp, (size_t)n * 3);
-    T* cwc = align_ptr<T>(sp, n);
-    T* cb = align_ptr<T>(sp, n);
-    T* cbw = align_ptr<T>(sp, n);
-    int* cid = align_ptr<int>(sp, n);
-    int* cgrp_end = align_ptr<int>(sp, n);          // end column of the column's group
-    T* rxl = align_ptr<T>(sp, (size_t)rows * 3);
-    T* rb = align_ptr<T>(sp, rows);
-    T* rwc = align_ptr<T>(sp, rows);
-    int* rid = align_ptr<int>(sp, rows);
-    T* CK = align_ptr<T>(sp, (size_t)ldc * n);
-    T* CS = sci ? align_ptr<T>(sp, (size_t)ldc * n) : nullptr;
-    T* hh = align_ptr<T>(sp, 4);
-    T* R;
-    T* const Rws = static_cast<T*>(args.Rws);
-    if (args.R_in_smem) R = align_ptr<T>(sp, (size_t)n * n);
-    else R = Rws + bx.R_off;
-    T* GK = sci ? static_cast<T*>(args.GKws) + bx.R_off : nullptr;
-    T* GS = sci ? static_cast<T*>(args.GSws) + bx.R_off : nullptr;
+    T* rxl = align_ptr<T>(sp, (size_t)RC * 3);
+    T* rb = align_ptr<T>(sp, RC);
+    T* rwc = align_ptr<T>(sp, RC);
+    int* rid = align_ptr<int>(sp, RC);
+    T* vbuf = align_ptr<T>(sp, 2 * RC);
+    T* taub = align_ptr<T>(sp, 2);
+    T* CK = align_ptr<T>(sp, (size_t)RC * n);    // the chunk (its kernel part in second-kind mode)
+    T* CS = grams ? align_ptr<T>(sp, (size_t)RC * n) : nullptr;
+    T* R = args.R_in_smem ? align_ptr<T>(sp, (size_t)n * n) : static_cast<T*>(args.Rws) + bx.R_off;
+    T* GK = grams ? static_cast<T*>(args.GKws) + bx.R_off : nullptr;
+    T* GS = grams ? static_cast<T*>(args.GSws) + bx.R_off : nullptr;
 
-    const int* cols = args.cols + bx.col_off;
-    const int* near = args.near + bx.near_off;
     const double c0 = bx.ctr[0], c1 = bx.ctr[1], c2 = dim == 3 ? bx.ctr[2] : 0.0;
+    // column data of this thread
+    int jid = 0, lend = 0;
+    T xj0 = T(0), xj1 = T(0), xj2 = T(0), cwc = T(0), cb = T(0), cbw = T(0);
+    if (col) {
+        jid = args.cols[bx.col_off + l];
+        xj0 = (T)(args.g.x[(int64_t)dim * jid + 0] - c0);
+        xj1 = (T)(args.g.x[(int64_t)dim * jid + 1] - c1);
+        xj2 = dim == 3 ? (T)(args.g.x[(int64_t)dim * jid + 2] - c2) : T(0);
+        cwc = (T)(args.g.w[jid] * args.g.c[jid]);
+        cb = (T)args.g.b[jid];
+        cbw = (T)(args.g.b[jid] * args.g.w[jid]);
+        for (int gi = 0; gi < bx.ngroups; ++gi) {
+            const GroupDesc gd = args.groups[bx.grp_off + gi];
+            if (l >= gd.col0 && l < gd.col0 + gd.n) lend = gd.col0 + gd.n;
+        }
+        for (int j = 0; j < n; ++j) R[(int64_t)j * n + l] = T(0);
+        if (grams)
+            for (int t = 0; t < n - l; ++t) {
+                GK[(int64_t)t * n + l] = T(0);
+                GS[(int64_t)t * n + l] = T(0);
+            }
+    }
 
-    for (int l = threadIdx.x; l < n; l += blockDim.x) {
-        const int j = cols[l];
-        cid[l] = j;
-        cxl[3 * l + 0] = (T)(args.g.x[(int64_t)dim * j + 0] - c0);
-        cxl[3 * l + 1] = (T)(args.g.x[(int64_t)dim * j + 1] - c1);
-        cxl[3 * l + 2] = dim == 3 ? (T)(args.g.x[(int64_t)dim * j + 2] - c2) : T(0);
-        cwc[l] = (T)(args.g.w[j] * args.g.c[j]);
-        cb[l] = (T)args.g.b[j];
-        cbw[l] = (T)(args.g.b[j] * args.g.w[j]);
-    }
-    for (int gi = 0; gi < bx.ngroups; ++gi) {
-        const GroupDesc gd = args.groups[bx.grp_off + gi];
-        for (int l = gd.col0 + threadIdx.x; l < gd.col0 + gd.n; l += blockDim.x) cgrp_end[l] = gd.col0 + gd.n;
-    }
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        R[e] = T(0);
-        if (sci) { GK[e] = T(0); GS[e] = T(0); }
-    }
-    __syncthreads();
-
+    const int* near = args.near + bx.near_off;
     const int npairs = bx.m_near + args.P;
+    T c[RC];
     for (int p0 = 0; p0 < npairs; p0 += ppc) {
         const int np = min(ppc, npairs - p0);
-        // ---- row data of this chunk
+        __syncthreads();                        // previous chunk's row data and Gram reads done
         for (int q = threadIdx.x; q < ppc; q += blockDim.x) {
             const int p = p0 + q;
             if (q >= np) {
@@ -130,90 +134,96 @@ __global__ void __launch_bounds__(128) fold_kernel(FoldArgs args) {
             }
         }
         __syncthreads();
-        // ---- generate the chunk: rows (2q, 2q+1) = (outgoing, incoming) of
-        // pair q, or row q = outgoing alone for symmetric A
-        for (int l = threadIdx.x; l < n; l += blockDim.x) {
-            const T xj0 = cxl[3 * l], xj1 = cxl[3 * l + 1], xj2 = cxl[3 * l + 2];
-            const int j = cid[l];
+        // ---- this column's entries of the chunk, staged in shared memory:
+        // rows (2q, 2q+1) = (outgoing, incoming) of pair q, or row q alone
+        // for symmetric A; kernel and SCI parts apart when the Grams need them
+        if (col) {
             for (int q = 0; q < ppc; ++q) {
                 T k1, k2, s1, s2;
-                y_pair<T>(kid, rid[q], rxl[3 * q], rxl[3 * q + 1], rxl[3 * q + 2], rb[q], rwc[q], j, xj0, xj1, xj2,
-                          cwc[l], cb[l], cbw[l], scival, args.sci, k1, k2, s1, s2);
+                y_pair<T>(kid, rid[q], rxl[3 * q], rxl[3 * q + 1], rxl[3 * q + 2], rb[q], rwc[q], jid, xj0, xj1,
+                          xj2, cwc, cb, cbw, scival, args.sci, k1, k2, s1, s2);
                 const int i1 = sym ? q : 2 * q;
-                if (sci) {
-                    CK[i1 + ldc * l] = k1;
-                    CS[i1 + ldc * l] = s1;
+                if (grams) {
+                    CK[i1 * n + l] = k1;
+                    CS[i1 * n + l] = s1;
                     if (!sym) {
-                        CK[i1 + 1 + ldc * l] = k2;
-                        CS[i1 + 1 + ldc * l] = s2;
+                        CK[(i1 + 1) * n + l] = k2;
+                        CS[(i1 + 1) * n + l] = s2;
                     }
                 } else {
-                    CK[i1 + ldc * l] = k1 + s1;
-                    if (!sym) CK[i1 + 1 + ldc * l] = k2 + s2;
+                    CK[i1 * n + l] = k1 + s1;
+                    if (!sym) CK[(i1 + 1) * n + l] = k2 + s2;
                 }
             }
+#pragma unroll
+            for (int i = 0; i < RC; ++i) c[i] = grams ? CK[i * n + l] + CS[i * n + l] : CK[i * n + l];
+        } else {
+#pragma unroll
+            for (int i = 0; i < RC; ++i) c[i] = T(0);
         }
-        __syncthreads();
-        // ---- Gram matrices of Y^K and Y^S inside each group (second kind)
-        if (sci) {
-            for (int l = threadIdx.x; l < n; l += blockDim.x) {
-                const int lend = cgrp_end[l];
+        // ---- Gram matrices of Y^K_g and Y^S_g (this thread: row l, l <= l2 < group end)
+        if (grams) {
+            __syncthreads();
+            if (col) {
                 for (int l2 = l; l2 < lend; ++l2) {
                     T gk = T(0), gs = T(0);
-                    for (int i = 0; i < rows; ++i) {
-                        gk += CK[i + ldc * l] * CK[i + ldc * l2];
-                        gs += CS[i + ldc * l] * CS[i + ldc * l2];
+#pragma unroll 8
+                    for (int i = 0; i < RC; ++i) {
+                        gk += CK[i * n + l] * CK[i * n + l2];
+                        gs += CS[i * n + l] * CS[i * n + l2];
                     }
-                    GK[(int64_t)l * n + l2] += gk;
-                    GS[(int64_t)l * n + l2] += gs;
+                    GK[(int64_t)(l2 - l) * n + l] += gk;
+                    GS[(int64_t)(l2 - l) * n + l] += gs;
                 }
             }
-            __syncthreads();
-            for (int e = threadIdx.x; e < ldc * n; e += blockDim.x) CK[e] += CS[e];
-            __syncthreads();
         }
-        // ---- fold the chunk into R: QR of [R; C] (row-major R, n x n)
+        // ---- fold the chunk into R: Householder QR of [R; C]
         for (int j = 0; j < n; ++j) {
-            if (threadIdx.x < 32) {
-                T s = T(0);
-                for (int i = threadIdx.x; i < rows; i += 32) {
-                    const T v = CK[i + ldc * j];
-                    s += v * v;
+            const int buf = j & 1;
+            if (l == j) {
+                T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
+#pragma unroll
+                for (int i = 0; i < RC; i += 4) {
+                    q0 += c[i] * c[i];
+                    q1 += c[i + 1] * c[i + 1];
+                    q2 += c[i + 2] * c[i + 2];
+                    q3 += c[i + 3] * c[i + 3];
                 }
-                s = warp_sum(s);
-                if (threadIdx.x == 0) {
+                const T ss = (q0 + q1) + (q2 + q3);
+                T tau = T(0);
+                if (ss != T(0)) {
                     const T alpha = R[(int64_t)j * n + j];
-                    if (s == T(0)) {
-                        hh[0] = T(0);
-                        hh[1] = T(0);
-                    } else {
-                        const T beta = -copysign(sqrt(alpha * alpha + s), alpha);
-                        hh[0] = (beta - alpha) / beta;       // tau
-                        hh[1] = T(1) / (alpha - beta);       // scale of v
-                        R[(int64_t)j * n + j] = beta;
-                    }
+                    const T beta = -copysign(sqrt(alpha * alpha + ss), alpha);
+                    tau = (beta - alpha) / beta;
+                    const T scal = T(1) / (alpha - beta);
+                    R[(int64_t)j * n + j] = beta;
+#pragma unroll
+                    for (int i = 0; i < RC; ++i) vbuf[buf * RC + i] = c[i] * scal;
                 }
+                taub[buf] = tau;
             }
             __syncthreads();
-            const T tau = hh[0];
-            if (tau != T(0)) {
-                const T scal = hh[1];
-                for (int i = threadIdx.x; i < rows; i += blockDim.x) CK[i + ldc * j] *= scal;
-                __syncthreads();
-                for (int l = j + 1 + threadIdx.x; l < n; l += blockDim.x) {
-                    T w = R[(int64_t)j * n + l];
-                    for (int i = 0; i < rows; ++i) w += CK[i + ldc * j] * CK[i + ldc * l];
-                    w *= tau;
-                    R[(int64_t)j * n + l] -= w;
-                    for (int i = 0; i < rows; ++i) CK[i + ldc * l] -= w * CK[i + ldc * j];
+            const T tau = taub[buf];
+            if (l > j && col && tau != T(0)) {
+                const T* v = vbuf + buf * RC;
+                T w0 = R[(int64_t)j * n + l], w1 = T(0), w2 = T(0), w3 = T(0);
+#pragma unroll
+                for (int i = 0; i < RC; i += 4) {
+                    w0 += v[i] * c[i];
+                    w1 += v[i + 1] * c[i + 1];
+                    w2 += v[i + 2] * c[i + 2];
+                    w3 += v[i + 3] * c[i + 3];
                 }
+                const T w = ((w0 + w1) + (w2 + w3)) * tau;
+                R[(int64_t)j * n + l] -= w;
+#pragma unroll
+                for (int i = 0; i < RC; ++i) c[i] -= w * v[i];
             }
-            __syncthreads();
         }
     }
-    if (args.R_in_smem) {
-        T* Rg = Rws + bx.R_off;
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rg[e] = R[e];
+    if (args.R_in_smem && col) {
+        T* Rg = static_cast<T*>(args.Rws) + bx.R_off;
+        for (int j = 0; j < n; ++j) Rg[(int64_t)j * n + l] = R[(int64_t)j * n + l];
     }
 }
 
@@ -409,7 +419,8 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
                     const int gl = gd.col0 + l;
                     for (int q = 0; q < ng; ++q) {
                         const int gq = gd.col0 + q;
-                        const T gv = gl <= gq ? G[(int64_t)gl * n + gq] : G[(int64_t)gq * n + gl];
+                        // diagonal-major upper triangle: G[a][a + t] at t * n + a
+                        const T gv = gl <= gq ? G[(int64_t)(gq - gl) * n + gl] : G[(int64_t)(gl - gq) * n + gq];
                         acc += gv * v[q];
                     }
                     wv[l] = acc;
@@ -670,14 +681,16 @@ cudaError_t launch_id_batched(int count, const double* mats, const int64_t* off,
 
 // ---------------------------------------------------------- launchers ----
 
+// Rows of Y_c per fold chunk (registers per thread of the fold kernel).
+constexpr int kFoldRC = 32;
+
 size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem) {
-    const size_t rows = 2 * (size_t)bpairs + 1;
+    (void)bpairs;
+    const size_t rc = kFoldRC;
     size_t b = 0;
-    b += (size_t)n * 6 * elem + 64;       // cxl, cwc, cb, cbw
-    b += (size_t)n * 8 + 32;              // cid, cgrp_end
-    b += 2 * (size_t)bpairs * (5 * elem + 4) + 64;   // row data for up to 2 bpairs rows
-    b += rows * n * elem * (sci ? 2 : 1) + 32;
-    b += 4 * elem + 16;
+    b += rc * (5 * (size_t)elem + 4) + 64;             // row data
+    b += 2 * rc * elem + 2 * (size_t)elem + 32;        // reflector buffers
+    b += rc * (size_t)n * elem * (sci ? 2 : 1) + 32;   // the chunk (K and S parts apart for the Grams)
     if (R_in_smem) b += (size_t)n * n * elem + 16;
     return b + 128;
 }
@@ -688,13 +701,16 @@ size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem) {
     return b + 64;
 }
 
+// threads: the launch's largest box width rounded up to a warp (<= 256)
 template <typename T>
-cudaError_t launch_fold(const FoldArgs& a, int nbox, size_t smem, cudaStream_t st) {
+cudaError_t launch_fold(const FoldArgs& a, int nbox, int threads, size_t smem, cudaStream_t st) {
     if (nbox == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fold_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fold_kernel<T, kFoldRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    fold_kernel<T><<<nbox, 128, smem, st>>>(a);
+    fold_kernel<T, kFoldRC><<<nbox, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -716,8 +732,8 @@ cudaError_t launch_elim(const ElimArgs& a, int nbox, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fold<double>(const FoldArgs&, int, size_t, cudaStream_t);
-template cudaError_t launch_fold<float>(const FoldArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_fold<double>(const FoldArgs&, int, int, size_t, cudaStream_t);
+template cudaError_t launch_fold<float>(const FoldArgs&, int, int, size_t, cudaStream_t);
 template cudaError_t launch_id<double>(const IdArgs&, int, size_t, cudaStream_t);
 template cudaError_t launch_id<float>(const IdArgs&, int, size_t, cudaStream_t);
 template cudaError_t launch_elim<double>(const ElimArgs&, int, cudaStream_t);

@@ -179,7 +179,7 @@ template <typename T> cudaError_t big_elim_batch(const BatchElimArgs&, int max_n
 size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem);
 size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem);
 
-template <typename T> cudaError_t launch_fold(const FoldArgs&, int nbox, size_t smem, cudaStream_t);
+template <typename T> cudaError_t launch_fold(const FoldArgs&, int nbox, int threads, size_t smem, cudaStream_t);
 template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t smem, cudaStream_t);
 template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStream_t);
 
