@@ -696,6 +696,7 @@ static void run_factor(hif_handle h) {
 
     for (size_t tau = 0; tau < nsub; ++tau) {
         const auto tr0 = std::chrono::steady_clock::now();
+        auto tr_fold = tr0;
         // ---- index sets of this sublevel, problem by problem, merged
         SublevelPlan p;
         p.nbox = 0;
@@ -833,12 +834,16 @@ static void run_factor(hif_handle h) {
                     FoldArgs fb = fa;
                     fb.box_list = d_small_sorted.as<int>() + b0;
                     size_t smem = fold_smem_bytes(w, 0, grams, true, sizeof(T));
-                    fb.R_in_smem = smem <= 200 * 1024;
+                    fb.R_in_smem = smem <= 220 * 1024;
                     if (!fb.R_in_smem) smem = fold_smem_bytes(w, 0, grams, false, sizeof(T));
                     if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
                     HIF_CUDA((launch_fold<T>(fb, (int)(at - b0), w, smem, st)));
                 }
                 if (at != (int64_t)small_boxes.size()) fail(HIF_EINVAL, "box too wide for the fold kernel");
+            }
+            if (trace) {
+                HIF_CUDA(cudaStreamSynchronize(st));
+                tr_fold = std::chrono::steady_clock::now();
             }
 
             IdArgs ia{};
@@ -1013,6 +1018,8 @@ static void run_factor(hif_handle h) {
             auto ms = [](auto a0, auto b0) { return std::chrono::duration<double, std::milli>(b0 - a0).count(); };
             std::fprintf(stderr, "[hif] sub %2zu kind %d level %d boxes %d big %zu maxn %d | plan+launch %.1f ms, id %.1f ms, elim+host %.1f ms\n",
                          tau, kind, ell, nb, big_boxes.size(), maxbox, ms(tr0, tr1), ms(tr1, tr2), ms(tr2, tr3));
+            if (!small_boxes.empty())
+                std::fprintf(stderr, "[hif]        plan+fold %.1f ms (fold ends at the sync)\n", ms(tr0, tr_fold));
         }
         h->subs.push_back(std::move(sf));
     }

@@ -49,7 +49,10 @@ __device__ inline T* align_ptr(unsigned char*& p, size_t count) {
 // from its own registers and publishes it (RC values and tau) in shared
 // memory, then every column l > j applies it to its registers and to R[j][l].
 // Column l of R is touched by thread l only, so one CTA barrier per step
-// suffices (the reflector buffer is double-buffered).  In second-kind mode
+// suffices (the reflector buffer is double-buffered).  R lives in shared
+// memory as a packed upper triangle, column l at l (l + 1) / 2 (triangular
+// numbers are distinct modulo 32, so a warp's accesses of one row are free of
+// bank conflicts), or, when it does not fit, row-major in global memory.  In second-kind mode
 // the chunk's kernel and SCI parts also pass through shared memory for the
 // Gram matrices of Y^K and Y^S inside each column group (Sec. 4.4), stored
 // diagonal-major: G[l][l + t] at t * n + l.
@@ -77,7 +80,11 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
     T* taub = align_ptr<T>(sp, 2);
     T* CK = align_ptr<T>(sp, (size_t)RC * n);    // the chunk (its kernel part in second-kind mode)
     T* CS = grams ? align_ptr<T>(sp, (size_t)RC * n) : nullptr;
-    T* R = args.R_in_smem ? align_ptr<T>(sp, (size_t)n * n) : static_cast<T*>(args.Rws) + bx.R_off;
+    T* const Rglob = static_cast<T*>(args.Rws) + bx.R_off;
+    T* const Rpack = args.R_in_smem ? align_ptr<T>(sp, (size_t)n * (n + 1) / 2) : nullptr;
+    // R[j][l] of this thread's column (j <= l)
+    T* const Rcol = args.R_in_smem ? Rpack + (size_t)l * (l + 1) / 2 : Rglob + l;
+    const int64_t rstride = args.R_in_smem ? 1 : n;
     T* GK = grams ? static_cast<T*>(args.GKws) + bx.R_off : nullptr;
     T* GS = grams ? static_cast<T*>(args.GSws) + bx.R_off : nullptr;
 
@@ -97,7 +104,7 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
             const GroupDesc gd = args.groups[bx.grp_off + gi];
             if (l >= gd.col0 && l < gd.col0 + gd.n) lend = gd.col0 + gd.n;
         }
-        for (int j = 0; j < n; ++j) R[(int64_t)j * n + l] = T(0);
+        for (int j = 0; j < (args.R_in_smem ? l + 1 : n); ++j) Rcol[j * rstride] = T(0);
         if (grams)
             for (int t = 0; t < n - l; ++t) {
                 GK[(int64_t)t * n + l] = T(0);
@@ -192,11 +199,11 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
                 const T ss = (q0 + q1) + (q2 + q3);
                 T tau = T(0);
                 if (ss != T(0)) {
-                    const T alpha = R[(int64_t)j * n + j];
+                    const T alpha = Rcol[j * rstride];
                     const T beta = -copysign(sqrt(alpha * alpha + ss), alpha);
                     tau = (beta - alpha) / beta;
                     const T scal = T(1) / (alpha - beta);
-                    R[(int64_t)j * n + j] = beta;
+                    Rcol[j * rstride] = beta;
 #pragma unroll
                     for (int i = 0; i < RC; ++i) vbuf[buf * RC + i] = c[i] * scal;
                 }
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
             const T tau = taub[buf];
             if (l > j && col && tau != T(0)) {
                 const T* v = vbuf + buf * RC;
-                T w0 = R[(int64_t)j * n + l], w1 = T(0), w2 = T(0), w3 = T(0);
+                T w0 = Rcol[j * rstride], w1 = T(0), w2 = T(0), w3 = T(0);
 #pragma unroll
                 for (int i = 0; i < RC; i += 4) {
                     w0 += v[i] * c[i];
@@ -215,38 +222,67 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
                     w3 += v[i + 3] * c[i + 3];
                 }
                 const T w = ((w0 + w1) + (w2 + w3)) * tau;
-                R[(int64_t)j * n + l] -= w;
+                Rcol[j * rstride] -= w;
 #pragma unroll
                 for (int i = 0; i < RC; ++i) c[i] -= w * v[i];
             }
         }
     }
-    if (args.R_in_smem && col) {
-        T* Rg = static_cast<T*>(args.Rws) + bx.R_off;
-        for (int j = 0; j < n; ++j) Rg[(int64_t)j * n + l] = R[(int64_t)j * n + l];
-    }
+    if (args.R_in_smem && col)
+        for (int j = 0; j < n; ++j) Rglob[(int64_t)j * n + l] = j <= l ? Rcol[j] : T(0);
 }
 
 // --------------------------------------------------------------- ID ------
 
-// Column-pivoted Householder QR of W (mrow x ng, column-major, leading
-// dimension ldw, overwritten) to relative tolerance tol (Lemma 2.2 with the
-// adaptive rank of Sec. 2.2): pivot = largest remaining column 2-norm (ties:
-// lowest original index), norms recomputed exactly in FP64 after every step,
-// stop at the first step whose pivot norm is <= tol times the first one.
-// Writes k, the column order (skeletons in pivot order, then redundants in
-// ascending order) and T = R1^{-1} R2 (k x (ng-k), column-major, columns in
-// the redundant order).  perm, rank_of: ng ints; redv/redi: blockDim entries.
-template <typename T>
-__device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm, int* perm, int* rank_of,
-                        double* redv, int* redi, T* hh, T* Tout, int* pout, int* kout) {
-    for (int l = threadIdx.x; l < ng; l += blockDim.x) perm[l] = l;
+// Block-wide argmax of (v, original index o) over one candidate per thread:
+// largest v, ties to the lowest o; candidates with pos < 0 are ignored.
+// Returns the winner's pos on every thread (-1 if none).  Two barriers.
+__device__ inline int cta_argmax_v_o(double v, int o, int pos, double* wv, int* wo, int* wp) {
+    for (int off = 16; off > 0; off >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const int o2 = __shfl_xor_sync(0xffffffffu, o, off);
+        const int p2 = __shfl_xor_sync(0xffffffffu, pos, off);
+        if (p2 >= 0 && (pos < 0 || v2 > v || (v2 == v && o2 < o))) { v = v2; o = o2; pos = p2; }
+    }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { wv[warp] = v; wo[warp] = o; wp[warp] = pos; }
     __syncthreads();
+    if (warp == 0) {
+        const int lane = threadIdx.x & 31;
+        v = lane < nw ? wv[lane] : -1.0;
+        o = lane < nw ? wo[lane] : (1 << 30);
+        pos = lane < nw ? wp[lane] : -1;
+        for (int off = 16; off > 0; off >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+            const int o2 = __shfl_xor_sync(0xffffffffu, o, off);
+            const int p2 = __shfl_xor_sync(0xffffffffu, pos, off);
+            if (p2 >= 0 && (pos < 0 || v2 > v || (v2 == v && o2 < o))) { v = v2; o = o2; pos = p2; }
+        }
+        if (lane == 0) wp[32] = pos;
+    }
+    __syncthreads();
+    return wp[32];
+}
+
+// Column-pivoted Householder QR of W (mrow x ng; element (i, l) at
+// W[i * rs + l * cs], overwritten) to relative tolerance tol (Lemma 2.2 with
+// the adaptive rank of Sec. 2.2): pivot = largest remaining column 2-norm
+// (ties: lowest original index), norms recomputed exactly in FP64 after every
+// step, stop at the first step whose pivot norm is <= tol times the first
+// one.  Writes k, the column order (skeletons in pivot order, then
+// redundants in ascending order) and T = R1^{-1} R2 (k x (ng-k),
+// column-major, columns in the redundant order).  Row-major W (cs = 1) makes
+// the per-column sweeps of the trailing update coalesced.  perm, rank_of: ng
+// ints; wv/wo/wp: 33 entries of scratch each.
+template <typename T>
+__device__ void cpqr_id(T* W, int rs, int cs, int mrow, int ng, double tol, double* nrm, int* perm,
+                        int* rank_of, double* wv, int* wo, int* wp, T* hh, T* Tout, int* pout, int* kout) {
+    for (int l = threadIdx.x; l < ng; l += blockDim.x) perm[l] = l;
     // ---- column-pivoted Householder QR with exact norm recomputation
     for (int l = threadIdx.x; l < ng; l += blockDim.x) {
         double s = 0.0;
         for (int i = 0; i < mrow; ++i) {
-            const double v = (double)W[i + (int64_t)ldw * l];
+            const double v = (double)W[i * rs + l * cs];
             s += v * v;
         }
         nrm[l] = s;
@@ -263,50 +299,33 @@ __device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm
             const double v = nrm[l];
             if (v > best || (v == best && perm[l] < bo)) { best = v; bo = perm[l]; bl = l; }
         }
-        redv[threadIdx.x] = best;
-        redi[threadIdx.x] = bl;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                const double v2 = redv[threadIdx.x + s];
-                const int l2 = redi[threadIdx.x + s];
-                const double v1 = redv[threadIdx.x];
-                const int l1 = redi[threadIdx.x];
-                if (l2 >= 0 && (l1 < 0 || v2 > v1 || (v2 == v1 && perm[l2] < perm[l1]))) {
-                    redv[threadIdx.x] = v2;
-                    redi[threadIdx.x] = l2;
-                }
-            }
-            __syncthreads();
-        }
-        const double bsq = redv[0];
-        const int p = redi[0];
-        __syncthreads();
-        const double bnorm = sqrt(fmax(bsq, 0.0));
+        const int p = cta_argmax_v_o(best, bo, bl, wv, wo, wp);
+        if (p < j) break;                                  // no comparable norm left
+        const double bnorm = sqrt(fmax(nrm[p], 0.0));
         if (j == 0) nu0 = bnorm;
         if (bnorm <= tol * nu0 || bnorm == 0.0) break;
         if (p != j) {
             for (int i = threadIdx.x; i < mrow; i += blockDim.x) {
-                const T t = W[i + (int64_t)ldw * j];
-                W[i + (int64_t)ldw * j] = W[i + (int64_t)ldw * p];
-                W[i + (int64_t)ldw * p] = t;
-            }
-            if (threadIdx.x == 0) {
-                const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
-                const double tn = nrm[j]; nrm[j] = nrm[p]; nrm[p] = tn;
+                const T t = W[i * rs + j * cs];
+                W[i * rs + j * cs] = W[i * rs + p * cs];
+                W[i * rs + p * cs] = t;
             }
         }
         __syncthreads();
+        if (p != j && threadIdx.x == 0) {
+            const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+            const double tn = nrm[j]; nrm[j] = nrm[p]; nrm[p] = tn;
+        }
         // Householder reflector for W[j:, j]
         if (threadIdx.x < 32) {
             T s = T(0);
             for (int i = j + 1 + threadIdx.x; i < mrow; i += 32) {
-                const T v = W[i + (int64_t)ldw * j];
+                const T v = W[i * rs + j * cs];
                 s += v * v;
             }
             s = warp_sum(s);
             if (threadIdx.x == 0) {
-                const T alpha = W[j + (int64_t)ldw * j];
+                const T alpha = W[j * rs + j * cs];
                 if (s == T(0)) {
                     hh[0] = T(0);
                     hh[1] = T(0);
@@ -314,7 +333,7 @@ __device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm
                     const T beta = -copysign(sqrt(alpha * alpha + s), alpha);
                     hh[0] = (beta - alpha) / beta;
                     hh[1] = T(1) / (alpha - beta);
-                    W[j + (int64_t)ldw * j] = beta;
+                    W[j * rs + j * cs] = beta;
                 }
             }
         }
@@ -322,22 +341,22 @@ __device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm
         const T tau = hh[0];
         if (tau != T(0)) {
             const T scal = hh[1];
-            for (int i = j + 1 + threadIdx.x; i < mrow; i += blockDim.x) W[i + (int64_t)ldw * j] *= scal;
+            for (int i = j + 1 + threadIdx.x; i < mrow; i += blockDim.x) W[i * rs + j * cs] *= scal;
         }
         __syncthreads();
         for (int l = j + 1 + threadIdx.x; l < ng; l += blockDim.x) {
-            T* col = W + (int64_t)ldw * l;
-            const T* v = W + (int64_t)ldw * j;
+            T* col = W + l * cs;
+            const T* v = W + j * cs;
             if (tau != T(0)) {
-                T w = col[j];
-                for (int i = j + 1; i < mrow; ++i) w += v[i] * col[i];
+                T w = col[j * rs];
+                for (int i = j + 1; i < mrow; ++i) w += v[i * rs] * col[i * rs];
                 w *= tau;
-                col[j] -= w;
-                for (int i = j + 1; i < mrow; ++i) col[i] -= w * v[i];
+                col[j * rs] -= w;
+                for (int i = j + 1; i < mrow; ++i) col[i * rs] -= w * v[i * rs];
             }
             double s = 0.0;
             for (int i = j + 1; i < mrow; ++i) {
-                const double c = (double)col[i];
+                const double c = (double)col[i * rs];
                 s += c * c;
             }
             nrm[l] = s;
@@ -345,6 +364,7 @@ __device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm
         __syncthreads();
         k = j + 1;
     }
+    __syncthreads();
     // ---- T = R1^{-1} R2, written with the redundant columns in ascending order
     const int r = ng - k;
     for (int l = threadIdx.x; l < r; l += blockDim.x) {
@@ -355,14 +375,14 @@ __device__ void cpqr_id(T* W, int ldw, int mrow, int ng, double tol, double* nrm
     }
     __syncthreads();
     for (int l = threadIdx.x; l < r; l += blockDim.x) {
-        T* col = W + (int64_t)ldw * (k + l);
+        T* col = W + (k + l) * cs;
         for (int i = k - 1; i >= 0; --i) {
-            T v = col[i];
-            for (int q = i + 1; q < k; ++q) v -= W[i + (int64_t)ldw * q] * col[q];
-            col[i] = v / W[i + (int64_t)ldw * i];
+            T v = col[i * rs];
+            for (int q = i + 1; q < k; ++q) v -= W[i * rs + q * cs] * col[q * rs];
+            col[i * rs] = v / W[i * rs + i * cs];
         }
         const int pos = rank_of[l];
-        for (int i = 0; i < k; ++i) Tout[i + (int64_t)k * pos] = col[i];
+        for (int i = 0; i < k; ++i) Tout[i + (int64_t)k * pos] = col[i * rs];
     }
     for (int l = threadIdx.x; l < k; l += blockDim.x) pout[l] = perm[l];
     for (int l = threadIdx.x; l < r; l += blockDim.x) pout[k + rank_of[l]] = perm[k + l];
@@ -378,7 +398,7 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
     const int n = bx.n;
     const int ng = gd.n;
     const int mrow = gd.col0 + ng;                 // rows of R[:, g] that can be nonzero
-    const int ldw = mrow | 1;
+    const int ldw = ng;                            // W = R[:mrow, g], row-major
     const T* R = static_cast<const T*>(args.Rws) + bx.R_off;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -387,16 +407,16 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
     int* perm = align_ptr<int>(sp, ng);
     int* rank_of = align_ptr<int>(sp, ng);
     double* redv = align_ptr<double>(sp, blockDim.x);
-    int* redi = align_ptr<int>(sp, blockDim.x);
+    int* redi = align_ptr<int>(sp, 72);
     T* vec = align_ptr<T>(sp, 2 * (size_t)ng);
     T* hh = align_ptr<T>(sp, 4);
     T* W;
-    if (args.W_in_smem) W = align_ptr<T>(sp, (size_t)ldw * ng);
+    if (args.W_in_smem) W = align_ptr<T>(sp, (size_t)mrow * ng);
     else W = static_cast<T*>(args.Wws) + args.W_off[gidx];
 
     for (int e = threadIdx.x; e < mrow * ng; e += blockDim.x) {
-        const int i = e % mrow, l = e / mrow;
-        W[i + (int64_t)ldw * l] = R[(int64_t)i * n + gd.col0 + l];
+        const int i = e / ng, l = e % ng;
+        W[(int64_t)i * ldw + l] = R[(int64_t)i * n + gd.col0 + l];
     }
     __syncthreads();
 
@@ -451,7 +471,7 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
     double tol = rho * args.eps;
     if (tol < args.tol_floor) tol = args.tol_floor;
 
-    cpqr_id<T>(W, ldw, mrow, ng, tol, nrm, perm, rank_of, redv, redi, hh,
+    cpqr_id<T>(W, ldw, 1, mrow, ng, tol, nrm, perm, rank_of, redv, redi, redi + 36, hh,
                static_cast<T*>(args.Tws) + gd.T_off, args.perm_out + gd.perm_off, args.k_out + gidx);
 }
 
@@ -641,7 +661,8 @@ __global__ void __launch_bounds__(128) id_batched_kernel(const double* mats, con
     double* hh = align_ptr<double>(sp, 4);
     for (int e = threadIdx.x; e < mm * nn; e += blockDim.x) W[(e % mm) + (int64_t)ldw * (e / mm)] = M[e];
     __syncthreads();
-    cpqr_id<double>(W, ldw, mm, nn, tol[b], nrm, pm, rk, redv, redi, hh, T + toff[b], perm + poff[b], k + b);
+    cpqr_id<double>(W, 1, ldw, mm, nn, tol[b], nrm, pm, rk, redv, redi, redi + 64, hh, T + toff[b], perm + poff[b],
+                    k + b);
 }
 
 cudaError_t launch_id_batched(int count, const double* mats, const int64_t* off, const int* m, const int* n,
@@ -691,13 +712,13 @@ size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem) {
     b += rc * (5 * (size_t)elem + 4) + 64;             // row data
     b += 2 * rc * elem + 2 * (size_t)elem + 32;        // reflector buffers
     b += rc * (size_t)n * elem * (sci ? 2 : 1) + 32;   // the chunk (K and S parts apart for the Grams)
-    if (R_in_smem) b += (size_t)n * n * elem + 16;
+    if (R_in_smem) b += (size_t)n * (n + 1) / 2 * elem + 16;   // packed upper triangle
     return b + 128;
 }
 
 size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem) {
-    size_t b = (size_t)ng * 16 + 128 * 12 + 2 * (size_t)ng * elem + 4 * elem + 160;
-    if (W_in_smem) b += (size_t)(mrow | 1) * ng * elem + 16;
+    size_t b = (size_t)ng * 16 + 128 * 8 + 72 * 4 + 2 * (size_t)ng * elem + 4 * elem + 160;
+    if (W_in_smem) b += (size_t)mrow * ng * elem + 16;
     return b + 64;
 }
 
@@ -799,7 +820,8 @@ __global__ void __launch_bounds__(128) id_noalloc_kernel(unsigned char* scratch,
     __shared__ double hh[4];
     for (int e = threadIdx.x; e < mm * nn; e += blockDim.x) W[(e % mm) + (int64_t)ldw * (e / mm)] = M[e];
     __syncthreads();
-    cpqr_id<double>(W, ldw, mm, nn, tol[b], nrm, pm, rk, redv, redi, hh, T + toff[b], perm + poff[b], k + b);
+    cpqr_id<double>(W, 1, ldw, mm, nn, tol[b], nrm, pm, rk, redv, redi, redi + 64, hh, T + toff[b], perm + poff[b],
+                    k + b);
 }
 
 // Device address of the scratch array for the current device, looked up once
