@@ -564,6 +564,90 @@ static void place_box(ElimDesc& e, BoxFac& bf, int k, int r, bool ldl, int64_t& 
     bf.piv_off = e.piv_out;
 }
 
+// ID of the large boxes that the fold kernel reduced to their n x n factor R
+// (the ID of R[:, g] is that of Y_c[:, g]): R in column-major order, rho_g
+// from the box Grams, then the pivoted QR by per-step launches shared by all
+// such groups, on the col0 + n_g rows of R[:, g] that can be nonzero.
+template <typename T>
+static void run_big_id_R(hif_handle h, const std::vector<BoxDesc>& bd, const std::vector<GroupDesc>& gd,
+                         const std::vector<int>& boxes, DevMem& d_boxes, DevMem& d_groups, DevMem& Rws, void* GK,
+                         void* GS, DevMem& Tws, DevMem& perm_out, DevMem& k_out, double tol_floor, BigBuffers& B) {
+    const cudaStream_t st = h->st;
+    std::vector<BigGroup> bgv;
+    std::vector<int64_t> roff;
+    int64_t yoff = 0, voff = 0;
+    int max_n = 0, maxk = 0, max_ng = 0;
+    for (int bI : boxes) {
+        const BoxDesc& b = bd[bI];
+        roff.push_back(yoff);
+        for (int q = 0; q < b.ngroups; ++q) {
+            const int64_t gi = b.grp_off + q;
+            const GroupDesc& G = gd[gi];
+            BigGroup y{};
+            y.group = (int)gi;
+            y.n = G.n;
+            y.m = G.col0 + G.n;
+            y.ld = b.n;
+            y.need_rho = (h->second_kind && G.has_sci && b.has_sci && GK) ? 1 : 0;
+            y.y_off = yoff + (int64_t)b.n * G.col0;
+            y.vec_off = voff;
+            y.row_off = 0;
+            voff += G.n;
+            max_n = std::max(max_n, G.n);
+            max_ng = std::max(max_ng, G.n);
+            maxk = std::max(maxk, std::min(y.m, G.n));
+            bgv.push_back(y);
+        }
+        yoff += (int64_t)b.n * b.n;
+    }
+    const int ng = (int)bgv.size();
+    upload(B.bg, bgv, st);
+    B.state.ensure(sizeof(BigState) * ng);
+    B.YK.ensure(sizeof(T) * std::max<int64_t>(yoff, 1));
+    B.nrm.ensure(sizeof(double) * std::max<int64_t>(voff, 1));
+    B.perm.ensure(sizeof(int) * std::max<int64_t>(voff, 1));
+    for (size_t q = 0; q < boxes.size(); ++q) {
+        const BoxDesc& b = bd[boxes[q]];
+        HIF_CUDA((launch_r_colmajor<T>(Rws.as<T>() + b.R_off, b.n, B.YK.as<T>() + roff[q], st)));
+    }
+    GramTolArgs ga{};
+    ga.groups = B.bg.as<BigGroup>();
+    ga.gdesc = d_groups.as<GroupDesc>();
+    ga.boxes = d_boxes.as<BoxDesc>();
+    ga.GKws = GK;
+    ga.GSws = GS;
+    ga.eps = h->eps;
+    ga.tol_floor = tol_floor;
+    HIF_CUDA((launch_gram_tol<T>(ga, ng, max_ng, st)));
+    BigArgs a{};
+    a.groups = B.bg.as<BigGroup>();
+    a.state = B.state.as<BigState>();
+    a.gdesc = d_groups.as<GroupDesc>();
+    a.YK = B.YK.p;
+    a.nrm = B.nrm.as<double>();
+    a.perm = B.perm.as<int>();
+    a.Tws = Tws.p;
+    a.perm_out = perm_out.as<int>();
+    a.k_out = k_out.as<int>();
+    HIF_CUDA((big_qr_init<T>(a, ng, max_n, st)));
+    std::vector<BigState> hs(ng);
+    for (int j = 0; j < maxk; ++j) {
+        {
+            ProfRange pr(PROF_BIG_QR, st, 0.0, 0.0);   // bytes added once the ranks are known
+            HIF_CUDA((big_qr_step<T>(a, ng, max_n, j, st)));
+        }
+        if ((j + 1) % 16 == 0) {
+            HIF_CUDA(cudaMemcpyAsync(hs.data(), B.state.p, sizeof(BigState) * ng, cudaMemcpyDeviceToHost, st));
+            HIF_CUDA(cudaStreamSynchronize(st));
+            bool all = true;
+            for (const BigState& x : hs) all = all && x.stop;
+            if (all) break;
+        }
+    }
+    ProfRange pr(PROF_BIG_T, st, 0.0, 0.0);
+    HIF_CUDA((big_finish<T>(a, ng, max_n, st)));
+}
+
 // The eliminations of one sublevel (or of the top blocks): boxes in factor
 // order, each in the one-CTA list (ed) or the batched multi-CTA list
 // (ed_big).  Places every box in the sublevel's pools, launches, and, if an
@@ -684,8 +768,11 @@ static void run_factor(hif_handle h) {
     DevMem d_boxes, d_groups, d_cols, d_near, Rws, GKws, GSws, Tws, Wws, Woff, perm_out, k_out;
     DevMem d_small_boxes, d_small_groups, d_small_sorted;
     FactorScratch S;
-    BigBuffers big;
+    BigBuffers big, bigR;
     const int big_id_n = env_int("HIF_BIG_ID", sizeof(T) == 8 ? 128 : 256);
+    // large FP32 boxes up to 1024 columns: fold to R, pivoted QR on R
+    // (HIF_FOLD_BIG=0 keeps them on the materialized-proxy-matrix path)
+    const bool fold_big = sizeof(T) == 4 && env_int("HIF_FOLD_BIG", 1) != 0;
     // boxes with k + r above this are eliminated by the batched multi-CTA
     // kernels instead of one CTA per box (measured on GB300 for the n = 1024
     // grid: 400 beats 600 by 15% in FP32 and 5% in FP64)
@@ -736,11 +823,17 @@ static void run_factor(hif_handle h) {
         int maxn = 0, maxng = 0, maxmrow = 0;
         bool any_sci = false;
         std::vector<int64_t> woff(ngr);
-        std::vector<int> small_boxes, small_groups, big_boxes;
+        std::vector<int> small_boxes, small_groups, big_boxes, rbig_boxes;
+        std::vector<char> box_class(nb, 0);   // 0 small, 1 folded large, 2 materialized large
         double fold_flops = 0.0;
         for (int bI = 0; bI < nb; ++bI) {
             BoxDesc& b = bd[bI];
-            const bool isbig = (p.box_off[bI + 1] - p.box_off[bI]) > big_id_n;
+            const int nbI = (int)(p.box_off[bI + 1] - p.box_off[bI]);
+            // large boxes whose proxy matrix the fold kernel can still reduce
+            // to R (FP32, up to 1024 columns) take their pivoted QR on R
+            const bool folded = nbI > big_id_n && fold_big && fold_cpt(nbI, (int)sizeof(T)) > 0;
+            const bool isbig = nbI > big_id_n && !folded;
+            box_class[bI] = isbig ? 2 : folded ? 1 : 0;
             b.n = (int)(p.box_off[bI + 1] - p.box_off[bI]);
             b.m_near = (int)(p.near_off[bI + 1] - p.near_off[bI]);
             b.ngroups = (int)(p.grp_off[bI + 1] - p.grp_off[bI]);
@@ -755,7 +848,8 @@ static void run_factor(hif_handle h) {
             b.radius = radius[bI];
             if (isbig) big_boxes.push_back(bI);
             else {
-                small_boxes.push_back(bI);
+                small_boxes.push_back(bI);          // every folded box
+                if (folded) rbig_boxes.push_back(bI);
                 maxn = std::max(maxn, b.n);
                 if (b.has_sci) any_sci = true;
             }
@@ -776,7 +870,7 @@ static void run_factor(hif_handle h) {
                 G.perm_off = b.col_off + G.col0;
                 const int mrow = G.col0 + G.n;
                 woff[gi] = Woffs;
-                if (!isbig) {
+                if (!isbig && !folded) {
                     small_groups.push_back((int)gi);
                     Woffs += (int64_t)(mrow | 1) * G.n;
                     maxng = std::max(maxng, G.n);
@@ -827,17 +921,21 @@ static void run_factor(hif_handle h) {
                 // CTA is the box width rounded up to a warp
                 ProfRange pr(PROF_FOLD, st, fold_flops, 0.0);
                 int64_t at = 0;
-                for (int w = 32; w <= 256 && at < (int64_t)small_boxes.size(); w += 32) {
+                const int widths[] = {32, 64, 96, 128, 160, 192, 224, 256, 512, 1024};
+                for (int w : widths) {
+                    if (at >= (int64_t)small_boxes.size()) break;
                     const int64_t b0 = at;
                     while (at < (int64_t)small_boxes.size() && bd[small_sorted[at]].n <= w) ++at;
                     if (at == b0) continue;
+                    const int cpt = fold_cpt(w, (int)sizeof(T));
+                    if (cpt == 0) fail(HIF_EINVAL, "box too wide for the fold kernel");
                     FoldArgs fb = fa;
                     fb.box_list = d_small_sorted.as<int>() + b0;
-                    size_t smem = fold_smem_bytes(w, 0, grams, true, sizeof(T));
+                    size_t smem = fold_smem_bytes(w, cpt, grams, true, sizeof(T));
                     fb.R_in_smem = smem <= 220 * 1024;
-                    if (!fb.R_in_smem) smem = fold_smem_bytes(w, 0, grams, false, sizeof(T));
+                    if (!fb.R_in_smem) smem = fold_smem_bytes(w, cpt, grams, false, sizeof(T));
                     if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
-                    HIF_CUDA((launch_fold<T>(fb, (int)(at - b0), w, smem, st)));
+                    HIF_CUDA((launch_fold<T>(fb, (int)(at - b0), cpt == 1 ? w : 256, cpt, smem, st)));
                 }
                 if (at != (int64_t)small_boxes.size()) fail(HIF_EINVAL, "box too wide for the fold kernel");
             }
@@ -871,6 +969,9 @@ static void run_factor(hif_handle h) {
                 ProfRange pr(PROF_ID, st, 0.0, 0.0);     // work added once the ranks are known
                 HIF_CUDA((launch_id<T>(ia, (int)small_groups.size(), ismem, st)));
             }
+            if (!rbig_boxes.empty())
+                run_big_id_R<T>(h, bd, gd, rbig_boxes, d_boxes, d_groups, Rws, grams ? GKws.p : nullptr,
+                                grams ? GSws.p : nullptr, Tws, perm_out, k_out, tol_floor, bigR);
         }
         if (!big_boxes.empty()) run_big_id<T>(h, tau, bd, gd, p, big_boxes, d_boxes, d_groups, d_cols, d_near, Tws,
                                               perm_out, k_out, tol_floor, big);
@@ -890,10 +991,13 @@ static void run_factor(hif_handle h) {
                 const GroupDesc& G = gd[gi];
                 const BoxDesc& b = bd[G.box];
                 const double k = kg[gi], n = G.n, r = n - k;
-                const bool isbig = b.n > big_id_n;
-                if (!isbig) {
+                const int cls = box_class[G.box];
+                if (cls == 0) {
                     const double mr = G.col0 + G.n;
                     idf += 4.0 * mr * n * k - 2.0 * k * k * (mr + n) + 4.0 * k * k * k / 3.0 + k * k * r;
+                } else if (cls == 1) {
+                    const double mr = G.col0 + G.n;
+                    for (int j = 0; j < kg[gi]; ++j) qr_bytes += 2.0 * sizeof(T) * (mr - j) * (n - j);
                 } else {
                     const double m = (b.sym ? 1.0 : 2.0) * (b.m_near + h->P);
                     for (int j = 0; j < kg[gi]; ++j) qr_bytes += 2.0 * sizeof(T) * m * (n - j);

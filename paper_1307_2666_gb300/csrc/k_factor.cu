@@ -42,26 +42,26 @@ __device__ inline T* align_ptr(unsigned char*& p, size_t count) {
 
 // ------------------------------------------------------------- fold ------
 //
-// One CTA per box, one thread per column of Y_c (blockDim = n rounded up to
-// a warp).  Y_c is generated RC rows at a time; thread l holds its column's
-// RC entries in registers and folds them into column l of R by Householder
-// reflections of [R; C]: at step j the owner of column j forms the reflector
-// from its own registers and publishes it (RC values and tau) in shared
-// memory, then every column l > j applies it to its registers and to R[j][l].
-// Column l of R is touched by thread l only, so one CTA barrier per step
-// suffices (the reflector buffer is double-buffered).  R lives in shared
-// memory as a packed upper triangle, column l at l (l + 1) / 2 (triangular
-// numbers are distinct modulo 32, so a warp's accesses of one row are free of
-// bank conflicts), or, when it does not fit, row-major in global memory.  In second-kind mode
-// the chunk's kernel and SCI parts also pass through shared memory for the
-// Gram matrices of Y^K and Y^S inside each column group (Sec. 4.4), stored
-// diagonal-major: G[l][l + t] at t * n + l.
-template <typename T, int RC>
-__global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
+// One CTA per box; thread t owns the columns l = t + q * blockDim.x
+// (q < CPT) of Y_c.  Y_c is generated RC rows at a time; each thread holds its
+// columns' RC entries in registers and folds them into its columns of R by
+// Householder reflections of [R; C]: at step j the owner of column j forms
+// the reflector from its registers and publishes it (RC values and tau) in
+// shared memory, then every column l > j applies it to its registers and to
+// R[j][l].  Column l of R is touched by its owner only, so one CTA barrier
+// per step suffices (the reflector buffer is double-buffered), and the next
+// step's R[j + 1][l] is loaded a step ahead.  R lives in shared memory as a
+// packed upper triangle, column l at l (l + 1) / 2 (triangular numbers are
+// distinct modulo 32, so a warp's accesses of one row are free of bank
+// conflicts), or, when it does not fit, row-major in global memory.  In
+// second-kind mode the chunk's kernel and SCI parts also pass through shared
+// memory for the Gram matrices of Y^K and Y^S inside each column group
+// (Sec. 4.4), stored diagonal-major: G[l][l + t] at t * n + l.
+template <typename T, int RC, int CPT>
+__global__ void __launch_bounds__(256, CPT == 1 ? 2 : 1) fold_kernel(FoldArgs args) {
     const BoxDesc bx = args.boxes[args.box_list[blockIdx.x]];
     const int n = bx.n;
-    const int l = threadIdx.x;                  // this thread's column
-    const bool col = l < n;
+    const int NT = blockDim.x;
     const bool sym = bx.sym != 0;               // one row per pair: Y'_c
     const int ppc = sym ? RC : RC / 2;          // pairs per chunk
     const int nsub = args.sci.nsub;
@@ -82,43 +82,51 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
     T* CS = grams ? align_ptr<T>(sp, (size_t)RC * n) : nullptr;
     T* const Rglob = static_cast<T*>(args.Rws) + bx.R_off;
     T* const Rpack = args.R_in_smem ? align_ptr<T>(sp, (size_t)n * (n + 1) / 2) : nullptr;
-    // R[j][l] of this thread's column (j <= l)
-    T* const Rcol = args.R_in_smem ? Rpack + (size_t)l * (l + 1) / 2 : Rglob + l;
-    const int64_t rstride = args.R_in_smem ? 1 : n;
     T* GK = grams ? static_cast<T*>(args.GKws) + bx.R_off : nullptr;
     T* GS = grams ? static_cast<T*>(args.GSws) + bx.R_off : nullptr;
 
     const double c0 = bx.ctr[0], c1 = bx.ctr[1], c2 = dim == 3 ? bx.ctr[2] : 0.0;
-    // column data of this thread
-    int jid = 0, lend = 0;
-    T xj0 = T(0), xj1 = T(0), xj2 = T(0), cwc = T(0), cb = T(0), cbw = T(0);
-    if (col) {
-        jid = args.cols[bx.col_off + l];
-        xj0 = (T)(args.g.x[(int64_t)dim * jid + 0] - c0);
-        xj1 = (T)(args.g.x[(int64_t)dim * jid + 1] - c1);
-        xj2 = dim == 3 ? (T)(args.g.x[(int64_t)dim * jid + 2] - c2) : T(0);
-        cwc = (T)(args.g.w[jid] * args.g.c[jid]);
-        cb = (T)args.g.b[jid];
-        cbw = (T)(args.g.b[jid] * args.g.w[jid]);
-        for (int gi = 0; gi < bx.ngroups; ++gi) {
-            const GroupDesc gd = args.groups[bx.grp_off + gi];
-            if (l >= gd.col0 && l < gd.col0 + gd.n) lend = gd.col0 + gd.n;
-        }
-        for (int j = 0; j < (args.R_in_smem ? l + 1 : n); ++j) Rcol[j * rstride] = T(0);
-        if (grams)
-            for (int t = 0; t < n - l; ++t) {
-                GK[(int64_t)t * n + l] = T(0);
-                GS[(int64_t)t * n + l] = T(0);
+    // column data of this thread's columns
+    int jid[CPT], lend[CPT];
+    T xj0[CPT], xj1[CPT], xj2[CPT], cwc[CPT], cb[CPT], cbw[CPT];
+    T* Rcol[CPT];                               // R[j][l] at Rcol[q][j * rstride]
+    const int64_t rstride = args.R_in_smem ? 1 : n;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int l = threadIdx.x + q * NT;
+        jid[q] = 0;
+        lend[q] = 0;
+        xj0[q] = xj1[q] = xj2[q] = cwc[q] = cb[q] = cbw[q] = T(0);
+        Rcol[q] = args.R_in_smem ? Rpack + (size_t)l * (l + 1) / 2 : Rglob + l;
+        if (l < n) {
+            const int j = args.cols[bx.col_off + l];
+            jid[q] = j;
+            xj0[q] = (T)(args.g.x[(int64_t)dim * j + 0] - c0);
+            xj1[q] = (T)(args.g.x[(int64_t)dim * j + 1] - c1);
+            xj2[q] = dim == 3 ? (T)(args.g.x[(int64_t)dim * j + 2] - c2) : T(0);
+            cwc[q] = (T)(args.g.w[j] * args.g.c[j]);
+            cb[q] = (T)args.g.b[j];
+            cbw[q] = (T)(args.g.b[j] * args.g.w[j]);
+            for (int gi = 0; gi < bx.ngroups; ++gi) {
+                const GroupDesc gd = args.groups[bx.grp_off + gi];
+                if (l >= gd.col0 && l < gd.col0 + gd.n) lend[q] = gd.col0 + gd.n;
             }
+            for (int j2 = 0; j2 < (args.R_in_smem ? l + 1 : n); ++j2) Rcol[q][j2 * rstride] = T(0);
+            if (grams)
+                for (int t = 0; t < n - l; ++t) {
+                    GK[(int64_t)t * n + l] = T(0);
+                    GS[(int64_t)t * n + l] = T(0);
+                }
+        }
     }
 
     const int* near = args.near + bx.near_off;
     const int npairs = bx.m_near + args.P;
-    T c[RC];
+    T c[CPT][RC];
     for (int p0 = 0; p0 < npairs; p0 += ppc) {
         const int np = min(ppc, npairs - p0);
         __syncthreads();                        // previous chunk's row data and Gram reads done
-        for (int q = threadIdx.x; q < ppc; q += blockDim.x) {
+        for (int q = threadIdx.x; q < ppc; q += NT) {
             const int p = p0 + q;
             if (q >= np) {
                 rid[q] = -2;
@@ -141,38 +149,45 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
             }
         }
         __syncthreads();
-        // ---- this column's entries of the chunk, staged in shared memory:
+        // ---- this thread's columns of the chunk, staged in shared memory:
         // rows (2q, 2q+1) = (outgoing, incoming) of pair q, or row q alone
         // for symmetric A; kernel and SCI parts apart when the Grams need them
-        if (col) {
-            for (int q = 0; q < ppc; ++q) {
-                T k1, k2, s1, s2;
-                y_pair<T>(kid, rid[q], rxl[3 * q], rxl[3 * q + 1], rxl[3 * q + 2], rb[q], rwc[q], jid, xj0, xj1,
-                          xj2, cwc, cb, cbw, scival, args.sci, k1, k2, s1, s2);
-                const int i1 = sym ? q : 2 * q;
-                if (grams) {
-                    CK[i1 * n + l] = k1;
-                    CS[i1 * n + l] = s1;
-                    if (!sym) {
-                        CK[(i1 + 1) * n + l] = k2;
-                        CS[(i1 + 1) * n + l] = s2;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int l = threadIdx.x + q * NT;
+            if (l < n) {
+                for (int pq = 0; pq < ppc; ++pq) {
+                    T k1, k2, s1, s2;
+                    y_pair<T>(kid, rid[pq], rxl[3 * pq], rxl[3 * pq + 1], rxl[3 * pq + 2], rb[pq], rwc[pq], jid[q],
+                              xj0[q], xj1[q], xj2[q], cwc[q], cb[q], cbw[q], scival, args.sci, k1, k2, s1, s2);
+                    const int i1 = sym ? pq : 2 * pq;
+                    if (grams) {
+                        CK[i1 * n + l] = k1;
+                        CS[i1 * n + l] = s1;
+                        if (!sym) {
+                            CK[(i1 + 1) * n + l] = k2;
+                            CS[(i1 + 1) * n + l] = s2;
+                        }
+                    } else {
+                        CK[i1 * n + l] = k1 + s1;
+                        if (!sym) CK[(i1 + 1) * n + l] = k2 + s2;
                     }
-                } else {
-                    CK[i1 * n + l] = k1 + s1;
-                    if (!sym) CK[(i1 + 1) * n + l] = k2 + s2;
                 }
+#pragma unroll
+                for (int i = 0; i < RC; ++i) c[q][i] = grams ? CK[i * n + l] + CS[i * n + l] : CK[i * n + l];
+            } else {
+#pragma unroll
+                for (int i = 0; i < RC; ++i) c[q][i] = T(0);
             }
-#pragma unroll
-            for (int i = 0; i < RC; ++i) c[i] = grams ? CK[i * n + l] + CS[i * n + l] : CK[i * n + l];
-        } else {
-#pragma unroll
-            for (int i = 0; i < RC; ++i) c[i] = T(0);
         }
-        // ---- Gram matrices of Y^K_g and Y^S_g (this thread: row l, l <= l2 < group end)
+        // ---- Gram matrices of Y^K_g and Y^S_g (row l, l <= l2 < group end)
         if (grams) {
             __syncthreads();
-            if (col) {
-                for (int l2 = l; l2 < lend; ++l2) {
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int l = threadIdx.x + q * NT;
+                if (l >= n) continue;
+                for (int l2 = l; l2 < lend[q]; ++l2) {
                     T gk = T(0), gs = T(0);
 #pragma unroll 8
                     for (int i = 0; i < RC; ++i) {
@@ -185,54 +200,80 @@ __global__ void __launch_bounds__(256, 2) fold_kernel(FoldArgs args) {
             }
         }
         // ---- fold the chunk into R: Householder QR of [R; C]
+        T rcur[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) rcur[q] = threadIdx.x + q * NT < n ? Rcol[q][0] : T(0);
         for (int j = 0; j < n; ++j) {
             const int buf = j & 1;
-            if (l == j) {
-                T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
+            // the next step's R[j + 1][l], read a step ahead (only this thread writes it)
+            T rnext[CPT];
 #pragma unroll
-                for (int i = 0; i < RC; i += 4) {
-                    q0 += c[i] * c[i];
-                    q1 += c[i + 1] * c[i + 1];
-                    q2 += c[i + 2] * c[i + 2];
-                    q3 += c[i + 3] * c[i + 3];
-                }
-                const T ss = (q0 + q1) + (q2 + q3);
-                T tau = T(0);
-                if (ss != T(0)) {
-                    const T alpha = Rcol[j * rstride];
-                    const T beta = -copysign(sqrt(alpha * alpha + ss), alpha);
-                    tau = (beta - alpha) / beta;
-                    const T scal = T(1) / (alpha - beta);
-                    Rcol[j * rstride] = beta;
+            for (int q = 0; q < CPT; ++q) {
+                const int l = threadIdx.x + q * NT;
+                rnext[q] = (l < n && j + 1 <= l) ? Rcol[q][(j + 1) * rstride] : T(0);
+            }
+            const int oq = j / NT;                   // the owner's slot
+            if (threadIdx.x == j % NT) {
 #pragma unroll
-                    for (int i = 0; i < RC; ++i) vbuf[buf * RC + i] = c[i] * scal;
+                for (int q = 0; q < CPT; ++q) {
+                    if (q != oq) continue;
+                    T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
+#pragma unroll
+                    for (int i = 0; i < RC; i += 4) {
+                        q0 += c[q][i] * c[q][i];
+                        if (i + 1 < RC) q1 += c[q][i + 1] * c[q][i + 1];
+                        if (i + 2 < RC) q2 += c[q][i + 2] * c[q][i + 2];
+                        if (i + 3 < RC) q3 += c[q][i + 3] * c[q][i + 3];
+                    }
+                    const T ss = (q0 + q1) + (q2 + q3);
+                    T tau = T(0);
+                    if (ss != T(0)) {
+                        const T alpha = rcur[q];
+                        const T beta = -copysign(sqrt(alpha * alpha + ss), alpha);
+                        tau = (beta - alpha) / beta;
+                        const T scal = T(1) / (alpha - beta);
+                        Rcol[q][j * rstride] = beta;
+#pragma unroll
+                        for (int i = 0; i < RC; ++i) vbuf[buf * RC + i] = c[q][i] * scal;
+                    }
+                    taub[buf] = tau;
                 }
-                taub[buf] = tau;
             }
             __syncthreads();
             const T tau = taub[buf];
-            if (l > j && col && tau != T(0)) {
+            if (tau != T(0)) {
                 const T* v = vbuf + buf * RC;
-                T w0 = Rcol[j * rstride], w1 = T(0), w2 = T(0), w3 = T(0);
 #pragma unroll
-                for (int i = 0; i < RC; i += 4) {
-                    w0 += v[i] * c[i];
-                    w1 += v[i + 1] * c[i + 1];
-                    w2 += v[i + 2] * c[i + 2];
-                    w3 += v[i + 3] * c[i + 3];
+                for (int q = 0; q < CPT; ++q) {
+                    const int l = threadIdx.x + q * NT;
+                    if (l > j && l < n) {
+                        T w0 = rcur[q], w1 = T(0), w2 = T(0), w3 = T(0);
+#pragma unroll
+                        for (int i = 0; i < RC; i += 4) {
+                            w0 += v[i] * c[q][i];
+                            if (i + 1 < RC) w1 += v[i + 1] * c[q][i + 1];
+                            if (i + 2 < RC) w2 += v[i + 2] * c[q][i + 2];
+                            if (i + 3 < RC) w3 += v[i + 3] * c[q][i + 3];
+                        }
+                        const T w = ((w0 + w1) + (w2 + w3)) * tau;
+                        Rcol[q][j * rstride] = rcur[q] - w;
+#pragma unroll
+                        for (int i = 0; i < RC; ++i) c[q][i] -= w * v[i];
+                    }
                 }
-                const T w = ((w0 + w1) + (w2 + w3)) * tau;
-                Rcol[j * rstride] -= w;
-#pragma unroll
-                for (int i = 0; i < RC; ++i) c[i] -= w * v[i];
             }
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) rcur[q] = rnext[q];
         }
     }
-    if (args.R_in_smem && col)
-        for (int j = 0; j < n; ++j) Rglob[(int64_t)j * n + l] = j <= l ? Rcol[j] : T(0);
+    if (args.R_in_smem)
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int l = threadIdx.x + q * NT;
+            if (l < n)
+                for (int j = 0; j < n; ++j) Rglob[(int64_t)j * n + l] = j <= l ? Rcol[q][j] : T(0);
+        }
 }
-
-// --------------------------------------------------------------- ID ------
 
 // Block-wide argmax of (v, original index o) over one candidate per thread:
 // largest v, ties to the lowest o; candidates with pos < 0 are ignored.
@@ -391,6 +432,9 @@ __device__ void cpqr_id(T* W, int rs, int cs, int mrow, int ng, double tol, doub
 
 
 template <typename T>
+__device__ double group_rho(const T* GKb, const T* GSb, int n, int col0, int ng, T* vec, double* redv);
+
+template <typename T>
 __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
     const int gidx = args.group_list[blockIdx.x];
     const GroupDesc gd = args.groups[gidx];
@@ -420,25 +464,41 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
     }
     __syncthreads();
 
-    // ---- rho_g (Sec. 4.4): 8 power iterations from the all-ones vector on
-    // the Gram matrices of Y^K_g and Y^S_g
+    // ---- rho_g (Sec. 4.4)
     double rho = 1.0;
-    if (args.second_kind && gd.has_sci && bx.has_sci && args.GKws != nullptr) {
+    if (args.second_kind && gd.has_sci && bx.has_sci && args.GKws != nullptr)
+        rho = group_rho<T>(static_cast<const T*>(args.GKws) + bx.R_off, static_cast<const T*>(args.GSws) + bx.R_off,
+                           n, gd.col0, ng, vec, redv);
+    double tol = rho * args.eps;
+    if (tol < args.tol_floor) tol = args.tol_floor;
+
+    cpqr_id<T>(W, ldw, 1, mrow, ng, tol, nrm, perm, rank_of, redv, redi, redi + 36, hh,
+               static_cast<T*>(args.Tws) + gd.T_off, args.perm_out + gd.perm_off, args.k_out + gidx);
+}
+
+// rho_g = min(1, |Y^K_g| / |Y^S_g|) (Sec. 4.4) from the Gram matrices of the
+// group's kernel and SCI parts (n x n box Grams, diagonal-major upper
+// triangles): 8 power iterations from the normalized all-ones vector, then
+// |Y v| = sqrt(v^T G v).  vec: 2 ng scratch, redv: blockDim doubles.
+template <typename T>
+__device__ double group_rho(const T* GKb, const T* GSb, int n, int col0, int ng, T* vec, double* redv) {
+    double rho = 1.0;
+    {
         double est[2];
         for (int which = 0; which < 2; ++which) {
-            const T* G = static_cast<const T*>(which == 0 ? args.GKws : args.GSws) + bx.R_off;
+            const T* G = which == 0 ? GKb : GSb;
             T* v = vec;
             T* wv = vec + ng;
             for (int l = threadIdx.x; l < ng; l += blockDim.x) v[l] = T(1) / sqrt(T(ng));
             __syncthreads();
             double result = 0.0;
             for (int it = 0; it <= 8; ++it) {
-                // w = G v (G symmetric, upper triangle stored row-major)
+                // w = G v (G symmetric, upper triangle stored diagonal-major)
                 for (int l = threadIdx.x; l < ng; l += blockDim.x) {
                     T acc = T(0);
-                    const int gl = gd.col0 + l;
+                    const int gl = col0 + l;
                     for (int q = 0; q < ng; ++q) {
-                        const int gq = gd.col0 + q;
+                        const int gq = col0 + q;
                         // diagonal-major upper triangle: G[a][a + t] at t * n + a
                         const T gv = gl <= gq ? G[(int64_t)(gq - gl) * n + gl] : G[(int64_t)(gl - gq) * n + gq];
                         acc += gv * v[q];
@@ -468,11 +528,37 @@ __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
         }
         if (est[1] > 0.0) rho = fmin(1.0, est[0] / est[1]);
     }
-    double tol = rho * args.eps;
-    if (tol < args.tol_floor) tol = args.tol_floor;
+    return rho;
+}
 
-    cpqr_id<T>(W, ldw, 1, mrow, ng, tol, nrm, perm, rank_of, redv, redi, redi + 36, hh,
-               static_cast<T*>(args.Tws) + gd.T_off, args.perm_out + gd.perm_off, args.k_out + gidx);
+// Tolerances of the large groups whose box was folded into R: one CTA per
+// group, rho_g from the box Grams when the group has SCI (Sec. 4.4).
+template <typename T>
+__global__ void __launch_bounds__(128) gram_tol_kernel(GramTolArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* sp = smem;
+    BigGroup& G = a.groups[blockIdx.x];
+    const GroupDesc gd = a.gdesc[G.group];
+    const BoxDesc bx = a.boxes[gd.box];
+    double* redv = align_ptr<double>(sp, blockDim.x);
+    T* vec = align_ptr<T>(sp, 2 * (size_t)gd.n);
+    double rho = 1.0;
+    if (G.need_rho && a.GKws != nullptr)
+        rho = group_rho<T>(static_cast<const T*>(a.GKws) + bx.R_off, static_cast<const T*>(a.GSws) + bx.R_off, bx.n,
+                           gd.col0, gd.n, vec, redv);
+    double tol = rho * a.eps;
+    if (tol < a.tol_floor) tol = a.tol_floor;
+    if (threadIdx.x == 0) G.tol = tol;
+}
+
+// R (n x n row-major, upper triangle) -> column-major with leading dimension n
+template <typename T>
+__global__ void r_colmajor_kernel(const T* R, int n, T* out) {
+    const int64_t tot = (int64_t)n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, j = e / n;
+        out[e] = R[i * n + j];
+    }
 }
 
 // ------------------------------------------------------ elimination ------
@@ -702,12 +788,21 @@ cudaError_t launch_id_batched(int count, const double* mats, const int64_t* off,
 
 // ---------------------------------------------------------- launchers ----
 
-// Rows of Y_c per fold chunk (registers per thread of the fold kernel).
-constexpr int kFoldRC = 32;
+// Fold configurations: rows per chunk (RC) and columns per thread (CPT);
+// RC * CPT registers of the element type hold a thread's share of the chunk.
+int fold_cpt(int n, int elem) {
+    if (n <= 256) return elem == 8 && n > 128 ? 2 : 1;
+    if (n <= 512) return elem == 8 ? 4 : 2;
+    if (n <= 1024) return elem == 8 ? 0 : 4;
+    return 0;                                         // too wide: the materialized path
+}
+static int fold_rc(int cpt, int elem) {
+    if (elem == 4) return cpt == 1 ? 32 : cpt == 2 ? 32 : 16;
+    return cpt == 1 ? 32 : cpt == 2 ? 16 : 8;
+}
 
-size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem) {
-    (void)bpairs;
-    const size_t rc = kFoldRC;
+size_t fold_smem_bytes(int n, int cpt, bool sci, bool R_in_smem, int elem) {
+    const size_t rc = fold_rc(cpt, elem);
     size_t b = 0;
     b += rc * (5 * (size_t)elem + 4) + 64;             // row data
     b += 2 * rc * elem + 2 * (size_t)elem + 32;        // reflector buffers
@@ -722,17 +817,32 @@ size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem) {
     return b + 64;
 }
 
-// threads: the launch's largest box width rounded up to a warp (<= 256)
-template <typename T>
-cudaError_t launch_fold(const FoldArgs& a, int nbox, int threads, size_t smem, cudaStream_t st) {
-    if (nbox == 0) return cudaSuccess;
-    if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fold_kernel<T, kFoldRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename T, int RC, int CPT>
+static cudaError_t launch_fold_cfg(const FoldArgs& a, int nbox, int threads, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(fold_kernel<T, RC, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    fold_kernel<T, kFoldRC><<<nbox, threads, smem, st>>>(a);
+    fold_kernel<T, RC, CPT><<<nbox, threads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// threads: the launch's largest box width rounded up to a warp (<= 256) for
+// one column per thread, else 256; cpt from fold_cpt of the widest box
+template <typename T>
+cudaError_t launch_fold(const FoldArgs& a, int nbox, int threads, int cpt, size_t smem, cudaStream_t st) {
+    if (nbox == 0) return cudaSuccess;
+    if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
+    if constexpr (sizeof(T) == 4) {
+        if (cpt == 1) return launch_fold_cfg<T, 32, 1>(a, nbox, threads, smem, st);
+        if (cpt == 2) return launch_fold_cfg<T, 32, 2>(a, nbox, threads, smem, st);
+        if (cpt == 4) return launch_fold_cfg<T, 16, 4>(a, nbox, threads, smem, st);
+    } else {
+        if (cpt == 1) return launch_fold_cfg<T, 32, 1>(a, nbox, threads, smem, st);
+        if (cpt == 2) return launch_fold_cfg<T, 16, 2>(a, nbox, threads, smem, st);
+        if (cpt == 4) return launch_fold_cfg<T, 8, 4>(a, nbox, threads, smem, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -753,8 +863,33 @@ cudaError_t launch_elim(const ElimArgs& a, int nbox, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fold<double>(const FoldArgs&, int, int, size_t, cudaStream_t);
-template cudaError_t launch_fold<float>(const FoldArgs&, int, int, size_t, cudaStream_t);
+template <typename T>
+cudaError_t launch_gram_tol(const GramTolArgs& a, int ngroups, int max_ng, cudaStream_t st) {
+    if (ngroups == 0) return cudaSuccess;
+    const size_t smem = 128 * sizeof(double) + 2 * (size_t)max_ng * sizeof(T) + 64;
+    cudaError_t e = cudaFuncSetAttribute(gram_tol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    gram_tol_kernel<T><<<ngroups, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_r_colmajor(const void* R, int n, void* out, cudaStream_t st) {
+    const int64_t tot = (int64_t)n * n;
+    if (tot == 0) return cudaSuccess;
+    note_launch();
+    r_colmajor_kernel<T><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 2048), 256, 0, st>>>(
+        static_cast<const T*>(R), n, static_cast<T*>(out));
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gram_tol<double>(const GramTolArgs&, int, int, cudaStream_t);
+template cudaError_t launch_gram_tol<float>(const GramTolArgs&, int, int, cudaStream_t);
+template cudaError_t launch_r_colmajor<double>(const void*, int, void*, cudaStream_t);
+template cudaError_t launch_r_colmajor<float>(const void*, int, void*, cudaStream_t);
+template cudaError_t launch_fold<double>(const FoldArgs&, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_fold<float>(const FoldArgs&, int, int, int, size_t, cudaStream_t);
 template cudaError_t launch_id<double>(const IdArgs&, int, size_t, cudaStream_t);
 template cudaError_t launch_id<float>(const IdArgs&, int, size_t, cudaStream_t);
 template cudaError_t launch_elim<double>(const ElimArgs&, int, cudaStream_t);

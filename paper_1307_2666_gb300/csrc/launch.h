@@ -176,10 +176,26 @@ struct BatchElimArgs {
 };
 template <typename T> cudaError_t big_elim_batch(const BatchElimArgs&, int max_n, int max_k, int max_r, cudaStream_t);
 
-size_t fold_smem_bytes(int n, int bpairs, bool sci, bool R_in_smem, int elem);
+size_t fold_smem_bytes(int n, int cpt, bool sci, bool R_in_smem, int elem);
 size_t id_smem_bytes(int ng, int mrow, bool W_in_smem, int elem);
 
-template <typename T> cudaError_t launch_fold(const FoldArgs&, int nbox, int threads, size_t smem, cudaStream_t);
+// tolerances of large groups from the box Grams (boxes folded into R)
+struct GramTolArgs {
+    BigGroup* groups;
+    const GroupDesc* gdesc;
+    const BoxDesc* boxes;
+    const void* GKws;
+    const void* GSws;
+    double eps;
+    double tol_floor;
+};
+template <typename T> cudaError_t launch_gram_tol(const GramTolArgs&, int ngroups, int max_ng, cudaStream_t);
+template <typename T> cudaError_t launch_r_colmajor(const void* R, int n, void* out, cudaStream_t);
+
+// columns per thread of the fold kernel for a box of n columns (0: too wide)
+int fold_cpt(int n, int elem);
+template <typename T>
+cudaError_t launch_fold(const FoldArgs&, int nbox, int threads, int cpt, size_t smem, cudaStream_t);
 template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t smem, cudaStream_t);
 template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStream_t);
 

@@ -195,3 +195,29 @@ def test_ldl_not_used_for_nonsymmetric_problems(P):
     f = factor(P, pb, 1e-6)
     assert f.stats()["ldl_boxes"] == 0 and f.stats()["symmetric_problems"] == 0
     f.close()
+
+
+def test_large_boxes_folded_to_R_fp32(P, monkeypatch):
+    # FP32 boxes above the one-column-per-thread width are folded to R by the
+    # multi-column fold and their pivoted QR runs on R (Sec. 2.2: the ID of
+    # R[:, g] is that of Y_c[:, g]); against the materialized-Y_c path and the
+    # dense solve, with boxes above 40 columns sent down the large-box paths
+    pb = hi.volume_problem(64, 2, smooth_seed=1002, rhs_seed=1001)
+    monkeypatch.setenv("HIF_BIG_ID", "40")
+    fr = factor(P, pb, 1e-6, precision="fp32")
+    monkeypatch.setenv("HIF_FOLD_BIG", "0")
+    fm = factor(P, pb, 1e-6, precision="fp32")
+    monkeypatch.delenv("HIF_FOLD_BIG")
+    monkeypatch.delenv("HIF_BIG_ID")
+    sr, sm = fr.stats(), fm.stats()
+    for a, b in zip(sr["per_sublevel"], sm["per_sublevel"]):
+        assert abs(a["skeletons"] - b["skeletons"]) <= 2 + 0.01 * b["skeletons"]
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    f = pb.f[:, 0]
+    u = dense.DenseSolver(op).solve(f)
+    assert relerr(fr.solve(T(f)).cpu().numpy(), u) <= 1e-4
+    assert relerr(fr.solve(T(f)).cpu().numpy(), fm.solve(T(f)).cpu().numpy()) <= 1e-4
+    x, its, rel = fr.solve_refined(T(f), tol=1e-10)
+    assert rel <= 1e-10 and relerr(x.cpu().numpy(), u) <= 1e-9
+    fr.close()
+    fm.close()
