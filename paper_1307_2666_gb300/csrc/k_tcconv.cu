@@ -8,12 +8,15 @@
 // |dT_s|, |dX_t| <= 128 (round-to-nearest digit extraction in FP64, exact).
 // Digits are BF16 integers, so dT_s * dX_t is exact in the tensor core and
 // a sum of up to 1024 of them (<= 2^24) is exact in its FP32 accumulator.
-// Products of digit pairs (s, t) are accumulated separately, converted to
-// integers every 1024 sources and added into 64-bit integer class sums
-// (class k = s + t, weight 2^(eT + eX - 8(k + 2))), so the only rounding is
-// the dropped digits (below 2^-55 of max|t| max|v|) and the final FP64
-// combination of eight class sums.  Table digits 0..6 and source digits 0..7
-// are kept, and pairs with s + t >= 8 are not formed.
+// Products of digit pairs (s, t) of the same class k = s + t carry the same
+// weight 2^(eT + eX - 8(k + 2)), so they share one accumulator column: the
+// MMA of table digit s writes the columns of classes s .. s + t_max.  A
+// column then sums at most 8 pairs x 128 sources = 1024 products per slot
+// (<= 2^24, exact in FP32); every slot's columns are converted to integers
+// and added into 64-bit integer class sums, so the only rounding is the
+// dropped digits (below 2^-55 of max|t| max|v|) and the final FP64
+// combination of eight class sums.  Table digits 0..6 and source digits
+// 0..7 are kept, and pairs with s + t >= 8 are not formed.
 //
 // On a grid K_ij depends only on the offset i - j, so the kernel block of a
 // tile of 128 targets on one grid line against 128 sources on another line is
@@ -40,10 +43,10 @@
 //   warps 5-7  builders of the Hankel operand from mirrored digit rows; one
 //              of them also issues the bulk copies of the source digits.
 // Slots (one Hankel operand, a pair of 128-source chunks) flow through a
-// 3-stage shared-memory ring into one 512-column accumulator that the
-// epilogue drains every 8 slots.  Every wait is bounded; on time-out the
-// kernel sets *status = 1, drains its own MMAs and copies, frees TMEM and
-// returns.
+// 3-stage shared-memory ring into four 128-column accumulators used in turn,
+// so the MMAs of the next slots proceed while the epilogue drains one.  Every
+// wait is bounded; on time-out the kernel sets *status = 1, drains its own
+// MMAs and copies, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cstdlib>
@@ -74,28 +77,25 @@ constexpr int TBLK = NR * KC * 2;               // the rows of one digit of one 
 constexpr int B_BYTES = 2 * CHUNK;              // the mirrored pair
 constexpr int STAGE = A_BYTES + B_BYTES;
 constexpr int NST = 3;                          // ring depth
-constexpr int GROUP = 8;                        // slots per exact FP32 window (1024 sources per column)
-constexpr int ACC = 512;                        // TMEM columns of the accumulator
+constexpr int ACCB = 128;                       // TMEM columns of one accumulator: (class, half, rhs)
+constexpr int NACC = 4;                         // accumulators, used slot by slot in turn
+constexpr int ACC = ACCB * NACC;                // TMEM columns allocated
 constexpr int NBUILD = 96;                      // builder threads
 constexpr int NPAIR = ST * NBLK;                // (slice, core matrix) build items per slot
 constexpr long long WAIT_CYCLES = 4000000000LL; // ~2 s at GB300 clocks
 
 static_assert(STAGE % 16 == 0 && A_BYTES % 16 == 0 && TBLK % 16 == 0, "stage alignment");
-static_assert(GROUP * KC * 128 * 128 <= (1 << 24), "exact FP32 window");
+static_assert(8 * KC * 128 * 128 <= (1 << 24), "exact FP32 accumulation of one slot");
 
-// accumulator columns of table digit s: (source digit t, half, rhs) rows of
-// B, t limited so that s + t <= 7 (rounded up to the 16-row MMA granularity
-// per half)
+// columns of table digit s: B rows (source digit t, half, rhs) for t below
+// ncols(s) / 16 (s + t <= 7, even t counts: 16-row granularity per half),
+// written to the accumulator columns (class s + t, half, rhs), i.e. from
+// column 16 s on
 __host__ __device__ constexpr int ncols(int s) { return s == 0 ? 128 : s <= 2 ? 96 : s <= 4 ? 64 : 32; }
-__host__ __device__ constexpr int coloff(int s) {
-    return s == 0 ? 0 : s == 1 ? 128 : s == 2 ? 224 : s == 3 ? 320 : s == 4 ? 384 : s == 5 ? 448 : 480;
-}
-__host__ __device__ constexpr int col_slice(int c) {
-    return c < 128 ? 0 : c < 224 ? 1 : c < 320 ? 2 : c < 384 ? 3 : c < 448 ? 4 : c < 480 ? 5 : 6;
-}
-__host__ __device__ constexpr int col_class(int c) { return col_slice(c) + (c - coloff(col_slice(c))) / 16; }
-__host__ __device__ constexpr int col_rhs(int c) { return (c - coloff(col_slice(c))) % 8; }
-static_assert(coloff(6) + ncols(6) == ACC, "column map");
+__host__ __device__ constexpr int coloff(int s) { return 16 * s; }
+__host__ __device__ constexpr int col_class(int c) { return c / 16; }
+__host__ __device__ constexpr int col_rhs(int c) { return c % 8; }
+static_assert(coloff(6) + ncols(6) <= ACCB && ncols(0) == ACCB, "column map");
 
 __device__ __forceinline__ int scale_exp(unsigned long long maxbits) {
     const double m = __longlong_as_double((long long)maxbits);
@@ -122,8 +122,8 @@ struct Bars {
     uint64_t full[NST];         // Hankel operand built (NBUILD arrivals)
     uint64_t bfull[NST];        // source digits landed (1 arrival + bytes)
     uint64_t mma_done[NST];
-    uint64_t acc_full;
-    uint64_t acc_empty;
+    uint64_t acc_full[NACC];    // accumulator written (1 commit)
+    uint64_t acc_empty[NACC];   // accumulator drained (128 epilogue arrivals)
     uint64_t drain;
     uint32_t tmem;
     int abort;
@@ -297,8 +297,10 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
             tc::mbar_init(&bars->bfull[i], 1);
             tc::mbar_init(&bars->mma_done[i], 1);
         }
-        tc::mbar_init(&bars->acc_full, 1);
-        tc::mbar_init(&bars->acc_empty, 128);
+        for (int i = 0; i < NACC; ++i) {
+            tc::mbar_init(&bars->acc_full[i], 1);
+            tc::mbar_init(&bars->acc_empty[i], 128);
+        }
         tc::mbar_init(&bars->drain, 1);
         bars->abort = 0;
         tc::fence_mbar_init();
@@ -321,13 +323,12 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
             w.init(a, a.stall ? a.tiles : (int64_t)blockIdx.x, gridDim.x);
             int st = 0;
             uint32_t ph = 0;
-            int64_t si = 0, G = 0;
+            int64_t si = 0;                      // slots issued: accumulator si % NACC, use si / NACC
             bool ok = true;
             while (w.ok) {
-                const bool first = (si & (GROUP - 1)) == 0;
-                const bool tend = w.tile_end();
-                const bool last = (si & (GROUP - 1)) == GROUP - 1 || tend;
-                if (first && G >= 1 && !wait_bounded(&bars->acc_empty, (uint32_t)((G - 1) & 1), abort)) {
+                const int ab = (int)(si % NACC);
+                const int64_t use = si / NACC;
+                if (use >= 1 && !wait_bounded(&bars->acc_empty[ab], (uint32_t)((use - 1) & 1), abort)) {
                     ok = false;
                     break;
                 }
@@ -344,21 +345,20 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
                 // slice by slice: consecutive MMAs of one slice read
                 // overlapping Hankel windows and keep N and D fixed, which
                 // the tensor core streams faster than alternating slices
+                // (the first MMA, slice 0 with N = 128, initializes all the
+                // accumulator's columns; the others add into theirs)
 #pragma unroll
                 for (int s = 0; s < ST; ++s) {
                     const uint64_t as = a0 + (uint64_t)(s * A_SLICE / 16);
-                    const uint32_t d = tmem + coloff(s);
+                    const uint32_t d = tmem + ACCB * ab + coloff(s);
 #pragma unroll
                     for (int kk = 0; kk < KC / 16; ++kk)
                         tc::mma_bf16(d, as + (uint64_t)(2 * CM * kk / 16), b0 + (uint64_t)(16 * kk),
-                                     tc::idesc_bf16_f32(TM, ncols(s)), !(first && kk == 0));
+                                     tc::idesc_bf16_f32(TM, ncols(s)), !(s == 0 && kk == 0));
                 }
                 tc::mma_commit(&bars->mma_done[st]);
-                if (last) {
-                    tc::mma_commit(&bars->acc_full);
-                    ++G;
-                }
-                si = tend ? 0 : si + 1;
+                tc::mma_commit(&bars->acc_full[ab]);
+                ++si;
                 w.next();
                 if (++st == NST) {
                     st = 0;
@@ -472,22 +472,23 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
 #pragma unroll
             for (int r = 0; r < NR; ++r) acc[k][r] = 0;
         const int eT = scale_exp(*a.tmax);
-        int64_t G = 0;
+        int64_t si = 0;                                        // slots drained
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < a.tiles && ok; tile += gridDim.x) {
             Walk w;
             w.init(a, tile, a.tiles);                          // this tile only
-            const int64_t ngr = (w.slots() + GROUP - 1) / GROUP;
-            for (int64_t g = 0; g < ngr; ++g, ++G) {
-                if (!wait_bounded(&bars->acc_full, (uint32_t)(G & 1), abort)) {
+            const int64_t nsl = w.slots();
+            for (int64_t g = 0; g < nsl; ++g, ++si) {
+                const int ab = (int)(si % NACC);
+                if (!wait_bounded(&bars->acc_full[ab], (uint32_t)((si / NACC) & 1), abort)) {
                     ok = false;
                     break;
                 }
                 tc::tc_fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
+                const uint32_t tbase = tmem + ACCB * ab + ((uint32_t)(32 * warp) << 16);
                 // 64 columns per TMEM load and wait
 #pragma unroll
-                for (int cb = 0; cb < ACC / 64; ++cb) {
+                for (int cb = 0; cb < ACCB / 64; ++cb) {
                     float v[64];
                     tc::tmem_ld64(tbase + 64 * cb, v);
 #pragma unroll
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
                         acc[col_class(64 * cb + i)][col_rhs(64 * cb + i)] += (long long)__float2int_rn(v[i]);
                 }
                 tc::tc_fence_before();
-                tc::mbar_arrive(&bars->acc_empty);
+                tc::mbar_arrive(&bars->acc_empty[ab]);
             }
             if (!ok) break;
             const int il = TM * w.b + TM - 1 - (32 * warp + lane);
