@@ -24,6 +24,7 @@ __all__ = [
     "Problem",
     "volume_problem",
     "batched_sizes",
+    "helmholtz_problem",
 ]
 
 
@@ -133,6 +134,28 @@ def volume_problem(n: int, dim: int = 2, *, smooth_seed: int | None = None,
     f = gaussian_rhs(N, nrhs, rhs_seed)
     return Problem(n=n, dim=dim, kernel_id=0 if dim == 2 else 1, points=pts, weights=w,
                    a=a, b=bc.copy(), c=bc.copy(), f=f, proxy=proxy_directions(dim, seed=proxy_seed))
+
+
+def helmholtz_problem(n: int, kappa: float, *, rhs_seed: int = 1101, nrhs: int = 1) -> Problem:
+    """Lippmann-Schwinger scattering on the unit square (Sec. 5, Example 3).
+
+    Wavenumber k = 2 pi kappa (kappa wavelengths across the domain), scatterer
+    omega(x) = exp(-32 |x - (1/2, 1/2)|^2), a = 1 and b = c = k sqrt(omega);
+    the kernel (kernel_id 2) is (i/4) H_0^(1)(k r).  Right-hand sides are
+    complex with independent standard normal real and imaginary parts.
+    """
+    pts, w = grid_points(n, 2)
+    N = pts.shape[0]
+    k = 2.0 * math.pi * kappa
+    d = pts - 0.5
+    omega = np.exp(-32.0 * (d * d).sum(axis=1))
+    bc = k * np.sqrt(omega)
+    rng = np.random.default_rng(rhs_seed)
+    f = np.asfortranarray(rng.standard_normal((N, nrhs)) + 1j * rng.standard_normal((N, nrhs)))
+    pb = Problem(n=n, dim=2, kernel_id=2, points=pts, weights=w, a=np.ones(N), b=bc.copy(), c=bc.copy(), f=f,
+                 proxy=proxy_directions(2))
+    pb.k = k
+    return pb
 
 
 def batched_sizes(P: int, seed: int, choices=tuple(range(32, 257, 16))) -> list[int]:

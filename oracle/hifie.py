@@ -64,6 +64,11 @@ Readings of points the paper leaves open (the GPU path uses the same ones):
     instead (2 x 2 pivots are not used).  With U = L^T P the factored form
     is the LU one, P B_rr = L D U, and Y = D^{-1} L^{-1} P B_rs = X^T, so
     only X is kept; the Schur update -X D X^T is symmetric by construction.
+10. Helmholtz (Sec. 5, Example 3): complex arithmetic is carried out in the
+    real 2 x 2 embedding z -> [[Re z, -Im z], [Im z, Re z]] (oracle/helmholtz.py):
+    DOF j becomes real DOFs 2j, 2j + 1 at the same point, the proxy surface
+    contributes two rows per point and direction, and the whole method runs
+    unchanged on the real operator.  Its transposes are the complex adjoints.
 """
 from __future__ import annotations
 
@@ -325,15 +330,22 @@ def sublevel_plan(dim: int, L: int, fractional: bool = True, skip_levels: int = 
 def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
            *, second_kind: bool = True, occupancy: int = 64, proxy_radius: float = 1.5,
            fractional: bool = True, skip_levels: int = 0, symmetric=None, ldl=None,
-           trace=None) -> HIFFactor:
+           wavenumber=None, trace=None) -> HIFFactor:
     """HIF-IE (Algorithm 4.1 / 4.2) of A = diag(a) + diag(b) K diag(c).
 
     ``symmetric``: None compresses Y'_c exactly when ``is_symmetric`` holds,
     False always compresses the full Y_c, True requires ``is_symmetric``.
     ``ldl``: None factors B_rr by LDL exactly when Y'_c is compressed
     (reading 9), False always by LU.
+    kernel_id 2 (Helmholtz, Sec. 5 Example 3, wavenumber k): the factorization
+    runs on the real 2 x 2 embedding of the complex operator (reading 10), on
+    2N real DOFs, two at every point; occupancy counts real DOFs.
     """
-    op = Operator(points, weights, a, b, c, kernel_id)
+    if kernel_id == 2:
+        from .helmholtz import EmbeddedOperator
+        op = EmbeddedOperator(points, weights, a, b, c, wavenumber)
+    else:
+        op = Operator(points, weights, a, b, c, kernel_id)
     if symmetric is None:
         symmetric = is_symmetric(op)
     elif symmetric and not is_symmetric(op):
@@ -389,7 +401,11 @@ def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
 
 
 def is_symmetric(op: Operator) -> bool:
-    """Sufficient test for A = A^T: b = c entrywise and equal weights."""
+    """Sufficient test for A = A^T: b = c entrywise and equal weights.  The
+    real embedding of a complex symmetric matrix is not symmetric (its
+    transpose embeds the conjugate transpose)."""
+    if op.kernel_id == 2:
+        return False
     return bool(np.array_equal(op.b, op.c) and np.all(op.w == op.w[0]))
 
 
@@ -454,18 +470,16 @@ def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_d
     # symmetric A the one-sided Y'_c of Sec. 5 (reading 8)
     xE = center[None, :] + radius * proxy_dirs
     YK_near1 = op.kernel_entries(cN, cbox)
-    dE = xE[:, None, :] - x[cbox][None, :, :]
-    gE = green(op.kernel_id, np.sqrt((dE * dE).sum(axis=2)))          # P x n
-    YK_out = gE * (op.w[cbox] * op.c[cbox])[None, :]
+    YK_out = op.proxy_out(xE, cbox)
     if symmetric:
         YK = np.vstack([YK_near1, YK_out])
-        YS = np.vstack([S[np.ix_(cN, cbox)], np.zeros((proxy_dirs.shape[0], n))])
+        YS = np.vstack([S[np.ix_(cN, cbox)], np.zeros((YK_out.shape[0], n))])
     else:
         YK_near2 = op.kernel_entries(cbox, cN).T
-        YK_in = gE * (op.b[cbox] * op.w[cbox])[None, :]
+        YK_in = op.proxy_in(xE, cbox)
         YK = np.vstack([YK_near1, YK_near2, YK_out, YK_in])
         YS = np.vstack([S[np.ix_(cN, cbox)], S[np.ix_(cbox, cN)].T,
-                        np.zeros((2 * proxy_dirs.shape[0], n))])
+                        np.zeros((YK_out.shape[0] + YK_in.shape[0], n))])
     Y = YK + YS
     m = Y.shape[0]
 

@@ -101,6 +101,19 @@ class Operator:
         idx = np.arange(self.N)
         return self.entries(idx, idx)
 
+    def proxy_out(self, xE, cols) -> np.ndarray:
+        """Outgoing proxy rows Y_{cE,c} (Lemma 3.3 with quadrature weights):
+        G(|x^E_e - x_j|) w_j c_j for proxy points xE (P x d)."""
+        cols = np.asarray(cols, dtype=np.int64)
+        d = xE[:, None, :] - self.x[cols][None, :, :]
+        return green(self.kernel_id, np.sqrt((d * d).sum(axis=2))) * (self.w[cols] * self.c[cols])[None, :]
+
+    def proxy_in(self, xE, cols) -> np.ndarray:
+        """Incoming proxy rows (Y_{c,cE})^T: b_j G(|x_j - x^E_e|) w_j."""
+        cols = np.asarray(cols, dtype=np.int64)
+        d = xE[:, None, :] - self.x[cols][None, :, :]
+        return green(self.kernel_id, np.sqrt((d * d).sum(axis=2))) * (self.b[cols] * self.w[cols])[None, :]
+
     def matvec(self, x: np.ndarray, trans: bool = False, block: int = 512) -> np.ndarray:
         """Direct sum y = A x (or A^T x), row block by row block, FP64."""
         x = np.asarray(x, dtype=np.float64)
