@@ -77,6 +77,7 @@ typedef struct {
                                symmetric and the one-sided proxy matrix Y'_c = [A_{cN,c};
                                Y_{cE,c}] is compressed (Sec. 5; same ID, half the rows);
                                0: always the full Y_c of Eq. (3.3)                        */
+    double wavenumber;      /* kernel_id 2: the wavenumber k of (i/4) H_0^(1)(k r) (> 0)     */
     int ldl;                /* 1 (default): when the symmetric shortcut applies, factor the
                                diagonal blocks B_rr by LDL with 1 x 1 symmetric pivots and
                                keep X only (Y = X^T; Sec. 5); a block whose pivot fails the

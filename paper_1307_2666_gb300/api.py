@@ -24,6 +24,20 @@ def _colmajor(x: torch.Tensor) -> torch.Tensor:
     return x.t().contiguous().t()
 
 
+def _to_real(x: torch.Tensor) -> torch.Tensor:
+    """A complex (N,) or (N, nrhs) tensor as its interleaved real form, the
+    vectors of the real 2 x 2 embedding (2N,) or (2N, nrhs), column-major."""
+    if x.ndim == 1:
+        return torch.view_as_real(x.contiguous()).reshape(-1)
+    return torch.view_as_real(x.t().contiguous()).reshape(x.shape[1], -1).t()
+
+
+def _to_complex(y: torch.Tensor) -> torch.Tensor:
+    if y.ndim == 1:
+        return torch.view_as_complex(y.contiguous().reshape(-1, 2))
+    return torch.view_as_complex(y.t().contiguous().reshape(y.shape[1], -1, 2)).t()
+
+
 def _empty_like_cm(x: torch.Tensor) -> torch.Tensor:
     if x.ndim == 1:
         return torch.empty_like(x)
@@ -39,6 +53,10 @@ class Factorization:
     digits), "df64" (paired FP32) or "fp64".
     graphs: replay the factored-form sweeps from captured CUDA graphs.
     autotune: pick each sublevel's sweep CTA size by timing after factoring.
+    kernel_id 2: the Helmholtz kernel (i/4) H_0^(1)(k r) of Sec. 5, Example 3,
+    with ``wavenumber`` k; a, b, c stay real, vectors are complex (complex128
+    tensors), and the library works on the real 2 x 2 embedding of the
+    complex operator; the transposed operations are the complex adjoints.
     symmetric: compress the one-sided Y'_c when b == c and the weights are
     equal (A symmetric; Sec. 5); False always compresses the full Y_c.
     ldl: with the symmetric shortcut, factor the diagonal blocks by LDL and
@@ -49,7 +67,7 @@ class Factorization:
                  second_kind: bool = True, occupancy: int = 64, proxy_dirs=None, fractional: bool = True,
                  skip_levels: int = 0, proxy_radius: float = 1.5, fp32_tol_floor: float | None = None,
                  root=None, stream=None, direct: str = "tc", graphs: bool = True, autotune: bool = True,
-                 symmetric: bool = True, ldl: bool = True):
+                 symmetric: bool = True, ldl: bool = True, wavenumber: float | None = None):
         dim = (points[0][0] if isinstance(points, (list, tuple)) else points).shape[1]
         opt = _h.hif_options_default(dim)
         opt.leaf_occupancy = int(occupancy)
@@ -63,6 +81,9 @@ class Factorization:
         opt.autotune = 1 if autotune else 0
         opt.symmetric = 1 if symmetric else 0
         opt.ldl = 1 if ldl else 0
+        if wavenumber is not None:
+            opt.wavenumber = float(wavenumber)
+        self.complex = kernel_id == 2
         self._keep = []
         if proxy_dirs is not None:
             pd = np.ascontiguousarray(np.asarray(proxy_dirs.cpu() if hasattr(proxy_dirs, "cpu") else proxy_dirs,
@@ -104,11 +125,21 @@ class Factorization:
         return cls(list(problems), None, None, None, None, kernel_id, eps, **kw)
 
     # -- factored operators ------------------------------------------------
+    def _real_in(self, x):
+        if self.complex:
+            if not torch.is_complex(x):
+                x = x.to(torch.complex128)
+            return _to_real(x.to(torch.complex128))
+        return x
+
+    def _real_out(self, y):
+        return _to_complex(y) if self.complex else y
+
     def _op(self, fn, x):
-        xin = _colmajor(x)
+        xin = _colmajor(self._real_in(x))
         out = _empty_like_cm(xin)
         fn(self.h, xin, out)
-        return out
+        return self._real_out(out)
 
     def solve(self, b):
         return self._op(_h.hif_solve, b)
@@ -123,17 +154,17 @@ class Factorization:
         return self._op(_h.hif_apply_transpose, x)
 
     def matvec(self, x, trans: bool = False):
-        xin = _colmajor(x)
+        xin = _colmajor(self._real_in(x))
         out = _empty_like_cm(xin)
         _h.hif_matvec(self.h, 1 if trans else 0, xin, out)
-        return out
+        return self._real_out(out)
 
     def solve_refined(self, f, trans: bool = False, tol: float = 1e-10, maxit: int = 50, method: str = "ir"):
-        fin = _colmajor(f)
+        fin = _colmajor(self._real_in(f))
         out = _empty_like_cm(fin)
         st, its, rel = _h.hif_solve_refined(self.h, 1 if trans else 0, fin, out, tol, maxit,
                                             0 if method == "ir" else 1)
-        return out, its, rel
+        return self._real_out(out), its, rel
 
     def eliminated_dofs(self, sublevel: int):
         """numpy int32 array of the DOFs eliminated at a sublevel; the index

@@ -165,7 +165,9 @@ struct hif_handle_s {
     hif_options opt{};
     cudaStream_t st = nullptr;
     int elem = 8;
-    hif::DevMem x, w, a, b, c, kself, proxy;
+    hif::DevMem x, w, a, b, c, kself, kself_im, proxy;
+    double wavenumber = 0.0;   // kernel 2
+    int ncomp = 1;             // real DOFs per point (2: real embedding of the complex operator)
     std::vector<double> hx, hw;
     std::vector<std::unique_ptr<hif::Segment>> segs;
     hif::DevMem seg_off, seg_n;
@@ -203,9 +205,12 @@ static GeomDev geom(hif_handle h) {
     g.b = h->b.as<double>();
     g.c = h->c.as<double>();
     g.kself = h->kself.as<double>();
+    g.kself_im = h->ncomp == 2 ? h->kself_im.as<double>() : nullptr;
+    g.wavenumber = h->wavenumber;
     g.N = h->N;
     g.dim = h->dim;
     g.kernel_id = h->kernel_id;
+    g.ncomp = h->ncomp;
     return g;
 }
 
@@ -1445,7 +1450,8 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
             da.seg_off = sg.off;
             da.seg_n = sg.N;
             ProfRange pr(PROF_DIRECT, st, 2.0 * (double)sg.N * sg.N * nrhs, 0.0);
-            HIF_CUDA(launch_direct_general(da, st));
+            if (h->ncomp == 2) HIF_CUDA(launch_direct_helmholtz(da, st));
+            else HIF_CUDA(launch_direct_general(da, st));
         }
     }
 }
@@ -1783,6 +1789,57 @@ hif_status hif_options_default(int dim, hif_options* opt) {
     return HIF_OK;
 }
 
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton's method on the
+// three-term recurrence of the Legendre polynomials).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Self-cell integral of the Helmholtz kernel G(r) = (i/4) H_0^(1)(k r) over
+// the square of side h centred at the singularity (Sec. 5, Example 3, with
+// the quadratures of the volume examples).  The real part is split as
+// -log(r)/(2 pi) (the Laplace kernel, whose integral is in closed form) plus
+// the bounded rest -Y_0(k r)/4 + log(r)/(2 pi); the rest and the imaginary
+// part J_0(k r)/4 are integrated in polar coordinates about the centre,
+// 8 int_0^{pi/4} int_0^{h/(2 cos t)} f(r) r dr dt, by 48 x 48-point
+// Gauss-Legendre rules.  Bessel functions from the C math library.
+static void helmholtz_self(double k, double h, double* re, double* im) {
+    std::vector<double> xg, wg;
+    gauss_legendre(48, xg, wg);
+    double sr = 0.0, si = 0.0;
+    for (size_t a = 0; a < xg.size(); ++a) {
+        const double t = (xg[a] + 1.0) * kPi / 8.0, wt = wg[a] * kPi / 8.0;
+        const double R = 0.5 * h / std::cos(t);
+        for (size_t b = 0; b < xg.size(); ++b) {
+            const double r = 0.5 * (xg[b] + 1.0) * R, wr = 0.5 * wg[b] * R;
+            sr += wt * wr * r * (-0.25 * ::y0(k * r) + std::log(r) / (2.0 * kPi));
+            si += wt * wr * r * (0.25 * ::j0(k * r));
+        }
+    }
+    const double lap = -(h * h / (2.0 * kPi)) * (std::log(h) - 0.5 * std::log(2.0) - 1.5 + 0.25 * kPi);
+    *re = lap + 8.0 * sr;
+    *im = 8.0 * si;
+}
+
 static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id, double eps, const hif_options* opt_in,
                               hif_handle* out) {
     if (!out) return HIF_EINVAL;
@@ -1799,7 +1856,8 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
     }
     if (N > (int64_t)2000000000) return HIF_EINVAL;
     if (opt.dim != 2 && opt.dim != 3) return HIF_EINVAL;
-    if ((opt.dim == 2 && kernel_id != 0) || (opt.dim == 3 && kernel_id != 1)) return HIF_EINVAL;
+    if ((opt.dim == 2 && kernel_id != 0 && kernel_id != 2) || (opt.dim == 3 && kernel_id != 1)) return HIF_EINVAL;
+    if (kernel_id == 2 && !(opt.wavenumber > 0.0 && std::isfinite(opt.wavenumber))) return HIF_EINVAL;
     if (!(eps >= 0.0) || !std::isfinite(eps)) return HIF_EINVAL;
     if (opt.leaf_occupancy < 1 || opt.proxy_points < 1 || !(opt.proxy_radius > 0)) return HIF_EINVAL;
     if (opt.precision != 0 && opt.precision != 1) return HIF_EINVAL;
@@ -1872,12 +1930,51 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
             for (int k = 0; k < d; ++k)
                 if (!std::isfinite(h->hx[d * i + k])) fail(HIF_ENUMERIC, "non-finite point");
         }
+        if (kernel_id == 2) {
+            // complex operator (Sec. 5, Example 3) through its real 2 x 2
+            // embedding: point j carries the real DOFs 2j (real part) and
+            // 2j + 1 (imaginary part); every array is repeated per component,
+            // and from here on the handle works on 2N real DOFs
+            h->ncomp = 2;
+            h->wavenumber = opt.wavenumber;
+            auto rep2 = [](const std::vector<double>& v, int per) {
+                std::vector<double> o(v.size() * 2);
+                const size_t n = v.size() / per;
+                for (size_t i = 0; i < n; ++i)
+                    for (int r = 0; r < 2; ++r)
+                        for (int k = 0; k < per; ++k) o[(2 * i + r) * per + k] = v[i * per + k];
+                return o;
+            };
+            h->hx = rep2(h->hx, d);
+            h->hw = rep2(h->hw, 1);
+            ha = rep2(ha, 1);
+            hbv = rep2(hbv, 1);
+            hc = rep2(hc, 1);
+            N *= 2;
+            h->N = N;
+            for (auto& sp : h->segs) {
+                sp->off *= 2;
+                sp->N *= 2;
+            }
+            for (int q = 0; q < count; ++q) {
+                soff[q] *= 2;
+                sn[q] *= 2;
+            }
+            upload(h->seg_off, soff, st);
+            upload(h->seg_n, sn, st);
+            upload(h->x, h->hx, st);
+            upload(h->w, h->hw, st);
+            upload(h->a, ha, st);
+            upload(h->b, hbv, st);
+            upload(h->c, hc, st);
+        }
         // A = diag(a) + diag(b) K diag(c) with K_ij = G_ij w_j is symmetric
         // when b_i w_j c_j = b_j w_i c_i; tested in the sufficient form b = c
         // and equal weights, problem by problem
         for (auto& sp : h->segs) {
             Segment& sg = *sp;
-            bool sym = opt.symmetric != 0;
+            // (the real embedding of a complex symmetric matrix is not symmetric)
+            bool sym = opt.symmetric != 0 && kernel_id != 2;
             for (int64_t i = sg.off; sym && i < sg.off + sg.N; ++i)
                 sym = hbv[i] == hc[i] && h->hw[i] == h->hw[sg.off];
             sg.sym = sym;
@@ -1898,14 +1995,39 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
                 pd[2 * k + 1] = std::sin(th);
             }
         }
+        if (h->ncomp == 2) {
+            // every proxy direction once per component (rows 2e, 2e + 1)
+            std::vector<double> pd2((size_t)2 * h->P * d);
+            for (int e = 0; e < h->P; ++e)
+                for (int r = 0; r < 2; ++r)
+                    for (int k = 0; k < d; ++k) pd2[((size_t)2 * e + r) * d + k] = pd[(size_t)e * d + k];
+            pd.swap(pd2);
+            h->P *= 2;
+        }
         upload(h->proxy, pd, st);
         h->kself.ensure(sizeof(double) * N);
-        HIF_CUDA(launch_kself(geom(h.get()), h->kself.as<double>(), st));
         std::vector<double> hks(N);
-        HIF_CUDA(cudaMemcpyAsync(hks.data(), h->kself.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        if (h->ncomp == 2) {
+            std::vector<double> ksi(N);
+            double last_w = -1.0, kr = 0.0, ki = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                if (h->hw[i] != last_w) {
+                    helmholtz_self(h->wavenumber, std::sqrt(h->hw[i]), &kr, &ki);
+                    last_w = h->hw[i];
+                }
+                hks[i] = kr;
+                ksi[i] = ki;
+            }
+            upload(h->kself, hks, st);
+            upload(h->kself_im, ksi, st);
+        } else {
+            HIF_CUDA(launch_kself(geom(h.get()), h->kself.as<double>(), st));
+            HIF_CUDA(cudaMemcpyAsync(hks.data(), h->kself.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        }
         HIF_CUDA(cudaStreamSynchronize(st));
         for (auto& sp : h->segs) {
             Segment& sg = *sp;
+            if (h->ncomp == 2) continue;               // no grid convolution for the complex kernel
             detect_grid(h.get(), sg);
             if (!sg.grid) continue;
             const int64_t tsz = d == 2 ? (int64_t)sg.gn * sg.gn : (int64_t)sg.gn * sg.gn * sg.gn;
@@ -1985,6 +2107,10 @@ hif_status hif_adjoint_gradients(hif_handle h, const double* u, const double* la
                                  double* grad_a, double* grad_b, double* grad_c) {
     if (!h || !u || !lam || !grad_a || !grad_b || !grad_c || nrhs < 1 || ld < h->N || nrhs > (1 << 20))
         return HIF_EINVAL;
+    if (h->ncomp != 1) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "hif_adjoint_gradients: real kernels only");
+        return HIF_EINVAL;
+    }
     return guard([&] {
         const int64_t N = h->N;
         const cudaStream_t st = h->st;
@@ -2089,7 +2215,7 @@ hif_status hif_kernel_block(const double* points, int64_t N, int dim, const doub
             dcp = dc.as<int>();
         }
         dk.ensure(sizeof(double) * N);
-        GeomDev g{px.d, pw.d, pa.d, pb.d, pc.d, dk.as<double>(), N, dim, kernel_id};
+        GeomDev g{px.d, pw.d, pa.d, pb.d, pc.d, dk.as<double>(), nullptr, 0.0, N, dim, kernel_id, 1};
         HIF_CUDA(launch_kself(g, dk.as<double>(), st));
         const bool dev_out = is_device_ptr(out);
         double* o = out;

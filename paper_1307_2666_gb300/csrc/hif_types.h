@@ -15,10 +15,13 @@ struct GeomDev {
     const double* a;
     const double* b;
     const double* c;
-    const double* kself;  // exact self-cell integral K_ii
+    const double* kself;  // self-cell integral K_ii (its real part for kernel 2)
+    const double* kself_im; // kernel 2: imaginary part of K_ii
+    double wavenumber;    // kernel 2: k
     int64_t N;
     int dim;
-    int kernel_id;        // 0: -log(r)/(2 pi), 1: 1/(4 pi r)
+    int kernel_id;        // 0: -log(r)/(2 pi), 1: 1/(4 pi r), 2: (i/4) H_0^(1)(k r)
+    int ncomp;            // real DOFs per point: 2 for kernel 2 (real 2 x 2 embedding), else 1
 };
 
 // Schur-complement interaction (SCI) history.  Every box that eliminated

@@ -118,6 +118,83 @@ __global__ void __launch_bounds__(DS_T) direct_general_kernel(DirectArgs a, int 
     }
 }
 
+// Helmholtz kernel (kernel 2) on the real embedding: complex unknowns are the
+// pairs of real DOFs (2p, 2p + 1), vectors interleave real and imaginary
+// parts.  y = A x with A_pq = a_p delta_pq + b_p K_pq c_q, K_pq = G(r_pq) w_q
+// (one-point rule), K_pp the self-cell integral; trans = 1 gives the adjoint
+// A^H x (the transpose of the real embedding).  One thread per complex
+// target, sources staged in shared memory; G is evaluated once per pair and
+// used for every right-hand side.
+constexpr int DH_R = 4;     // right-hand sides per pass
+
+__global__ void __launch_bounds__(DS_T) direct_helmholtz_kernel(DirectArgs a, int r0, int nr) {
+    __shared__ double sx[DS_S * 2];
+    __shared__ double sv[DS_S * DH_R * 2];
+    const GeomDev& g = a.g;
+    const int64_t p_beg = a.seg_off / 2, p_end = (a.seg_off + a.seg_n) / 2;
+    const int64_t p = p_beg + blockIdx.x * (int64_t)DS_T + threadIdx.x;
+    const bool valid = p < p_end;
+    const double conj_sign = a.trans ? -1.0 : 1.0;
+    double xi0 = 0.0, xi1 = 0.0;
+    if (valid) {
+        xi0 = g.x[4 * p];
+        xi1 = g.x[4 * p + 1];
+    }
+    double ar[DH_R], ai[DH_R];
+    for (int c = 0; c < DH_R; ++c) ar[c] = ai[c] = 0.0;
+    for (int64_t q0 = p_beg; q0 < p_end; q0 += DS_S) {
+        const int ns = (int)(p_end - q0 < DS_S ? p_end - q0 : DS_S);
+        __syncthreads();
+        for (int s = threadIdx.x; s < ns; s += DS_T) {
+            const int64_t q = q0 + s;
+            sx[2 * s] = g.x[4 * q];
+            sx[2 * s + 1] = g.x[4 * q + 1];
+            const double sw = a.trans ? g.b[2 * q] : g.w[2 * q] * g.c[2 * q];
+            for (int c = 0; c < DH_R; ++c) {
+                const bool on = c < nr;
+                sv[(s * DH_R + c) * 2] = on ? sw * a.x[2 * q + a.ldx * (r0 + c)] : 0.0;
+                sv[(s * DH_R + c) * 2 + 1] = on ? sw * a.x[2 * q + 1 + a.ldx * (r0 + c)] : 0.0;
+            }
+        }
+        __syncthreads();
+        if (valid) {
+            for (int s = 0; s < ns; ++s) {
+                if (q0 + s == p) continue;
+                const double d0 = xi0 - sx[2 * s], d1 = xi1 - sx[2 * s + 1];
+                double gr, gi;
+                green_helmholtz(g.wavenumber, d0 * d0 + d1 * d1, gr, gi);
+                gi *= conj_sign;
+                for (int c = 0; c < DH_R; ++c) {
+                    const double vr = sv[(s * DH_R + c) * 2], vi = sv[(s * DH_R + c) * 2 + 1];
+                    ar[c] += gr * vr - gi * vi;
+                    ai[c] += gr * vi + gi * vr;
+                }
+            }
+        }
+    }
+    if (valid) {
+        const int64_t e = 2 * p;
+        const double tf = a.trans ? g.c[e] * g.w[e] : g.b[e];
+        const double sr = g.b[e] * g.kself[e] * g.c[e] + g.a[e];
+        const double si = conj_sign * g.b[e] * g.kself_im[e] * g.c[e];
+        for (int c = 0; c < nr; ++c) {
+            const double xr = a.x[e + a.ldx * (r0 + c)], xim = a.x[e + 1 + a.ldx * (r0 + c)];
+            a.y[e + a.ldy * (r0 + c)] = tf * ar[c] + sr * xr - si * xim;
+            a.y[e + 1 + a.ldy * (r0 + c)] = tf * ai[c] + sr * xim + si * xr;
+        }
+    }
+}
+
+cudaError_t launch_direct_helmholtz(const DirectArgs& a, cudaStream_t st) {
+    if (a.seg_n == 0) return cudaSuccess;
+    const int blocks = (int)((a.seg_n / 2 + DS_T - 1) / DS_T);
+    for (int r0 = 0; r0 < a.nrhs; r0 += DH_R) {
+        note_launch();
+        direct_helmholtz_kernel<<<blocks, DS_T, 0, st>>>(a, r0, std::min(DH_R, a.nrhs - r0));
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_direct_general(const DirectArgs& a, cudaStream_t st) {
     if (a.seg_n == 0) return cudaSuccess;
     const int blocks = (int)((a.seg_n + DS_T - 1) / DS_T);

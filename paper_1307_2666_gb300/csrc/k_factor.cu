@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256, CPT == 1 ? 2 : 1) fold_kernel(FoldArgs ar
     T* rb = align_ptr<T>(sp, RC);
     T* rwc = align_ptr<T>(sp, RC);
     int* rid = align_ptr<int>(sp, RC);
+    int* rcm = align_ptr<int>(sp, RC);           // row component (real embedding, kernel 2)
     T* vbuf = align_ptr<T>(sp, 2 * RC);
     T* taub = align_ptr<T>(sp, 2);
     T* CK = align_ptr<T>(sp, (size_t)RC * n);    // the chunk (its kernel part in second-kind mode)
@@ -128,11 +129,13 @@ __global__ void __launch_bounds__(256, CPT == 1 ? 2 : 1) fold_kernel(FoldArgs ar
         __syncthreads();                        // previous chunk's row data and Gram reads done
         for (int q = threadIdx.x; q < ppc; q += NT) {
             const int p = p0 + q;
+            rcm[q] = 0;
             if (q >= np) {
                 rid[q] = -2;
             } else if (p < bx.m_near) {
                 const int i = near[p];
                 rid[q] = i;
+                rcm[q] = args.g.ncomp == 2 ? (i & 1) : 0;
                 rxl[3 * q + 0] = (T)(args.g.x[(int64_t)dim * i + 0] - c0);
                 rxl[3 * q + 1] = (T)(args.g.x[(int64_t)dim * i + 1] - c1);
                 rxl[3 * q + 2] = dim == 3 ? (T)(args.g.x[(int64_t)dim * i + 2] - c2) : T(0);
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(256, CPT == 1 ? 2 : 1) fold_kernel(FoldArgs ar
             } else {
                 const int kx = p - bx.m_near;
                 rid[q] = -1;
+                rcm[q] = args.g.ncomp == 2 ? (kx & 1) : 0;
                 rxl[3 * q + 0] = (T)(bx.radius * args.proxy[dim * kx + 0]);
                 rxl[3 * q + 1] = (T)(bx.radius * args.proxy[dim * kx + 1]);
                 rxl[3 * q + 2] = dim == 3 ? (T)(bx.radius * args.proxy[dim * kx + 2]) : T(0);
@@ -159,7 +163,8 @@ __global__ void __launch_bounds__(256, CPT == 1 ? 2 : 1) fold_kernel(FoldArgs ar
                 for (int pq = 0; pq < ppc; ++pq) {
                     T k1, k2, s1, s2;
                     y_pair<T>(kid, rid[pq], rxl[3 * pq], rxl[3 * pq + 1], rxl[3 * pq + 2], rb[pq], rwc[pq], jid[q],
-                              xj0[q], xj1[q], xj2[q], cwc[q], cb[q], cbw[q], scival, args.sci, k1, k2, s1, s2);
+                              xj0[q], xj1[q], xj2[q], cwc[q], cb[q], cbw[q], scival, args.sci, k1, k2, s1, s2,
+                              rcm[pq], (T)args.g.wavenumber);
                     const int i1 = sym ? pq : 2 * pq;
                     if (grams) {
                         CK[i1 * n + l] = k1;
@@ -804,7 +809,7 @@ static int fold_rc(int cpt, int elem) {
 size_t fold_smem_bytes(int n, int cpt, bool sci, bool R_in_smem, int elem) {
     const size_t rc = fold_rc(cpt, elem);
     size_t b = 0;
-    b += rc * (5 * (size_t)elem + 4) + 64;             // row data
+    b += rc * (5 * (size_t)elem + 8) + 80;             // row data
     b += 2 * rc * elem + 2 * (size_t)elem + 32;        // reflector buffers
     b += rc * (size_t)n * elem * (sci ? 2 : 1) + 32;   // the chunk (K and S parts apart for the Grams)
     if (R_in_smem) b += (size_t)n * (n + 1) / 2 * elem + 16;   // packed upper triangle

@@ -45,10 +45,11 @@ __global__ void big_ygen_kernel(BigArgs a) {
         const int j = cols[l];
         const T cx0 = (T)(a.g.x[(int64_t)dim * j] - c0), cx1 = (T)(a.g.x[(int64_t)dim * j + 1] - c1);
         const T cx2 = dim == 3 ? (T)(a.g.x[(int64_t)dim * j + 2] - c2) : T(0);
-        int rid;
+        int rid, rcomp = 0;
         T rx0, rx1, rx2, rb, rwc;
         if (p < bx.m_near) {
             rid = near[p];
+            if (a.g.ncomp == 2) rcomp = rid & 1;
             rx0 = (T)(a.g.x[(int64_t)dim * rid] - c0);
             rx1 = (T)(a.g.x[(int64_t)dim * rid + 1] - c1);
             rx2 = dim == 3 ? (T)(a.g.x[(int64_t)dim * rid + 2] - c2) : T(0);
@@ -57,6 +58,7 @@ __global__ void big_ygen_kernel(BigArgs a) {
         } else {
             const int kx = p - bx.m_near;
             rid = -1;
+            if (a.g.ncomp == 2) rcomp = kx & 1;
             rx0 = (T)(bx.radius * a.proxy[dim * kx]);
             rx1 = (T)(bx.radius * a.proxy[dim * kx + 1]);
             rx2 = dim == 3 ? (T)(bx.radius * a.proxy[dim * kx + 2]) : T(0);
@@ -65,7 +67,8 @@ __global__ void big_ygen_kernel(BigArgs a) {
         }
         T k1, k2, s1, s2;
         y_pair<T>(a.g.kernel_id, rid, rx0, rx1, rx2, rb, rwc, j, cx0, cx1, cx2, (T)(a.g.w[j] * a.g.c[j]),
-                  (T)a.g.b[j], (T)(a.g.b[j] * a.g.w[j]), scival, a.sci, k1, k2, s1, s2);
+                  (T)a.g.b[j], (T)(a.g.b[j] * a.g.w[j]), scival, a.sci, k1, k2, s1, s2, rcomp,
+                  (T)a.g.wavenumber);
         T* col = YK + m * l;
         if (sym) {
             col[p] = split ? k1 : k1 + s1;

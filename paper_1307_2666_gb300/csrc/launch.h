@@ -222,6 +222,7 @@ struct DirectArgs {
     int64_t seg_n;
 };
 cudaError_t launch_direct_general(const DirectArgs&, cudaStream_t);
+cudaError_t launch_direct_helmholtz(const DirectArgs&, cudaStream_t);
 
 struct GridDirectArgs {     // uniform tensor grid: K depends on the index offset only
     const double* table;    // n^dim entries: G(h |delta|) for delta != 0, K_self / w at 0

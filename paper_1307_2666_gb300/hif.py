@@ -38,6 +38,7 @@ class hif_options(C.Structure):
         ("use_graphs", C.c_int),
         ("autotune", C.c_int),
         ("symmetric", C.c_int),
+        ("wavenumber", C.c_double),
         ("ldl", C.c_int),
     ]
 
