@@ -552,6 +552,73 @@ def run_examples(args):
             fac.close()
 
 
+def run_example3(args):
+    """Rows of the paper's Example 3 tables (Sec. 5): the Lippmann-Schwinger
+    equation for Helmholtz scattering, kernel (i/4) H_0^(1)(k r), a = 1,
+    b = c = k sqrt(omega) with the Gaussian bump omega = exp(-32 |x - x0|^2),
+    kappa = n / 32 wavelengths across the square (32 DOFs per wavelength),
+    factored in FP64 by HIF-IE with and without the Sec. 4.4 modifications
+    (hifx, hif) and by RSF.  One JSON line per (method, eps): |s_L|, t_f, m_f,
+    t_a/s, e_a, e_s (power iteration on the complex operator's real
+    embedding, from a uniform start, stopped at 1e-2) and n_i (GMRES with
+    F^{-1} as right preconditioner to 1e-12 from a complex Gaussian
+    right-hand side)."""
+    import numpy as np
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import hif_inputs as hi
+    import paper_1307_2666_gb300 as P
+    dev = torch.device(f"cuda:{local}")
+    n = args.n if args.n != 1024 else 128
+    pb = hi.helmholtz_problem(n, n / 32.0)
+    T = lambda v: torch.as_tensor(np.ascontiguousarray(v), device=dev)
+    ins = [T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)]
+    v0 = T(hi.uniform_vector(2 * pb.N, 3))
+    f = T(pb.f[:, 0])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0, out
+
+    w = P.Factorization(*ins, 2, 1e-3, wavenumber=pb.k)
+    w.apply(f)
+    w.close()
+    methods = args.methods or "hif,hifx,rsf"
+    for method in methods.split(","):
+        for eps in [float(e) for e in args.eps_list.split(",")]:
+            t_f, fac = timed(lambda: P.Factorization(*ins, 2, eps, wavenumber=pb.k, fractional=method != "rsf",
+                                                     second_kind=method == "hifx"))
+            fac.apply(f)
+            fac.solve(f)
+            t_a = min(timed(lambda: fac.apply(f))[0] for _ in range(3))
+            t_s = min(timed(lambda: fac.solve(f))[0] for _ in range(3))
+            t_e, est = timed(lambda: fac.error_estimates(v0))
+            t_g, (u, n_i, rel) = timed(lambda: fac.solve_refined(f, tol=1e-12, method="gmres"))
+            st = fac.stats()
+            line = {
+                "metric": "Example 3 table row (Lippmann-Schwinger, Helmholtz, Sec. 5)", "method": method,
+                "n": n, "N": pb.N, "kappa": n / 32.0, "k": pb.k, "eps": eps, "second_kind_mode": method == "hifx",
+                "dtype": "f64 (complex through the real 2x2 embedding)", "data": "synthetic",
+                "s_L_real_dofs": st["top_size"], "t_f": t_f, "m_f_gb": st["factor_bytes"] / 1e9, "t_a": t_a,
+                "t_s": t_s, "e_a": est["e_a"], "e_s": est["e_s"], "power_iters": est["iters"], "t_estimates": t_e,
+                "n_i": n_i, "gmres_relres": rel, "t_gmres": t_g, "levels": st["levels"],
+                "sublevels": st["sublevels"],
+            }
+            print(json.dumps(line), flush=True)
+            fac.close()
+
+
 def run_adjoint(args):
     """The adjoint workload: 2D second-kind IE on the n = 256 grid (N = 65,536),
     b = c = 1 + 0.5 phi (seed 1005), eps = 1e-9, FP64 factorization; loss
@@ -654,9 +721,11 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["grid", "batched", "example1", "example2", "adjoint"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "batched", "example1", "example2", "example3", "adjoint"],
+                    default="grid",
                     help="grid: the n x n bench workload (default); batched: independent problems in one handle; "
-                         "example1 / example2: the paper's first- / second-kind table rows (RSF and HIF-IE)")
+                         "example1 / example2: the paper's first- / second-kind table rows (RSF and HIF-IE); "
+                         "example3: the Helmholtz (Lippmann-Schwinger) table rows, n = 128 unless --n is given")
     ap.add_argument("--methods", default=None,
                     help="example workloads: any of rsf, hif (hifie2), hifx (hifie2x); default hif,rsf for "
                          "example1 and hif,hifx,rsf for example2")
@@ -676,6 +745,8 @@ def main():
         run_batched(args)
     elif args.workload in ("example1", "example2"):
         run_examples(args)
+    elif args.workload == "example3":
+        run_example3(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
     else:
