@@ -71,8 +71,11 @@ typedef struct {
     int use_graphs;         /* capture the sweeps of each (operation, nrhs) in a CUDA graph
                                and replay it (default 1)                                   */
     int autotune;           /* time the candidate CTA sizes of every sublevel's sweep after
-                               the factorization and keep the fastest (default 1; the
-                               sweep's arithmetic does not depend on it)                   */
+                               the factorization and keep the fastest (the sweep's
+                               arithmetic does not depend on it); in FP32 factorizations
+                               also time 16 and 32 rows per fold chunk for every box-width
+                               bucket on its first sighting in the process and keep the
+                               faster (default 1)                                         */
     int symmetric;          /* 1 (default): when b == c and all weights are equal, A is
                                symmetric and the one-sided proxy matrix Y'_c = [A_{cN,c};
                                Y_{cE,c}] is compressed (Sec. 5; same ID, half the rows);

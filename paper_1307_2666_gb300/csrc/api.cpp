@@ -13,7 +13,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -44,6 +46,9 @@ struct Err {
     } while (0)
 
 static thread_local char g_last_error[512];
+// rows per fold chunk chosen by the autotuner, per (box width, element size)
+static std::mutex g_fold_rc_mu;
+static std::map<int, int> g_fold_rc;
 static std::atomic<unsigned long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -188,10 +193,33 @@ struct hif_handle_s {
     // CUDA graphs of the sweeps, captured on a stream of the handle's own
     std::vector<hif::SweepGraph> graphs;
     cudaStream_t cap_st = nullptr;
+    // streams forked from st for concurrent launches of one sublevel, and
+    // the fork / join events (created on first use)
+    cudaStream_t aux[8] = {};
+    cudaEvent_t fork = nullptr, join[8] = {};
+    cudaStream_t aux_stream(size_t i) {
+        i %= 8;
+        if (!aux[i] && cudaStreamCreateWithFlags(&aux[i], cudaStreamNonBlocking) != cudaSuccess) aux[i] = nullptr;
+        return aux[i] ? aux[i] : st;
+    }
+    cudaEvent_t fork_ev() {
+        if (!fork) cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        return fork;
+    }
+    cudaEvent_t join_ev(size_t i) {
+        i %= 8;
+        if (!join[i]) cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+        return join[i];
+    }
     ~hif_handle_s() {
         for (auto& g : graphs)
             if (g.exec) cudaGraphExecDestroy(g.exec);
         if (cap_st) cudaStreamDestroy(cap_st);
+        for (auto& s2 : aux)
+            if (s2) cudaStreamDestroy(s2);
+        if (fork) cudaEventDestroy(fork);
+        for (auto& e : join)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -771,7 +799,7 @@ static void run_factor(hif_handle h) {
     std::vector<char> active(N, 1);
     std::vector<int> box_of(N, -1);
     DevMem d_boxes, d_groups, d_cols, d_near, Rws, GKws, GSws, Tws, Wws, Woff, perm_out, k_out;
-    DevMem d_small_boxes, d_small_groups, d_small_sorted;
+    DevMem d_small_boxes, d_small_groups, d_small_sorted, id_counter;
     FactorScratch S;
     BigBuffers big, bigR;
     const int big_id_n = env_int("HIF_BIG_ID", sizeof(T) == 8 ? 128 : 256);
@@ -896,6 +924,12 @@ static void run_factor(hif_handle h) {
         std::stable_sort(small_sorted.begin(), small_sorted.end(),
                          [&](int x, int y) { return bd[x].n < bd[y].n; });
         upload(d_small_sorted, small_sorted, st);
+        // the ID's work items, largest first (a persistent launch takes them in order)
+        std::stable_sort(small_groups.begin(), small_groups.end(), [&](int x, int y) {
+            const double wx = (double)(gd[x].col0 + gd[x].n) * gd[x].n * gd[x].n;
+            const double wy = (double)(gd[y].col0 + gd[y].n) * gd[y].n * gd[y].n;
+            return wx > wy;
+        });
         upload(d_small_groups, small_groups, st);
         Rws.ensure(sizeof(T) * std::max<int64_t>(Roff, 1));
         const bool grams = h->second_kind && any_sci;
@@ -925,8 +959,13 @@ static void run_factor(hif_handle h) {
             fa.GSws = grams ? GSws.p : nullptr;
             {
                 // one launch per width bucket: a thread per column, so the
-                // CTA is the box width rounded up to a warp
+                // CTA is the box width rounded up to a warp.  The buckets of
+                // a sublevel run concurrently on streams forked from the
+                // handle's; the rows per chunk of each one-column-per-thread
+                // bucket are autotuned once per process (and precision, width)
                 ProfRange pr(PROF_FOLD, st, fold_flops, 0.0);
+                struct Bucket { FoldArgs fa; int count, w, cpt, rc; size_t smem; };
+                std::vector<Bucket> buckets;
                 int64_t at = 0;
                 const int widths[] = {32, 64, 96, 128, 160, 192, 224, 256, 512, 1024};
                 for (int w : widths) {
@@ -936,15 +975,69 @@ static void run_factor(hif_handle h) {
                     if (at == b0) continue;
                     const int cpt = fold_cpt(w, (int)sizeof(T));
                     if (cpt == 0) fail(HIF_EINVAL, "box too wide for the fold kernel");
-                    FoldArgs fb = fa;
-                    fb.box_list = d_small_sorted.as<int>() + b0;
-                    size_t smem = fold_smem_bytes(w, cpt, grams, true, sizeof(T));
-                    fb.R_in_smem = smem <= 220 * 1024;
-                    if (!fb.R_in_smem) smem = fold_smem_bytes(w, cpt, grams, false, sizeof(T));
-                    if (smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
-                    HIF_CUDA((launch_fold<T>(fb, (int)(at - b0), cpt == 1 ? w : 256, cpt, smem, st)));
+                    Bucket bk{fa, (int)(at - b0), w, cpt, 0, 0};
+                    bk.fa.box_list = d_small_sorted.as<int>() + b0;
+                    bk.smem = fold_smem_bytes(w, cpt, grams, true, sizeof(T));
+                    bk.fa.R_in_smem = bk.smem <= 220 * 1024;
+                    if (!bk.fa.R_in_smem) bk.smem = fold_smem_bytes(w, cpt, grams, false, sizeof(T));
+                    if (bk.smem > 220 * 1024) fail(HIF_EINVAL, "box too large for the fold kernel");
+                    buckets.push_back(bk);
                 }
                 if (at != (int64_t)small_boxes.size()) fail(HIF_EINVAL, "box too wide for the fold kernel");
+                // autotune (synchronous, first sighting of a bucket only)
+                std::vector<char> done(buckets.size(), 0);
+                for (size_t q = 0; q < buckets.size(); ++q) {
+                    Bucket& bk = buckets[q];
+                    if (bk.cpt != 1) continue;
+                    const int key = bk.w * 16 + (int)sizeof(T);
+                    if (h->opt.autotune && sizeof(T) == 4) {
+                        std::lock_guard<std::mutex> lk(g_fold_rc_mu);
+                        auto it = g_fold_rc.find(key);
+                        if (it != g_fold_rc.end()) { bk.rc = it->second; continue; }
+                    }
+                    // (FP64 keeps 32 rows so that its rounding never depends on a timing)
+                    if (!h->opt.autotune || sizeof(T) == 8) { bk.rc = 32; continue; }
+                    cudaEvent_t e0, e1;
+                    HIF_CUDA(cudaEventCreate(&e0));
+                    HIF_CUDA(cudaEventCreate(&e1));
+                    float t16 = 0.f, t32 = 0.f;
+                    for (int rc : {16, 32}) {
+                        HIF_CUDA(cudaEventRecord(e0, st));
+                        HIF_CUDA((launch_fold<T>(bk.fa, bk.count, bk.w, 1, bk.smem, st, rc)));
+                        HIF_CUDA(cudaEventRecord(e1, st));
+                        HIF_CUDA(cudaEventSynchronize(e1));
+                        HIF_CUDA(cudaEventElapsedTime(rc == 16 ? &t16 : &t32, e0, e1));
+                    }
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    bk.rc = t16 < t32 ? 16 : 32;
+                    // the bucket's R must come from the kept variant
+                    if (bk.rc == 16) HIF_CUDA((launch_fold<T>(bk.fa, bk.count, bk.w, 1, bk.smem, st, 16)));
+                    done[q] = 1;
+                    std::lock_guard<std::mutex> lk(g_fold_rc_mu);
+                    g_fold_rc[key] = bk.rc;
+                }
+                std::vector<size_t> todo;
+                for (size_t q = 0; q < buckets.size(); ++q)
+                    if (!done[q]) todo.push_back(q);
+                if (todo.size() <= 1) {
+                    for (size_t q : todo) {
+                        const Bucket& bk = buckets[q];
+                        HIF_CUDA((launch_fold<T>(bk.fa, bk.count, bk.cpt == 1 ? bk.w : 256, bk.cpt, bk.smem, st,
+                                                 bk.rc)));
+                    }
+                } else {
+                    HIF_CUDA(cudaEventRecord(h->fork_ev(), st));
+                    for (size_t i = 0; i < todo.size(); ++i) {
+                        const Bucket& bk = buckets[todo[i]];
+                        cudaStream_t s2 = h->aux_stream(i);
+                        HIF_CUDA(cudaStreamWaitEvent(s2, h->fork_ev(), 0));
+                        HIF_CUDA((launch_fold<T>(bk.fa, bk.count, bk.cpt == 1 ? bk.w : 256, bk.cpt, bk.smem, s2,
+                                                 bk.rc)));
+                        HIF_CUDA(cudaEventRecord(h->join_ev(i), s2));
+                    }
+                    for (size_t i = 0; i < todo.size(); ++i) HIF_CUDA(cudaStreamWaitEvent(st, h->join_ev(i), 0));
+                }
             }
             if (trace) {
                 HIF_CUDA(cudaStreamSynchronize(st));
@@ -954,6 +1047,9 @@ static void run_factor(hif_handle h) {
             IdArgs ia{};
             ia.groups = d_groups.as<GroupDesc>();
             ia.group_list = d_small_groups.as<int>();
+            ia.nitems = (int)small_groups.size();
+            id_counter.ensure(sizeof(int));
+            ia.next_item = id_counter.as<int>();
             ia.boxes = d_boxes.as<BoxDesc>();
             ia.Rws = Rws.p;
             ia.GKws = grams ? GKws.p : nullptr;
@@ -974,7 +1070,7 @@ static void run_factor(hif_handle h) {
             ia.W_off = Woff.as<int64_t>();
             {
                 ProfRange pr(PROF_ID, st, 0.0, 0.0);     // work added once the ranks are known
-                HIF_CUDA((launch_id<T>(ia, (int)small_groups.size(), ismem, st)));
+                HIF_CUDA((launch_id<T>(ia, (int)small_groups.size(), ismem, h->num_sms, st)));
             }
             if (!rbig_boxes.empty())
                 run_big_id_R<T>(h, bd, gd, rbig_boxes, d_boxes, d_groups, Rws, grams ? GKws.p : nullptr,

@@ -438,10 +438,27 @@ __device__ void cpqr_id(T* W, int rs, int cs, int mrow, int ng, double tol, doub
 
 template <typename T>
 __device__ double group_rho(const T* GKb, const T* GSb, int n, int col0, int ng, T* vec, double* redv);
+template <typename T>
+__device__ void id_group(const IdArgs& args, int gidx);
 
+// Persistent: each CTA takes groups from a work queue (largest first, so the
+// long pivoted QRs start early and the small ones fill in behind them).
 template <typename T>
 __global__ void __launch_bounds__(128) id_kernel(IdArgs args) {
-    const int gidx = args.group_list[blockIdx.x];
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(args.next_item, 1);
+        __syncthreads();
+        const int it = item;
+        __syncthreads();
+        if (it >= args.nitems) break;
+        id_group<T>(args, args.group_list[it]);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ void id_group(const IdArgs& args, const int gidx) {
     const GroupDesc gd = args.groups[gidx];
     const BoxDesc bx = args.boxes[gd.box];
     const int n = bx.n;
@@ -807,7 +824,7 @@ static int fold_rc(int cpt, int elem) {
 }
 
 size_t fold_smem_bytes(int n, int cpt, bool sci, bool R_in_smem, int elem) {
-    const size_t rc = fold_rc(cpt, elem);
+    const size_t rc = fold_rc(cpt, elem);       // the largest rows per chunk of the configuration
     size_t b = 0;
     b += rc * (5 * (size_t)elem + 8) + 80;             // row data
     b += 2 * rc * elem + 2 * (size_t)elem + 32;        // reflector buffers
@@ -835,9 +852,10 @@ static cudaError_t launch_fold_cfg(const FoldArgs& a, int nbox, int threads, siz
 // threads: the launch's largest box width rounded up to a warp (<= 256) for
 // one column per thread, else 256; cpt from fold_cpt of the widest box
 template <typename T>
-cudaError_t launch_fold(const FoldArgs& a, int nbox, int threads, int cpt, size_t smem, cudaStream_t st) {
+cudaError_t launch_fold(const FoldArgs& a, int nbox, int threads, int cpt, size_t smem, cudaStream_t st, int rc) {
     if (nbox == 0) return cudaSuccess;
     if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
+    if (cpt == 1 && rc == 16) return launch_fold_cfg<T, 16, 1>(a, nbox, threads, smem, st);
     if constexpr (sizeof(T) == 4) {
         if (cpt == 1) return launch_fold_cfg<T, 32, 1>(a, nbox, threads, smem, st);
         if (cpt == 2) return launch_fold_cfg<T, 32, 2>(a, nbox, threads, smem, st);
@@ -850,13 +868,21 @@ cudaError_t launch_fold(const FoldArgs& a, int nbox, int threads, int cpt, size_
     return cudaErrorInvalidValue;
 }
 
+// One persistent launch over the sublevel's groups: as many CTAs as fit on
+// the GPU at once (at most one per group).
 template <typename T>
-cudaError_t launch_id(const IdArgs& a, int ngroups, size_t smem, cudaStream_t st) {
+cudaError_t launch_id(const IdArgs& a, int ngroups, size_t smem, int num_sms, cudaStream_t st) {
     if (ngroups == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, id_kernel<T>, 128, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(ngroups, std::max(per_sm, 1) * std::max(num_sms, 1)));
+    e = cudaMemsetAsync(a.next_item, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
     note_launch();
-    id_kernel<T><<<ngroups, 128, smem, st>>>(a);
+    id_kernel<T><<<grid, 128, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -893,10 +919,10 @@ template cudaError_t launch_gram_tol<double>(const GramTolArgs&, int, int, cudaS
 template cudaError_t launch_gram_tol<float>(const GramTolArgs&, int, int, cudaStream_t);
 template cudaError_t launch_r_colmajor<double>(const void*, int, void*, cudaStream_t);
 template cudaError_t launch_r_colmajor<float>(const void*, int, void*, cudaStream_t);
-template cudaError_t launch_fold<double>(const FoldArgs&, int, int, int, size_t, cudaStream_t);
-template cudaError_t launch_fold<float>(const FoldArgs&, int, int, int, size_t, cudaStream_t);
-template cudaError_t launch_id<double>(const IdArgs&, int, size_t, cudaStream_t);
-template cudaError_t launch_id<float>(const IdArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_fold<double>(const FoldArgs&, int, int, int, size_t, cudaStream_t, int);
+template cudaError_t launch_fold<float>(const FoldArgs&, int, int, int, size_t, cudaStream_t, int);
+template cudaError_t launch_id<double>(const IdArgs&, int, size_t, int, cudaStream_t);
+template cudaError_t launch_id<float>(const IdArgs&, int, size_t, int, cudaStream_t);
 template cudaError_t launch_elim<double>(const ElimArgs&, int, cudaStream_t);
 template cudaError_t launch_elim<float>(const ElimArgs&, int, cudaStream_t);
 

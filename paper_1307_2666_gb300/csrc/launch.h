@@ -29,7 +29,9 @@ struct FoldArgs {
 
 struct IdArgs {
     const GroupDesc* groups;
-    const int* group_list;    // groups handled by this launch (blockIdx.x -> group)
+    const int* group_list;    // work items of this launch, largest first
+    int nitems;               // entries of group_list
+    int* next_item;           // work-queue counter (zero at launch)
     const BoxDesc* boxes;
     const void* Rws;
     const void* GKws;
@@ -195,8 +197,8 @@ template <typename T> cudaError_t launch_r_colmajor(const void* R, int n, void* 
 // columns per thread of the fold kernel for a box of n columns (0: too wide)
 int fold_cpt(int n, int elem);
 template <typename T>
-cudaError_t launch_fold(const FoldArgs&, int nbox, int threads, int cpt, size_t smem, cudaStream_t);
-template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t smem, cudaStream_t);
+cudaError_t launch_fold(const FoldArgs&, int nbox, int threads, int cpt, size_t smem, cudaStream_t, int rc = 0);
+template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t smem, int num_sms, cudaStream_t);
 template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStream_t);
 
 // sweeps
