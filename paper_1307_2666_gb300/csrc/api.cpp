@@ -708,40 +708,55 @@ static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc
                          const double* work);
 
 template <typename T>
-static void eliminate(hif_handle h, SubFactor& sf, ElimPlan& ep, void* sci_pool, int nsub_sci, DevMem& Tws,
-                      FactorScratch& S) {
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        int64_t fac_off = 0, piv_off = 0, ws_off = 0;
+struct Eliminator {
+    hif_handle h;
+    SubFactor& sf;
+    ElimPlan& ep;
+    void* sci_pool;
+    int nsub_sci;
+    DevMem& Tws;
+    FactorScratch& S;
+    int64_t fac_off = 0, piv_off = 0;
+
+    void place_and_launch() {
+        int64_t ws_off = 0;
+        fac_off = piv_off = 0;
         for (size_t q = 0; q < ep.where.size(); ++q) {
             ElimDesc& e = ep.where[q].first ? ep.ed_big[ep.where[q].second] : ep.ed[ep.where[q].second];
             place_box(e, sf.hbox[q], e.k, e.r, e.ldl != 0, fac_off, piv_off, ws_off);
         }
         launch_elims<T>(h, sf, ep.ed, ep.ed_big, ep.eg, ep.skv, ep.rdv, fac_off, piv_off, ws_off, sci_pool, nsub_sci,
                         Tws, S, ep.work);
-        bool any_ldl = false;
-        for (const ElimDesc& e : ep.ed) any_ldl = any_ldl || e.ldl;
-        int stw = 0;
-        if (any_ldl) {
-            HIF_CUDA(cudaMemcpyAsync(&stw, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-            HIF_CUDA(cudaStreamSynchronize(h->st));
-        }
-        if (!(stw & DEV_LDL_FALLBACK) || attempt == 1) {
-            h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
-            for (const ElimDesc& e : ep.ed) h->stats.ldl_boxes += e.ldl ? 1 : 0;
-            if (stw & DEV_LDL_FALLBACK) fail(HIF_ENUMERIC, "LDL fallback repeated");
-            return;
-        }
-        std::vector<int> failed(ep.ed.size());
-        HIF_CUDA(cudaMemcpyAsync(failed.data(), S.ldl_fail.p, sizeof(int) * failed.size(), cudaMemcpyDeviceToHost,
-                                 h->st));
-        stw &= ~(int)DEV_LDL_FALLBACK;
-        HIF_CUDA(cudaMemcpyAsync(h->status.p, &stw, sizeof(int), cudaMemcpyHostToDevice, h->st));
-        HIF_CUDA(cudaStreamSynchronize(h->st));
-        for (size_t q = 0; q < failed.size(); ++q)
-            if (failed[q]) ep.ed[q].ldl = 0;
-        h->stats.ldl_fallbacks += (int64_t)std::count(failed.begin(), failed.end(), 1);
     }
-}
+    // issues the eliminations and returns without waiting for them
+    void launch() { place_and_launch(); }
+    // waits for them; an LDL box whose pivot failed the 1 x 1 test takes the
+    // LU form and the eliminations run once more (every box recomputes its
+    // block from the unchanged inputs, so the others are reproduced exactly)
+    void finish() {
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            bool any_ldl = false;
+            for (const ElimDesc& e : ep.ed) any_ldl = any_ldl || e.ldl;
+            int stw = 0;
+            if (any_ldl) HIF_CUDA(cudaMemcpyAsync(&stw, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+            HIF_CUDA(cudaStreamSynchronize(h->st));
+            if (!(stw & DEV_LDL_FALLBACK)) break;
+            if (attempt == 1) fail(HIF_ENUMERIC, "LDL fallback repeated");
+            std::vector<int> failed(ep.ed.size());
+            HIF_CUDA(cudaMemcpyAsync(failed.data(), S.ldl_fail.p, sizeof(int) * failed.size(),
+                                     cudaMemcpyDeviceToHost, h->st));
+            stw &= ~(int)DEV_LDL_FALLBACK;
+            HIF_CUDA(cudaMemcpyAsync(h->status.p, &stw, sizeof(int), cudaMemcpyHostToDevice, h->st));
+            HIF_CUDA(cudaStreamSynchronize(h->st));
+            for (size_t q = 0; q < failed.size(); ++q)
+                if (failed[q]) ep.ed[q].ldl = 0;
+            h->stats.ldl_fallbacks += (int64_t)std::count(failed.begin(), failed.end(), 1);
+            place_and_launch();
+        }
+        h->stats.factor_bytes += (int64_t)(fac_off * sizeof(T) + piv_off * sizeof(int));
+        for (const ElimDesc& e : ep.ed) h->stats.ldl_boxes += e.ldl ? 1 : 0;
+    }
+};
 
 static void append_plan(SublevelPlan& p, const SublevelPlan& q) {
     const int64_t mo = (int64_t)p.members.size(), no = (int64_t)p.near.size(), go = p.grp_off.back();
@@ -816,18 +831,24 @@ static void run_factor(hif_handle h) {
     double flops = 0, evals = 0;
     const double tol_floor = sizeof(T) == 4 ? h->opt.fp32_tol_floor : 0.0;
 
-    for (size_t tau = 0; tau < nsub; ++tau) {
-        const auto tr0 = std::chrono::steady_clock::now();
-        auto tr_fold = tr0;
-        // ---- index sets of this sublevel, problem by problem, merged
+    // ---- index sets of one sublevel, problem by problem, merged (host work;
+    // the plan of sublevel tau + 1 is made while the GPU eliminates tau)
+    struct Planned {
         SublevelPlan p;
+        std::vector<double> radius;
+        std::vector<int> symv;
+        int kind = -1, ell = -1;
+    };
+    auto plan_sublevel = [&](size_t tau, Planned& P) {
+        SublevelPlan& p = P.p;
+        std::vector<double>& radius = P.radius;
+        std::vector<int>& symv = P.symv;
+        int& kind = P.kind;
+        int& ell = P.ell;
         p.nbox = 0;
         p.box_off.assign(1, 0);
         p.near_off.assign(1, 0);
         p.grp_off.assign(1, 0);
-        std::vector<double> radius;
-        std::vector<int> symv;
-        int kind = -1, ell = -1;
         for (auto& sp : h->segs) {
             Segment& sg = *sp;
             if (tau >= sg.kinds.size()) continue;
@@ -848,6 +869,18 @@ static void run_factor(hif_handle h) {
             radius.insert(radius.end(), ps.nbox, h->opt.proxy_radius * wl);
             symv.insert(symv.end(), ps.nbox, sg.sym ? 1 : 0);
         }
+    };
+    Planned next;
+    if (nsub > 0) plan_sublevel(0, next);
+    for (size_t tau = 0; tau < nsub; ++tau) {
+        const auto tr0 = std::chrono::steady_clock::now();
+        auto tr_fold = tr0;
+        Planned cur = std::move(next);
+        next = Planned();
+        SublevelPlan& p = cur.p;
+        const std::vector<double>& radius = cur.radius;
+        const std::vector<int>& symv = cur.symv;
+        const int kind = cur.kind, ell = cur.ell;
         const int nb = p.nbox;
         const int64_t ngr = p.grp_off[nb];
 
@@ -1195,7 +1228,8 @@ static void run_factor(hif_handle h) {
             h->blk_ptr_h.push_back(static_cast<char*>(pool->p) + sizeof(T) * nbk.sci_off);
             h->blk_k_h.push_back(nbk.k);
         }
-        if (sf->nbox) eliminate<T>(h, *sf, ep, pool->p, (int)tau, Tws, S);
+        Eliminator<T> elim{h, *sf, ep, pool->p, (int)tau, Tws, S};
+        if (sf->nbox) elim.launch();
         h->sci_pools.push_back(std::move(pool));
 
         // ---- state for the next sublevel: active set and SCI membership
@@ -1213,6 +1247,10 @@ static void run_factor(hif_handle h) {
             sci.members.push_back(std::move(mem));
         }
         for (int i : rdv) active[i] = 0;
+        // the next sublevel's plan needs only host state: made while the GPU eliminates
+        if (tau + 1 < nsub) plan_sublevel(tau + 1, next);
+        const auto tr_plan = std::chrono::steady_clock::now();
+        if (sf->nbox) elim.finish();
         HIF_CUDA(cudaStreamSynchronize(st));   // kernels of this sublevel hold the old block table
         HIF_CUDA(cudaMemcpyAsync(h->sci_blk.as<int>() + tau * N, hb.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
         HIF_CUDA(cudaMemcpyAsync(h->sci_loc.as<int>() + tau * N, hl.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
@@ -1223,10 +1261,12 @@ static void run_factor(hif_handle h) {
         if (trace) {
             const auto tr3 = std::chrono::steady_clock::now();
             auto ms = [](auto a0, auto b0) { return std::chrono::duration<double, std::milli>(b0 - a0).count(); };
-            std::fprintf(stderr, "[hif] sub %2zu kind %d level %d boxes %d big %zu maxn %d | plan+launch %.1f ms, id %.1f ms, elim+host %.1f ms\n",
-                         tau, kind, ell, nb, big_boxes.size(), maxbox, ms(tr0, tr1), ms(tr1, tr2), ms(tr2, tr3));
+            std::fprintf(stderr, "[hif] sub %2zu kind %d level %d boxes %d big %zu maxn %d | launch %.1f ms, id %.1f ms, "
+                                 "elim+next plan %.1f ms (plan done at %.1f ms)\n",
+                         tau, kind, ell, nb, big_boxes.size(), maxbox, ms(tr0, tr1), ms(tr1, tr2), ms(tr2, tr3),
+                         ms(tr2, tr_plan));
             if (!small_boxes.empty())
-                std::fprintf(stderr, "[hif]        plan+fold %.1f ms (fold ends at the sync)\n", ms(tr0, tr_fold));
+                std::fprintf(stderr, "[hif]        fold %.1f ms (ends at the sync)\n", ms(tr0, tr_fold));
         }
         h->subs.push_back(std::move(sf));
     }
@@ -1270,7 +1310,9 @@ static void run_factor(hif_handle h) {
         sf->nbox = (int)sf->hbox.size();
         h->stats.top_size = top;
         if (sf->nbox) {
-            eliminate<T>(h, *sf, ep, nullptr, (int)nsub, Tws, S);
+            Eliminator<T> elim{h, *sf, ep, nullptr, (int)nsub, Tws, S};
+            elim.launch();
+            elim.finish();
             HIF_CUDA(cudaStreamSynchronize(st));
             check_status(h);
         }
