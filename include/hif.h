@@ -335,6 +335,37 @@ hif_status hif_id_batched(int count, const double* mats, const int64_t* off,
                           int32_t* k, int32_t* perm, const int64_t* poff,
                           double* T, const int64_t* toff, void* stream);
 
+/* One product of hif_gemm_batched_f32. */
+typedef struct {
+    const float* A;         /* device, column-major                                      */
+    const float* B;         /* device, column-major                                      */
+    float* C;               /* device, column-major, m x n                               */
+    int64_t lda, ldb, ldc;  /* leading dimensions (>= the stored rows, >= 1)             */
+    int32_t m, n, k;        /* op(A) is m x k, op(B) k x n                               */
+    int32_t trans_a;        /* 0: op(A) = A (m x k stored); 1: op(A) = A^T (k x m stored) */
+    int32_t trans_b;        /* 0: op(B) = B (k x n stored); 1: op(B) = B^T (n x k stored) */
+    float alpha;
+    int32_t beta;           /* 0: C = alpha op(A) op(B); 1: C += alpha op(A) op(B)       */
+} hif_gemm_problem;
+
+/*
+ * hif_gemm_batched_f32 -- the dense contractions of the large-box elimination
+ * of the FP32 factorization, exposed for testing and reuse: the products of
+ * Lemma 2.4 (B_sr = A_sr - A_ss T, B_rr = A_rr - T^T B_sr - A_rs T,
+ * B_rs = A_rs - T^T A_ss) and the Schur update -X Z of the skeleton block
+ * (Sec. 3.1, Eq. (3.2)) are products of this form.  For every problem,
+ *     C = beta C + alpha op(A) op(B)
+ * on the tcgen05 tensor cores: FP32 values are split into three BF16 pieces
+ * and the six piece products of weight >= 2^-16 are accumulated in FP32, so
+ * the result has FP32 accuracy (error ~ k 2^-24 max|a| max|b|).  Problems run
+ * concurrently and must not write overlapping C.  `problems` is a host array
+ * (copied by the call); the matrices are device arrays.  Returns HIF_EINVAL
+ * for negative sizes, NULL pointers where a product needs them, leading
+ * dimensions too small or beta not 0 / 1; HIF_ETIMEOUT if a bounded wait of
+ * the kernel ran out (C then undefined).  Synchronizes `stream`.
+ */
+hif_status hif_gemm_batched_f32(int count, const hif_gemm_problem* problems, void* stream);
+
 /*
  * hif_id_batched_noalloc -- the batched interpolative decomposition of
  * hif_id_batched for callers that must not allocate device memory: services

@@ -128,7 +128,7 @@ struct Segment {
 };
 
 struct FactorScratch {
-    DevMem d_ed, d_ed_big, d_eg, ews, piv, ldl_fail;
+    DevMem d_ed, d_ed_big, d_eg, ews, piv, ldl_fail, gemm_probs;
 };
 
 constexpr int KIND_TOP = 3;   // the top blocks, eliminated as boxes without skeletons
@@ -259,6 +259,7 @@ static void check_status(hif_handle h) {
     HIF_CUDA(cudaStreamSynchronize(h->st));
     if (st & DEV_SINGULAR) fail(HIF_ESINGULAR, "zero pivot in an elimination block");
     if (st & DEV_NONFINITE) fail(HIF_ENUMERIC, "non-finite value in the factorization");
+    if (st & DEV_TIMEOUT) fail(HIF_ETIMEOUT, "a bounded wait of a tensor-core kernel ran out");
 }
 
 // Detect whether a problem is a full uniform tensor grid: x = lo + h (idx + 1/2)
@@ -558,6 +559,15 @@ static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc
         ba.perm = sf.perm.as<int>();
         ba.sci_pool = sci_pool;
         ba.status = h->status.as<int>();
+        // HIF_TC_GEMM=1: the products on the tensor cores (hif_gemm_batched_f32).
+        // Off by default: the tensor core's FP32 accumulation of the long
+        // products (K = k or r) is less accurate than the SIMT FMA chains, and
+        // at N = 1M the FP32 factor's refinement contraction went from ~1e-3
+        // to ~4e-3 per step (one refinement step more), for no gain in time.
+        if (env_int("HIF_TC_GEMM", 0)) {
+            S.gemm_probs.ensure(sizeof(TcGemmProb) * 5 * ed_big.size());
+            ba.gemm_probs = S.gemm_probs.p;
+        }
         ProfRange pr(PROF_BIG_ELIM, st, work[1], 0.0);
         HIF_CUDA((big_elim_batch<T>(ba, mxn, mxk, mxr, st)));
     }
@@ -1658,6 +1668,7 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
         const std::vector<double> rn = seg_norms(h, r.as<double>(), nrhs);
         worst = 0;
         for (size_t q = 0; q < rn.size(); ++q) worst = std::max(worst, fn[q] > 0 ? rn[q] / fn[q] : 0.0);
+        if (env_int("HIF_TRACE", 0)) std::fprintf(stderr, "[hif] refinement %d: relative residual %.3e\n", it, worst);
         if (worst <= tol || it >= maxit) break;
         solve_dev(h, trans, r.as<double>(), du.as<double>(), nrhs);
         HIF_CUDA(launch_axpby(N, nrhs, 1.0, du.as<double>(), N, 1.0, u, N, h->st));
@@ -2365,6 +2376,51 @@ hif_status hif_kernel_block(const double* points, int64_t N, int dim, const doub
         if (!dev_out && nr * nc)
             HIF_CUDA(cudaMemcpyAsync(out, o, sizeof(double) * ldo * nc, cudaMemcpyDeviceToHost, st));
         HIF_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+hif_status hif_gemm_batched_f32(int count, const hif_gemm_problem* problems, void* stream) {
+    g_last_error[0] = 0;
+    if (count < 0 || (count > 0 && !problems)) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "hif_gemm_batched_f32: %s",
+                      count < 0 ? "negative count" : "NULL problem array");
+        return HIF_EINVAL;
+    }
+    std::vector<TcGemmProb> hp;
+    int max_m = 0, max_n = 0;
+    for (int i = 0; i < count; ++i) {
+        const hif_gemm_problem& q = problems[i];
+        const int64_t ra = q.trans_a ? q.k : q.m, rb = q.trans_b ? q.n : q.k;
+        const bool bad = q.m < 0 || q.n < 0 || q.k < 0 || (q.beta != 0 && q.beta != 1) ||
+                         (q.m > 0 && q.n > 0 && (!q.C || q.ldc < std::max(1, q.m))) ||
+                         (q.m > 0 && q.n > 0 && q.k > 0 &&
+                          (!q.A || !q.B || q.lda < std::max<int64_t>(1, ra) || q.ldb < std::max<int64_t>(1, rb)));
+        if (bad) {
+            std::snprintf(g_last_error, sizeof(g_last_error), "hif_gemm_batched_f32: problem %d is invalid", i);
+            return HIF_EINVAL;
+        }
+        if (q.m == 0 || q.n == 0 || (q.k == 0 && q.beta == 1)) continue;
+        hp.push_back(TcGemmProb{q.A, q.B, q.C, q.lda, q.ldb, q.ldc, q.m, q.n, q.k, q.trans_a ? 1 : 0,
+                                q.trans_b ? 1 : 0, q.alpha, q.beta});
+        max_m = std::max(max_m, q.m);
+        max_n = std::max(max_n, q.n);
+    }
+    if (hp.empty()) return HIF_OK;
+    return guard([&] {
+        const cudaStream_t st = static_cast<cudaStream_t>(stream);
+        DevMem dp, ds;
+        dp.ensure(sizeof(TcGemmProb) * hp.size());
+        ds.ensure(sizeof(int));
+        HIF_CUDA(cudaMemsetAsync(ds.p, 0, sizeof(int), st));
+        HIF_CUDA(cudaMemcpyAsync(dp.p, hp.data(), sizeof(TcGemmProb) * hp.size(), cudaMemcpyHostToDevice, st));
+        for (size_t off = 0; off < hp.size(); off += 65535) {
+            const int cnt = (int)std::min<size_t>(65535, hp.size() - off);
+            HIF_CUDA(launch_tc_gemm(dp.as<TcGemmProb>() + off, cnt, max_m, max_n, ds.as<int>(), 1, st));
+        }
+        int flag = 0;
+        HIF_CUDA(cudaMemcpyAsync(&flag, ds.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HIF_CUDA(cudaStreamSynchronize(st));
+        if (flag) fail(HIF_ETIMEOUT, "hif_gemm_batched_f32: a bounded wait of the kernel ran out");
     });
 }
 

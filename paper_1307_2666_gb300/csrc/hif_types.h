@@ -95,7 +95,9 @@ struct BoxFac {
 };
 
 // Status word written by kernels that detect trouble (checked by the host).
-enum DevStatus : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADSIZE = 4, DEV_LDL_FALLBACK = 8 };
+enum DevStatus : int {
+    DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADSIZE = 4, DEV_LDL_FALLBACK = 8, DEV_TIMEOUT = 16
+};
 
 // Counts kernel launches made by the library (diagnostic, see hif_kernel_launches).
 void note_launch();

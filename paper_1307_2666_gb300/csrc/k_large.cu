@@ -723,6 +723,37 @@ __global__ void __launch_bounds__(256) be_gemm_kernel(BatchElimArgs a, int op) {
         }
 }
 
+// The same products as tensor-core problems (FP32): one TcGemmProb per box
+// for op, C -= op(A) op(B) (op 4: C = -X Z); a box without work gets m = 0.
+__global__ void be_probs_kernel(BatchElimArgs a, int op, TcGemmProb* out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.nbox) return;
+    const ElimDesc d = a.ed[e];
+    const EBox<float> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    const int64_t ld = Bx.n;
+    float* Arr = Bx.A;
+    float* Asr = Bx.A + r;
+    float* Ars = Bx.A + ld * r;
+    float* Ass = Bx.A + ld * r + r;
+    TcGemmProb p{};
+    p.alpha = -1.f;
+    p.beta = 1;
+    switch (op) {
+        case 0: p = TcGemmProb{Ass, Bx.Tm, Asr, ld, k, ld, k, r, k, 0, 0, -1.f, 1}; break;
+        case 1: p = TcGemmProb{Bx.Tm, Asr, Arr, k, ld, ld, r, r, k, 1, 0, -1.f, 1}; break;
+        case 2: p = TcGemmProb{Ars, Bx.Tm, Arr, ld, k, ld, r, r, k, 0, 0, -1.f, 1}; break;
+        case 3: p = TcGemmProb{Bx.Tm, Ass, Ars, k, ld, ld, r, k, k, 1, 0, -1.f, 1}; break;
+        default:
+            p = TcGemmProb{Asr, Ars, static_cast<float*>(a.sci_pool) + (d.sci_out < 0 ? 0 : d.sci_out), ld, ld, k,
+                           k, k, r, 0, 0, -1.f, 0};
+            if (k == 0 || d.sci_out < 0) p.m = 0;
+            break;
+    }
+    if (k == 0 && op < 4) p.m = 0;
+    out[e] = p;
+}
+
 // blocked LU of B_rr (Lemma 2.1), panel / interchange+TRSM / update stages
 template <typename T>
 __global__ void __launch_bounds__(256) be_panel_kernel(BatchElimArgs a, int j0) {
@@ -964,7 +995,21 @@ cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max
     note_launch();
     be_T_kernel<T><<<nb, 256, 0, st>>>(a);
     const int tk = (max_k + 63) / 64, tr = (max_r + 63) / 64;
-    if (max_k > 0) {
+    // FP32: the products of Lemma 2.4 and the Schur update on the tensor cores
+    TcGemmProb* probs = static_cast<TcGemmProb*>(a.gemm_probs);
+    const bool tcg = sizeof(T) == 4 && probs != nullptr;
+    auto tc_op = [&](int op, int mm, int nn) -> cudaError_t {
+        note_launch();
+        be_probs_kernel<<<(nb + 127) / 128, 128, 0, st>>>(a, op, probs + (int64_t)op * nb);
+        return launch_tc_gemm(probs + (int64_t)op * nb, nb, mm, nn, a.status, DEV_TIMEOUT, st);
+    };
+    if (max_k > 0 && tcg) {
+        cudaError_t e;
+        if ((e = tc_op(0, max_k, max_r)) != cudaSuccess) return e;
+        if ((e = tc_op(1, max_r, max_r)) != cudaSuccess) return e;
+        if ((e = tc_op(2, max_r, max_r)) != cudaSuccess) return e;
+        if ((e = tc_op(3, max_r, max_k)) != cudaSuccess) return e;
+    } else if (max_k > 0) {
         note_launch();
         be_gemm_kernel<T><<<dim3(tk, tr, nb), 256, 0, st>>>(a, 0);
         note_launch();
@@ -988,8 +1033,13 @@ cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max
     if (max_k > 0) {
         note_launch();
         be_tri_kernel<T><<<dim3((2 * max_k + 127) / 128, nb), 128, 0, st>>>(a);
-        note_launch();
-        be_gemm_kernel<T><<<dim3(tk, tk, nb), 256, 0, st>>>(a, 4);
+        if (tcg) {
+            const cudaError_t e = tc_op(4, max_k, max_k);
+            if (e != cudaSuccess) return e;
+        } else {
+            note_launch();
+            be_gemm_kernel<T><<<dim3(tk, tk, nb), 256, 0, st>>>(a, 4);
+        }
     }
     note_launch();
     be_out_kernel<T><<<dim3((unsigned)std::min<int64_t>(((int64_t)max_n * max_n + 255) / 256, 512), nb), 256, 0, st>>>(a);

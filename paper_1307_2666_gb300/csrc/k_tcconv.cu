@@ -29,24 +29,30 @@
 // shared-memory bank conflicts).
 //
 // The block also depends only on |offset| along the slowest axis, so the
-// source lines at -d and +d from the target line share it: one MMA takes
-// both source chunks as the two halves of its B operand (rows ordered digit,
-// half, rhs), which doubles N per instruction.  Every tcgen05.mma with M = 128
-// costs a fixed ~46 cycles up to N ~ 90, so the pair roughly halves the
-// instruction time per source; a line without a mirror partner gets a zero
-// half.
+// source lines at -d and +d from a target line share it, and so do the two
+// target lines i0 and i0 + 1 of a tile with their sources at i0 +- d and
+// i0 + 1 +- d: one MMA takes the four source chunks as the four quarters of
+// its B operand (rows ordered digit, quarter, rhs), so N = 32 per source
+// digit.  An M = 128 MMA reads its 4 KB A operand from shared memory whatever
+// N is, and shared-memory bandwidth (128 B per clock) bounds the MMAs of
+// small N: the four-chunk operand takes the A reads per target line to half
+// those of one line with its mirror pair.  A missing source line reads a
+// zero chunk.
 //
-// CTA roles (256 threads, persistent, one CTA per SM, TMEM 512 columns):
-//   warps 0-3  epilogue: TMEM -> integer class sums -> FP64 y (one thread
-//              per target row),
-//   warp 4     one thread: the MMAs,
-//   warps 5-7  builders of the Hankel operand from mirrored digit rows; one
+// CTA roles (384 threads, persistent, one CTA per SM, TMEM 512 columns):
+//   warps 0-7  epilogue: TMEM -> integer class sums -> FP64 y (one thread
+//              per target row; warps 0-3 the first line, 4-7 the second),
+//   warp 8     one thread: the MMAs,
+//   warps 9-11 builders of the Hankel operand from mirrored digit rows; one
 //              of them also issues the bulk copies of the source digits.
-// Slots (one Hankel operand, a pair of 128-source chunks) flow through a
-// 3-stage shared-memory ring into four 128-column accumulators used in turn,
-// so the MMAs of the next slots proceed while the epilogue drains one.  Every
-// wait is bounded; on time-out the kernel sets *status = 1, drains its own
-// MMAs and copies, frees TMEM and returns.
+// Slots (one Hankel operand, four 128-source chunks) flow through a 2-stage
+// shared-memory ring into two 256-column accumulators used in turn, so the
+// MMAs of the next slot proceed while the epilogue drains one.  The class
+// sums are kept as an int64 for class 0 and int32 for classes 1..7, and
+// every 32 slots the carries of classes 7..1 move up (c = s_k >> 8, s_k -=
+// 256 c, s_(k-1) += c), which keeps their value and their range.  Every wait
+// is bounded; on time-out the kernel sets *status = 1, drains its own MMAs
+// and copies, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cstdlib>
@@ -74,27 +80,32 @@ constexpr int A_SLICE = NBLK * CM;              // bytes
 constexpr int A_BYTES = ST * A_SLICE;
 constexpr int CHUNK = SX * NR * KC * 2;         // one source chunk: (digit, rhs) rows x KC, BF16
 constexpr int TBLK = NR * KC * 2;               // the rows of one digit of one chunk
-constexpr int B_BYTES = 2 * CHUNK;              // the mirrored pair
+constexpr int NL = 2;                           // target lines per tile
+constexpr int NQ = 2 * NL;                      // source chunks per slot (mirror pair per target line)
+constexpr int B_BYTES = NQ * CHUNK;
 constexpr int STAGE = A_BYTES + B_BYTES;
-constexpr int NST = 3;                          // ring depth
-constexpr int ACCB = 128;                       // TMEM columns of one accumulator: (class, half, rhs)
-constexpr int NACC = 4;                         // accumulators, used slot by slot in turn
+constexpr int NST = 2;                          // ring depth
+constexpr int ACCB = 32 * 8;                    // TMEM columns of one accumulator: (class, quarter, rhs)
+constexpr int NACC = 2;                         // accumulators, used slot by slot in turn
 constexpr int ACC = ACCB * NACC;                // TMEM columns allocated
+constexpr int NEPI = 256;                       // epilogue threads
 constexpr int NBUILD = 96;                      // builder threads
+constexpr int NTHR = NEPI + 32 + NBUILD;
+constexpr int CARRY = 32;                       // slots between carry passes of the class sums
 constexpr int NPAIR = ST * NBLK;                // (slice, core matrix) build items per slot
 constexpr long long WAIT_CYCLES = 4000000000LL; // ~2 s at GB300 clocks
 
 static_assert(STAGE % 16 == 0 && A_BYTES % 16 == 0 && TBLK % 16 == 0, "stage alignment");
 static_assert(8 * KC * 128 * 128 <= (1 << 24), "exact FP32 accumulation of one slot");
+// a class sum gains at most 2 columns x 7 pairs x 128 sources x 2^14 per slot
+static_assert(2.0 * 7 * KC * 16384 * CARRY + 2.0 * 16777216 < 2147483647.0, "int32 class sums between carries");
 
-// columns of table digit s: B rows (source digit t, half, rhs) for t below
-// ncols(s) / 16 (s + t <= 7, even t counts: 16-row granularity per half),
-// written to the accumulator columns (class s + t, half, rhs), i.e. from
-// column 16 s on
-__host__ __device__ constexpr int ncols(int s) { return s == 0 ? 128 : s <= 2 ? 96 : s <= 4 ? 64 : 32; }
-__host__ __device__ constexpr int coloff(int s) { return 16 * s; }
-__host__ __device__ constexpr int col_class(int c) { return c / 16; }
-__host__ __device__ constexpr int col_rhs(int c) { return c % 8; }
+// columns of table digit s: B rows (source digit t, quarter, rhs) for t below
+// nt(s) = ncols(s) / 32 (s + t <= 7 except for the odd counts rounded down),
+// written to the accumulator columns (class s + t, quarter, rhs), i.e. from
+// column 32 s on
+__host__ __device__ constexpr int ncols(int s) { return s == 0 ? 256 : s <= 2 ? 192 : s <= 4 ? 128 : 64; }
+__host__ __device__ constexpr int coloff(int s) { return 32 * s; }
 static_assert(coloff(6) + ncols(6) <= ACCB && ncols(0) == ACCB, "column map");
 
 __device__ __forceinline__ int scale_exp(unsigned long long maxbits) {
@@ -227,8 +238,8 @@ struct TcConvArgs {
     int n;
     int64_t lines;              // n^(dim-1)
     int dim;
-    int nb, nc;                 // target tiles / source chunks per line
-    int64_t tiles;
+    int nb, nc;                 // target chunks / source chunks per line
+    int64_t tiles;              // (line pair, target chunk)
     int r0, nr;
     int* status;
     int stall;                  // test of the bounded waits: issue no MMA at all
@@ -237,12 +248,13 @@ struct TcConvArgs {
 namespace {
 
 // The slot sequence of one CTA, identical in every role: its tiles
-// (round-robin), and per tile the offsets d0 = 0..max(i0, n-1-i0) along the
-// slowest axis, the middle source coordinate j1 (3D), the chunk c.
+// (round-robin; a tile is the target lines i0 = 2 p and i0 + 1 along the
+// slowest axis, the middle coordinate i1 in 3D, and one chunk b along the
+// last), and per tile the offsets d0 = 0..dmax along the slowest axis, the
+// middle source coordinate j1 (3D), the chunk c.
 struct Walk {
     int n, dim, nb, nc;
     int64_t tiles, step, tile;
-    int64_t L;
     int b, i0, i1, dmax, d0, j1, c;
     bool ok;
 
@@ -252,12 +264,19 @@ struct Walk {
         if (ok) start();
     }
     __device__ void start() {
-        L = tile / nb;
+        const int64_t p = tile / nb;
         b = (int)(tile % nb);
-        i0 = dim == 2 ? (int)L : (int)(L / n);
-        i1 = dim == 2 ? 0 : (int)(L % n);
+        i0 = 2 * (dim == 2 ? (int)p : (int)(p / n));
+        i1 = dim == 2 ? 0 : (int)(p % n);
         dmax = i0 > n - 1 - i0 ? i0 : n - 1 - i0;
+        if (i0 + 1 < n && i0 + 1 > dmax) dmax = i0 + 1;
         d0 = 0; j1 = 0; c = 0;
+    }
+    // line index (all but the last coordinate) of target line l, -1 if none
+    __device__ int64_t line(int l) const {
+        const int il = i0 + l;
+        if (il >= n) return -1;
+        return dim == 2 ? (int64_t)il : (int64_t)il * n + i1;
     }
     __device__ int64_t slots() const { return (int64_t)(dmax + 1) * (dim == 3 ? n : 1) * nc; }
     __device__ bool tile_end() const { return c == nc - 1 && (dim == 2 || j1 == n - 1) && d0 == dmax; }
@@ -273,10 +292,12 @@ struct Walk {
     }
     // offset index of the line pair (all but the last coordinate)
     __device__ int64_t dl() const { return d0 + (dim == 3 ? (int64_t)n * (i1 > j1 ? i1 - j1 : j1 - i1) : 0); }
-    // source line of half h (h = 0: i0 - d0, h = 1: i0 + d0), -1 if none
-    __device__ int64_t src_line(int h) const {
-        if (h == 1 && d0 == 0) return -1;
-        const int j0 = h == 0 ? i0 - d0 : i0 + d0;
+    // source line of quarter q = 2 l + h (target line i0 + l; h = 0: minus
+    // d0, h = 1: plus d0), -1 if none
+    __device__ int64_t src_line(int q) const {
+        const int il = i0 + (q >> 1), h = q & 1;
+        if (il >= n || (h == 1 && d0 == 0)) return -1;
+        const int j0 = h == 0 ? il - d0 : il + d0;
         if (j0 < 0 || j0 >= n) return -1;
         return dim == 2 ? (int64_t)j0 : (int64_t)j0 * n + j1;
     }
@@ -284,7 +305,7 @@ struct Walk {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
+__global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     Bars* bars = (Bars*)(smem + NST * STAGE);
@@ -299,7 +320,7 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
         }
         for (int i = 0; i < NACC; ++i) {
             tc::mbar_init(&bars->acc_full[i], 1);
-            tc::mbar_init(&bars->acc_empty[i], 128);
+            tc::mbar_init(&bars->acc_empty[i], NEPI);
         }
         tc::mbar_init(&bars->drain, 1);
         bars->abort = 0;
@@ -313,7 +334,7 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
     const int64_t Z0 = 128LL * a.nc - 1, RL = 256LL * a.nc;
     const int64_t zero_chunk = a.lines * a.nc;
 
-    if (warp == 4) {
+    if (warp == NEPI / 32) {
         // ---------------------------------------------------------- issuer
         // (counters are stepped, not divided, and the thread does nothing
         // but wait and issue: its scalar work between MMA batches shows up
@@ -371,13 +392,13 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
             while (!tc::mbar_try_wait(&bars->drain, 0) && clock64() - t0 < WAIT_CYCLES) {}
             if (!ok) *abort = 1;
         }
-    } else if (warp >= 5) {
+    } else if (warp > NEPI / 32) {
         // ------------------------------------------------------- builders
         // each thread owns up to PPT (slice, core matrix) items per slot; the
         // 16 digits of every item are fetched one slot ahead, so the L2
         // latency overlaps the build of the current slot
         constexpr int PPT = (NPAIR + NBUILD - 1) / NBUILD;
-        const int bt = threadIdx.x - 160;
+        const int bt = threadIdx.x - (NEPI + 32);
         uint4 cur[PPT][2], nxt[PPT][2];
         auto fetch = [&](const Walk& v, uint4 (&buf)[PPT][2]) {
             const int64_t dl = v.dl();
@@ -409,17 +430,17 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
             if (gs >= NST && !wait_bounded(&bars->mma_done[st], ph ^ 1, abort)) break;
             unsigned char* a_st = smem + st * STAGE;
             if (bt == 0) {
-                // source digits of both halves, digit block by digit block
-                // into rows (digit, half, rhs); a missing half reads zeros
+                // source digits of the four chunks, digit block by digit
+                // block into rows (digit, quarter, rhs); a missing line reads zeros
                 tc::mbar_arrive_expect_tx(&bars->bfull[st], B_BYTES);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int64_t J = w.src_line(h);
+                for (int q = 0; q < NQ; ++q) {
+                    const int64_t J = w.src_line(q);
                     const int64_t chunk = J >= 0 ? J * a.nc + w.c : zero_chunk;
                     const unsigned char* src = a.XB + chunk * (int64_t)CHUNK;
 #pragma unroll
                     for (int t = 0; t < SX; ++t)
-                        tc::bulk_g2s(a_st + A_BYTES + (2 * t + h) * TBLK, src + t * TBLK, TBLK, &bars->bfull[st]);
+                        tc::bulk_g2s(a_st + A_BYTES + (NQ * t + q) * TBLK, src + t * TBLK, TBLK, &bars->bfull[st]);
                 }
                 ++issued;
             }
@@ -464,13 +485,32 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
                 while (!tc::mbar_try_wait(&bars->bfull[i % NST], (uint32_t)((i / NST) & 1)) &&
                        clock64() - t1 < WAIT_CYCLES) {}
             }
-    } else if (warp < 4) {
+    } else {
         // ------------------------------------------------------- epilogue
-        long long acc[8][NR];
+        // warp w: target line w / 4 of the tile, TMEM lane quarter w % 4
+        const int ln = warp >> 2, quad = warp & 3;
+        long long s0[NR];          // class 0
+        int sk[7][NR];             // classes 1..7
+        auto carry = [&]() {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+            for (int r = 0; r < NR; ++r) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[k][r] = 0;
+                for (int k = 6; k >= 1; --k) {
+                    const int c = sk[k][r] >> 8;
+                    sk[k][r] -= c * 256;
+                    sk[k - 1][r] += c;
+                }
+                const int c = sk[0][r] >> 8;
+                sk[0][r] -= c * 256;
+                s0[r] += c;
+            }
+        };
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            s0[r] = 0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) sk[k][r] = 0;
+        }
         const int eT = scale_exp(*a.tmax);
         int64_t si = 0;                                        // slots drained
         bool ok = true;
@@ -485,37 +525,45 @@ __global__ void __launch_bounds__(256, 1) tc_conv_kernel(TcConvArgs a) {
                     break;
                 }
                 tc::tc_fence_after();
-                const uint32_t tbase = tmem + ACCB * ab + ((uint32_t)(32 * warp) << 16);
-                // 64 columns per TMEM load and wait
+                // class k of this line: columns 32 k + 16 ln + (h, rhs)
+                const uint32_t tbase = tmem + ACCB * ab + 16 * ln + ((uint32_t)(32 * quad) << 16);
 #pragma unroll
-                for (int cb = 0; cb < ACCB / 64; ++cb) {
-                    float v[64];
-                    tc::tmem_ld64(tbase + 64 * cb, v);
+                for (int k = 0; k < 8; ++k) {
+                    float v[16];
+                    tc::tmem_ld16(tbase + 32 * k, v);
 #pragma unroll
-                    for (int i = 0; i < 64; ++i)
-                        acc[col_class(64 * cb + i)][col_rhs(64 * cb + i)] += (long long)__float2int_rn(v[i]);
+                    for (int e = 0; e < 16; ++e) {
+                        if (k == 0) s0[e % 8] += (long long)__float2int_rn(v[e]);
+                        else sk[k - 1][e % 8] += __float2int_rn(v[e]);
+                    }
                 }
                 tc::tc_fence_before();
                 tc::mbar_arrive(&bars->acc_empty[ab]);
+                if (g % CARRY == CARRY - 1) carry();
             }
             if (!ok) break;
-            const int il = TM * w.b + TM - 1 - (32 * warp + lane);
-            if (il < a.n) {
-                const int64_t gpos = w.L * a.n + il;
+            carry();
+            const int il = TM * w.b + TM - 1 - (32 * quad + lane);
+            const int64_t L = w.line(ln);
+            if (il < a.n && L >= 0) {
+                const int64_t gpos = L * a.n + il;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     if (r < a.nr) {
                         double y = 0.0, wt = 1.0 / 72057594037927936.0;          // 2^-56
 #pragma unroll
-                        for (int k = 7; k >= 0; --k, wt *= 256.0) y += (double)acc[k][r] * wt;
+                        for (int k = 7; k >= 1; --k, wt *= 256.0) y += (double)sk[k - 1][r] * wt;
+                        y += (double)s0[r];
                         a.ybuf[gpos + a.N * (a.r0 + r)] = ldexp(y, eT + scale_exp(a.xmax[r]) - 16);
                     }
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
+            for (int r = 0; r < NR; ++r) {
+                s0[r] = 0;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) acc[k][r] = 0;
+                for (int k = 0; k < 7; ++k) sk[k][r] = 0;
+            }
         }
     }
     tc::tc_fence_before();
@@ -629,7 +677,7 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
         t.dim = a.dim;
         t.nb = nb;
         t.nc = nc;
-        t.tiles = lines * nb;
+        t.tiles = (a.dim == 2 ? (int64_t)((a.n + 1) / 2) : (int64_t)((a.n + 1) / 2) * a.n) * nb;
         t.r0 = r0;
         t.nr = nr;
         t.status = status;
@@ -652,7 +700,7 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
             }
         }
         note_launch();
-        tc_conv_kernel<<<grid, 256, smem, st>>>(t);
+        tc_conv_kernel<<<grid, NTHR, smem, st>>>(t);
         if (e1) cudaEventRecord(e1, st);
     }
     grid_finish_kernel_launch(a, N, eb, st);

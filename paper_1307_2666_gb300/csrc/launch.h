@@ -175,6 +175,7 @@ struct BatchElimArgs {
     int* perm;
     void* sci_pool;
     int* status;
+    void* gemm_probs;         // FP32: 5 nbox TcGemmProb of work space for the tensor-core products
 };
 template <typename T> cudaError_t big_elim_batch(const BatchElimArgs&, int max_n, int max_k, int max_r, cudaStream_t);
 
@@ -225,6 +226,25 @@ struct DirectArgs {
 };
 cudaError_t launch_direct_general(const DirectArgs&, cudaStream_t);
 cudaError_t launch_direct_helmholtz(const DirectArgs&, cudaStream_t);
+
+// Batched FP32 products on the tensor cores (k_tcgemm.cu):
+// C = beta C + alpha op(A) op(B), column-major; op(A)[i, l] = tA ? A[l + lda i]
+// : A[i + lda l], op(B)[l, j] = tB ? B[j + ldb l] : B[l + ldb j]; beta 0 or 1.
+struct TcGemmProb {
+    const float* A;
+    const float* B;
+    float* C;
+    int64_t lda, ldb, ldc;
+    int m, n, k;
+    int tA, tB;
+    float alpha;
+    int beta;
+};
+// dprobs: device array of nprob problems; max_m / max_n bound their m / n.
+// `flag` is ORed into *status when a bounded wait of the kernel runs out.
+cudaError_t launch_tc_gemm(const TcGemmProb* dprobs, int nprob, int max_m, int max_n, int* status, int flag,
+                           cudaStream_t st);
+size_t tc_gemm_smem_bytes();
 
 struct GridDirectArgs {     // uniform tensor grid: K depends on the index offset only
     const double* table;    // n^dim entries: G(h |delta|) for delta != 0, K_self / w at 0

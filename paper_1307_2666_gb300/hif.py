@@ -87,6 +87,24 @@ class hif_stats_t(C.Structure):
     ]
 
 
+class hif_gemm_problem(C.Structure):
+    _fields_ = [
+        ("A", C.c_void_p),
+        ("B", C.c_void_p),
+        ("C", C.c_void_p),
+        ("lda", C.c_int64),
+        ("ldb", C.c_int64),
+        ("ldc", C.c_int64),
+        ("m", C.c_int32),
+        ("n", C.c_int32),
+        ("k", C.c_int32),
+        ("trans_a", C.c_int32),
+        ("trans_b", C.c_int32),
+        ("alpha", C.c_float),
+        ("beta", C.c_int32),
+    ]
+
+
 EXPORTS = {
     "hif_options_default": (C.c_int, [C.c_int, C.POINTER(hif_options)]),
     "hif_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -117,6 +135,7 @@ EXPORTS = {
                                    C.c_void_p]),
     "hif_id_batched": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hif_gemm_batched_f32": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
     "hif_id_batched_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -351,3 +370,17 @@ def hif_id_batched_noalloc(mats, off, m, n, tol, k, perm, poff, T, toff, stream=
     return _check(load().hif_id_batched_noalloc(len(m), _ptr(mats), _ptr(off), _ptr(m), _ptr(n), _ptr(tol), _ptr(k),
                                                 _ptr(perm), _ptr(poff), _ptr(T), _ptr(toff), stream),
                   "hif_id_batched_noalloc", allow=(HIF_EINVAL,))
+
+
+def hif_gemm_batched_f32(problems, stream=None):
+    """C = beta C + alpha op(A) op(B) for each problem, FP32 on the tensor
+    cores.  problems: a sequence of dicts with keys A, B, C (device tensors
+    or raw pointers), lda, ldb, ldc, m, n, k, trans_a, trans_b, alpha, beta."""
+    arr = (hif_gemm_problem * max(1, len(problems)))()
+    for i, q in enumerate(problems):
+        raw = lambda x: None if x is None else (x if isinstance(x, int) else _ptr(x).value)
+        arr[i] = hif_gemm_problem(raw(q["A"]), raw(q["B"]), raw(q["C"]), int(q["lda"]), int(q["ldb"]),
+                                  int(q["ldc"]), int(q["m"]), int(q["n"]), int(q["k"]), int(q.get("trans_a", 0)),
+                                  int(q.get("trans_b", 0)), float(q.get("alpha", 1.0)), int(q.get("beta", 0)))
+    return _check(load().hif_gemm_batched_f32(len(problems), C.cast(arr, C.c_void_p), stream),
+                  "hif_gemm_batched_f32", allow=(HIF_EINVAL,))

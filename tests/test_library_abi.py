@@ -64,20 +64,23 @@ def test_ctypes_layouts_match_c_compiler(tmp_path):
     src.write_text('''#include <stdio.h>
 #include <stddef.h>
 #include "hif.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hif_options),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hif_options),
  offsetof(hif_options, proxy_radius),
  offsetof(hif_options, stream), offsetof(hif_options, direct_precision), offsetof(hif_options, autotune),
  offsetof(hif_options, symmetric), offsetof(hif_options, ldl), offsetof(hif_options, wavenumber),
  sizeof(hif_stats_t), offsetof(hif_stats_t, kinds), offsetof(hif_stats_t, flops),
  offsetof(hif_stats_t, top_size), offsetof(hif_stats_t, ldl_fallbacks),
- sizeof(hif_profile_entry), offsetof(hif_profile_entry, bytes)); return 0;}''')
+ sizeof(hif_profile_entry), offsetof(hif_profile_entry, bytes),
+ sizeof(hif_gemm_problem), offsetof(hif_gemm_problem, m), offsetof(hif_gemm_problem, alpha),
+ offsetof(hif_gemm_problem, beta)); return 0;}''')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    O, S, E = hif.hif_options, hif.hif_stats_t, hif.hif_profile_entry
+    O, S, E, G = hif.hif_options, hif.hif_stats_t, hif.hif_profile_entry, hif.hif_gemm_problem
     want = [ctypes.sizeof(O), O.proxy_radius.offset, O.stream.offset, O.direct_precision.offset, O.autotune.offset,
             O.symmetric.offset, O.ldl.offset, O.wavenumber.offset, ctypes.sizeof(S), S.kinds.offset, S.flops.offset, S.top_size.offset,
-            S.ldl_fallbacks.offset, ctypes.sizeof(E), E.bytes.offset]
+            S.ldl_fallbacks.offset, ctypes.sizeof(E), E.bytes.offset, ctypes.sizeof(G), G.m.offset, G.alpha.offset,
+            G.beta.offset]
     assert got == want
 
 
