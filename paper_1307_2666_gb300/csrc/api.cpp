@@ -848,6 +848,7 @@ static void run_factor(hif_handle h) {
         std::vector<double> radius;
         std::vector<int> symv;
         int kind = -1, ell = -1;
+        double ms_partition = 0, ms_near = 0;    // host time (trace)
     };
     auto plan_sublevel = [&](size_t tau, Planned& P) {
         SublevelPlan& p = P.p;
@@ -872,9 +873,14 @@ static void run_factor(hif_handle h) {
                 if (active[i]) act_ids.push_back((int)i);
             for (int i : act_ids) box_of[i] = -1;
             SublevelPlan ps;
+            const auto q0 = std::chrono::steady_clock::now();
             partition(sg.tree, h->hx.data(), kd, s, act_ids, ps, box_of);
+            const auto q1 = std::chrono::steady_clock::now();
             build_near_groups(sg.tree, h->hx.data(), s, h->opt.proxy_radius, h->second_kind, act_ids, active, box_of,
                               sci, ps);
+            const auto q2 = std::chrono::steady_clock::now();
+            P.ms_partition += std::chrono::duration<double, std::milli>(q1 - q0).count();
+            P.ms_near += std::chrono::duration<double, std::milli>(q2 - q1).count();
             append_plan(p, ps);
             radius.insert(radius.end(), ps.nbox, h->opt.proxy_radius * wl);
             symv.insert(symv.end(), ps.nbox, sg.sym ? 1 : 0);
@@ -1277,6 +1283,9 @@ static void run_factor(hif_handle h) {
                          ms(tr2, tr_plan));
             if (!small_boxes.empty())
                 std::fprintf(stderr, "[hif]        fold %.1f ms (ends at the sync)\n", ms(tr0, tr_fold));
+            if (tau + 1 < nsub)
+                std::fprintf(stderr, "[hif]        next plan: partition %.1f ms, near fields and groups %.1f ms\n",
+                             next.ms_partition, next.ms_near);
         }
         h->subs.push_back(std::move(sf));
     }

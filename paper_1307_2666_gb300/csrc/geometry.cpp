@@ -10,6 +10,9 @@
 #include <cmath>
 #include <numeric>
 #include <unordered_map>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace hif {
 
@@ -188,6 +191,36 @@ void partition(const Tree& t, const double* x, int kind, int s, const std::vecto
     out.nbox = (int)out.box_off.size() - 1;
 }
 
+namespace {
+
+// Work arrays of one thread of build_near_groups, reused box after box, and
+// the thread's share of the output (boxes in the order the thread took them).
+struct NearScratch {
+    std::vector<int> nl, blocks;
+    std::vector<int> order, col_pat, pat_data, canon, gid, gfirst;
+    std::vector<int64_t> pat_off;
+    std::vector<uint64_t> pat_hash;
+    // output arena
+    std::vector<int> near, cols, gcol0, gn, gsci;
+};
+
+struct BoxOut {
+    int thread;
+    int64_t near0, near1, cols0, grp0, grp1;
+    int sci;
+};
+
+inline uint64_t hash_ints(const int* p, int64_t n) {
+    uint64_t h = 1469598103934665603ULL;
+    for (int64_t e = 0; e < n; ++e) {
+        h ^= (uint64_t)(uint32_t)p[e];
+        h *= 1099511628211ULL;
+    }
+    return h ^ (uint64_t)n;
+}
+
+}  // namespace
+
 void build_near_groups(const Tree& t, const double* x, int s, double proxy_radius, int second_kind,
                        const std::vector<int>& active_ids, const std::vector<char>& active,
                        const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p) {
@@ -209,21 +242,39 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
         boff[flat + 1]++;
     }
     for (int64_t b = 0; b < nbins; ++b) boff[b + 1] += boff[b];
-    std::vector<int> bins(active_ids.size());
+    // binned copies of the ids, coordinates and boxes, so that the proxy
+    // scans below read contiguous memory
+    std::vector<int> bins(active_ids.size()), bins_box(active_ids.size());
+    std::vector<double> bins_x(active_ids.size() * (size_t)dim);
     {
         std::vector<int64_t> pos(boff.begin(), boff.end() - 1);
-        for (size_t a = 0; a < active_ids.size(); ++a) bins[pos[bin_of[a]]++] = active_ids[a];
+        for (size_t a = 0; a < active_ids.size(); ++a) {
+            const int64_t e = pos[bin_of[a]]++;
+            const int i = active_ids[a];
+            bins[e] = i;
+            bins_box[e] = box_of[i];
+            for (int k = 0; k < dim; ++k) bins_x[(size_t)dim * e + k] = x[(int64_t)dim * i + k];
+        }
     }
 
     const int nb = p.nbox;
-    std::vector<std::vector<int>> near(nb), cols(nb);
-    std::vector<std::vector<int>> gcol0(nb), gn(nb), gsci(nb);
-    std::vector<int> bsci(nb, 0);
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    std::vector<NearScratch> scr(nthr);
+    std::vector<BoxOut> bo(nb);
 
 #pragma omp parallel for schedule(dynamic, 16)
     for (int b = 0; b < nb; ++b) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        NearScratch& S = scr[tid];
         const double* ctr = &p.centers[3 * (size_t)b];
-        std::vector<int>& nl = near[b];
+        std::vector<int>& nl = S.nl;
+        nl.clear();
         // proxy interior
         int lo_b[3] = {0, 0, 0}, hi_b[3] = {0, 0, 0};
         for (int k = 0; k < dim; ++k) {
@@ -236,99 +287,153 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
                     int64_t flat = (int64_t)b0 * s + b1;
                     if (dim == 3) flat = flat * s + b2;
                     for (int64_t e = boff[flat]; e < boff[flat + 1]; ++e) {
-                        const int i = bins[e];
-                        if (box_of[i] == b) continue;
-                        const double* q = x + (int64_t)dim * i;
+                        if (bins_box[e] == b) continue;
+                        const double* q = &bins_x[(size_t)dim * e];
                         double d2 = 0.0;
                         for (int k = 0; k < dim; ++k) {
                             const double dd = q[k] - ctr[k];
                             d2 = d2 + dd * dd;
                         }
-                        if (d2 < R2) nl.push_back(i);
+                        if (d2 < R2) nl.push_back(bins[e]);
                     }
                     if (dim == 2) break;
                 }
-        // SCI-coupled DOFs
-        std::vector<int> blocks;
-        for (int64_t e = p.box_off[b]; e < p.box_off[b + 1]; ++e) {
-            const int j = p.members[e];
-            for (int q = 0; q < nsub; ++q) {
-                const int bid = sci.blk[q][j];
-                if (bid >= 0) blocks.push_back(bid);
+
+        // SCI patterns (Sec. 4.3/4.4): the pattern of column j is the set of
+        // active DOFs outside the box in the past SCI blocks holding j.  It
+        // depends only on j's block ids, so columns are sorted by that tuple
+        // and each distinct tuple's pattern is formed once.
+        const int64_t n0 = p.box_off[b], n1 = p.box_off[b + 1];
+        const int nc = (int)(n1 - n0);
+        auto blk = [&](int l, int q) { return sci.blk[q][p.members[n0 + l]]; };
+        std::vector<int>& order = S.order;
+        order.resize(nc);
+        for (int l = 0; l < nc; ++l) order[l] = l;
+        if (nsub > 0)
+            std::sort(order.begin(), order.end(), [&](int u, int v) {
+                for (int q = 0; q < nsub; ++q) {
+                    const int bu = blk(u, q), bv = blk(v, q);
+                    if (bu != bv) return bu < bv;
+                }
+                return u < v;
+            });
+        S.col_pat.assign(nc, 0);
+        S.pat_data.clear();
+        S.pat_off.assign(1, 0);
+        S.blocks.clear();
+        int npat = 0;
+        for (int e = 0; e < nc; ++e) {
+            const int l = order[e];
+            bool same = e > 0;
+            if (same)
+                for (int q = 0; q < nsub && same; ++q) same = blk(l, q) == blk(order[e - 1], q);
+            if (!same) {
+                const int64_t st = (int64_t)S.pat_data.size();
+                for (int q = 0; q < nsub; ++q) {
+                    const int bid = blk(l, q);
+                    if (bid < 0) continue;
+                    S.blocks.push_back(bid);
+                    for (int i : sci.members[bid])
+                        if (active[i] && box_of[i] != b) S.pat_data.push_back(i);
+                }
+                std::sort(S.pat_data.begin() + st, S.pat_data.end());
+                S.pat_data.erase(std::unique(S.pat_data.begin() + st, S.pat_data.end()), S.pat_data.end());
+                S.pat_off.push_back((int64_t)S.pat_data.size());
+                ++npat;
             }
+            S.col_pat[l] = npat - 1;
         }
-        std::sort(blocks.begin(), blocks.end());
-        blocks.erase(std::unique(blocks.begin(), blocks.end()), blocks.end());
-        for (int bid : blocks)
-            for (int i : sci.members[bid])
-                if (active[i] && box_of[i] != b) nl.push_back(i);
+        // the SCI-coupled DOFs of the near field: the union of all patterns
+        nl.insert(nl.end(), S.pat_data.begin(), S.pat_data.end());
         std::sort(nl.begin(), nl.end());
         nl.erase(std::unique(nl.begin(), nl.end()), nl.end());
 
-        // groups by structural SCI pattern (Sec. 4.4); columns ascending inside
-        const int64_t n0 = p.box_off[b], n1 = p.box_off[b + 1];
-        const int nc = (int)(n1 - n0);
-        std::vector<std::vector<int>> pats(nc);
         bool any = false;
-        for (int l = 0; l < nc; ++l) {
-            const int j = p.members[n0 + l];
-            std::vector<int>& pt = pats[l];
-            for (int q = 0; q < nsub; ++q) {
-                const int bid = sci.blk[q][j];
-                if (bid < 0) continue;
-                for (int i : sci.members[bid])
-                    if (active[i] && box_of[i] != b) pt.push_back(i);
-            }
-            std::sort(pt.begin(), pt.end());
-            pt.erase(std::unique(pt.begin(), pt.end()), pt.end());
-            if (!pt.empty()) any = true;
+        for (int q = 0; q < npat; ++q) any = any || S.pat_off[q + 1] > S.pat_off[q];
+        // patterns with equal content share a canonical id (hash, then exact)
+        S.canon.assign(npat, -1);
+        S.pat_hash.resize(npat);
+        for (int q = 0; q < npat; ++q)
+            S.pat_hash[q] = hash_ints(S.pat_data.data() + S.pat_off[q], S.pat_off[q + 1] - S.pat_off[q]);
+        for (int q = 0; q < npat; ++q) {
+            if (S.canon[q] >= 0) continue;
+            S.canon[q] = q;
+            const int64_t len = S.pat_off[q + 1] - S.pat_off[q];
+            for (int r = q + 1; r < npat; ++r)
+                if (S.canon[r] < 0 && S.pat_hash[r] == S.pat_hash[q] && S.pat_off[r + 1] - S.pat_off[r] == len &&
+                    std::equal(S.pat_data.begin() + S.pat_off[q], S.pat_data.begin() + S.pat_off[q + 1],
+                               S.pat_data.begin() + S.pat_off[r]))
+                    S.canon[r] = q;
         }
-        bsci[b] = any ? 1 : 0;
-        std::vector<int> gid(nc, 0);
+        // groups by pattern, numbered in order of first appearance
+        S.gid.assign(nc, 0);
         int ng = 1;
         if (second_kind) {
-            std::vector<int> first;  // representative column of each group
+            S.gfirst.assign(npat, -1);
+            ng = 0;
             for (int l = 0; l < nc; ++l) {
-                int g = -1;
-                for (size_t q = 0; q < first.size(); ++q)
-                    if (pats[first[q]] == pats[l]) { g = (int)q; break; }
-                if (g < 0) { g = (int)first.size(); first.push_back(l); }
-                gid[l] = g;
+                const int c = S.canon[S.col_pat[l]];
+                if (S.gfirst[c] < 0) S.gfirst[c] = ng++;
+                S.gid[l] = S.gfirst[c];
             }
-            ng = (int)first.size();
         }
-        std::vector<int>& cl = cols[b];
-        for (int g = 0; g < ng; ++g) {
-            gcol0[b].push_back((int)cl.size());
-            bool gs = false;
-            for (int l = 0; l < nc; ++l)
-                if (gid[l] == g) {
-                    cl.push_back(p.members[n0 + l]);
-                    if (!pats[l].empty()) gs = true;
-                }
-            gn[b].push_back((int)cl.size() - gcol0[b].back());
-            gsci[b].push_back(second_kind ? (gs ? 1 : 0) : (any ? 1 : 0));
+        BoxOut& o = bo[b];
+        o.thread = tid;
+        o.sci = any ? 1 : 0;
+        o.near0 = (int64_t)S.near.size();
+        S.near.insert(S.near.end(), nl.begin(), nl.end());
+        o.near1 = (int64_t)S.near.size();
+        o.cols0 = (int64_t)S.cols.size();
+        o.grp0 = (int64_t)S.gn.size();
+        if (ng == 1) {
+            S.gcol0.push_back(0);
+            S.cols.insert(S.cols.end(), p.members.begin() + n0, p.members.begin() + n1);
+            S.gn.push_back(nc);
+            S.gsci.push_back(any ? 1 : 0);
+        } else {
+            // counting sort of the columns by group, ascending inside a group
+            std::vector<int>& gcnt = S.gfirst;
+            gcnt.assign(ng + 1, 0);
+            for (int l = 0; l < nc; ++l) gcnt[S.gid[l] + 1]++;
+            for (int g = 0; g < ng; ++g) gcnt[g + 1] += gcnt[g];
+            const int64_t base = (int64_t)S.cols.size();
+            S.cols.resize(base + nc);
+            for (int g = 0; g < ng; ++g) {
+                S.gcol0.push_back(gcnt[g]);
+                S.gn.push_back(gcnt[g + 1] - gcnt[g]);
+                S.gsci.push_back(0);
+            }
+            for (int l = 0; l < nc; ++l) {
+                const int g = S.gid[l];
+                S.cols[base + gcnt[g]++] = p.members[n0 + l];
+                if (S.pat_off[S.col_pat[l] + 1] > S.pat_off[S.col_pat[l]]) S.gsci[o.grp0 + g] = 1;
+            }
         }
+        o.grp1 = (int64_t)S.gn.size();
     }
     p.near_off.assign(nb + 1, 0);
-    for (int b = 0; b < nb; ++b) p.near_off[b + 1] = p.near_off[b] + (int64_t)near[b].size();
+    for (int b = 0; b < nb; ++b) p.near_off[b + 1] = p.near_off[b] + (bo[b].near1 - bo[b].near0);
     p.near.resize(p.near_off[nb]);
     p.cols.resize(p.members.size());
     p.grp_off.assign(nb + 1, 0);
-    for (int b = 0; b < nb; ++b) p.grp_off[b + 1] = p.grp_off[b] + (int64_t)gn[b].size();
+    for (int b = 0; b < nb; ++b) p.grp_off[b + 1] = p.grp_off[b] + (bo[b].grp1 - bo[b].grp0);
     p.grp_col0.resize(p.grp_off[nb]);
     p.grp_n.resize(p.grp_off[nb]);
     p.grp_sci.resize(p.grp_off[nb]);
-    p.box_sci = bsci;
+    p.box_sci.assign(nb, 0);
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < nb; ++b) {
-        std::copy(near[b].begin(), near[b].end(), p.near.begin() + p.near_off[b]);
-        std::copy(cols[b].begin(), cols[b].end(), p.cols.begin() + p.box_off[b]);
-        for (size_t g = 0; g < gn[b].size(); ++g) {
-            p.grp_col0[p.grp_off[b] + g] = gcol0[b][g];
-            p.grp_n[p.grp_off[b] + g] = gn[b][g];
-            p.grp_sci[p.grp_off[b] + g] = gsci[b][g];
+        const BoxOut& o = bo[b];
+        const NearScratch& S = scr[o.thread];
+        std::copy(S.near.begin() + o.near0, S.near.begin() + o.near1, p.near.begin() + p.near_off[b]);
+        std::copy(S.cols.begin() + o.cols0, S.cols.begin() + o.cols0 + (p.box_off[b + 1] - p.box_off[b]),
+                  p.cols.begin() + p.box_off[b]);
+        for (int64_t g = 0; g < o.grp1 - o.grp0; ++g) {
+            p.grp_col0[p.grp_off[b] + g] = S.gcol0[o.grp0 + g];
+            p.grp_n[p.grp_off[b] + g] = S.gn[o.grp0 + g];
+            p.grp_sci[p.grp_off[b] + g] = S.gsci[o.grp0 + g];
         }
+        p.box_sci[b] = o.sci;
     }
 }
 

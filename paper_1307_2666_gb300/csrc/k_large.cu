@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(256) big_update_kernel(BigArgs a, int j) {
     T* col = W + ld * l;
     const T* v = W + ld * j;
     const T tau = (T)S.tau;
+    double s = 0.0;
     if (tau != T(0)) {
         T w = T(0);
         for (int i = j + 1 + lane; i < G.m; i += 32) w += v[i] * col[i];
@@ -314,12 +315,17 @@ __global__ void __launch_bounds__(256) big_update_kernel(BigArgs a, int j) {
         w = (w + col[j]) * tau;
         __syncwarp();
         if (lane == 0) col[j] -= w;
-        for (int i = j + 1 + lane; i < G.m; i += 32) col[i] -= w * v[i];
-    }
-    double s = 0.0;
-    for (int i = j + 1 + lane; i < G.m; i += 32) {
-        const double c = (double)col[i];
-        s += c * c;
+        // the update and the new norm of rows j+1.. in one pass
+        for (int i = j + 1 + lane; i < G.m; i += 32) {
+            const T c = col[i] - w * v[i];
+            col[i] = c;
+            s += (double)c * (double)c;
+        }
+    } else {
+        for (int i = j + 1 + lane; i < G.m; i += 32) {
+            const double c = (double)col[i];
+            s += c * c;
+        }
     }
     s = warp_sum(s);
     if (lane == 0) a.nrm[G.vec_off + l] = s;
