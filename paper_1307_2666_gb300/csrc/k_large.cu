@@ -307,21 +307,31 @@ __global__ void __launch_bounds__(256) big_update_kernel(BigArgs a, int j) {
     T* col = W + ld * l;
     const T* v = W + ld * j;
     const T tau = (T)S.tau;
-    double s = 0.0;
+    T w = T(0);
     if (tau != T(0)) {
-        T w = T(0);
         for (int i = j + 1 + lane; i < G.m; i += 32) w += v[i] * col[i];
         w = warp_sum(w);
         w = (w + col[j]) * tau;
         __syncwarp();
         if (lane == 0) col[j] -= w;
-        // the update and the new norm of rows j+1.. in one pass
+    }
+    double s = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 factorization: the update and the new norm in one pass, each
+        // lane's share of the norm summed in FP32 (its ~m/32 squares are FP32
+        // data) and the lanes in FP64 -- a warp-wide FP64 FMA in the loop
+        // would bind the step to the FP64 pipe
+        float sf = 0.f;
         for (int i = j + 1 + lane; i < G.m; i += 32) {
-            const T c = col[i] - w * v[i];
-            col[i] = c;
-            s += (double)c * (double)c;
+            const float c = tau != T(0) ? col[i] - w * v[i] : col[i];
+            if (tau != T(0)) col[i] = c;
+            sf = fmaf(c, c, sf);
         }
+        s = (double)sf;
     } else {
+        if (tau != T(0))
+            for (int i = j + 1 + lane; i < G.m; i += 32) col[i] -= w * v[i];
+        // FP64: the new norm in its own pass
         for (int i = j + 1 + lane; i < G.m; i += 32) {
             const double c = (double)col[i];
             s += c * c;
