@@ -685,6 +685,62 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_grid3d(args):
+    """The 3D workload: second-kind volume IE on the unit cube, kernel
+    1/(4 pi r), n = 64 (N = 262,144) unless --n is given, b = c = 1 + 0.5 phi
+    (seed 1008), 16 Gaussian RHS (seed 1009); for each eps of --eps-list the
+    FP32 factorization refined to 1e-10 against the direct sum and, unless
+    --no-compare-fp64, the FP64 factorization refined the same way.  One JSON
+    line per (precision, eps) with the factor and refined-solve times."""
+    import numpy as np
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import hif_inputs as hi
+    import paper_1307_2666_gb300 as P
+    dev = torch.device(f"cuda:{local}")
+    n = args.n if args.n != 1024 else 64
+    nrhs = args.nrhs if args.nrhs != 8 else 16
+    pb = hi.volume_problem(n, 3, smooth_seed=1008, rhs_seed=1009, nrhs=nrhs)
+    T = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev)
+    ins = [T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c)]
+    F = T(pb.f.T).t()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0, out
+
+    w = P.Factorization(*ins, 1, 1e-1, proxy_dirs=pb.proxy, precision="fp32")
+    w.close()
+    precs = ["fp32", "fp64"] if args.compare_fp64 else ["fp32"]
+    for eps in [float(e) for e in args.eps_list.split(",")]:
+        for prec in precs:
+            t_f, fac = timed(lambda: P.Factorization(*ins, 1, eps, proxy_dirs=pb.proxy, precision=prec))
+            t_s, (u, its, rel) = timed(lambda: fac.solve_refined(F, tol=TOL, method="ir"))
+            st = fac.stats()
+            line = {"metric": "3D second-kind volume IE: factor + refined solve to 1e-10", "precision": prec,
+                    "n": n, "N": pb.N, "nrhs": nrhs, "eps": eps, "data": "synthetic",
+                    "config": {"workload": f"3D second-kind volume IE, unit cube, n={n} (N={pb.N}), kernel "
+                                           f"1/(4 pi r), a=1, b=c=1+0.5*phi (seed 1008), {nrhs} Gaussian RHS "
+                                           f"(seed 1009), eps={eps:g}, {prec.upper()} factorization + iterative "
+                                           "refinement to 1e-10 against the direct sum"},
+                    "t_factor_s": t_f, "t_solve_s": t_s, "refine_iters": its, "relres": rel,
+                    "dofs_per_s": pb.N * nrhs / (t_f + t_s), "top_size": st["top_size"],
+                    "factor_bytes": st["factor_bytes"], "levels": st["levels"], "sublevels": st["sublevels"]}
+            print(json.dumps(line), flush=True)
+            fac.close()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -721,11 +777,12 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["grid", "batched", "example1", "example2", "example3", "adjoint"],
+    ap.add_argument("--workload", choices=["grid", "grid3d", "batched", "example1", "example2", "example3", "adjoint"],
                     default="grid",
                     help="grid: the n x n bench workload (default); batched: independent problems in one handle; "
                          "example1 / example2: the paper's first- / second-kind table rows (RSF and HIF-IE); "
-                         "example3: the Helmholtz (Lippmann-Schwinger) table rows, n = 128 unless --n is given")
+                         "example3: the Helmholtz (Lippmann-Schwinger) table rows, n = 128 unless --n is given; "
+                         "grid3d: the 3D n = 64 workload (16 RHS) at each eps of --eps-list, FP32 and FP64")
     ap.add_argument("--methods", default=None,
                     help="example workloads: any of rsf, hif (hifie2), hifx (hifie2x); default hif,rsf for "
                          "example1 and hif,hifx,rsf for example2")
@@ -749,6 +806,8 @@ def main():
         run_example3(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "grid3d":
+        run_grid3d(args)
     else:
         run_gpu(args)
 

@@ -760,9 +760,12 @@ __global__ void be_probs_kernel(BatchElimArgs a, int op, TcGemmProb* out) {
         case 1: p = TcGemmProb{Bx.Tm, Asr, Arr, k, ld, ld, r, r, k, 1, 0, -1.f, 1}; break;
         case 2: p = TcGemmProb{Ars, Bx.Tm, Arr, ld, k, ld, r, r, k, 0, 0, -1.f, 1}; break;
         case 3: p = TcGemmProb{Bx.Tm, Ass, Ars, k, ld, ld, r, k, k, 1, 0, -1.f, 1}; break;
-        default:
-            p = TcGemmProb{Asr, Ars, static_cast<float*>(a.sci_pool) + (d.sci_out < 0 ? 0 : d.sci_out), ld, ld, k,
-                           k, k, r, 0, 0, -1.f, 0};
+        default: {
+            const float* pool = static_cast<const float*>(a.pool);
+            p = TcGemmProb{pool + d.X_out, pool + d.Y_out,
+                           static_cast<float*>(a.sci_pool) + (d.sci_out < 0 ? 0 : d.sci_out), k, r, k, k, k, r, 0,
+                           0, -1.f, 0};
+            }
             if (k == 0 || d.sci_out < 0) p.m = 0;
             break;
     }
@@ -901,55 +904,29 @@ __global__ void __launch_bounds__(256) be_update_kernel(BatchElimArgs a, int j0)
         }
 }
 
-// X = B_sr (DU)^{-1} (thread per row of X) and Z = L^{-1} P B_rs (thread per column)
-template <typename T>
-__global__ void be_tri_kernel(BatchElimArgs a) {
-    const int e = blockIdx.y;
-    const ElimDesc d = a.ed[e];
-    const EBox<T> Bx(a, e);
-    const int k = Bx.k, r = Bx.r;
-    const int64_t ld = Bx.n;
-    const T* U = Bx.A;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < k) {
-        T* X = Bx.A + r;
-        for (int j = 0; j < r; ++j) {
-            T v = X[t + ld * j];
-            for (int l = 0; l < j; ++l) v -= X[t + ld * l] * U[l + ld * j];
-            X[t + ld * j] = v / U[j + ld * j];
-        }
-    } else if (t < 2 * k) {
-        const int c = t - k;
-        T* col = Bx.A + ld * r + ld * c;
-        const int* piv = a.piv + d.piv_out;
-        for (int j = 0; j < r; ++j) {
-            const int p = piv[j];
-            if (p != j) { const T tt = col[j]; col[j] = col[p]; col[p] = tt; }
-        }
-        for (int i = 0; i < r; ++i) {
-            T v = col[i];
-            for (int l = 0; l < i; ++l) v -= U[i + ld * l] * col[l];
-            col[i] = v;
-        }
-    }
-}
+// ---- after the LU of B_rr: the factor outputs by blocked products --------
+//
+// With P B_rr = L D U' (L, U' unit triangular), Lemma 2.4's blocks are
+// X = B_sr (D U')^{-1} = (B_sr U'^{-1}) D^{-1}, Z = L^{-1} P B_rs, the Schur
+// update S = -X Z, and the sweeps keep Y = D^{-1} Z and the unit triangular
+// inverses L^{-1}, U'^{-1}.  The inverses are formed by IB x IB blocks: the
+// diagonal blocks by substitution, then every block column J below the
+// diagonal as X_IJ = -inv(F_II) sum_{K=J..I-1} F_IK X_KJ (F = L, or U'^T for
+// the upper factor), and X, Z, S as tiled products with the inverses.
 
+// D, the unit factors (LU_out: L strictly below, U' strictly above, zero
+// diagonal) and the row permutation P of the pivots
 template <typename T>
-__global__ void be_out_kernel(BatchElimArgs a) {
+__global__ void be_lu_out_kernel(BatchElimArgs a) {
     const int e = blockIdx.y;
     const ElimDesc d = a.ed[e];
     const EBox<T> Bx(a, e);
-    const int k = Bx.k, r = Bx.r;
+    const int r = Bx.r;
     const int64_t ld = Bx.n;
     const T* Arr = Bx.A;
-    const T* Asr = Bx.A + r;
-    const T* Ars = Bx.A + ld * r;
     T* pool = static_cast<T*>(a.pool);
     T* Dv = pool + d.D_out;
     T* LUo = pool + d.LU_out;
-    T* Xo = pool + d.X_out;
-    T* Yo = pool + d.Y_out;
-    T* To = pool + d.T_out;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int64_t q = t0; q < r; q += stride) Dv[q] = Arr[q + ld * q];
@@ -957,28 +934,7 @@ __global__ void be_out_kernel(BatchElimArgs a) {
         const int i = (int)(q % r), j = (int)(q / r);
         LUo[q] = i == j ? T(0) : (i < j ? Arr[i + ld * j] / Arr[i + ld * i] : Arr[i + ld * j]);
     }
-    for (int64_t q = t0; q < (int64_t)k * r; q += stride) {
-        const int i = (int)(q % k), j = (int)(q / k);
-        Xo[q] = Asr[i + ld * j];
-        To[q] = Bx.Tm[q];
-    }
-    for (int64_t q = t0; q < (int64_t)r * k; q += stride) {
-        const int i = (int)(q % r), j = (int)(q / r);
-        Yo[q] = Ars[i + ld * j] / Arr[i + ld * i];
-    }
-}
-
-// unit triangular inverses (thread per column) and LAPACK pivots -> permutation
-template <typename T>
-__global__ void be_inv_kernel(BatchElimArgs a) {
-    const int e = blockIdx.y;
-    const ElimDesc d = a.ed[e];
-    const int r = d.r;
-    T* pool = static_cast<T*>(a.pool);
-    const T* A = pool + d.LU_out;
-    T* out = pool + d.LUi_out;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c == 0) {
+    if (t0 == 0) {
         int* pm = a.perm + d.piv_out;
         const int* piv = a.piv + d.piv_out;
         for (int i = 0; i < r; ++i) pm[i] = i;
@@ -987,19 +943,204 @@ __global__ void be_inv_kernel(BatchElimArgs a) {
             const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
         }
     }
-    if (c >= r) return;
-    const int64_t ld = r;
-    out[c + ld * c] = T(0);
-    for (int i = c + 1; i < r; ++i) {
-        T v = -A[i + ld * c];
-        for (int l = c + 1; l < i; ++l) v -= A[i + ld * l] * out[l + ld * c];
-        out[i + ld * c] = v;
+}
+
+constexpr int IB = 32;   // block size of the triangular inverses
+
+// Unit lower factor F(i, l), i > l: L itself (UP false) or U'^T (UP true);
+// its inverse's entries (i > j) go to LUi_out at (i, j) or, transposed, (j, i).
+template <typename T, bool UP>
+__device__ __forceinline__ T tri_f(const T* F, int64_t r, int i, int l) {
+    return UP ? F[l + r * i] : F[i + r * l];
+}
+template <typename T, bool UP>
+__device__ __forceinline__ T* tri_x(T* X, int64_t r, int i, int j) {
+    return UP ? X + j + r * i : X + i + r * j;
+}
+
+// inverses of the IB x IB diagonal blocks (one warp per block and box)
+template <typename T, bool UP>
+__global__ void be_dinv_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const int r = d.r;
+    const int b0 = blockIdx.x * IB;
+    if (b0 >= r) return;
+    const int nbk = min(IB, r - b0);
+    const T* F = static_cast<const T*>(a.pool) + d.LU_out;
+    T* X = static_cast<T*>(a.pool) + d.LUi_out;
+    __shared__ T Fs[IB][IB + 1];
+    __shared__ T Xs[IB][IB + 1];
+    const int t = threadIdx.x;
+    for (int q = t; q < IB * IB; q += 32) {
+        const int i = UP ? q / IB : q % IB, l = UP ? q % IB : q / IB;   // coalesced either way
+        Fs[i][l] = (i < nbk && l < nbk && i > l) ? tri_f<T, UP>(F, r, b0 + i, b0 + l) : T(0);
     }
-    for (int i = c - 1; i >= 0; --i) {
-        T v = -A[i + ld * c];
-        for (int l = i + 1; l < c; ++l) v -= A[i + ld * l] * out[l + ld * c];
-        out[i + ld * c] = v;
+    __syncthreads();
+    if (t < nbk) {
+        for (int i = 0; i < IB; ++i) Xs[i][t] = T(0);
+        for (int i = t + 1; i < nbk; ++i) {
+            T v = -Fs[i][t];
+            for (int l = t + 1; l < i; ++l) v -= Fs[i][l] * Xs[l][t];
+            Xs[i][t] = v;
+        }
     }
+    __syncthreads();
+    for (int q = t; q < IB * IB; q += 32) {
+        const int i = UP ? q / IB : q % IB, j = UP ? q % IB : q / IB;
+        if (i < nbk && j < nbk && i > j) *tri_x<T, UP>(X, r, b0 + i, b0 + j) = Xs[i][j];
+    }
+    if (t < nbk) X[(b0 + t) + (int64_t)r * (b0 + t)] = T(0);
+}
+
+// block column J of the inverse, blocks I = J+1.. in order (one CTA per
+// block column and box; 256 threads, 4 entries of the 32 x 32 block each)
+template <typename T, bool UP>
+__global__ void __launch_bounds__(256) be_binv_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const int r = d.r;
+    const int nb = (r + IB - 1) / IB;
+    const int J = blockIdx.x;
+    if (J >= nb - 1) return;
+    const T* F = static_cast<const T*>(a.pool) + d.LU_out;
+    T* X = static_cast<T*>(a.pool) + d.LUi_out;
+    __shared__ T Fs[IB][IB + 1];
+    __shared__ T Xs[IB][IB + 1];
+    const int t = threadIdx.x;
+    const int ti = t % IB, tj = t / IB;          // entries (ti, tj + 8 q)
+    for (int I = J + 1; I < nb; ++I) {
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int K = J; K < I; ++K) {
+            __syncthreads();
+            for (int q = t; q < IB * IB; q += 256) {
+                const int i = UP ? q / IB : q % IB, l = UP ? q % IB : q / IB;
+                const int gi = I * IB + i, gl = K * IB + l;
+                Fs[i][l] = (gi < r && gl < r) ? tri_f<T, UP>(F, r, gi, gl) : T(0);
+                // X_KJ (unit diagonal, zero above)
+                const int xk = UP ? q / IB : q % IB, xj = UP ? q % IB : q / IB;
+                const int gk = K * IB + xk, gj = J * IB + xj;
+                T xv = T(0);
+                if (gk < r && gj < r) xv = gk == gj ? T(1) : (gk > gj ? *tri_x<T, UP>(X, r, gk, gj) : T(0));
+                Xs[xk][xj] = xv;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int l = 0; l < IB; ++l) {
+                const T f = Fs[ti][l];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] += f * Xs[l][tj + 8 * q];
+            }
+        }
+        // X_IJ = -(I + S_II) acc, S_II the stored strict part of inv(F_II)
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Xs[ti][tj + 8 * q] = acc[q];
+        for (int q = t; q < IB * IB; q += 256) {
+            const int i = UP ? q / IB : q % IB, l = UP ? q % IB : q / IB;
+            const int gi = I * IB + i, gl = I * IB + l;
+            Fs[i][l] = (i > l && gi < r && gl < r) ? *tri_x<T, UP>(X, r, gi, gl) : T(0);
+        }
+        __syncthreads();
+        const int gi = I * IB + ti;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = tj + 8 * q, gj = J * IB + jj;
+            T v = Xs[ti][jj];
+            for (int l = 0; l < ti; ++l) v += Fs[ti][l] * Xs[l][jj];
+            if (gi < r && gj < r) *tri_x<T, UP>(X, r, gi, gj) = -v;
+        }
+    }
+}
+
+// Tiled products with the inverses (64 x 64 tiles, K by 16):
+//   mode 0: X_out = (B_sr + B_sr S_U) D^{-1}, S_U = U'^{-1} - I (strict upper)
+//   mode 1: Y_out = P B_rs + S_L P B_rs = Z, S_L = L^{-1} - I (strict lower)
+//   mode 2: S = -X Z into the SCI pool
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) be_tri_gemm_kernel(BatchElimArgs a) {
+    __shared__ T As[16][64 + 1];
+    __shared__ T Bs[16][64 + 1];
+    const int e = blockIdx.z;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    const int64_t ld = Bx.n;
+    const T* pool = static_cast<const T*>(a.pool);
+    const T* Si = pool + d.LUi_out;
+    const T* Dv = pool + d.D_out;
+    const int* pm = a.perm + d.piv_out;
+    const T* Asr = Bx.A + r;
+    const T* Ars = Bx.A + ld * r;
+    const int m = MODE == 1 ? r : k, n = MODE == 0 ? r : k;
+    if (MODE == 2 && (k == 0 || d.sci_out < 0)) return;
+    const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+    if (i0 >= m || j0 >= n) return;
+    // K range: l < j (mode 0), l < i (mode 1), all r (mode 2)
+    const int kend = MODE == 0 ? min(r, j0 + 64) : MODE == 1 ? min(r, i0 + 64) : r;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4] = {};
+    for (int l0 = 0; l0 < kend; l0 += 16) {
+        for (int q = threadIdx.x; q < 64 * 16; q += 256) {
+            const int rr = q % 64, l = q / 64;
+            const int i = i0 + rr, kx = l0 + l, jj = j0 + rr;
+            T av = T(0), bv = T(0);
+            if (kx < kend) {
+                if (MODE == 0) {
+                    if (i < m) av = Asr[i + ld * kx];
+                    if (jj < n && kx < jj) bv = Si[kx + (int64_t)r * jj];
+                } else if (MODE == 1) {
+                    if (i < m && kx < i) av = Si[i + (int64_t)r * kx];
+                    if (jj < n) bv = Ars[pm[kx] + ld * jj];
+                } else {
+                    if (i < m) av = pool[d.X_out + i + (int64_t)k * kx];
+                    if (jj < n) bv = pool[d.Y_out + kx + (int64_t)r * jj];
+                }
+            }
+            As[l][rr] = av;
+            Bs[l][rr] = bv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) av[q] = As[l][tx + 16 * q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bv[q] = Bs[l][ty + 16 * q];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+        }
+        __syncthreads();
+    }
+    T* out = static_cast<T*>(a.pool);
+    for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + tx + 16 * p, jj = j0 + ty + 16 * q;
+            if (i >= m || jj >= n) continue;
+            if (MODE == 0) out[d.X_out + i + (int64_t)k * jj] = (Asr[i + ld * jj] + acc[p][q]) / Dv[jj];
+            else if (MODE == 1) out[d.Y_out + i + (int64_t)r * jj] = Ars[pm[i] + ld * jj] + acc[p][q];
+            else static_cast<T*>(a.sci_pool)[d.sci_out + i + (int64_t)k * jj] = -acc[p][q];
+        }
+}
+
+// Y = D^{-1} Z in place, and T
+template <typename T>
+__global__ void be_finish_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    T* pool = static_cast<T*>(a.pool);
+    const T* Dv = pool + d.D_out;
+    T* Yo = pool + d.Y_out;
+    T* To = pool + d.T_out;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t q = t0; q < (int64_t)r * k; q += stride) Yo[q] /= Dv[q % r];
+    for (int64_t q = t0; q < (int64_t)k * r; q += stride) To[q] = Bx.Tm[q];
 }
 
 template <typename T>
@@ -1046,21 +1187,34 @@ cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max
             be_update_kernel<T><<<dim3((rest + 63) / 64, (rest + 63) / 64, nb), 256, 0, st>>>(a, j0);
         }
     }
+    note_launch();
+    be_lu_out_kernel<T><<<dim3((unsigned)std::min<int64_t>(((int64_t)max_r * max_r + 255) / 256, 512), nb), 256, 0, st>>>(a);
+    const int rb = (max_r + IB - 1) / IB;
+    note_launch();
+    be_dinv_kernel<T, false><<<dim3(rb, nb), 32, 0, st>>>(a);
+    note_launch();
+    be_dinv_kernel<T, true><<<dim3(rb, nb), 32, 0, st>>>(a);
+    if (rb > 1) {
+        note_launch();
+        be_binv_kernel<T, false><<<dim3(rb - 1, nb), 256, 0, st>>>(a);
+        note_launch();
+        be_binv_kernel<T, true><<<dim3(rb - 1, nb), 256, 0, st>>>(a);
+    }
     if (max_k > 0) {
         note_launch();
-        be_tri_kernel<T><<<dim3((2 * max_k + 127) / 128, nb), 128, 0, st>>>(a);
+        be_tri_gemm_kernel<T, 0><<<dim3(tk, tr, nb), 256, 0, st>>>(a);
+        note_launch();
+        be_tri_gemm_kernel<T, 1><<<dim3(tr, tk, nb), 256, 0, st>>>(a);
         if (tcg) {
             const cudaError_t e = tc_op(4, max_k, max_k);
             if (e != cudaSuccess) return e;
         } else {
             note_launch();
-            be_gemm_kernel<T><<<dim3(tk, tk, nb), 256, 0, st>>>(a, 4);
+            be_tri_gemm_kernel<T, 2><<<dim3(tk, tk, nb), 256, 0, st>>>(a);
         }
     }
     note_launch();
-    be_out_kernel<T><<<dim3((unsigned)std::min<int64_t>(((int64_t)max_n * max_n + 255) / 256, 512), nb), 256, 0, st>>>(a);
-    note_launch();
-    be_inv_kernel<T><<<dim3((max_r + 127) / 128, nb), 128, 0, st>>>(a);
+    be_finish_kernel<T><<<dim3((unsigned)std::min<int64_t>(((int64_t)max_k * max_r + 255) / 256, 512), nb), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
