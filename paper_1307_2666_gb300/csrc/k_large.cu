@@ -1214,7 +1214,8 @@ cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max
         }
     }
     note_launch();
-    be_finish_kernel<T><<<dim3((unsigned)std::min<int64_t>(((int64_t)max_k * max_r + 255) / 256, 512), nb), 256, 0, st>>>(a);
+    be_finish_kernel<T><<<dim3((unsigned)std::clamp<int64_t>(((int64_t)max_k * max_r + 255) / 256, 1, 512), nb), 256,
+                           0, st>>>(a);
     return cudaGetLastError();
 }
 
