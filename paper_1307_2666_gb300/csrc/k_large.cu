@@ -906,13 +906,15 @@ __global__ void __launch_bounds__(256) be_update_kernel(BatchElimArgs a, int j0)
 
 // ---- after the LU of B_rr: the factor outputs by blocked products --------
 //
-// With P B_rr = L D U' (L, U' unit triangular), Lemma 2.4's blocks are
-// X = B_sr (D U')^{-1} = (B_sr U'^{-1}) D^{-1}, Z = L^{-1} P B_rs, the Schur
-// update S = -X Z, and the sweeps keep Y = D^{-1} Z and the unit triangular
-// inverses L^{-1}, U'^{-1}.  The inverses are formed by IB x IB blocks: the
-// diagonal blocks by substitution, then every block column J below the
-// diagonal as X_IJ = -inv(F_II) sum_{K=J..I-1} F_IK X_KJ (F = L, or U'^T for
-// the upper factor), and X, Z, S as tiled products with the inverses.
+// With P B_rr = L U = L D U' (L, U' unit triangular), Lemma 2.4's blocks
+// are X = B_sr U^{-1}, Z = L^{-1} P B_rs, the Schur update S = -X Z, and the
+// sweeps keep Y = D^{-1} Z and the unit triangular inverses L^{-1}, U'^{-1}.
+// The inverses are formed by IB x IB blocks: the diagonal blocks by
+// substitution, then every block column J below the diagonal as
+// X_IJ = -inv(F_II) sum_{K=J..I-1} F_IK X_KJ (F = L, or U'^T for the upper
+// factor).  X and Z are blocked substitutions (only the IB x IB diagonal
+// blocks enter through their inverses: multiplying by the whole explicit
+// inverse measured a less accurate FP32 factor), S a tiled product.
 
 // D, the unit factors (LU_out: L strictly below, U' strictly above, zero
 // diagonal) and the row permutation P of the pivots
@@ -1053,52 +1055,159 @@ __global__ void __launch_bounds__(256) be_binv_kernel(BatchElimArgs a) {
     }
 }
 
-// Tiled products with the inverses (64 x 64 tiles, K by 16):
-//   mode 0: X_out = (B_sr + B_sr S_U) D^{-1}, S_U = U'^{-1} - I (strict upper)
-//   mode 1: Y_out = P B_rs + S_L P B_rs = Z, S_L = L^{-1} - I (strict lower)
-//   mode 2: S = -X Z into the SCI pool
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) be_tri_gemm_kernel(BatchElimArgs a) {
+// X = B_sr U^{-1} by block columns: X_J = (B_J - sum_{K<J} X_K U_KJ) inv(U_JJ),
+// inv(U_JJ) = (I + S_JJ) D_J^{-1} with S_JJ the stored strict upper part of
+// the diagonal block of U'^{-1}.  One CTA per 64 rows of X and box; thread
+// (tx, ty) holds entries (tx, ty + 4 q), q < 8, of the 64 x 32 block.
+template <typename T>
+__global__ void __launch_bounds__(256) be_trsm_x_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    const int i0 = blockIdx.x * 64;
+    if (i0 >= k) return;
+    const int64_t ld = Bx.n;
+    const T* Arr = Bx.A;
+    const T* Asr = Bx.A + r;
+    T* X = static_cast<T*>(a.pool) + d.X_out;
+    const T* Si = static_cast<const T*>(a.pool) + d.LUi_out;
+    const T* Dv = static_cast<const T*>(a.pool) + d.D_out;
+    __shared__ T Xs[64][IB + 1];
+    __shared__ T Us[IB][IB + 1];
+    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;
+    const int i = i0 + tx;
+    const int rb = (r + IB - 1) / IB;
+    for (int J = 0; J < rb; ++J) {
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = J * IB + ty + 4 * q;
+            acc[q] = (i < k && c < r) ? Asr[i + ld * c] : T(0);
+        }
+        for (int K = 0; K < J; ++K) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < 64 * IB; q += 256) {
+                const int rr = q % 64, l = q / 64, gl = K * IB + l;
+                Xs[rr][l] = (i0 + rr < k && gl < r) ? X[(i0 + rr) + (int64_t)k * gl] : T(0);
+            }
+            for (int q = threadIdx.x; q < IB * IB; q += 256) {
+                const int l = q % IB, c = q / IB, gl = K * IB + l, gc = J * IB + c;
+                Us[l][c] = (gl < r && gc < r) ? Arr[gl + ld * gc] : T(0);
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int l = 0; l < IB; ++l) {
+                const T xv = Xs[tx][l];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] -= xv * Us[l][ty + 4 * q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Xs[tx][ty + 4 * q] = acc[q];
+        for (int q = threadIdx.x; q < IB * IB; q += 256) {
+            const int l = q % IB, c = q / IB, gl = J * IB + l, gc = J * IB + c;
+            Us[l][c] = (l < c && gc < r) ? Si[gl + (int64_t)r * gc] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = ty + 4 * q, gc = J * IB + c;
+            T v = Xs[tx][c];
+            for (int l = 0; l < c; ++l) v += Xs[tx][l] * Us[l][c];
+            if (i < k && gc < r) X[i + (int64_t)k * gc] = v / Dv[gc];
+        }
+    }
+}
+
+// Z = L^{-1} P B_rs by block rows: Z_I = (I + S_II) (PB_I - sum_{K<I} L_IK Z_K),
+// S_II the stored strict lower part of the diagonal block of L^{-1}.  Z goes
+// to Y_out (scaled by D^{-1} later).  One CTA per 64 columns of Z and box;
+// thread (tr, tc) holds entries (tr, tc + 8 q), q < 8, of the 32 x 64 block.
+template <typename T>
+__global__ void __launch_bounds__(256) be_trsm_z_kernel(BatchElimArgs a) {
+    const int e = blockIdx.y;
+    const ElimDesc d = a.ed[e];
+    const EBox<T> Bx(a, e);
+    const int k = Bx.k, r = Bx.r;
+    const int j0 = blockIdx.x * 64;
+    if (j0 >= k) return;
+    const int64_t ld = Bx.n;
+    const T* Arr = Bx.A;
+    const T* Ars = Bx.A + ld * r;
+    T* Z = static_cast<T*>(a.pool) + d.Y_out;
+    const T* Si = static_cast<const T*>(a.pool) + d.LUi_out;
+    const int* pm = a.perm + d.piv_out;
+    __shared__ T Ls[IB][IB + 1];
+    __shared__ T Zs[IB][64 + 1];
+    const int tr = threadIdx.x % IB, tc = threadIdx.x / IB;
+    const int rb = (r + IB - 1) / IB;
+    for (int I = 0; I < rb; ++I) {
+        const int gi = I * IB + tr;
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + tc + 8 * q;
+            acc[q] = (gi < r && j < k) ? Ars[pm[gi] + ld * j] : T(0);
+        }
+        for (int K = 0; K < I; ++K) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < IB * IB; q += 256) {
+                const int rr = q % IB, l = q / IB, g1 = I * IB + rr, g2 = K * IB + l;
+                Ls[rr][l] = (g1 < r && g2 < r) ? Arr[g1 + ld * g2] : T(0);
+            }
+            for (int q = threadIdx.x; q < IB * 64; q += 256) {
+                const int l = q % IB, c = q / IB, gl = K * IB + l;
+                Zs[l][c] = (gl < r && j0 + c < k) ? Z[gl + (int64_t)r * (j0 + c)] : T(0);
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int l = 0; l < IB; ++l) {
+                const T lv = Ls[tr][l];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] -= lv * Zs[l][tc + 8 * q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Zs[tr][tc + 8 * q] = acc[q];
+        for (int q = threadIdx.x; q < IB * IB; q += 256) {
+            const int rr = q % IB, l = q / IB, g1 = I * IB + rr, g2 = I * IB + l;
+            Ls[rr][l] = (rr > l && g1 < r) ? Si[g1 + (int64_t)r * g2] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = tc + 8 * q;
+            T v = Zs[tr][c];
+            for (int l = 0; l < tr; ++l) v += Ls[tr][l] * Zs[l][c];
+            if (gi < r && j0 + c < k) Z[gi + (int64_t)r * (j0 + c)] = v;
+        }
+    }
+}
+
+// S = -X Z into the SCI pool (64 x 64 tiles, K = r by 16)
+template <typename T>
+__global__ void __launch_bounds__(256) be_schur_kernel(BatchElimArgs a) {
     __shared__ T As[16][64 + 1];
     __shared__ T Bs[16][64 + 1];
     const int e = blockIdx.z;
     const ElimDesc d = a.ed[e];
-    const EBox<T> Bx(a, e);
-    const int k = Bx.k, r = Bx.r;
-    const int64_t ld = Bx.n;
-    const T* pool = static_cast<const T*>(a.pool);
-    const T* Si = pool + d.LUi_out;
-    const T* Dv = pool + d.D_out;
-    const int* pm = a.perm + d.piv_out;
-    const T* Asr = Bx.A + r;
-    const T* Ars = Bx.A + ld * r;
-    const int m = MODE == 1 ? r : k, n = MODE == 0 ? r : k;
-    if (MODE == 2 && (k == 0 || d.sci_out < 0)) return;
+    const int k = d.k, r = d.r;
+    if (k == 0 || d.sci_out < 0) return;
     const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
-    if (i0 >= m || j0 >= n) return;
-    // K range: l < j (mode 0), l < i (mode 1), all r (mode 2)
-    const int kend = MODE == 0 ? min(r, j0 + 64) : MODE == 1 ? min(r, i0 + 64) : r;
+    if (i0 >= k || j0 >= k) return;
+    const T* X = static_cast<const T*>(a.pool) + d.X_out;
+    const T* Z = static_cast<const T*>(a.pool) + d.Y_out;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     T acc[4][4] = {};
-    for (int l0 = 0; l0 < kend; l0 += 16) {
+    for (int l0 = 0; l0 < r; l0 += 16) {
         for (int q = threadIdx.x; q < 64 * 16; q += 256) {
             const int rr = q % 64, l = q / 64;
             const int i = i0 + rr, kx = l0 + l, jj = j0 + rr;
-            T av = T(0), bv = T(0);
-            if (kx < kend) {
-                if (MODE == 0) {
-                    if (i < m) av = Asr[i + ld * kx];
-                    if (jj < n && kx < jj) bv = Si[kx + (int64_t)r * jj];
-                } else if (MODE == 1) {
-                    if (i < m && kx < i) av = Si[i + (int64_t)r * kx];
-                    if (jj < n) bv = Ars[pm[kx] + ld * jj];
-                } else {
-                    if (i < m) av = pool[d.X_out + i + (int64_t)k * kx];
-                    if (jj < n) bv = pool[d.Y_out + kx + (int64_t)r * jj];
-                }
-            }
-            As[l][rr] = av;
-            Bs[l][rr] = bv;
+            As[l][rr] = (i < k && kx < r) ? X[i + (int64_t)k * kx] : T(0);
+            Bs[l][rr] = (jj < k && kx < r) ? Z[kx + (int64_t)r * jj] : T(0);
         }
         __syncthreads();
 #pragma unroll
@@ -1115,14 +1224,11 @@ __global__ void __launch_bounds__(256) be_tri_gemm_kernel(BatchElimArgs a) {
         }
         __syncthreads();
     }
-    T* out = static_cast<T*>(a.pool);
+    T* S = static_cast<T*>(a.sci_pool) + d.sci_out;
     for (int p = 0; p < 4; ++p)
         for (int q = 0; q < 4; ++q) {
             const int i = i0 + tx + 16 * p, jj = j0 + ty + 16 * q;
-            if (i >= m || jj >= n) continue;
-            if (MODE == 0) out[d.X_out + i + (int64_t)k * jj] = (Asr[i + ld * jj] + acc[p][q]) / Dv[jj];
-            else if (MODE == 1) out[d.Y_out + i + (int64_t)r * jj] = Ars[pm[i] + ld * jj] + acc[p][q];
-            else static_cast<T*>(a.sci_pool)[d.sci_out + i + (int64_t)k * jj] = -acc[p][q];
+            if (i < k && jj < k) S[i + (int64_t)k * jj] = -acc[p][q];
         }
 }
 
@@ -1202,15 +1308,15 @@ cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max
     }
     if (max_k > 0) {
         note_launch();
-        be_tri_gemm_kernel<T, 0><<<dim3(tk, tr, nb), 256, 0, st>>>(a);
+        be_trsm_x_kernel<T><<<dim3(tk, nb), 256, 0, st>>>(a);
         note_launch();
-        be_tri_gemm_kernel<T, 1><<<dim3(tr, tk, nb), 256, 0, st>>>(a);
+        be_trsm_z_kernel<T><<<dim3(tk, nb), 256, 0, st>>>(a);
         if (tcg) {
             const cudaError_t e = tc_op(4, max_k, max_k);
             if (e != cudaSuccess) return e;
         } else {
             note_launch();
-            be_tri_gemm_kernel<T, 2><<<dim3(tk, tk, nb), 256, 0, st>>>(a);
+            be_schur_kernel<T><<<dim3(tk, tk, nb), 256, 0, st>>>(a);
         }
     }
     note_launch();
