@@ -145,6 +145,12 @@ struct SubFactor {
     DevMem gws_off;
     int64_t gws_units = 0;
     int threads = 256;
+    // boxes of the one-CTA sweep kernel (sboxes) and the wide boxes whose
+    // passes run as stage launches over the whole GPU (wboxes, work space at
+    // wws_off per box in units of k + 2 r, per right-hand side)
+    DevMem sboxes, wboxes, wws_off;
+    int nsmall = 0, nwide = 0, wmax_k = 0, wmax_r = 0, max_kr2_small = 0;
+    int64_t wws_units = 0;
     // algorithmic elements the two passes of one sweep read from the factors
     // (T twice, X or Y once each, one triangle of L^{-1}/U^{-1} or L/U per
     // pass, D) and the box vectors they gather and scatter (sum of k + r)
@@ -1352,12 +1358,27 @@ template <typename T>
 static void sweep_one(hif_handle h, SubFactor& sf, int mode, T* xw, int64_t ldx, int nrhs, int threads,
                       cudaStream_t st) {
     if (!sf.nbox) return;
-    const size_t per_col = (size_t)sf.max_kr2 * sizeof(T);
+    for (int r0 = 0; sf.nwide && r0 < nrhs; r0 += 16) {
+        WideArgs w{};
+        w.boxes = sf.wboxes.as<BoxFac>();
+        w.sk_ids = sf.sk.as<int>();
+        w.rd_ids = sf.rd.as<int>();
+        w.pool = sf.pool.p;
+        w.perm = sf.perm.as<int>();
+        w.x = xw + ldx * r0;
+        w.ldx = ldx;
+        w.nr = std::min(16, nrhs - r0);
+        w.ws = h->sweep_ws.p;
+        w.ws_off = sf.wws_off.as<int64_t>();
+        HIF_CUDA((launch_wide_sweep<T>(w, sf.nwide, sf.wmax_k, sf.wmax_r, mode, st)));
+    }
+    if (!sf.nsmall) return;
+    const size_t per_col = (size_t)sf.max_kr2_small * sizeof(T);
     const int batch = sf.global ? nrhs : (int)std::min<size_t>((size_t)nrhs, std::max<size_t>(1, (200 * 1024) / per_col));
     for (int r0 = 0; r0 < nrhs; r0 += batch) {
         const int nr = std::min(batch, nrhs - r0);
         SweepArgs a{};
-        a.boxes = sf.boxes.as<BoxFac>();
+        a.boxes = sf.sboxes.as<BoxFac>();
         a.sk_ids = sf.sk.as<int>();
         a.rd_ids = sf.rd.as<int>();
         a.pool = sf.pool.p;
@@ -1369,7 +1390,7 @@ static void sweep_one(hif_handle h, SubFactor& sf, int mode, T* xw, int64_t ldx,
         a.mode = mode | (int)(smem << 8);
         a.gws = sf.global ? h->sweep_ws.p : nullptr;
         a.gws_off = sf.global ? sf.gws_off.as<int64_t>() : nullptr;
-        HIF_CUDA((launch_sweep<T>(a, sf.nbox, threads > 0 ? threads : sf.threads, st)));
+        HIF_CUDA((launch_sweep<T>(a, sf.nsmall, threads > 0 ? threads : sf.threads, st)));
     }
 }
 
@@ -1382,9 +1403,10 @@ static void sweep_seq(hif_handle h, T* xw, int64_t ldx, int nrhs, int op, cudaSt
 }
 
 static void ensure_sweep_ws(hif_handle h, int nrhs, size_t elem) {
-    int64_t units = 1;
-    for (auto& sf : h->subs) units = std::max(units, sf->gws_units);
-    h->sweep_ws.ensure(elem * (size_t)units * (size_t)std::max(nrhs, 1));
+    int64_t need = 1;
+    for (auto& sf : h->subs)
+        need = std::max({need, sf->gws_units * std::max(nrhs, 1), sf->wws_units * std::min(std::max(nrhs, 1), 16)});
+    h->sweep_ws.ensure(elem * (size_t)need);
 }
 
 // All sweeps of one operation.  With use_graphs the launch sequence for this
@@ -1452,13 +1474,38 @@ static void prepare_sweeps(hif_handle h) {
             sf.sweep_perm_ints += r;
             sf.sweep_vec_elems += k + r;
         }
-        sf.global = (size_t)sf.max_kr2 * sizeof(T) > 200 * 1024;
-        if (!sf.global || !sf.nbox) continue;
-        std::vector<int64_t> offs(sf.hbox.size());
+        // wide LU boxes take the stage path (HIF_SWEEP_WIDE: the k + r above
+        // which a box is wide)
+        const int wide_min = env_int("HIF_SWEEP_WIDE", 768);
+        std::vector<BoxFac> sb, wb;
+        std::vector<int64_t> woffs;
+        sf.wmax_k = sf.wmax_r = sf.max_kr2_small = 0;
+        sf.wws_units = 0;
+        for (const BoxFac& bf : sf.hbox) {
+            if (!bf.ldl && bf.k + bf.r > wide_min) {
+                wb.push_back(bf);
+                woffs.push_back(sf.wws_units);
+                sf.wws_units += (int64_t)bf.k + 2 * (int64_t)bf.r;
+                sf.wmax_k = std::max(sf.wmax_k, bf.k);
+                sf.wmax_r = std::max(sf.wmax_r, bf.r);
+            } else {
+                sb.push_back(bf);
+                sf.max_kr2_small = std::max(sf.max_kr2_small, bf.k + 2 * bf.r);
+            }
+        }
+        sf.nsmall = (int)sb.size();
+        sf.nwide = (int)wb.size();
+        upload(sf.sboxes, sb, st);
+        upload(sf.wboxes, wb, st);
+        upload(sf.wws_off, woffs, st);
+        sf.global = (size_t)sf.max_kr2_small * sizeof(T) > 200 * 1024;
+        sf.gws_units = 0;
+        if (!sf.global || !sf.nsmall) continue;
+        std::vector<int64_t> offs(sb.size());
         int64_t tot = 0;
-        for (size_t q = 0; q < sf.hbox.size(); ++q) {
+        for (size_t q = 0; q < sb.size(); ++q) {
             offs[q] = tot;
-            tot += (int64_t)(sf.hbox[q].k + 2 * sf.hbox[q].r);
+            tot += (int64_t)(sb[q].k + 2 * sb[q].r);
         }
         upload(sf.gws_off, offs, st);
         sf.gws_units = tot;
@@ -1475,7 +1522,7 @@ static void prepare_sweeps(hif_handle h) {
     const int cand[3] = {128, 256, 512};
     for (auto& sp : h->subs) {
         SubFactor& sf = *sp;
-        if (!sf.nbox) continue;
+        if (!sf.nsmall) continue;
         float best = 1e30f;
         for (int c : cand) {
             float t = 0.f;

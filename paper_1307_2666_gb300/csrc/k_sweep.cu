@@ -230,6 +230,312 @@ cudaError_t launch_sweep(const SweepArgs& a, int nbox, int threads, cudaStream_t
 template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, cudaStream_t);
 template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, cudaStream_t);
 
+// ---- wide boxes: the same passes spread over the GPU ------------------------
+//
+// A box with k + r in the thousands keeps one CTA busy for its whole pass
+// while the other SMs idle, so the wide boxes of a sublevel take their pass as
+// a sequence of stage launches over (box, 64-row tile): gather, matrix-vector
+// products with T, X, Y, the triangular products (I + strict op(M)) with the
+// unit factors or their inverses, permutations, scatter.  Each box keeps its
+// three vectors in a global work space: B0 = skeleton part (k x nr), B1 =
+// redundant part (r x nr), B2 = a second redundant vector.  Right-hand sides
+// go 16 at a time.  The stage order of every mode is that of sweep_box.
+
+namespace {
+
+constexpr int WR = 16;      // right-hand sides per stage launch
+
+template <typename T>
+struct WideView {
+    int k, r;
+    T* B[3];
+    int len[3];
+    __device__ WideView(const WideArgs& a, int e, const BoxFac& bf) {
+        k = bf.k;
+        r = bf.r;
+        T* base = static_cast<T*>(a.ws) + a.ws_off[e] * (int64_t)a.nr;
+        B[0] = base;
+        B[1] = base + (int64_t)k * a.nr;
+        B[2] = B[1] + (int64_t)r * a.nr;
+        len[0] = k;
+        len[1] = r;
+        len[2] = r;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ const T* wide_mat(const WideArgs& a, const BoxFac& bf, int mat, int64_t& ld) {
+    const T* pool = static_cast<const T*>(a.pool);
+    switch (mat) {
+        case 0: ld = bf.k; return pool + bf.T_off;       // T: k x r
+        case 1: ld = bf.k; return pool + bf.X_off;       // X: k x r
+        case 2: ld = bf.r; return pool + bf.Y_off;       // Y: r x k
+        case 3: ld = bf.r; return pool + bf.LU_off;      // unit factors, r x r
+        default: ld = bf.r; return pool + bf.LUi_off;    // their inverses, r x r
+    }
+}
+
+}  // namespace
+
+template <typename T>
+__global__ void wide_gather_kernel(WideArgs a, int div_d) {
+    const int e = blockIdx.y;
+    const BoxFac bf = a.boxes[e];
+    WideView<T> v(a, e, bf);
+    const T* x = static_cast<const T*>(a.x);
+    const int* sk = a.sk_ids + bf.sk_off;
+    const int* rd = a.rd_ids + bf.rd_off;
+    const T* D = static_cast<const T*>(a.pool) + bf.D_off;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)(v.k + v.r) * a.nr; q += stride) {
+        const int c = (int)(q / (v.k + v.r)), i = (int)(q % (v.k + v.r));
+        if (i < v.k) v.B[0][i + (int64_t)v.k * c] = x[sk[i] + a.ldx * c];
+        else {
+            const int j = i - v.k;
+            const T val = x[rd[j] + a.ldx * c];
+            v.B[1][j + (int64_t)v.r * c] = div_d ? val / D[j] : val;
+        }
+    }
+}
+
+template <typename T>
+__global__ void wide_scatter_kernel(WideArgs a, int xr_buf, int mul_d) {
+    const int e = blockIdx.y;
+    const BoxFac bf = a.boxes[e];
+    WideView<T> v(a, e, bf);
+    T* x = static_cast<T*>(a.x);
+    const int* sk = a.sk_ids + bf.sk_off;
+    const int* rd = a.rd_ids + bf.rd_off;
+    const T* D = static_cast<const T*>(a.pool) + bf.D_off;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)(v.k + v.r) * a.nr; q += stride) {
+        const int c = (int)(q / (v.k + v.r)), i = (int)(q % (v.k + v.r));
+        if (i < v.k) x[sk[i] + a.ldx * c] = v.B[0][i + (int64_t)v.k * c];
+        else {
+            const int j = i - v.k;
+            const T val = v.B[xr_buf][j + (int64_t)v.r * c];
+            x[rd[j] + a.ldx * c] = mul_d ? val * D[j] : val;
+        }
+    }
+}
+
+// out = P in (inverse 0: out[i] = in[perm[i]]) or P^T in (out[perm[i]] = in[i])
+template <typename T>
+__global__ void wide_perm_kernel(WideArgs a, int out_buf, int in_buf, int inverse) {
+    const int e = blockIdx.y;
+    const BoxFac bf = a.boxes[e];
+    WideView<T> v(a, e, bf);
+    const int* perm = a.perm + bf.piv_off;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)v.r * a.nr; q += stride) {
+        const int c = (int)(q / v.r), i = (int)(q % v.r);
+        const int64_t o = (int64_t)v.r * c;
+        if (!inverse) v.B[out_buf][i + o] = v.B[in_buf][perm[i] + o];
+        else v.B[out_buf][perm[i] + o] = v.B[in_buf][i + o];
+    }
+}
+
+// One product stage on rows [64 blockIdx.x, +64) of `out` for every wide box:
+//   tri 0: out += s op(M) in                      (M = T, X or Y)
+//   tri 1: out  = in' + strict op(M) in'          (M = LU or LUi; in' = P in
+//          with perm_in, else in), opLower = lower_store != trans
+// op(M)[i, l] = trans ? M[l + ld i] : M[i + ld l].  Not transposed: a thread
+// per output row (coalesced column reads of M), the input staged in shared
+// memory 64 rows at a time; transposed: a warp per output row (coalesced
+// reads of column i of M) with warp reductions.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) wide_mv_kernel(WideArgs a, int out_buf, int in_buf, int mat, T s, int tri,
+                                                      int lower_store, int perm_in) {
+    const int e = blockIdx.y;
+    const BoxFac bf = a.boxes[e];
+    WideView<T> v(a, e, bf);
+    const int p = v.len[out_buf], q = v.len[in_buf];
+    const int i0 = blockIdx.x * 64;
+    if (i0 >= p) return;
+    int64_t ld;
+    const T* M = wide_mat<T>(a, bf, mat, ld);
+    const int* perm = a.perm + bf.piv_off;
+    T* out = v.B[out_buf];
+    const T* in = v.B[in_buf];
+    const int nr = a.nr;
+    const bool opLower = (lower_store != 0) != TRANS;
+    auto inval = [&](int l, int c) -> T { return in[(perm_in ? perm[l] : l) + (int64_t)q * c]; };
+    if (!TRANS) {
+        __shared__ T ins[64][WR + 1];
+        const int tx = threadIdx.x % 64, tc = threadIdx.x / 64;      // rhs tc, tc + 4, ...
+        const int i = i0 + tx;
+        T acc[WR / 4];
+#pragma unroll
+        for (int u = 0; u < WR / 4; ++u) acc[u] = T(0);
+        // tri: only l < i (opLower) or l > i contribute
+        const int lbeg = tri && !opLower ? i0 + 1 : 0;
+        const int lend = tri && opLower ? min(q, i0 + 64) : q;
+        for (int l0 = lbeg; l0 < lend; l0 += 64) {
+            __syncthreads();
+            for (int z = threadIdx.x; z < 64 * WR; z += 256) {
+                const int ll = z % 64, c = z / 64;
+                ins[ll][c] = (l0 + ll < lend && c < nr) ? inval(l0 + ll, c) : T(0);
+            }
+            __syncthreads();
+            if (i < p) {
+                const int cnt = min(64, lend - l0);
+                for (int ll = 0; ll < cnt; ++ll) {
+                    const int l = l0 + ll;
+                    if (tri && (opLower ? l >= i : l <= i)) continue;
+                    const T m = M[i + ld * l];
+#pragma unroll
+                    for (int u = 0; u < WR / 4; ++u) acc[u] += m * ins[ll][tc + 4 * u];
+                }
+            }
+        }
+        if (i < p)
+#pragma unroll
+            for (int u = 0; u < WR / 4; ++u) {
+                const int c = tc + 4 * u;
+                if (c >= nr) continue;
+                T* o = out + i + (int64_t)p * c;
+                if (tri) *o = inval(i, c) + acc[u];
+                else *o += s * acc[u];
+            }
+    } else {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int ii = w; ii < 64; ii += 8) {
+            const int i = i0 + ii;
+            if (i >= p) break;
+            const T* col = M + ld * i;
+            T acc[WR];
+#pragma unroll
+            for (int c = 0; c < WR; ++c) acc[c] = T(0);
+            const int lbeg = tri && !opLower ? i + 1 : 0;
+            const int lend = tri && opLower ? i : q;
+            for (int l = lbeg + lane; l < lend; l += 32) {
+                const T m = col[l];
+#pragma unroll
+                for (int c = 0; c < WR; ++c)
+                    if (c < nr) acc[c] += m * inval(l, c);
+            }
+#pragma unroll
+            for (int c = 0; c < WR; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < nr) {
+                T val = T(0);
+#pragma unroll
+                for (int c = 0; c < WR; ++c)
+                    if (c == lane) val = acc[c];
+                T* o = out + i + (int64_t)p * lane;
+                if (tri) *o = inval(i, lane) + val;
+                else *o += s * val;
+            }
+        }
+    }
+}
+
+template <typename T>
+static cudaError_t wide_mv(const WideArgs& a, int nwide, int rows, int out_buf, int in_buf, int mat, bool trans,
+                           T s, int tri, int lower_store, int perm_in, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const dim3 g((rows + 63) / 64, nwide);
+    note_launch();
+    if (trans) wide_mv_kernel<T, true><<<g, 256, 0, st>>>(a, out_buf, in_buf, mat, s, tri, lower_store, perm_in);
+    else wide_mv_kernel<T, false><<<g, 256, 0, st>>>(a, out_buf, in_buf, mat, s, tri, lower_store, perm_in);
+    return cudaGetLastError();
+}
+
+// The pass of `mode` for the wide boxes; a.nr <= 16 right-hand sides.
+template <typename T>
+cudaError_t launch_wide_sweep(const WideArgs& a, int nwide, int max_k, int max_r, int mode, cudaStream_t st) {
+    if (nwide == 0) return cudaSuccess;
+    if (a.nr < 1 || a.nr > WR) return cudaErrorInvalidValue;
+    const dim3 ge((unsigned)std::min<int64_t>(((int64_t)(max_k + max_r) * a.nr + 255) / 256, 256), nwide);
+    const dim3 gp((unsigned)std::min<int64_t>(((int64_t)max_r * a.nr + 255) / 256, 256), nwide);
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (err == cudaSuccess) err = x; };
+    auto mv = [&](int rows, int ob, int ib, int mat, bool tr, T sg) { chk(wide_mv<T>(a, nwide, rows, ob, ib, mat, tr, sg, 0, 0, 0, st)); };
+    auto tri = [&](int ob, int ib, int mat, bool lower_store, bool tr, bool pin) {
+        chk(wide_mv<T>(a, nwide, max_r, ob, ib, mat, tr, T(1), 1, lower_store ? 1 : 0, pin ? 1 : 0, st));
+    };
+    auto perm = [&](int ob, int ib, bool inv) {
+        note_launch();
+        wide_perm_kernel<T><<<gp, 256, 0, st>>>(a, ob, ib, inv ? 1 : 0);
+        chk(cudaGetLastError());
+    };
+    auto gather = [&](bool divd) {
+        note_launch();
+        wide_gather_kernel<T><<<ge, 256, 0, st>>>(a, divd ? 1 : 0);
+        chk(cudaGetLastError());
+    };
+    auto scatter = [&](int xr_buf, bool muld) {
+        note_launch();
+        wide_scatter_kernel<T><<<ge, 256, 0, st>>>(a, xr_buf, muld ? 1 : 0);
+        chk(cudaGetLastError());
+    };
+    enum { MT = 0, MX = 1, MY = 2, MLU = 3, MLUI = 4 };
+    switch (mode) {
+        case SOLVE_UP:        // xr -= T^T xs; xr <- L^{-1} P xr; xs -= X xr
+            gather(false);
+            mv(max_r, 1, 0, MT, true, T(-1));
+            tri(2, 1, MLUI, true, false, true);
+            mv(max_k, 0, 2, MX, false, T(-1));
+            scatter(2, false);
+            break;
+        case SOLVE_DOWN:      // xr /= D; xr -= Y xs; xr <- U'^{-1} xr; xs -= T xr
+            gather(true);
+            mv(max_r, 1, 0, MY, false, T(-1));
+            tri(2, 1, MLUI, false, false, false);
+            mv(max_k, 0, 2, MT, false, T(-1));
+            scatter(2, false);
+            break;
+        case APPLY_UP:        // xs += T xr; xr <- U' xr; xr += Y xs; xr *= D
+            gather(false);
+            mv(max_k, 0, 1, MT, false, T(1));
+            tri(2, 1, MLU, false, false, false);
+            mv(max_r, 2, 0, MY, false, T(1));
+            scatter(2, true);
+            break;
+        case APPLY_DOWN:      // xs += X xr; xr <- P^T L xr; xr += T^T xs
+            gather(false);
+            mv(max_k, 0, 1, MX, false, T(1));
+            tri(2, 1, MLU, true, false, false);
+            perm(1, 2, true);
+            mv(max_r, 1, 0, MT, true, T(1));
+            scatter(1, false);
+            break;
+        case SOLVET_UP:       // xr -= T^T xs; xr <- U'^{-T} xr; xs -= Y^T xr
+            gather(false);
+            mv(max_r, 1, 0, MT, true, T(-1));
+            tri(2, 1, MLUI, false, true, false);
+            mv(max_k, 0, 2, MY, true, T(-1));
+            scatter(2, false);
+            break;
+        case SOLVET_DOWN:     // xr /= D; xr -= X^T xs; xr <- P^T L^{-T} xr; xs -= T xr
+            gather(true);
+            mv(max_r, 1, 0, MX, true, T(-1));
+            tri(2, 1, MLUI, true, true, false);
+            perm(1, 2, true);
+            mv(max_k, 0, 1, MT, false, T(-1));
+            scatter(1, false);
+            break;
+        case APPLYT_UP:       // xs += T xr; xr <- L^T P xr; xr += X^T xs; xr *= D
+            gather(false);
+            mv(max_k, 0, 1, MT, false, T(1));
+            tri(2, 1, MLU, true, true, true);
+            mv(max_r, 2, 0, MX, true, T(1));
+            scatter(2, true);
+            break;
+        case APPLYT_DOWN:     // xs += Y^T xr; xr <- U'^T xr; xr += T^T xs
+            gather(false);
+            mv(max_k, 0, 1, MY, true, T(1));
+            tri(2, 1, MLU, false, true, false);
+            mv(max_r, 2, 0, MT, true, T(1));
+            scatter(2, false);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return err;
+}
+
+template cudaError_t launch_wide_sweep<double>(const WideArgs&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_wide_sweep<float>(const WideArgs&, int, int, int, int, cudaStream_t);
+
 // ---------------------------------------------------- precision moves ----
 
 template <typename T>

@@ -207,6 +207,23 @@ template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStr
 // not depend on it)
 template <typename T> cudaError_t launch_sweep(const SweepArgs&, int nbox, int threads, cudaStream_t);
 
+// Wide boxes of a sublevel: the pass as stage launches over (box, row tile).
+// ws holds per box (k + 2 r) x nr values from ws_off[box] * nr; nr <= 16.
+struct WideArgs {
+    const BoxFac* boxes;
+    const int* sk_ids;
+    const int* rd_ids;
+    const void* pool;
+    const int* perm;
+    void* x;
+    int64_t ldx;
+    int nr;
+    void* ws;
+    const int64_t* ws_off;
+};
+template <typename T>
+cudaError_t launch_wide_sweep(const WideArgs&, int nwide, int max_k, int max_r, int mode, cudaStream_t);
+
 // vectors and direct sums (FP64 inputs)
 template <typename T> cudaError_t launch_to_work(const double* src, int64_t lds, T* dst, int64_t ldd,
                                                  int64_t N, int nrhs, cudaStream_t);

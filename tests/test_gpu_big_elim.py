@@ -69,3 +69,27 @@ def test_batched_elimination_fp32_refined(P, monkeypatch):
     x, its, r = fb.solve_refined(T(pb.f), tol=1e-10)
     assert r <= 1e-10 and rel(x.cpu().numpy(), u) <= 1e-9
     fb.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_wide_box_sweeps_match_one_cta_sweeps(P, monkeypatch, precision, tol):
+    # HIF_SWEEP_WIDE sets the k + r above which a box's sweep passes run as
+    # stage launches over the GPU (gather, products with T, X, Y and the unit
+    # factors or their inverses, permutations, scatter); at 30 nearly every
+    # LU box of the n = 64 grid does.  All four operations, 1 and 20 RHS
+    # (the stage launches take 16 at a time), against the one-CTA sweeps of
+    # the same factorization.
+    pb = hi.volume_problem(64, 2, smooth_seed=1002, rhs_seed=1001, nrhs=20)
+    args = (T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c), 0, 1e-6)
+    monkeypatch.setenv("HIF_BIG_ELIM", "40")
+    monkeypatch.setenv("HIF_SWEEP_WIDE", "30")
+    fw = P.Factorization(*args, symmetric=False, precision=precision)
+    monkeypatch.setenv("HIF_SWEEP_WIDE", "100000")
+    fo = P.Factorization(*args, symmetric=False, precision=precision)
+    monkeypatch.delenv("HIF_SWEEP_WIDE")
+    monkeypatch.delenv("HIF_BIG_ELIM")
+    for F in (T(pb.f[:, :1]), T(pb.f)):
+        for op in ("apply", "solve", "apply_transpose", "solve_transpose"):
+            assert rel(getattr(fw, op)(F).cpu().numpy(), getattr(fo, op)(F).cpu().numpy()) <= tol, op
+    fw.close()
+    fo.close()
