@@ -322,9 +322,62 @@ static int env_int(const char* name, int dflt) {
 }
 
 struct BigBuffers {
-    DevMem bb, bg, state, YK, YS, vv, vw, vt, est, nrm, perm;
+    DevMem bb, bg, state, YK, YS, vv, vw, vt, est, nrm, perm, F, gv, nrm0;
     DevMem q_yoff, q_m, q_n, q_tau, q_G, q_T, q_W, q_Gp, q_Wp, q_gpoff, q_wpoff;
 };
+
+// The column-pivoted QR of all large groups of a sublevel: by panels of
+// HIF_BIG_QP_NB pivots (default 32; blocked, one trailing product per panel)
+// or, at 1, one launch pair per pivot.
+template <typename T>
+static void run_big_pivoted_qr(BigArgs& a, BigBuffers& B, const std::vector<BigGroup>& bgv, int max_n, int maxk,
+                               int64_t voff, cudaStream_t st) {
+    const int ng = (int)bgv.size();
+    int max_m = 0;
+    for (const BigGroup& x : bgv) max_m = std::max(max_m, x.m);
+    const int nbq = std::min(32, std::max(1, env_int("HIF_BIG_QP_NB", 32)));
+    std::vector<BigState> hs(ng);
+    if (nbq > 1) {
+        B.F.ensure(sizeof(T) * std::max<int64_t>(voff, 1) * nbq);
+        B.gv.ensure(sizeof(T) * 32 * std::max(ng, 1));
+        B.nrm0.ensure(sizeof(double) * std::max<int64_t>(voff, 1));
+        a.F = B.F.p;
+        a.gv = B.gv.p;
+        a.nrm0 = B.nrm0.as<double>();
+        a.nb = nbq;
+    } else {
+        a.nrm0 = nullptr;
+    }
+    HIF_CUDA((big_qr_init<T>(a, ng, max_n, st)));
+    if (nbq > 1) {
+        int step = 0;
+        for (int panel = 0; panel <= maxk; ++panel) {
+            {
+                ProfRange pr(PROF_BIG_QR, st, 0.0, 0.0);   // bytes added once the ranks are known
+                HIF_CUDA((big_qp_panel<T>(a, ng, max_n, max_m, step, st)));
+            }
+            HIF_CUDA(cudaMemcpyAsync(hs.data(), a.state, sizeof(BigState) * ng, cudaMemcpyDeviceToHost, st));
+            HIF_CUDA(cudaStreamSynchronize(st));
+            bool all = true;
+            for (const BigState& x : hs) all = all && x.stop;
+            if (all) break;
+        }
+        return;
+    }
+    for (int j = 0; j < maxk; ++j) {
+        {
+            ProfRange pr(PROF_BIG_QR, st, 0.0, 0.0);   // bytes added once the ranks are known
+            HIF_CUDA((big_qr_step<T>(a, ng, max_n, j, st)));
+        }
+        if ((j + 1) % 16 == 0) {
+            HIF_CUDA(cudaMemcpyAsync(hs.data(), a.state, sizeof(BigState) * ng, cudaMemcpyDeviceToHost, st));
+            HIF_CUDA(cudaStreamSynchronize(st));
+            bool all = true;
+            for (const BigState& x : hs) all = all && x.stop;
+            if (all) break;
+        }
+    }
+}
 
 // ID of the large boxes of one sublevel: Y_c materialized in HBM and, when it
 // has more rows than columns, reduced to its n x n factor R by a blocked
@@ -481,21 +534,7 @@ static void run_big_id(hif_handle h, size_t tau, const std::vector<BoxDesc>& bd,
             upload(B.bg, bgv, st);
         }
     }
-    HIF_CUDA((big_qr_init<T>(a, ng, max_n, st)));
-    std::vector<BigState> hs(ng);
-    for (int j = 0; j < maxk; ++j) {
-        {
-            ProfRange pr(PROF_BIG_QR, st, 0.0, 0.0);   // bytes added once the ranks are known
-            HIF_CUDA((big_qr_step<T>(a, ng, max_n, j, st)));
-        }
-        if ((j + 1) % 16 == 0) {
-            HIF_CUDA(cudaMemcpyAsync(hs.data(), B.state.p, sizeof(BigState) * ng, cudaMemcpyDeviceToHost, st));
-            HIF_CUDA(cudaStreamSynchronize(st));
-            bool all = true;
-            for (const BigState& x : hs) all = all && x.stop;
-            if (all) break;
-        }
-    }
+    run_big_pivoted_qr<T>(a, B, bgv, max_n, maxk, voff, st);
     ProfRange pr(PROF_BIG_T, st, 0.0, 0.0);
     HIF_CUDA((big_finish<T>(a, ng, max_n, st)));
 }
@@ -678,21 +717,7 @@ static void run_big_id_R(hif_handle h, const std::vector<BoxDesc>& bd, const std
     a.Tws = Tws.p;
     a.perm_out = perm_out.as<int>();
     a.k_out = k_out.as<int>();
-    HIF_CUDA((big_qr_init<T>(a, ng, max_n, st)));
-    std::vector<BigState> hs(ng);
-    for (int j = 0; j < maxk; ++j) {
-        {
-            ProfRange pr(PROF_BIG_QR, st, 0.0, 0.0);   // bytes added once the ranks are known
-            HIF_CUDA((big_qr_step<T>(a, ng, max_n, j, st)));
-        }
-        if ((j + 1) % 16 == 0) {
-            HIF_CUDA(cudaMemcpyAsync(hs.data(), B.state.p, sizeof(BigState) * ng, cudaMemcpyDeviceToHost, st));
-            HIF_CUDA(cudaStreamSynchronize(st));
-            bool all = true;
-            for (const BigState& x : hs) all = all && x.stop;
-            if (all) break;
-        }
-    }
+    run_big_pivoted_qr<T>(a, B, bgv, max_n, maxk, voff, st);
     ProfRange pr(PROF_BIG_T, st, 0.0, 0.0);
     HIF_CUDA((big_finish<T>(a, ng, max_n, st)));
 }

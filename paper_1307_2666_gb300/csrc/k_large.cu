@@ -188,6 +188,9 @@ __global__ void big_norm_init_kernel(BigArgs a) {
         S.stop = 0;
         S.nu0 = 0.0;
         S.tau = 0.0;
+        S.j0 = 0;
+        S.pend = 0;
+        S.last_step = -1;
     }
     if (l >= G.n) return;
     double s = 0.0;
@@ -198,6 +201,7 @@ __global__ void big_norm_init_kernel(BigArgs a) {
     s = warp_sum(s);
     if (lane == 0) {
         a.nrm[G.vec_off + l] = s;
+        if (a.nrm0) a.nrm0[G.vec_off + l] = s;
         a.perm[G.vec_off + l] = l;
     }
 }
@@ -339,6 +343,314 @@ __global__ void __launch_bounds__(256) big_update_kernel(BigArgs a, int j) {
     }
     s = warp_sum(s);
     if (lane == 0) a.nrm[G.vec_off + l] = s;
+}
+
+// ---------------------------------------- blocked pivoted QR (panels) ----
+//
+// The pivoted QR of Lemma 2.2 with delayed trailing updates: within a panel
+// of nb pivots only the pivot column and the pivot row are brought up to
+// date; every trailing column l keeps F[l, q] = tau_q (W^T v_q)_l minus the
+// earlier reflectors' share, so that W_updated = W - V F^T, and the panel
+// ends with one product W[rows below the panel, trailing] -= V F^T.  The
+// pivot choice and the rank test use the squared column norms downdated by
+// the new pivot row's entries (in FP64); when a norm falls below
+// sqrt(eps_T) of its value at the last exact computation the group ends its
+// panel early, and every panel ends with the norms recomputed from the
+// updated columns.  Per pivot the trailing columns are read once (for F),
+// instead of read twice and written once.
+
+constexpr int QPB = 32;   // maximum panel width
+
+// start of a panel for every group still pivoting
+__global__ void bqp_start_kernel(BigArgs a, int ngroups) {
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ngroups) return;
+    BigState& S = a.state[gi];
+    if (S.stop) return;
+    S.j0 = S.k;
+    S.pend = 0;
+}
+
+// one pivot of the panel (one CTA per group): argmax of the downdated norms,
+// column swap, the pivot column brought up to date, its reflector, and
+// g = V_panel^T v
+template <typename T>
+__global__ void __launch_bounds__(256) bqp_pivot_kernel(BigArgs a, int step) {
+    const BigGroup G = a.groups[blockIdx.x];
+    BigState* S = a.state + blockIdx.x;
+    if (S->stop || S->pend) return;
+    const int j = S->k, j0 = S->j0, jj = j - j0;
+    const int nb = a.nb;
+    if (jj >= nb) return;
+    const int kmax = min(G.m, G.n);
+    if (j >= kmax) {
+        if (threadIdx.x == 0) S->stop = 1;
+        return;
+    }
+    T* W = static_cast<T*>(a.YK) + G.y_off;
+    const int64_t ld = G.ld;
+    const int n = G.n;
+    double* nrm = a.nrm + G.vec_off;
+    double* nrm0 = a.nrm0 + G.vec_off;
+    int* perm = a.perm + G.vec_off;
+    T* F = static_cast<T*>(a.F) + G.vec_off * nb;
+    T* gq = static_cast<T*>(a.gv) + (int64_t)blockIdx.x * QPB;
+    __shared__ double redv[256];
+    __shared__ int redi[256];
+    __shared__ T hs[256];
+    __shared__ T fj[QPB];
+    __shared__ T part[8][QPB];
+    // pivot: largest downdated norm, ties to the lowest original column
+    double best = -1.0;
+    int bl = -1, bo = 1 << 30;
+    for (int l = j + threadIdx.x; l < n; l += blockDim.x) {
+        const double v = nrm[l];
+        if (v > best || (v == best && perm[l] < bo)) { best = v; bo = perm[l]; bl = l; }
+    }
+    redv[threadIdx.x] = best;
+    redi[threadIdx.x] = bl;
+    __syncthreads();
+    for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) {
+            const double v2 = redv[threadIdx.x + s2], v1 = redv[threadIdx.x];
+            const int l2 = redi[threadIdx.x + s2], l1 = redi[threadIdx.x];
+            if (l2 >= 0 && (l1 < 0 || v2 > v1 || (v2 == v1 && perm[l2] < perm[l1]))) {
+                redv[threadIdx.x] = v2;
+                redi[threadIdx.x] = l2;
+            }
+        }
+        __syncthreads();
+    }
+    const double bnorm = sqrt(fmax(redv[0], 0.0));
+    const int p = redi[0];
+    const double nu0 = j == 0 ? bnorm : S->nu0;
+    __syncthreads();
+    if (bnorm <= G.tol * nu0 || bnorm == 0.0 || p < j) {
+        if (threadIdx.x == 0) {
+            S->stop = 1;
+            if (j == 0) S->nu0 = bnorm;
+        }
+        return;
+    }
+    if (p != j) {
+        for (int i = threadIdx.x; i < G.m; i += blockDim.x) {
+            const T t = W[i + ld * j];
+            W[i + ld * j] = W[i + ld * p];
+            W[i + ld * p] = t;
+        }
+        for (int q = threadIdx.x; q < jj; q += blockDim.x) {
+            const T t = F[j + (int64_t)n * q];
+            F[j + (int64_t)n * q] = F[p + (int64_t)n * q];
+            F[p + (int64_t)n * q] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && p != j) {
+        const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+        double tn = nrm[j]; nrm[j] = nrm[p]; nrm[p] = tn;
+        tn = nrm0[j]; nrm0[j] = nrm0[p]; nrm0[p] = tn;
+    }
+    for (int q = threadIdx.x; q < jj; q += blockDim.x) fj[q] = F[j + (int64_t)n * q];
+    __syncthreads();
+    // rows j.. of the pivot column: W[i, j] -= sum_q W[i, j0 + q] F[j, q]
+    if (jj > 0)
+        for (int i = j + threadIdx.x; i < G.m; i += blockDim.x) {
+            T acc = W[i + ld * j];
+            for (int q = 0; q < jj; ++q) acc -= W[i + ld * (j0 + q)] * fj[q];
+            W[i + ld * j] = acc;
+        }
+    __syncthreads();
+    // reflector for W[j:, j]
+    T ssum = T(0);
+    for (int i = j + 1 + threadIdx.x; i < G.m; i += blockDim.x) {
+        const T v = W[i + ld * j];
+        ssum += v * v;
+    }
+    hs[threadIdx.x] = ssum;
+    __syncthreads();
+    for (int k2 = blockDim.x / 2; k2 > 0; k2 >>= 1) {
+        if (threadIdx.x < k2) hs[threadIdx.x] += hs[threadIdx.x + k2];
+        __syncthreads();
+    }
+    const T ss = hs[0];
+    const T alpha = W[j + ld * j];
+    T tau = T(0), scal = T(0), beta = alpha;
+    if (ss != T(0)) {
+        beta = -copysign(sqrt(alpha * alpha + ss), alpha);
+        tau = (beta - alpha) / beta;
+        scal = T(1) / (alpha - beta);
+    }
+    __syncthreads();
+    if (tau != T(0)) {
+        for (int i = j + 1 + threadIdx.x; i < G.m; i += blockDim.x) W[i + ld * j] *= scal;
+        if (threadIdx.x == 0) W[j + ld * j] = beta;
+    }
+    __syncthreads();
+    // g[q] = sum_{i >= j} W[i, j0 + q] v_i, v_j = 1, v_i = W[i, j] below
+    if (jj > 0) {
+        T acc[QPB];
+#pragma unroll
+        for (int q = 0; q < QPB; ++q) acc[q] = T(0);
+        for (int i = j + threadIdx.x; i < G.m; i += blockDim.x) {
+            const T vi = i == j ? T(1) : W[i + ld * j];
+#pragma unroll
+            for (int q = 0; q < QPB; ++q)
+                if (q < jj) acc[q] += W[i + ld * (j0 + q)] * vi;
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int q = 0; q < QPB; ++q) {
+            const T v = warp_sum(acc[q]);
+            if (lane == 0) part[wid][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < jj) {
+            T v = T(0);
+            for (int w = 0; w < 8; ++w) v += part[w][threadIdx.x];
+            gq[threadIdx.x] = v;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (j == 0) S->nu0 = bnorm;
+        S->tau = (double)tau;
+        S->k = j + 1;
+        S->last_step = step;
+    }
+}
+
+// F[l, jj] for the trailing columns (a warp per column), the pivot row's
+// entry brought up to date, and the norm downdated
+template <typename T>
+__global__ void __launch_bounds__(256) bqp_f_kernel(BigArgs a, int step) {
+    const BigGroup G = a.groups[blockIdx.y];
+    const BigState S = a.state[blockIdx.y];
+    if (S.stop || S.last_step != step) return;
+    const int j = S.k - 1, j0 = S.j0, jj = j - j0;
+    const int nb = a.nb;
+    const int lane = threadIdx.x & 31;
+    const int l = j + 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (l >= G.n) return;
+    T* W = static_cast<T*>(a.YK) + G.y_off;
+    const int64_t ld = G.ld;
+    const int n = G.n;
+    T* F = static_cast<T*>(a.F) + G.vec_off * nb;
+    const T* gq = static_cast<const T*>(a.gv) + (int64_t)blockIdx.y * QPB;
+    const T tau = (T)S.tau;
+    T* col = W + ld * l;
+    const T* v = W + ld * j;
+    T dot = T(0);
+    for (int i = j + 1 + lane; i < G.m; i += 32) dot += v[i] * col[i];
+    dot = warp_sum(dot);
+    if (lane == 0) {
+        dot += col[j];
+        T corr = T(0);
+        for (int q = 0; q < jj; ++q) corr += F[l + (int64_t)n * q] * gq[q];
+        const T f = tau * (dot - corr);
+        F[l + (int64_t)n * jj] = f;
+        // pivot row: W[j, l] -= sum_{q < jj} W[j, j0 + q] F[l, q] + F[l, jj]
+        T r = col[j] - f;
+        for (int q = 0; q < jj; ++q) r -= W[j + ld * (j0 + q)] * F[l + (int64_t)n * q];
+        col[j] = r;
+        double* nrm = a.nrm + G.vec_off;
+        const double* nrm0 = a.nrm0 + G.vec_off;
+        const double nn = fmax(nrm[l] - (double)r * (double)r, 0.0);
+        nrm[l] = nn;
+        // the downdated norm keeps ~sqrt(eps_T) relative accuracy only while
+        // it stays above sqrt(eps_T) of the last exact value
+        const double tol3z = sizeof(T) == 4 ? 3.4526698e-4 : 1.4901161e-8;
+        if (nn <= tol3z * nrm0[l]) atomicExch(&a.state[blockIdx.y].pend, 1);
+    }
+}
+
+// end of a panel: rows below the panel of the trailing columns, W -= V F^T
+// (64 x 64 tiles, K = the panel's pivots)
+template <typename T>
+__global__ void __launch_bounds__(256) bqp_update_kernel(BigArgs a) {
+    const BigGroup G = a.groups[blockIdx.z];
+    const BigState S = a.state[blockIdx.z];
+    if (S.stop) return;
+    const int j0 = S.j0, kb = S.k - S.j0, r0 = S.k;
+    if (kb <= 0) return;
+    const int i0 = r0 + blockIdx.x * 64, c0 = r0 + blockIdx.y * 64;
+    if (i0 >= G.m || c0 >= G.n) return;
+    T* W = static_cast<T*>(a.YK) + G.y_off;
+    const int64_t ld = G.ld;
+    const int n = G.n;
+    const T* F = static_cast<const T*>(a.F) + G.vec_off * a.nb;
+    __shared__ T Vs[QPB][64 + 1];
+    __shared__ T Fs[QPB][64 + 1];
+    for (int q = threadIdx.x; q < 64 * QPB; q += 256) {
+        const int rr = q % 64, c = q / 64;
+        const int i = i0 + rr, l = c0 + rr;
+        Vs[c][rr] = (c < kb && i < G.m) ? W[i + ld * (j0 + c)] : T(0);
+        Fs[c][rr] = (c < kb && l < n) ? F[l + (int64_t)n * c] : T(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4] = {};
+    for (int c = 0; c < kb; ++c) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) av[q] = Vs[c][tx + 16 * q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bv[q] = Fs[c][ty + 16 * q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bv[w];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int i = i0 + tx + 16 * u, l = c0 + ty + 16 * w;
+            if (i < G.m && l < n) W[i + ld * l] -= acc[u][w];
+        }
+}
+
+// exact norms of rows k.. of the trailing columns (a warp per column)
+template <typename T>
+__global__ void __launch_bounds__(256) bqp_norm_kernel(BigArgs a) {
+    const BigGroup G = a.groups[blockIdx.y];
+    const BigState S = a.state[blockIdx.y];
+    if (S.stop) return;
+    const int r0 = S.k;
+    const int lane = threadIdx.x & 31;
+    const int l = r0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (l >= G.n) return;
+    const T* col = static_cast<const T*>(a.YK) + G.y_off + G.ld * l;
+    double s = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        float sf = 0.f;
+        for (int i = r0 + lane; i < G.m; i += 32) sf = fmaf(col[i], col[i], sf);
+        s = (double)sf;
+    } else {
+        for (int i = r0 + lane; i < G.m; i += 32) s += (double)col[i] * (double)col[i];
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+        a.nrm[G.vec_off + l] = s;
+        a.nrm0[G.vec_off + l] = s;
+    }
+}
+
+template <typename T>
+cudaError_t big_qp_panel(const BigArgs& a, int ngroups, int max_n, int max_m, int& step, cudaStream_t st) {
+    if (ngroups == 0) return cudaSuccess;
+    if (a.nb < 1 || a.nb > QPB) return cudaErrorInvalidValue;
+    note_launch();
+    bqp_start_kernel<<<(ngroups + 127) / 128, 128, 0, st>>>(a, ngroups);
+    for (int jj = 0; jj < a.nb; ++jj, ++step) {
+        note_launch();
+        bqp_pivot_kernel<T><<<ngroups, 256, 0, st>>>(a, step);
+        note_launch();
+        bqp_f_kernel<T><<<dim3((max_n + 7) / 8, ngroups), 256, 0, st>>>(a, step);
+    }
+    note_launch();
+    bqp_update_kernel<T><<<dim3((max_m + 63) / 64, (max_n + 63) / 64, ngroups), 256, 0, st>>>(a);
+    note_launch();
+    bqp_norm_kernel<T><<<dim3((max_n + 7) / 8, ngroups), 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 // T = R1^{-1} R2 (redundant columns in ascending original order), outputs
@@ -1331,6 +1643,7 @@ cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max
     template cudaError_t big_add<T>(void*, const void*, int64_t, cudaStream_t);                                \
     template cudaError_t big_qr_init<T>(const BigArgs&, int, int, cudaStream_t);                               \
     template cudaError_t big_qr_step<T>(const BigArgs&, int, int, int, cudaStream_t);                          \
+    template cudaError_t big_qp_panel<T>(const BigArgs&, int, int, int, int&, cudaStream_t);                   \
     template cudaError_t big_finish<T>(const BigArgs&, int, int, cudaStream_t);                                \
     template cudaError_t big_elim_batch<T>(const BatchElimArgs&, int, int, int, cudaStream_t);
 HIF_INST(double)

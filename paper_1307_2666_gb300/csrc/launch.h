@@ -124,6 +124,13 @@ struct BigState {
     int stop;
     double nu0;
     double tau;
+    // blocked pivoted QR (big_qp): first pivot of the current panel, panel
+    // ended early (a norm lost too much to downdating), launch step of the
+    // last pivot taken
+    int j0;
+    int pend;
+    int last_step;
+    int pad;
 };
 
 struct BigArgs {
@@ -152,6 +159,12 @@ struct BigArgs {
     int* k_out;
     double eps;
     double tol_floor;
+    // blocked pivoted QR: F (n x nb per group at vec_off * nb), the panel's
+    // V^T v (32 per group), the norms at the last exact computation, panel width
+    void* F;
+    void* gv;
+    double* nrm0;
+    int nb;
 };
 
 template <typename T> cudaError_t big_ygen(const BigArgs&, int nbig, int64_t max_entries, cudaStream_t);
@@ -159,6 +172,10 @@ template <typename T> cudaError_t big_rho(const BigArgs&, int ngroups, int max_m
 template <typename T> cudaError_t big_add(void* YK, const void* YS, int64_t n, cudaStream_t);
 template <typename T> cudaError_t big_qr_init(const BigArgs&, int ngroups, int max_n, cudaStream_t);
 template <typename T> cudaError_t big_qr_step(const BigArgs&, int ngroups, int max_n, int j, cudaStream_t);
+// Blocked column-pivoted QR of all large groups: one panel of up to a.nb
+// pivots per call, its trailing update one product; step counts the pivot
+// launches (the state's last_step) across calls.
+template <typename T> cudaError_t big_qp_panel(const BigArgs&, int ngroups, int max_n, int max_m, int& step, cudaStream_t);
 template <typename T> cudaError_t big_finish(const BigArgs&, int ngroups, int max_n, cudaStream_t);
 struct BatchElimArgs {
     GeomDev g;

@@ -93,3 +93,35 @@ def test_wide_box_sweeps_match_one_cta_sweeps(P, monkeypatch, precision, tol):
             assert rel(getattr(fw, op)(F).cpu().numpy(), getattr(fo, op)(F).cpu().numpy()) <= tol, op
     fw.close()
     fo.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_blocked_pivoted_qr_matches_per_step_qr(P, monkeypatch, precision):
+    # the large-box pivoted QR by panels of 32 pivots (delayed trailing
+    # updates, downdated norms recomputed at every panel end) against one
+    # launch pair per pivot; HIF_BIG_ID=40 sends the boxes above 40 columns
+    # down the large-box path
+    pb = hi.volume_problem(64, 2, smooth_seed=1002, rhs_seed=1001, nrhs=2)
+    args = (T(pb.points), T(pb.weights), T(pb.a), T(pb.b), T(pb.c), 0, 1e-6)
+    monkeypatch.setenv("HIF_BIG_ID", "40")
+    monkeypatch.setenv("HIF_BIG_QP_NB", "32")
+    fb = P.Factorization(*args, precision=precision)
+    monkeypatch.setenv("HIF_BIG_QP_NB", "1")
+    fs = P.Factorization(*args, precision=precision)
+    monkeypatch.delenv("HIF_BIG_QP_NB")
+    monkeypatch.delenv("HIF_BIG_ID")
+    kb = [s["skeletons"] for s in fb.stats()["per_sublevel"]]
+    ks = [s["skeletons"] for s in fs.stats()["per_sublevel"]]
+    if precision == "fp64":
+        assert kb == ks
+        for sub in range(len(kb)):
+            np.testing.assert_array_equal(fb.eliminated_dofs(sub), fs.eliminated_dofs(sub))
+        assert rel(fb.solve(T(pb.f)).cpu().numpy(), fs.solve(T(pb.f)).cpu().numpy()) <= 1e-12
+    else:
+        for a, b in zip(kb, ks):
+            assert abs(a - b) <= 2 + 0.05 * b
+    u = dense.DenseSolver(kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)).solve(pb.f)
+    x, its, r = fb.solve_refined(T(pb.f), tol=1e-10)
+    assert r <= 1e-10 and rel(x.cpu().numpy(), u) <= 1e-9
+    fb.close()
+    fs.close()
