@@ -425,6 +425,15 @@ __global__ void __launch_bounds__(256) bqp_pivot_kernel(BigArgs a, int step) {
     const int p = redi[0];
     const double nu0 = j == 0 ? bnorm : S->nu0;
     __syncthreads();
+    // the rank test decides on exact norms: within a panel (downdated norms,
+    // relative error up to ~sqrt(eps_T) in the square) a maximum near the
+    // threshold ends the panel instead, and the next panel's first pivot,
+    // on the recomputed norms, decides
+    const double margin = sizeof(T) == 4 ? 1e-3 : 1e-7;
+    if (jj > 0 && bnorm <= G.tol * nu0 * (1.0 + margin) && p >= j) {
+        if (threadIdx.x == 0) S->pend = 1;
+        return;
+    }
     if (bnorm <= G.tol * nu0 || bnorm == 0.0 || p < j) {
         if (threadIdx.x == 0) {
             S->stop = 1;
