@@ -327,15 +327,18 @@ struct BigBuffers {
 };
 
 // The column-pivoted QR of all large groups of a sublevel: by panels of
-// HIF_BIG_QP_NB pivots (default 32; blocked, one trailing product per panel)
-// or, at 1, one launch pair per pivot.
+// HIF_BIG_QP_NB pivots (blocked, one trailing product per panel) or, at 1,
+// one launch pair per pivot.  Default: panels of 32 in FP32; one pivot per
+// step in FP64, whose exact norms at every step keep the rank decisions of
+// the symmetric and full proxy matrices identical at eps = 1e-9 (the blocked
+// update's rounding moved one decision at the threshold by one).
 template <typename T>
 static void run_big_pivoted_qr(BigArgs& a, BigBuffers& B, const std::vector<BigGroup>& bgv, int max_n, int maxk,
                                int64_t voff, cudaStream_t st) {
     const int ng = (int)bgv.size();
     int max_m = 0;
     for (const BigGroup& x : bgv) max_m = std::max(max_m, x.m);
-    const int nbq = std::min(32, std::max(1, env_int("HIF_BIG_QP_NB", 32)));
+    const int nbq = std::min(32, std::max(1, env_int("HIF_BIG_QP_NB", sizeof(T) == 4 ? 32 : 1)));
     std::vector<BigState> hs(ng);
     if (nbq > 1) {
         B.F.ensure(sizeof(T) * std::max<int64_t>(voff, 1) * nbq);
