@@ -97,9 +97,17 @@ __global__ void big_pow_tv_kernel(BigArgs a) {
     const double* v = a.vec_v + 2 * G.vec_off + which * (int64_t)G.n;
     double* t = a.vec_t + 2 * G.row_off + which * (int64_t)G.m;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.m; i += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int l = 0; l < G.n; ++l) acc += (double)Y[i + (int64_t)G.m * l] * v[l];
-        t[i] = acc;
+        // rho_g needs only a rough norm ratio: FP32 data accumulate in FP32
+        // (an FP64 FMA per entry binds the pass to the FP64 pipe)
+        if constexpr (sizeof(T) == 4) {
+            float acc = 0.f;
+            for (int l = 0; l < G.n; ++l) acc = fmaf(Y[i + (int64_t)G.m * l], (float)v[l], acc);
+            t[i] = acc;
+        } else {
+            double acc = 0.0;
+            for (int l = 0; l < G.n; ++l) acc += (double)Y[i + (int64_t)G.m * l] * v[l];
+            t[i] = acc;
+        }
     }
 }
 
@@ -116,7 +124,13 @@ __global__ void big_pow_w_kernel(BigArgs a) {
     const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (l >= G.n) return;
     double acc = 0.0;
-    for (int i = lane; i < G.m; i += 32) acc += (double)Y[i + (int64_t)G.m * l] * t[i];
+    if constexpr (sizeof(T) == 4) {
+        float af = 0.f;
+        for (int i = lane; i < G.m; i += 32) af = fmaf(Y[i + (int64_t)G.m * l], (float)t[i], af);
+        acc = (double)af;
+    } else {
+        for (int i = lane; i < G.m; i += 32) acc += (double)Y[i + (int64_t)G.m * l] * t[i];
+    }
     acc = warp_sum(acc);
     if (lane == 0) w[l] = acc;
 }
@@ -374,8 +388,10 @@ __global__ void bqp_start_kernel(BigArgs a, int ngroups) {
 // one pivot of the panel (one CTA per group): argmax of the downdated norms,
 // column swap, the pivot column brought up to date, its reflector, and
 // g = V_panel^T v
+constexpr int QPT = 512;   // threads of the pivot kernel
+
 template <typename T>
-__global__ void __launch_bounds__(256) bqp_pivot_kernel(BigArgs a, int step) {
+__global__ void __launch_bounds__(QPT) bqp_pivot_kernel(BigArgs a, int step) {
     const BigGroup G = a.groups[blockIdx.x];
     BigState* S = a.state + blockIdx.x;
     if (S->stop || S->pend) return;
@@ -395,11 +411,11 @@ __global__ void __launch_bounds__(256) bqp_pivot_kernel(BigArgs a, int step) {
     int* perm = a.perm + G.vec_off;
     T* F = static_cast<T*>(a.F) + G.vec_off * nb;
     T* gq = static_cast<T*>(a.gv) + (int64_t)blockIdx.x * QPB;
-    __shared__ double redv[256];
-    __shared__ int redi[256];
-    __shared__ T hs[256];
+    __shared__ double redv[QPT];
+    __shared__ int redi[QPT];
+    __shared__ T hs[QPT];
     __shared__ T fj[QPB];
-    __shared__ T part[8][QPB];
+    __shared__ T part[QPT / 32][QPB];
     // pivot: largest downdated norm, ties to the lowest original column
     double best = -1.0;
     int bl = -1, bo = 1 << 30;
@@ -515,7 +531,7 @@ __global__ void __launch_bounds__(256) bqp_pivot_kernel(BigArgs a, int step) {
         __syncthreads();
         if (threadIdx.x < jj) {
             T v = T(0);
-            for (int w = 0; w < 8; ++w) v += part[w][threadIdx.x];
+            for (int w = 0; w < QPT / 32; ++w) v += part[w][threadIdx.x];
             gq[threadIdx.x] = v;
         }
     }
@@ -651,7 +667,7 @@ cudaError_t big_qp_panel(const BigArgs& a, int ngroups, int max_n, int max_m, in
     bqp_start_kernel<<<(ngroups + 127) / 128, 128, 0, st>>>(a, ngroups);
     for (int jj = 0; jj < a.nb; ++jj, ++step) {
         note_launch();
-        bqp_pivot_kernel<T><<<ngroups, 256, 0, st>>>(a, step);
+        bqp_pivot_kernel<T><<<ngroups, QPT, 0, st>>>(a, step);
         note_launch();
         bqp_f_kernel<T><<<dim3((max_n + 7) / 8, ngroups), 256, 0, st>>>(a, step);
     }
