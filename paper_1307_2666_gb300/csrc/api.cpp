@@ -1093,7 +1093,12 @@ static void run_factor(hif_handle h) {
                     }
                     cudaEventDestroy(e0);
                     cudaEventDestroy(e1);
-                    bk.rc = t16 < t32 ? 16 : 32;
+                    // 16 rows only on a clear win: the choice changes the FP32
+                    // rounding of R, so it should not follow timing noise
+                    bk.rc = t16 < 0.85f * t32 ? 16 : 32;
+                    if (env_int("HIF_TRACE", 0))
+                        std::fprintf(stderr, "[hif] fold autotune width %d: 16 rows %.3f ms, 32 rows %.3f ms -> %d\n",
+                                     bk.w, t16, t32, bk.rc);
                     // the bucket's R must come from the kept variant
                     if (bk.rc == 16) HIF_CUDA((launch_fold<T>(bk.fa, bk.count, bk.w, 1, bk.smem, st, 16)));
                     done[q] = 1;
