@@ -872,6 +872,7 @@ static void run_factor(hif_handle h) {
     // grid: 400 beats 600 by 15% in FP32 and 5% in FP64)
     const int big_elim_n = env_int("HIF_BIG_ELIM", 400);
     const bool trace = env_int("HIF_TRACE", 0) != 0;
+    if (trace) geometry_trace(true, nullptr);
     double flops = 0, evals = 0;
     const double tol_floor = sizeof(T) == 4 ? h->opt.fp32_tol_floor : 0.0;
 
@@ -1322,9 +1323,14 @@ static void run_factor(hif_handle h) {
                          ms(tr2, tr_plan));
             if (!small_boxes.empty())
                 std::fprintf(stderr, "[hif]        fold %.1f ms (ends at the sync)\n", ms(tr0, tr_fold));
-            if (tau + 1 < nsub)
-                std::fprintf(stderr, "[hif]        next plan: partition %.1f ms, near fields and groups %.1f ms\n",
-                             next.ms_partition, next.ms_near);
+            if (tau + 1 < nsub) {
+                double gm[6];
+                geometry_trace(true, gm);
+                std::fprintf(stderr, "[hif]        next plan: partition %.1f ms, near fields and groups %.1f ms "
+                                     "(bins %.1f, gather %.1f; thread ms: proxy %.1f, patterns %.1f, near list %.1f, "
+                                     "groups %.1f)\n",
+                             next.ms_partition, next.ms_near, gm[0], gm[1], gm[2], gm[3], gm[4], gm[5]);
+            }
         }
         h->subs.push_back(std::move(sf));
     }

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <chrono>
 #include <unordered_map>
 #ifdef _OPENMP
 #include <omp.h>
@@ -193,6 +194,14 @@ void partition(const Tree& t, const double* x, int kind, int s, const std::vecto
 
 namespace {
 
+// per-phase time of build_near_groups (trace only)
+bool g_geo_trace = false;
+double g_geo_ms[6] = {0, 0, 0, 0, 0, 0};
+
+inline double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 // Work arrays of one thread of build_near_groups, reused box after box, and
 // the thread's share of the output (boxes in the order the thread took them).
 struct NearScratch {
@@ -200,8 +209,11 @@ struct NearScratch {
     std::vector<int> order, col_pat, pat_data, canon, gid, gfirst;
     std::vector<int64_t> pat_off;
     std::vector<uint64_t> pat_hash;
+    std::vector<uint32_t> mark;   // epoch stamps over all DOFs
+    uint32_t epoch = 0;
     // output arena
     std::vector<int> near, cols, gcol0, gn, gsci;
+    double ms[4] = {0, 0, 0, 0};   // trace: proxy scan, patterns, near list, groups
 };
 
 struct BoxOut {
@@ -210,20 +222,29 @@ struct BoxOut {
     int sci;
 };
 
-inline uint64_t hash_ints(const int* p, int64_t n) {
-    uint64_t h = 1469598103934665603ULL;
-    for (int64_t e = 0; e < n; ++e) {
-        h ^= (uint64_t)(uint32_t)p[e];
-        h *= 1099511628211ULL;
-    }
-    return h ^ (uint64_t)n;
+// a 64-bit mixing function (the splitmix64 finalizer), summed over a set
+// for an order-independent hash
+inline uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
 }
 
 }  // namespace
 
+void geometry_trace(bool on, double* ms) {
+    if (ms)
+        for (int q = 0; q < 6; ++q) ms[q] = g_geo_ms[q];
+    for (double& v : g_geo_ms) v = 0.0;
+    g_geo_trace = on;
+}
+
 void build_near_groups(const Tree& t, const double* x, int s, double proxy_radius, int second_kind,
                        const std::vector<int>& active_ids, const std::vector<char>& active,
                        const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p) {
+    const bool tr = g_geo_trace;
+    const double tb0 = tr ? now_ms() : 0.0;
     const int dim = t.dim;
     const double w = t.W / s;
     const double R = proxy_radius * w;
@@ -264,6 +285,7 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
 #endif
     std::vector<NearScratch> scr(nthr);
     std::vector<BoxOut> bo(nb);
+    const double tb1 = tr ? now_ms() : 0.0;
 
 #pragma omp parallel for schedule(dynamic, 16)
     for (int b = 0; b < nb; ++b) {
@@ -272,6 +294,7 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
         tid = omp_get_thread_num();
 #endif
         NearScratch& S = scr[tid];
+        double c0 = tr ? now_ms() : 0.0;
         const double* ctr = &p.centers[3 * (size_t)b];
         std::vector<int>& nl = S.nl;
         nl.clear();
@@ -299,6 +322,7 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
                     if (dim == 2) break;
                 }
 
+        double c1 = tr ? now_ms() : 0.0;
         // SCI patterns (Sec. 4.3/4.4): the pattern of column j is the set of
         // active DOFs outside the box in the past SCI blocks holding j.  It
         // depends only on j's block ids, so columns are sorted by that tuple
@@ -317,10 +341,23 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
                 }
                 return u < v;
             });
+        // Distinct tuples' patterns are formed with an epoch-stamped mark
+        // array over the DOFs (deduplicated, unsorted) together with an
+        // order-independent hash; equal patterns are found by sorting on
+        // (hash, size) and confirmed element by element with the marks.
+        std::vector<uint32_t>& mark = S.mark;
+        if (mark.size() < box_of.size()) mark.assign(box_of.size(), 0u);
+        auto next_epoch = [&]() {
+            if (++S.epoch == 0) {
+                std::fill(mark.begin(), mark.end(), 0u);
+                S.epoch = 1;
+            }
+            return S.epoch;
+        };
         S.col_pat.assign(nc, 0);
         S.pat_data.clear();
         S.pat_off.assign(1, 0);
-        S.blocks.clear();
+        S.pat_hash.clear();
         int npat = 0;
         for (int e = 0; e < nc; ++e) {
             const int l = order[e];
@@ -328,42 +365,70 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
             if (same)
                 for (int q = 0; q < nsub && same; ++q) same = blk(l, q) == blk(order[e - 1], q);
             if (!same) {
-                const int64_t st = (int64_t)S.pat_data.size();
+                const uint32_t ep = next_epoch();
+                uint64_t h = 0;
                 for (int q = 0; q < nsub; ++q) {
                     const int bid = blk(l, q);
                     if (bid < 0) continue;
-                    S.blocks.push_back(bid);
                     for (int i : sci.members[bid])
-                        if (active[i] && box_of[i] != b) S.pat_data.push_back(i);
+                        if (active[i] && box_of[i] != b && mark[i] != ep) {
+                            mark[i] = ep;
+                            S.pat_data.push_back(i);
+                            h += mix64((uint64_t)(uint32_t)i);
+                        }
                 }
-                std::sort(S.pat_data.begin() + st, S.pat_data.end());
-                S.pat_data.erase(std::unique(S.pat_data.begin() + st, S.pat_data.end()), S.pat_data.end());
                 S.pat_off.push_back((int64_t)S.pat_data.size());
+                S.pat_hash.push_back(h);
                 ++npat;
             }
             S.col_pat[l] = npat - 1;
         }
+        double c2 = tr ? now_ms() : 0.0;
         // the SCI-coupled DOFs of the near field: the union of all patterns
-        nl.insert(nl.end(), S.pat_data.begin(), S.pat_data.end());
+        {
+            const uint32_t ep = next_epoch();
+            for (int i : nl) mark[i] = ep;
+            for (int i : S.pat_data)
+                if (mark[i] != ep) {
+                    mark[i] = ep;
+                    nl.push_back(i);
+                }
+        }
         std::sort(nl.begin(), nl.end());
-        nl.erase(std::unique(nl.begin(), nl.end()), nl.end());
 
+        double c3 = tr ? now_ms() : 0.0;
         bool any = false;
         for (int q = 0; q < npat; ++q) any = any || S.pat_off[q + 1] > S.pat_off[q];
-        // patterns with equal content share a canonical id (hash, then exact)
+        // patterns with equal content share a canonical id
+        auto plen = [&](int q) { return S.pat_off[q + 1] - S.pat_off[q]; };
+        std::vector<int>& byh = S.gid;               // scratch: pattern ids by (hash, size)
+        byh.resize(npat);
+        for (int q = 0; q < npat; ++q) byh[q] = q;
+        std::sort(byh.begin(), byh.end(), [&](int u, int v) {
+            if (S.pat_hash[u] != S.pat_hash[v]) return S.pat_hash[u] < S.pat_hash[v];
+            if (plen(u) != plen(v)) return plen(u) < plen(v);
+            return u < v;
+        });
         S.canon.assign(npat, -1);
-        S.pat_hash.resize(npat);
-        for (int q = 0; q < npat; ++q)
-            S.pat_hash[q] = hash_ints(S.pat_data.data() + S.pat_off[q], S.pat_off[q + 1] - S.pat_off[q]);
-        for (int q = 0; q < npat; ++q) {
-            if (S.canon[q] >= 0) continue;
-            S.canon[q] = q;
-            const int64_t len = S.pat_off[q + 1] - S.pat_off[q];
-            for (int r = q + 1; r < npat; ++r)
-                if (S.canon[r] < 0 && S.pat_hash[r] == S.pat_hash[q] && S.pat_off[r + 1] - S.pat_off[r] == len &&
-                    std::equal(S.pat_data.begin() + S.pat_off[q], S.pat_data.begin() + S.pat_off[q + 1],
-                               S.pat_data.begin() + S.pat_off[r]))
-                    S.canon[r] = q;
+        for (int e0 = 0; e0 < npat;) {
+            int e1 = e0 + 1;
+            while (e1 < npat && S.pat_hash[byh[e1]] == S.pat_hash[byh[e0]] && plen(byh[e1]) == plen(byh[e0])) ++e1;
+            for (int u = e0; u < e1; ++u) {
+                const int q = byh[u];
+                if (S.canon[q] >= 0) continue;
+                S.canon[q] = q;
+                if (u + 1 == e1) break;
+                const uint32_t ep = next_epoch();
+                for (int64_t z = S.pat_off[q]; z < S.pat_off[q + 1]; ++z) mark[S.pat_data[z]] = ep;
+                for (int v = u + 1; v < e1; ++v) {
+                    const int r = byh[v];
+                    if (S.canon[r] >= 0) continue;
+                    bool eq = true;
+                    for (int64_t z = S.pat_off[r]; z < S.pat_off[r + 1] && eq; ++z) eq = mark[S.pat_data[z]] == ep;
+                    if (eq) S.canon[r] = q;
+                }
+            }
+            e0 = e1;
         }
         // groups by pattern, numbered in order of first appearance
         S.gid.assign(nc, 0);
@@ -410,7 +475,15 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
             }
         }
         o.grp1 = (int64_t)S.gn.size();
+        if (tr) {
+            const double c4 = now_ms();
+            S.ms[0] += c1 - c0;
+            S.ms[1] += c2 - c1;
+            S.ms[2] += c3 - c2;
+            S.ms[3] += c4 - c3;
+        }
     }
+    const double tb2 = tr ? now_ms() : 0.0;
     p.near_off.assign(nb + 1, 0);
     for (int b = 0; b < nb; ++b) p.near_off[b + 1] = p.near_off[b] + (bo[b].near1 - bo[b].near0);
     p.near.resize(p.near_off[nb]);
@@ -434,6 +507,12 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
             p.grp_sci[p.grp_off[b] + g] = S.gsci[o.grp0 + g];
         }
         p.box_sci[b] = o.sci;
+    }
+    if (tr) {
+        g_geo_ms[0] += tb1 - tb0;                      // bins and set-up (wall)
+        g_geo_ms[1] += now_ms() - tb2;                 // gather (wall)
+        for (const NearScratch& S : scr)               // per-box phases (thread time)
+            for (int q = 0; q < 4; ++q) g_geo_ms[2 + q] += S.ms[q];
     }
 }
 

@@ -53,4 +53,9 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
                        const std::vector<int>& active_ids, const std::vector<char>& active,
                        const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p);
 
+// Trace of build_near_groups: returns the per-phase times summed since the
+// previous call into ms[6] (bins, gather: wall ms; proxy scan, SCI patterns,
+// near list, groups: thread ms) and sets the collection on or off.
+void geometry_trace(bool on, double* ms);
+
 }  // namespace hif
