@@ -128,7 +128,7 @@ struct Segment {
 };
 
 struct FactorScratch {
-    DevMem d_ed, d_ed_big, d_eg, ews, piv, ldl_fail, gemm_probs;
+    DevMem d_ed, d_ed_big, d_eg, ews, piv, ldl_fail, gemm_probs, elim_order, elim_next;
 };
 
 constexpr int KIND_TOP = 3;   // the top blocks, eliminated as boxes without skeletons
@@ -580,9 +580,22 @@ static void launch_elims(hif_handle h, SubFactor& sf, const std::vector<ElimDesc
     // the LU fallback of LDL boxes can be exercised on any problem
     ea.ldl_alpha = (1.0 + std::sqrt(17.0)) / 8.0;
     if (const char* v = std::getenv("HIF_LDL_TEST_ALPHA")) ea.ldl_alpha = std::atof(v);
+    // work list of the persistent launch: boxes by (k + r)^3 descending
+    {
+        std::vector<int> order(ed.size());
+        for (size_t q = 0; q < ed.size(); ++q) order[q] = (int)q;
+        std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+            return ed[u].k + ed[u].r > ed[v].k + ed[v].r;
+        });
+        upload(S.elim_order, order, st);
+        S.elim_next.ensure(sizeof(int));
+        ea.order = S.elim_order.as<int>();
+        ea.nitems = (int)ed.size();
+        ea.next_item = S.elim_next.as<int>();
+    }
     {
         ProfRange pr(PROF_ELIM, st, work[0], 0.0);
-        HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), st)));
+        HIF_CUDA((launch_elim<T>(ea, (int)ed.size(), h->num_sms, st)));
     }
     if (!ed_big.empty()) {
         upload(S.d_ed_big, ed_big, st);

@@ -585,9 +585,11 @@ __global__ void r_colmajor_kernel(const T* R, int n, T* out) {
 
 // ------------------------------------------------------ elimination ------
 
+// One box of the elimination (a CTA's work item); every return is uniform
+// over the CTA.
 template <typename T>
-__global__ void __launch_bounds__(128) elim_kernel(ElimArgs args) {
-    const ElimDesc ed = args.boxes[blockIdx.x];
+__device__ void elim_box(const ElimArgs& args, int bi) {
+    const ElimDesc ed = args.boxes[bi];
     const int k = ed.k, r = ed.r, n = k + r;
     T* A = static_cast<T*>(args.ws) + ed.ws_off;   // n x n, order (rd, sk), column-major
     T* Tm = A + (int64_t)n * n;          // k x r
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(128) elim_kernel(ElimArgs args) {
         const int res = cta_ldl_diag<T>(r, Arr, ld, piv, Asr, ld, k, redv, redi, (T)args.ldl_alpha);
         if (res != 0) {
             if (threadIdx.x == 0) atomicOr(args.status, res == 2 ? (int)DEV_SINGULAR : (int)DEV_LDL_FALLBACK);
-            if (threadIdx.x == 0 && res == 1) args.ldl_fail[blockIdx.x] = 1;
+            if (threadIdx.x == 0 && res == 1) args.ldl_fail[bi] = 1;
             return;
         }
         // X' = B_sr P^T L^{-T}, then X = X' D^{-1}
@@ -745,6 +747,21 @@ __global__ void __launch_bounds__(128) elim_kernel(ElimArgs args) {
             const int p = piv[j];
             const int t = pm[j]; pm[j] = pm[p]; pm[p] = t;
         }
+    }
+}
+
+// Persistent elimination: the CTAs take boxes from the list (largest first)
+// through an atomic counter until it runs out.
+template <typename T>
+__global__ void __launch_bounds__(128) elim_kernel(ElimArgs args) {
+    __shared__ int item;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(args.next_item, 1);
+        __syncthreads();
+        const int q = item;
+        if (q >= args.nitems) return;
+        elim_box<T>(args, args.order[q]);
     }
 }
 
@@ -887,10 +904,16 @@ cudaError_t launch_id(const IdArgs& a, int ngroups, size_t smem, int num_sms, cu
 }
 
 template <typename T>
-cudaError_t launch_elim(const ElimArgs& a, int nbox, cudaStream_t st) {
+cudaError_t launch_elim(const ElimArgs& a, int nbox, int num_sms, cudaStream_t st) {
     if (nbox == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, elim_kernel<T>, 128, 0);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nbox, std::max(1, per_sm) * std::max(1, num_sms));
+    e = cudaMemsetAsync(a.next_item, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
     note_launch();
-    elim_kernel<T><<<nbox, 128, 0, st>>>(a);
+    elim_kernel<T><<<grid, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -923,8 +946,8 @@ template cudaError_t launch_fold<double>(const FoldArgs&, int, int, int, size_t,
 template cudaError_t launch_fold<float>(const FoldArgs&, int, int, int, size_t, cudaStream_t, int);
 template cudaError_t launch_id<double>(const IdArgs&, int, size_t, int, cudaStream_t);
 template cudaError_t launch_id<float>(const IdArgs&, int, size_t, int, cudaStream_t);
-template cudaError_t launch_elim<double>(const ElimArgs&, int, cudaStream_t);
-template cudaError_t launch_elim<float>(const ElimArgs&, int, cudaStream_t);
+template cudaError_t launch_elim<double>(const ElimArgs&, int, int, cudaStream_t);
+template cudaError_t launch_elim<float>(const ElimArgs&, int, int, cudaStream_t);
 
 }  // namespace hif
 

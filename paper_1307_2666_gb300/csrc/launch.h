@@ -63,6 +63,9 @@ struct ElimArgs {
     int* status;
     int* ldl_fail;          // per box of the launch: 1 when its LDL pivot failed the test
     double ldl_alpha;       // 1 x 1 pivot acceptance constant ((1 + sqrt 17) / 8)
+    const int* order;       // work list: box indices, largest first
+    int nitems;
+    int* next_item;         // atomic counter of the persistent CTAs
 };
 
 struct SweepArgs {
@@ -217,7 +220,7 @@ int fold_cpt(int n, int elem);
 template <typename T>
 cudaError_t launch_fold(const FoldArgs&, int nbox, int threads, int cpt, size_t smem, cudaStream_t, int rc = 0);
 template <typename T> cudaError_t launch_id(const IdArgs&, int ngroups, size_t smem, int num_sms, cudaStream_t);
-template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, cudaStream_t);
+template <typename T> cudaError_t launch_elim(const ElimArgs&, int nbox, int num_sms, cudaStream_t);
 
 // sweeps
 // threads: CTA size, a multiple of 32 up to 512 (the sweep's arithmetic does
