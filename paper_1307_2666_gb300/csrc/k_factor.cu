@@ -204,53 +204,10 @@ __global__ void __launch_bounds__(256, CPT == 1 ? 2 : 1) fold_kernel(FoldArgs ar
                 }
             }
         }
-        // ---- fold the chunk into R: Householder QR of [R; C].  Look-ahead:
-        // the owner of column j + 1 applies reflector j to its column first
-        // and forms reflector j + 1 while the other threads apply reflector j
-        // to theirs, so one barrier per step publishes the next reflector
-        // (double-buffered: buffer (j + 1) & 1 was last read before this
-        // step's barrier).
+        // ---- fold the chunk into R: Householder QR of [R; C]
         T rcur[CPT];
 #pragma unroll
         for (int q = 0; q < CPT; ++q) rcur[q] = threadIdx.x + q * NT < n ? Rcol[q][0] : T(0);
-        // reflector of the column in slot q at row jr, from its chunk entries
-        // and alpha = R[jr][jr]; written to buffer b
-        auto reflect = [&](int q, int jr, T alpha, int b) {
-            T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
-#pragma unroll
-            for (int i = 0; i < RC; i += 4) {
-                q0 += c[q][i] * c[q][i];
-                if (i + 1 < RC) q1 += c[q][i + 1] * c[q][i + 1];
-                if (i + 2 < RC) q2 += c[q][i + 2] * c[q][i + 2];
-                if (i + 3 < RC) q3 += c[q][i + 3] * c[q][i + 3];
-            }
-            const T ss = (q0 + q1) + (q2 + q3);
-            T tau = T(0);
-            if (ss != T(0)) {
-                const T beta = -copysign(sqrt(alpha * alpha + ss), alpha);
-                tau = (beta - alpha) / beta;
-                const T scal = T(1) / (alpha - beta);
-                Rcol[q][jr * rstride] = beta;
-#pragma unroll
-                for (int i = 0; i < RC; ++i) vbuf[b * RC + i] = c[q][i] * scal;
-            }
-            taub[b] = tau;
-        };
-        auto apply = [&](int q, int jr, T tau, const T* v) {
-            T w0 = rcur[q], w1 = T(0), w2 = T(0), w3 = T(0);
-#pragma unroll
-            for (int i = 0; i < RC; i += 4) {
-                w0 += v[i] * c[q][i];
-                if (i + 1 < RC) w1 += v[i + 1] * c[q][i + 1];
-                if (i + 2 < RC) w2 += v[i + 2] * c[q][i + 2];
-                if (i + 3 < RC) w3 += v[i + 3] * c[q][i + 3];
-            }
-            const T w = ((w0 + w1) + (w2 + w3)) * tau;
-            Rcol[q][jr * rstride] = rcur[q] - w;
-#pragma unroll
-            for (int i = 0; i < RC; ++i) c[q][i] -= w * v[i];
-        };
-        if (n > 0 && threadIdx.x == 0) reflect(0, 0, rcur[0], 0);
         for (int j = 0; j < n; ++j) {
             const int buf = j & 1;
             // the next step's R[j + 1][l], read a step ahead (only this thread writes it)
@@ -260,30 +217,59 @@ __global__ void __launch_bounds__(256, CPT == 1 ? 2 : 1) fold_kernel(FoldArgs ar
                 const int l = threadIdx.x + q * NT;
                 rnext[q] = (l < n && j + 1 <= l) ? Rcol[q][(j + 1) * rstride] : T(0);
             }
-            __syncthreads();
-            const T tau = taub[buf];
-            const T* v = vbuf + buf * RC;
-            const int nq = (j + 1) / NT;               // slot of column j + 1 in its owner
-            const bool next_owner = j + 1 < n && threadIdx.x == (j + 1) % NT;
-            if (next_owner) {
+            const int oq = j / NT;                   // the owner's slot
+            if (threadIdx.x == j % NT) {
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
-                    if (q != nq) continue;
-                    if (tau != T(0)) apply(q, j, tau, v);
-                    reflect(q, j + 1, rnext[q], buf ^ 1);
+                    if (q != oq) continue;
+                    T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
+#pragma unroll
+                    for (int i = 0; i < RC; i += 4) {
+                        q0 += c[q][i] * c[q][i];
+                        if (i + 1 < RC) q1 += c[q][i + 1] * c[q][i + 1];
+                        if (i + 2 < RC) q2 += c[q][i + 2] * c[q][i + 2];
+                        if (i + 3 < RC) q3 += c[q][i + 3] * c[q][i + 3];
+                    }
+                    const T ss = (q0 + q1) + (q2 + q3);
+                    T tau = T(0);
+                    if (ss != T(0)) {
+                        const T alpha = rcur[q];
+                        const T beta = -copysign(sqrt(alpha * alpha + ss), alpha);
+                        tau = (beta - alpha) / beta;
+                        const T scal = T(1) / (alpha - beta);
+                        Rcol[q][j * rstride] = beta;
+#pragma unroll
+                        for (int i = 0; i < RC; ++i) vbuf[buf * RC + i] = c[q][i] * scal;
+                    }
+                    taub[buf] = tau;
                 }
             }
+            __syncthreads();
+            const T tau = taub[buf];
             if (tau != T(0)) {
+                const T* v = vbuf + buf * RC;
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     const int l = threadIdx.x + q * NT;
-                    if (l > j && l < n && !(next_owner && q == nq)) apply(q, j, tau, v);
+                    if (l > j && l < n) {
+                        T w0 = rcur[q], w1 = T(0), w2 = T(0), w3 = T(0);
+#pragma unroll
+                        for (int i = 0; i < RC; i += 4) {
+                            w0 += v[i] * c[q][i];
+                            if (i + 1 < RC) w1 += v[i + 1] * c[q][i + 1];
+                            if (i + 2 < RC) w2 += v[i + 2] * c[q][i + 2];
+                            if (i + 3 < RC) w3 += v[i + 3] * c[q][i + 3];
+                        }
+                        const T w = ((w0 + w1) + (w2 + w3)) * tau;
+                        Rcol[q][j * rstride] = rcur[q] - w;
+#pragma unroll
+                        for (int i = 0; i < RC; ++i) c[q][i] -= w * v[i];
+                    }
                 }
             }
 #pragma unroll
             for (int q = 0; q < CPT; ++q) rcur[q] = rnext[q];
         }
-        __syncthreads();
     }
     if (args.R_in_smem)
 #pragma unroll
