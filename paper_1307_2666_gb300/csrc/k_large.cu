@@ -1111,8 +1111,10 @@ __global__ void be_probs_kernel(BatchElimArgs a, int op, TcGemmProb* out) {
 }
 
 // blocked LU of B_rr (Lemma 2.1), panel / interchange+TRSM / update stages
+constexpr int PNT = 512;   // threads of the LU panel kernel (the pivot search spans all rows)
+
 template <typename T>
-__global__ void __launch_bounds__(256) be_panel_kernel(BatchElimArgs a, int j0) {
+__global__ void __launch_bounds__(PNT) be_panel_kernel(BatchElimArgs a, int j0) {
     const int e = blockIdx.x;
     const ElimDesc d = a.ed[e];
     const EBox<T> Bx(a, e);
@@ -1122,8 +1124,8 @@ __global__ void __launch_bounds__(256) be_panel_kernel(BatchElimArgs a, int j0) 
     const int64_t ld = Bx.n;
     T* A = Bx.A;
     int* piv = a.piv + d.piv_out;
-    __shared__ T redv[256];
-    __shared__ int redi[256];
+    __shared__ T redv[PNT];
+    __shared__ int redi[PNT];
     for (int j = j0 + threadIdx.x; j < j0 + nb; j += blockDim.x) piv[j] = j;
     __syncthreads();
     for (int j = j0; j < j0 + nb; ++j) {
@@ -1621,7 +1623,7 @@ cudaError_t big_elim_batch(const BatchElimArgs& a, int max_n, int max_k, int max
     }
     for (int j0 = 0; j0 < max_r; j0 += 32) {
         note_launch();
-        be_panel_kernel<T><<<nb, 256, 0, st>>>(a, j0);
+        be_panel_kernel<T><<<nb, PNT, 0, st>>>(a, j0);
         note_launch();
         be_swap_trsm_kernel<T><<<dim3((max_r + 127) / 128, nb), 128, 0, st>>>(a, j0);
         const int rest = max_r - j0 - 32;
