@@ -163,7 +163,8 @@ def kernel_rooflines(prof, peaks, precision):
              "big_qr_step": ("hbm", hbm, "MEASURED_PEAKS.json hbm_gbs"),
              "big_ygen_kernel": ("hbm", hbm, "MEASURED_PEAKS.json hbm_gbs"),
              "sweep": ("hbm", hbm, "MEASURED_PEAKS.json hbm_gbs"),
-             "direct_sum": ("tensor", tens, "MEASURED_PEAKS.json bf16_tflops_sustained")}
+             "direct_sum": ("tensor", tens, "MEASURED_PEAKS.json bf16_tflops_sustained"),
+             "direct_sum_short": ("tensor", tens, "MEASURED_PEAKS.json bf16_tflops_sustained")}
     out = []
     for name, e in prof.items():
         if not e["ranges"]:

@@ -192,11 +192,31 @@ hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y,
                       int64_t nrhs, int64_t ld);
 
 /*
+ * hif_matvec_digits -- hif_matvec with the tensor-core sum limited to the
+ * digit classes 0..classes-1 (classes = 5 or 6; 8 is hif_matvec itself): the
+ * pairs of table digit s and source digit t with s + t < classes, the shorter
+ * sums that hif_solve_refined's method 0 takes for residuals that do not
+ * decide convergence (Sec. 5 refinement; the full sum decides).  Dropped
+ * pairs are below (classes + 1) 2^(-2 - 8 classes) x 16 max|K| max|c x| per
+ * term, of mean zero over the terms: relative errors of y are ~2e-11
+ * (classes 5) and ~1e-13 (classes 6) on the 2D log-kernel grid.  Problems
+ * without the tensor-core sum (direct_precision != 2, or points not on a full
+ * grid) compute their one sum.  HIF_EINVAL for other class counts.
+ */
+hif_status hif_matvec_digits(hif_handle h, int trans, int classes, const double* x, double* y,
+                             int64_t nrhs, int64_t ld);
+
+/*
  * hif_solve_refined -- solve A u = f (trans = 0) or A^T u = f (trans = 1) to
  * relative residual |f - A u| / |f| <= tol per column, with F^{-1} as right
  * preconditioner: method 0 = iterative refinement u += F^{-1}(f - A u),
  * method 1 = right-preconditioned restarted GMRES(20) with modified
- * Gram-Schmidt (Sec. 5).  Residuals use hif_matvec (FP64 direct sum).
+ * Gram-Schmidt (Sec. 5).  Residuals use hif_matvec (FP64 direct sum); with
+ * the tensor-core sum, method 0 computes the residuals that do not decide
+ * convergence by the short sums of hif_matvec_digits (5 classes for the
+ * first residual of an FP32 factorization, 6 while the predicted residual is
+ * above 10 tol; none when tol < 1e-11 or HIF_SHORT_RESIDUAL=0), and every
+ * residual at or below tol, or at maxit, is recomputed in full.
  *   iters   (may be NULL) receives the largest iteration count over columns
  *   relres  (may be NULL) receives the largest final relative residual
  * Returns HIF_ENOTCONV (with u holding the last iterate) when maxit is reached.
@@ -271,8 +291,9 @@ const char* hif_last_error(void);
 uint64_t hif_kernel_launches(void);
 
 /* Device time of the tensor-core direct-sum kernel (direct_precision = 2),
- * for measurement: while enabled, every launch is bracketed by a pair of CUDA
- * events on its own stream.  Each call returns in *ms the summed event time
+ * for measurement: while enabled, every launch of the full digit set (not the
+ * short sums of hif_matvec_digits) is bracketed by a pair of CUDA events on
+ * its own stream.  Each call returns in *ms the summed event time
  * and in *launches the number of launches recorded since the previous call
  * (either pointer may be NULL), synchronizing on the recorded events, and
  * then sets recording on (enable != 0) or off.  Process-wide; not

@@ -16,6 +16,7 @@ from .hif import (  # noqa: F401
     hif_id_batched,
     hif_kernel_block,
     hif_matvec,
+    hif_matvec_digits,
     hif_options_default,
     hif_solve,
     hif_solve_refined,

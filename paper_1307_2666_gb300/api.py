@@ -153,10 +153,15 @@ class Factorization:
     def apply_transpose(self, x):
         return self._op(_h.hif_apply_transpose, x)
 
-    def matvec(self, x, trans: bool = False):
+    def matvec(self, x, trans: bool = False, classes: int = 8):
+        """A x (or A^T x) by the direct sum; classes 5 or 6 takes the short
+        digit sets of the tensor-core sum (hif_matvec_digits)."""
         xin = _colmajor(self._real_in(x))
         out = _empty_like_cm(xin)
-        _h.hif_matvec(self.h, 1 if trans else 0, xin, out)
+        if classes == 8:
+            _h.hif_matvec(self.h, 1 if trans else 0, xin, out)
+        else:
+            _h.hif_matvec_digits(self.h, 1 if trans else 0, int(classes), xin, out)
         return self._real_out(out)
 
     def solve_refined(self, f, trans: bool = False, tol: float = 1e-10, maxit: int = 50, method: str = "ir"):

@@ -1639,8 +1639,11 @@ static void apply_op(hif_handle h, const double* in, double* out, int64_t nrhs, 
 }
 
 // Direct sum on device arrays, problem by problem (the operator of a handle
-// is block diagonal over its problems).
-static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs) {
+// is block diagonal over its problems).  classes < 8 selects a short digit set
+// of the tensor-core sum (grid problems with direct_precision 2); every other
+// path computes its one sum.
+static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs,
+                       int classes = 8) {
     const cudaStream_t st = h->st;
     for (auto& sp : h->segs) {
         Segment& sg = *sp;
@@ -1681,10 +1684,10 @@ static void matvec_dev(hif_handle h, int trans, const double* x, int64_t ldx, do
                 h->tc_status.ensure(sizeof(int));
                 HIF_CUDA(cudaMemsetAsync(h->tc_status.p, 0, sizeof(int), st));
                 {
-                    ProfRange pr(PROF_DIRECT, st, 2.0 * (double)n * n * nrhs, 0.0);
+                    ProfRange pr(classes == 8 ? PROF_DIRECT : PROF_DIRECT_SHORT, st, 2.0 * (double)n * n * nrhs, 0.0);
                     HIF_CUDA(launch_direct_grid_tc(ga, sg.tc_rows.p, sg.tc_tmax.as<unsigned long long>(), h->tc_xb.p,
                                                    h->tc_xmax.as<unsigned long long>(), h->tc_status.as<int>(),
-                                                   h->num_sms, st));
+                                                   h->num_sms, classes, st));
                 }
                 int flag = 0;
                 HIF_CUDA(cudaMemcpyAsync(&flag, h->tc_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1758,7 +1761,30 @@ static std::vector<double> seg_norms(hif_handle h, const double* v, int nrhs) {
     return out;
 }
 
-// Iterative refinement: u = F^{-1} f; r = f - A u; u += F^{-1} r ...
+// Digit classes of the residual of refinement step k (8: the full sum).  A
+// residual's error enters the next correction, so only the residual that
+// decides convergence has to be the full sum: the others may take a short
+// digit set if its error stays far below the residual itself and below tol.
+// Measured relative errors of the short sums: ~2e-11 (5 classes) and ~1e-13
+// (6 classes).  Step 0 of an FP32 factorization (whose first residual is of
+// the order of its 2^-17 tolerance floor or above) takes 5 classes; a later
+// step takes 6 classes when its predicted residual, the last one times the
+// last contraction (sqrt of the first residual for the first contraction), is
+// above 10 tol; otherwise, and when tol < 1e-11, the full sum.
+static int residual_classes(hif_handle h, int k, const std::vector<double>& hist, double tol) {
+    if (h->opt.direct_precision != 2 || tol < 1e-11 || !env_int("HIF_SHORT_RESIDUAL", 1)) return 8;
+    for (auto& sp : h->segs)
+        if (!sp->grid) return 8;
+    if (k == 0) return h->precision == 1 ? 5 : 6;
+    const double last = hist[k - 1];
+    const double rho = k == 1 ? std::sqrt(hist[0]) : (hist[k - 2] > 0 ? last / hist[k - 2] : 0.0);
+    return last * rho > 10.0 * tol ? 6 : 8;
+}
+
+// Iterative refinement: u = F^{-1} f; r = f - A u; u += F^{-1} r ...  The
+// returned residual is always that of the full sum (a short residual at or
+// below tol, below 1e-6 with 5 classes, or at the last step is recomputed in
+// full).
 static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u, int nrhs, double tol, int maxit,
                             int* iters, double* relres) {
     const int64_t N = h->N;
@@ -1770,13 +1796,22 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
     solve_dev(h, trans, f, u, nrhs);
     int it = 0;
     double worst = 0;
+    std::vector<double> hist;
     for (;; ++it) {
-        matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs);
-        HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, h->st));
-        const std::vector<double> rn = seg_norms(h, r.as<double>(), nrhs);
-        worst = 0;
-        for (size_t q = 0; q < rn.size(); ++q) worst = std::max(worst, fn[q] > 0 ? rn[q] / fn[q] : 0.0);
-        if (env_int("HIF_TRACE", 0)) std::fprintf(stderr, "[hif] refinement %d: relative residual %.3e\n", it, worst);
+        int classes = residual_classes(h, it, hist, tol);
+        for (;;) {
+            matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs, classes);
+            HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, h->st));
+            const std::vector<double> rn = seg_norms(h, r.as<double>(), nrhs);
+            worst = 0;
+            for (size_t q = 0; q < rn.size(); ++q) worst = std::max(worst, fn[q] > 0 ? rn[q] / fn[q] : 0.0);
+            if (env_int("HIF_TRACE", 0))
+                std::fprintf(stderr, "[hif] refinement %d: relative residual %.3e (%d digit classes)\n", it, worst,
+                             classes);
+            if (classes == 8 || (worst > tol && it < maxit && (classes == 6 || worst >= 1e-6))) break;
+            classes = 8;
+        }
+        hist.push_back(worst);
         if (worst <= tol || it >= maxit) break;
         solve_dev(h, trans, r.as<double>(), du.as<double>(), nrhs);
         HIF_CUDA(launch_axpby(N, nrhs, 1.0, du.as<double>(), N, 1.0, u, N, h->st));
@@ -2341,6 +2376,21 @@ hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y, int64
     return guard([&] {
         with_dev_io(h, x, y, nrhs, ld, [&](const double* dx, double* dy) {
             matvec_dev(h, trans ? 1 : 0, dx, h->N, dy, h->N, (int)nrhs);
+        });
+    });
+}
+
+hif_status hif_matvec_digits(hif_handle h, int trans, int classes, const double* x, double* y, int64_t nrhs,
+                             int64_t ld) {
+    if (!h || !x || !y || nrhs < 0 || ld < (h ? h->N : 0) || (classes != 5 && classes != 6 && classes != 8)) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "%s",
+                      "hif_matvec_digits: invalid argument (classes must be 5, 6 or 8)");
+        return HIF_EINVAL;
+    }
+    if (nrhs == 0) return HIF_OK;
+    return guard([&] {
+        with_dev_io(h, x, y, nrhs, ld, [&](const double* dx, double* dy) {
+            matvec_dev(h, trans ? 1 : 0, dx, h->N, dy, h->N, (int)nrhs, classes);
         });
     });
 }

@@ -18,6 +18,16 @@
 // combination of eight class sums.  Table digits 0..6 and source digits
 // 0..7 are kept, and pairs with s + t >= 8 are not formed.
 //
+// Shorter digit sets serve the residuals of the refinement that are not the
+// last one (their error only enters the next correction, which the last,
+// full-digit residual then measures): with KD classes the kernel keeps table
+// and source digits 0..KD-1 and the pairs with s + t < KD.  Per term the
+// dropped part is below (KD + 1) 2^(-2 - 8 KD) of 2^(eT + eX) <= 16 max|t|
+// max|v|, and it behaves like a sum of independent terms of mean zero
+// (round-to-nearest digits): on the 2D log-kernel grid with Gaussian sources
+// the relative error of y is ~2e-11 with KD = 5 and ~1e-13 with KD = 6, at
+// every N from 4096 to 262144 (exact integer convolutions of the digits).
+//
 // On a grid K_ij depends only on the offset i - j, so the kernel block of a
 // tile of 128 targets on one grid line against 128 sources on another line is
 // a Toeplitz matrix in the last coordinate.  With the target rows taken in
@@ -69,22 +79,19 @@ namespace {
 
 constexpr int TM = 128;                         // targets per tile (TMEM lanes)
 constexpr int KC = 128;                         // sources per chunk
-constexpr int ST = 7;                           // table digits
-constexpr int SX = 8;                           // source digits
+constexpr int ST = 7;                           // table digits stored
+constexpr int SX = 8;                           // source digits stored per chunk
 constexpr int NR = 8;                           // right-hand sides per launch
 constexpr int NBLK = (TM + KC) / 8 - 1;         // distinct Hankel core matrices per slice (31)
 constexpr int CM = 144;                         // core-matrix stride: 128 B + 16 B so that the
                                                 // builders' 16-B row stores of consecutive core
                                                 // matrices fall in different bank groups
 constexpr int A_SLICE = NBLK * CM;              // bytes
-constexpr int A_BYTES = ST * A_SLICE;
 constexpr int CHUNK = SX * NR * KC * 2;         // one source chunk: (digit, rhs) rows x KC, BF16
 constexpr int TBLK = NR * KC * 2;               // the rows of one digit of one chunk
 constexpr int NL = 2;                           // target lines per tile
 constexpr int NQ = 2 * NL;                      // source chunks per slot (mirror pair per target line)
-constexpr int B_BYTES = NQ * CHUNK;
-constexpr int STAGE = A_BYTES + B_BYTES;
-constexpr int NST = 2;                          // ring depth
+constexpr int NST_MAX = 3;                      // deepest ring of the variants below
 constexpr int ACCB = 32 * 8;                    // TMEM columns of one accumulator: (class, quarter, rhs)
 constexpr int NACC = 2;                         // accumulators, used slot by slot in turn
 constexpr int ACC = ACCB * NACC;                // TMEM columns allocated
@@ -92,21 +99,36 @@ constexpr int NEPI = 256;                       // epilogue threads
 constexpr int NBUILD = 96;                      // builder threads
 constexpr int NTHR = NEPI + 32 + NBUILD;
 constexpr int CARRY = 32;                       // slots between carry passes of the class sums
-constexpr int NPAIR = ST * NBLK;                // (slice, core matrix) build items per slot
 constexpr long long WAIT_CYCLES = 4000000000LL; // ~2 s at GB300 clocks
 
-static_assert(STAGE % 16 == 0 && A_BYTES % 16 == 0 && TBLK % 16 == 0, "stage alignment");
 static_assert(8 * KC * 128 * 128 <= (1 << 24), "exact FP32 accumulation of one slot");
 // a class sum gains at most 2 columns x 7 pairs x 128 sources x 2^14 per slot
 static_assert(2.0 * 7 * KC * 16384 * CARRY + 2.0 * 16777216 < 2147483647.0, "int32 class sums between carries");
 
-// columns of table digit s: B rows (source digit t, quarter, rhs) for t below
-// nt(s) = ncols(s) / 32 (s + t <= 7 except for the odd counts rounded down),
-// written to the accumulator columns (class s + t, quarter, rhs), i.e. from
-// column 32 s on
-__host__ __device__ constexpr int ncols(int s) { return s == 0 ? 256 : s <= 2 ? 192 : s <= 4 ? 128 : 64; }
+// The variant with KD digit classes (8: every class, the full sum; 5 or 6:
+// the short sums).  Columns of table digit s: B rows (source digit t,
+// quarter, rhs) for t below nt(s) = ncols(s) / 32, written to the accumulator
+// columns (class s + t, quarter, rhs), i.e. from column 32 s on; the full sum
+// takes s + t <= 7 except for the odd counts rounded down, a short one every
+// pair with s + t < KD.
+template <int KD>
+struct Digits {
+    static constexpr int ST = KD == 8 ? 7 : KD;          // table digits read
+    static constexpr int SX = KD;                        // source digits read
+    static constexpr int A_BYTES = ST * A_SLICE;
+    static constexpr int B_BYTES = NQ * SX * TBLK;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int NST = KD == 8 ? 2 : 3;         // ring depth within 227 KB of shared memory
+    static constexpr int NPAIR = ST * NBLK;             // (slice, core matrix) build items per slot
+    __host__ __device__ static constexpr int ncols(int s) {
+        return KD == 8 ? (s == 0 ? 256 : s <= 2 ? 192 : s <= 4 ? 128 : 64) : 32 * (KD - s);
+    }
+    static_assert(STAGE % 16 == 0 && A_BYTES % 16 == 0 && TBLK % 16 == 0, "stage alignment");
+    static_assert(NST <= NST_MAX && NST * STAGE + 1024 + 256 <= 232448, "shared memory");
+    static_assert(ncols(0) == 32 * KD && ncols(ST - 1) >= 32, "column map");
+};
 __host__ __device__ constexpr int coloff(int s) { return 32 * s; }
-static_assert(coloff(6) + ncols(6) <= ACCB && ncols(0) == ACCB, "column map");
+static_assert(coloff(6) + Digits<8>::ncols(6) <= ACCB && Digits<8>::ncols(0) == ACCB, "column map");
 
 __device__ __forceinline__ int scale_exp(unsigned long long maxbits) {
     const double m = __longlong_as_double((long long)maxbits);
@@ -130,9 +152,9 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 
 struct Bars {
-    uint64_t full[NST];         // Hankel operand built (NBUILD arrivals)
-    uint64_t bfull[NST];        // source digits landed (1 arrival + bytes)
-    uint64_t mma_done[NST];
+    uint64_t full[NST_MAX];     // Hankel operand built (NBUILD arrivals)
+    uint64_t bfull[NST_MAX];    // source digits landed (1 arrival + bytes)
+    uint64_t mma_done[NST_MAX];
     uint64_t acc_full[NACC];    // accumulator written (1 commit)
     uint64_t acc_empty[NACC];   // accumulator drained (128 epilogue arrivals)
     uint64_t drain;
@@ -194,7 +216,7 @@ __global__ void tc_table_rows_kernel(const double* table, int n, int64_t lines, 
 // chunk: element (digit t, rhs r, source q) of chunk ch at
 // ((ch * SX + t) * (KC/8) + q/8) * 64 + r * 8 + q % 8 (BF16 units).
 __global__ void tc_source_digits_kernel(const double* v, int64_t N, int n, int64_t lines, int nc, int r0, int nr,
-                                        const unsigned long long* xmax, uint4* XB) {
+                                        int sx, const unsigned long long* xmax, uint4* XB) {
     const int64_t tot = lines * nc * (KC / 8) * NR;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e % NR);
@@ -216,6 +238,7 @@ __global__ void tc_source_digits_kernel(const double* v, int64_t N, int n, int64
         }
 #pragma unroll
         for (int t = 0; t < SX; ++t) {
+            if (t >= sx) break;
             uint4 w;
             w.x = pack2(d[0][t], d[1][t]);
             w.y = pack2(d[2][t], d[3][t]);
@@ -305,7 +328,10 @@ struct Walk {
 
 }  // namespace
 
+template <int KD>
 __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
+    using C = Digits<KD>;
+    constexpr int NST = C::NST, STAGE = C::STAGE, A_BYTES = C::A_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     Bars* bars = (Bars*)(smem + NST * STAGE);
@@ -369,13 +395,13 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
                 // (the first MMA, slice 0 with N = 128, initializes all the
                 // accumulator's columns; the others add into theirs)
 #pragma unroll
-                for (int s = 0; s < ST; ++s) {
+                for (int s = 0; s < C::ST; ++s) {
                     const uint64_t as = a0 + (uint64_t)(s * A_SLICE / 16);
                     const uint32_t d = tmem + ACCB * ab + coloff(s);
 #pragma unroll
                     for (int kk = 0; kk < KC / 16; ++kk)
                         tc::mma_bf16(d, as + (uint64_t)(2 * CM * kk / 16), b0 + (uint64_t)(16 * kk),
-                                     tc::idesc_bf16_f32(TM, ncols(s)), !(s == 0 && kk == 0));
+                                     tc::idesc_bf16_f32(TM, C::ncols(s)), !(s == 0 && kk == 0));
                 }
                 tc::mma_commit(&bars->mma_done[st]);
                 tc::mma_commit(&bars->acc_full[ab]);
@@ -397,6 +423,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
         // each thread owns up to PPT (slice, core matrix) items per slot; the
         // 16 digits of every item are fetched one slot ahead, so the L2
         // latency overlaps the build of the current slot
+        constexpr int NPAIR = C::NPAIR;
         constexpr int PPT = (NPAIR + NBUILD - 1) / NBUILD;
         const int bt = threadIdx.x - (NEPI + 32);
         uint4 cur[PPT][2], nxt[PPT][2];
@@ -432,14 +459,14 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
             if (bt == 0) {
                 // source digits of the four chunks, digit block by digit
                 // block into rows (digit, quarter, rhs); a missing line reads zeros
-                tc::mbar_arrive_expect_tx(&bars->bfull[st], B_BYTES);
+                tc::mbar_arrive_expect_tx(&bars->bfull[st], C::B_BYTES);
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
                     const int64_t J = w.src_line(q);
                     const int64_t chunk = J >= 0 ? J * a.nc + w.c : zero_chunk;
                     const unsigned char* src = a.XB + chunk * (int64_t)CHUNK;
 #pragma unroll
-                    for (int t = 0; t < SX; ++t)
+                    for (int t = 0; t < C::SX; ++t)
                         tc::bulk_g2s(a_st + A_BYTES + (NQ * t + q) * TBLK, src + t * TBLK, TBLK, &bars->bfull[st]);
                 }
                 ++issued;
@@ -490,12 +517,12 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
         // warp w: target line w / 4 of the tile, TMEM lane quarter w % 4
         const int ln = warp >> 2, quad = warp & 3;
         long long s0[NR];          // class 0
-        int sk[7][NR];             // classes 1..7
+        int sk[KD - 1][NR];        // classes 1..KD-1
         auto carry = [&]() {
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
 #pragma unroll
-                for (int k = 6; k >= 1; --k) {
+                for (int k = KD - 2; k >= 1; --k) {
                     const int c = sk[k][r] >> 8;
                     sk[k][r] -= c * 256;
                     sk[k - 1][r] += c;
@@ -509,7 +536,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
         for (int r = 0; r < NR; ++r) {
             s0[r] = 0;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) sk[k][r] = 0;
+            for (int k = 0; k < KD - 1; ++k) sk[k][r] = 0;
         }
         const int eT = scale_exp(*a.tmax);
         int64_t si = 0;                                        // slots drained
@@ -528,7 +555,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
                 // class k of this line: columns 32 k + 16 ln + (h, rhs)
                 const uint32_t tbase = tmem + ACCB * ab + 16 * ln + ((uint32_t)(32 * quad) << 16);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < KD; ++k) {
                     float v[16];
                     tc::tmem_ld16(tbase + 32 * k, v);
 #pragma unroll
@@ -550,9 +577,9 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     if (r < a.nr) {
-                        double y = 0.0, wt = 1.0 / 72057594037927936.0;          // 2^-56
+                        double y = 0.0, wt = ldexp(1.0, -8 * (KD - 1));
 #pragma unroll
-                        for (int k = 7; k >= 1; --k, wt *= 256.0) y += (double)sk[k - 1][r] * wt;
+                        for (int k = KD - 1; k >= 1; --k, wt *= 256.0) y += (double)sk[k - 1][r] * wt;
                         y += (double)s0[r];
                         a.ybuf[gpos + a.N * (a.r0 + r)] = ldexp(y, eT + scale_exp(a.xmax[r]) - 16);
                     }
@@ -562,7 +589,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_conv_kernel(TcConvArgs a) {
             for (int r = 0; r < NR; ++r) {
                 s0[r] = 0;
 #pragma unroll
-                for (int k = 0; k < 7; ++k) sk[k][r] = 0;
+                for (int k = 0; k < KD - 1; ++k) sk[k][r] = 0;
             }
         }
     }
@@ -635,19 +662,39 @@ cudaError_t launch_tc_table(const double* table, int n, int dim, unsigned long l
     return cudaGetLastError();
 }
 
+namespace {
+// the kernel variant of KD digit classes and its shared-memory size (the
+// opt-in above 48 KB is set once per variant)
+template <int KD>
+cudaError_t tc_variant(void (**fn)(TcConvArgs), size_t* smem) {
+    static bool attr_set = false;
+    *fn = tc_conv_kernel<KD>;
+    *smem = (size_t)Digits<KD>::NST * Digits<KD>::STAGE + sizeof(Bars) + 1024;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tc_conv_kernel<KD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)*smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const unsigned long long* tmax,
-                                  void* XB, unsigned long long* xmax, int* status, int num_sms, cudaStream_t st) {
+                                  void* XB, unsigned long long* xmax, int* status, int num_sms, int classes,
+                                  cudaStream_t st) {
     const int64_t N = a.dim == 2 ? (int64_t)a.n * a.n : (int64_t)a.n * a.n * a.n;
     if (N == 0) return cudaSuccess;
+    if (classes != 5 && classes != 6 && classes != 8) return cudaErrorInvalidValue;
     const int nc = (a.n + KC - 1) / KC, nb = (a.n + TM - 1) / TM;
     const int64_t lines = a.dim == 2 ? (int64_t)a.n : (int64_t)a.n * a.n;
     const int eb = (int)std::min<int64_t>((N * a.nrhs + 255) / 256, 152 * 16);
-    static bool attr_set = false;
-    const size_t smem = (size_t)NST * STAGE + sizeof(Bars) + 1024;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void (*kfn)(TcConvArgs) = nullptr;
+    size_t smem = 0;
+    {
+        cudaError_t e = classes == 8 ? tc_variant<8>(&kfn, &smem)
+                        : classes == 6 ? tc_variant<6>(&kfn, &smem) : tc_variant<5>(&kfn, &smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     grid_scatter_kernel_launch(a, N, eb, st);
     {
@@ -664,7 +711,7 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
         const int64_t items = lines * nc * (KC / 8) * NR;
         note_launch();
         tc_source_digits_kernel<<<(int)std::min<int64_t>((items + 255) / 256, 152 * 16), 256, 0, st>>>(
-            a.vbuf, N, a.n, lines, nc, r0, nr, xmax, (uint4*)XB);
+            a.vbuf, N, a.n, lines, nc, r0, nr, classes, xmax, (uint4*)XB);
         TcConvArgs t{};
         t.R = (const __nv_bfloat16*)R;
         t.XB = (const unsigned char*)XB;
@@ -692,7 +739,8 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         {
             std::lock_guard<std::mutex> lk(g_tm_mu);
-            if (g_tm_on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+            if (g_tm_on && classes == 8 && cudaEventCreate(&e0) == cudaSuccess &&
+                cudaEventCreate(&e1) == cudaSuccess) {
                 cudaEventRecord(e0, st);
                 g_tm_ev.emplace_back(e0, e1);
             } else {
@@ -700,7 +748,7 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
             }
         }
         note_launch();
-        tc_conv_kernel<<<grid, NTHR, smem, st>>>(t);
+        kfn<<<grid, NTHR, smem, st>>>(t);
         if (e1) cudaEventRecord(e1, st);
     }
     grid_finish_kernel_launch(a, N, eb, st);

@@ -321,8 +321,11 @@ cudaError_t launch_tc_table(const double* table, int n, int dim, unsigned long l
 // CUDA-event timing of tc_conv_kernel launches (see hif_kernel_timing)
 void tc_timing_set(bool enable);
 cudaError_t tc_timing_collect(double* ms, int64_t* launches);
+// classes: digit classes kept (8: the full sum; 6 or 5: the shorter sums of
+// the refinement's intermediate residuals)
 cudaError_t launch_direct_grid_tc(const GridDirectArgs&, const void* R, const unsigned long long* tmax,
-                                  void* XB, unsigned long long* xmax, int* status, int num_sms, cudaStream_t);
+                                  void* XB, unsigned long long* xmax, int* status, int num_sms, int classes,
+                                  cudaStream_t);
 cudaError_t launch_grid_table(double* table, int n, int dim, double h, int kernel_id, double kself_over_w,
                               cudaStream_t);
 

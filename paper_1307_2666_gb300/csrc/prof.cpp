@@ -19,7 +19,7 @@ double g_flops[PROF_COUNT] = {};
 double g_bytes[PROF_COUNT] = {};
 const char* const kNames[PROF_COUNT] = {
     "fold_kernel", "id_kernel", "elim_kernel", "big_ygen_kernel", "big_rho", "big_qr_step",
-    "big_T_kernel", "big_elim_batch", "sweep", "direct_sum"};
+    "big_T_kernel", "big_elim_batch", "sweep", "direct_sum", "direct_sum_short"};
 }  // namespace
 
 bool prof_enabled() { return g_on.load(std::memory_order_relaxed); }

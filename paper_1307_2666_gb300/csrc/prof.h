@@ -23,6 +23,7 @@ enum ProfKind {
     PROF_BIG_ELIM,      // batched multi-CTA elimination of large boxes
     PROF_SWEEP,         // one full solve/apply sweep (all sublevels, both passes)
     PROF_DIRECT,        // direct sum (one launch per block of right-hand sides)
+    PROF_DIRECT_SHORT,  // tensor-core direct sum with a short digit set (intermediate residuals)
     PROF_COUNT
 };
 

@@ -116,6 +116,7 @@ EXPORTS = {
     "hif_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "hif_solve_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "hif_matvec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
+    "hif_matvec_digits": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64]),
     "hif_solve_refined": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                     C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "hif_adjoint_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
@@ -262,6 +263,12 @@ def hif_solve_transpose(h, b, x):
 def hif_matvec(h, trans: int, x, y):
     ld, nrhs = _ld(x)
     _check(load().hif_matvec(h, int(trans), _ptr(x), _ptr(y), nrhs, ld), "hif_matvec")
+    return y
+
+
+def hif_matvec_digits(h, trans: int, classes: int, x, y):
+    ld, nrhs = _ld(x)
+    _check(load().hif_matvec_digits(h, int(trans), int(classes), _ptr(x), _ptr(y), nrhs, ld), "hif_matvec_digits")
     return y
 
 

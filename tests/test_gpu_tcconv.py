@@ -141,3 +141,69 @@ def test_tc_sum_bounded_wait_reports_timeout_and_context_survives(P):
     op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
     close_cols(fac.matvec(T(x)).cpu().numpy(), op.matvec(x))
     fac.close()
+
+
+# ---- short digit sets (the refinement's intermediate residuals) -------------
+
+def _short_bounds(pb, x, classes, trans):
+    """Per-term bound of the pairs a short sum drops, from the oracle's K
+    (b = c = 1): (classes + 1) 2^(-2 - 8 classes) x 2^(eT + eX), with
+    2^(eT + eX) <= 16 max|K| max|s x| per column (s = c, or b for A^T), and
+    2% for the classes further down."""
+    one = np.ones(pb.N)
+    K0 = kernels.Operator(pb.points, pb.weights, pb.a, one, one, 0).kernel_entries(np.array([0]), np.arange(pb.N))
+    kmax = np.abs(K0).max()                  # on the grid every |offset| occurs in row 0
+    vmax = np.abs((pb.b if trans else pb.c)[:, None] * x).max(axis=0)
+    return 1.02 * (classes + 1) * 2.0 ** (-2 - 8 * classes) * 16.0 * kmax * vmax
+
+
+@pytest.mark.parametrize("classes", [5, 6])
+@pytest.mark.parametrize("n,nrhs", [(100, 3), (130, 11)])
+def test_short_sums_within_their_bounds(P, n, nrhs, classes):
+    # the kernel part of the error, (A_short x - A x) / b (or / c for A^T),
+    # against the dropped pairs: every entry below N per-term bounds (worst
+    # case) and, as a sum of N terms of mean zero, every entry below
+    # 8 sqrt(N) and the column norm below N per-term bounds
+    pb = hi.volume_problem(n, 2, smooth_seed=1002 + n)
+    x = hi.gaussian_rhs(pb.N, nrhs, 40 + n)
+    fac = handle(P, pb)
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    N = pb.N
+    for trans in (False, True):
+        beta = _short_bounds(pb, x, classes, trans)
+        y = fac.matvec(T(x), trans=trans, classes=classes).cpu().numpy()
+        ref = op.matvec(x, trans=trans)
+        ek = np.abs(y - ref) / np.abs((pb.c if trans else pb.b)[:, None])
+        assert np.all(ek.max(axis=0) <= N * beta)
+        assert np.all(ek.max(axis=0) <= 8.0 * np.sqrt(N) * beta), ek.max(axis=0) / (np.sqrt(N) * beta)
+        assert np.all(np.linalg.norm(ek, axis=0) <= N * beta)
+        # the short kernel ran: its result is not the full sum's
+        full = fac.matvec(T(x), trans=trans).cpu().numpy()
+        assert np.any(full != y)
+    fac.close()
+
+
+def test_refinement_short_residuals_reach_the_full_residual(P, capfd, monkeypatch):
+    # FP32 factor, 4 RHS: the refinement with short intermediate residuals
+    # and with every residual in full reach the same iteration count, and the
+    # returned residual (always a full sum) is the oracle's at the returned u
+    n = 128
+    pb = hi.volume_problem(n, 2, smooth_seed=1002, rhs_seed=1003, nrhs=4)
+    fac = handle(P, pb, eps=1e-6)
+    monkeypatch.setenv("HIF_TRACE", "1")
+    u_s, its_s, rel_s = fac.solve_refined(T(pb.f), tol=1e-10)
+    trace = capfd.readouterr().err
+    monkeypatch.setenv("HIF_SHORT_RESIDUAL", "0")
+    u_f, its_f, rel_f = fac.solve_refined(T(pb.f), tol=1e-10)
+    trace_f = capfd.readouterr().err
+    assert "(5 digit classes)" in trace and "(8 digit classes)" in trace
+    assert "(5 digit classes)" not in trace_f and "(6 digit classes)" not in trace_f
+    assert its_s == its_f and rel_s <= 1e-10 and rel_f <= 1e-10
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    u = u_s.cpu().numpy()
+    r = pb.f - op.matvec(u)
+    rel = np.max(np.linalg.norm(r, axis=0) / np.linalg.norm(pb.f, axis=0))
+    assert abs(rel - rel_s) <= 1e-3 * rel_s + 1e-16
+    uf = u_f.cpu().numpy()
+    assert np.linalg.norm(u - uf) <= 1e-9 * np.linalg.norm(uf)
+    fac.close()
