@@ -193,13 +193,14 @@ hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y,
 
 /*
  * hif_matvec_digits -- hif_matvec with the tensor-core sum limited to the
- * digit classes 0..classes-1 (classes = 5 or 6; 8 is hif_matvec itself): the
+ * digit classes 0..classes-1 (classes = 4, 5 or 6; 8 is hif_matvec itself): the
  * pairs of table digit s and source digit t with s + t < classes, the shorter
  * sums that hif_solve_refined's method 0 takes for residuals that do not
  * decide convergence (Sec. 5 refinement; the full sum decides).  Dropped
  * pairs are below (classes + 1) 2^(-2 - 8 classes) x 16 max|K| max|c x| per
- * term, of mean zero over the terms: relative errors of y are ~2e-11
- * (classes 5) and ~1e-13 (classes 6) on the 2D log-kernel grid.  Problems
+ * term, of mean zero over the terms: relative errors of y are ~6e-9
+ * (classes 4), ~2e-11 (classes 5) and ~1e-13 (classes 6) on the 2D
+ * log-kernel grid with Gaussian sources.  Problems
  * without the tensor-core sum (direct_precision != 2, or points not on a full
  * grid) compute their one sum.  HIF_EINVAL for other class counts.
  */
@@ -213,10 +214,13 @@ hif_status hif_matvec_digits(hif_handle h, int trans, int classes, const double*
  * method 1 = right-preconditioned restarted GMRES(20) with modified
  * Gram-Schmidt (Sec. 5).  Residuals use hif_matvec (FP64 direct sum); with
  * the tensor-core sum, method 0 computes the residuals that do not decide
- * convergence by the short sums of hif_matvec_digits (5 classes for the
- * first residual of an FP32 factorization, 6 while the predicted residual is
- * above 10 tol; none when tol < 1e-11 or HIF_SHORT_RESIDUAL=0), and every
- * residual at or below tol, or at maxit, is recomputed in full.
+ * convergence by the short sums of hif_matvec_digits: the first residual
+ * with 5 classes (FP32 factorization) or 6 (FP64), a later one, while its
+ * predicted size is above 10 tol, with the fewest classes whose estimated
+ * error (the sum's relative error times |b K c u| / |f|) stays below
+ * 0.05 tol and 1e-4 of the residual; none when tol < 1e-11 or
+ * HIF_SHORT_RESIDUAL=0.  Every residual at or below tol, at maxit, or whose
+ * error estimate misses that bound is recomputed in full.
  *   iters   (may be NULL) receives the largest iteration count over columns
  *   relres  (may be NULL) receives the largest final relative residual
  * Returns HIF_ENOTCONV (with u holding the last iterate) when maxit is reached.

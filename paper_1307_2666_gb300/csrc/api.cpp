@@ -1761,30 +1761,47 @@ static std::vector<double> seg_norms(hif_handle h, const double* v, int nrhs) {
     return out;
 }
 
-// Digit classes of the residual of refinement step k (8: the full sum).  A
-// residual's error enters the next correction, so only the residual that
-// decides convergence has to be the full sum: the others may take a short
-// digit set if its error stays far below the residual itself and below tol.
-// Measured relative errors of the short sums: ~2e-11 (5 classes) and ~1e-13
-// (6 classes).  Step 0 of an FP32 factorization (whose first residual is of
-// the order of its 2^-17 tolerance floor or above) takes 5 classes; a later
-// step takes 6 classes when its predicted residual, the last one times the
-// last contraction (sqrt of the first residual for the first contraction), is
-// above 10 tol; otherwise, and when tol < 1e-11, the full sum.
-static int residual_classes(hif_handle h, int k, const std::vector<double>& hist, double tol) {
-    if (h->opt.direct_precision != 2 || tol < 1e-11 || !env_int("HIF_SHORT_RESIDUAL", 1)) return 8;
+// Short digit sets for the residuals of the refinement.  A residual computed
+// with an error d enters the next one in full (r' = (I - A F^{-1}) r - d), so
+// only the residual that decides convergence has to be the full sum; another
+// may take KD < 8 digit classes while its error stays below both 0.05 tol and
+// 1e-4 of the residual itself (an FP32 factor contracts by >= 1e-3 per step,
+// so the next residual keeps at least ~10x that margin).  The error of a short
+// sum is estimated as c_KD Y: c_KD the relative error of y = K v for Gaussian
+// sources (the worst case measured: ~6e-9, ~2e-11, ~1e-13 for KD = 4, 5, 6,
+// taken with a factor 5 of margin) and Y = |b K c u| / |f|, the size of the
+// kernel part of A u, measured after every residual.
+static constexpr double kShortErr[3] = {3e-8, 1.5e-10, 6e-13};     // KD = 4, 5, 6
+
+static bool short_residuals_on(hif_handle h, double tol) {
+    if (h->opt.direct_precision != 2 || tol < 1e-11 || !env_int("HIF_SHORT_RESIDUAL", 1)) return false;
     for (auto& sp : h->segs)
-        if (!sp->grid) return 8;
+        if (!sp->grid) return false;
+    return true;
+}
+
+// Digit classes of residual k (8: the full sum).  Step 0 has no Y yet and
+// takes 5 classes after an FP32 factorization (its first residual is of the
+// order of the 2^-17 tolerance floor or above), 6 after an FP64 one; step k >= 1
+// takes the fewest classes whose estimated error meets the bound above for its
+// predicted residual, the last one times the last contraction (sqrt of the
+// first residual for the first contraction), if that prediction is above
+// 10 tol, and the full sum otherwise.
+static int residual_classes(hif_handle h, int k, const std::vector<double>& hist, double Y, double tol) {
     if (k == 0) return h->precision == 1 ? 5 : 6;
     const double last = hist[k - 1];
     const double rho = k == 1 ? std::sqrt(hist[0]) : (hist[k - 2] > 0 ? last / hist[k - 2] : 0.0);
-    return last * rho > 10.0 * tol ? 6 : 8;
+    const double pred = last * rho;
+    if (!(pred > 10.0 * tol)) return 8;
+    for (int kd = 4; kd <= 6; ++kd)
+        if (kShortErr[kd - 4] * Y <= std::max(0.05 * tol, 1e-4 * pred)) return kd;
+    return 8;
 }
 
 // Iterative refinement: u = F^{-1} f; r = f - A u; u += F^{-1} r ...  The
-// returned residual is always that of the full sum (a short residual at or
-// below tol, below 1e-6 with 5 classes, or at the last step is recomputed in
-// full).
+// returned residual is always that of the full sum: a short residual at or
+// below tol, at the last step, or whose estimated error misses the bound for
+// the residual it found is recomputed in full.
 static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u, int nrhs, double tol, int maxit,
                             int* iters, double* relres) {
     const int64_t N = h->N;
@@ -1794,21 +1811,31 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
     // relative residuals are judged per problem and per column
     const std::vector<double> fn = seg_norms(h, f, nrhs);
     solve_dev(h, trans, f, u, nrhs);
+    const bool shorts = short_residuals_on(h, tol);
     int it = 0;
-    double worst = 0;
+    double worst = 0, Y = 0;
     std::vector<double> hist;
     for (;; ++it) {
-        int classes = residual_classes(h, it, hist, tol);
+        int classes = shorts ? residual_classes(h, it, hist, Y, tol) : 8;
         for (;;) {
             matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs, classes);
             HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, h->st));
             const std::vector<double> rn = seg_norms(h, r.as<double>(), nrhs);
             worst = 0;
             for (size_t q = 0; q < rn.size(); ++q) worst = std::max(worst, fn[q] > 0 ? rn[q] / fn[q] : 0.0);
+            if (shorts) {
+                // Y: the kernel part f - r - a u against f (du is free until the correction)
+                HIF_CUDA(launch_kpart(N, nrhs, f, r.as<double>(), h->a.as<double>(), u, du.as<double>(), h->st));
+                const std::vector<double> yn = seg_norms(h, du.as<double>(), nrhs);
+                Y = 0;
+                for (size_t q = 0; q < yn.size(); ++q) Y = std::max(Y, fn[q] > 0 ? yn[q] / fn[q] : 0.0);
+            }
             if (env_int("HIF_TRACE", 0))
-                std::fprintf(stderr, "[hif] refinement %d: relative residual %.3e (%d digit classes)\n", it, worst,
-                             classes);
-            if (classes == 8 || (worst > tol && it < maxit && (classes == 6 || worst >= 1e-6))) break;
+                std::fprintf(stderr, "[hif] refinement %d: relative residual %.3e (%d digit classes, |bKcu|/|f| %.2e)\n",
+                             it, worst, classes, Y);
+            if (classes == 8 ||
+                (worst > tol && it < maxit && kShortErr[classes - 4] * Y <= std::max(0.05 * tol, 1e-4 * worst)))
+                break;
             classes = 8;
         }
         hist.push_back(worst);
@@ -2382,9 +2409,9 @@ hif_status hif_matvec(hif_handle h, int trans, const double* x, double* y, int64
 
 hif_status hif_matvec_digits(hif_handle h, int trans, int classes, const double* x, double* y, int64_t nrhs,
                              int64_t ld) {
-    if (!h || !x || !y || nrhs < 0 || ld < (h ? h->N : 0) || (classes != 5 && classes != 6 && classes != 8)) {
+    if (!h || !x || !y || nrhs < 0 || ld < (h ? h->N : 0) || classes < 4 || classes == 7 || classes > 8) {
         std::snprintf(g_last_error, sizeof(g_last_error), "%s",
-                      "hif_matvec_digits: invalid argument (classes must be 5, 6 or 8)");
+                      "hif_matvec_digits: invalid argument (classes must be 4, 5, 6 or 8)");
         return HIF_EINVAL;
     }
     if (nrhs == 0) return HIF_OK;

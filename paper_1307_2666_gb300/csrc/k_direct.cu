@@ -497,6 +497,22 @@ cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int
     return cudaGetLastError();
 }
 
+// The kernel part b K c u of A u from a residual r = f - A u: out = f - r - a u
+// (ld = N everywhere).
+__global__ void kpart_kernel(int64_t N, int nrhs, const double* f, const double* r, const double* a, const double* u,
+                             double* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * nrhs; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = f[e] - r[e] - a[e % N] * u[e];
+}
+
+cudaError_t launch_kpart(int64_t N, int nrhs, const double* f, const double* r, const double* a, const double* u,
+                         double* out, cudaStream_t st) {
+    if (N * nrhs == 0) return cudaSuccess;
+    note_launch();
+    kpart_kernel<<<(int)std::min<int64_t>((N * nrhs + 255) / 256, 152 * 16), 256, 0, st>>>(N, nrhs, f, r, a, u, out);
+    return cudaGetLastError();
+}
+
 // Coefficient gradients of the adjoint method for L(u), A u = f, per DOF i and
 // summed over the columns: ga_i = -sum lam u, gb_i = -sum lam (F u - a u)_i / b_i,
 // gc_i = -sum u (F^T lam - a lam)_i / c_i (F u - a u stands for b K c u, F^T lam

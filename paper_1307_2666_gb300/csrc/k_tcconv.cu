@@ -20,13 +20,14 @@
 //
 // Shorter digit sets serve the residuals of the refinement that are not the
 // last one (their error only enters the next correction, which the last,
-// full-digit residual then measures): with KD classes the kernel keeps table
-// and source digits 0..KD-1 and the pairs with s + t < KD.  Per term the
-// dropped part is below (KD + 1) 2^(-2 - 8 KD) of 2^(eT + eX) <= 16 max|t|
-// max|v|, and it behaves like a sum of independent terms of mean zero
+// full-digit residual then measures): with KD classes (4, 5 or 6) the kernel
+// keeps table and source digits 0..KD-1 and the pairs with s + t < KD.  Per
+// term the dropped part is below (KD + 1) 2^(-2 - 8 KD) of 2^(eT + eX) <= 16
+// max|t| max|v|, and it behaves like a sum of independent terms of mean zero
 // (round-to-nearest digits): on the 2D log-kernel grid with Gaussian sources
-// the relative error of y is ~2e-11 with KD = 5 and ~1e-13 with KD = 6, at
-// every N from 4096 to 262144 (exact integer convolutions of the digits).
+// the relative error of y is ~6e-9 with KD = 4, ~2e-11 with KD = 5 and ~1e-13
+// with KD = 6, at every N from 4096 to 262144 (exact integer convolutions of
+// the digits).
 //
 // On a grid K_ij depends only on the offset i - j, so the kernel block of a
 // tile of 128 targets on one grid line against 128 sources on another line is
@@ -105,8 +106,8 @@ static_assert(8 * KC * 128 * 128 <= (1 << 24), "exact FP32 accumulation of one s
 // a class sum gains at most 2 columns x 7 pairs x 128 sources x 2^14 per slot
 static_assert(2.0 * 7 * KC * 16384 * CARRY + 2.0 * 16777216 < 2147483647.0, "int32 class sums between carries");
 
-// The variant with KD digit classes (8: every class, the full sum; 5 or 6:
-// the short sums).  Columns of table digit s: B rows (source digit t,
+// The variant with KD digit classes (8: every class, the full sum; 4, 5 or
+// 6: the short sums).  Columns of table digit s: B rows (source digit t,
 // quarter, rhs) for t below nt(s) = ncols(s) / 32, written to the accumulator
 // columns (class s + t, quarter, rhs), i.e. from column 32 s on; the full sum
 // takes s + t <= 7 except for the odd counts rounded down, a short one every
@@ -685,15 +686,17 @@ cudaError_t launch_direct_grid_tc(const GridDirectArgs& a, const void* R, const 
                                   cudaStream_t st) {
     const int64_t N = a.dim == 2 ? (int64_t)a.n * a.n : (int64_t)a.n * a.n * a.n;
     if (N == 0) return cudaSuccess;
-    if (classes != 5 && classes != 6 && classes != 8) return cudaErrorInvalidValue;
+    if (classes < 4 || classes == 7 || classes > 8) return cudaErrorInvalidValue;
     const int nc = (a.n + KC - 1) / KC, nb = (a.n + TM - 1) / TM;
     const int64_t lines = a.dim == 2 ? (int64_t)a.n : (int64_t)a.n * a.n;
     const int eb = (int)std::min<int64_t>((N * a.nrhs + 255) / 256, 152 * 16);
     void (*kfn)(TcConvArgs) = nullptr;
     size_t smem = 0;
     {
-        cudaError_t e = classes == 8 ? tc_variant<8>(&kfn, &smem)
-                        : classes == 6 ? tc_variant<6>(&kfn, &smem) : tc_variant<5>(&kfn, &smem);
+        cudaError_t e = classes == 8   ? tc_variant<8>(&kfn, &smem)
+                        : classes == 6 ? tc_variant<6>(&kfn, &smem)
+                        : classes == 5 ? tc_variant<5>(&kfn, &smem)
+                                       : tc_variant<4>(&kfn, &smem);
         if (e != cudaSuccess) return e;
     }
     grid_scatter_kernel_launch(a, N, eb, st);

@@ -321,8 +321,8 @@ cudaError_t launch_tc_table(const double* table, int n, int dim, unsigned long l
 // CUDA-event timing of tc_conv_kernel launches (see hif_kernel_timing)
 void tc_timing_set(bool enable);
 cudaError_t tc_timing_collect(double* ms, int64_t* launches);
-// classes: digit classes kept (8: the full sum; 6 or 5: the shorter sums of
-// the refinement's intermediate residuals)
+// classes: digit classes kept (8: the full sum; 6, 5 or 4: the shorter sums
+// of the refinement's intermediate residuals)
 cudaError_t launch_direct_grid_tc(const GridDirectArgs&, const void* R, const unsigned long long* tmax,
                                   void* XB, unsigned long long* xmax, int* status, int num_sms, int classes,
                                   cudaStream_t);
@@ -337,6 +337,8 @@ cudaError_t launch_kself(const GeomDev& g, double* kself, cudaStream_t);
 cudaError_t launch_adjoint_coef(int64_t N, int nrhs, const double* a, const double* b, const double* c,
                                 const double* u, const double* lam, const double* Fu, const double* Ftl, double* ga,
                                 double* gb, double* gc, int* bad, cudaStream_t st);
+cudaError_t launch_kpart(int64_t N, int nrhs, const double* f, const double* r, const double* a, const double* u,
+                         double* out, cudaStream_t);
 cudaError_t launch_axpby(int64_t N, int nrhs, double alpha, const double* x, int64_t ldx, double beta,
                          double* y, int64_t ldy, cudaStream_t);
 cudaError_t launch_seg_dots(int nseg, const int64_t* off, const int64_t* cnt, int nrhs, const double* x, int64_t ldx,

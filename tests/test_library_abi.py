@@ -103,7 +103,7 @@ def test_status_strings_and_argument_errors(lib):
     assert L.hif_eliminated_dofs(None, 0, None, 0, ctypes.byref(cnt)) == hif.HIF_EINVAL
     assert L.hif_adjoint_gradients(None, None, None, 1, 1, None, None, None) == hif.HIF_EINVAL
     assert L.hif_matvec_digits(None, 0, 6, None, None, 1, 1) == hif.HIF_EINVAL
-    assert b"classes must be 5, 6 or 8" in L.hif_last_error()
+    assert b"classes must be 4, 5, 6 or 8" in L.hif_last_error()
     # a symmetric option outside {0, 1} is rejected before any device work
     o = hif.hif_options_default(2)
     o.symmetric = 2
