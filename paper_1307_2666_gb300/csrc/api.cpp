@@ -1765,13 +1765,13 @@ static std::vector<double> seg_norms(hif_handle h, const double* v, int nrhs) {
 // with an error d enters the next one in full (r' = (I - A F^{-1}) r - d), so
 // only the residual that decides convergence has to be the full sum; another
 // may take KD < 8 digit classes while its error stays below both 0.05 tol and
-// 1e-4 of the residual itself (an FP32 factor contracts by >= 1e-3 per step,
-// so the next residual keeps at least ~10x that margin).  The error of a short
+// 1e-4 of the residual itself (an FP32 factor reduces the residual by at most
+// ~10^3 per step, so the next residual stays >= 10x above that error).  The error of a short
 // sum is estimated as c_KD Y: c_KD the relative error of y = K v for Gaussian
-// sources (the worst case measured: ~6e-9, ~2e-11, ~1e-13 for KD = 4, 5, 6,
-// taken with a factor 5 of margin) and Y = |b K c u| / |f|, the size of the
+// sources (the largest measured: 6.5e-9, 2.9e-11, 1.3e-13 for KD = 4, 5, 6,
+// taken with a factor 3 of margin) and Y = |b K c u| / |f|, the size of the
 // kernel part of A u, measured after every residual.
-static constexpr double kShortErr[3] = {3e-8, 1.5e-10, 6e-13};     // KD = 4, 5, 6
+static constexpr double kShortErr[3] = {2e-8, 1e-10, 4e-13};       // KD = 4, 5, 6
 
 static bool short_residuals_on(hif_handle h, double tol) {
     if (h->opt.direct_precision != 2 || tol < 1e-11 || !env_int("HIF_SHORT_RESIDUAL", 1)) return false;
