@@ -217,8 +217,9 @@ hif_status hif_matvec_digits(hif_handle h, int trans, int classes, const double*
  * convergence by the short sums of hif_matvec_digits: the first residual
  * with 5 classes (FP32 factorization) or 6 (FP64), a later one, while its
  * predicted size is above 10 tol, with the fewest classes whose estimated
- * error (the sum's relative error times |b K c u| / |f|) stays below
- * 0.05 tol and 1e-4 of the residual; none when tol < 1e-11 or
+ * error (a bound on the sum's relative error per unit of the grid table's
+ * spread max|T| sqrt(#T) / |T|_2, times that spread, times |b K c u| / |f|)
+ * stays below 0.05 tol and 1e-4 of the residual; none when tol < 1e-11 or
  * HIF_SHORT_RESIDUAL=0.  Every residual at or below tol, at maxit, or whose
  * error estimate misses that bound is recomputed in full.
  *   iters   (may be NULL) receives the largest iteration count over columns

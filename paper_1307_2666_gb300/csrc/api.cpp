@@ -125,6 +125,7 @@ struct Segment {
     double gh = 0;
     DevMem dof_of, table, table_df;
     DevMem tc_rows, tc_tmax;      // digit rows of the table for the tensor-core sum (built on first use)
+    double spread = 1.0;          // max|T| sqrt(#T) / |T|_2 of the table (scale of the short sums' error)
 };
 
 struct FactorScratch {
@@ -1766,12 +1767,50 @@ static std::vector<double> seg_norms(hif_handle h, const double* v, int nrhs) {
 // only the residual that decides convergence has to be the full sum; another
 // may take KD < 8 digit classes while its error stays below both 0.05 tol and
 // 1e-4 of the residual itself (an FP32 factor reduces the residual by at most
-// ~10^3 per step, so the next residual stays >= 10x above that error).  The error of a short
-// sum is estimated as c_KD Y: c_KD the relative error of y = K v for Gaussian
-// sources (the largest measured: 6.5e-9, 2.9e-11, 1.3e-13 for KD = 4, 5, 6,
-// taken with a factor 3 of margin) and Y = |b K c u| / |f|, the size of the
-// kernel part of A u, measured after every residual.
-static constexpr double kShortErr[3] = {2e-8, 1e-10, 4e-13};       // KD = 4, 5, 6
+// ~10^3 per step, so the next residual stays >= 10x above that error).  The
+// error of a short sum is estimated as C_KD S Y.  The dropped digits sit at a
+// fixed level below max|T| whatever the entry, so the relative error of
+// y = K v grows with the table's spread S = max|T| sqrt(#T) / |T|_2; C_KD
+// bounds the ratio of the two measured for Gaussian sources (exact integer
+// convolutions of the digits, self term included: 2D log kernel n = 64..1024,
+// S = 8..13, ratios up to 3.2e-9, 1.4e-11, 6.2e-14; 3D 1/r kernel n = 16..64,
+// S = 23..104, up to 1.9e-9, 8.6e-12, 3.8e-14; the spread of the ratios comes
+// from where max|T| and max|v| fall against their power-of-two scales), and
+// Y = |b K c u| / |f|, the size of the kernel part of A u, is measured after
+// every residual.
+static constexpr double kShortErr[3] = {4e-9, 1.6e-11, 7e-14};      // C_KD, KD = 4, 5, 6
+
+// S of the grid table T(o) = G(h |o|) (o != 0), T(0) = k0, over the offsets
+// o in [0, n)^dim, in fixed chunks so that the sum is the same on every run.
+static double table_spread(int n, int dim, double h, int kernel_id, double k0) {
+    const int64_t tot = dim == 2 ? (int64_t)n * n : (int64_t)n * n * n;
+    constexpr int64_t NCH = 256;
+    std::vector<double> ss(NCH, 0.0), mx(NCH, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < NCH; ++c) {
+        const int64_t e0 = tot * c / NCH, e1 = tot * (c + 1) / NCH;
+        for (int64_t e = e0; e < e1; ++e) {
+            int64_t t = e;
+            double r2 = 0.0;
+            for (int q = 0; q < dim; ++q) {
+                const double dd = (double)(t % n) * h;
+                r2 += dd * dd;
+                t /= n;
+            }
+            const double v = e == 0 ? k0
+                             : kernel_id == 0 ? -std::log(r2) * (0.25 / kPi)
+                                              : (0.25 / kPi) / std::sqrt(r2);
+            ss[c] += v * v;
+            mx[c] = std::max(mx[c], std::fabs(v));
+        }
+    }
+    double s = 0.0, m = 0.0;
+    for (int64_t c = 0; c < NCH; ++c) {
+        s += ss[c];
+        m = std::max(m, mx[c]);
+    }
+    return s > 0.0 ? m * std::sqrt((double)tot / s) : 1.0;
+}
 
 static bool short_residuals_on(hif_handle h, double tol) {
     if (h->opt.direct_precision != 2 || tol < 1e-11 || !env_int("HIF_SHORT_RESIDUAL", 1)) return false;
@@ -1780,21 +1819,22 @@ static bool short_residuals_on(hif_handle h, double tol) {
     return true;
 }
 
-// Digit classes of residual k (8: the full sum).  Step 0 has no Y yet and
-// takes 5 classes after an FP32 factorization (its first residual is of the
-// order of the 2^-17 tolerance floor or above), 6 after an FP64 one; step k >= 1
-// takes the fewest classes whose estimated error meets the bound above for its
-// predicted residual, the last one times the last contraction (sqrt of the
+// Digit classes of residual k (8: the full sum); SY = S Y from the last
+// residual.  Step 0 has no Y yet and takes 5 classes after an FP32
+// factorization (its first residual is of the order of the 2^-17 tolerance
+// floor or above), 6 after an FP64 one; step k >= 1 takes the fewest classes
+// whose estimated error C_KD S Y meets the bound above for its predicted
+// residual, the last one times the last contraction (sqrt of the
 // first residual for the first contraction), if that prediction is above
 // 10 tol, and the full sum otherwise.
-static int residual_classes(hif_handle h, int k, const std::vector<double>& hist, double Y, double tol) {
+static int residual_classes(hif_handle h, int k, const std::vector<double>& hist, double SY, double tol) {
     if (k == 0) return h->precision == 1 ? 5 : 6;
     const double last = hist[k - 1];
     const double rho = k == 1 ? std::sqrt(hist[0]) : (hist[k - 2] > 0 ? last / hist[k - 2] : 0.0);
     const double pred = last * rho;
     if (!(pred > 10.0 * tol)) return 8;
     for (int kd = 4; kd <= 6; ++kd)
-        if (kShortErr[kd - 4] * Y <= std::max(0.05 * tol, 1e-4 * pred)) return kd;
+        if (kShortErr[kd - 4] * SY <= std::max(0.05 * tol, 1e-4 * pred)) return kd;
     return 8;
 }
 
@@ -1812,11 +1852,13 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
     const std::vector<double> fn = seg_norms(h, f, nrhs);
     solve_dev(h, trans, f, u, nrhs);
     const bool shorts = short_residuals_on(h, tol);
+    double S = 1.0;
+    for (auto& sp : h->segs) S = std::max(S, sp->spread);
     int it = 0;
     double worst = 0, Y = 0;
     std::vector<double> hist;
     for (;; ++it) {
-        int classes = shorts ? residual_classes(h, it, hist, Y, tol) : 8;
+        int classes = shorts ? residual_classes(h, it, hist, S * Y, tol) : 8;
         for (;;) {
             matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs, classes);
             HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, h->st));
@@ -1834,7 +1876,7 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
                 std::fprintf(stderr, "[hif] refinement %d: relative residual %.3e (%d digit classes, |bKcu|/|f| %.2e)\n",
                              it, worst, classes, Y);
             if (classes == 8 ||
-                (worst > tol && it < maxit && kShortErr[classes - 4] * Y <= std::max(0.05 * tol, 1e-4 * worst)))
+                (worst > tol && it < maxit && kShortErr[classes - 4] * S * Y <= std::max(0.05 * tol, 1e-4 * worst)))
                 break;
             classes = 8;
         }
@@ -2353,6 +2395,7 @@ static hif_status factor_impl(int count, const hif_problem* probs, int kernel_id
             sg.table.ensure(sizeof(double) * tsz);
             HIF_CUDA(launch_grid_table(sg.table.as<double>(), sg.gn, d, sg.gh, kernel_id,
                                        hks[sg.off] / h->hw[sg.off], st));
+            sg.spread = table_spread(sg.gn, d, sg.gh, kernel_id, hks[sg.off] / h->hw[sg.off]);
             sg.table_df.ensure(sizeof(float2) * tsz);
             HIF_CUDA(launch_split_df(sg.table.as<double>(), sg.table_df.as<float2>(), tsz, st));
         }

@@ -1,0 +1,110 @@
+"""The error model of the short digit sums (the refinement's intermediate
+residuals) on the CPU: the tensor-core direct sum writes table entries and
+sources as signed 8-bit digits, u = 2^e sum_k d_k 2^-8(k+1) (round to
+nearest, |u| 2^-e < 1/2), and a short sum with KD classes keeps the digit
+pairs s + t < KD.  Each digit layer of the grid table is itself a function of
+the offset, so the short sum is a sum of integer convolutions of digit
+layers, computed here exactly (FFT, rounded to integers).
+
+The library estimates the relative error of y = K v as C_KD S, S the table's
+spread max|T| sqrt(#T) / |T|_2 (the dropped digits sit at a fixed level below
+max|T|).  The constants C_KD are read from the library source and must bound
+the emulated error for Gaussian sources on the 2D log-kernel and 3D 1/r
+grids; the error must also fall by ~2^8 per class (a dropped class or a wrong
+digit weight fails that).
+"""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _constants():
+    src = open(os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "api.cpp")).read()
+    m = re.search(r"kShortErr\[3\]\s*=\s*\{([^}]*)\}", src)
+    return [float(v) for v in m.group(1).split(",")]
+
+
+def _digits(u, nd):
+    out = []
+    for _ in range(nd):
+        x = u * 256.0
+        d = np.rint(x)
+        out.append(d)
+        u = x - d
+    return out
+
+
+def _scale_exp(m):
+    return math.frexp(m)[1] + 1 if m > 0 else 0          # ilogb(m) + 2: |u| 2^-e < 1/2
+
+
+def _table(n, dim):
+    # T(o) over the offsets o in (-n, n)^dim, wrapped for a circular
+    # convolution of size 2n; the self term as the kernels' exact cell integral
+    h = 1.0 / n
+    o = np.arange(2 * n)
+    o = np.where(o < n, o, o - 2 * n)
+    grids = np.meshgrid(*([o] * dim), indexing="ij")
+    r = h * np.sqrt(sum(g.astype(np.float64) ** 2 for g in grids))
+    with np.errstate(divide="ignore"):
+        if dim == 2:
+            T = -np.log(r) / (2 * np.pi)
+            T0 = (math.log(n) + 0.5 * math.log(2) + 1.5 - math.pi / 4) / (2 * math.pi)
+        else:
+            T = 1.0 / (4 * np.pi * r)
+            T0 = n / (4 * math.pi) * (3 * math.log(2 + math.sqrt(3)) - math.pi / 2)
+    T[(0,) * dim] = T0
+    for g in grids:
+        T[np.abs(g) >= n] = 0.0
+    oct_ = T[(slice(0, n),) * dim]
+    spread = np.abs(oct_).max() * math.sqrt(oct_.size) / np.linalg.norm(oct_)
+    return T, spread
+
+
+def _conv(T, v, n, dim):
+    V = np.zeros((2 * n,) * dim)
+    V[(slice(0, n),) * dim] = v
+    ax = tuple(range(dim))
+    y = np.fft.irfftn(np.fft.rfftn(T, axes=ax) * np.fft.rfftn(V, axes=ax), s=(2 * n,) * dim, axes=ax)
+    return y[(slice(0, n),) * dim]
+
+
+def _short_errors(n, dim, seed):
+    T, spread = _table(n, dim)
+    v = np.random.default_rng(seed).standard_normal((n,) * dim)
+    y = _conv(T, v, n, dim)
+    eT, eX = _scale_exp(np.abs(T).max()), _scale_exp(np.abs(v).max())
+    dT, dX = _digits(np.ldexp(T, -eT), 6), _digits(np.ldexp(v, -eX), 6)
+    cls = [np.zeros((n,) * dim) for _ in range(6)]
+    for s in range(6):
+        for t in range(6 - s):
+            cls[s + t] += np.rint(_conv(dT[s], dX[t], n, dim))      # exact integer sums
+    err = {}
+    for kd in (4, 5, 6):
+        yk = sum(cls[k] * 2.0 ** (-8 * (k + 2)) for k in range(kd)) * 2.0 ** (eT + eX)
+        err[kd] = np.linalg.norm(yk - y) / np.linalg.norm(y)
+    return err, spread
+
+
+@pytest.mark.parametrize("n,dim", [(64, 2), (256, 2), (512, 2), (16, 3), (32, 3), (48, 3)])
+def test_short_sum_errors_within_the_model(n, dim):
+    C = _constants()
+    err, spread = _short_errors(n, dim, seed=1 + n)
+    for kd in (4, 5, 6):
+        assert err[kd] <= C[kd - 4] * spread, (kd, err[kd], C[kd - 4] * spread)
+    # about 8 bits per class
+    assert 60 < err[4] / err[5] < 1000 and 60 < err[5] / err[6] < 1000
+
+
+def test_spread_grows_with_the_3d_grid():
+    # the 1/r table's spread roughly doubles with n (the far field dominates
+    # |T|_2), the 2D log table's grows like log n
+    s3 = [_table(n, 3)[1] for n in (8, 16)]
+    s2 = [_table(n, 2)[1] for n in (64, 128)]
+    assert 1.7 < s3[1] / s3[0] < 2.3
+    assert 1.0 < s2[1] / s2[0] < 1.3
