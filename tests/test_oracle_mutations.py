@@ -1,0 +1,168 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Every parity claim rests on the oracle, and the oracle rests on its pins
+(tests/test_oracle_pins*.py).  Each case below copies the oracle package into
+a scratch directory, plants one plausible mistake in that copy (a dropped
+term, a flipped sign, a wrong index range, a transposed block, an
+off-by-one), and runs the pins that should catch it against the copy in a
+fresh interpreter.  The case passes when those pins fail (pytest exit code 1:
+test failures, not a collection or import error).  The tree under test is
+never modified.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+P = "tests/test_oracle_pins.py::"
+PT = "tests/test_oracle_pins_tree.py::"
+PH = "tests/test_oracle_pins_helmholtz.py::"
+
+# (case id, oracle file, function (or Class.method) whose body holds the text,
+# original text, planted text, pins that must fail)
+MUTATIONS = [
+    ("self-term-constant", "kernels.py", "self_integral",
+     "- 1.5 + 0.25 * math.pi", "+ 1.5 + 0.25 * math.pi",
+     [P + "test_self_cell_2d_matches_quadrature"]),
+    ("green-3d-factor", "kernels.py", "green",
+     "return 1.0 / (FOUR_PI * r)", "return 1.0 / (TWO_PI * r)",
+     [P + "test_green_functions_eq_1_4"]),
+    ("operator-b-c-swapped", "kernels.py", "kernel_entries",
+     "return self.b[rows][:, None] * K * self.c[cols][None, :]",
+     "return self.c[rows][:, None] * K * self.b[cols][None, :]",
+     [P + "test_operator_b_scales_rows_c_scales_columns"]),
+    ("id-tie-highest-index", "idqr.py", "interp_decomp",
+     "p = j + cand[np.argmin(perm[j + cand])]", "p = j + cand[np.argmax(perm[j + cand])]",
+     [P + "test_id_tie_break_lowest_index"]),
+    ("id-threshold-from-current-pivot", "idqr.py", "interp_decomp",
+     "        if j == 0:\n            nu0 = best\n", "        nu0 = best\n",
+     [P + "test_id_exact_low_rank", P + "test_id_bounds_eq_2_3"]),
+    ("id-T-columns-unordered", "idqr.py", "interp_decomp",
+     "    T = T[:, order]\n", "",
+     [P + "test_id_exact_low_rank", P + "test_id_bounds_eq_2_3"]),
+    ("B_rr-dropped-term", "hifie.py", "_skeletonize",
+     "B_rr = A_rr - T.T @ A_sr - A_rs @ T + T.T @ A_ss @ T", "B_rr = A_rr - T.T @ A_sr - A_rs @ T",
+     [P + "test_skeletonization_decouples_redundant_dofs_lemma_2_3"]),
+    ("B_sr-sign", "hifie.py", "_skeletonize",
+     "B_sr = A_sr - A_ss @ T", "B_sr = A_sr + A_ss @ T",
+     [P + "test_skeletonization_decouples_redundant_dofs_lemma_2_3"]),
+    ("schur-sign", "hifie.py", "_skeletonize",
+     "delta = -B_sr @ np.linalg.solve(B_rr, B_rs)", "delta = B_sr @ np.linalg.solve(B_rr, B_rs)",
+     [P + "test_nonsymmetric_accuracy_full_compression"]),
+    ("proxy-in-rows-missing", "hifie.py", "_skeletonize",
+     "YK = np.vstack([YK_near1, YK_near2, YK_out, YK_in])",
+     "YK = np.vstack([YK_near1, YK_near2, YK_out, 0.0 * YK_in])",
+     [P + "test_proxy_rows_span_far_field_lemma_3_3"]),
+    ("proxy-out-rows-missing", "hifie.py", "_skeletonize",
+     "YK = np.vstack([YK_near1, YK_out])", "YK = np.vstack([YK_near1, 0.0 * YK_out])",
+     [P + "test_symmetric_compression_equals_full_sec_5"]),
+    ("sci-neighbours-missing", "hifie.py", "_skeletonize",
+     "cN = np.nonzero(near | sci)[0]", "cN = np.nonzero(near)[0]",
+     [P + "test_sci_coupled_dofs_join_near_field_sec_4_3"]),
+    ("no-group-split", "hifie.py", "_skeletonize",
+     "groups = sci_groups(M[np.ix_(cN, cbox)]) if second_kind else [np.arange(n)]",
+     "groups = [np.arange(n)]",
+     [P + "test_sci_groups_lemma_4_2_and_half_edges"]),
+    ("top-block-without-sci", "hifie.py", "factor",
+     "top_A = op.entries(top, top) + S[np.ix_(top, top)]", "top_A = op.entries(top, top)",
+     [P + "test_accuracy_bounds_2d"]),
+    ("solve-sweep-sign", "hifie.py", "solve",
+     "            x[bf.sk] -= bf.X @ x[bf.rd]\n", "            x[bf.sk] += bf.X @ x[bf.rd]\n",
+     [P + "test_sweeps_match_product_formula_eq_4_1"]),
+    ("depth-off-by-one", "hifie.py", "num_levels",
+     "if np.bincount(flat).max() <= occupancy:", "if np.bincount(flat).max() < occupancy:",
+     [PT + "test_depth_is_smallest_with_occupancy_met"]),
+    ("edge-range-from-zero", "hifie.py", "centers",
+     "ranges = [range(1, s) if t == _I else range(0, s) for t in fam]",
+     "ranges = [range(0, s) if t == _I else range(0, s) for t in fam]",
+     [PT + "test_2d_edge_centres_are_interior_cell_sides"]),
+    ("refine-residual-sign", "krylov.py", "refine",
+     "r = f - matvec(u)", "r = matvec(u) - f",
+     [PT + "test_refine_contracts_by_norm_of_E"]),
+    ("refine-count-off-by-one", "krylov.py", "refine",
+     "return u, it, hist", "return u, it + 1, hist",
+     [PT + "test_refine_contracts_by_norm_of_E"]),
+    ("ldl-no-pivoting", "hifie.py", "ldl_diag_pivot",
+     "p = j + int(np.argmax(diag))", "p = j",
+     [P + "test_ldl_diag_pivot_reconstructs_and_pivots_on_largest_diagonal"]),
+    ("helmholtz-block-convention", "helmholtz.py", "EmbeddedOperator.kernel_entries",
+     "return np.where(ra == cb, Z.real, np.where(ra == 1, Z.imag, -Z.imag))",
+     "return np.where(ra == cb, Z.real, np.where(ra == 1, -Z.imag, Z.imag))",
+     [PH + "test_embedded_operator_entries_and_dense_solve"]),
+    ("helmholtz-proxy-in-untransposed", "helmholtz.py", "EmbeddedOperator.proxy_in",
+     "out[0::2] = np.where(cb == 0, Z.real, Z.imag)\n        out[1::2] = np.where(cb == 0, -Z.imag, Z.real)",
+     "out[0::2] = np.where(cb == 0, Z.real, -Z.imag)\n        out[1::2] = np.where(cb == 0, Z.imag, Z.real)",
+     [PH + "test_embedded_proxy_blocks_are_operator_blocks"]),
+]
+
+
+def _plant(src, func, old, new):
+    """Replace ``old`` by ``new`` exactly once, inside the body of ``func``
+    (the def line through the last line indented deeper than it)."""
+    if func is None:
+        start, end = 0, len(src)
+    else:
+        lines = src.splitlines(keepends=True)
+        cls, _, name = func.rpartition(".")
+        lo, hi = 0, len(lines)
+        if cls:                                        # a method: search inside its class only
+            ch = [i for i, ln in enumerate(lines) if ln.startswith(f"class {cls}(") or ln.startswith(f"class {cls}:")]
+            assert len(ch) == 1, f"class {cls} is defined {len(ch)} times"
+            lo = ch[0] + 1
+            hi = next((i for i in range(lo, len(lines)) if lines[i].strip() and not lines[i][0].isspace()), len(lines))
+        heads = [i for i in range(lo, hi) if lines[i].lstrip().startswith(f"def {name}(")]
+        assert len(heads) == 1, f"{func} is defined {len(heads)} times"
+        h = heads[0]
+        indent = len(lines[h]) - len(lines[h].lstrip())
+        e = h + 1
+        while e < len(lines) and (not lines[e].strip() or len(lines[e]) - len(lines[e].lstrip()) > indent):
+            e += 1
+        start, end = sum(map(len, lines[:h])), sum(map(len, lines[:e]))
+    body = src[start:end]
+    assert body.count(old) == 1, f"planted text found {body.count(old)} times in {func}"
+    return src[:start] + body.replace(old, new) + src[end:]
+
+
+@pytest.fixture(scope="module")
+def scratch(tmp_path_factory):
+    base = tmp_path_factory.mktemp("mutants")
+    ign = shutil.ignore_patterns("__pycache__", "*.pyc")
+    for d in ("tests", "hif_inputs"):
+        shutil.copytree(os.path.join(ROOT, d), base / d, ignore=ign)
+    return base, ign
+
+
+@pytest.mark.parametrize("case", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(scratch, case):
+    base, ign = scratch
+    _, fname, func, old, new, pins = case
+    odir = base / "oracle"
+    if odir.exists():
+        shutil.rmtree(odir)
+    shutil.copytree(os.path.join(ROOT, "oracle"), odir, ignore=ign)
+    path = odir / fname
+    path.write_text(_plant(path.read_text(), func, old, new))
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu",
+                        *pins], cwd=base, env=env, capture_output=True, text=True, timeout=600)
+    tail = "\n".join((r.stdout + r.stderr).splitlines()[-8:])
+    assert r.returncode == 1, f"planted mistake not caught (exit {r.returncode}):\n{tail}"
+
+
+def test_unmutated_copy_passes_the_same_pins(scratch):
+    # the copies themselves are sound: with nothing planted every pin above passes
+    base, ign = scratch
+    odir = base / "oracle"
+    if odir.exists():
+        shutil.rmtree(odir)
+    shutil.copytree(os.path.join(ROOT, "oracle"), odir, ignore=ign)
+    pins = sorted({p for m in MUTATIONS for p in m[5]})
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", "-m", "not gpu", *pins],
+                       cwd=base, env=env, capture_output=True, text=True, timeout=900)
+    tail = "\n".join((r.stdout + r.stderr).splitlines()[-8:])
+    assert r.returncode == 0, tail

@@ -108,6 +108,33 @@ def test_operator_structure():
     assert A[0, 1] == pytest.approx(-math.log(h) / (2 * math.pi) * h * h, rel=1e-14)
 
 
+def test_operator_b_scales_rows_c_scales_columns():
+    # Eq. (1.1): b multiplies the integral (the row of DOF i), c sits inside it
+    # (the column of DOF j), a only the diagonal; scaling one coefficient
+    # entry must move exactly that row, column or diagonal entry
+    pb = hi.volume_problem(10, 2, smooth_seed=5)
+    N = pb.N
+    A = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0).dense()
+    Kpart = A - np.diag(pb.a)
+    i, j = 17, 42
+    b2, c2, a2 = pb.b.copy(), pb.c.copy(), pb.a.copy()
+    b2[i] *= 3.0
+    c2[j] *= 3.0
+    a2[i] += 0.5
+    Db = kernels.Operator(pb.points, pb.weights, pb.a, b2, pb.c, 0).dense() - A
+    Dc = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, c2, 0).dense() - A
+    Da = kernels.Operator(pb.points, pb.weights, a2, pb.b, pb.c, 0).dense() - A
+    others = np.arange(N) != i
+    assert np.all(Db[others] == 0.0)
+    np.testing.assert_allclose(Db[i], 2.0 * Kpart[i], rtol=1e-13, atol=0)
+    others = np.arange(N) != j
+    assert np.all(Dc[:, others] == 0.0)
+    np.testing.assert_allclose(Dc[:, j], 2.0 * Kpart[:, j], rtol=1e-13, atol=0)
+    E = np.zeros((N, N))
+    E[i, i] = 0.5
+    np.testing.assert_allclose(Da, E, rtol=0, atol=1e-15)
+
+
 def test_direct_sum_rows_match_full():
     pb = hi.volume_problem(10, 2, smooth_seed=5)
     op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)

@@ -122,11 +122,39 @@ def test_hifie_on_embedding_matches_complex_dense(eps):
     np.testing.assert_allclose(hz.to_complex(ug), u, rtol=1e-10, atol=1e-12)
 
 
-def test_helmholtz_proxy_rows_span_far_field_lemma_3_3():
+def test_embedded_proxy_blocks_are_operator_blocks():
+    # Lemma 3.3's proxy blocks are interactions with the proxy points taken as
+    # extra DOFs (unit b and c, the box's quadrature weight): Y_{cE,c} =
+    # A_{E,c} and the incoming rows (A_{c,E})^T, i.e. the transpose of the
+    # embedded block (the embedding of the conjugate-transposed complex block)
+    pb = _ls_problem(8, 1.0)
+    pb.c = pb.b * (1.0 + 0.5 * hi.smooth_field(pb.points, 77)) + 0.3       # b != c
+    box = np.array([9, 10, 17, 18])                                         # complex DOFs
+    ctr = pb.points[box].mean(axis=0)
+    xE = ctr[None, :] + 0.3 * pb.proxy[:16]
+    eop = hz.EmbeddedOperator(pb.points, pb.weights, pb.a, pb.b, pb.c, pb.k)
+    cols = np.sort(np.concatenate([2 * box, 2 * box + 1]))                  # real DOFs of the box
+    pts = np.vstack([pb.points[box], xE])
+    nb, ne = box.size, xE.shape[0]
+    one = np.ones(ne)
+    ext = hz.EmbeddedOperator(pts, np.full(nb + ne, pb.weights[0]), np.ones(nb + ne),
+                              np.concatenate([pb.b[box], one]), np.concatenate([pb.c[box], one]), pb.k)
+    bcols = np.arange(2 * nb)                                               # box DOFs in ext, same order
+    erows = np.arange(2 * nb, 2 * (nb + ne))                                # proxy points as DOFs
+    np.testing.assert_allclose(eop.proxy_out(xE, cols), ext.kernel_entries(erows, bcols), rtol=1e-13, atol=0)
+    np.testing.assert_allclose(eop.proxy_in(xE, cols), ext.kernel_entries(bcols, erows).T, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("b_ne_c", [False, True])
+def test_helmholtz_proxy_rows_span_far_field_lemma_3_3(b_ne_c):
     # the proxy argument of Lemma 3.3 holds for the Helmholtz kernel: the ID
     # of each leaf's Y_c (near rows plus proxy rows) interpolates the leaf's
-    # whole far field W_c = [A_{F,c}; A_{c,F}^T] of the embedded operator
+    # whole far field W_c = [A_{F,c}; A_{c,F}^T] of the embedded operator;
+    # with b != c the incoming rows (b_j G w_j, transposed 2 x 2 blocks) carry
+    # information the outgoing ones do not
     pb = _ls_problem(32, 1.5)
+    if b_ne_c:
+        pb.c = pb.b * (1.0 + 0.5 * hi.smooth_field(pb.points, 77)) + 0.3
     eps = 1e-8
     F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 2, eps, pb.proxy, wavenumber=pb.k, occupancy=128)
     eop = hz.EmbeddedOperator(pb.points, pb.weights, pb.a, pb.b, pb.c, pb.k)
