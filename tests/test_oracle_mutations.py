@@ -89,6 +89,47 @@ MUTATIONS = [
     ("ldl-no-pivoting", "hifie.py", "ldl_diag_pivot",
      "p = j + int(np.argmax(diag))", "p = j",
      [P + "test_ldl_diag_pivot_reconstructs_and_pivots_on_largest_diagonal"]),
+    ("proxy-out-weight-b", "kernels.py", "Operator.proxy_out",
+     "(self.w[cols] * self.c[cols])[None, :]", "(self.w[cols] * self.b[cols])[None, :]",
+     [P + "test_proxy_rows_span_far_field_lemma_3_3"]),
+    ("matvec-ignores-transpose", "kernels.py", "Operator.matvec",
+     "Y[rows] = self.entries(idx, rows).T @ X", "Y[rows] = self.entries(rows, idx) @ X",
+     [P + "test_direct_sum_rows_match_full"]),
+    ("norm2-returns-gram-norm", "idqr.py", "norm2_estimate",
+     "return float(np.linalg.norm(Y @ v))", "return float(np.linalg.norm(Y.T @ (Y @ v)))",
+     [P + "test_norm2_estimate"]),
+    ("apply-transpose-sweep-sign", "hifie.py", "HIFFactor.apply_transpose",
+     "x[bf.sk] += bf.Y.T @ x[bf.rd]", "x[bf.sk] -= bf.Y.T @ x[bf.rd]",
+     [P + "test_sweeps_match_product_formula_eq_4_1"]),
+    ("solve-transpose-top-untransposed", "hifie.py", "HIFFactor.solve_transpose",
+     "x[self.top] = lu_solve(self.top_lu, x[self.top], trans=1)", "x[self.top] = lu_solve(self.top_lu, x[self.top])",
+     [P + "test_sweeps_match_product_formula_eq_4_1"]),
+    ("symmetry-test-ignores-b-c", "hifie.py", "is_symmetric",
+     "return bool(np.array_equal(op.b, op.c) and np.all(op.w == op.w[0]))",
+     "return bool(np.all(op.w == op.w[0]))",
+     [P + "test_symmetry_test_matches_dense_transpose"]),
+    ("3d-face-family", "hifie.py", None,
+     "(3, \"face\"): [(_I, _H, _H), (_H, _I, _H), (_H, _H, _I)]",
+     "(3, \"face\"): [(_I, _H, _H), (_H, _I, _H), (_H, _I, _I)]",
+     [PT + "test_3d_face_and_edge_centres_are_interior"]),
+    ("root-box-without-cells", "hifie.py", "root_box",
+     "lo = (points - 0.5 * side[:, None]).min(axis=0)", "lo = points.min(axis=0)",
+     [PT + "test_depth_is_smallest_with_occupancy_met"]),
+    ("ldl-never-refuses", "hifie.py", "ldl_diag_pivot",
+     "abs(Bw[p, p]) < LDL_ALPHA * colmax", "abs(Bw[p, p]) < 0.0 * colmax",
+     [P + "test_ldl_diag_pivot_refuses_weak_pivots"]),
+    ("gmres-mgs-sign", "krylov.py", "gmres",
+     "wv = wv - H[i, j] * V[:, i]", "wv = wv + H[i, j] * V[:, i]",
+     [P + "test_gmres_lemma_5_1_iteration_bound"]),
+    ("gmres-unpreconditioned", "krylov.py", "gmres",
+     "Z[:, j] = M(V[:, j])", "Z[:, j] = V[:, j]",
+     [P + "test_gmres_exact_preconditioner_one_step"]),
+    ("power-norm-without-sqrt", "krylov.py", "power_norm",
+     "new = np.sqrt(nw)", "new = nw",
+     [P + "test_error_estimates_match_dense_two_norms"]),
+    ("power-norm-E-E-instead-of-Et-E", "krylov.py", "power_norm",
+     "w = apply_op_t(apply_op(v))", "w = apply_op(apply_op(v))",
+     [P + "test_error_estimates_match_dense_two_norms"]),
     ("helmholtz-block-convention", "helmholtz.py", "EmbeddedOperator.kernel_entries",
      "return np.where(ra == cb, Z.real, np.where(ra == 1, Z.imag, -Z.imag))",
      "return np.where(ra == cb, Z.real, np.where(ra == 1, -Z.imag, Z.imag))",

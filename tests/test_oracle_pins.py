@@ -137,7 +137,8 @@ def test_operator_b_scales_rows_c_scales_columns():
 
 def test_direct_sum_rows_match_full():
     pb = hi.volume_problem(10, 2, smooth_seed=5)
-    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    c = pb.c * (1.0 + 0.5 * hi.smooth_field(pb.points, 6))          # b != c: A^T != A
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, c, 0)
     x = np.random.default_rng(3).standard_normal(op.N)
     y = op.matvec(x, block=37)
     yt = op.matvec(x, trans=True, block=29)
@@ -147,6 +148,7 @@ def test_direct_sum_rows_match_full():
     # A^T x differs from A x when b != c only through the scaling: check with the dense matrix
     A = op.dense()
     assert np.allclose(A.T @ x, yt, rtol=1e-13, atol=1e-15)
+    assert not np.allclose(y, yt, rtol=1e-6)
 
 
 # ---------------------------------------------------------------------- ID ---
@@ -217,10 +219,17 @@ def _setup(n, dim=2, smooth=None, **kw):
     return pb, op
 
 
-def test_sweeps_match_product_formula_eq_4_1():
-    pb, op = _setup(8, smooth=11)
-    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, 1e-4, pb.proxy, occupancy=4)
+@pytest.mark.parametrize("b_ne_c", [False, True])
+def test_sweeps_match_product_formula_eq_4_1(b_ne_c):
+    # the four factored-form sweeps against the dense product of Eq. (4.1);
+    # with b != c (LU boxes, a non-symmetric top block) every transpose shows
+    pb, op = _setup(12 if b_ne_c else 8, smooth=11)
+    c = pb.c * (1.0 + 0.5 * hi.smooth_field(pb.points, 12)) if b_ne_c else pb.c
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, c, 0)
+    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, c, 0, 1e-4, pb.proxy, occupancy=4)
     assert any(bf.rd.size for sl in F.sublevels for bf in sl.boxes)
+    if b_ne_c:
+        assert not np.allclose(F.top_A, F.top_A.T)
     Fd = F.dense_F()
     I = np.eye(op.N)
     assert np.allclose(F.apply(I), Fd, rtol=0, atol=1e-13)
