@@ -168,42 +168,55 @@ def _plant(src, func, old, new):
     return src[:start] + body.replace(old, new) + src[end:]
 
 
-@pytest.fixture(scope="module")
-def scratch(tmp_path_factory):
-    base = tmp_path_factory.mktemp("mutants")
+PIN_FILES = ("conftest.py", "test_oracle_pins.py", "test_oracle_pins_tree.py", "test_oracle_pins_helmholtz.py")
+
+
+def _run_case(base, planted, pins):
+    """Copy the pins, the input generators and the oracle (with ``planted``:
+    (file, function, old, new), or None) under ``base`` and run ``pins``
+    there in a fresh interpreter; returns (exit code, output tail)."""
     ign = shutil.ignore_patterns("__pycache__", "*.pyc")
-    for d in ("tests", "hif_inputs"):
-        shutil.copytree(os.path.join(ROOT, d), base / d, ignore=ign)
-    return base, ign
+    os.makedirs(base / "tests")
+    for f in PIN_FILES:
+        shutil.copy(os.path.join(ROOT, "tests", f), base / "tests" / f)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), base / "tests" / "golden", ignore=ign)
+    shutil.copytree(os.path.join(ROOT, "hif_inputs"), base / "hif_inputs", ignore=ign)
+    shutil.copytree(os.path.join(ROOT, "oracle"), base / "oracle", ignore=ign)
+    if planted is not None:
+        fname, func, old, new = planted
+        path = base / "oracle" / fname
+        path.write_text(_plant(path.read_text(), func, old, new))
+    # one BLAS thread per run: the runs themselves go side by side
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                        *(["-x"] if planted is not None else []), *pins],
+                       cwd=base, env=env, capture_output=True, text=True, timeout=900)
+    return r.returncode, "\n".join((r.stdout + r.stderr).splitlines()[-8:])
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    # every case in its own scratch tree, several at a time
+    from concurrent.futures import ThreadPoolExecutor
+    root = tmp_path_factory.mktemp("mutants")
+    jobs = {m[0]: (m[1:5], m[5]) for m in MUTATIONS}
+    allpins = sorted({p for m in MUTATIONS for p in m[5]})
+    for c in range(6):                                   # the unplanted copy, in six chunks
+        jobs[f"unplanted {c}"] = (None, allpins[c::6])
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        futs = {k: ex.submit(_run_case, root / f"case{i}", planted, pins)
+                for i, (k, (planted, pins)) in enumerate(jobs.items())}
+        return {k: f.result() for k, f in futs.items()}
 
 
 @pytest.mark.parametrize("case", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_fails_a_pin(scratch, case):
-    base, ign = scratch
-    _, fname, func, old, new, pins = case
-    odir = base / "oracle"
-    if odir.exists():
-        shutil.rmtree(odir)
-    shutil.copytree(os.path.join(ROOT, "oracle"), odir, ignore=ign)
-    path = odir / fname
-    path.write_text(_plant(path.read_text(), func, old, new))
-    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu",
-                        *pins], cwd=base, env=env, capture_output=True, text=True, timeout=600)
-    tail = "\n".join((r.stdout + r.stderr).splitlines()[-8:])
-    assert r.returncode == 1, f"planted mistake not caught (exit {r.returncode}):\n{tail}"
+def test_planted_mistake_fails_a_pin(outcomes, case):
+    rc, tail = outcomes[case[0]]
+    assert rc == 1, f"planted mistake not caught (exit {rc}):\n{tail}"
 
 
-def test_unmutated_copy_passes_the_same_pins(scratch):
+def test_unplanted_copy_passes_the_same_pins(outcomes):
     # the copies themselves are sound: with nothing planted every pin above passes
-    base, ign = scratch
-    odir = base / "oracle"
-    if odir.exists():
-        shutil.rmtree(odir)
-    shutil.copytree(os.path.join(ROOT, "oracle"), odir, ignore=ign)
-    pins = sorted({p for m in MUTATIONS for p in m[5]})
-    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", "-m", "not gpu", *pins],
-                       cwd=base, env=env, capture_output=True, text=True, timeout=900)
-    tail = "\n".join((r.stdout + r.stderr).splitlines()[-8:])
-    assert r.returncode == 0, tail
+    bad = {k: v for k, v in outcomes.items() if k.startswith("unplanted ") and v[0] != 0}
+    assert not bad, bad
