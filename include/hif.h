@@ -179,7 +179,9 @@ hif_status hif_solve_transpose(hif_handle h, const double* b, double* x, int64_t
 /*
  * hif_matvec -- y = A x (trans = 0) or y = A^T x (trans = 1) by direct
  * summation over all N^2 pairs, exactly the operator the handle factored
- * (same quadrature, same self terms), with FP64 inputs and outputs.  On a
+ * (A = diag(a) + diag(b) K diag(c) of Eq. (1.1) discretized as in Sec. 3.1,
+ * Eq. (3.1): same quadrature, same self terms), with FP64 inputs and
+ * outputs; the operator the refinement and GMRES of Sec. 5 apply.  On a
  * full uniform grid the sum is a convolution with an FP64 table; it is
  * accumulated in FP64 (direct_precision = 1), in paired FP32 with
  * error-free transformations, good to ~2^-48 relative per operation
@@ -284,15 +286,18 @@ hif_status hif_stats(hif_handle h, hif_stats_t* st);
  * accepted.  Waits for the handle's stream first; always returns HIF_OK. */
 hif_status hif_destroy(hif_handle h);
 
-/* Static, human-readable name of a status code. */
+/* Static, human-readable name of a status code.  Error reporting of this
+ * library; the paper has no counterpart. */
 const char* hif_status_string(hif_status s);
 
 /* Detail of the last failure on the calling thread (file:line and the CUDA
- * error text when the failure came from the runtime); empty if none. */
+ * error text when the failure came from the runtime); empty if none.  Error
+ * reporting of this library; the paper has no counterpart. */
 const char* hif_last_error(void);
 
 /* Number of CUDA kernels the library has launched in this process so far
- * (all handles, all threads); callers difference it around a region. */
+ * (all handles, all threads); callers difference it around a region.  For
+ * measurement; the paper has no counterpart. */
 uint64_t hif_kernel_launches(void);
 
 /* Device time of the tensor-core direct-sum kernel (direct_precision = 2),
