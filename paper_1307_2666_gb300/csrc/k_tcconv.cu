@@ -57,7 +57,8 @@
 //   warps 9-11 builders of the Hankel operand from mirrored digit rows; one
 //              of them also issues the bulk copies of the source digits.
 // Slots (one Hankel operand, four 128-source chunks) flow through a 2-stage
-// shared-memory ring into two 256-column accumulators used in turn, so the
+// shared-memory ring (3 stages for the short sums, whose stages are smaller)
+// into two 256-column accumulators used in turn, so the
 // MMAs of the next slot proceed while the epilogue drains one.  The class
 // sums are kept as an int64 for class 0 and int32 for classes 1..7, and
 // every 32 slots the carries of classes 7..1 move up (c = s_k >> 8, s_k -=
