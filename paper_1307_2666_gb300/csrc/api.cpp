@@ -899,6 +899,7 @@ static void run_factor(hif_handle h) {
         int kind = -1, ell = -1;
         double ms_partition = 0, ms_near = 0;    // host time (trace)
     };
+    NearCache near_cache;                    // mark arrays reused by every sublevel's plan
     auto plan_sublevel = [&](size_t tau, Planned& P) {
         SublevelPlan& p = P.p;
         std::vector<double>& radius = P.radius;
@@ -926,7 +927,7 @@ static void run_factor(hif_handle h) {
             partition(sg.tree, h->hx.data(), kd, s, act_ids, ps, box_of);
             const auto q1 = std::chrono::steady_clock::now();
             build_near_groups(sg.tree, h->hx.data(), s, h->opt.proxy_radius, h->second_kind, act_ids, active, box_of,
-                              sci, ps);
+                              sci, ps, &near_cache);
             const auto q2 = std::chrono::steady_clock::now();
             P.ms_partition += std::chrono::duration<double, std::milli>(q1 - q0).count();
             P.ms_near += std::chrono::duration<double, std::milli>(q2 - q1).count();

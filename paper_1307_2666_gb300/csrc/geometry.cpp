@@ -242,7 +242,8 @@ void geometry_trace(bool on, double* ms) {
 
 void build_near_groups(const Tree& t, const double* x, int s, double proxy_radius, int second_kind,
                        const std::vector<int>& active_ids, const std::vector<char>& active,
-                       const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p) {
+                       const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p,
+                       NearCache* cache) {
     const bool tr = g_geo_trace;
     const double tb0 = tr ? now_ms() : 0.0;
     const int dim = t.dim;
@@ -284,10 +285,23 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
     nthr = omp_get_max_threads();
 #endif
     std::vector<NearScratch> scr(nthr);
+    if (cache) {
+        // the stamps left in a reused array are all at most its epoch, so the
+        // epochs that follow never match them
+        cache->mark.resize(nthr);
+        cache->epoch.resize(nthr, 0u);
+        for (int q = 0; q < nthr; ++q) {
+            scr[q].mark.swap(cache->mark[q]);
+            scr[q].epoch = cache->epoch[q];
+        }
+    }
     std::vector<BoxOut> bo(nb);
     const double tb1 = tr ? now_ms() : 0.0;
 
-#pragma omp parallel for schedule(dynamic, 16)
+    // chunks of up to 16 boxes, but at least ~8 chunks per thread, so that the
+    // few-box sublevels near the top spread over all threads
+    const int chunk = std::max(1, std::min(16, nb / (8 * nthr)));
+#pragma omp parallel for schedule(dynamic, chunk)
     for (int b = 0; b < nb; ++b) {
         int tid = 0;
 #ifdef _OPENMP
@@ -508,6 +522,11 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
         }
         p.box_sci[b] = o.sci;
     }
+    if (cache)
+        for (int q = 0; q < nthr; ++q) {
+            scr[q].mark.swap(cache->mark[q]);
+            cache->epoch[q] = scr[q].epoch;
+        }
     if (tr) {
         g_geo_ms[0] += tb1 - tb0;                      // bins and set-up (wall)
         g_geo_ms[1] += now_ms() - tb2;                 // gather (wall)

@@ -48,10 +48,21 @@ void plan_sublevels(int dim, int L, bool fractional, int skip_levels, std::vecto
 void partition(const Tree& t, const double* x, int kind, int s, const std::vector<int>& active_ids,
                SublevelPlan& out, std::vector<int>& box_of);
 
-// Near fields and groups; `active` flags DOFs active at the start of the sublevel.
+// Per-thread mark arrays (epoch stamps over all DOFs) kept by the caller from
+// one sublevel to the next, so that build_near_groups does not allocate and
+// clear N entries per thread per sublevel.
+struct NearCache {
+    std::vector<std::vector<uint32_t>> mark;
+    std::vector<uint32_t> epoch;
+};
+
+// Near fields and groups; `active` flags DOFs active at the start of the
+// sublevel.  `cache` (may be null) keeps the mark arrays between calls; it is
+// used by one call at a time.
 void build_near_groups(const Tree& t, const double* x, int s, double proxy_radius, int second_kind,
                        const std::vector<int>& active_ids, const std::vector<char>& active,
-                       const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p);
+                       const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p,
+                       NearCache* cache = nullptr);
 
 // Trace of build_near_groups: returns the per-phase times summed since the
 // previous call into ms[6] (bins, gather: wall ms; proxy scan, SCI patterns,
