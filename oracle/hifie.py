@@ -31,7 +31,12 @@ Readings of points the paper leaves open (the GPU path uses the same ones):
  2. Cells: DOF -> cell floor((x - lo) / w), clamped to [0, s-1] (a point on a
     split plane goes to the upper cell).  Edges/faces: only interior ones
     exist (Sec. 4.1/4.2 index ranges); each active DOF joins the nearest
-    centre by squared distance, ties to the lowest centre id.  Centre ids:
+    centre by squared distance; centres within a relative TIE = 2^-40 of the
+    smallest squared distance count as tied, and the lowest centre id wins
+    (on a grid, tied centres are exactly equidistant, but their computed
+    distances can differ by rounding: three squares summed in different
+    orders, or a cube root for the root box's cell side that is not
+    correctly rounded everywhere).  Centre ids:
     the paper's listing order of the families (2D edges: x-normal then
     y-normal; 3D faces: x-, y-, z-normal; 3D edges: z-, y-, x-directed),
     lexicographic with the first index slowest inside each family.
@@ -82,6 +87,7 @@ from .idqr import interp_decomp, norm2_estimate
 from .kernels import Operator, green
 
 _H, _I = "h", "i"
+TIE = 2.0 ** -40          # relative squared-distance difference counted as a tie (reading 2)
 FAMILIES = {
     (2, "cell"): [(_H, _H)],
     (2, "edge"): [(_I, _H), (_H, _I)],
@@ -330,7 +336,7 @@ def sublevel_plan(dim: int, L: int, fractional: bool = True, skip_levels: int = 
 def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
            *, second_kind: bool = True, occupancy: int = 64, proxy_radius: float = 1.5,
            fractional: bool = True, skip_levels: int = 0, symmetric=None, ldl=None,
-           wavenumber=None, trace=None) -> HIFFactor:
+           wavenumber=None, trace=None, trace_sets=None) -> HIFFactor:
     """HIF-IE (Algorithm 4.1 / 4.2) of A = diag(a) + diag(b) K diag(c).
 
     ``symmetric``: None compresses Y'_c exactly when ``is_symmetric`` holds,
@@ -340,6 +346,9 @@ def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
     kernel_id 2 (Helmholtz, Sec. 5 Example 3, wavenumber k): the factorization
     runs on the real 2 x 2 embedding of the complex operator (reading 10), on
     2N real DOFs, two at every point; occupancy counts real DOFs.
+    ``trace_sets`` (a list) receives, box by box, the index sets of every
+    skeletonization: (kind, level, box DOFs c, near field c^N, column groups,
+    skeletons, redundants), all global ids.
     """
     if kernel_id == 2:
         from .helmholtz import EmbeddedOperator
@@ -378,7 +387,8 @@ def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
             ctr = centers(kind, d, s, lo, w)
             diff = x[act_idx][:, None, :] - ctr[None, :, :]
             dist2 = (diff * diff).sum(axis=2)
-            owner = np.argmin(dist2, axis=1)           # first minimum = lowest id
+            best = dist2.min(axis=1, keepdims=True)
+            owner = np.argmax(dist2 <= best * (1.0 + TIE), axis=1)    # first tied centre = lowest id
         snapshot = active.copy()                       # level-synchronous reading
         R2 = (proxy_radius * w) ** 2
         sl = Sublevel(kind=kind, level=ell)
@@ -386,12 +396,15 @@ def factor(points, weights, a, b, c, kernel_id: int, eps: float, proxy_dirs,
             cbox = act_idx[owner == bid]
             if cbox.size == 0:
                 continue
+            sets = {} if trace_sets is not None else None
             bf = _skeletonize(op, S, M, snapshot, cbox, ctr[bid], R2, proxy_radius * w,
-                              proxy_dirs, eps, second_kind, bool(symmetric), use_ldl)
+                              proxy_dirs, eps, second_kind, bool(symmetric), use_ldl, sets)
             sl.boxes.append(bf)
             active[bf.rd] = False
             if trace is not None:
                 trace.append((kind, ell, bid, cbox.size, bf.sk.size, bf.m, bf.ngroups))
+            if trace_sets is not None:
+                trace_sets.append((kind, ell, cbox, sets["near"], sets["groups"], bf.sk, bf.rd))
         sublevels.append(sl)
 
     top = np.nonzero(active)[0]
@@ -455,14 +468,16 @@ def ldl_diag_pivot(B):
 
 
 def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_dirs,
-                 eps, second_kind, symmetric=False, use_ldl=False) -> BoxFactor:
+                 eps, second_kind, symmetric=False, use_ldl=False, sets=None) -> BoxFactor:
     x = op.x
     n = cbox.size
     inbox = np.zeros(op.N, dtype=bool)
     inbox[cbox] = True
     cand = snapshot & ~inbox
     diff = x - center[None, :]
-    near = cand & ((diff * diff).sum(axis=1) < R2)
+    # strictly inside: within a relative TIE of the radius counts as on it
+    # (grids put DOFs exactly on the proxy sphere; rounding must not decide)
+    near = cand & ((diff * diff).sum(axis=1) < R2 * (1.0 - TIE))
     sci = cand & M[:, cbox].any(axis=1)
     cN = np.nonzero(near | sci)[0]
 
@@ -485,6 +500,9 @@ def _skeletonize(op: Operator, S, M, snapshot, cbox, center, R2, radius, proxy_d
 
     # groups by structural SCI pattern (Lemma 4.2)
     groups = sci_groups(M[np.ix_(cN, cbox)]) if second_kind else [np.arange(n)]
+    if sets is not None:
+        sets["near"] = cN.copy()
+        sets["groups"] = [cbox[g] for g in groups]
 
     sk_l, rd_l, T_blocks = [], [], []
     for g in groups:

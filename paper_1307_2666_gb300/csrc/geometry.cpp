@@ -3,7 +3,13 @@
 // The arithmetic that decides memberships (cell floor indices, squared
 // distances to edge/face centres and to the proxy centre) is written as plain
 // IEEE double operations in a fixed order and compiled without FMA
-// contraction, so that the same inputs always give the same index sets.
+// contraction, so that the same inputs always give the same index sets.  A
+// DOF joins the nearest edge/face centre; centres whose squared distance is
+// within a relative kTie of the nearest one count as tied, and the lowest
+// centre id wins.  On a grid, tied centres are exactly equidistant, but the
+// computed distances can differ in the last bits (three squares summed in
+// different orders; a cube root for the root box's cell side that is not
+// correctly rounded in every math library moves all centres by an ulp).
 #include "geometry.h"
 
 #include <algorithm>
@@ -16,6 +22,9 @@
 #endif
 
 namespace hif {
+
+// relative distance difference within which two centres count as tied
+constexpr double kTie = 0x1p-40;
 
 void root_box(const double* x, const double* w, int64_t N, int dim, double lo[3], double* W) {
     double hi[3];
@@ -125,34 +134,37 @@ void partition(const Tree& t, const double* x, int kind, int s, const std::vecto
             owner[a] = flat;
             continue;
         }
-        int64_t best_id = -1;
-        double best = 0.0;
-        for (int q = 0; q < fam.nf; ++q) {
-            int jlo[3], jhi[3];
-            for (int k = 0; k < 3; ++k) { jlo[k] = 0; jhi[k] = 0; }
-            for (int k = 0; k < dim; ++k) {
-                if (fam.I[q][k]) { jlo[k] = std::max(1, c[k] - 1); jhi[k] = std::min(s - 1, c[k] + 2); }
-                else { jlo[k] = std::max(0, c[k] - 1); jhi[k] = std::min(s - 1, c[k] + 1); }
+        // the candidate centres around the DOF's cell, visited twice: for the
+        // smallest distance, then for the lowest id within kTie of it
+        auto visit = [&](auto&& f) {
+            for (int q = 0; q < fam.nf; ++q) {
+                int jlo[3], jhi[3];
+                for (int k = 0; k < 3; ++k) { jlo[k] = 0; jhi[k] = 0; }
+                for (int k = 0; k < dim; ++k) {
+                    if (fam.I[q][k]) { jlo[k] = std::max(1, c[k] - 1); jhi[k] = std::min(s - 1, c[k] + 2); }
+                    else { jlo[k] = std::max(0, c[k] - 1); jhi[k] = std::min(s - 1, c[k] + 1); }
+                }
+                for (int j0 = jlo[0]; j0 <= jhi[0]; ++j0)
+                    for (int j1 = jlo[1]; j1 <= jhi[1]; ++j1)
+                        for (int j2 = jlo[2]; j2 <= jhi[2]; ++j2) {
+                            const int js[3] = {j0, j1, j2};
+                            int64_t id = 0;
+                            double d2 = 0.0;
+                            for (int k = 0; k < dim; ++k) {
+                                const double ck = t.lo[k] + ((double)js[k] + (fam.I[q][k] ? 0.0 : 0.5)) * w;
+                                const double dd = p[k] - ck;
+                                d2 = d2 + dd * dd;
+                                id = id * ext[q][k] + (fam.I[q][k] ? js[k] - 1 : js[k]);
+                            }
+                            f(id + fam_off[q], d2);
+                        }
             }
-            for (int j0 = jlo[0]; j0 <= jhi[0]; ++j0)
-                for (int j1 = jlo[1]; j1 <= jhi[1]; ++j1)
-                    for (int j2 = jlo[2]; j2 <= jhi[2]; ++j2) {
-                        const int js[3] = {j0, j1, j2};
-                        int64_t id = 0;
-                        double d2 = 0.0;
-                        for (int k = 0; k < dim; ++k) {
-                            const double ck = t.lo[k] + ((double)js[k] + (fam.I[q][k] ? 0.0 : 0.5)) * w;
-                            const double dd = p[k] - ck;
-                            d2 = d2 + dd * dd;
-                            id = id * ext[q][k] + (fam.I[q][k] ? js[k] - 1 : js[k]);
-                        }
-                        id += fam_off[q];
-                        if (best_id < 0 || d2 < best || (d2 == best && id < best_id)) {
-                            best = d2;
-                            best_id = id;
-                        }
-                    }
-        }
+        };
+        double best = -1.0;
+        visit([&](int64_t, double d2) { if (best < 0.0 || d2 < best) best = d2; });
+        const double lim = best * (1.0 + kTie);
+        int64_t best_id = -1;
+        visit([&](int64_t id, double d2) { if (d2 <= lim && (best_id < 0 || id < best_id)) best_id = id; });
         owner[a] = best_id;
     }
     // bucket by owner (stable: ascending DOF ids inside a box)
@@ -249,7 +261,10 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
     const int dim = t.dim;
     const double w = t.W / s;
     const double R = proxy_radius * w;
-    const double R2 = R * R;
+    // strictly inside the proxy sphere: a DOF within a relative kTie of the
+    // radius counts as on it (grids put DOFs exactly there, e.g. the 3D
+    // faces of a 3 x 3 x 3 cell; rounding must not decide)
+    const double R2 = R * R * (1.0 - kTie);
     const int nsub = (int)sci.blk.size();
     // bins of the active DOFs: cells of width w at this level
     int64_t nbins = 1;

@@ -1,0 +1,126 @@
+"""The library's host planner against the oracle, on the CPU.
+
+The planner (csrc/geometry.cpp: tree, partition into cells, edges and faces,
+near fields, column groups) runs on the host in the GPU path; here it is
+compiled with a small driver (tests/plan_replay.cpp) and fed the oracle's own
+skeletonization decisions sublevel by sublevel, so that every plan can be
+compared with the oracle's index sets box by box: the root box and depth
+(Sec. 3.1 / 4.1), the sublevel sequence (Algorithms 4.1 / 4.2), and per box
+its DOFs, its near field (the proxy interior and the SCI-coupled DOFs,
+Sec. 3.3 / 4.3) and its column groups (Sec. 4.4, Lemma 4.2).
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import hif_inputs as hi
+from oracle import hifie
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KIND = {"cell": 0, "face": 1, "edge": 2}
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    out = tmp_path_factory.mktemp("replay") / "plan_replay"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(out),
+                    os.path.join(ROOT, "tests", "plan_replay.cpp"),
+                    os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")], check=True)
+    return str(out)
+
+
+def _replay(driver, pb, eps, c=None, occupancy=64):
+    c = pb.c if c is None else c
+    sets = []
+    hifie.factor(pb.points, pb.weights, pb.a, pb.b, c, pb.kernel_id, eps, pb.proxy, occupancy=occupancy,
+                 trace_sets=sets)
+    subs = []                                   # the oracle's boxes, sublevel by sublevel
+    for e in sets:
+        if not subs or subs[-1][0] != (e[0], e[1]):
+            subs.append(((e[0], e[1]), []))
+        subs[-1][1].append(e)
+    N, d = pb.points.shape
+    lines = [f"{N} {d} {occupancy} 1.5 1", " ".join(repr(float(v)) for v in pb.points.reshape(-1)),
+             " ".join(repr(float(v)) for v in pb.weights), str(len(subs))]
+    for _, boxes in subs:
+        lines.append(str(len(boxes)))
+        for e in boxes:
+            sk, rd = e[5], e[6]
+            lines.append(" ".join(map(str, [sk.size, *sk.tolist(), rd.size, *rd.tolist()])))
+    r = subprocess.run([driver], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    return subs, r.stdout.split("\n")
+
+
+def _parse(out):
+    tree = plan = None
+    subs = []
+    it = iter(out)
+    for ln in it:
+        f = ln.split()
+        if not f:
+            continue
+        if f[0] == "TREE":
+            tree = (np.array([float(v) for v in f[1:4]]), float(f[4]), int(f[5]))
+        elif f[0] == "PLAN":
+            v = list(map(int, f[1:]))
+            plan = list(zip(v[0::2], v[1::2]))
+        elif f[0] == "SUB":
+            subs.append(((int(f[1]), int(f[2])), []))
+        elif f[0] == "BOX":
+            mem = np.array(next(it).split()[2:], dtype=np.int64)
+            near = np.array(next(it).split()[2:], dtype=np.int64)
+            ng = int(next(it).split()[1])
+            groups = []
+            for _ in range(ng):
+                g = next(it).split()
+                groups.append(np.array(g[3:], dtype=np.int64))
+            subs[-1][1].append((mem, near, groups))
+    return tree, plan, subs
+
+
+@pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "3d", "3d-occ27", "3d-n16"])
+def test_host_plan_matches_oracle_sets(driver, case):
+    occ = 64
+    if case == "2d-symmetric":
+        pb, c, eps = hi.volume_problem(32, 2, smooth_seed=21), None, 1e-6
+    elif case == "2d-b-ne-c-ragged":
+        pb = hi.volume_problem(48, 2, smooth_seed=22)
+        c, eps = pb.c * (1.0 + 0.5 * hi.smooth_field(pb.points, 23)), 1e-6
+    elif case == "2d-n64":
+        pb, c, eps = hi.volume_problem(64, 2, smooth_seed=1002), None, 1e-6
+    elif case == "3d":
+        pb, c, eps = hi.volume_problem(12, 3, smooth_seed=24), None, 1e-3
+    elif case == "3d-occ27":
+        pb, c, eps, occ = hi.volume_problem(12, 3, smooth_seed=5), None, 1e-3, 27
+    else:
+        pb, c, eps = hi.volume_problem(16, 3, smooth_seed=25), None, 1e-3
+    osubs, out = _replay(driver, pb, eps, c, occupancy=occ)
+    tree, plan, csubs = _parse(out)
+    # tree and sublevel sequence
+    lo, W = hifie.root_box(pb.points, pb.weights)
+    L = hifie.num_levels(pb.points, lo, W, occ)
+    d = pb.points.shape[1]
+    np.testing.assert_allclose(tree[0][:d], lo, rtol=0, atol=1e-15)
+    assert tree[1] == pytest.approx(W, rel=1e-15) and tree[2] == L
+    assert plan == [(KIND[k], l) for k, l in hifie.sublevel_plan(d, L)]
+    # every sublevel's boxes, near fields and groups
+    assert [s[0] for s in csubs] == [(KIND[k], l) for (k, l), _ in osubs]
+    nbox = ngrp = 0
+    for (_, oboxes), (_, cboxes) in zip(osubs, csubs):
+        assert len(cboxes) == len(oboxes)
+        for o, (mem, near, groups) in zip(oboxes, cboxes):
+            np.testing.assert_array_equal(mem, o[2])
+            np.testing.assert_array_equal(near, o[3])
+            assert len(groups) == len(o[4])
+            for g, og in zip(groups, o[4]):
+                np.testing.assert_array_equal(g, og)
+            nbox += 1
+            ngrp += len(groups)
+    # the comparison covered SCI groups, not only single-group boxes
+    assert nbox > 20 and ngrp > nbox
