@@ -124,8 +124,8 @@ def test_graphs_and_autotune_leave_results_unchanged(P):
     assert counts[0] == counts[1] == counts[2] == counts[3] > 0
 
 
-def test_config3_batched_256_problems_refined(P):
-    # the batched configuration at its stated size: 256 problems with n drawn
+def test_batched_256_problems_n32_to_256_refined(P):
+    # the batched workload at full size: 256 problems with n drawn
     # from {32, 48, ..., 256} (seed 1004), b = c = 1 + 0.5 phi_p (seed
     # 2000 + p), 4 Gaussian right-hand sides each (seed 3000 + p), eps 1e-6,
     # FP32 batched handle refined to 1e-10; every problem's residual is

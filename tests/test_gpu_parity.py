@@ -197,7 +197,7 @@ def test_direct_sum_3d_grid(lib):
 
 # ---------------------------------------------------------- factorization --
 
-def test_config1_accuracy_and_rank_parity(lib):
+def test_n64_eps1e6_accuracy_and_rank_parity(lib):
     """n=64 (N=4096), log kernel, a=1, b=c=1, eps=1e-6, FP64, 1 RHS."""
     P = lib
     eps = 1e-6
@@ -409,7 +409,7 @@ def test_full_size_3d_refined_solve_residual_by_oracle_rows(lib):
 
 @pytest.mark.parametrize("n,occ", [(12, 27), (16, 64)])
 def test_3d_eps_1e6_against_dense(lib, n, occ):
-    # the 3D configuration's tighter tolerance: cells -> faces -> edges at
+    # the 3D grid at the tighter tolerance: cells -> faces -> edges at
     # eps = 1e-6 with b = c = 1 + 0.5 phi, FP64, against the dense solve
     P = lib
     eps = 1e-6

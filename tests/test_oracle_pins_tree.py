@@ -103,7 +103,7 @@ def test_3d_face_and_edge_centres_are_interior(s):
         assert ge == _shared_entities(s, 3, 2)
 
 
-def test_config_counts_per_level():
+def test_box_counts_per_level_2d_n64_n1024_3d_n64():
     # n = 64 (2D, occupancy 64): L = 3, cells 64/16/4, edges 112/24/4;
     # n = 1024: edges 2 s (s - 1) = 32512, 8064, 1984, 480, 112, 24, 4;
     # 3D n = 64 (occupancy 64): L = 4, faces 11520/1344/144/12, edges
@@ -125,8 +125,8 @@ def test_config_counts_per_level():
     assert [k for k, _ in hifie.sublevel_plan(3, 2)] == ["cell", "face", "edge", "cell", "face", "edge"]
 
 
-def test_config_1_factor_visits_every_box():
-    # the oracle's sublevel loop on config 1 (n = 64, eps = 1e-6): every cell
+def test_n64_factor_visits_every_box():
+    # the oracle's sublevel loop on the 2D n = 64 grid at eps = 1e-6: every cell
     # and every interior edge holds active DOFs, so the non-empty boxes per
     # sublevel are exactly the counts above
     pb = hi.volume_problem(64, 2, rhs_seed=1001)
@@ -138,7 +138,7 @@ def test_config_1_factor_visits_every_box():
     assert [per[(k, l)] for k, l in hifie.sublevel_plan(2, 3)] == [64, 112, 16, 24, 4, 4]
     assert [(sl.kind, sl.level, len(sl.boxes)) for sl in F.sublevels] == [
         ("cell", 0, 64), ("edge", 0, 112), ("cell", 1, 16), ("edge", 1, 24), ("cell", 2, 4), ("edge", 2, 4)]
-    # every leaf cell of config 1 compresses all 64 of its DOFs
+    # every leaf cell of the n = 64 grid compresses all 64 of its DOFs
     assert all(b.n == 64 for b in F.sublevels[0].boxes)
 
 
