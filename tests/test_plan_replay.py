@@ -84,7 +84,8 @@ def _parse(out):
     return tree, plan, subs
 
 
-@pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "3d", "3d-occ27", "3d-n16"])
+@pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "2d-odd-cells", "3d", "3d-occ27",
+                                  "3d-n16"])
 def test_host_plan_matches_oracle_sets(driver, case):
     occ = 64
     if case == "2d-symmetric":
@@ -94,6 +95,9 @@ def test_host_plan_matches_oracle_sets(driver, case):
         c, eps = pb.c * (1.0 + 0.5 * hi.smooth_field(pb.points, 23)), 1e-6
     elif case == "2d-n64":
         pb, c, eps = hi.volume_problem(64, 2, smooth_seed=1002), None, 1e-6
+    elif case == "2d-odd-cells":
+        # 5 x 5 DOFs per leaf cell: DOFs lie exactly on the proxy circles of the edges
+        pb, c, eps = hi.volume_problem(40, 2, smooth_seed=26), None, 1e-6
     elif case == "3d":
         pb, c, eps = hi.volume_problem(12, 3, smooth_seed=24), None, 1e-3
     elif case == "3d-occ27":
