@@ -11,6 +11,7 @@
 // different orders; a cube root for the root box's cell side that is not
 // correctly rounded in every math library moves all centres by an ulp).
 #include "geometry.h"
+#include "hif_types.h"
 
 #include <algorithm>
 #include <cmath>
@@ -244,6 +245,38 @@ inline uint64_t mix64(uint64_t z) {
 }
 
 }  // namespace
+
+// S of the grid table T(o) = G(h |o|) (o != 0), T(0) = k0, over the offsets
+// o in [0, n)^dim, in fixed chunks so that the sum is the same on every run.
+double table_spread(int n, int dim, double h, int kernel_id, double k0) {
+    const int64_t tot = dim == 2 ? (int64_t)n * n : (int64_t)n * n * n;
+    constexpr int64_t NCH = 256;
+    std::vector<double> ss(NCH, 0.0), mx(NCH, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < NCH; ++c) {
+        const int64_t e0 = tot * c / NCH, e1 = tot * (c + 1) / NCH;
+        for (int64_t e = e0; e < e1; ++e) {
+            int64_t t = e;
+            double r2 = 0.0;
+            for (int q = 0; q < dim; ++q) {
+                const double dd = (double)(t % n) * h;
+                r2 += dd * dd;
+                t /= n;
+            }
+            const double v = e == 0 ? k0
+                             : kernel_id == 0 ? -std::log(r2) * (0.25 / kPi)
+                                              : (0.25 / kPi) / std::sqrt(r2);
+            ss[c] += v * v;
+            mx[c] = std::max(mx[c], std::fabs(v));
+        }
+    }
+    double s = 0.0, m = 0.0;
+    for (int64_t c = 0; c < NCH; ++c) {
+        s += ss[c];
+        m = std::max(m, mx[c]);
+    }
+    return s > 0.0 ? m * std::sqrt((double)tot / s) : 1.0;
+}
 
 void geometry_trace(bool on, double* ms) {
     if (ms)

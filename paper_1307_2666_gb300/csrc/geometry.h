@@ -64,6 +64,12 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
                        const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p,
                        NearCache* cache = nullptr);
 
+// Spread S = max|T| sqrt(#T) / |T|_2 of the uniform-grid table T(o) =
+// G(h |o|) (o != 0; kernel 0: -log(r)/(2 pi), kernel 1: 1/(4 pi r)), T(0) =
+// k0, over the offsets o in [0, n)^dim: the scale of the short tensor-core
+// sums' relative error (the refinement's error estimate).
+double table_spread(int n, int dim, double h, int kernel_id, double k0);
+
 // Trace of build_near_groups: returns the per-phase times summed since the
 // previous call into ms[6] (bins, gather: wall ms; proxy scan, SCI patterns,
 // near list, groups: thread ms) and sets the collection on or off.

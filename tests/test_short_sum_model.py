@@ -101,6 +101,29 @@ def test_short_sum_errors_within_the_model(n, dim):
     assert 60 < err[4] / err[5] < 1000 and 60 < err[5] / err[6] < 1000
 
 
+def test_library_spread_matches_the_model(tmp_path):
+    # the spread the library computes for its error estimate (table_spread,
+    # host code) is the one the constants above were measured against
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = tmp_path / "spread"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(exe),
+                    os.path.join(ROOT, "tests", "spread_driver.cpp"),
+                    os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")], check=True)
+    cases = [(64, 2), (1024, 2), (16, 3), (64, 3)]
+    inp = []
+    for n, dim in cases:
+        T, _ = _table(n, dim)
+        inp.append(f"{n} {dim} {float(T[(0,) * dim])!r}")
+    out = subprocess.run([str(exe)], input="\n".join(inp) + "\n", capture_output=True, text=True, check=True)
+    got = [float(v) for v in out.stdout.split()]
+    for (n, dim), g in zip(cases, got):
+        assert g == pytest.approx(_table(n, dim)[1], rel=1e-12), (n, dim)
+
+
 def test_spread_grows_with_the_3d_grid():
     # the 1/r table's spread roughly doubles with n (the far field dominates
     # |T|_2), the 2D log table's grows like log n
