@@ -26,6 +26,7 @@
 #include "geometry.h"
 #include "launch.h"
 #include "prof.h"
+#include "refine_rule.h"
 
 namespace hif {
 
@@ -1763,49 +1764,11 @@ static std::vector<double> seg_norms(hif_handle h, const double* v, int nrhs) {
     return out;
 }
 
-// Short digit sets for the residuals of the refinement.  A residual computed
-// with an error d enters the next one in full (r' = (I - A F^{-1}) r - d), so
-// only the residual that decides convergence has to be the full sum; another
-// may take KD < 8 digit classes while its error stays below both 0.05 tol and
-// 1e-4 of the residual itself (an FP32 factor reduces the residual by at most
-// ~10^3 per step, so the next residual stays >= 10x above that error).  The
-// error of a short sum is estimated as C_KD S Y.  The dropped digits sit at a
-// fixed level below max|T| whatever the entry, so the relative error of
-// y = K v grows with the table's spread S = max|T| sqrt(#T) / |T|_2; C_KD
-// bounds the ratio of the two measured for Gaussian sources (exact integer
-// convolutions of the digits, self term included: 2D log kernel n = 64..1024,
-// S = 8..13, ratios up to 3.2e-9, 1.4e-11, 6.2e-14; 3D 1/r kernel n = 16..64,
-// S = 23..104, up to 1.9e-9, 8.6e-12, 3.8e-14; the spread of the ratios comes
-// from where max|T| and max|v| fall against their power-of-two scales), and
-// Y = |b K c u| / |f|, the size of the kernel part of A u, is measured after
-// every residual.
-static constexpr double kShortErr[3] = {4e-9, 1.6e-11, 7e-14};      // C_KD, KD = 4, 5, 6
-
-
 static bool short_residuals_on(hif_handle h, double tol) {
     if (h->opt.direct_precision != 2 || tol < 1e-11 || !env_int("HIF_SHORT_RESIDUAL", 1)) return false;
     for (auto& sp : h->segs)
         if (!sp->grid) return false;
     return true;
-}
-
-// Digit classes of residual k (8: the full sum); SY = S Y from the last
-// residual.  Step 0 has no Y yet and takes 5 classes after an FP32
-// factorization (its first residual is of the order of the 2^-17 tolerance
-// floor or above), 6 after an FP64 one; step k >= 1 takes the fewest classes
-// whose estimated error C_KD S Y meets the bound above for its predicted
-// residual, the last one times the last contraction (sqrt of the
-// first residual for the first contraction), if that prediction is above
-// 10 tol, and the full sum otherwise.
-static int residual_classes(hif_handle h, int k, const std::vector<double>& hist, double SY, double tol) {
-    if (k == 0) return h->precision == 1 ? 5 : 6;
-    const double last = hist[k - 1];
-    const double rho = k == 1 ? std::sqrt(hist[0]) : (hist[k - 2] > 0 ? last / hist[k - 2] : 0.0);
-    const double pred = last * rho;
-    if (!(pred > 10.0 * tol)) return 8;
-    for (int kd = 4; kd <= 6; ++kd)
-        if (kShortErr[kd - 4] * SY <= std::max(0.05 * tol, 1e-4 * pred)) return kd;
-    return 8;
 }
 
 // Iterative refinement: u = F^{-1} f; r = f - A u; u += F^{-1} r ...  The
@@ -1828,7 +1791,7 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
     double worst = 0, Y = 0;
     std::vector<double> hist;
     for (;; ++it) {
-        int classes = shorts ? residual_classes(h, it, hist, S * Y, tol) : 8;
+        int classes = shorts ? short_residual_classes(it, h->precision == 1, hist.data(), S * Y, tol) : 8;
         for (;;) {
             matvec_dev(h, trans, u, N, r.as<double>(), N, nrhs, classes);
             HIF_CUDA(launch_axpby(N, nrhs, 1.0, f, N, -1.0, r.as<double>(), N, h->st));
@@ -1845,9 +1808,7 @@ static hif_status refine_ir(hif_handle h, int trans, const double* f, double* u,
             if (env_int("HIF_TRACE", 0))
                 std::fprintf(stderr, "[hif] refinement %d: relative residual %.3e (%d digit classes, |bKcu|/|f| %.2e)\n",
                              it, worst, classes, Y);
-            if (classes == 8 ||
-                (worst > tol && it < maxit && kShortErr[classes - 4] * S * Y <= std::max(0.05 * tol, 1e-4 * worst)))
-                break;
+            if (classes == 8 || short_residual_usable(classes, worst, S * Y, tol, it >= maxit)) break;
             classes = 8;
         }
         hist.push_back(worst);

@@ -24,7 +24,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _constants():
-    src = open(os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "api.cpp")).read()
+    src = open(os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "refine_rule.cpp")).read()
     m = re.search(r"kShortErr\[3\]\s*=\s*\{([^}]*)\}", src)
     return [float(v) for v in m.group(1).split(",")]
 
@@ -131,3 +131,47 @@ def test_spread_grows_with_the_3d_grid():
     s2 = [_table(n, 2)[1] for n in (64, 128)]
     assert 1.7 < s3[1] / s3[0] < 2.3
     assert 1.0 < s2[1] / s2[0] < 1.3
+
+
+def _build(tmp_path, name, src, extra=()):
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = tmp_path / name
+    subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(exe),
+                    os.path.join(ROOT, "tests", src),
+                    *[os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", f) for f in extra]], check=True)
+    return str(exe)
+
+
+def test_refinement_digit_rule(tmp_path):
+    # the rule the refinement applies (csrc/refine_rule.cpp), on the residual
+    # sequences it meets: the bench workload's FP32 solve (9.45e-6, 2.48e-8,
+    # 8.19e-11; S = 12.65, |bKcu|/|f| = 2.1e-4), an FP64 solve, a tiny kernel
+    # part, and the cases that must fall back to the full sum
+    import subprocess
+    exe = _build(tmp_path, "rule", "refine_rule_driver.cpp", ["refine_rule.cpp"])
+    C = _constants()
+    SY = 12.65 * 2.1e-4
+    tol = 1e-10
+    q = [
+        f"C 0 1 0 {tol} 0",                                 # first residual, FP32 factor
+        f"C 0 0 0 {tol} 0",                                 # first residual, FP64 factor
+        f"C 1 1 {SY!r} {tol} 1 9.45e-6",                    # second: 4 classes estimated too coarse
+        f"C 2 1 {SY!r} {tol} 2 9.45e-6 2.48e-8",            # third: predicted below 10 tol
+        f"C 1 1 1e-6 {tol} 1 9.45e-6",                      # tiny kernel part: 4 classes
+        f"C 1 1 1e3 {tol} 1 9.45e-6",                       # huge kernel part: the full sum
+        f"C 1 1 nan {tol} 1 9.45e-6",                       # no estimate: the full sum
+        f"U 5 9.45e-6 {SY!r} {tol} 0",                      # usable
+        f"U 5 5e-11 {SY!r} {tol} 0",                        # at or below tol: recompute in full
+        f"U 5 9.45e-6 {SY!r} {tol} 1",                      # last step: recompute in full
+        f"U 4 2.48e-8 {SY!r} {tol} 0",                      # estimate above the bound
+        f"U 6 2.48e-8 {SY!r} {tol} 0",
+        f"U 8 2.48e-8 {SY!r} {tol} 0",                      # not a short sum
+    ]
+    out = subprocess.run([exe], input="\n".join(q) + "\n", capture_output=True, text=True, check=True).stdout.split()
+    got = list(map(int, out))
+    assert C[0] * SY > 0.05 * tol and C[1] * SY <= 0.05 * tol       # the premise of the bench case
+    assert got == [5, 6, 5, 8, 4, 8, 8, 1, 0, 0, 0, 1, 0]
