@@ -2532,7 +2532,7 @@ hif_status hif_kernel_block(const double* points, int64_t N, int dim, const doub
             o = dout.as<double>();
         }
         HIF_CUDA(launch_kernel_block(g, drp, nr, dcp, nc, o, ldo, st));
-        if (!dev_out && nr * nc)
+        if (!dev_out && nr > 0 && nc > 0)
             HIF_CUDA(cudaMemcpyAsync(out, o, sizeof(double) * ldo * nc, cudaMemcpyDeviceToHost, st));
         HIF_CUDA(cudaStreamSynchronize(st));
     });

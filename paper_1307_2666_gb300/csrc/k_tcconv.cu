@@ -304,7 +304,6 @@ struct Walk {
         return dim == 2 ? (int64_t)il : (int64_t)il * n + i1;
     }
     __device__ int64_t slots() const { return (int64_t)(dmax + 1) * (dim == 3 ? n : 1) * nc; }
-    __device__ bool tile_end() const { return c == nc - 1 && (dim == 2 || j1 == n - 1) && d0 == dmax; }
     __device__ void next() {
         if (++c < nc) return;
         c = 0;
