@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <numeric>
 #include <chrono>
 #include <unordered_map>
@@ -26,6 +27,59 @@ namespace hif {
 
 // relative distance difference within which two centres count as tied
 constexpr double kTie = 0x1p-40;
+
+// Stable counting sort of the indices 0..n-1 by key[a] in [0, nkeys): on
+// return order[off[k] .. off[k+1]) lists the a with key k, ascending.  With
+// several threads every thread counts and places one contiguous range of a,
+// the ranges of one key following one another in order, so the result is the
+// serial one.
+// Work array whose entries are left uninitialized (every use writes them
+// before reading): large per-sublevel buffers skip the serial zero fill.
+template <class T>
+struct RawBuf {
+    std::unique_ptr<T[]> p;
+    explicit RawBuf(size_t n) : p(new T[n > 0 ? n : 1]) {}
+    T& operator[](size_t i) { return p[i]; }
+    const T& operator[](size_t i) const { return p[i]; }
+    T* data() { return p.get(); }
+};
+
+static void stable_bucket(const int64_t* key, int64_t n, int64_t nkeys, std::vector<int64_t>& off, int64_t* order) {
+    off.assign(nkeys + 1, 0);
+    int nch = 1;
+#ifdef _OPENMP
+    nch = omp_get_max_threads();
+#endif
+    if (n < 65536 || (int64_t)nch * nkeys > ((int64_t)1 << 22)) nch = 1;
+    if (nch == 1) {
+        for (int64_t a = 0; a < n; ++a) off[key[a] + 1]++;
+        for (int64_t k = 0; k < nkeys; ++k) off[k + 1] += off[k];
+        std::vector<int64_t> pos(off.begin(), off.end() - 1);
+        for (int64_t a = 0; a < n; ++a) order[pos[key[a]]++] = a;
+        return;
+    }
+    std::vector<int64_t> cnt((size_t)nch * nkeys, 0);
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < nch; ++c) {
+        int64_t* h = &cnt[(size_t)c * nkeys];
+        for (int64_t a = n * c / nch; a < n * (c + 1) / nch; ++a) h[key[a]]++;
+    }
+    int64_t run = 0;
+    for (int64_t k = 0; k < nkeys; ++k) {
+        off[k] = run;
+        for (int c = 0; c < nch; ++c) {
+            const int64_t v = cnt[(size_t)c * nkeys + k];
+            cnt[(size_t)c * nkeys + k] = run;
+            run += v;
+        }
+    }
+    off[nkeys] = run;
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < nch; ++c) {
+        int64_t* pos = &cnt[(size_t)c * nkeys];
+        for (int64_t a = n * c / nch; a < n * (c + 1) / nch; ++a) order[pos[key[a]]++] = a;
+    }
+}
 
 void root_box(const double* x, const double* w, int64_t N, int dim, double lo[3], double* W) {
     double hi[3];
@@ -121,7 +175,7 @@ void partition(const Tree& t, const double* x, int kind, int s, const std::vecto
     }
     const int64_t ncent = fam_off[fam.nf];
     const int64_t na = (int64_t)active_ids.size();
-    std::vector<int64_t> owner(na);
+    RawBuf<int64_t> owner((size_t)na);
 
 #pragma omp parallel for schedule(static)
     for (int64_t a = 0; a < na; ++a) {
@@ -135,8 +189,8 @@ void partition(const Tree& t, const double* x, int kind, int s, const std::vecto
             owner[a] = flat;
             continue;
         }
-        // the candidate centres around the DOF's cell, visited twice: for the
-        // smallest distance, then for the lowest id within kTie of it
+        // the candidate centres around the DOF's cell: the smallest distance,
+        // then the lowest id within kTie of it
         auto visit = [&](auto&& f) {
             for (int q = 0; q < fam.nf; ++q) {
                 int jlo[3], jhi[3];
@@ -161,28 +215,45 @@ void partition(const Tree& t, const double* x, int kind, int s, const std::vecto
                         }
             }
         };
+        // at most 3 families x (4 x 4 x 3) candidates (3D edges)
+        constexpr int MAXC = 160;
+        int64_t cid[MAXC];
+        double cd2[MAXC];
+        int ncand = 0;
         double best = -1.0;
-        visit([&](int64_t, double d2) { if (best < 0.0 || d2 < best) best = d2; });
+        visit([&](int64_t id, double d2) {
+            if (ncand < MAXC) {
+                cid[ncand] = id;
+                cd2[ncand] = d2;
+                ++ncand;
+            }
+            if (best < 0.0 || d2 < best) best = d2;
+        });
         const double lim = best * (1.0 + kTie);
         int64_t best_id = -1;
-        visit([&](int64_t id, double d2) { if (d2 <= lim && (best_id < 0 || id < best_id)) best_id = id; });
+        for (int e = 0; e < ncand; ++e)
+            if (cd2[e] <= lim && (best_id < 0 || cid[e] < best_id)) best_id = cid[e];
         owner[a] = best_id;
     }
-    // bucket by owner (stable: ascending DOF ids inside a box)
-    std::vector<int64_t> count(ncent + 1, 0);
-    for (int64_t a = 0; a < na; ++a) count[owner[a] + 1]++;
-    for (int64_t b = 0; b < ncent; ++b) count[b + 1] += count[b];
-    std::vector<int> sorted(na);
-    {
-        std::vector<int64_t> pos(count.begin(), count.end() - 1);
-        for (int64_t a = 0; a < na; ++a) sorted[pos[owner[a]]++] = active_ids[a];
-    }
-    out.box_off.clear();
-    out.members.clear();
-    out.centers.clear();
-    out.box_off.push_back(0);
-    for (int64_t b = 0; b < ncent; ++b) {
-        if (count[b + 1] == count[b]) continue;
+    // bucket by owner (stable: ascending DOF ids inside a box); the members
+    // of the non-empty centres, in centre order, are the bucketed ids
+    std::vector<int64_t> count;
+    RawBuf<int64_t> order((size_t)na);
+    stable_bucket(owner.data(), na, ncent, count, order.data());
+    out.members.resize(na);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < na; ++e) out.members[e] = active_ids[order[e]];
+    std::vector<int64_t> used;                       // the non-empty centres
+    for (int64_t b = 0; b < ncent; ++b)
+        if (count[b + 1] > count[b]) used.push_back(b);
+    const int nbox = (int)used.size();
+    out.box_off.resize(nbox + 1);
+    out.centers.resize(3 * (size_t)nbox);
+    out.box_off[0] = 0;
+#pragma omp parallel for schedule(static)
+    for (int bi = 0; bi < nbox; ++bi) {
+        const int64_t b = used[bi];
+        out.box_off[bi + 1] = count[b + 1];
         // centre of box b
         int q = 0;
         while (b >= fam_off[q + 1]) ++q;
@@ -193,16 +264,11 @@ void partition(const Tree& t, const double* x, int kind, int s, const std::vecto
             rem /= ext[q][k];
             if (fam.I[q][k]) js[k] += 1;
         }
-        for (int k = 0; k < 3; ++k) {
-            out.centers.push_back(k < dim ? t.lo[k] + ((double)js[k] + (fam.I[q][k] ? 0.0 : 0.5)) * w : 0.0);
-        }
-        for (int64_t e = count[b]; e < count[b + 1]; ++e) {
-            out.members.push_back(sorted[e]);
-            box_of[sorted[e]] = (int)(out.box_off.size() - 1);
-        }
-        out.box_off.push_back((int64_t)out.members.size());
+        for (int k = 0; k < 3; ++k)
+            out.centers[3 * (size_t)bi + k] = k < dim ? t.lo[k] + ((double)js[k] + (fam.I[q][k] ? 0.0 : 0.5)) * w : 0.0;
+        for (int64_t e = count[b]; e < count[b + 1]; ++e) box_of[out.members[e]] = bi;
     }
-    out.nbox = (int)out.box_off.size() - 1;
+    out.nbox = nbox;
 }
 
 namespace {
@@ -302,29 +368,28 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
     // bins of the active DOFs: cells of width w at this level
     int64_t nbins = 1;
     for (int k = 0; k < dim; ++k) nbins *= s;
-    std::vector<int64_t> boff(nbins + 1, 0);
-    std::vector<int64_t> bin_of(active_ids.size());
-    for (size_t a = 0; a < active_ids.size(); ++a) {
+    const int64_t nact = (int64_t)active_ids.size();
+    RawBuf<int64_t> bin_of((size_t)nact);
+#pragma omp parallel for schedule(static)
+    for (int64_t a = 0; a < nact; ++a) {
         const double* q = x + (int64_t)dim * active_ids[a];
         int64_t flat = 0;
         for (int k = 0; k < dim; ++k) flat = flat * s + cell_coord(q[k], t.lo[k], w, s);
         bin_of[a] = flat;
-        boff[flat + 1]++;
     }
-    for (int64_t b = 0; b < nbins; ++b) boff[b + 1] += boff[b];
+    std::vector<int64_t> boff;
+    RawBuf<int64_t> border((size_t)nact);
+    stable_bucket(bin_of.data(), nact, nbins, boff, border.data());
     // binned copies of the ids, coordinates and boxes, so that the proxy
     // scans below read contiguous memory
-    std::vector<int> bins(active_ids.size()), bins_box(active_ids.size());
-    std::vector<double> bins_x(active_ids.size() * (size_t)dim);
-    {
-        std::vector<int64_t> pos(boff.begin(), boff.end() - 1);
-        for (size_t a = 0; a < active_ids.size(); ++a) {
-            const int64_t e = pos[bin_of[a]]++;
-            const int i = active_ids[a];
-            bins[e] = i;
-            bins_box[e] = box_of[i];
-            for (int k = 0; k < dim; ++k) bins_x[(size_t)dim * e + k] = x[(int64_t)dim * i + k];
-        }
+    RawBuf<int> bins((size_t)nact), bins_box((size_t)nact);
+    RawBuf<double> bins_x((size_t)nact * dim);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < nact; ++e) {
+        const int i = active_ids[border[e]];
+        bins[e] = i;
+        bins_box[e] = box_of[i];
+        for (int k = 0; k < dim; ++k) bins_x[(size_t)dim * e + k] = x[(int64_t)dim * i + k];
     }
 
     const int nb = p.nbox;
