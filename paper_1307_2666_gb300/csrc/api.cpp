@@ -817,7 +817,15 @@ struct Eliminator {
     }
 };
 
-static void append_plan(SublevelPlan& p, const SublevelPlan& q) {
+static void append_plan(SublevelPlan& p, SublevelPlan&& q) {
+    // the first problem's plan is taken over whole (the offsets of an empty
+    // plan are all 0), which saves copying its near-field lists
+    if (p.nbox == 0 && p.members.empty() && p.near.empty() && p.cols.empty() && p.centers.empty() &&
+        p.grp_col0.empty() && p.box_sci.empty() && p.box_off.size() == 1 && p.near_off.size() == 1 &&
+        p.grp_off.size() == 1 && q.box_off.size() == (size_t)q.nbox + 1) {
+        p = std::move(q);
+        return;
+    }
     const int64_t mo = (int64_t)p.members.size(), no = (int64_t)p.near.size(), go = p.grp_off.back();
     for (int b = 1; b <= q.nbox; ++b) {
         p.box_off.push_back(q.box_off[b] + mo);
@@ -932,9 +940,10 @@ static void run_factor(hif_handle h) {
             const auto q2 = std::chrono::steady_clock::now();
             P.ms_partition += std::chrono::duration<double, std::milli>(q1 - q0).count();
             P.ms_near += std::chrono::duration<double, std::milli>(q2 - q1).count();
-            append_plan(p, ps);
-            radius.insert(radius.end(), ps.nbox, h->opt.proxy_radius * wl);
-            symv.insert(symv.end(), ps.nbox, sg.sym ? 1 : 0);
+            const int nb_seg = ps.nbox;
+            append_plan(p, std::move(ps));
+            radius.insert(radius.end(), nb_seg, h->opt.proxy_radius * wl);
+            symv.insert(symv.end(), nb_seg, sg.sym ? 1 : 0);
         }
     };
     Planned next;
