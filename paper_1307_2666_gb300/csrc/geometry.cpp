@@ -344,6 +344,32 @@ double table_spread(int n, int dim, double h, int kernel_id, double k0) {
     return s > 0.0 ? m * std::sqrt((double)tot / s) : 1.0;
 }
 
+void append_plan(SublevelPlan& p, SublevelPlan&& q) {
+    // the first problem's plan is taken over whole (the offsets of an empty
+    // plan are all 0), which saves copying its near-field lists
+    if (p.nbox == 0 && p.members.empty() && p.near.empty() && p.cols.empty() && p.centers.empty() &&
+        p.grp_col0.empty() && p.box_sci.empty() && p.box_off.size() == 1 && p.near_off.size() == 1 &&
+        p.grp_off.size() == 1 && q.box_off.size() == (size_t)q.nbox + 1) {
+        p = std::move(q);
+        return;
+    }
+    const int64_t mo = (int64_t)p.members.size(), no = (int64_t)p.near.size(), go = p.grp_off.back();
+    for (int b = 1; b <= q.nbox; ++b) {
+        p.box_off.push_back(q.box_off[b] + mo);
+        p.near_off.push_back(q.near_off[b] + no);
+        p.grp_off.push_back(q.grp_off[b] + go);
+    }
+    p.members.insert(p.members.end(), q.members.begin(), q.members.end());
+    p.cols.insert(p.cols.end(), q.cols.begin(), q.cols.end());
+    p.near.insert(p.near.end(), q.near.begin(), q.near.end());
+    p.centers.insert(p.centers.end(), q.centers.begin(), q.centers.end());
+    p.grp_col0.insert(p.grp_col0.end(), q.grp_col0.begin(), q.grp_col0.end());
+    p.grp_n.insert(p.grp_n.end(), q.grp_n.begin(), q.grp_n.end());
+    p.grp_sci.insert(p.grp_sci.end(), q.grp_sci.begin(), q.grp_sci.end());
+    p.box_sci.insert(p.box_sci.end(), q.box_sci.begin(), q.box_sci.end());
+    p.nbox += q.nbox;
+}
+
 void geometry_trace(bool on, double* ms) {
     if (ms)
         for (int q = 0; q < 6; ++q) ms[q] = g_geo_ms[q];

@@ -64,6 +64,11 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
                        const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p,
                        NearCache* cache = nullptr);
 
+// Appends the plan q of the next problem of a batched handle to the combined
+// plan p (boxes, members, near fields and groups concatenated, offsets
+// shifted); the first problem's plan is moved in.
+void append_plan(SublevelPlan& p, SublevelPlan&& q);
+
 // Spread S = max|T| sqrt(#T) / |T|_2 of the uniform-grid table T(o) =
 // G(h |o|) (o != 0; kernel 0: -log(r)/(2 pi), kernel 1: 1/(4 pi r)), T(0) =
 // k0, over the offsets o in [0, n)^dim: the scale of the short tensor-core

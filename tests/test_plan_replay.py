@@ -128,3 +128,62 @@ def test_host_plan_matches_oracle_sets(driver, case):
             ngrp += len(groups)
     # the comparison covered SCI groups, not only single-group boxes
     assert nbox > 20 and ngrp > nbox
+
+
+def test_batched_plans_concatenate(tmp_path):
+    # a batched handle's sublevel plan is its problems' plans one after the
+    # other (append_plan): every array concatenated, the box, near-field and
+    # group offsets shifted by what precedes them; 1 to 4 problems, empty
+    # near fields included
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = tmp_path / "append"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(exe),
+                    os.path.join(ROOT, "tests", "plan_append_driver.cpp"),
+                    os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")], check=True)
+    rng = np.random.default_rng(3)
+    for trial in range(40):
+        plans = []
+        for _ in range(int(rng.integers(1, 5))):
+            boxes = []
+            for _ in range(int(rng.integers(1, 6))):
+                mem = rng.integers(0, 1000, int(rng.integers(1, 6))).tolist()
+                near = rng.integers(0, 1000, int(rng.integers(0, 6))).tolist()
+                groups = [(int(rng.integers(0, 5)), int(rng.integers(1, 5)), int(rng.integers(0, 2)))
+                          for _ in range(int(rng.integers(1, 3)))]
+                boxes.append((mem, near, groups, int(rng.integers(0, 2)), rng.standard_normal(3).tolist()))
+            plans.append(boxes)
+        lines = [str(len(plans))]
+        for boxes in plans:
+            lines.append(str(len(boxes)))
+            for mem, near, groups, sci, ctr in boxes:
+                lines.append(" ".join(map(str, [len(mem), *mem, len(near), *near, len(groups)]
+                                          + [v for g in groups for v in g] + [sci])) + " " +
+                             " ".join(repr(c) for c in ctr))
+        out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True,
+                             check=True).stdout.split("\n")
+        got = {}
+        for ln in out:
+            f = ln.split()
+            if f:
+                got[f[0]] = [float(v) for v in f[2:]] if f[0] != "nbox" else int(f[1])
+        allb = [b for boxes in plans for b in boxes]
+        exp = {"nbox": len(allb), "members": [], "near": [], "grp_col0": [], "grp_n": [], "grp_sci": [],
+               "box_sci": [], "centers": [], "box_off": [0], "near_off": [0], "grp_off": [0]}
+        for mem, near, groups, sci, ctr in allb:
+            exp["members"] += mem
+            exp["near"] += near
+            exp["grp_col0"] += [g[0] for g in groups]
+            exp["grp_n"] += [g[1] for g in groups]
+            exp["grp_sci"] += [g[2] for g in groups]
+            exp["box_sci"].append(sci)
+            exp["centers"] += ctr
+            exp["box_off"].append(len(exp["members"]))
+            exp["near_off"].append(len(exp["near"]))
+            exp["grp_off"].append(len(exp["grp_col0"]))
+        exp["cols"] = exp["members"]
+        assert got["nbox"] == exp["nbox"]
+        for k in exp:
+            if k != "nbox":
+                assert got[k] == [float(v) for v in exp[k]], (trial, k)
