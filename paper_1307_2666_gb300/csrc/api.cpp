@@ -275,42 +275,12 @@ static void check_status(hif_handle h) {
 // direct sum is a convolution.
 static void detect_grid(hif_handle h, Segment& sg) {
     sg.grid = false;
-    const int d = h->dim;
-    const int64_t N = sg.N;
-    const double* X = h->hx.data() + (size_t)d * sg.off;
-    const double* Wt = h->hw.data() + sg.off;
-    const int n = (int)std::llround(std::pow((double)N, 1.0 / d));
-    int64_t nn = 1;
-    for (int k = 0; k < d; ++k) nn *= n;
-    if (n < 2 || nn != N) return;
-    double lo[3], hx = 0;
-    for (int k = 0; k < d; ++k) {
-        double mn = X[k], mx = X[k];
-        for (int64_t i = 0; i < N; ++i) {
-            mn = std::min(mn, X[d * i + k]);
-            mx = std::max(mx, X[d * i + k]);
-        }
-        const double hk = (mx - mn) / (n - 1);
-        if (k == 0) hx = hk;
-        if (std::fabs(hk - hx) > 1e-12 * hx) return;
-        lo[k] = mn;
-    }
-    const double wv = Wt[0];
-    for (int64_t i = 0; i < N; ++i)
-        if (Wt[i] != wv) return;
-    if (std::fabs(std::pow(wv, 1.0 / d) - hx) > 1e-9 * hx) return;
-    std::vector<int> dof_of(N, -1);
-    for (int64_t i = 0; i < N; ++i) {
-        int64_t gpos = 0;
-        for (int k = 0; k < d; ++k) {
-            const double t = (X[d * i + k] - lo[k]) / hx;
-            const int64_t id = std::llround(t);
-            if (id < 0 || id >= n || std::fabs(t - id) > 1e-6) return;
-            gpos = gpos * n + id;
-        }
-        if (dof_of[gpos] != -1) return;
-        dof_of[gpos] = (int)(sg.off + i);
-    }
+    std::vector<int> dof_of;
+    int n = 0;
+    double hx = 0.0;
+    if (!grid_layout(h->hx.data() + (size_t)h->dim * sg.off, h->hw.data() + sg.off, sg.N, h->dim, sg.off, &n, &hx,
+                     dof_of))
+        return;
     sg.grid = true;
     sg.gn = n;
     sg.gh = hx;

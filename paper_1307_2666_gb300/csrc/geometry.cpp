@@ -370,6 +370,45 @@ void append_plan(SublevelPlan& p, SublevelPlan&& q) {
     p.nbox += q.nbox;
 }
 
+bool grid_layout(const double* X, const double* Wt, int64_t N, int d, int64_t off, int* n_out, double* h_out,
+                 std::vector<int>& dof_of) {
+    const int n = (int)std::llround(std::pow((double)N, 1.0 / d));
+    int64_t nn = 1;
+    for (int k = 0; k < d; ++k) nn *= n;
+    if (n < 2 || nn != N) return false;
+    double lo[3], hx = 0;
+    for (int k = 0; k < d; ++k) {
+        double mn = X[k], mx = X[k];
+        for (int64_t i = 0; i < N; ++i) {
+            mn = std::min(mn, X[d * i + k]);
+            mx = std::max(mx, X[d * i + k]);
+        }
+        const double hk = (mx - mn) / (n - 1);
+        if (k == 0) hx = hk;
+        if (std::fabs(hk - hx) > 1e-12 * hx) return false;
+        lo[k] = mn;
+    }
+    const double wv = Wt[0];
+    for (int64_t i = 0; i < N; ++i)
+        if (Wt[i] != wv) return false;
+    if (std::fabs(std::pow(wv, 1.0 / d) - hx) > 1e-9 * hx) return false;
+    dof_of.assign((size_t)N, -1);
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t gpos = 0;
+        for (int k = 0; k < d; ++k) {
+            const double t = (X[d * i + k] - lo[k]) / hx;
+            const int64_t id = std::llround(t);
+            if (id < 0 || id >= n || std::fabs(t - id) > 1e-6) return false;
+            gpos = gpos * n + id;
+        }
+        if (dof_of[gpos] != -1) return false;
+        dof_of[gpos] = (int)(off + i);
+    }
+    *n_out = n;
+    *h_out = hx;
+    return true;
+}
+
 void geometry_trace(bool on, double* ms) {
     if (ms)
         for (int q = 0; q < 6; ++q) ms[q] = g_geo_ms[q];

@@ -64,6 +64,14 @@ void build_near_groups(const Tree& t, const double* x, int s, double proxy_radiu
                        const std::vector<int>& box_of, const SciHost& sci, SublevelPlan& p,
                        NearCache* cache = nullptr);
 
+// Whether the N points (row-major, dim d) with weights Wt fill a full uniform
+// n^d grid of spacing h with cell volumes h^d (in any order); if so sets n, h
+// and dof_of[grid position] = off + point index (grid position: the first
+// coordinate slowest), the layout of the grid convolution (Sec. 3.1: K_ij
+// depends only on the offset).
+bool grid_layout(const double* X, const double* Wt, int64_t N, int d, int64_t off, int* n_out, double* h_out,
+                 std::vector<int>& dof_of);
+
 // Appends the plan q of the next problem of a batched handle to the combined
 // plan p (boxes, members, near fields and groups concatenated, offsets
 // shifted); the first problem's plan is moved in.

@@ -187,3 +187,52 @@ def test_batched_plans_concatenate(tmp_path):
         for k in exp:
             if k != "nbox":
                 assert got[k] == [float(v) for v in exp[k]], (trial, k)
+
+
+def test_uniform_grid_detection(tmp_path):
+    # the direct sum takes the grid convolution (and the tensor-core path)
+    # only for points that fill a full uniform n^d grid with cell volumes h^d,
+    # in any order; any other point set keeps the general sum
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = tmp_path / "grid"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(exe),
+                    os.path.join(ROOT, "tests", "grid_layout_driver.cpp"),
+                    os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")], check=True)
+
+    def run(pts, w, off=0):
+        N, d = pts.shape
+        inp = f"{N} {d} {off}\n" + " ".join(repr(float(v)) for v in pts.reshape(-1)) + "\n" + \
+            " ".join(repr(float(v)) for v in w) + "\n"
+        out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout.split()
+        if out[0] == "0":
+            return None
+        return int(out[1]), float(out[2]), np.array(out[3:], dtype=np.int64)
+
+    for n, d in [(8, 2), (5, 3), (2, 2)]:
+        pts, w = hi.grid_points(n, d)
+        r = run(pts, w, off=100)
+        assert r is not None and r[0] == n and r[1] == pytest.approx(1.0 / n, rel=1e-14)
+        np.testing.assert_array_equal(r[2], np.arange(n ** d) + 100)      # first coordinate slowest
+        perm = np.random.default_rng(n).permutation(n ** d)
+        r = run(pts[perm], w[perm])
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        np.testing.assert_array_equal(r[2], inv)                           # grid position -> permuted DOF
+    pts, w = hi.grid_points(8, 2)
+    h = 1.0 / 8
+    assert run(pts[:-1], w[:-1]) is None                                   # a point missing
+    p2 = pts.copy()
+    p2[5] += 1e-3 * h
+    assert run(p2, w) is None                                              # off the grid
+    p3 = pts.copy()
+    p3[7] = p3[8]
+    assert run(p3, w) is None                                              # two points in one cell
+    w2 = w.copy()
+    w2[3] *= 1.5
+    assert run(pts, w2) is None                                            # unequal weights
+    assert run(pts, 2.0 * w) is None                                       # weights are not h^d
+    p4 = pts.copy()
+    p4[:, 0] *= 2.0
+    assert run(p4, w) is None                                              # unequal spacing per axis
