@@ -35,18 +35,18 @@ def driver(tmp_path_factory):
     return str(out)
 
 
-def _replay(driver, pb, eps, c=None, occupancy=64):
+def _replay(driver, pb, eps, c=None, occupancy=64, second_kind=True):
     c = pb.c if c is None else c
     sets = []
     hifie.factor(pb.points, pb.weights, pb.a, pb.b, c, pb.kernel_id, eps, pb.proxy, occupancy=occupancy,
-                 trace_sets=sets)
+                 second_kind=second_kind, trace_sets=sets)
     subs = []                                   # the oracle's boxes, sublevel by sublevel
     for e in sets:
         if not subs or subs[-1][0] != (e[0], e[1]):
             subs.append(((e[0], e[1]), []))
         subs[-1][1].append(e)
     N, d = pb.points.shape
-    lines = [f"{N} {d} {occupancy} 1.5 1", " ".join(repr(float(v)) for v in pb.points.reshape(-1)),
+    lines = [f"{N} {d} {occupancy} 1.5 {1 if second_kind else 0}", " ".join(repr(float(v)) for v in pb.points.reshape(-1)),
              " ".join(repr(float(v)) for v in pb.weights), str(len(subs))]
     for _, boxes in subs:
         lines.append(str(len(boxes)))
@@ -84,10 +84,10 @@ def _parse(out):
     return tree, plan, subs
 
 
-@pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "2d-odd-cells", "3d", "3d-occ27",
-                                  "3d-n16"])
+@pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "2d-odd-cells", "2d-no-groups", "3d",
+                                  "3d-occ27", "3d-n16"])
 def test_host_plan_matches_oracle_sets(driver, case):
-    occ = 64
+    occ, second_kind = 64, True
     if case == "2d-symmetric":
         pb, c, eps = hi.volume_problem(32, 2, smooth_seed=21), None, 1e-6
     elif case == "2d-b-ne-c-ragged":
@@ -98,13 +98,16 @@ def test_host_plan_matches_oracle_sets(driver, case):
     elif case == "2d-odd-cells":
         # 5 x 5 DOFs per leaf cell: DOFs lie exactly on the proxy circles of the edges
         pb, c, eps = hi.volume_problem(40, 2, smooth_seed=26), None, 1e-6
+    elif case == "2d-no-groups":
+        # without the Sec. 4.4 modifications: one group per box
+        pb, c, eps, second_kind = hi.volume_problem(32, 2, smooth_seed=27), None, 1e-6, False
     elif case == "3d":
         pb, c, eps = hi.volume_problem(12, 3, smooth_seed=24), None, 1e-3
     elif case == "3d-occ27":
         pb, c, eps, occ = hi.volume_problem(12, 3, smooth_seed=5), None, 1e-3, 27
     else:
         pb, c, eps = hi.volume_problem(16, 3, smooth_seed=25), None, 1e-3
-    osubs, out = _replay(driver, pb, eps, c, occupancy=occ)
+    osubs, out = _replay(driver, pb, eps, c, occupancy=occ, second_kind=second_kind)
     tree, plan, csubs = _parse(out)
     # tree and sublevel sequence
     lo, W = hifie.root_box(pb.points, pb.weights)
@@ -127,7 +130,7 @@ def test_host_plan_matches_oracle_sets(driver, case):
             nbox += 1
             ngrp += len(groups)
     # the comparison covered SCI groups, not only single-group boxes
-    assert nbox > 20 and ngrp > nbox
+    assert nbox > 20 and (ngrp > nbox if second_kind else ngrp == nbox)
 
 
 def test_batched_plans_concatenate(tmp_path):
