@@ -39,6 +39,50 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def _declared_signatures():
+    """name -> list of parameter type strings, from the header's prototypes."""
+    text = ""
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text += re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", fn)).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(hif_[a-z_0-9]+)\s*\(([^)]*)\)\s*;",
+                         text, flags=re.M):
+        params = [p.strip() for p in " ".join(m.group(2).split()).split(",") if p.strip()]
+        out[m.group(1)] = [] if params == ["void"] else params
+    return out
+
+
+def _ctypes_kind(t):
+    # the C type a ctypes argtype stands for, coarsely: pointer, 8-byte integer,
+    # 4-byte integer, double, float
+    import ctypes as C
+    if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "ptr"
+    return {C.c_int64: "i64", C.c_uint64: "i64", C.c_int: "i32", C.c_int32: "i32", C.c_double: "f64",
+            C.c_float: "f32"}[t]
+
+
+def _c_kind(p):
+    if "*" in p:
+        return "ptr"
+    base = p.split()[0] if p.split()[0] != "const" else p.split()[1]
+    return {"int64_t": "i64", "uint64_t": "i64", "int": "i32", "int32_t": "i32", "double": "f64", "float": "f32",
+            "hif_handle": "ptr", "hif_status": "i32"}[base]
+
+
+def test_binding_signatures_match_header():
+    # every exported call takes, in the binding, as many arguments of the same
+    # kinds (pointer, 64-bit or 32-bit integer, double, float) as the header declares
+    from paper_1307_2666_gb300 import hif
+    sigs = _declared_signatures()
+    assert set(sigs) == set(_declared())
+    for name, params in sigs.items():
+        argtypes = hif.EXPORTS[name][1]
+        assert len(argtypes) == len(params), (name, params)
+        assert [_ctypes_kind(t) for t in argtypes] == [_c_kind(p) for p in params], (name, params)
+
+
 def test_binding_covers_header(lib):
     from paper_1307_2666_gb300 import hif
     for name in _declared():
