@@ -46,10 +46,10 @@ def _declared_signatures():
         if fn.endswith(".h"):
             text += re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", fn)).read(), flags=re.S)
     out = {}
-    for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(hif_[a-z_0-9]+)\s*\(([^)]*)\)\s*;",
+    for m in re.finditer(r"^\s*((?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?)\s*(hif_[a-z_0-9]+)\s*\(([^)]*)\)\s*;",
                          text, flags=re.M):
-        params = [p.strip() for p in " ".join(m.group(2).split()).split(",") if p.strip()]
-        out[m.group(1)] = [] if params == ["void"] else params
+        params = [p.strip() for p in " ".join(m.group(3).split()).split(",") if p.strip()]
+        out[m.group(2)] = (" ".join(m.group(1).split()), [] if params == ["void"] else params)
     return out
 
 
@@ -75,10 +75,13 @@ def test_binding_signatures_match_header():
     # every exported call takes, in the binding, as many arguments of the same
     # kinds (pointer, 64-bit or 32-bit integer, double, float) as the header declares
     from paper_1307_2666_gb300 import hif
+    import ctypes as C
     sigs = _declared_signatures()
     assert set(sigs) == set(_declared())
-    for name, params in sigs.items():
-        argtypes = hif.EXPORTS[name][1]
+    ret = {"hif_status": C.c_int, "const char*": C.c_char_p, "const char *": C.c_char_p, "uint64_t": C.c_uint64}
+    for name, (rtype, params) in sigs.items():
+        restype, argtypes = hif.EXPORTS[name]
+        assert restype is ret[rtype], (name, rtype)
         assert len(argtypes) == len(params), (name, params)
         assert [_ctypes_kind(t) for t in argtypes] == [_c_kind(p) for p in params], (name, params)
 
