@@ -239,3 +239,63 @@ def test_uniform_grid_detection(tmp_path):
     p4 = pts.copy()
     p4[:, 0] *= 2.0
     assert run(p4, w) is None                                              # unequal spacing per axis
+
+
+# planted mistakes in a copy of the planner: the replay must see each one
+PLANNER_MUTATIONS = [
+    ("proxy-boundary-included", "const double R2 = R * R * (1.0 - kTie);", "const double R2 = R * R * (1.0 + kTie);"),
+    ("inactive-sci-neighbours", "if (active[i] && box_of[i] != b && mark[i] != ep) {",
+     "if (box_of[i] != b && mark[i] != ep) {"),
+    ("upper-edge-candidates-missing", "jhi[k] = std::min(s - 1, c[k] + 2); }",
+     "jhi[k] = std::min(s - 1, c[k]); }"),
+    ("own-box-in-patterns", "if (active[i] && box_of[i] != b && mark[i] != ep) {",
+     "if (active[i] && mark[i] != ep) {"),
+    ("ties-to-highest-id", "if (cd2[e] <= lim && (best_id < 0 || cid[e] < best_id)) best_id = cid[e];",
+     "if (cd2[e] <= lim && (best_id < 0 || cid[e] > best_id)) best_id = cid[e];"),
+]
+
+
+def test_replay_sees_planted_planner_mistakes(tmp_path):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    import concurrent.futures as cf
+    src = open(os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")).read()
+    pb = hi.volume_problem(40, 2, smooth_seed=26)          # on-circle DOFs, SCI groups
+    c = pb.c * (1.0 + 0.5 * hi.smooth_field(pb.points, 28))
+
+    def build(name, text):
+        d = tmp_path / name
+        d.mkdir()
+        (d / "geometry.cpp").write_text(text)
+        exe = d / "replay"
+        subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off",
+                        "-I", os.path.join(ROOT, "paper_1307_2666_gb300", "csrc"), "-o", str(exe),
+                        os.path.join(ROOT, "tests", "plan_replay.cpp"), str(d / "geometry.cpp")], check=True)
+        return str(exe)
+
+    def matches(exe):
+        try:
+            osubs, out = _replay(exe, pb, 1e-6, c)
+        except subprocess.CalledProcessError:
+            return False                                  # the planted mistake broke the planner outright
+        _, _, csubs = _parse(out)
+        if [len(s[1]) for s in csubs] != [len(s[1]) for s in osubs]:
+            return False
+        for (_, oboxes), (_, cboxes) in zip(osubs, csubs):
+            for o, (mem, near, groups) in zip(oboxes, cboxes):
+                if not (np.array_equal(mem, o[2]) and np.array_equal(near, o[3]) and len(groups) == len(o[4])
+                        and all(np.array_equal(g, og) for g, og in zip(groups, o[4]))):
+                    return False
+        return True
+
+    cases = PLANNER_MUTATIONS
+    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+        exes = {name: ex.submit(build, name, src.replace(old, new, 1)) for name, old, new in cases}
+        exes["unplanted"] = ex.submit(build, "unplanted", src)
+        exes = {k: f.result() for k, f in exes.items()}
+    for name, old, _ in cases:
+        assert src.count(old) == 1, name
+    assert matches(exes["unplanted"])
+    for name, _, _ in cases:
+        assert not matches(exes[name]), f"planted planner mistake not seen: {name}"
