@@ -22,5 +22,14 @@ Everything is plain, slow FP64 numpy written from the paper:
 * ``krylov``   -- right-preconditioned restarted GMRES (Sec. 5) and the power
   iteration error estimates e_a, e_s (Sec. 5).
 * ``dense``    -- dense FP64 LU solve, the ground truth for small N.
+* ``helmholtz`` -- the Helmholtz / Lippmann-Schwinger operator of Sec. 5
+  Example 3 and its real 2 x 2 embedding, on which ``hifie`` runs unchanged.
+
+Every function is pinned by tests/test_oracle_pins*.py (closed forms,
+invariants, brute force, library routines), and tests/test_oracle_mutations.py
+plants mistakes that those pins must catch.  Parity unpinned: the factor
+values of single boxes (T, X, Y, L, U), which a rank decision within rounding
+of its threshold changes; they are compared only through the accuracy of F
+and F^{-1}.
 """
 from . import kernels, idqr, hifie, krylov, dense  # noqa: F401
