@@ -1,4 +1,4 @@
-// C ABI of the HIF-IE library: factorization driver (Algorithms 4.1 / 4.2),
+// C ABI of the HIF-IE library: host orchestration of the factorization (Algorithms 4.1 / 4.2),
 // apply / solve sweeps, FP64 direct-sum operator and refinement loops.
 //
 // The host runs the integer bookkeeping of each sublevel (geometry.cpp) and

@@ -2,7 +2,7 @@
 
 The planner (csrc/geometry.cpp: tree, partition into cells, edges and faces,
 near fields, column groups) runs on the host in the GPU path; here it is
-compiled with a small driver (tests/plan_replay.cpp) and fed the oracle's own
+compiled with a small harness (tests/plan_replay.cpp) and fed the oracle's own
 skeletonization decisions sublevel by sublevel, so that every plan can be
 compared with the oracle's index sets box by box: the root box and depth
 (Sec. 3.1 / 4.1), the sublevel sequence (Algorithms 4.1 / 4.2), and per box
@@ -24,7 +24,7 @@ KIND = {"cell": 0, "face": 1, "edge": 2}
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def harness(tmp_path_factory):
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("g++ not available")
@@ -35,7 +35,7 @@ def driver(tmp_path_factory):
     return str(out)
 
 
-def _replay(driver, pb, eps, c=None, occupancy=64, second_kind=True):
+def _replay(harness, pb, eps, c=None, occupancy=64, second_kind=True):
     c = pb.c if c is None else c
     sets = []
     hifie.factor(pb.points, pb.weights, pb.a, pb.b, c, pb.kernel_id, eps, pb.proxy, occupancy=occupancy,
@@ -53,7 +53,7 @@ def _replay(driver, pb, eps, c=None, occupancy=64, second_kind=True):
         for e in boxes:
             sk, rd = e[5], e[6]
             lines.append(" ".join(map(str, [sk.size, *sk.tolist(), rd.size, *rd.tolist()])))
-    r = subprocess.run([driver], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    r = subprocess.run([harness], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
     return subs, r.stdout.split("\n")
 
 
@@ -86,7 +86,7 @@ def _parse(out):
 
 @pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "2d-odd-cells", "2d-no-groups", "3d",
                                   "3d-occ27", "3d-n16"])
-def test_host_plan_matches_oracle_sets(driver, case):
+def test_host_plan_matches_oracle_sets(harness, case):
     occ, second_kind = 64, True
     if case == "2d-symmetric":
         pb, c, eps = hi.volume_problem(32, 2, smooth_seed=21), None, 1e-6
@@ -107,7 +107,7 @@ def test_host_plan_matches_oracle_sets(driver, case):
         pb, c, eps, occ = hi.volume_problem(12, 3, smooth_seed=5), None, 1e-3, 27
     else:
         pb, c, eps = hi.volume_problem(16, 3, smooth_seed=25), None, 1e-3
-    osubs, out = _replay(driver, pb, eps, c, occupancy=occ, second_kind=second_kind)
+    osubs, out = _replay(harness, pb, eps, c, occupancy=occ, second_kind=second_kind)
     tree, plan, csubs = _parse(out)
     # tree and sublevel sequence
     lo, W = hifie.root_box(pb.points, pb.weights)
@@ -143,7 +143,7 @@ def test_batched_plans_concatenate(tmp_path):
         pytest.skip("g++ not available")
     exe = tmp_path / "append"
     subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(exe),
-                    os.path.join(ROOT, "tests", "plan_append_driver.cpp"),
+                    os.path.join(ROOT, "tests", "plan_append_harness.cpp"),
                     os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")], check=True)
     rng = np.random.default_rng(3)
     for trial in range(40):
@@ -201,7 +201,7 @@ def test_uniform_grid_detection(tmp_path):
         pytest.skip("g++ not available")
     exe = tmp_path / "grid"
     subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(exe),
-                    os.path.join(ROOT, "tests", "grid_layout_driver.cpp"),
+                    os.path.join(ROOT, "tests", "grid_layout_harness.cpp"),
                     os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")], check=True)
 
     def run(pts, w, off=0):

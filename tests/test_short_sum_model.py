@@ -111,7 +111,7 @@ def test_library_spread_matches_the_model(tmp_path):
         pytest.skip("g++ not available")
     exe = tmp_path / "spread"
     subprocess.run([gxx, "-O1", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-o", str(exe),
-                    os.path.join(ROOT, "tests", "spread_driver.cpp"),
+                    os.path.join(ROOT, "tests", "spread_harness.cpp"),
                     os.path.join(ROOT, "paper_1307_2666_gb300", "csrc", "geometry.cpp")], check=True)
     cases = [(64, 2), (1024, 2), (16, 3), (64, 3)]
     inp = []
@@ -152,7 +152,7 @@ def test_refinement_digit_rule(tmp_path):
     # 8.19e-11; S = 12.65, |bKcu|/|f| = 2.1e-4), an FP64 solve, a tiny kernel
     # part, and the cases that must fall back to the full sum
     import subprocess
-    exe = _build(tmp_path, "rule", "refine_rule_driver.cpp", ["refine_rule.cpp"])
+    exe = _build(tmp_path, "rule", "refine_rule_harness.cpp", ["refine_rule.cpp"])
     C = _constants()
     SY = 12.65 * 2.1e-4
     tol = 1e-10
