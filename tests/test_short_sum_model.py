@@ -175,3 +175,67 @@ def test_refinement_digit_rule(tmp_path):
     got = list(map(int, out))
     assert C[0] * SY > 0.05 * tol and C[1] * SY <= 0.05 * tol       # the premise of the bench case
     assert got == [5, 6, 5, 8, 4, 8, 8, 1, 0, 0, 0, 1, 0]
+
+
+def test_refinement_with_short_residuals_on_the_oracle(tmp_path):
+    # reading 16 end to end on the CPU: the oracle's factorization (FP64,
+    # eps = 1e-4, one refinement step contracts by ~3e-7) refined with
+    # residuals from emulated short sums.  A residual's error enters the next
+    # one in full: with 4 classes the residual stalls at that sum's error
+    # (~2e-11 of |f|) until a full residual follows; the rule of the library
+    # (refine_rule.cpp, through its harness) refuses 4 classes here and takes
+    # 5, whose error (~8e-14 of |f|) stays far below tol, and the residuals
+    # then reach tol as with full sums
+    import subprocess
+    import hif_inputs as hi
+    from oracle import hifie, kernels
+    n = 32
+    pb = hi.volume_problem(n, 2, smooth_seed=1002, rhs_seed=1003)
+    T, S = _table(n, 2)
+    T = T * (1.0 / n) ** 2
+    T[0, 0] = kernels.self_integral(0, pb.weights[:1])[0]
+
+    def Ax(x, kd=8):
+        v = (pb.c * x).reshape(n, n)
+        if kd == 8:
+            y = _conv(T, v, n, 2)
+        else:
+            eT, eX = _scale_exp(np.abs(T).max()), _scale_exp(np.abs(v).max())
+            dT, dX = _digits(np.ldexp(T, -eT), kd), _digits(np.ldexp(v, -eX), kd)
+            y = sum(np.rint(_conv(dT[s], dX[t], n, 2)) * 2.0 ** (-8 * (s + t + 2))
+                    for s in range(kd) for t in range(kd - s)) * 2.0 ** (eT + eX)
+        return pb.a * x + pb.b * y.reshape(-1)
+
+    op = kernels.Operator(pb.points, pb.weights, pb.a, pb.b, pb.c, 0)
+    x = np.random.default_rng(0).standard_normal(op.N)
+    assert np.abs(Ax(x) - op.matvec(x)).max() <= 1e-14 * np.abs(op.matvec(x)).max()
+    F = hifie.factor(pb.points, pb.weights, pb.a, pb.b, pb.c, 0, 1e-4, pb.proxy)
+    f = pb.f[:, 0]
+    fn = np.linalg.norm(f)
+
+    def refine(schedule):
+        u, hist = F.solve(f), []
+        for kd in schedule:
+            hist.append(np.linalg.norm(f - Ax(u)) / fn)            # the true residual
+            u = u + F.solve(f - Ax(u, kd))
+        hist.append(np.linalg.norm(f - Ax(u)) / fn)
+        return hist
+
+    full = refine([8, 8, 8])
+    four = refine([4, 4, 8])
+    assert full[1] < 1e-12 and full[2] < 1e-15
+    assert four[1] > 1e2 * full[1] and four[2] > 1e3 * full[2]      # stalls at the 4-class error
+    assert four[3] < 1e-15                                           # until a full residual
+    # the rule, with the measured S Y, refuses 4 classes for the first residual and takes 5
+    u0 = F.solve(f)
+    Y = np.linalg.norm(Ax(u0) - pb.a * u0) / fn
+    r0 = np.linalg.norm(f - Ax(u0)) / fn
+    exe = _build(tmp_path, "rule", "refine_rule_harness.cpp", ["refine_rule.cpp"])
+    r0, SY = float(r0), float(S * Y)
+    q = [f"U 4 {r0!r} {SY!r} 1e-10 0", f"U 5 {r0!r} {SY!r} 1e-10 0"]
+    got = subprocess.run([exe], input="\n".join(q) + "\n", capture_output=True, text=True,
+                         check=True).stdout.split()
+    assert got == ["0", "1"]
+    five = refine([5, 5, 8])
+    assert five[1] < 0.05 * 1e-10 and five[2] < 0.05 * 1e-10     # its error, far below tol
+    assert five[3] < 1e-15
