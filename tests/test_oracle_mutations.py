@@ -130,6 +130,21 @@ MUTATIONS = [
     ("power-norm-E-E-instead-of-Et-E", "krylov.py", "power_norm",
      "w = apply_op_t(apply_op(v))", "w = apply_op(apply_op(v))",
      [P + "test_error_estimates_match_dense_two_norms"]),
+    ("self-term-3d-sign", "kernels.py", "self_integral",
+     "(3.0 * math.log(2.0 + math.sqrt(3.0)) - 0.5 * math.pi)", "(3.0 * math.log(2.0 + math.sqrt(3.0)) + 0.5 * math.pi)",
+     [P + "test_self_cell_3d_matches_quadrature"]),
+    ("ldl-schur-divides-by-D", "hifie.py", "_skeletonize",
+     "delta = -(X * Dg[None, :]) @ X.T", "delta = -(X / Dg[None, :]) @ X.T",
+     [P + "test_ldl_factor_equals_lu_factor"]),
+    ("apply-top-block-transposed", "hifie.py", "HIFFactor.apply",
+     "x[self.top] = self.top_A @ x[self.top]", "x[self.top] = self.top_A.T @ x[self.top]",
+     [P + "test_sweeps_match_product_formula_eq_4_1"]),
+    ("gmres-givens-sign", "krylov.py", "gmres",
+     "g[j + 1] = -sn[j] * g[j]", "g[j + 1] = sn[j] * g[j]",
+     [P + "test_gmres_lemma_5_1_iteration_bound"]),
+    ("helmholtz-self-term-sign", "helmholtz.py", "self_integral_helmholtz",
+     "re = part(lambda r: -0.25 * ss.y0(k * r))", "re = part(lambda r: 0.25 * ss.y0(k * r))",
+     [PH + "test_self_integral_small_k_limit"]),
     ("helmholtz-block-convention", "helmholtz.py", "EmbeddedOperator.kernel_entries",
      "return np.where(ra == cb, Z.real, np.where(ra == 1, Z.imag, -Z.imag))",
      "return np.where(ra == cb, Z.real, np.where(ra == 1, -Z.imag, Z.imag))",
