@@ -84,8 +84,8 @@ def _parse(out):
     return tree, plan, subs
 
 
-@pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "2d-odd-cells", "2d-no-groups", "3d",
-                                  "3d-occ27", "3d-n16"])
+@pytest.mark.parametrize("case", ["2d-symmetric", "2d-b-ne-c-ragged", "2d-n64", "2d-odd-cells", "2d-no-groups",
+                                  "2d-jittered", "3d", "3d-occ27", "3d-n16"])
 def test_host_plan_matches_oracle_sets(harness, case):
     occ, second_kind = 64, True
     if case == "2d-symmetric":
@@ -101,6 +101,10 @@ def test_host_plan_matches_oracle_sets(harness, case):
     elif case == "2d-no-groups":
         # without the Sec. 4.4 modifications: one group per box
         pb, c, eps, second_kind = hi.volume_problem(32, 2, smooth_seed=27), None, 1e-6, False
+    elif case == "2d-jittered":
+        # points off the grid (uniform jitter of up to 0.3 h): no exact ties anywhere
+        pb, c, eps = hi.volume_problem(32, 2, smooth_seed=29), None, 1e-6
+        pb.points = pb.points + 0.3 / 32 * (np.random.default_rng(29).uniform(size=pb.points.shape) - 0.5)
     elif case == "3d":
         pb, c, eps = hi.volume_problem(12, 3, smooth_seed=24), None, 1e-3
     elif case == "3d-occ27":
