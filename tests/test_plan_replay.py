@@ -303,3 +303,28 @@ def test_replay_sees_planted_planner_mistakes(tmp_path):
     assert matches(exes["unplanted"])
     for name, _, _ in cases:
         assert not matches(exes[name]), f"planted planner mistake not seen: {name}"
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_plan_random_configurations(harness, seed):
+    # random sizes, occupancies, coefficients and (for some) off-grid points:
+    # the planner's sets equal the oracle's for every box
+    rng = np.random.default_rng(100 + seed)
+    dim = 2 if seed < 4 else 3
+    n = int(rng.integers(16, 41)) if dim == 2 else int(rng.integers(6, 11))
+    occ = int(rng.choice([16, 27, 64]))
+    pb = hi.volume_problem(n, dim, smooth_seed=200 + seed)
+    c = pb.c * (1.0 + 0.4 * hi.smooth_field(pb.points, 300 + seed)) if seed % 2 else None
+    if seed in (2, 5):
+        pb.points = pb.points + 0.2 / n * (rng.uniform(size=pb.points.shape) - 0.5)
+    osubs, out = _replay(harness, pb, 1e-4, c, occupancy=occ)
+    tree, plan, csubs = _parse(out)
+    assert [s[0] for s in csubs] == [(KIND[k], l) for (k, l), _ in osubs]
+    for (_, oboxes), (_, cboxes) in zip(osubs, csubs):
+        assert len(cboxes) == len(oboxes)
+        for o, (mem, near, groups) in zip(oboxes, cboxes):
+            np.testing.assert_array_equal(mem, o[2])
+            np.testing.assert_array_equal(near, o[3])
+            assert len(groups) == len(o[4])
+            for g, og in zip(groups, o[4]):
+                np.testing.assert_array_equal(g, og)
